@@ -1,0 +1,142 @@
+"""Newton-Raphson backward-Euler step, Delta-t ramp and coarse-to-fine steady continuation.
+
+* ``step``: one implicit step k -> k+1 of eq. 7 (with eqs. 8-13), solved by
+  Newton-Raphson (Sec. 2): linearise into eq. 14, solve J du = -F by multigrid,
+  u += du, until every field's scale-free residual rho_f <= tol.  The step is
+  rejected when Newton needs more than ``max_newton`` iterations (the paper
+  observed fewer than 10), when max |dV| exceeds ``corr_limit`` (the "upper
+  limit" on the Newton correction norm of Sec. 2, read as 0.5 |V_cathode|), when
+  the linear solve fails, or on non-finite values.
+* ``march``: Delta t_1, then Delta t_{k+1} = n Delta t_k (n = 5) capped at dt_max;
+  after a rejection go back and retry with the previous accepted Delta t, and
+  halve it if that fails as well (Sec. 2 says "go back and choose
+  Delta t_{k+1} = Delta t_k"; the halving is this project's addition).  Stops
+  when the steady residual (time term dropped) is <= tol.
+* ``solve_steady``: the "multilevel prolongation" of Sec. 2 / abstract: steady
+  state on the grid coarsened by two, prolonged bilinearly to the fine grid,
+  then the fine march starts with the long step dt_max.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+from . import discretization as disc
+from . import multigrid as mg
+from .grid import Grid
+
+
+@dataclasses.dataclass
+class SolverOptions:
+    nu1: int = 2
+    nu2: int = 2
+    eta: float = 1e-3               # inexact-Newton linear tolerance
+    max_vcycles: int = 60
+    coarsest: int = 4
+    max_newton: int = 10
+    corr_limit_frac: float = 0.5    # reject if max|dV| > frac * |V_cathode|
+    dt1: float = 1e-9
+    dt_growth: float = 5.0
+    dt_max: float = 1e-6
+    max_steps: int = 400
+    newton_tol: Optional[float] = None   # per-step Newton tolerance; default 0.1 * steady tol
+
+
+@dataclasses.dataclass
+class StepStats:
+    accepted: bool
+    newton: int
+    vcycles: List[int]
+    rho: np.ndarray
+    reason: str = ""
+
+
+def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: float,
+         opt: SolverOptions):
+    """One backward-Euler step; returns (u_new, StepStats).  u is not modified."""
+    u_old = u
+    x = disc.apply_dirichlet(u, phys)
+    vcyc = []
+    limit = opt.corr_limit_frac * abs(phys.V_cathode)
+    for it in range(opt.max_newton + 1):
+        F, T = disc.residual(g, x, u_old, S_e, S_p, dt, phys, with_terms=True)
+        r = disc.rho(F, T)
+        if not np.all(np.isfinite(r)):
+            return u, StepStats(False, it, vcyc, r, "nonfinite")
+        if r.max() <= tol:
+            return x, StepStats(True, it, vcyc, r)
+        if it == opt.max_newton:
+            break
+        H = mg.Hierarchy(g, x, dt, phys, opt.coarsest, opt.nu1, opt.nu2)
+        tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+        du, hist = H.solve(-disc.to_vec(g, F), opt.eta, opt.max_vcycles, scale=tn)
+        vcyc.append(len(hist) - 1)
+        if not np.isfinite(hist[-1]) or hist[-1] > opt.eta:
+            return u, StepStats(False, it + 1, vcyc, r, "linear solve failed")
+        d = disc.from_vec(g, du)
+        if np.abs(d[2]).max() > limit:
+            return u, StepStats(False, it + 1, vcyc, r, "correction limit")
+        x = x + d
+    return u, StepStats(False, opt.max_newton, vcyc, r, "newton cap")
+
+
+def steady_rho(g: Grid, u, S_e, S_p, phys):
+    F, T = disc.residual(g, u, None, S_e, S_p, None, phys, with_terms=True)
+    return disc.rho(F, T)
+
+
+def march(g: Grid, u, S_e, S_p, phys, tol, opt: SolverOptions, dt_start: float, log=None):
+    """Time-march with the Delta-t ramp until the steady residual <= tol.
+
+    Returns (u, converged, records) where records lists (dt, accepted, newton, vcycles, steady_rho).
+    """
+    dt = dt_start
+    dt_prev = None
+    records = []
+    newton_tol = 0.1 * tol if opt.newton_tol is None else opt.newton_tol
+    for _ in range(opt.max_steps):
+        u_new, st = step(g, u, S_e, S_p, dt, phys, newton_tol, opt)
+        if st.accepted:
+            u = u_new
+            rs = steady_rho(g, u, S_e, S_p, phys)
+            records.append((dt, True, st.newton, sum(st.vcycles), rs.max()))
+            if log:
+                log(records[-1])
+            if rs.max() <= tol:
+                return u, True, records
+            dt_prev = dt
+            dt = min(dt * opt.dt_growth, opt.dt_max)
+        else:
+            records.append((dt, False, st.newton, sum(st.vcycles), np.nan))
+            if log:
+                log(records[-1] + (st.reason,))
+            if dt_prev is not None and dt > dt_prev:
+                dt = dt_prev
+            else:
+                dt = 0.5 * dt
+                dt_prev = None if dt_prev is None else min(dt_prev, dt)
+    return u, False, records
+
+
+def prolong_state(gc: Grid, gf: Grid, uc: np.ndarray) -> np.ndarray:
+    """Bilinear interpolation of node arrays (3, ...) from gc to the nested finer gf."""
+    out = np.zeros((uc.shape[0],) + gf.shape)
+    out[:, ::2, ::2] = uc
+    out[:, ::2, 1::2] = 0.5 * (uc[:, :, :-1] + uc[:, :, 1:])
+    w1 = (gf.z[1::2] - gc.z[:-1]) / (gc.z[1:] - gc.z[:-1])
+    out[:, 1::2, :] = (1.0 - w1)[None, :, None] * out[:, 0:-1:2, :] + w1[None, :, None] * out[:, 2::2, :]
+    return out
+
+
+def solve_steady(g: Grid, u0, S_e, S_p, phys, tol, opt: SolverOptions, log=None):
+    """Coarse (N/2) steady solve from u0 injected, prolong, fine steady solve from dt_max."""
+    gc = g.coarse()
+    uc = disc.apply_dirichlet(mg.inject(g, u0), phys)
+    uc, okc, rec_c = march(gc, uc, mg.inject(g, S_e), mg.inject(g, S_p), phys, tol, opt, opt.dt1, log)
+    if not okc:
+        return u0, False, rec_c, []
+    uf = disc.apply_dirichlet(prolong_state(gc, g, uc), phys)
+    uf, okf, rec_f = march(g, uf, S_e, S_p, phys, tol, opt, opt.dt_max, log)
+    return uf, okf, rec_c, rec_f

@@ -1,0 +1,201 @@
+"""Pins for the discrete fluxes, residual and Jacobian of the oracle (eqs. 3-14).
+
+Each check compares against something fixed by the paper or by mathematics,
+not against a retyped copy of the oracle's own formula:
+* SG flux: exact for 1-D constant-field constant-flux drift-diffusion, and its
+  alpha -> 0 limit is the central drift-diffusion flux of eqs. 3-4 (this fixes
+  the G/F pairing of eq. 9, printed there as G/G);
+* Poisson rows divided by A/dr^2 reproduce the printed coefficients of eq. 12
+  (interior) and eq. 13 (axis);
+* the flux divergence telescopes: summed over all rows it equals the net flux
+  through the electrode faces (discrete charge balance / Gauss law);
+* the Jacobian matches central finite differences of the residual;
+* manufactured cylindrical Poisson solution converges at second order.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import bernoulli as bn
+from oracle import discretization as disc
+from oracle.grid import Grid
+
+
+def _grid(n, nz=None, ratio=1.05):
+    nz = n if nz is None else nz
+    return Grid(n, nz, 1e-2, W.z_nodes(nz, 1e-2, ratio_ref=ratio))
+
+
+# ---------------------------------------------------------------- SG flux (eqs. 8-11)
+@pytest.mark.parametrize("s", [-1.0, 1.0])
+@pytest.mark.parametrize("E", [-3e4, -50.0, 1e-3, 2e2, 5e5])
+def test_sg_flux_exact_for_constant_field(s, E):
+    # phi = s mu E n - D dn/dx = phi0 has n(x) = phi0/(s mu E) + C exp(s mu E x / D)
+    mu, D, h, phi0, C = 0.15, 0.0038, 3e-5, 2.5e18, 4e13
+    k = s * mu * E / D
+    n = lambda x: phi0 / (s * mu * E) + C * np.exp(k * x)
+    VL, VR = 0.0, -E * h            # E = -(V_R - V_L)/h
+    got = disc.sg_flux(1.0 / h, mu, D, s, n(0.0), n(h), VL, VR)
+    assert abs(got - phi0) <= 1e-9 * abs(phi0) + 1e-12 * abs(C * D / h * max(1, np.exp(k * h))), (got, phi0)
+
+
+@pytest.mark.parametrize("s", [-1.0, 1.0])
+def test_sg_flux_small_alpha_limit_is_central_drift_diffusion(s):
+    mu, D, h = 30.0, 60.0, 1e-4
+    nL, nR = 3e15, 1e15
+    errs = []
+    for dV in (1e-2, 5e-3, 2.5e-3, 1.25e-3):
+        VL, VR = 0.0, dV
+        E = -(VR - VL) / h
+        central = s * mu * E * 0.5 * (nL + nR) - D * (nR - nL) / h      # eqs. 3-4
+        sg = disc.sg_flux(1.0 / h, mu, D, s, nL, nR, VL, VR)
+        errs.append(abs(sg - central) / abs(central))
+        # the printed G/G pairing carries no drift: for uniform n it gives zero flux
+        a = -s * (mu / D) * (VR - VL)
+        nu = 2e15
+        gg = (D / h) * (nu * bn.G(np.array([a]))[0] - nu * bn.G(np.array([a]))[0])
+        drift = s * mu * E * nu
+        assert gg == 0.0 and abs(drift) > 0
+        assert np.isclose(disc.sg_flux(1.0 / h, mu, D, s, nu, nu, VL, VR), drift, rtol=1e-12)
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(ratios > 3.5) and np.all(ratios < 4.5), errs    # O(alpha^2)
+
+
+# ---------------------------------------------------------------- Poisson rows (eqs. 12-13)
+def test_poisson_rows_reproduce_eq12_and_eq13():
+    g = _grid(8)
+    u = np.zeros((3,) + g.shape)
+    J = disc.jacobian(g, u, None, disc.Physics()).toarray()
+    idx = g.node_index()
+    kap = disc.E_CHARGE / disc.EPS0
+    dr, dz = g.dr, g.dz
+    for j in range(1, g.nz):
+        dzm, dzp = dz[j - 1], dz[j]
+        dzc = 0.5 * (dzm + dzp)          # the control width written delta z_{j-1/2} in eq. 12
+        for i in range(0, g.nr):         # the outer wall row is the half cell (not in eq. 12)
+            row = 3 * idx[j, i] + 2
+            scale = g.A[j, i] / dr ** 2
+            c = lambda jj, ii, f=2: J[row, 3 * idx[jj, ii] + f] / scale if idx[jj, ii] >= 0 else None
+            zc = dr ** 2 * (dzm + dzp) / (dzc * dzm * dzp)
+            if i == 0:     # eq. 13
+                assert np.isclose(c(j, 0), -4.0 - zc, rtol=1e-13)
+                assert np.isclose(c(j, 1), 4.0, rtol=1e-13)
+            else:          # eq. 12
+                assert np.isclose(c(j, i), -2.0 - zc, rtol=1e-13)
+                assert np.isclose(c(j, i - 1), 1.0 - 1.0 / (2 * i), rtol=1e-13)
+                assert np.isclose(c(j, i + 1), 1.0 + 1.0 / (2 * i), rtol=1e-13)
+            if j > 1:
+                assert np.isclose(c(j - 1, i), dr ** 2 / (dzc * dzm), rtol=1e-13)
+            if j < g.nz - 1:
+                assert np.isclose(c(j + 1, i), dr ** 2 / (dzc * dzp), rtol=1e-13)
+            assert np.isclose(c(j, i, 0), -kap * dr ** 2, rtol=1e-13)
+            assert np.isclose(c(j, i, 1), kap * dr ** 2, rtol=1e-13)
+
+
+def _mms_error(n):
+    R = d = 1e-2
+    g = _grid(n)
+    rr, zz = np.meshgrid(g.r, g.z)
+    Vex = np.sin(np.pi * zz / d) * (1 - rr ** 2 / R ** 2) ** 2
+    lap = np.sin(np.pi * zz / d) * (-8 / R ** 2 + 16 * rr ** 2 / R ** 4) \
+        - (np.pi / d) ** 2 * Vex
+    phys = disc.Physics(V_cathode=0.0, V_anode=0.0, mu_e=0.0, mu_p=0.0)
+    u = np.zeros((3,) + g.shape)
+    u[1] = -lap / disc.KAPPA                    # kappa (n_p - n_e) = -lap V
+    F = disc.residual(g, u, None, 0 * rr, 0 * rr, None, phys)
+    J = disc.jacobian(g, u, None, phys)
+    Jvv = J[2::3, 2::3]
+    V = spla.spsolve(Jvv.tocsc(), -disc.to_vec(g, F)[2::3])
+    Vh = np.zeros(g.shape)
+    Vh[1:-1] = V.reshape(g.nz - 1, g.nr + 1)
+    return np.abs(Vh - Vex).max()
+
+
+def test_manufactured_cylindrical_poisson_second_order():
+    errs = [_mms_error(n) for n in (16, 32, 64, 128)]
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(ratios > 3.5) and np.all(ratios < 4.6), (errs, ratios)
+
+
+# ---------------------------------------------------------------- conservation
+def _random_state(g, rng, V_c=-200.0):
+    u = np.zeros((3,) + g.shape)
+    u[0] = 1e14 * (1 + rng.random(g.shape))
+    u[1] = 1e14 * (1 + rng.random(g.shape))
+    rr, zz = np.meshgrid(g.r, g.z)
+    u[2] = V_c * (1 - zz / g.z[-1]) + 5 * rng.standard_normal(g.shape)
+    return disc.apply_dirichlet(u, disc.Physics(V_cathode=V_c))
+
+
+@pytest.mark.parametrize("table", [False, True])
+def test_flux_divergence_telescopes_to_electrode_flux(table):
+    rng = np.random.default_rng(7)
+    g = _grid(16, 32)
+    phys = disc.Physics(table=W.transport_table(2) if table else None, pressure_factor=1.3)
+    u = _random_state(g, rng)
+    S = 1e20 * rng.random(g.shape)
+    zero = np.zeros(g.shape)
+    F = disc.residual(g, u, None, S, S, None, phys)
+    (mer, der, mpr, dpr), (mez, dez, mpz, dpz) = disc.face_transport(g, u[2], phys)
+    for fi, s, mu, D in ((0, -1.0, mez, dez), (1, 1.0, mpz, dpz)):
+        n, V = u[fi], u[2]
+        # flux leaving through the cathode face (j = 1/2, outward = toward -z) and the anode face
+        cath = disc.sg_flux(g.gz[0], mu[0], D[0], s, n[0], n[1], V[0], V[1])
+        anod = disc.sg_flux(g.gz[-1], mu[-1], D[-1], s, n[-2], n[-1], V[-2], V[-1])
+        net_out = anod.sum() - cath.sum()
+        lhs = (F[fi, 1:-1] + g.A[1:-1] * S[1:-1]).sum()
+        assert np.isclose(lhs, net_out, rtol=1e-10, atol=1e-12 * np.abs(F[fi]).sum()), (lhs, net_out)
+    # discrete Gauss law: sum of Poisson rows = electrode-face field flux + enclosed charge
+    V = u[2]
+    gauss = (g.gz[-1] * (V[-1] - V[-2])).sum() - (g.gz[0] * (V[1] - V[0])).sum()
+    charge = (g.A[1:-1] * disc.KAPPA * (u[1, 1:-1] - u[0, 1:-1])).sum()
+    assert np.isclose(F[2, 1:-1].sum(), gauss + charge, rtol=1e-10)
+    del zero
+
+
+def test_time_term_volume_weighting():
+    # uniform change of n with no flux change: F = A dn/dt summed = total volume * dn/dt
+    g = _grid(8)
+    u = np.zeros((3,) + g.shape)
+    u_old = u.copy()
+    u[0, 1:-1] = 2.0
+    phys = disc.Physics(mu_e=0.0, D_e=1e-300, mu_p=0.0, D_p=1e-300, V_cathode=0.0)
+    F = disc.residual(g, u, u_old, 0 * u[0], 0 * u[0], 0.5, phys)
+    vol_rows = np.pi * g.R ** 2 / (2 * np.pi) * (g.z[-1] - g.z[0] - 0.5 * (g.dz[0] + g.dz[-1]))
+    assert np.isclose(F[0, 1:-1].sum(), 4.0 * vol_rows, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- Jacobian
+@pytest.mark.parametrize("dt", [1e-9, None])
+def test_jacobian_matches_finite_differences(dt):
+    rng = np.random.default_rng(3)
+    g = _grid(8)
+    phys = disc.Physics()
+    u = _random_state(g, rng)
+    u_old = _random_state(g, rng)
+    S = 1e20 * rng.random(g.shape)
+    J = disc.jacobian(g, u, dt, phys)
+    F0 = lambda x: disc.to_vec(g, disc.residual(g, x, u_old, S, S, dt, phys))
+    for _ in range(4):
+        v = disc.from_vec(g, rng.standard_normal(3 * g.n_nodes_unknown))
+        v[0:2] *= 1e12
+        eps = 1e-4
+        fd = (F0(u + eps * v) - F0(u - eps * v)) / (2 * eps)
+        jv = J @ disc.to_vec(g, v)
+        for f in range(3):
+            a, b = fd[f::3], jv[f::3]
+            assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), (f, np.linalg.norm(a - b), np.linalg.norm(b))
+
+
+def test_block_structure_of_eq14():
+    # 3x3 diagonal block has 7 structural nonzeros, off-diagonal blocks 5 (eq. 14)
+    rng = np.random.default_rng(5)
+    g = _grid(8)
+    J = disc.jacobian(g, _random_state(g, rng), 1e-9, disc.Physics()).toarray()
+    k = g.node_index()[4, 4]
+    kn = g.node_index()[4, 5]
+    diag = J[3 * k:3 * k + 3, 3 * k:3 * k + 3]
+    off = J[3 * k:3 * k + 3, 3 * kn:3 * kn + 3]
+    assert (diag != 0).sum() == 7 and diag[0, 1] == 0 and diag[1, 0] == 0
+    assert (off != 0).sum() == 5 and off[2, 0] == 0 and off[2, 1] == 0

@@ -1,0 +1,142 @@
+"""Pins for the oracle's Newton time step, Delta-t ramp and steady continuation (Sec. 2).
+
+* a Newton step solved with V-cycles equals the same step solved with a direct
+  dense solve of eq. 14 (single-level hierarchy);
+* with mu = 0 the system is linear, so exact Newton converges in one iteration;
+* the paper's run statistics: fewer than 10 Newton iterations per step;
+* a steady state is a fixed point of the implicit step for any dt;
+* the Delta-t ramp follows Delta t_{k+1} = 5 Delta t_k from 1 ns (the values printed
+  in Sec. 2, stored under tests/golden/) and goes back to the previous Delta t after a
+  forced rejection;
+* the state prolongation of the continuation is exact for bilinear functions.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import discretization as disc
+from oracle import multigrid as mg
+from oracle import solver as so
+from oracle.grid import Grid
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _case(n=16, V_c=-200.0, table=False, seed=0):
+    d = W.make_discharge(n, seed=seed, V_cathode=V_c, use_table=table)
+    g = Grid(d.nr, d.nz, d.R, d.z)
+    phys = disc.Physics(V_cathode=d.V_cathode, table=d.table)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    return d, g, phys, u
+
+
+def test_paper_printed_driver_constants():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as fh:
+        pc = json.load(fh)
+    opt = so.SolverOptions()
+    assert opt.dt1 == pc["dt1_s"]["value"]
+    assert opt.dt_growth == pc["dt_growth_n"]["value"]
+    assert opt.max_newton == pc["newton_iterations_below"]["value"]
+
+
+def test_mg_step_equals_direct_step():
+    d, g, phys, u = _case(16)
+    opt_mg = so.SolverOptions(eta=1e-13)
+    opt_lu = so.SolverOptions(eta=1e-13, coarsest=10 ** 6)   # one level: dense LU
+    a, sa = so.step(g, u, d.S_e, d.S_p, 1e-9, phys, 1e-12, opt_mg)
+    b, sb = so.step(g, u, d.S_e, d.S_p, 1e-9, phys, 1e-12, opt_lu)
+    assert sa.accepted and sb.accepted
+    for f in range(3):
+        assert np.abs(a[f] - b[f]).max() <= 1e-11 * np.abs(b[f]).max()
+
+
+def test_linear_case_newton_converges_in_one_iteration():
+    d, g, phys, u = _case(16)
+    phys.mu_e = 0.0
+    phys.mu_p = 0.0
+    opt = so.SolverOptions(eta=1e-14, max_vcycles=200)
+    _, st = so.step(g, u, d.S_e, d.S_p, 1e-8, phys, 1e-12, opt)
+    assert st.accepted and st.newton == 1, st
+
+
+def test_transient_33_newton_iterations_below_ten():
+    d = W.transient_33()
+    g = Grid(d.nr, d.nz, d.R, d.z)
+    phys = disc.Physics(V_cathode=d.V_cathode)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    opt = so.SolverOptions(eta=1e-12)
+    for _ in range(3):
+        u, st = so.step(g, u, d.S_e, d.S_p, 1e-9, phys, 1e-10, opt)
+        assert st.accepted and st.newton < 10 and st.rho.max() <= 1e-10
+
+
+def test_steady_state_is_fixed_point_of_the_step():
+    d, g, phys, u = _case(16, V_c=-300.0, table=True)
+    opt = so.SolverOptions(eta=1e-6)
+    us, ok, rec = so.march(g, u, d.S_e, d.S_p, phys, 1e-10, opt, 1e-9)
+    assert ok
+    for dt in (1e-9, 1e-6, 1e-3):
+        F, T = disc.residual(g, us, us, d.S_e, d.S_p, dt, phys, with_terms=True)
+        assert disc.rho(F, T).max() <= 1e-9
+
+
+def test_dt_ramp_and_rejection():
+    d, g, phys, u = _case(8, V_c=-300.0)
+    opt = so.SolverOptions(eta=1e-6, dt_max=1e-7, max_steps=6, newton_tol=1e-8)
+    _, _, rec = so.march(g, u, d.S_e, d.S_p, phys, 1e-30, opt, 1e-9)
+    dts = [r[0] for r in rec if r[1]]
+    assert np.allclose(dts[:4], [1e-9, 5e-9, 2.5e-8, 1e-7])
+    # force a rejection at the first step with a correction limit of ~0: the ramp halves dt
+    opt2 = so.SolverOptions(eta=1e-6, corr_limit_frac=1e-12, max_steps=3, newton_tol=1e-8)
+    _, ok, rec2 = so.march(g, u, d.S_e, d.S_p, phys, 1e-30, opt2, 1e-9)
+    assert not ok and [r[1] for r in rec2] == [False] * 3
+    assert np.allclose([r[0] for r in rec2], [1e-9, 5e-10, 2.5e-10])
+
+
+def test_rejected_step_goes_back_to_previous_dt():
+    d, g, phys, u = _case(8, V_c=-300.0)
+    calls = []
+    real_step = so.step
+
+    def fake_step(g_, u_, Se, Sp, dt, ph, tol, opt):
+        calls.append(dt)
+        if len(calls) == 3:            # third attempt (dt = 2.5e-8) is rejected
+            return u_, so.StepStats(False, 1, [1], np.zeros(3), "forced")
+        return real_step(g_, u_, Se, Sp, dt, ph, tol, opt)
+
+    so.step = fake_step
+    try:
+        so.march(g, u, d.S_e, d.S_p, phys, 1e-30, so.SolverOptions(eta=1e-6, max_steps=5, newton_tol=1e-8), 1e-9)
+    finally:
+        so.step = real_step
+    assert np.allclose(calls[:5], [1e-9, 5e-9, 2.5e-8, 5e-9, 2.5e-8])
+
+
+def test_prolong_state_exact_for_bilinear():
+    gf = Grid(16, 16, 1e-2, W.z_nodes(16, 1e-2))
+    gc = gf.coarse()
+    f = lambda r, z: 1.0 - 2.0 * r / 1e-2 + 0.5 * z / 1e-2 + 3.0 * r * z / 1e-4
+    rc, zc = np.meshgrid(gc.r, gc.z)
+    rf, zf = np.meshgrid(gf.r, gf.z)
+    out = so.prolong_state(gc, gf, np.stack([f(rc, zc)] * 3))
+    assert np.allclose(out, np.stack([f(rf, zf)] * 3), rtol=1e-13, atol=1e-13)
+
+
+def test_transient_33_regression_golden():
+    """Regression against values written by tests/golden/make_golden.py (oracle only)."""
+    with open(os.path.join(GOLDEN, "oracle_transient_33.json")) as fh:
+        gold = json.load(fh)
+    d = W.transient_33()
+    g = Grid(d.nr, d.nz, d.R, d.z)
+    phys = disc.Physics(V_cathode=d.V_cathode)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    opt = so.SolverOptions(eta=1e-12)
+    for _ in range(gold["steps"]):
+        u, st = so.step(g, u, d.S_e, d.S_p, gold["dt"], phys, gold["tol"], opt)
+        assert st.accepted
+    for k, name in enumerate(("ne", "np", "V")):
+        assert np.isclose(np.abs(u[k]).sum(), gold[name + "_l1"], rtol=1e-10)
+        assert np.isclose(u[k][gold["probe_j"], gold["probe_i"]], gold[name + "_probe"], rtol=1e-10)
