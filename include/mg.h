@@ -1,0 +1,208 @@
+/*
+ * mg.h - C ABI of the GB300 (sm_103a) multigrid solver for the axisymmetric
+ * drift-diffusion + Poisson fluid equations of Ristivojevic & Petrovic,
+ * "Multigrid solver for axisymmetrical 2D fluid equations" (arXiv:0811.4446).
+ *
+ * Problem (Sec. 2 of the paper):
+ *   continuity       dn/dt + div(n v) = S             (eqs. 1-2), electrons and ions
+ *   fluxes           phi_e = -n_e mu_e E - D_e grad n_e,  phi_p = n_p mu_p E - D_p grad n_p (eqs. 3-4)
+ *   Poisson          lap V = -(e/eps0)(n_p - n_e),  E = -grad V                 (eqs. 5-6)
+ * on (r, z) in [0, R] x [0, d], azimuthal symmetry, nodes r_i = i R/N_r and a
+ * caller-given non-equidistant z_0 < ... < z_Nz.  Discretisation: backward Euler
+ * (eq. 7), Scharfetter-Gummel face fluxes (eqs. 8-11; eq. 9 read with the G/F
+ * pairing of eq. 8), finite-volume cylindrical Poisson rows (eqs. 12-13).  Each
+ * implicit step is solved by Newton-Raphson (eq. 14, 3x3-block five-point
+ * Jacobian) whose linear systems are solved by multigrid V-cycles; the steady
+ * state is reached by the Delta-t ramp and the coarse-to-fine continuation of
+ * Sec. 2 ("multilevel prolongation").
+ *
+ * Boundary conditions: electrode rows z = z_0 (cathode) and z = z_Nz (anode) are
+ * Dirichlet: n_e = n_p = 0, V = V_cathode / V_anode.  Axis r = 0: symmetry.
+ * Outer wall r = R: zero normal particle flux and dV/dr = 0.
+ *
+ * Conventions
+ *  - Arrays are node arrays of (N_z + 1) x (N_r + 1) doubles, row-major with the
+ *    radial index i fastest: a[j * (N_r + 1) + i].  SI units (m, V, s, m^-3).
+ *  - `where` selects the memory space of a caller pointer: MG_HOST (pageable or
+ *    pinned host memory) or MG_DEVICE (device memory on the state's GPU).
+ *  - Caller arrays are copied in or out and never retained.
+ *  - Every call is issued on the stream given to mg_create and returns after the
+ *    results it reports are available (calls that return norms or statuses
+ *    synchronise that stream).
+ *  - Return value: MG_OK or a negative MG_E* code; mg_last_error() gives text.
+ *    On any error inside a step the state is left at the last accepted step.
+ *  - There is no CPU fallback: every arithmetic step runs in CUDA kernels.
+ */
+#ifndef PAPER_0811_4446_GB300_MG_H
+#define PAPER_0811_4446_GB300_MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MG_OK = 0,
+  MG_EINVAL = -1,     /* bad sizes or parameters                            */
+  MG_ECUDA = -2,      /* a CUDA runtime call failed                         */
+  MG_ENOCONV = -3,    /* Newton or multigrid exceeded its iteration caps    */
+  MG_EREJECT = -4,    /* Delta-t retries exhausted / step count exhausted   */
+  MG_ENONFINITE = -5, /* NaN or Inf appeared in a residual or correction    */
+  MG_ETIMEOUT = -6,   /* a bounded device-side wait expired                 */
+  MG_ENOMEM = -7      /* workspace too small                                */
+};
+
+enum { MG_HOST = 0, MG_DEVICE = 1 };
+enum { MG_FP64 = 0, MG_MIXED = 1 };
+
+/* Grid (Sec. 2): N_r, N_z intervals (powers of two, >= 2); radius R; z holds
+ * N_z + 1 strictly increasing axial node coordinates (host memory).  The
+ * multigrid hierarchy takes every other node, so the coarse grids are nested. */
+typedef struct mg_grid {
+  int32_t nr, nz;
+  double R;
+  const double *z;
+} mg_grid;
+
+/* Physical inputs and solver knobs.  mu, D in m^2/(V s), m^2/s.  When `table`
+ * is non-NULL it holds `table_rows` rows of (|E|, mu_e, D_e, mu_p, D_p) with
+ * increasing |E| (host memory); mu and D at a face are then interpolated
+ * linearly in the face |E| (clamped at the table ends), the inputs the paper
+ * says come "from lookup tables" (Sec. 2).  All mu, D are divided by
+ * pressure_factor. */
+typedef struct mg_params {
+  double V_cathode, V_anode;
+  double mu_e, D_e, mu_p, D_p;
+  const double *table;
+  int32_t table_rows;
+  int32_t precision;      /* MG_FP64 or MG_MIXED (FP32 V-cycle in FP64 Newton) */
+  double pressure_factor;
+  int32_t nu1, nu2;       /* pre/post red-black sweeps per level              */
+  int32_t coarsest;       /* stop coarsening at min(N_r, N_z) <= coarsest (2..8)*/
+  int32_t max_vcycles;    /* per linear solve                                  */
+  int32_t max_newton;     /* per time step (the paper observed < 10)           */
+  int32_t max_steps;      /* per march                                         */
+  double eta;             /* linear tolerance relative to the Newton residual  */
+  double newton_tol;      /* per-step tolerance in a march; 0 -> 0.1 * tol     */
+  double corr_limit_frac; /* reject a step if max|dV| > frac * |V_cathode|     */
+  double dt1, dt_growth, dt_max; /* Delta-t ramp of Sec. 2                     */
+  double n0;              /* density unit of the FP32 inner cycle (eq. 12's n0), m^-3 */
+} mg_params;
+
+/* Per-call statistics. */
+typedef struct mg_stats {
+  int32_t steps_accepted, steps_rejected;
+  int32_t newton_iterations;  /* summed over accepted and rejected steps */
+  int32_t vcycles;            /* summed over all linear solves            */
+  int32_t last_newton;        /* Newton iterations of the last step       */
+  double rho[3];              /* last scale-free residual per field (n_e, n_p, V) */
+  double steady_rho;          /* last steady residual (max over fields)  */
+  double dt_last;
+  double sim_time;            /* accumulated accepted Delta t             */
+  int32_t coarse_steps;       /* part of the counts above spent on the coarse grid */
+  int32_t coarse_newton;      /* of mg_solve_steady's continuation                 */
+  int32_t coarse_vcycles;
+} mg_stats;
+
+typedef struct mg_state mg_state;
+
+/* Fill *p with the defaults: mu_e = 30, D_e = 60, mu_p = 0.15, D_p = 0.0038,
+ * V_cathode = -200, V_anode = 0, nu1 = nu2 = 2, coarsest = 4, eta = 1e-3,
+ * max_newton = 10, max_vcycles = 60, max_steps = 400, dt1 = 1e-9,
+ * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14.
+ *
+ * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
+ * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on
+ * FP32 copies of the face coefficients, densities in units of n0); the face coefficients
+ * (Bernoulli functions) are evaluated in FP64 and the coarsest level is solved in FP64. */
+void mg_params_default(mg_params *p);
+
+/* Bytes of device workspace mg_create needs for this grid and parameters. */
+size_t mg_workspace_bytes(const mg_grid *g, const mg_params *p);
+
+/* Create a solver state.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream) that the state borrows for all its work.  `workspace` is caller-owned
+ * device memory of at least mg_workspace_bytes() bytes (256-byte aligned) that
+ * must outlive the state; pass NULL to let the library allocate (and free) it.
+ * The state starts from n_e = n_p = 0, V linear in z, sources 0. */
+int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspace,
+              size_t workspace_bytes, mg_state **out);
+void mg_destroy(mg_state *s);
+const char *mg_last_error(const mg_state *s);
+
+/* Copy the state (n_e, n_p, V) in or out.  mg_set_state overwrites the
+ * electrode rows with the Dirichlet values. */
+int mg_set_state(mg_state *s, const double *ne, const double *np, const double *V, int where);
+int mg_get_state(const mg_state *s, double *ne, double *np, double *V, int where);
+
+/* The time level n^k used by mg_residual / mg_jacobian_apply / mg_linear_solve.
+ * mg_step sets it itself from the current state. */
+int mg_set_old_state(mg_state *s, const double *ne, const double *np, const double *V, int where);
+
+/* Sources S_e, S_p in m^-3 s^-1 (eqs. 1-2). */
+int mg_set_sources(mg_state *s, const double *S_e, const double *S_p, int where);
+
+/* Nonlinear residual rows of eq. 7 + eqs. 12/13 in finite-volume form, at the
+ * current state, with time level n^k from mg_set_old_state and step dt
+ * (dt <= 0: steady residual, time term dropped).  F (3 node arrays n_e, n_p, V
+ * rows, zero on the electrode rows, may be NULL) and rho[3] = ||F_f|| / ||T_f||
+ * where T_f sums the absolute values of the terms of each row (may be NULL). */
+int mg_residual(mg_state *s, double dt, double *F_ne, double *F_np, double *F_V, double rho[3], int where);
+
+/* Jacobian-vector product (eq. 14) at the current state: out = J v.  v and out
+ * are 3 node arrays each (electrode rows of v ignored, of out set to 0). */
+int mg_jacobian_apply(mg_state *s, double dt, const double *v_ne, const double *v_np, const double *v_V,
+                      double *o_ne, double *o_np, double *o_V, int where);
+
+/* Solve J x = f (eq. 14) at the current state by V-cycles from x = 0 until the
+ * field-weighted residual has dropped by eta (weights: the norms of the
+ * nonlinear residual's absolute terms at the current state), or max_cycles.
+ * history (may be NULL) receives up to max_cycles + 1 relative residuals;
+ * *cycles the number of V-cycles run. */
+int mg_linear_solve(mg_state *s, double dt, const double *f_ne, const double *f_np, const double *f_V,
+                    double *x_ne, double *x_np, double *x_V, double eta, int max_cycles,
+                    double *history, int *cycles, int where);
+
+/* One backward-Euler step of length dt (eq. 7) solved by Newton-Raphson with
+ * multigrid (eq. 14) until every field's rho <= tol.  On rejection (Newton cap,
+ * correction limit, linear failure, non-finite) the state is unchanged and the
+ * return value is MG_ENOCONV or MG_ENONFINITE.  stats may be NULL. */
+int mg_step(mg_state *s, double dt, double tol, mg_stats *stats);
+
+/* March with the Delta-t ramp of Sec. 2 from dt_start until the steady
+ * residual <= tol (MG_EREJECT if max_steps is exhausted first). */
+int mg_march(mg_state *s, double dt_start, double tol, mg_stats *stats);
+
+/* Steady state by the continuation of Sec. 2 / abstract: the current state and
+ * sources are injected onto the grid coarsened by two, marched there from dt1
+ * to steady, prolonged bilinearly back, and marched on the full grid starting
+ * with the long step dt_max, until the steady residual <= tol. */
+int mg_solve_steady(mg_state *s, double tol, mg_stats *stats);
+
+/* Statistics accumulated since creation (or the last mg_reset_stats). */
+int mg_get_stats(const mg_state *s, mg_stats *out);
+void mg_reset_stats(mg_state *s);
+
+/* Number of CUDA kernels this library has launched (all states, process-wide). */
+uint64_t mg_kernel_launches(void);
+
+/* Kernel timing for measurement: between mg_profile_begin and mg_profile_end every launch
+ * of `kernel` on multigrid level `level` (0 = finest) is bracketed by CUDA events recorded on
+ * the state's stream (up to 16384 launches).  mg_profile_end synchronises the stream and
+ * returns the number of bracketed launches and their summed device time in milliseconds. */
+enum { MG_PROF_SMOOTH = 1, MG_PROF_LINRES = 2, MG_PROF_COEF = 3, MG_PROF_RESIDUAL = 4,
+       MG_PROF_RESTRICT = 5, MG_PROF_PROLONG = 6 };
+int mg_profile_begin(mg_state *s, int kernel, int level);
+int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms);
+
+/* Measured FP64 fused-multiply-add throughput of the current device in GFLOP/s (2 flops per
+ * FMA), from a kernel of independent FMA chains on every SM; used as the ALU roofline of the
+ * FP64 path.  Returns a negative value on a CUDA error. */
+double mg_probe_fp64_gflops(void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,817 @@
+// Host side of the C ABI declared in include/mg.h: state and workspace layout, the multigrid
+// V-cycle schedule, Newton-Raphson, the Delta-t ramp and the coarse-to-fine continuation
+// (Ristivojevic & Petrovic, arXiv:0811.4446, Sec. 2).  All arithmetic on the solution runs in
+// the kernels of mg_kernels.cu; the host only sequences launches and reads back norms.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_impl.cuh"
+
+using namespace mgk;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCoarse = 3 * 9 * 9;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+bool pow2(int x) { return x >= 2 && (x & (x - 1)) == 0; }
+
+// Host-side record of one level: dimensions and device pointers.
+struct LevelBuf {
+  int nr, nz, P;
+  size_t nodes;
+  Level L;               // FP64 view (geometry + MG work arrays)
+  LevelT<float> M;       // FP32 view (mixed form only)
+  StateView sv;          // FP64 nonlinear state on this level
+  double *geo;           // device geometry block
+  float *geo32;
+};
+
+}  // namespace
+
+struct mg_state {
+  mg_params prm;
+  std::vector<double> table_h;
+  int nr, nz;
+  double R;
+  std::vector<double> z;
+  int nlev;
+  LevelBuf lv[kMaxLevels];
+  Transport tr;
+  cudaStream_t stream;
+  void *ws;
+  size_t ws_bytes;
+  bool owns_ws;
+  // scratch
+  double *partials;
+  size_t partials_cap;   // doubles
+  unsigned *counter;
+  double *dout;          // device outputs of reductions (16 doubles)
+  double *hout;          // pinned host mirror (16 doubles)
+  double *M, *Minv, *rs, *cs;
+  int *flag;
+  double *table_d;
+  mg_stats stats;
+  std::string err;
+  // kernel timing (mg_profile_begin / mg_profile_end)
+  int prof_kernel = 0, prof_level = -1, prof_n = 0;
+  std::vector<cudaEvent_t> prof_ev;
+};
+
+namespace {
+
+int fail(mg_state *s, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(s, MG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Level dimensions of the hierarchy.
+int plan_levels(int nr, int nz, int coarsest, int *lnr, int *lnz) {
+  int n = 0;
+  lnr[n] = nr; lnz[n] = nz; ++n;
+  while (n < kMaxLevels && std::min(lnr[n - 1], lnz[n - 1]) > coarsest && lnr[n - 1] % 2 == 0 && lnz[n - 1] % 2 == 0) {
+    lnr[n] = lnr[n - 1] / 2; lnz[n] = lnz[n - 1] / 2; ++n;
+  }
+  return n;
+}
+
+int pitch_of(int nr) { return ((nr + 1) + 3) & ~3; }
+
+// Workspace layout: computed twice, once to size it and once to carve it.
+struct Carver {
+  char *base;
+  size_t off;
+  template <typename T>
+  T *take(size_t count) {
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+constexpr int kFieldsPerLevel = 29;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3
+constexpr int kGeoPerLevel = 4;      // dz, dzc, volr, wz (each up to max(nr, nz) + 1)
+
+size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz + 1 + 7) / 8); }
+
+constexpr int kFields32PerLevel = 21;  // cr 6, cz 6, du 3, f 3, r 3
+
+void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int table_rows, bool mixed) {
+  for (int l = 0; l < nlev; ++l) {
+    LevelBuf &b = s->lv[l];
+    b.nr = lnr[l]; b.nz = lnz[l]; b.P = pitch_of(lnr[l]);
+    b.nodes = (size_t)(b.nz + 1) * b.P;
+    const int glen = std::max(b.nr, b.nz) + 2;
+    b.geo = c.take<double>((size_t)kGeoPerLevel * glen);
+    double *f[kFieldsPerLevel];
+    for (int q = 0; q < kFieldsPerLevel; ++q) f[q] = c.take<double>(b.nodes);
+    int q = 0;
+    for (int a = 0; a < 3; ++a) b.sv.u[a] = f[q++];
+    for (int a = 0; a < 3; ++a) b.sv.uold[a] = f[q++];
+    for (int a = 0; a < 2; ++a) b.sv.S[a] = f[q++];
+    for (int a = 0; a < NCOEF; ++a) b.L.cr[a] = f[q++];
+    for (int a = 0; a < NCOEF; ++a) b.L.cz[a] = f[q++];
+    for (int a = 0; a < 3; ++a) b.L.du[a] = f[q++];
+    for (int a = 0; a < 3; ++a) b.L.f[a] = f[q++];
+    for (int a = 0; a < 3; ++a) b.L.r[a] = f[q++];
+    b.L.nr = b.nr; b.L.nz = b.nz; b.L.P = b.P;
+    if (b.geo) {
+      b.L.dz = b.geo;
+      b.L.dzc = b.geo + glen;
+      b.L.volr = b.geo + 2 * glen;
+      b.L.wz = b.geo + 3 * glen;
+    }
+    b.M = LevelT<float>();
+    b.geo32 = nullptr;
+    if (mixed) {
+      b.geo32 = c.take<float>((size_t)kGeoPerLevel * glen);
+      float *g[kFields32PerLevel];
+      for (int q2 = 0; q2 < kFields32PerLevel; ++q2) g[q2] = c.take<float>(b.nodes);
+      int w = 0;
+      for (int a = 0; a < NCOEF; ++a) b.M.cr[a] = g[w++];
+      for (int a = 0; a < NCOEF; ++a) b.M.cz[a] = g[w++];
+      for (int a = 0; a < 3; ++a) b.M.du[a] = g[w++];
+      for (int a = 0; a < 3; ++a) b.M.f[a] = g[w++];
+      for (int a = 0; a < 3; ++a) b.M.r[a] = g[w++];
+      b.M.nr = b.nr; b.M.nz = b.nz; b.M.P = b.P;
+      if (b.geo32) {
+        b.M.dz = b.geo32;
+        b.M.dzc = b.geo32 + glen;
+        b.M.volr = b.geo32 + 2 * glen;
+        b.M.wz = b.geo32 + 3 * glen;
+      }
+    }
+  }
+  s->partials_cap = 8 * max_blocks(lnr[0], lnz[0]) + 64;
+  s->partials = c.take<double>(s->partials_cap);
+  s->counter = c.take<unsigned>(4);
+  s->dout = c.take<double>(16);
+  s->M = c.take<double>((size_t)kMaxCoarse * kMaxCoarse);
+  s->Minv = c.take<double>((size_t)kMaxCoarse * kMaxCoarse);
+  s->rs = c.take<double>(kMaxCoarse);
+  s->cs = c.take<double>(kMaxCoarse);
+  s->flag = c.take<int>(4);
+  s->table_d = table_rows > 0 ? c.take<double>((size_t)table_rows * 5) : nullptr;
+}
+
+// Geometry of one level (finite-volume control volumes of eqs. 12-13, per radian).
+void host_geometry(const std::vector<double> &zl, int nr, double R, std::vector<double> &out, int glen) {
+  const int nz = (int)zl.size() - 1;
+  out.assign((size_t)kGeoPerLevel * glen, 0.0);
+  double *dz = out.data(), *dzc = dz + glen, *volr = dz + 2 * glen, *wz = dz + 3 * glen;
+  const double dr = R / nr;
+  for (int j = 0; j < nz; ++j) dz[j] = zl[j + 1] - zl[j];
+  for (int j = 1; j < nz; ++j) dzc[j] = 0.5 * (dz[j - 1] + dz[j]);
+  for (int i = 0; i <= nr; ++i) volr[i] = i * dr * dr;
+  volr[0] = dr * dr / 8.0;
+  volr[nr] = (nr - 0.25) * dr * dr / 2.0;
+  for (int j = 1; j < nz; j += 2) wz[j] = (zl[j] - zl[j - 1]) / (zl[j + 1] - zl[j - 1]);
+}
+
+cudaMemcpyKind kind_in(int where) { return where == MG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int where) { return where == MG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+// Copy rows [j0, j1] of a dense (nz+1) x (nr+1) caller array into a pitched level array.
+int copy_in(mg_state *s, const LevelBuf &b, double *dst, const double *src, int where, int j0, int j1) {
+  const size_t w = (size_t)(b.nr + 1) * sizeof(double);
+  CK(cudaMemcpy2DAsync(dst + (size_t)j0 * b.P, b.P * sizeof(double), src + (size_t)j0 * (b.nr + 1), w, w,
+                       j1 - j0 + 1, kind_in(where), s->stream));
+  return MG_OK;
+}
+
+int copy_out(mg_state *s, const LevelBuf &b, double *dst, const double *src, int where) {
+  const size_t w = (size_t)(b.nr + 1) * sizeof(double);
+  CK(cudaMemcpy2DAsync(dst, w, src, b.P * sizeof(double), w, b.nz + 1, kind_out(where), s->stream));
+  return MG_OK;
+}
+
+bool mixed(const mg_state *s) { return s->prm.precision == MG_MIXED; }
+
+int sync_read(mg_state *s, int n) {
+  CK(cudaMemcpyAsync(s->hout, s->dout, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+constexpr int kProfMax = 16384;
+
+// Record a timing event pair around one launch when (kernel, level) is being profiled.
+struct ProfScope {
+  mg_state *s;
+  bool on;
+  ProfScope(mg_state *s_, int kernel, int level) : s(s_), on(false) {
+    if (s->prof_kernel == kernel && s->prof_level == level && s->prof_n < kProfMax) {
+      on = true;
+      cudaEventRecord(s->prof_ev[2 * s->prof_n], s->stream);
+    }
+  }
+  ~ProfScope() {
+    if (on) {
+      cudaEventRecord(s->prof_ev[2 * s->prof_n + 1], s->stream);
+      s->prof_n++;
+    }
+  }
+};
+
+// ---------------------------------------------------------------- building blocks
+// Nonlinear residual on root level l0; rho[3] and the term norms tn[3]; f = -F written if write_f.
+int residual(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], double rho[3], double tn[3]) {
+  LevelBuf &b = s->lv[l0];
+  {
+    ProfScope ps(s, MG_PROF_RESIDUAL, l0);
+    CK(launch_residual(b.L, b.sv, s->tr, dt, write_f, Fout, s->partials, s->counter, s->dout, s->stream));
+  }
+  int rc = sync_read(s, 6);
+  if (rc) return rc;
+  for (int q = 0; q < 3; ++q) {
+    const double fn = std::sqrt(s->hout[q]), t = std::sqrt(s->hout[3 + q]);
+    if (tn) tn[q] = t;
+    if (rho) rho[q] = fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
+  }
+  return MG_OK;
+}
+
+// Coefficients on levels l0..nlev-1 at the state of l0 injected downward; coarsest inverse.
+int build_hierarchy(mg_state *s, int l0, double dt) {
+  for (int l = l0; l < s->nlev; ++l) {
+    LevelBuf &b = s->lv[l];
+    if (l > l0) CK(launch_inject(s->lv[l - 1].L, s->lv[l - 1].sv, b.L, b.sv, false, false, s->stream));
+    ProfScope ps(s, MG_PROF_COEF, l);
+    CK(launch_coef(b.L, b.sv, s->tr, s->stream));
+    if (mixed(s)) CK(launch_coef_to32(b.L, b.M, s->prm.n0, s->stream));
+  }
+  LevelBuf &c = s->lv[s->nlev - 1];
+  CK(launch_coarse_factor(c.L, dt, s->M, s->Minv, s->rs, s->cs, s->flag, s->stream));
+  return MG_OK;
+}
+
+template <typename T> const LevelT<T> &view(const LevelBuf &b);
+template <> const LevelT<double> &view<double>(const LevelBuf &b) { return b.L; }
+template <> const LevelT<float> &view<float>(const LevelBuf &b) { return b.M; }
+// e/eps0 in the unknowns of the view: the FP32 inner cycle counts densities in units of n0
+template <typename T> double kap_of(const mg_state *s);
+template <> double kap_of<double>(const mg_state *) { return kKappa; }
+template <> double kap_of<float>(const mg_state *s) { return kKappa * s->prm.n0; }
+template <typename T> double nscale_of(const mg_state *s);
+template <> double nscale_of<double>(const mg_state *) { return 1.0; }
+template <> double nscale_of<float>(const mg_state *s) { return s->prm.n0; }
+
+template <typename T>
+int smooth(mg_state *s, int l, double dt, int color) {
+  ProfScope ps(s, MG_PROF_SMOOTH, l);
+  CK(launch_smooth<T>(view<T>(s->lv[l]), dt, kap_of<T>(s), color, s->stream));
+  return MG_OK;
+}
+
+template <typename T>
+int vcycle(mg_state *s, int l, double dt) {
+  const LevelT<T> &b = view<T>(s->lv[l]);
+  if (l == s->nlev - 1) {
+    CK(launch_coarse_solve<T>(b, s->Minv, s->rs, s->cs, nscale_of<T>(s), s->stream));
+    return MG_OK;
+  }
+  const LevelT<T> &c = view<T>(s->lv[l + 1]);
+  int rc;
+  for (int k = 0; k < s->prm.nu1; ++k)
+    for (int col = 0; col < 2; ++col)
+      if ((rc = smooth<T>(s, l, dt, col))) return rc;
+  {
+    ProfScope ps(s, MG_PROF_LINRES, l);
+    CK(launch_linres<T>(b, dt, kap_of<T>(s), b.du, b.f, const_cast<T **>(b.r), nullptr, nullptr, nullptr,
+                        s->stream));
+  }
+  {
+    ProfScope ps(s, MG_PROF_RESTRICT, l);
+    CK(launch_restrict<T>(b, c, s->stream));
+  }
+  if ((rc = vcycle<T>(s, l + 1, dt))) return rc;
+  {
+    ProfScope ps(s, MG_PROF_PROLONG, l);
+    CK(launch_prolong_add<T>(c, b, s->stream));
+  }
+  for (int k = 0; k < s->prm.nu2; ++k)
+    for (int col = 0; col < 2; ++col)
+      if ((rc = smooth<T>(s, l, dt, col))) return rc;
+  return MG_OK;
+}
+
+// Weighted linear-residual norm max_f ||f - J du||_f / w_f on level l0.
+int lin_norm(mg_state *s, int l0, double dt, const double w[3], double *out) {
+  LevelBuf &b = s->lv[l0];
+  if (mixed(s)) {
+    CK(launch_outer_residual(b.L, b.M, dt, s->prm.n0, s->partials, s->counter, s->dout, s->stream));
+  } else {
+    CK(launch_linres<double>(b.L, dt, kKappa, b.L.du, b.L.f, b.L.r, s->partials, s->counter, s->dout, s->stream));
+  }
+  int rc = sync_read(s, 3);
+  if (rc) return rc;
+  double m = 0.0;
+  for (int q = 0; q < 3; ++q) {
+    const double v = std::sqrt(s->hout[q]) / w[q];
+    if (!(v == v)) { m = NAN; break; }
+    m = std::max(m, v);
+  }
+  *out = m;
+  return MG_OK;
+}
+
+// V-cycles on level l0 from du = 0 until the weighted residual drops by eta.
+int linear_solve(mg_state *s, int l0, double dt, double eta, int max_cycles, const double tn[3], double *hist,
+                 int *ncyc, bool *ok) {
+  double w[3];
+  for (int q = 0; q < 3; ++q) w[q] = tn[q] > 0.0 ? tn[q] : 1.0;
+  CK(launch_zero_du<double>(s->lv[l0].L, s->stream));
+  double r0;
+  int rc = lin_norm(s, l0, dt, w, &r0);
+  if (rc) return rc;
+  *ncyc = 0;
+  *ok = true;
+  if (hist) hist[0] = r0 > 0.0 ? 1.0 : 0.0;
+  if (r0 == 0.0) return MG_OK;
+  double rel = 1.0;
+  while (rel > eta && *ncyc < max_cycles) {
+    if (mixed(s)) {
+      // FP32 correction of the FP64 defect, then x += e in FP64
+      CK(launch_zero_du<float>(s->lv[l0].M, s->stream));
+      rc = vcycle<float>(s, l0, dt);
+      if (rc) return rc;
+      CK(launch_mixed_update(s->lv[l0].L, s->lv[l0].M, s->prm.n0, s->stream));
+    } else {
+      rc = vcycle<double>(s, l0, dt);
+      if (rc) return rc;
+    }
+    double r;
+    rc = lin_norm(s, l0, dt, w, &r);
+    if (rc) return rc;
+    ++*ncyc;
+    rel = r / r0;
+    if (hist) hist[*ncyc] = rel;
+    if (!(rel == rel) || std::isinf(rel)) { *ok = false; return MG_OK; }
+  }
+  s->stats.vcycles += *ncyc;
+  *ok = rel <= eta;
+  return MG_OK;
+}
+
+void copy_state_async(mg_state *s, int l0, bool to_old) {
+  LevelBuf &b = s->lv[l0];
+  for (int q = 0; q < 3; ++q) {
+    if (to_old) cudaMemcpyAsync(b.sv.uold[q], b.sv.u[q], b.nodes * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    else cudaMemcpyAsync(b.sv.u[q], b.sv.uold[q], b.nodes * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  }
+}
+
+// One backward-Euler step on level l0 (eq. 7 by Newton-Raphson on eq. 14).
+// Returns MG_OK (accepted), MG_ENOCONV or MG_ENONFINITE (rejected; state restored).
+int step(mg_state *s, int l0, double dt, double tol, int *newton_out) {
+  LevelBuf &b = s->lv[l0];
+  copy_state_async(s, l0, true);
+  CK(cudaGetLastError());
+  const double limit = s->prm.corr_limit_frac * std::fabs(s->prm.V_cathode);
+  int rc;
+  int reason = MG_ENOCONV;
+  for (int it = 0; it <= s->prm.max_newton; ++it) {
+    double rho[3], tn[3];
+    rc = residual(s, l0, dt, true, nullptr, rho, tn);
+    if (rc) return rc;
+    for (int q = 0; q < 3; ++q) s->stats.rho[q] = rho[q];
+    const double rmax = std::max(rho[0], std::max(rho[1], rho[2]));
+    if (!(rmax == rmax) || std::isinf(rmax)) { reason = MG_ENONFINITE; *newton_out = it; break; }
+    if (rmax <= tol) {
+      *newton_out = it;
+      s->stats.newton_iterations += it;
+      s->stats.last_newton = it;
+      return MG_OK;
+    }
+    if (it == s->prm.max_newton) { *newton_out = it; break; }
+    rc = build_hierarchy(s, l0, dt);
+    if (rc) return rc;
+    int ncyc;
+    bool ok;
+    rc = linear_solve(s, l0, dt, s->prm.eta, s->prm.max_vcycles, tn, nullptr, &ncyc, &ok);
+    if (rc) return rc;
+    if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
+    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout, s->stream));
+    rc = sync_read(s, 2);
+    if (rc) return rc;
+    if (s->hout[1] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
+    if (s->hout[0] > limit) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
+  }
+  s->stats.newton_iterations += *newton_out;
+  s->stats.last_newton = *newton_out;
+  copy_state_async(s, l0, false);
+  CK(cudaGetLastError());
+  return reason;
+}
+
+// March on level l0 with the Delta-t ramp until the steady residual <= tol.
+int march(mg_state *s, int l0, double dt_start, double tol) {
+  double dt = dt_start, dt_prev = -1.0;
+  const double ntol = s->prm.newton_tol > 0.0 ? s->prm.newton_tol : 0.1 * tol;
+  for (int n = 0; n < s->prm.max_steps; ++n) {
+    int newton = 0;
+    int rc = step(s, l0, dt, ntol, &newton);
+    if (rc == MG_ECUDA) return rc;
+    s->stats.dt_last = dt;
+    if (rc == MG_OK) {
+      s->stats.steps_accepted++;
+      s->stats.sim_time += dt;
+      double rho[3];
+      rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr);
+      if (rc) return rc;
+      const double r = std::max(rho[0], std::max(rho[1], rho[2]));
+      s->stats.steady_rho = r;
+      if (r <= tol) return MG_OK;
+      dt_prev = dt;
+      dt = std::min(dt * s->prm.dt_growth, s->prm.dt_max);
+    } else {
+      s->stats.steps_rejected++;
+      if (dt_prev > 0.0 && dt > dt_prev) {
+        dt = dt_prev;
+      } else {
+        dt *= 0.5;
+        if (dt_prev > 0.0) dt_prev = std::min(dt_prev, dt);
+      }
+    }
+  }
+  return fail(s, MG_EREJECT, "march: steady residual not reached in %d steps", s->prm.max_steps);
+}
+
+int check_where(mg_state *s, int where) {
+  if (where != MG_HOST && where != MG_DEVICE) return fail(s, MG_EINVAL, "where must be MG_HOST or MG_DEVICE");
+  return MG_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+void mg_params_default(mg_params *p) {
+  std::memset(p, 0, sizeof(*p));
+  p->V_cathode = -200.0; p->V_anode = 0.0;
+  p->mu_e = 30.0; p->D_e = 60.0; p->mu_p = 0.15; p->D_p = 0.0038;
+  p->table = nullptr; p->table_rows = 0;
+  p->precision = MG_FP64;
+  p->pressure_factor = 1.0;
+  p->nu1 = 2; p->nu2 = 2; p->coarsest = 4;
+  p->max_vcycles = 60; p->max_newton = 10; p->max_steps = 400;
+  p->eta = 1e-3; p->newton_tol = 0.0; p->corr_limit_frac = 0.5;
+  p->dt1 = 1e-9; p->dt_growth = 5.0; p->dt_max = 1e-6;
+  p->n0 = 1e14;
+}
+
+static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
+  if (!g || !p) { *why = "null grid or params"; return MG_EINVAL; }
+  if (!pow2(g->nr) || !pow2(g->nz)) { *why = "nr and nz must be powers of two >= 2"; return MG_EINVAL; }
+  if (!(g->R > 0.0) || !g->z) { *why = "R must be positive and z given"; return MG_EINVAL; }
+  for (int j = 0; j < g->nz; ++j)
+    if (!(g->z[j + 1] > g->z[j])) { *why = "z must increase strictly"; return MG_EINVAL; }
+  if (p->coarsest < 2 || p->coarsest > 8) { *why = "coarsest must be in 2..8"; return MG_EINVAL; }
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) { *why = "need at least one smoothing sweep"; return MG_EINVAL; }
+  if (!(p->pressure_factor > 0.0) || !(p->D_e > 0.0) || !(p->D_p > 0.0) || p->mu_e < 0 || p->mu_p < 0) {
+    *why = "transport coefficients must be positive"; return MG_EINVAL;
+  }
+  if (p->table) {
+    if (p->table_rows < 2) { *why = "table needs >= 2 rows"; return MG_EINVAL; }
+    for (int r = 0; r < p->table_rows; ++r) {
+      if (r > 0 && !(p->table[5 * r] > p->table[5 * (r - 1)])) { *why = "table |E| must increase"; return MG_EINVAL; }
+      if (!(p->table[5 * r + 2] > 0.0) || !(p->table[5 * r + 4] > 0.0)) { *why = "table D must be positive"; return MG_EINVAL; }
+    }
+  }
+  if (p->precision != MG_FP64 && p->precision != MG_MIXED) { *why = "unknown precision"; return MG_EINVAL; }
+  if (p->precision == MG_MIXED && !(p->n0 > 0.0)) { *why = "n0 must be positive"; return MG_EINVAL; }
+  int lnr[kMaxLevels], lnz[kMaxLevels];
+  const int n = plan_levels(g->nr, g->nz, p->coarsest, lnr, lnz);
+  if (3 * (lnr[n - 1] + 1) * (lnz[n - 1] - 1) > kMaxCoarse) { *why = "coarsest level too large (too anisotropic grid)"; return MG_EINVAL; }
+  return MG_OK;
+}
+
+size_t mg_workspace_bytes(const mg_grid *g, const mg_params *p) {
+  std::string why;
+  if (validate(g, p, &why) != MG_OK) return 0;
+  int lnr[kMaxLevels], lnz[kMaxLevels];
+  const int n = plan_levels(g->nr, g->nz, p->coarsest, lnr, lnz);
+  mg_state tmp;
+  Carver c{nullptr, 0};
+  carve(c, &tmp, n, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED);
+  return c.off;
+}
+
+int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspace, size_t workspace_bytes,
+              mg_state **out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  std::string why;
+  int v = validate(g, p, &why);
+  if (v != MG_OK) return v;
+  mg_state *s = new (std::nothrow) mg_state();
+  if (!s) return MG_ENOMEM;
+  s->prm = *p;
+  s->nr = g->nr; s->nz = g->nz; s->R = g->R;
+  s->z.assign(g->z, g->z + g->nz + 1);
+  if (p->table) {
+    s->table_h.assign(p->table, p->table + 5 * p->table_rows);
+    s->prm.table = s->table_h.data();
+  }
+  s->stream = (cudaStream_t)stream;
+  int lnr[kMaxLevels], lnz[kMaxLevels];
+  s->nlev = plan_levels(g->nr, g->nz, p->coarsest, lnr, lnz);
+  Carver sizer{nullptr, 0};
+  carve(sizer, s, s->nlev, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED);
+  const size_t need = sizer.off;
+  if (workspace) {
+    if (workspace_bytes < need || ((uintptr_t)workspace & (kAlign - 1))) {
+      delete s;
+      return MG_ENOMEM;
+    }
+    s->ws = workspace; s->owns_ws = false;
+  } else {
+    if (cudaMalloc(&s->ws, need) != cudaSuccess) { delete s; return MG_ENOMEM; }
+    s->owns_ws = true;
+  }
+  s->ws_bytes = need;
+  if (cudaMallocHost(&s->hout, 16 * sizeof(double)) != cudaSuccess) {
+    if (s->owns_ws) cudaFree(s->ws);
+    delete s;
+    return MG_ECUDA;
+  }
+  Carver c{(char *)s->ws, 0};
+  carve(c, s, s->nlev, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED);
+  int rc = MG_OK;
+  // zero everything once (electrode rows of du stay zero forever)
+  if (cudaMemsetAsync(s->ws, 0, need, s->stream) != cudaSuccess) rc = fail(s, MG_ECUDA, "memset workspace");
+  // geometry per level
+  std::vector<double> geo;
+  for (int l = 0; l < s->nlev && rc == MG_OK; ++l) {
+    LevelBuf &b = s->lv[l];
+    std::vector<double> zl;
+    for (int j = 0; j <= g->nz; j += (1 << l)) zl.push_back(g->z[j]);
+    const int glen = std::max(b.nr, b.nz) + 2;
+    host_geometry(zl, b.nr, g->R, geo, glen);
+    b.L.dr = g->R / b.nr;
+    b.M.dr = (float)(g->R / b.nr);
+    if (cudaMemcpyAsync(b.geo, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream) !=
+        cudaSuccess)
+      rc = fail(s, MG_ECUDA, "geometry copy");
+    std::vector<float> geo32(geo.begin(), geo.end());
+    if (b.geo32 && cudaMemcpyAsync(b.geo32, geo32.data(), geo32.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                   s->stream) != cudaSuccess)
+      rc = fail(s, MG_ECUDA, "geometry copy (FP32)");
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) rc = fail(s, MG_ECUDA, "geometry sync");
+  }
+  s->tr.mu_e = p->mu_e / p->pressure_factor; s->tr.D_e = p->D_e / p->pressure_factor;
+  s->tr.mu_p = p->mu_p / p->pressure_factor; s->tr.D_p = p->D_p / p->pressure_factor;
+  s->tr.inv_pf = 1.0 / p->pressure_factor;
+  s->tr.table = nullptr; s->tr.rows = 0;
+  if (p->table && rc == MG_OK) {
+    if (cudaMemcpy(s->table_d, s->table_h.data(), s->table_h.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      rc = fail(s, MG_ECUDA, "table copy");
+    s->tr.table = s->table_d; s->tr.rows = p->table_rows;
+  }
+  if (rc == MG_OK) {
+    // initial state: n = 0, V linear in z; old level = state
+    std::vector<double> V((size_t)(g->nz + 1) * (g->nr + 1));
+    for (int j = 0; j <= g->nz; ++j)
+      for (int i = 0; i <= g->nr; ++i)
+        V[(size_t)j * (g->nr + 1) + i] =
+            p->V_cathode + (p->V_anode - p->V_cathode) * (g->z[j] - g->z[0]) / (g->z[g->nz] - g->z[0]);
+    rc = copy_in(s, s->lv[0], s->lv[0].sv.u[NV], V.data(), MG_HOST, 0, g->nz);
+    if (rc == MG_OK && launch_dirichlet(s->lv[0].L, s->lv[0].sv, p->V_cathode, p->V_anode, s->stream) != cudaSuccess)
+      rc = fail(s, MG_ECUDA, "dirichlet");
+    if (rc == MG_OK) copy_state_async(s, 0, true);
+    if (rc == MG_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = fail(s, MG_ECUDA, "init sync");
+  }
+  if (rc != MG_OK) {
+    mg_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return MG_OK;
+}
+
+void mg_destroy(mg_state *s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  else cudaDeviceSynchronize();
+  for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+  if (s->owns_ws && s->ws) cudaFree(s->ws);
+  if (s->hout) cudaFreeHost(s->hout);
+  delete s;
+}
+
+const char *mg_last_error(const mg_state *s) { return s ? s->err.c_str() : "null state"; }
+
+int mg_set_state(mg_state *s, const double *ne, const double *np, const double *V, int where) {
+  if (!s || !ne || !np || !V) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  LevelBuf &b = s->lv[0];
+  const double *src[3] = {ne, np, V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_in(s, b, b.sv.u[q], src[q], where, 0, b.nz))) return rc;
+  CK(launch_dirichlet(b.L, b.sv, s->prm.V_cathode, s->prm.V_anode, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+int mg_set_old_state(mg_state *s, const double *ne, const double *np, const double *V, int where) {
+  if (!s || !ne || !np || !V) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  LevelBuf &b = s->lv[0];
+  const double *src[3] = {ne, np, V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_in(s, b, b.sv.uold[q], src[q], where, 0, b.nz))) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+int mg_get_state(const mg_state *cs, double *ne, double *np, double *V, int where) {
+  mg_state *s = const_cast<mg_state *>(cs);
+  if (!s || !ne || !np || !V) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  LevelBuf &b = s->lv[0];
+  double *dst[3] = {ne, np, V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_out(s, b, dst[q], b.sv.u[q], where))) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+int mg_set_sources(mg_state *s, const double *S_e, const double *S_p, int where) {
+  if (!s || !S_e || !S_p) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  LevelBuf &b = s->lv[0];
+  if ((rc = copy_in(s, b, (double *)b.sv.S[0], S_e, where, 0, b.nz))) return rc;
+  if ((rc = copy_in(s, b, (double *)b.sv.S[1], S_p, where, 0, b.nz))) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+int mg_residual(mg_state *s, double dt, double *F_ne, double *F_np, double *F_V, double rho[3], int where) {
+  if (!s) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  LevelBuf &b = s->lv[0];
+  double *Fo[3] = {b.L.r[0], b.L.r[1], b.L.r[2]};
+  double rh[3];
+  if ((rc = residual(s, 0, dt, false, Fo, rh, nullptr))) return rc;
+  if (rho) for (int q = 0; q < 3; ++q) rho[q] = rh[q];
+  double *dst[3] = {F_ne, F_np, F_V};
+  for (int q = 0; q < 3; ++q)
+    if (dst[q] && (rc = copy_out(s, b, dst[q], b.L.r[q], where))) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+int mg_jacobian_apply(mg_state *s, double dt, const double *v_ne, const double *v_np, const double *v_V,
+                      double *o_ne, double *o_np, double *o_V, int where) {
+  if (!s || !v_ne || !v_np || !v_V || !o_ne || !o_np || !o_V) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  LevelBuf &b = s->lv[0];
+  CK(launch_coef(b.L, b.sv, s->tr, s->stream));
+  const double *src[3] = {v_ne, v_np, v_V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_in(s, b, b.L.du[q], src[q], where, 1, b.nz - 1))) return rc;
+  CK(launch_linres<double>(b.L, dt, kKappa, b.L.du, nullptr, b.L.r, nullptr, nullptr, nullptr, s->stream));
+  double *dst[3] = {o_ne, o_np, o_V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_out(s, b, dst[q], b.L.r[q], where))) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+int mg_linear_solve(mg_state *s, double dt, const double *f_ne, const double *f_np, const double *f_V,
+                    double *x_ne, double *x_np, double *x_V, double eta, int max_cycles, double *history,
+                    int *cycles, int where) {
+  if (!s || !f_ne || !f_np || !f_V || !x_ne || !x_np || !x_V || max_cycles < 0) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  LevelBuf &b = s->lv[0];
+  double tn[3];
+  if ((rc = residual(s, 0, dt, false, nullptr, nullptr, tn))) return rc;
+  if ((rc = build_hierarchy(s, 0, dt))) return rc;
+  const double *src[3] = {f_ne, f_np, f_V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_in(s, b, b.L.f[q], src[q], where, 1, b.nz - 1))) return rc;
+  int nc = 0;
+  bool ok;
+  if ((rc = linear_solve(s, 0, dt, eta, max_cycles, tn, history, &nc, &ok))) return rc;
+  if (cycles) *cycles = nc;
+  double *dst[3] = {x_ne, x_np, x_V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_out(s, b, dst[q], b.L.du[q], where))) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return ok ? MG_OK : fail(s, MG_ENOCONV, "linear solve: tolerance not reached in %d V-cycles", nc);
+}
+
+int mg_step(mg_state *s, double dt, double tol, mg_stats *st) {
+  if (!s || !(dt > 0.0) || !(tol > 0.0)) return MG_EINVAL;
+  int newton = 0;
+  int rc = step(s, 0, dt, tol, &newton);
+  if (rc == MG_OK) { s->stats.steps_accepted++; s->stats.sim_time += dt; }
+  else if (rc != MG_ECUDA) s->stats.steps_rejected++;
+  s->stats.dt_last = dt;
+  if (st) *st = s->stats;
+  if (rc == MG_ENOCONV) fail(s, rc, "step rejected (Newton cap, linear solve or correction limit)");
+  if (rc == MG_ENONFINITE) fail(s, rc, "step rejected (non-finite values)");
+  return rc;
+}
+
+int mg_march(mg_state *s, double dt_start, double tol, mg_stats *st) {
+  if (!s || !(dt_start > 0.0) || !(tol > 0.0)) return MG_EINVAL;
+  int rc = march(s, 0, dt_start, tol);
+  if (st) *st = s->stats;
+  return rc;
+}
+
+int mg_solve_steady(mg_state *s, double tol, mg_stats *st) {
+  if (!s || !(tol > 0.0)) return MG_EINVAL;
+  if (s->nlev < 2) return fail(s, MG_EINVAL, "continuation needs at least two grid levels");
+  LevelBuf &f = s->lv[0], &c = s->lv[1];
+  CK(launch_inject(f.L, f.sv, c.L, c.sv, false, true, s->stream));
+  const mg_stats before = s->stats;
+  int rc = march(s, 1, s->prm.dt1, tol);
+  s->stats.coarse_steps += s->stats.steps_accepted + s->stats.steps_rejected - before.steps_accepted -
+                           before.steps_rejected;
+  s->stats.coarse_newton += s->stats.newton_iterations - before.newton_iterations;
+  s->stats.coarse_vcycles += s->stats.vcycles - before.vcycles;
+  if (rc == MG_OK) {
+    CK(launch_prolong_state(c.L, c.sv, f.L, f.sv, s->stream));
+    CK(launch_dirichlet(f.L, f.sv, s->prm.V_cathode, s->prm.V_anode, s->stream));
+    rc = march(s, 0, s->prm.dt_max, tol);
+  }
+  if (st) *st = s->stats;
+  return rc;
+}
+
+int mg_get_stats(const mg_state *s, mg_stats *out) {
+  if (!s || !out) return MG_EINVAL;
+  *out = s->stats;
+  return MG_OK;
+}
+
+void mg_reset_stats(mg_state *s) {
+  if (s) std::memset(&s->stats, 0, sizeof(s->stats));
+}
+
+uint64_t mg_kernel_launches(void) { return (uint64_t)total_launches(); }
+
+int mg_profile_begin(mg_state *s, int kernel, int level) {
+  if (!s || kernel < MG_PROF_SMOOTH || kernel > MG_PROF_PROLONG || level < 0 || level >= s->nlev)
+    return fail(s, MG_EINVAL, "mg_profile_begin: bad kernel or level");
+  if (s->prof_ev.empty()) {
+    s->prof_ev.resize(2 * kProfMax);
+    for (auto &e : s->prof_ev) CK(cudaEventCreate(&e));
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  s->prof_kernel = kernel;
+  s->prof_level = level;
+  s->prof_n = 0;
+  return MG_OK;
+}
+
+int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms) {
+  if (!s) return MG_EINVAL;
+  CK(cudaStreamSynchronize(s->stream));
+  double tot = 0.0;
+  for (int k = 0; k < s->prof_n; ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, s->prof_ev[2 * k], s->prof_ev[2 * k + 1]));
+    tot += ms;
+  }
+  if (launches) *launches = s->prof_n;
+  if (total_ms) *total_ms = tot;
+  s->prof_kernel = 0;
+  s->prof_level = -1;
+  s->prof_n = 0;
+  return MG_OK;
+}
+
+double mg_probe_fp64_gflops(void *stream) { return probe_fp64_gflops((cudaStream_t)stream); }
+
+}  // extern "C"

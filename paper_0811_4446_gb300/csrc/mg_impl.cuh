@@ -1,0 +1,93 @@
+// Internal declarations of the GB300 multigrid solver (not part of the C ABI).
+//
+// Storage: every node field is a (nz + 1) x P array (P = pitch >= nr + 1, a
+// multiple of 4 so that each row starts on a 32-byte boundary), row j (axial)
+// slow, column i (radial) fast.  Face coefficients are stored at the node that
+// is the lower-index end of the face: r-face (i+1/2, j) at [j][i], z-face
+// (i, j+1/2) at [j][i].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mgk {
+
+// Physical constants (SI): e / eps0 of eq. 5.
+constexpr double kECharge = 1.602176634e-19;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kKappa = kECharge / kEps0;
+
+enum { NE = 0, NP = 1, NV = 2 };
+// face-coefficient slots: per species s (0 = electrons, 1 = ions): G-term, F-term, V-derivative
+enum { CGE = 0, CFE = 1, CVE = 2, CGP = 3, CFP = 4, CVP = 5, NCOEF = 6 };
+
+// Transport inputs (mu, D constant or tabulated in |E|), already divided by the pressure factor.
+struct Transport {
+  double mu_e, D_e, mu_p, D_p;
+  const double *table;  // device, rows x 5 (|E|, mu_e, D_e, mu_p, D_p), or nullptr
+  int rows;
+  double inv_pf;        // 1 / pressure factor (applied to tabulated values)
+};
+
+// One multigrid level: geometry, state and work arrays (device pointers).
+template <typename T>
+struct LevelT {
+  int nr, nz, P;
+  T dr;
+  const T *dz, *dzc, *volr;  // nz, nz+1, nr+1 (geometry in the level's arithmetic type)
+  const T *wz;               // odd fine row j: weight of the upper coarse node (nz+1 entries)
+  T *cr[NCOEF], *cz[NCOEF];  // face coefficients
+  T *du[3], *f[3], *r[3];
+};
+using Level = LevelT<double>;
+
+struct StateView {           // nonlinear state on one level (FP64)
+  double *u[3], *uold[3];
+  const double *S[2];
+};
+
+// ---- launch wrappers (mg_kernels.cu) ------------------------------------------------------
+// All take the stream last and return cudaGetLastError() of the launch.
+void count_launch(int n = 1);
+
+cudaError_t launch_coef(const Level &L, const StateView &sv, const Transport &tr, cudaStream_t st);
+// Residual rows F at the state; writes f = -F into L.f (if write_f) and F into Fout (may be null);
+// partial sums of F^2 and T^2 per field reduced to out6[0..5] (F2 e,p,V ; T2 e,p,V).
+cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport &tr, double dt,
+                            bool write_f, double *Fout[3], double *partials, unsigned *counter,
+                            double *out6, cudaStream_t st);
+template <typename T>
+cudaError_t launch_smooth(const LevelT<T> &L, double dt, double kap, int color, cudaStream_t st);
+// r = f - J v (or out = J v when f == nullptr); optional per-field norms (sum of squares) -> out3
+template <typename T>
+cudaError_t launch_linres(const LevelT<T> &L, double dt, double kap, T *const v[3], T *const f[3], T *out[3],
+                          double *partials, unsigned *counter, double *out3, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong_add(const LevelT<T> &C, const LevelT<T> &F, cudaStream_t st);
+cudaError_t launch_inject(const Level &F, const StateView &fs, const Level &C, const StateView &cs,
+                          bool with_old, bool with_sources, cudaStream_t st);
+cudaError_t launch_prolong_state(const Level &C, const StateView &cs, const Level &F,
+                                 const StateView &fs, cudaStream_t st);
+// Coarsest level: assemble the dense Jacobian, equilibrate, invert (one CTA).
+cudaError_t launch_coarse_factor(const Level &L, double dt, double *M, double *Minv, double *rs,
+                                 double *cs, int *flag, cudaStream_t st);
+template <typename T>
+cudaError_t launch_coarse_solve(const LevelT<T> &L, const double *Minv, const double *rs, const double *cs,
+                                double nscale, cudaStream_t st);
+// u += du on unknown rows; out2[0] = max |dV|, out2[1] = sum of du^2 (non-finite check)
+cudaError_t launch_update(const Level &L, const StateView &sv, double *partials, unsigned *counter,
+                          double *out2, cudaStream_t st);
+template <typename T>
+cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st);
+// mixed form
+cudaError_t launch_coef_to32(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);
+cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);
+cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double dt, double n0, double *partials,
+                                  unsigned *counter, double *out3, cudaStream_t st);
+cudaError_t launch_dirichlet(const Level &L, const StateView &sv, double Vc, double Va, cudaStream_t st);
+unsigned long long total_launches();
+double probe_fp64_gflops(cudaStream_t st);
+
+}  // namespace mgk

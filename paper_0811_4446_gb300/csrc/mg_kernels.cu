@@ -1,0 +1,911 @@
+// CUDA kernels of the axisymmetric drift-diffusion / Poisson multigrid solver (FP64 path).
+//
+// Paper: Ristivojevic & Petrovic, arXiv:0811.4446, Sec. 2.
+//  * coefficient build: Scharfetter-Gummel face fluxes (eqs. 8-11) and their
+//    derivatives, which make up the 3x3 blocks of the Newton system (eq. 14);
+//  * nonlinear residual: eq. 7 for both species and eqs. 12-13 (Poisson), in
+//    finite-volume form (rows multiplied by the control volume);
+//  * red-black collective (3x3 point-block) Gauss-Seidel smoother, linear
+//    residual, full-weighting restriction R = P^T, bilinear prolongation, dense
+//    coarsest-level inverse: the multigrid solver of eq. 14.
+//
+// Thread mapping: one thread per node (or per node of one colour), 32 x 8 blocks,
+// x = radial index (coalesced), y = axial index.
+#include <cstdio>
+
+#include "mg_impl.cuh"
+
+namespace mgk {
+
+static unsigned long long g_launches = 0;
+void count_launch(int n) { __atomic_add_fetch(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+unsigned long long total_launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+constexpr int BX = 32, BY = 8, NT = BX * BY;
+
+// ------------------------------------------------------------------------------------------
+// Bernoulli function B(x) = x / (e^x - 1): F(x) = B(x), G(x) = B(-x) (definitions after eq. 11).
+// Returns B(x), B(-x), B'(x), B'(-x).  |x| < 0.1: Bernoulli-number series
+// (B_2 = 1/6, B_4 = -1/30, B_6 = 1/42, B_8 = -1/30, B_10 = 5/66); otherwise, for y = |x|,
+// B(y) = y e^{-y} / (1 - e^{-y}) with 1 - e^{-y} = -expm1(-y) (no overflow), and the
+// reflections B(-y) = B(y) + y, B'(-y) = -B'(y) - 1.
+struct Bern {
+  double Bp, Bm, dBp, dBm;
+};
+
+__device__ __forceinline__ Bern bernoulli(double x) {
+  const double y = fabs(x);
+  double by, dby;
+  if (y < 0.1) {
+    const double y2 = y * y;
+    const double even =
+        1.0 + y2 * (1.0 / 12.0 +
+                    y2 * (-1.0 / 720.0 + y2 * (1.0 / 30240.0 + y2 * (-1.0 / 1209600.0 + y2 * (1.0 / 47900160.0)))));
+    by = even - 0.5 * y;
+    const double odd =
+        y * (1.0 / 6.0 + y2 * (-1.0 / 180.0 + y2 * (1.0 / 5040.0 + y2 * (-1.0 / 151200.0 + y2 * (1.0 / 4790016.0)))));
+    dby = odd - 0.5;
+  } else {
+    const double t = exp(-y);
+    const double em = -expm1(-y);
+    by = y * t / em;
+    dby = t * (em - y) / (em * em);
+  }
+  Bern b;
+  if (x >= 0.0) {
+    b.Bp = by; b.Bm = by + y; b.dBp = dby; b.dBm = -dby - 1.0;
+  } else {
+    b.Bp = by + y; b.Bm = by; b.dBp = -dby - 1.0; b.dBm = dby;
+  }
+  return b;
+}
+
+// ------------------------------------------------------------------------------------------
+// Transport at a face: constants, or linear interpolation in |E| between table rows.
+struct FaceTr {
+  double mu_e, D_e, mu_p, D_p;
+};
+
+__device__ __forceinline__ FaceTr lookup(const Transport &tr, double Eabs) {
+  const double *T = tr.table;
+  const int n = tr.rows;
+  const double x = fmin(fmax(Eabs, __ldg(T)), __ldg(T + 5 * (n - 1)));
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(T + 5 * mid) <= x) lo = mid; else hi = mid;
+  }
+  const double *a = T + 5 * lo, *b = a + 5;
+  const double t = (x - __ldg(a)) / (__ldg(b) - __ldg(a));
+  FaceTr f;
+  f.mu_e = (__ldg(a + 1) + t * (__ldg(b + 1) - __ldg(a + 1))) * tr.inv_pf;
+  f.D_e = (__ldg(a + 2) + t * (__ldg(b + 2) - __ldg(a + 2))) * tr.inv_pf;
+  f.mu_p = (__ldg(a + 3) + t * (__ldg(b + 3) - __ldg(a + 3))) * tr.inv_pf;
+  f.D_p = (__ldg(a + 4) + t * (__ldg(b + 4) - __ldg(a + 4))) * tr.inv_pf;
+  return f;
+}
+
+// |E| on the r-face (i+1/2, j) (1 <= j <= nz-1): normal part across the face, transverse part the
+// mean of the four adjacent z-face fields (E = -grad V, eq. 6).
+__device__ __forceinline__ double eabs_rface(const Level &L, const double *V, int j, int i) {
+  const size_t k = (size_t)j * L.P + i;
+  const double En = -(V[k + 1] - V[k]) / L.dr;
+  const double dzm = L.dz[j - 1], dzp = L.dz[j];
+  const double a = -(V[k] - V[k - L.P]) / dzm, b = -(V[k + L.P] - V[k]) / dzp;
+  const double c = -(V[k + 1] - V[k + 1 - L.P]) / dzm, d = -(V[k + 1 + L.P] - V[k + 1]) / dzp;
+  const double Et = 0.25 * (((a + b) + c) + d);
+  return sqrt(En * En + Et * Et);
+}
+
+// |E| on the z-face (i, j+1/2) (0 <= j <= nz-1): the transverse part is zero on the axis and
+// on the outer wall (dV/dr = 0 there by symmetry).
+__device__ __forceinline__ double eabs_zface(const Level &L, const double *V, int j, int i) {
+  const size_t k = (size_t)j * L.P + i;
+  const double En = -(V[k + L.P] - V[k]) / L.dz[j];
+  double Et = 0.0;
+  if (i > 0 && i < L.nr) {
+    const double a = -(V[k] - V[k - 1]) / L.dr, b = -(V[k + 1] - V[k]) / L.dr;
+    const double c = -(V[k + L.P] - V[k + L.P - 1]) / L.dr, d = -(V[k + L.P + 1] - V[k + L.P]) / L.dr;
+    Et = 0.25 * (((a + b) + c) + d);
+  }
+  return sqrt(En * En + Et * Et);
+}
+
+__device__ __forceinline__ FaceTr tr_rface(const Level &L, const Transport &tr, const double *V, int j, int i) {
+  if (!tr.table) return FaceTr{tr.mu_e, tr.D_e, tr.mu_p, tr.D_p};
+  return lookup(tr, eabs_rface(L, V, j, i));
+}
+__device__ __forceinline__ FaceTr tr_zface(const Level &L, const Transport &tr, const double *V, int j, int i) {
+  if (!tr.table) return FaceTr{tr.mu_e, tr.D_e, tr.mu_p, tr.D_p};
+  return lookup(tr, eabs_zface(L, V, j, i));
+}
+
+// SG flux through a face from L to R (eqs. 8-11): alpha = -s (mu/D)(V_R - V_L),
+// flux = g D (n_L G(alpha) - n_R F(alpha)).
+__device__ __forceinline__ double sg_flux(double g, double mu, double D, double s, double nL, double nR,
+                                          double dV) {
+  const Bern b = bernoulli(-s * (mu / D) * dV);
+  return g * D * (nL * b.Bm - nR * b.Bp);
+}
+
+// Derivatives of the SG flux: cG = d/dn_L, cF = -d/dn_R, cV = d/dV_R = -d/dV_L (mu, D frozen).
+__device__ __forceinline__ void sg_coef(double g, double mu, double D, double s, double nL, double nR, double dV,
+                                        double &cG, double &cF, double &cV) {
+  const Bern b = bernoulli(-s * (mu / D) * dV);
+  cG = g * D * b.Bm;
+  cF = g * D * b.Bp;
+  // G'(a) = -B'(-a), F'(a) = B'(a):  cV = -s g mu (n_L G' - n_R F') = s g mu (n_L B'(-a) + n_R B'(a))
+  cV = s * g * mu * (nL * b.dBm + nR * b.dBp);
+}
+
+// ------------------------------------------------------------------------------------------
+// Deterministic block reduction: every block writes K partials, the last block to finish sums
+// them in block order and writes out[K].  op: 0 = sum, 1 = max.
+template <int K>
+__device__ void reduce_finish(double (&v)[K], double *partials, unsigned *counter, double *out, int op) {
+  __shared__ double sh[K][NT / 32];
+  __shared__ bool last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double x = v[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = op ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) sh[q][wid] = x;
+  }
+  __syncthreads();
+  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double x = sh[q][0];
+      for (int w = 1; w < nwarps; ++w) x = op ? fmax(x, sh[q][w]) : x + sh[q][w];
+      partials[(size_t)bid * K + q] = x;
+    }
+    __threadfence();
+    const unsigned done = atomicAdd(counter, 1u);
+    last = (done == (unsigned)nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nthr = blockDim.x * blockDim.y;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double x = op ? 0.0 : 0.0;
+    bool first = true;
+    for (int b = tid; b < nblocks; b += nthr) {
+      const double y = ((volatile double *)partials)[(size_t)b * K + q];
+      x = first ? y : (op ? fmax(x, y) : x + y);
+      first = false;
+    }
+    if (first) x = op ? -1.0 : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = op ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) sh[q][wid] = x;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double x = sh[q][0];
+      for (int w = 1; w < nwarps; ++w) x = op ? fmax(x, sh[q][w]) : x + sh[q][w];
+      out[q] = x;
+    }
+    *counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// K1: face coefficients (eqs. 8-11 differentiated) for the east r-face and north z-face of each node.
+__global__ void k_coef(Level L, StateView sv, Transport tr) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.nr || j > L.nz) return;
+  const size_t k = (size_t)j * L.P + i;
+  const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
+  if (i < L.nr && j >= 1 && j < L.nz) {
+    const double g = (i + 0.5) * L.dzc[j];
+    const FaceTr t = tr_rface(L, tr, V, j, i);
+    const double dV = V[k + 1] - V[k];
+    double cG, cF, cV;
+    sg_coef(g, t.mu_e, t.D_e, -1.0, ne[k], ne[k + 1], dV, cG, cF, cV);
+    L.cr[CGE][k] = cG; L.cr[CFE][k] = cF; L.cr[CVE][k] = cV;
+    sg_coef(g, t.mu_p, t.D_p, 1.0, np[k], np[k + 1], dV, cG, cF, cV);
+    L.cr[CGP][k] = cG; L.cr[CFP][k] = cF; L.cr[CVP][k] = cV;
+  }
+  if (j < L.nz) {
+    const double g = L.volr[i] / L.dz[j];
+    const FaceTr t = tr_zface(L, tr, V, j, i);
+    const double dV = V[k + L.P] - V[k];
+    double cG, cF, cV;
+    sg_coef(g, t.mu_e, t.D_e, -1.0, ne[k], ne[k + L.P], dV, cG, cF, cV);
+    L.cz[CGE][k] = cG; L.cz[CFE][k] = cF; L.cz[CVE][k] = cV;
+    sg_coef(g, t.mu_p, t.D_p, 1.0, np[k], np[k + L.P], dV, cG, cF, cV);
+    L.cz[CGP][k] = cG; L.cz[CFP][k] = cF; L.cz[CVP][k] = cV;
+  }
+}
+
+cudaError_t launch_coef(const Level &L, const StateView &sv, const Transport &tr, cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
+  k_coef<<<g, b, 0, st>>>(L, sv, tr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// K2: nonlinear residual (eq. 7 x control volume; eqs. 12-13 x control volume) and term sums.
+__global__ void k_residual(Level L, StateView sv, Transport tr, double dt_inv, int write_f, double *F0,
+                           double *F1, double *F2, double *partials, unsigned *counter, double *out6) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (i <= L.nr && j < L.nz) {
+    const int P = L.P;
+    const size_t k = (size_t)j * P + i;
+    const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
+    const double A = L.volr[i] * L.dzc[j];
+    double Fe = 0, Fp = 0, FV = 0, Te = 0, Tp = 0, TV = 0;
+    if (dt_inv > 0.0) {
+      Fe += A * (ne[k] - sv.uold[NE][k]) * dt_inv;
+      Fp += A * (np[k] - sv.uold[NP][k]) * dt_inv;
+      Te += A * (fabs(ne[k]) + fabs(sv.uold[NE][k])) * dt_inv;
+      Tp += A * (fabs(np[k]) + fabs(sv.uold[NP][k])) * dt_inv;
+    }
+    Fe -= A * sv.S[0][k];
+    Fp -= A * sv.S[1][k];
+    Te += A * fabs(sv.S[0][k]);
+    Tp += A * fabs(sv.S[1][k]);
+    // faces: sign +1 where this node is the L end (east, north), -1 where it is the R end (west, south)
+#pragma unroll
+    for (int face = 0; face < 4; ++face) {
+      size_t kL, kR;
+      double g;
+      FaceTr t;
+      double sgn;
+      if (face == 0) {          // east r-face (i+1/2, j)
+        if (i >= L.nr) continue;
+        kL = k; kR = k + 1; g = (i + 0.5) * L.dzc[j]; t = tr_rface(L, tr, V, j, i); sgn = 1.0;
+      } else if (face == 1) {   // west r-face (i-1/2, j)
+        if (i == 0) continue;
+        kL = k - 1; kR = k; g = (i - 0.5) * L.dzc[j]; t = tr_rface(L, tr, V, j, i - 1); sgn = -1.0;
+      } else if (face == 2) {   // north z-face (i, j+1/2)
+        kL = k; kR = k + P; g = L.volr[i] / L.dz[j]; t = tr_zface(L, tr, V, j, i); sgn = 1.0;
+      } else {                  // south z-face (i, j-1/2)
+        kL = k - P; kR = k; g = L.volr[i] / L.dz[j - 1]; t = tr_zface(L, tr, V, j - 1, i); sgn = -1.0;
+      }
+      const double dV = V[kR] - V[kL];
+      const double pe = sg_flux(g, t.mu_e, t.D_e, -1.0, ne[kL], ne[kR], dV);
+      const double pp = sg_flux(g, t.mu_p, t.D_p, 1.0, np[kL], np[kR], dV);
+      const double ps = g * dV;
+      Fe += sgn * pe; Fp += sgn * pp; FV += sgn * ps;
+      Te += fabs(pe); Tp += fabs(pp); TV += fabs(ps);
+    }
+    FV += A * kKappa * (np[k] - ne[k]);
+    TV += A * kKappa * (fabs(np[k]) + fabs(ne[k]));
+    if (write_f) { L.f[NE][k] = -Fe; L.f[NP][k] = -Fp; L.f[NV][k] = -FV; }
+    if (F0) { F0[k] = Fe; F1[k] = Fp; F2[k] = FV; }
+    acc[0] = Fe * Fe; acc[1] = Fp * Fp; acc[2] = FV * FV;
+    acc[3] = Te * Te; acc[4] = Tp * Tp; acc[5] = TV * TV;
+  }
+  reduce_finish<6>(acc, partials, counter, out6, 0);
+}
+
+cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport &tr, double dt, bool write_f,
+                            double *Fout[3], double *partials, unsigned *counter, double *out6, cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
+  k_residual<<<g, b, 0, st>>>(L, sv, tr, dt > 0 ? 1.0 / dt : 0.0, write_f ? 1 : 0, Fout ? Fout[0] : nullptr,
+                              Fout ? Fout[1] : nullptr, Fout ? Fout[2] : nullptr, partials, counter, out6);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Stencil of eq. 14 at node (j, i): diagonal block a (7 nonzeros) and the products of the
+// four off-diagonal blocks with a vector v (off-diagonal blocks have 5 nonzeros).  T is the
+// arithmetic type (double: FP64 path; float: inner V-cycle of the mixed form, whose density
+// unknowns and rows are scaled by n0 so that kap = (e/eps0) n0 and cV carries 1/n0).
+template <typename T>
+struct Stencil {
+  T a11, a13, a22, a23, a31, a32, a33;  // diagonal block
+  T oe, op, oV;                         // sum over neighbours of (off-diagonal block) * v_nb
+};
+
+template <typename T>
+__device__ __forceinline__ Stencil<T> stencil(const LevelT<T> &L, T dt_inv, T kap, int j, int i, const T *ve,
+                                              const T *vp, const T *vV) {
+  const int P = L.P;
+  const size_t k = (size_t)j * P + i;
+  const T A = L.volr[i] * L.dzc[j];
+  Stencil<T> s;
+  s.a11 = A * dt_inv; s.a22 = A * dt_inv;
+  s.a13 = 0; s.a23 = 0; s.a33 = 0;
+  s.a31 = -A * kap; s.a32 = A * kap;
+  s.oe = 0; s.op = 0; s.oV = 0;
+  if (i < L.nr) {  // east: this node is L
+    const T cGe = L.cr[CGE][k], cFe = L.cr[CFE][k], cVe = L.cr[CVE][k];
+    const T cGp = L.cr[CGP][k], cFp = L.cr[CFP][k], cVp = L.cr[CVP][k];
+    const T g = (T(i) + T(0.5)) * L.dzc[j];
+    s.a11 += cGe; s.a13 -= cVe; s.a22 += cGp; s.a23 -= cVp; s.a33 -= g;
+    const T we = ve[k + 1], wp = vp[k + 1], wV = vV[k + 1];
+    s.oe += -cFe * we + cVe * wV; s.op += -cFp * wp + cVp * wV; s.oV += g * wV;
+  }
+  if (i > 0) {     // west: this node is R
+    const size_t kw = k - 1;
+    const T cGe = L.cr[CGE][kw], cFe = L.cr[CFE][kw], cVe = L.cr[CVE][kw];
+    const T cGp = L.cr[CGP][kw], cFp = L.cr[CFP][kw], cVp = L.cr[CVP][kw];
+    const T g = (T(i) - T(0.5)) * L.dzc[j];
+    s.a11 += cFe; s.a13 -= cVe; s.a22 += cFp; s.a23 -= cVp; s.a33 -= g;
+    const T we = ve[kw], wp = vp[kw], wV = vV[kw];
+    s.oe += -cGe * we + cVe * wV; s.op += -cGp * wp + cVp * wV; s.oV += g * wV;
+  }
+  {                // north: this node is L (the neighbour may be an electrode node: v = 0 there)
+    const T cGe = L.cz[CGE][k], cFe = L.cz[CFE][k], cVe = L.cz[CVE][k];
+    const T cGp = L.cz[CGP][k], cFp = L.cz[CFP][k], cVp = L.cz[CVP][k];
+    const T g = L.volr[i] / L.dz[j];
+    s.a11 += cGe; s.a13 -= cVe; s.a22 += cGp; s.a23 -= cVp; s.a33 -= g;
+    const size_t kn = k + P;
+    const T we = ve[kn], wp = vp[kn], wV = vV[kn];
+    s.oe += -cFe * we + cVe * wV; s.op += -cFp * wp + cVp * wV; s.oV += g * wV;
+  }
+  {                // south: this node is R
+    const size_t ks = k - P;
+    const T cGe = L.cz[CGE][ks], cFe = L.cz[CFE][ks], cVe = L.cz[CVE][ks];
+    const T cGp = L.cz[CGP][ks], cFp = L.cz[CFP][ks], cVp = L.cz[CVP][ks];
+    const T g = L.volr[i] / L.dz[j - 1];
+    s.a11 += cFe; s.a13 -= cVe; s.a22 += cFp; s.a23 -= cVp; s.a33 -= g;
+    const T we = ve[ks], wp = vp[ks], wV = vV[ks];
+    s.oe += -cGe * we + cVe * wV; s.op += -cGp * wp + cVp * wV; s.oV += g * wV;
+  }
+  return s;
+}
+
+// K3: red-black collective Gauss-Seidel half sweep: solve the 3x3 diagonal block of every node of
+// one colour (red = (i + j) even) against the current neighbours.  The block has the pattern
+// [[a11, 0, a13], [0, a22, a23], [a31, a32, a33]] and is solved through its Schur complement in V.
+template <typename T>
+__global__ void k_smooth(LevelT<T> L, T dt_inv, T kap, int color) {
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + color) & 1);
+  if (j >= L.nz || i > L.nr) return;
+  const size_t k = (size_t)j * L.P + i;
+  const Stencil<T> s = stencil<T>(L, dt_inv, kap, j, i, L.du[NE], L.du[NP], L.du[NV]);
+  const T re = L.f[NE][k] - s.oe, rp = L.f[NP][k] - s.op, rV = L.f[NV][k] - s.oV;
+  const T i11 = T(1) / s.a11, i22 = T(1) / s.a22;
+  const T sch = s.a33 - s.a31 * s.a13 * i11 - s.a32 * s.a23 * i22;
+  const T xV = (rV - s.a31 * re * i11 - s.a32 * rp * i22) / sch;
+  L.du[NE][k] = (re - s.a13 * xV) * i11;
+  L.du[NP][k] = (rp - s.a23 * xV) * i22;
+  L.du[NV][k] = xV;
+}
+
+template <typename T>
+cudaError_t launch_smooth(const LevelT<T> &L, double dt, double kap, int color, cudaStream_t st) {
+  dim3 b(BX, BY), g(((L.nr + 2) / 2 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
+  k_smooth<T><<<g, b, 0, st>>>(L, T(dt > 0 ? 1.0 / dt : 0.0), T(kap), color);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_smooth<double>(const LevelT<double> &, double, double, int, cudaStream_t);
+template cudaError_t launch_smooth<float>(const LevelT<float> &, double, double, int, cudaStream_t);
+
+// K4: linear residual r = f - J v (or J v when f is null), optional per-field sums of squares
+// (accumulated in FP64).
+template <typename T>
+__global__ void k_linres(LevelT<T> L, T dt_inv, T kap, const T *v0, const T *v1, const T *v2, const T *f0,
+                         const T *f1, const T *f2, T *o0, T *o1, T *o2, double *partials, unsigned *counter,
+                         double *out3) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  double acc[3] = {0, 0, 0};
+  if (i <= L.nr && j < L.nz) {
+    const size_t k = (size_t)j * L.P + i;
+    const Stencil<T> s = stencil<T>(L, dt_inv, kap, j, i, v0, v1, v2);
+    T je = s.a11 * v0[k] + s.a13 * v2[k] + s.oe;
+    T jp = s.a22 * v1[k] + s.a23 * v2[k] + s.op;
+    T jV = s.a31 * v0[k] + s.a32 * v1[k] + s.a33 * v2[k] + s.oV;
+    if (f0) { je = f0[k] - je; jp = f1[k] - jp; jV = f2[k] - jV; }
+    o0[k] = je; o1[k] = jp; o2[k] = jV;
+    acc[0] = (double)je * je; acc[1] = (double)jp * jp; acc[2] = (double)jV * jV;
+  }
+  if (out3) reduce_finish<3>(acc, partials, counter, out3, 0);
+}
+
+template <typename T>
+cudaError_t launch_linres(const LevelT<T> &L, double dt, double kap, T *const v[3], T *const f[3], T *out[3],
+                          double *partials, unsigned *counter, double *out3, cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
+  k_linres<T><<<g, b, 0, st>>>(L, T(dt > 0 ? 1.0 / dt : 0.0), T(kap), v[0], v[1], v[2], f ? f[0] : nullptr,
+                               f ? f[1] : nullptr, f ? f[2] : nullptr, out[0], out[1], out[2], partials, counter,
+                               out3);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_linres<double>(const LevelT<double> &, double, double, double *const[3],
+                                           double *const[3], double *[3], double *, unsigned *, double *,
+                                           cudaStream_t);
+template cudaError_t launch_linres<float>(const LevelT<float> &, double, double, float *const[3], float *const[3],
+                                          float *[3], double *, unsigned *, double *, cudaStream_t);
+
+// K5: restriction f_c = P^T r (full weighting in the node coordinates), and du_c = 0.
+template <typename T>
+__global__ void k_restrict(LevelT<T> F, LevelT<T> C) {
+  const int I = blockIdx.x * BX + threadIdx.x;
+  const int J = blockIdx.y * BY + threadIdx.y + 1;
+  if (I > C.nr || J >= C.nz) return;
+  const size_t kc = (size_t)J * C.P + I;
+  T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj) {
+    const int j = 2 * J + dj;
+    const T wz = dj == 0 ? T(1) : (dj < 0 ? F.wz[j] : T(1) - F.wz[j]);
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const int i = 2 * I + di;
+      if (i < 0 || i > F.nr) continue;
+      const T w = wz * (di == 0 ? T(1) : T(0.5));
+      const size_t kf = (size_t)j * F.P + i;
+      s0 += w * F.r[NE][kf]; s1 += w * F.r[NP][kf]; s2 += w * F.r[NV][kf];
+    }
+  }
+  C.f[NE][kc] = s0; C.f[NP][kc] = s1; C.f[NV][kc] = s2;
+  C.du[NE][kc] = T(0); C.du[NP][kc] = T(0); C.du[NV][kc] = T(0);
+}
+
+template <typename T>
+cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st) {
+  dim3 b(BX, BY), g((C.nr + 1 + BX - 1) / BX, (C.nz - 1 + BY - 1) / BY);
+  k_restrict<T><<<g, b, 0, st>>>(F, C);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_restrict<double>(const LevelT<double> &, const LevelT<double> &, cudaStream_t);
+template cudaError_t launch_restrict<float>(const LevelT<float> &, const LevelT<float> &, cudaStream_t);
+
+// K6: prolongation and correction du_f += P du_c (bilinear in (r, z)).
+template <typename T>
+__global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (i > F.nr || j >= F.nz) return;
+  const size_t kf = (size_t)j * F.P + i;
+  int J0, J1;
+  T w0, w1;
+  if (j & 1) { J0 = (j - 1) >> 1; J1 = J0 + 1; w1 = F.wz[j]; w0 = T(1) - w1; }
+  else { J0 = J1 = j >> 1; w0 = T(1); w1 = T(0); }
+  int I0, I1;
+  T v0, v1;
+  if (i & 1) { I0 = (i - 1) >> 1; I1 = I0 + 1; v0 = v1 = T(0.5); }
+  else { I0 = I1 = i >> 1; v0 = T(1); v1 = T(0); }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const T *c = C.du[q];
+    const T a = v0 * c[(size_t)J0 * C.P + I0] + v1 * c[(size_t)J0 * C.P + I1];
+    const T b = v0 * c[(size_t)J1 * C.P + I0] + v1 * c[(size_t)J1 * C.P + I1];
+    F.du[q][kf] += w0 * a + w1 * b;
+  }
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const LevelT<T> &C, const LevelT<T> &F, cudaStream_t st) {
+  dim3 b(BX, BY), g((F.nr + 1 + BX - 1) / BX, (F.nz - 1 + BY - 1) / BY);
+  k_prolong_add<T><<<g, b, 0, st>>>(C, F);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_prolong_add<double>(const LevelT<double> &, const LevelT<double> &, cudaStream_t);
+template cudaError_t launch_prolong_add<float>(const LevelT<float> &, const LevelT<float> &, cudaStream_t);
+
+// Injection of the state (and optionally the old time level and the sources) to the next grid.
+__global__ void k_inject(Level F, StateView fs, Level C, StateView cs, int with_old, int with_src) {
+  const int I = blockIdx.x * BX + threadIdx.x;
+  const int J = blockIdx.y * BY + threadIdx.y;
+  if (I > C.nr || J > C.nz) return;
+  const size_t kc = (size_t)J * C.P + I, kf = (size_t)(2 * J) * F.P + 2 * I;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) cs.u[q][kc] = fs.u[q][kf];
+  if (with_old) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cs.uold[q][kc] = fs.uold[q][kf];
+  }
+  if (with_src) {
+    ((double *)cs.S[0])[kc] = fs.S[0][kf];
+    ((double *)cs.S[1])[kc] = fs.S[1][kf];
+  }
+}
+
+cudaError_t launch_inject(const Level &F, const StateView &fs, const Level &C, const StateView &cs, bool with_old,
+                          bool with_sources, cudaStream_t st) {
+  dim3 b(BX, BY), g((C.nr + 1 + BX - 1) / BX, (C.nz + 1 + BY - 1) / BY);
+  k_inject<<<g, b, 0, st>>>(F, fs, C, cs, with_old ? 1 : 0, with_sources ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Continuation: bilinear interpolation of (n_e, n_p, V) from the coarse grid to every fine node.
+__global__ void k_prolong_state(Level C, StateView cs, Level F, StateView fs) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i > F.nr || j > F.nz) return;
+  const size_t kf = (size_t)j * F.P + i;
+  int J0, J1;
+  double w0, w1;
+  if (j & 1) { J0 = (j - 1) >> 1; J1 = J0 + 1; w1 = F.wz[j]; w0 = 1.0 - w1; }
+  else { J0 = J1 = j >> 1; w0 = 1.0; w1 = 0.0; }
+  int I0, I1;
+  double v0, v1;
+  if (i & 1) { I0 = (i - 1) >> 1; I1 = I0 + 1; v0 = v1 = 0.5; }
+  else { I0 = I1 = i >> 1; v0 = 1.0; v1 = 0.0; }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const double *c = cs.u[q];
+    const double a = v0 * c[(size_t)J0 * C.P + I0] + v1 * c[(size_t)J0 * C.P + I1];
+    const double b = v0 * c[(size_t)J1 * C.P + I0] + v1 * c[(size_t)J1 * C.P + I1];
+    fs.u[q][kf] = w0 * a + w1 * b;
+  }
+}
+
+cudaError_t launch_prolong_state(const Level &C, const StateView &cs, const Level &F, const StateView &fs,
+                                 cudaStream_t st) {
+  dim3 b(BX, BY), g((F.nr + 1 + BX - 1) / BX, (F.nz + 1 + BY - 1) / BY);
+  k_prolong_state<<<g, b, 0, st>>>(C, cs, F, fs);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// K7: coarsest level.  Assemble the dense 3-field Jacobian (unknown q = 3 * node + field,
+// node = (j - 1) * (nr + 1) + i), scale columns then rows to unit max-abs entry, and invert the
+// scaled matrix by Gauss-Jordan elimination with partial pivoting.  One CTA.
+constexpr int CT = 256;
+
+__global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, double *M, double *Minv,
+                                                      double *rs, double *cs, int *flag) {
+  const int nn = (L.nr + 1) * (L.nz - 1);
+  const int n = 3 * nn;
+  const int tid = threadIdx.x;
+  __shared__ double fac[3 * 9 * 9];
+  __shared__ double pv[CT];
+  __shared__ int pi[CT];
+  for (int e = tid; e < n * n; e += CT) { M[e] = 0.0; Minv[e] = 0.0; }
+  __syncthreads();
+  for (int node = tid; node < nn; node += CT) {
+    const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
+    const size_t k = (size_t)j * L.P + i;
+    const double A = L.volr[i] * L.dzc[j];
+    double a11 = A * dt_inv, a22 = A * dt_inv, a13 = 0, a23 = 0, a33 = 0;
+    const int re = 3 * node, rp = re + 1, rv = re + 2;
+    auto put = [&](int row, int col, double v) { M[(size_t)row * n + col] += v; };
+    // east
+    if (i < L.nr) {
+      const int nb = 3 * (node + 1);
+      const double g = (i + 0.5) * L.dzc[j];
+      a11 += L.cr[CGE][k]; a13 -= L.cr[CVE][k]; a22 += L.cr[CGP][k]; a23 -= L.cr[CVP][k]; a33 -= g;
+      put(re, nb, -L.cr[CFE][k]); put(re, nb + 2, L.cr[CVE][k]);
+      put(rp, nb + 1, -L.cr[CFP][k]); put(rp, nb + 2, L.cr[CVP][k]);
+      put(rv, nb + 2, g);
+    }
+    if (i > 0) {
+      const int nb = 3 * (node - 1);
+      const size_t kw = k - 1;
+      const double g = (i - 0.5) * L.dzc[j];
+      a11 += L.cr[CFE][kw]; a13 -= L.cr[CVE][kw]; a22 += L.cr[CFP][kw]; a23 -= L.cr[CVP][kw]; a33 -= g;
+      put(re, nb, -L.cr[CGE][kw]); put(re, nb + 2, L.cr[CVE][kw]);
+      put(rp, nb + 1, -L.cr[CGP][kw]); put(rp, nb + 2, L.cr[CVP][kw]);
+      put(rv, nb + 2, g);
+    }
+    {
+      const double g = L.volr[i] / L.dz[j];
+      a11 += L.cz[CGE][k]; a13 -= L.cz[CVE][k]; a22 += L.cz[CGP][k]; a23 -= L.cz[CVP][k]; a33 -= g;
+      if (j + 1 < L.nz) {
+        const int nb = 3 * (node + L.nr + 1);
+        put(re, nb, -L.cz[CFE][k]); put(re, nb + 2, L.cz[CVE][k]);
+        put(rp, nb + 1, -L.cz[CFP][k]); put(rp, nb + 2, L.cz[CVP][k]);
+        put(rv, nb + 2, g);
+      }
+    }
+    {
+      const size_t ks = k - L.P;
+      const double g = L.volr[i] / L.dz[j - 1];
+      a11 += L.cz[CFE][ks]; a13 -= L.cz[CVE][ks]; a22 += L.cz[CFP][ks]; a23 -= L.cz[CVP][ks]; a33 -= g;
+      if (j - 1 >= 1) {
+        const int nb = 3 * (node - L.nr - 1);
+        put(re, nb, -L.cz[CGE][ks]); put(re, nb + 2, L.cz[CVE][ks]);
+        put(rp, nb + 1, -L.cz[CGP][ks]); put(rp, nb + 2, L.cz[CVP][ks]);
+        put(rv, nb + 2, g);
+      }
+    }
+    put(re, re, a11); put(re, rv, a13);
+    put(rp, rp, a22); put(rp, rv, a23);
+    put(rv, re, -A * kKappa); put(rv, rp, A * kKappa); put(rv, rv, a33);
+  }
+  __syncthreads();
+  // equilibration: columns, then rows
+  for (int c = tid; c < n; c += CT) {
+    double m = 0.0;
+    for (int r = 0; r < n; ++r) m = fmax(m, fabs(M[(size_t)r * n + c]));
+    cs[c] = m > 0.0 ? 1.0 / m : 1.0;
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += CT) {
+    double m = 0.0;
+    for (int c = 0; c < n; ++c) m = fmax(m, fabs(M[(size_t)r * n + c] * cs[c]));
+    rs[r] = m > 0.0 ? 1.0 / m : 1.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += CT) {
+    const int r = e / n, c = e % n;
+    M[e] *= rs[r] * cs[c];
+    Minv[e] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // Gauss-Jordan with partial pivoting (ties: lowest row index)
+  for (int col = 0; col < n; ++col) {
+    double best = -1.0;
+    int bi = col;
+    for (int r = col + tid; r < n; r += CT) {
+      const double v = fabs(M[(size_t)r * n + col]);
+      if (v > best) { best = v; bi = r; }
+    }
+    pv[tid] = best; pi[tid] = bi;
+    __syncthreads();
+    for (int o = CT / 2; o > 0; o >>= 1) {
+      if (tid < o) {
+        const double a = pv[tid], b = pv[tid + o];
+        if (b > a || (b == a && pi[tid + o] < pi[tid])) { pv[tid] = b; pi[tid] = pi[tid + o]; }
+      }
+      __syncthreads();
+    }
+    const int p = pi[0];
+    if (pv[0] <= 0.0) { if (tid == 0) *flag = 1; return; }
+    if (p != col) {
+      for (int c = tid; c < n; c += CT) {
+        double t = M[(size_t)p * n + c]; M[(size_t)p * n + c] = M[(size_t)col * n + c]; M[(size_t)col * n + c] = t;
+        t = Minv[(size_t)p * n + c]; Minv[(size_t)p * n + c] = Minv[(size_t)col * n + c]; Minv[(size_t)col * n + c] = t;
+      }
+    }
+    __syncthreads();
+    const double piv = 1.0 / M[(size_t)col * n + col];
+    __syncthreads();
+    for (int c = tid; c < n; c += CT) { M[(size_t)col * n + c] *= piv; Minv[(size_t)col * n + c] *= piv; }
+    __syncthreads();
+    for (int r = tid; r < n; r += CT) fac[r] = (r == col) ? 0.0 : M[(size_t)r * n + col];
+    __syncthreads();
+    for (int e = tid; e < n * n; e += CT) {
+      const int r = e / n, c = e % n;
+      const double fr = fac[r];
+      if (fr != 0.0) {
+        M[e] -= fr * M[(size_t)col * n + c];
+        Minv[e] -= fr * Minv[(size_t)col * n + c];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *flag = 0;
+}
+
+cudaError_t launch_coarse_factor(const Level &L, double dt, double *M, double *Minv, double *rs, double *cs,
+                                 int *flag, cudaStream_t st) {
+  const int n = 3 * (L.nr + 1) * (L.nz - 1);
+  if (n > 3 * 9 * 9) return cudaErrorInvalidValue;
+  k_coarse_factor<<<1, CT, 0, st>>>(L, dt > 0 ? 1.0 / dt : 0.0, M, Minv, rs, cs, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// du = C Minv R f on the coarsest level (one CTA; one thread per unknown).  For the FP32 inner
+// cycle of the mixed form the density entries of f and du are in units of n0 (nscale = n0):
+// the FP64 inverse acts on unscaled values.
+template <typename T>
+__global__ void __launch_bounds__(CT) k_coarse_solve(LevelT<T> L, const double *Minv, const double *rs,
+                                                     const double *cs, double nscale) {
+  const int nn = (L.nr + 1) * (L.nz - 1);
+  const int n = 3 * nn;
+  __shared__ double fs[3 * 9 * 9];
+  for (int q = threadIdx.x; q < n; q += CT) {
+    const int node = q / 3, fld = q % 3;
+    const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
+    const double sc = fld == NV ? 1.0 : nscale;
+    fs[q] = rs[q] * sc * (double)L.f[fld][(size_t)j * L.P + i];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += CT) {
+    double x = 0.0;
+    for (int c = 0; c < n; ++c) x += Minv[(size_t)q * n + c] * fs[c];
+    const int node = q / 3, fld = q % 3;
+    const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
+    const double sc = fld == NV ? 1.0 : 1.0 / nscale;
+    L.du[fld][(size_t)j * L.P + i] = (T)(cs[q] * x * sc);
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(const LevelT<T> &L, const double *Minv, const double *rs, const double *cs,
+                                double nscale, cudaStream_t st) {
+  k_coarse_solve<T><<<1, CT, 0, st>>>(L, Minv, rs, cs, nscale);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse_solve<double>(const LevelT<double> &, const double *, const double *,
+                                                 const double *, double, cudaStream_t);
+template cudaError_t launch_coarse_solve<float>(const LevelT<float> &, const double *, const double *,
+                                                const double *, double, cudaStream_t);
+
+// Newton update u += du on unknown rows; reduces max |dV| and a non-finite indicator.
+__global__ void k_update(Level L, StateView sv, double *partials, unsigned *counter, double *out2) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  double acc[2] = {0.0, 0.0};
+  if (i <= L.nr && j < L.nz) {
+    const size_t k = (size_t)j * L.P + i;
+    const double a = L.du[NE][k], b = L.du[NP][k], c = L.du[NV][k];
+    sv.u[NE][k] += a; sv.u[NP][k] += b; sv.u[NV][k] += c;
+    acc[0] = fabs(c);
+    acc[1] = (isfinite(a) && isfinite(b) && isfinite(c)) ? 0.0 : 1.0;
+  }
+  reduce_finish<2>(acc, partials, counter, out2, 1);
+}
+
+cudaError_t launch_update(const Level &L, const StateView &sv, double *partials, unsigned *counter, double *out2,
+                          cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
+  k_update<<<g, b, 0, st>>>(L, sv, partials, counter, out2);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Dirichlet electrode rows: n_e = n_p = 0, V = V_cathode (j = 0) and V_anode (j = nz).
+__global__ void k_dirichlet(Level L, StateView sv, double Vc, double Va) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  if (i > L.nr) return;
+  const size_t k0 = i, k1 = (size_t)L.nz * L.P + i;
+  sv.u[NE][k0] = 0.0; sv.u[NP][k0] = 0.0; sv.u[NV][k0] = Vc;
+  sv.u[NE][k1] = 0.0; sv.u[NP][k1] = 0.0; sv.u[NV][k1] = Va;
+}
+
+cudaError_t launch_dirichlet(const Level &L, const StateView &sv, double Vc, double Va, cudaStream_t st) {
+  k_dirichlet<<<(L.nr + 1 + 127) / 128, 128, 0, st>>>(L, sv, Vc, Va);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_zero_du(LevelT<T> L) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.nr || j > L.nz) return;
+  const size_t k = (size_t)j * L.P + i;
+  L.du[NE][k] = T(0); L.du[NP][k] = T(0); L.du[NV][k] = T(0);
+}
+
+template <typename T>
+cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
+  k_zero_du<T><<<g, b, 0, st>>>(L);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_zero_du<double>(const LevelT<double> &, cudaStream_t);
+template cudaError_t launch_zero_du<float>(const LevelT<float> &, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
+// Mixed form.  FP64 face coefficients of one level -> FP32 copies in the n0-scaled unknowns
+// (density unknowns and density rows divided by n0: cG, cF unchanged, cV / n0).
+__global__ void k_coef_to32(Level L, LevelT<float> M, double inv_n0) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.nr || j > L.nz) return;
+  const size_t k = (size_t)j * L.P + i;
+#pragma unroll
+  for (int c = 0; c < NCOEF; ++c) {
+    const double sc = (c == CVE || c == CVP) ? inv_n0 : 1.0;
+    M.cr[c][k] = (float)(L.cr[c][k] * sc);
+    M.cz[c][k] = (float)(L.cz[c][k] * sc);
+  }
+}
+
+cudaError_t launch_coef_to32(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
+  k_coef_to32<<<g, b, 0, st>>>(L, M, 1.0 / n0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Outer FP64 defect of the mixed solve: x += e (e from the FP32 cycle, densities x n0), then
+// r = f - J x in FP64, written as the next FP32 right-hand side (densities / n0), with FP64
+// per-field sums of squares.  Two passes: the update must be complete before J x is applied.
+__global__ void k_mixed_update(Level L, LevelT<float> M, double n0) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (i > L.nr || j >= L.nz) return;
+  const size_t k = (size_t)j * L.P + i;
+  L.du[NE][k] += n0 * (double)M.du[NE][k];
+  L.du[NP][k] += n0 * (double)M.du[NP][k];
+  L.du[NV][k] += (double)M.du[NV][k];
+}
+
+cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
+  k_mixed_update<<<g, b, 0, st>>>(L, M, n0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_outer_residual(Level L, LevelT<float> M, double dt_inv, double inv_n0, double *partials,
+                                 unsigned *counter, double *out3) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  double acc[3] = {0, 0, 0};
+  if (i <= L.nr && j < L.nz) {
+    const size_t k = (size_t)j * L.P + i;
+    const double *v0 = L.du[NE], *v1 = L.du[NP], *v2 = L.du[NV];
+    const Stencil<double> s = stencil<double>(L, dt_inv, kKappa, j, i, v0, v1, v2);
+    const double re = L.f[NE][k] - (s.a11 * v0[k] + s.a13 * v2[k] + s.oe);
+    const double rp = L.f[NP][k] - (s.a22 * v1[k] + s.a23 * v2[k] + s.op);
+    const double rV = L.f[NV][k] - (s.a31 * v0[k] + s.a32 * v1[k] + s.a33 * v2[k] + s.oV);
+    M.f[NE][k] = (float)(re * inv_n0);
+    M.f[NP][k] = (float)(rp * inv_n0);
+    M.f[NV][k] = (float)rV;
+    acc[0] = re * re; acc[1] = rp * rp; acc[2] = rV * rV;
+  }
+  reduce_finish<3>(acc, partials, counter, out3, 0);
+}
+
+cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double dt, double n0, double *partials,
+                                  unsigned *counter, double *out3, cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
+  k_outer_residual<<<g, b, 0, st>>>(L, M, dt > 0 ? 1.0 / dt : 0.0, 1.0 / n0, partials, counter, out3);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 FMA throughput probe: 8 independent FMA chains per thread, enough warps to fill every SM.
+__global__ void k_fp64_probe(double *out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = threadIdx.x * 1e-3 + q;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += x[q];
+  if (s == 12345.678) out[0] = s;  // keeps the chains live
+}
+
+double probe_fp64_gflops(cudaStream_t st) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1.0;
+  double *out = nullptr;
+  if (cudaMalloc(&out, sizeof(double)) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  k_fp64_probe<<<blocks, threads, 0, st>>>(out, 64, 0.999999, 1e-7);  // warm-up
+  cudaEventRecord(e0, st);
+  k_fp64_probe<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-7);
+  cudaEventRecord(e1, st);
+  count_launch(2);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess || ms <= 0.f) return -1.0;
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+  return flops / (ms * 1e-3) / 1e9;
+}
+
+}  // namespace mgk

@@ -1,0 +1,289 @@
+"""GPU (CUDA, sm_103a) parity of the C-ABI library against the FP64 CPU oracle.
+
+Every call goes through libmg.so (include/mg.h) via the ctypes binding.  FP64
+tolerances: residual rows and Jacobian products agree to 1e-12 of the row
+scale (rounding order only); linear and Newton solves to 1e-10 relative
+max-norm per field (both sides solved to 1e-12 or tighter).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import discretization as disc
+from oracle import multigrid as omg
+from oracle import solver as osv
+from oracle.grid import Grid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0811_4446_gb300 import build, mg as mgmod
+    build.build()
+    return mgmod
+
+
+def _oracle(d):
+    g = Grid(d.nr, d.nz, d.R, d.z)
+    phys = disc.Physics(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p,
+                        D_p=d.D_p, table=d.table, pressure_factor=d.pressure_factor)
+    return g, phys
+
+
+def _random_state(d, rng, scale=1.0):
+    shape = d.shape
+    ne = 1e14 * (0.5 + rng.random(shape)) * scale
+    np_ = 1e14 * (0.5 + rng.random(shape)) * scale
+    V = d.V0 + 3.0 * rng.standard_normal(shape)
+    u = disc.apply_dirichlet(np.stack([ne, np_, V]), disc.Physics(V_cathode=d.V_cathode))
+    return u
+
+
+CASES = [(8, 8, False), (32, 32, False), (32, 32, True), (64, 16, True), (16, 64, False), (128, 128, True)]
+
+
+@pytest.mark.parametrize("nr,nz,table", CASES)
+@pytest.mark.parametrize("dt", [1e-9, 1e-6, 0.0])
+def test_residual_parity(mg, nr, nz, table, dt):
+    d = W.make_discharge(nr, nz=nz, seed=3, V_cathode=-250.0, use_table=table, pressure_factor=1.3)
+    g, phys = _oracle(d)
+    rng = np.random.default_rng(11)
+    u = _random_state(d, rng)
+    uo = _random_state(d, rng)
+    s = mg.from_discharge(d)
+    s.set_state(*[np.ascontiguousarray(a) for a in u])
+    s.set_old_state(*[np.ascontiguousarray(a) for a in uo])
+    Fg, rho_g = s.residual(dt)
+    F, T = disc.residual(g, u, uo, d.S_e, d.S_p, dt if dt > 0 else None, phys, with_terms=True)
+    for f in range(3):
+        scale = np.abs(T[f]).max()
+        assert np.abs(Fg[f] - F[f]).max() <= 1e-12 * scale, (f, np.abs(Fg[f] - F[f]).max(), scale)
+    assert np.allclose(rho_g, disc.rho(F, T), rtol=1e-9, atol=1e-300)
+
+
+@pytest.mark.parametrize("nr,nz,table", CASES[:5])
+def test_jacobian_apply_parity(mg, nr, nz, table):
+    d = W.make_discharge(nr, nz=nz, seed=5, V_cathode=-300.0, use_table=table)
+    g, phys = _oracle(d)
+    rng = np.random.default_rng(2)
+    u = _random_state(d, rng)
+    s = mg.from_discharge(d)
+    s.set_state(*[np.ascontiguousarray(a) for a in u])
+    for dt in (1e-9, 0.0):
+        v = np.zeros((3,) + d.shape)
+        v[:, 1:-1] = rng.standard_normal((3, d.nz - 1, d.nr + 1))
+        v[0:2] *= 1e12
+        Jg = s.jacobian_apply(dt, list(v))
+        J = disc.jacobian(g, u, dt if dt > 0 else None, phys)
+        Jv = disc.from_vec(g, J @ disc.to_vec(g, v))
+        absJ = abs(J)
+        scale = disc.from_vec(g, absJ @ np.abs(disc.to_vec(g, v)))
+        for f in range(3):
+            assert np.abs(Jg[f] - Jv[f]).max() <= 1e-12 * scale[f].max(), f
+
+
+@pytest.mark.parametrize("n,table,dt", [(4, False, 1e-9), (16, False, 1e-9), (32, True, 1e-7), (64, True, 1e-6)])
+def test_linear_solve_parity(mg, n, table, dt):
+    d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=table)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d)
+    s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, dt, phys, with_terms=True)
+    f = -F
+    xg, hg, rc = s.linear_solve(dt, list(f), 1e-12, 200)
+    assert rc == mg.MG_OK
+    H = omg.Hierarchy(g, u, dt, phys)
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    x, ho = H.solve(disc.to_vec(g, f), 1e-12, 200, scale=tn)
+    xo = disc.from_vec(g, x)
+    for q in range(3):
+        assert np.abs(xg[q] - xo[q]).max() <= 1e-10 * np.abs(xo[q]).max(), q
+    # same algorithm: the same cycle count and the same residual history
+    assert abs(len(hg) - len(ho)) <= 1
+    k = min(len(hg), len(ho), 6)
+    assert np.allclose(hg[:k], ho[:k], rtol=1e-5, atol=1e-14)
+
+
+def test_transient_33_ten_steps_parity(mg):
+    d = W.transient_33()
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-12, max_vcycles=100)
+    opt = osv.SolverOptions(eta=1e-12)
+    for k in range(10):
+        rc, st = s.step(1e-9, 1e-10)
+        assert rc == mg.MG_OK
+        u, so = osv.step(g, u, d.S_e, d.S_p, 1e-9, phys, 1e-10, opt)
+        assert so.accepted and st["last_newton"] == so.newton
+    ug = s.get_state()
+    for q in range(3):
+        assert np.abs(ug[q] - u[q]).max() <= 1e-10 * np.abs(u[q]).max(), q
+
+
+def test_steady_march_parity_small(mg):
+    d = W.make_discharge(16, seed=1, V_cathode=-300.0, use_table=True)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-10, max_vcycles=200)
+    rc, st = s.march(1e-9, 1e-10)
+    assert rc == mg.MG_OK
+    uo, ok, rec = osv.march(g, u, d.S_e, d.S_p, phys, 1e-10, osv.SolverOptions(eta=1e-10, max_vcycles=200), 1e-9)
+    assert ok
+    assert st["steps_accepted"] == sum(1 for r in rec if r[1])
+    ug = s.get_state()
+    for q in range(3):
+        assert np.abs(ug[q] - uo[q]).max() <= 1e-8 * np.abs(uo[q]).max(), q
+
+
+def test_solve_steady_continuation_parity_33(mg):
+    d = W.make_discharge(32, seed=0, V_cathode=-300.0, use_table=True)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-10, max_vcycles=200)
+    rc, st = s.solve_steady(1e-9)
+    assert rc == mg.MG_OK
+    uo, ok, rc_, rf_ = osv.solve_steady(g, u, d.S_e, d.S_p, phys, 1e-9, osv.SolverOptions(eta=1e-10, max_vcycles=200))
+    assert ok
+    ug = s.get_state()
+    for q in range(3):
+        assert np.abs(ug[q] - uo[q]).max() <= 1e-7 * np.abs(uo[q]).max(), q
+
+
+def test_steady_257_full_size_residual_property(mg):
+    """257 x 257, table transport, continuation to rho <= 1e-8: the oracle's residual of the result."""
+    d = W.steady_257()
+    g, phys = _oracle(d)
+    s = mg.from_discharge(d)
+    rc, st = s.solve_steady(1e-8)
+    assert rc == mg.MG_OK, st
+    ug = np.stack(s.get_state())
+    F, T = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
+    assert disc.rho(F, T).max() <= 1.05e-8
+    assert np.all(np.isfinite(ug))
+
+
+def test_device_and_host_io_agree(mg):
+    d = W.make_discharge(32, seed=2)
+    s = mg.from_discharge(d)
+    rng = np.random.default_rng(0)
+    u = _random_state(d, rng)
+    t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in u]
+    s.set_state(*t)
+    out = [torch.empty_like(a) for a in t]
+    s.get_state(out)
+    host = s.get_state()
+    for q in range(3):
+        assert np.array_equal(out[q].cpu().numpy(), host[q])
+        assert np.array_equal(host[q], u[q])
+
+
+@pytest.mark.parametrize("nr,nz", [(2, 2), (4, 4), (2, 8), (8, 2)])
+def test_smallest_grids_single_level(mg, nr, nz):
+    d = W.make_discharge(nr, nz=nz, seed=4)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-13)
+    rc, st = s.step(1e-9, 1e-11)
+    assert rc == mg.MG_OK
+    uo, so = osv.step(g, u, d.S_e, d.S_p, 1e-9, phys, 1e-11, osv.SolverOptions(eta=1e-13))
+    ug = s.get_state()
+    for q in range(3):
+        assert np.abs(ug[q] - uo[q]).max() <= 1e-10 * max(np.abs(uo[q]).max(), 1e-300), q
+
+
+def test_invalid_arguments_are_rejected(mg):
+    z = W.z_nodes(32, 1e-2)
+    with pytest.raises(mg.MGError):
+        mg.Solver(30, 32, 1e-2, W.z_nodes(32, 1e-2))          # not a power of two
+    bad = z.copy()
+    bad[5] = bad[4]
+    with pytest.raises(mg.MGError):
+        mg.Solver(32, 32, 1e-2, bad)                          # non-increasing z
+    with pytest.raises(mg.MGError):
+        mg.Solver(32, 32, 1e-2, z, mg.default_params(coarsest=1))
+    s = mg.Solver(32, 32, 1e-2, z)
+    rc = s.lib.mg_step(s.h, -1.0, 1e-8, None)
+    assert rc == mg.MG_EINVAL
+
+
+def test_rejected_step_leaves_state_unchanged(mg):
+    d = W.make_discharge(16, seed=0, V_cathode=-300.0)
+    s = mg.from_discharge(d, corr_limit_frac=1e-12)
+    before = s.get_state()
+    rc, st = s.step(1e-9, 1e-12)
+    assert rc == mg.MG_ENOCONV and st["steps_rejected"] == 1
+    after = s.get_state()
+    for q in range(3):
+        assert np.array_equal(before[q], after[q])
+
+
+def test_nonfinite_source_is_reported(mg):
+    d = W.make_discharge(16, seed=0)
+    s = mg.from_discharge(d)
+    S = d.S_e.copy()
+    S[5, 5] = np.nan
+    s.set_sources(S, d.S_p.copy())
+    before = s.get_state()
+    rc, st = s.step(1e-9, 1e-10)
+    assert rc == mg.MG_ENONFINITE
+    after = s.get_state()
+    for q in range(3):
+        assert np.array_equal(before[q], after[q])
+
+
+# ---------------------------------------------------------------- mixed precision (FP32 inner cycle)
+@pytest.mark.parametrize("n,table,dt", [(16, False, 1e-9), (64, True, 1e-6), (128, False, 1e-9)])
+def test_mixed_linear_solve_matches_oracle(mg, n, table, dt):
+    d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=table)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, precision=mg.MG_MIXED)
+    s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, dt, phys, with_terms=True)
+    xg, hg, rc = s.linear_solve(dt, list(-F), 1e-11, 200)
+    assert rc == mg.MG_OK, hg
+    H = omg.Hierarchy(g, u, dt, phys)
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    x, ho = H.solve(disc.to_vec(g, -F), 1e-12, 200, scale=tn)
+    xo = disc.from_vec(g, x)
+    for q in range(3):
+        assert np.abs(xg[q] - xo[q]).max() <= 1e-8 * np.abs(xo[q]).max(), q
+    # an FP32 cycle contracts about as well as an FP64 one until FP32 rounding is reached
+    assert len(hg) <= len(ho) + 3
+
+
+def test_mixed_transient_33_matches_oracle(mg):
+    d = W.transient_33()
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-11, max_vcycles=100, precision=mg.MG_MIXED)
+    opt = osv.SolverOptions(eta=1e-12)
+    for k in range(10):
+        rc, st = s.step(1e-9, 1e-10)
+        assert rc == mg.MG_OK
+        assert max(st["rho"]) <= 1e-10
+        u, so = osv.step(g, u, d.S_e, d.S_p, 1e-9, phys, 1e-10, opt)
+    ug = s.get_state()
+    for q in range(3):
+        assert np.abs(ug[q] - u[q]).max() <= 1e-8 * np.abs(u[q]).max(), q
+
+
+def test_mixed_steady_257_matches_fp64(mg):
+    d = W.steady_257()
+    g, phys = _oracle(d)
+    s64 = mg.from_discharge(d)
+    s32 = mg.from_discharge(d, precision=mg.MG_MIXED)
+    assert s64.solve_steady(1e-8)[0] == mg.MG_OK
+    rc, st = s32.solve_steady(1e-8)
+    assert rc == mg.MG_OK, st
+    a, b = np.stack(s64.get_state()), np.stack(s32.get_state())
+    F, T = disc.residual(g, b, None, d.S_e, d.S_p, None, phys, with_terms=True)
+    assert disc.rho(F, T).max() <= 1.05e-8
+    # both are the same discrete steady state to the solve tolerance
+    for q in range(3):
+        assert np.abs(a[q] - b[q]).max() <= 1e-6 * np.abs(a[q]).max(), q
