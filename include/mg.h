@@ -202,6 +202,29 @@ int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms);
  * FP64 path.  Returns a negative value on a CUDA error. */
 double mg_probe_fp64_gflops(void *stream);
 
+/* Allocation-free residual norms.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory (code running inside another framework's memory
+ * pool, real-time loops where cudaMalloc is forbidden or would synchronise the device, plug-ins
+ * that may only use the buffers their host hands them).  It evaluates the same residual rows
+ * and scale-free norms rho[3] as mg_residual, with the same kernel, without creating a state:
+ * every array argument is caller-owned DEVICE memory of (nz + 1) x (nr + 1) doubles (dense
+ * rows, i fastest) and rho is host memory.  ne_old, np_old, V_old are read only when dt > 0
+ * (dt <= 0: steady residual).  F_ne, F_np, F_V receive the rows when non-NULL (all three or
+ * none).  The electrode rows of the inputs must hold the Dirichlet values.
+ * Limits: nr, nz powers of two with 2 <= nr, nz <= 1024; at most 64 table rows; larger
+ * inputs return MG_EINVAL.  It calls no cudaMalloc, cudaFree or allocating library routine:
+ * its scratch (about 232 KB: geometry, table, block partial sums, a reduction counter and the
+ * results) is one file-scope device array that every GPU loading the library holds until
+ * the process exits.  All calls share that array and it keeps the last call's contents, so
+ * calls that overlap on the GPU race; serialise them (one stream, or synchronise between
+ * calls).  The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  The call
+ * synchronises `stream` (a cudaStream_t, NULL = legacy default stream) before returning. */
+int mg_residual_noalloc(const mg_grid *g, const mg_params *p, const double *ne, const double *np, const double *V,
+                        const double *ne_old, const double *np_old, const double *V_old, const double *S_e,
+                        const double *S_p, double dt, double *F_ne, double *F_np, double *F_V, double rho[3],
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

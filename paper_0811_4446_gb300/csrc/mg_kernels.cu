@@ -909,3 +909,127 @@ double probe_fp64_gflops(cudaStream_t st) {
 }
 
 }  // namespace mgk
+
+// ==========================================================================================
+// Allocation-free residual entry point (declared in include/mg.h as mg_residual_noalloc).
+//
+// Some callers cannot allocate device memory: code that runs inside another framework's
+// memory pool or a real-time loop where cudaMalloc is forbidden or would synchronise the
+// device, and plug-ins that may only use the buffers their host hands them.  For them this
+// entry point evaluates the same residual rows and norms as mg_residual with the same kernel
+// (k_residual) on caller-owned input and output arrays, and keeps its own scratch (geometry,
+// transport table, block partial sums, reduction counter and results) in the file-scope
+// device array below.  Every GPU that loads this library holds that array until the process
+// exits.  All calls share it and it keeps the last call's contents: calls that overlap on the
+// GPU (different streams, threads or devices' streams racing on one device) race on it.
+#include <mutex>
+
+#include "../../include/mg.h"
+
+namespace {
+
+constexpr int kNoallocMaxN = 1024;                       // largest N_r, N_z accepted
+constexpr int kNoallocGeo = kNoallocMaxN + 2;            // length of each geometry vector
+constexpr int kNoallocTableRows = 64;
+constexpr int kNoallocBlocks = ((kNoallocMaxN + 1 + 31) / 32) * ((kNoallocMaxN - 1 + 7) / 8);
+// layout (doubles): results [0, 8) | counter [8, 16) | dz | dzc | volr | table | partials
+constexpr size_t kOffOut = 0, kOffCounter = 8, kOffDz = 16;
+constexpr size_t kOffDzc = kOffDz + kNoallocGeo, kOffVolr = kOffDzc + kNoallocGeo;
+constexpr size_t kOffTable = kOffVolr + kNoallocGeo;
+constexpr size_t kOffPartials = kOffTable + 5 * kNoallocTableRows;
+constexpr size_t kNoallocDoubles = kOffPartials + 6 * (size_t)kNoallocBlocks;  // ~232 KB
+
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[128];  // device address of g_noalloc_scratch, per device ordinal
+
+// Device address of the scratch array on the current device, looked up once per device
+// (with that device current).  In host code the array's name is only a host-side stand-in.
+cudaError_t noalloc_scratch(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int mg_residual_noalloc(const mg_grid *g, const mg_params *p, const double *ne, const double *np,
+                                   const double *V, const double *ne_old, const double *np_old, const double *V_old,
+                                   const double *S_e, const double *S_p, double dt, double *F_ne, double *F_np,
+                                   double *F_V, double rho[3], void *stream) {
+  using namespace mgk;
+  if (!g || !p || !g->z || !ne || !np || !V || !S_e || !S_p || !rho) return MG_EINVAL;
+  const int nr = g->nr, nz = g->nz;
+  auto pow2 = [](int x) { return x >= 2 && (x & (x - 1)) == 0; };
+  if (!pow2(nr) || !pow2(nz) || nr > kNoallocMaxN || nz > kNoallocMaxN || !(g->R > 0.0)) return MG_EINVAL;
+  if (dt > 0.0 && (!ne_old || !np_old || !V_old)) return MG_EINVAL;
+  if ((F_ne || F_np || F_V) && !(F_ne && F_np && F_V)) return MG_EINVAL;
+  if (!(p->pressure_factor > 0.0) || !(p->D_e > 0.0) || !(p->D_p > 0.0)) return MG_EINVAL;
+  if (p->table && (p->table_rows < 2 || p->table_rows > kNoallocTableRows)) return MG_EINVAL;
+  for (int j = 0; j < nz; ++j)
+    if (!(g->z[j + 1] > g->z[j])) return MG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return MG_ECUDA;
+
+  // geometry of the finite-volume rows (same formulas as the state-based path), built on the
+  // host in fixed-size buffers and copied into the scratch array
+  double geo[3][kNoallocGeo];
+  const double dr = g->R / nr;
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < kNoallocGeo; ++k) geo[q][k] = 0.0;
+  for (int j = 0; j < nz; ++j) geo[0][j] = g->z[j + 1] - g->z[j];
+  for (int j = 1; j < nz; ++j) geo[1][j] = 0.5 * (geo[0][j - 1] + geo[0][j]);
+  for (int i = 0; i <= nr; ++i) geo[2][i] = i * dr * dr;
+  geo[2][0] = dr * dr / 8.0;
+  geo[2][nr] = (nr - 0.25) * dr * dr / 2.0;
+  if (cudaMemcpyAsync(base + kOffDz, geo, sizeof(geo), cudaMemcpyHostToDevice, st) != cudaSuccess) return MG_ECUDA;
+  if (p->table && cudaMemcpyAsync(base + kOffTable, p->table, sizeof(double) * 5 * p->table_rows,
+                                  cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return MG_ECUDA;
+  // the reduction counter must start at zero (an earlier call that failed may have left it set)
+  if (cudaMemsetAsync(base + kOffCounter, 0, sizeof(double), st) != cudaSuccess) return MG_ECUDA;
+
+  Level L = Level();
+  L.nr = nr; L.nz = nz; L.P = nr + 1;  // caller arrays are dense rows of nr + 1 nodes
+  L.dr = dr;
+  L.dz = base + kOffDz; L.dzc = base + kOffDzc; L.volr = base + kOffVolr;
+  StateView sv;
+  sv.u[NE] = const_cast<double *>(ne); sv.u[NP] = const_cast<double *>(np); sv.u[NV] = const_cast<double *>(V);
+  sv.uold[NE] = const_cast<double *>(ne_old); sv.uold[NP] = const_cast<double *>(np_old);
+  sv.uold[NV] = const_cast<double *>(V_old);
+  sv.S[0] = S_e; sv.S[1] = S_p;
+  Transport tr;
+  tr.mu_e = p->mu_e / p->pressure_factor; tr.D_e = p->D_e / p->pressure_factor;
+  tr.mu_p = p->mu_p / p->pressure_factor; tr.D_p = p->D_p / p->pressure_factor;
+  tr.inv_pf = 1.0 / p->pressure_factor;
+  tr.table = p->table ? base + kOffTable : nullptr;
+  tr.rows = p->table ? p->table_rows : 0;
+  double *Fo[3] = {F_ne, F_np, F_V};
+  if (launch_residual(L, sv, tr, dt, false, F_ne ? Fo : nullptr, base + kOffPartials,
+                      reinterpret_cast<unsigned *>(base + kOffCounter), base + kOffOut, st) != cudaSuccess)
+    return MG_ECUDA;
+  double out6[6];
+  if (cudaMemcpyAsync(out6, base + kOffOut, sizeof(out6), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MG_ECUDA;
+  for (int q = 0; q < 3; ++q) {
+    const double fn = sqrt(out6[q]), t = sqrt(out6[3 + q]);
+    rho[q] = fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
+  }
+  return MG_OK;
+}

@@ -80,6 +80,8 @@ SIGNATURES = {
     "mg_profile_begin": (_i, [_vp, _i, _i]),
     "mg_profile_end": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "mg_probe_fp64_gflops": (ctypes.c_double, [_vp]),
+    "mg_residual_noalloc": (_i, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_params), _vp, _vp, _vp, _vp, _vp, _vp,
+                                 _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp]),
 }
 MG_PROF_SMOOTH, MG_PROF_LINRES, MG_PROF_COEF, MG_PROF_RESIDUAL, MG_PROF_RESTRICT, MG_PROF_PROLONG = 1, 2, 3, 4, 5, 6
 
@@ -283,6 +285,36 @@ class Solver:
         ms = ctypes.c_double(0.0)
         self._check(self.lib.mg_profile_end(self.h, ctypes.byref(n), ctypes.byref(ms)))
         return int(n.value), float(ms.value)
+
+
+def residual_noalloc(nr: int, nz: int, R: float, z, params: mg_params, state, old_state, sources, dt: float,
+                     F_out=None, table=None, stream=None):
+    """rho[3] (and optionally the residual rows into F_out) through mg_residual_noalloc.
+
+    state, old_state (or None when dt <= 0), sources and F_out are CUDA float64 tensors of
+    shape (nz + 1, nr + 1); nothing is allocated on the device by the call.
+    """
+    torch = _torch()
+    lib = load()
+    zh = np.ascontiguousarray(z, dtype=np.float64)
+    grid = mg_grid(int(nr), int(nz), float(R), zh.ctypes.data_as(_dp))
+    keep = None
+    if table is not None:
+        keep = np.ascontiguousarray(table, dtype=np.float64)
+        params.table = keep.ctypes.data_as(_dp)
+        params.table_rows = keep.shape[0]
+    ptr = lambda a: None if a is None else _ptr(a)[0]
+    old = old_state if old_state is not None else (None, None, None)
+    F = F_out if F_out is not None else (None, None, None)
+    rho = (ctypes.c_double * 3)()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.mg_residual_noalloc(ctypes.byref(grid), ctypes.byref(params), *(ptr(a) for a in state),
+                                 *(ptr(a) for a in old), *(ptr(a) for a in sources), float(dt),
+                                 *(ptr(a) for a in F), rho, ctypes.c_void_p(st.cuda_stream))
+    del keep
+    if rc != MG_OK:
+        raise MGError(rc, "mg_residual_noalloc failed")
+    return np.array(rho[:])
 
 
 def kernel_launches() -> int:
