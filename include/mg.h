@@ -89,6 +89,8 @@ typedef struct mg_params {
   double corr_limit_frac; /* reject a step if max|dV| > frac * |V_cathode|     */
   double dt1, dt_growth, dt_max; /* Delta-t ramp of Sec. 2                     */
   double n0;              /* density unit of the FP32 inner cycle (eq. 12's n0), m^-3 */
+  int32_t use_graphs;     /* 1: each linear solve is one CUDA-graph launch whose V-cycle loop
+                             and stopping test run on the device; 0: host-driven loop */
 } mg_params;
 
 /* Per-call statistics. */
@@ -111,7 +113,8 @@ typedef struct mg_state mg_state;
 /* Fill *p with the defaults: mu_e = 30, D_e = 60, mu_p = 0.15, D_p = 0.0038,
  * V_cathode = -200, V_anode = 0, nu1 = nu2 = 2, coarsest = 4, eta = 1e-3,
  * max_newton = 10, max_vcycles = 60, max_steps = 400, dt1 = 1e-9,
- * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14.
+ * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14,
+ * use_graphs = 1.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on

@@ -3,6 +3,7 @@
 // (Ristivojevic & Petrovic, arXiv:0811.4446, Sec. 2).  All arithmetic on the solution runs in
 // the kernels of mg_kernels.cu; the host only sequences launches and reads back norms.
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -64,6 +65,11 @@ struct mg_state {
   // kernel timing (mg_profile_begin / mg_profile_end)
   int prof_kernel = 0, prof_level = -1, prof_n = 0;
   std::vector<cudaEvent_t> prof_ev;
+  // device-side linear solves: one instantiated graph per root level
+  cudaStream_t cap_stream = nullptr;
+  SolveCtl *ctl = nullptr, *hctl = nullptr;
+  cudaGraphExec_t vexec[kMaxLevels] = {};
+  int vprefix[kMaxLevels] = {}, vbody[kMaxLevels] = {};
 };
 
 namespace {
@@ -108,12 +114,12 @@ struct Carver {
   }
 };
 
-constexpr int kFieldsPerLevel = 29;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3
+constexpr int kFieldsPerLevel = 42;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3
 constexpr int kGeoPerLevel = 4;      // dz, dzc, volr, wz (each up to max(nr, nz) + 1)
 
 size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz + 1 + 7) / 8); }
 
-constexpr int kFields32PerLevel = 21;  // cr 6, cz 6, du 3, f 3, r 3
+constexpr int kFields32PerLevel = 34;  // cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3
 
 void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int table_rows, bool mixed) {
   for (int l = 0; l < nlev; ++l) {
@@ -133,6 +139,9 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
     for (int a = 0; a < 3; ++a) b.L.du[a] = f[q++];
     for (int a = 0; a < 3; ++a) b.L.f[a] = f[q++];
     for (int a = 0; a < 3; ++a) b.L.r[a] = f[q++];
+    b.L.gR = f[q++]; b.L.gZ = f[q++]; b.L.Ak = f[q++];
+    for (int a = 0; a < NFAC; ++a) b.L.fac[a] = f[q++];
+    for (int a = 0; a < NDIA; ++a) b.L.dia[a] = f[q++];
     b.L.nr = b.nr; b.L.nz = b.nz; b.L.P = b.P;
     if (b.geo) {
       b.L.dz = b.geo;
@@ -152,6 +161,9 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
       for (int a = 0; a < 3; ++a) b.M.du[a] = g[w++];
       for (int a = 0; a < 3; ++a) b.M.f[a] = g[w++];
       for (int a = 0; a < 3; ++a) b.M.r[a] = g[w++];
+      b.M.gR = g[w++]; b.M.gZ = g[w++]; b.M.Ak = g[w++];
+      for (int a = 0; a < NFAC; ++a) b.M.fac[a] = g[w++];
+      for (int a = 0; a < NDIA; ++a) b.M.dia[a] = g[w++];
       b.M.nr = b.nr; b.M.nz = b.nz; b.M.P = b.P;
       if (b.geo32) {
         b.M.dz = b.geo32;
@@ -170,6 +182,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
   s->rs = c.take<double>(kMaxCoarse);
   s->cs = c.take<double>(kMaxCoarse);
   s->flag = c.take<int>(4);
+  s->ctl = c.take<SolveCtl>(1);
   s->table_d = table_rows > 0 ? c.take<double>((size_t)table_rows * 5) : nullptr;
 }
 
@@ -258,6 +271,7 @@ int build_hierarchy(mg_state *s, int l0, double dt) {
     ProfScope ps(s, MG_PROF_COEF, l);
     CK(launch_coef(b.L, b.sv, s->tr, s->stream));
     if (mixed(s)) CK(launch_coef_to32(b.L, b.M, s->prm.n0, s->stream));
+    CK(launch_factor(b.L, mixed(s) ? &b.M : nullptr, dt, s->prm.n0, s->stream));
   }
   LevelBuf &c = s->lv[s->nlev - 1];
   CK(launch_coarse_factor(c.L, dt, s->M, s->Minv, s->rs, s->cs, s->flag, s->stream));
@@ -267,109 +281,218 @@ int build_hierarchy(mg_state *s, int l0, double dt) {
 template <typename T> const LevelT<T> &view(const LevelBuf &b);
 template <> const LevelT<double> &view<double>(const LevelBuf &b) { return b.L; }
 template <> const LevelT<float> &view<float>(const LevelBuf &b) { return b.M; }
-// e/eps0 in the unknowns of the view: the FP32 inner cycle counts densities in units of n0
-template <typename T> double kap_of(const mg_state *s);
-template <> double kap_of<double>(const mg_state *) { return kKappa; }
-template <> double kap_of<float>(const mg_state *s) { return kKappa * s->prm.n0; }
 template <typename T> double nscale_of(const mg_state *s);
 template <> double nscale_of<double>(const mg_state *) { return 1.0; }
 template <> double nscale_of<float>(const mg_state *s) { return s->prm.n0; }
 
 template <typename T>
-int smooth(mg_state *s, int l, double dt, int color) {
+int smooth(mg_state *s, int l, int color, cudaStream_t st) {
   ProfScope ps(s, MG_PROF_SMOOTH, l);
-  CK(launch_smooth<T>(view<T>(s->lv[l]), dt, kap_of<T>(s), color, s->stream));
+  CK(launch_smooth<T>(view<T>(s->lv[l]), color, st));
   return MG_OK;
 }
 
 template <typename T>
-int vcycle(mg_state *s, int l, double dt) {
+int vcycle(mg_state *s, int l, cudaStream_t st) {
   const LevelT<T> &b = view<T>(s->lv[l]);
   if (l == s->nlev - 1) {
-    CK(launch_coarse_solve<T>(b, s->Minv, s->rs, s->cs, nscale_of<T>(s), s->stream));
+    CK(launch_coarse_solve<T>(b, s->Minv, s->rs, s->cs, nscale_of<T>(s), st));
     return MG_OK;
   }
   const LevelT<T> &c = view<T>(s->lv[l + 1]);
   int rc;
   for (int k = 0; k < s->prm.nu1; ++k)
     for (int col = 0; col < 2; ++col)
-      if ((rc = smooth<T>(s, l, dt, col))) return rc;
+      if ((rc = smooth<T>(s, l, col, st))) return rc;
   {
     ProfScope ps(s, MG_PROF_LINRES, l);
-    CK(launch_linres<T>(b, dt, kap_of<T>(s), b.du, b.f, const_cast<T **>(b.r), nullptr, nullptr, nullptr,
-                        s->stream));
+    CK(launch_linres<T>(b, b.du, b.f, const_cast<T **>(b.r), nullptr, nullptr, nullptr, st));
   }
   {
     ProfScope ps(s, MG_PROF_RESTRICT, l);
-    CK(launch_restrict<T>(b, c, s->stream));
+    CK(launch_restrict<T>(b, c, st));
   }
-  if ((rc = vcycle<T>(s, l + 1, dt))) return rc;
+  if ((rc = vcycle<T>(s, l + 1, st))) return rc;
   {
     ProfScope ps(s, MG_PROF_PROLONG, l);
-    CK(launch_prolong_add<T>(c, b, s->stream));
+    CK(launch_prolong_add<T>(c, b, st));
   }
   for (int k = 0; k < s->prm.nu2; ++k)
     for (int col = 0; col < 2; ++col)
-      if ((rc = smooth<T>(s, l, dt, col))) return rc;
+      if ((rc = smooth<T>(s, l, col, st))) return rc;
   return MG_OK;
 }
 
-// Weighted linear-residual norm max_f ||f - J du||_f / w_f on level l0.
-int lin_norm(mg_state *s, int l0, double dt, const double w[3], double *out) {
+// Per-field sums of squares of the linear residual f - J du on level l0 into dout[0..2]; in the
+// mixed form this is the FP64 outer defect, also written as the next FP32 right-hand side.
+int launch_norm(mg_state *s, int l0, cudaStream_t st) {
   LevelBuf &b = s->lv[l0];
   if (mixed(s)) {
-    CK(launch_outer_residual(b.L, b.M, dt, s->prm.n0, s->partials, s->counter, s->dout, s->stream));
+    CK(launch_outer_residual(b.L, b.M, s->prm.n0, s->partials, s->counter, s->dout, st));
   } else {
-    CK(launch_linres<double>(b.L, dt, kKappa, b.L.du, b.L.f, b.L.r, s->partials, s->counter, s->dout, s->stream));
+    CK(launch_linres<double>(b.L, b.L.du, b.L.f, b.L.r, s->partials, s->counter, s->dout, st));
   }
-  int rc = sync_read(s, 3);
-  if (rc) return rc;
+  return MG_OK;
+}
+
+// One iteration of the linear-solve loop: a V-cycle (in the mixed form: an FP32 cycle on the
+// FP64 defect followed by x += e in FP64) and the residual norms.
+int cycle_and_norm(mg_state *s, int l0, cudaStream_t st) {
+  int rc;
+  if (mixed(s)) {
+    CK(launch_zero_du<float>(s->lv[l0].M, st));
+    if ((rc = vcycle<float>(s, l0, st))) return rc;
+    CK(launch_mixed_update(s->lv[l0].L, s->lv[l0].M, s->prm.n0, st));
+  } else {
+    if ((rc = vcycle<double>(s, l0, st))) return rc;
+  }
+  return launch_norm(s, l0, st);
+}
+
+double weighted(const mg_state *s, const double w[3]) {
   double m = 0.0;
   for (int q = 0; q < 3; ++q) {
     const double v = std::sqrt(s->hout[q]) / w[q];
-    if (!(v == v)) { m = NAN; break; }
+    if (!(v == v)) return NAN;
     m = std::max(m, v);
   }
-  *out = m;
-  return MG_OK;
+  return m;
 }
 
-// V-cycles on level l0 from du = 0 until the weighted residual drops by eta.
-int linear_solve(mg_state *s, int l0, double dt, double eta, int max_cycles, const double tn[3], double *hist,
-                 int *ncyc, bool *ok) {
-  double w[3];
-  for (int q = 0; q < 3; ++q) w[q] = tn[q] > 0.0 ? tn[q] : 1.0;
+// Host-driven loop (used while kernels are being timed, and when graphs are switched off).
+int linear_solve_eager(mg_state *s, int l0, double eta, int max_cycles, const double w[3], double *hist, int *ncyc,
+                       bool *ok) {
   CK(launch_zero_du<double>(s->lv[l0].L, s->stream));
-  double r0;
-  int rc = lin_norm(s, l0, dt, w, &r0);
-  if (rc) return rc;
+  int rc = launch_norm(s, l0, s->stream);
+  if (rc || (rc = sync_read(s, 3))) return rc;
+  const double r0 = weighted(s, w);
   *ncyc = 0;
   *ok = true;
   if (hist) hist[0] = r0 > 0.0 ? 1.0 : 0.0;
   if (r0 == 0.0) return MG_OK;
   double rel = 1.0;
   while (rel > eta && *ncyc < max_cycles) {
-    if (mixed(s)) {
-      // FP32 correction of the FP64 defect, then x += e in FP64
-      CK(launch_zero_du<float>(s->lv[l0].M, s->stream));
-      rc = vcycle<float>(s, l0, dt);
-      if (rc) return rc;
-      CK(launch_mixed_update(s->lv[l0].L, s->lv[l0].M, s->prm.n0, s->stream));
-    } else {
-      rc = vcycle<double>(s, l0, dt);
-      if (rc) return rc;
-    }
-    double r;
-    rc = lin_norm(s, l0, dt, w, &r);
-    if (rc) return rc;
+    if ((rc = cycle_and_norm(s, l0, s->stream)) || (rc = sync_read(s, 3))) return rc;
     ++*ncyc;
-    rel = r / r0;
+    rel = weighted(s, w) / r0;
     if (hist) hist[*ncyc] = rel;
     if (!(rel == rel) || std::isinf(rel)) { *ok = false; return MG_OK; }
   }
-  s->stats.vcycles += *ncyc;
   *ok = rel <= eta;
   return MG_OK;
+}
+
+// Record the device-side solve for root level l0 as a CUDA graph:
+//   zero du -> norms -> init -> WHILE(cond) { V-cycle -> norms -> check }
+// captured on a private stream and replayed on the state's stream.
+int build_solve_graph(mg_state *s, int l0) {
+  cudaStream_t cs = s->cap_stream;
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h;
+  int rc = MG_OK;
+  const char *where = "";
+  cudaGraphNodeParams cp = {};
+  cudaGraph_t body = nullptr;
+  cudaStreamCaptureStatus status;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edges = nullptr;
+  size_t nd = 0;
+  cudaGraphNode_t cnode;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 0, 0);
+  if (e != cudaSuccess) { rc = MG_ECUDA; where = "conditional handle"; goto done; }
+  set_capturing(true);
+  e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { rc = MG_ECUDA; where = "begin capture"; goto done; }
+  if (launch_zero_du<double>(s->lv[l0].L, cs) != cudaSuccess || launch_norm(s, l0, cs) != MG_OK ||
+      launch_solve_init(s->ctl, s->dout, h, cs) != cudaSuccess) {
+    rc = MG_ECUDA; where = "prefix launches";
+  }
+  s->vprefix[l0] = captured_launches();
+  if (rc == MG_OK && (e = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, &edges, &nd)) != cudaSuccess) {
+    rc = MG_ECUDA; where = "capture info";
+  }
+  if (rc == MG_OK) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&cnode, graph, deps, edges, nd, &cp)) != cudaSuccess) {
+      rc = MG_ECUDA; where = "conditional node";
+    } else if ((e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+               cudaSuccess) {
+      rc = MG_ECUDA; where = "capture dependencies";
+    }
+  }
+  {
+    cudaGraph_t g2 = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g2);
+    if (rc == MG_OK && e2 != cudaSuccess) { rc = MG_ECUDA; where = "end capture"; e = e2; }
+  }
+  if (rc != MG_OK) goto done;
+  body = cp.conditional.phGraph_out[0];
+  set_capturing(true);
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { rc = MG_ECUDA; where = "begin body capture"; goto done; }
+  if (cycle_and_norm(s, l0, cs) != MG_OK || launch_solve_check(s->ctl, s->dout, h, cs) != cudaSuccess) {
+    rc = MG_ECUDA; where = "body launches";
+  }
+  s->vbody[l0] = captured_launches();
+  {
+    cudaGraph_t g3 = nullptr;
+    const cudaError_t e3 = cudaStreamEndCapture(cs, &g3);
+    if (rc == MG_OK && e3 != cudaSuccess) { rc = MG_ECUDA; where = "end body capture"; e = e3; }
+  }
+  if (rc == MG_OK && (e = cudaGraphInstantiate(&s->vexec[l0], graph, 0)) != cudaSuccess) {
+    rc = MG_ECUDA; where = "instantiate";
+  }
+done:
+  set_capturing(false);
+  cudaGetLastError();
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != MG_OK) {
+    s->vexec[l0] = nullptr;
+    return fail(s, MG_ECUDA, "linear-solve graph: %s: %s", where, cudaGetErrorString(e));
+  }
+  return MG_OK;
+}
+
+int linear_solve_graph(mg_state *s, int l0, double eta, int max_cycles, const double w[3], double *hist, int *ncyc,
+                       bool *ok) {
+  if (!s->vexec[l0]) {
+    int rc = build_solve_graph(s, l0);
+    if (rc) return rc;
+  }
+  SolveCtl *h = s->hctl;
+  for (int q = 0; q < 3; ++q) h->w[q] = w[q];
+  h->eta = eta;
+  h->max_cycles = std::min(max_cycles, kMaxHist - 1);
+  h->ncyc = 0;
+  h->r0 = 0.0;
+  h->rel = 0.0;
+  CK(cudaMemcpyAsync(s->ctl, h, offsetof(SolveCtl, hist), cudaMemcpyHostToDevice, s->stream));
+  CK(cudaGraphLaunch(s->vexec[l0], s->stream));
+  CK(cudaMemcpyAsync(h, s->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  *ncyc = h->ncyc;
+  count_launch(s->vprefix[l0] + h->ncyc * s->vbody[l0]);
+  if (hist)
+    for (int k = 0; k <= h->ncyc; ++k) hist[k] = h->hist[k];
+  *ok = (h->r0 == 0.0) || (h->rel <= eta);
+  return MG_OK;
+}
+
+// V-cycles on level l0 from du = 0 until the weighted residual drops by eta (tn: the per-field
+// norms of the Newton residual's absolute terms, the weights of the test).
+int linear_solve(mg_state *s, int l0, double eta, int max_cycles, const double tn[3], double *hist, int *ncyc,
+                 bool *ok) {
+  double w[3];
+  for (int q = 0; q < 3; ++q) w[q] = tn[q] > 0.0 ? tn[q] : 1.0;
+  const bool graphs = s->prm.use_graphs && s->prof_kernel == 0 && max_cycles < kMaxHist;
+  const int rc = graphs ? linear_solve_graph(s, l0, eta, max_cycles, w, hist, ncyc, ok)
+                        : linear_solve_eager(s, l0, eta, max_cycles, w, hist, ncyc, ok);
+  if (rc == MG_OK) s->stats.vcycles += *ncyc;
+  return rc;
 }
 
 void copy_state_async(mg_state *s, int l0, bool to_old) {
@@ -407,7 +530,7 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out) {
     if (rc) return rc;
     int ncyc;
     bool ok;
-    rc = linear_solve(s, l0, dt, s->prm.eta, s->prm.max_vcycles, tn, nullptr, &ncyc, &ok);
+    rc = linear_solve(s, l0, s->prm.eta, s->prm.max_vcycles, tn, nullptr, &ncyc, &ok);
     if (rc) return rc;
     if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
     CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout, s->stream));
@@ -478,6 +601,7 @@ void mg_params_default(mg_params *p) {
   p->eta = 1e-3; p->newton_tol = 0.0; p->corr_limit_frac = 0.5;
   p->dt1 = 1e-9; p->dt_growth = 5.0; p->dt_max = 1e-6;
   p->n0 = 1e14;
+  p->use_graphs = 1;
 }
 
 static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
@@ -550,7 +674,9 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     s->owns_ws = true;
   }
   s->ws_bytes = need;
-  if (cudaMallocHost(&s->hout, 16 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost(&s->hout, 16 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&s->hctl, sizeof(SolveCtl)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     if (s->owns_ws) cudaFree(s->ws);
     delete s;
     return MG_ECUDA;
@@ -577,6 +703,38 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     if (b.geo32 && cudaMemcpyAsync(b.geo32, geo32.data(), geo32.size() * sizeof(float), cudaMemcpyHostToDevice,
                                    s->stream) != cudaSuccess)
       rc = fail(s, MG_ECUDA, "geometry copy (FP32)");
+    // node arrays of the Poisson face conductances (r-face (i+1/2, j) and z-face (i, j+1/2), stored
+    // at their lower node) and of (e/eps0) x control volume (x n0 for the FP32 copies)
+    {
+      const double *dz = geo.data(), *dzc = dz + glen, *volr = dz + 2 * glen;
+      std::vector<double> nd(3 * b.nodes, 0.0);
+      double *gR = nd.data(), *gZ = gR + b.nodes, *Ak = gZ + b.nodes;
+      for (int j = 0; j <= b.nz; ++j)
+        for (int i = 0; i <= b.nr; ++i) {
+          const size_t k = (size_t)j * b.P + i;
+          if (i < b.nr) gR[k] = (i + 0.5) * dzc[j];
+          if (j < b.nz) gZ[k] = volr[i] / dz[j];
+          Ak[k] = volr[i] * dzc[j] * kKappa;
+        }
+      const double *srcs[3] = {gR, gZ, Ak};
+      const double *dsts[3] = {b.L.gR, b.L.gZ, b.L.Ak};
+      for (int a = 0; a < 3 && rc == MG_OK; ++a)
+        if (cudaMemcpy((void *)dsts[a], srcs[a], b.nodes * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+          rc = fail(s, MG_ECUDA, "conductance copy");
+      if (p->precision == MG_MIXED && rc == MG_OK) {
+        std::vector<float> nf(3 * b.nodes);
+        for (size_t k = 0; k < b.nodes; ++k) {
+          nf[k] = (float)gR[k];
+          nf[b.nodes + k] = (float)gZ[k];
+          nf[2 * b.nodes + k] = (float)(Ak[k] * p->n0);
+        }
+        const float *dst32[3] = {b.M.gR, b.M.gZ, b.M.Ak};
+        for (int a = 0; a < 3 && rc == MG_OK; ++a)
+          if (cudaMemcpy((void *)dst32[a], nf.data() + a * b.nodes, b.nodes * sizeof(float), cudaMemcpyHostToDevice) !=
+              cudaSuccess)
+            rc = fail(s, MG_ECUDA, "conductance copy (FP32)");
+      }
+    }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) rc = fail(s, MG_ECUDA, "geometry sync");
   }
   s->tr.mu_e = p->mu_e / p->pressure_factor; s->tr.D_e = p->D_e / p->pressure_factor;
@@ -615,6 +773,10 @@ void mg_destroy(mg_state *s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   else cudaDeviceSynchronize();
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (s->vexec[l]) cudaGraphExecDestroy(s->vexec[l]);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->hctl) cudaFreeHost(s->hctl);
   if (s->owns_ws && s->ws) cudaFree(s->ws);
   if (s->hout) cudaFreeHost(s->hout);
   delete s;
@@ -694,10 +856,11 @@ int mg_jacobian_apply(mg_state *s, double dt, const double *v_ne, const double *
   if (rc) return rc;
   LevelBuf &b = s->lv[0];
   CK(launch_coef(b.L, b.sv, s->tr, s->stream));
+  CK(launch_factor(b.L, nullptr, dt, s->prm.n0, s->stream));
   const double *src[3] = {v_ne, v_np, v_V};
   for (int q = 0; q < 3; ++q)
     if ((rc = copy_in(s, b, b.L.du[q], src[q], where, 1, b.nz - 1))) return rc;
-  CK(launch_linres<double>(b.L, dt, kKappa, b.L.du, nullptr, b.L.r, nullptr, nullptr, nullptr, s->stream));
+  CK(launch_linres<double>(b.L, b.L.du, nullptr, b.L.r, nullptr, nullptr, nullptr, s->stream));
   double *dst[3] = {o_ne, o_np, o_V};
   for (int q = 0; q < 3; ++q)
     if ((rc = copy_out(s, b, dst[q], b.L.r[q], where))) return rc;
@@ -720,7 +883,7 @@ int mg_linear_solve(mg_state *s, double dt, const double *f_ne, const double *f_
     if ((rc = copy_in(s, b, b.L.f[q], src[q], where, 1, b.nz - 1))) return rc;
   int nc = 0;
   bool ok;
-  if ((rc = linear_solve(s, 0, dt, eta, max_cycles, tn, history, &nc, &ok))) return rc;
+  if ((rc = linear_solve(s, 0, eta, max_cycles, tn, history, &nc, &ok))) return rc;
   if (cycles) *cycles = nc;
   double *dst[3] = {x_ne, x_np, x_V};
   for (int q = 0; q < 3; ++q)

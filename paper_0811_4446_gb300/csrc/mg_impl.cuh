@@ -20,6 +20,11 @@ constexpr double kKappa = kECharge / kEps0;
 enum { NE = 0, NP = 1, NV = 2 };
 // face-coefficient slots: per species s (0 = electrons, 1 = ions): G-term, F-term, V-derivative
 enum { CGE = 0, CFE = 1, CVE = 2, CGP = 3, CFP = 4, CVP = 5, NCOEF = 6 };
+// per-node factors of the 3x3 diagonal block [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]]
+// (ak = A e/eps0): inverse pivots, Schur-complement multipliers q1 = -ak/a11, q2 = ak/a22,
+// inverse Schur complement, and the two couplings to V
+enum { FI11 = 0, FI22 = 1, FQ1 = 2, FQ2 = 3, FIS = 4, FA13 = 5, FA23 = 6, NFAC = 7 };
+enum { DA11 = 0, DA22 = 1, DA33 = 2, NDIA = 3 };
 
 // Transport inputs (mu, D constant or tabulated in |E|), already divided by the pressure factor.
 struct Transport {
@@ -36,7 +41,9 @@ struct LevelT {
   T dr;
   const T *dz, *dzc, *volr;  // nz, nz+1, nr+1 (geometry in the level's arithmetic type)
   const T *wz;               // odd fine row j: weight of the upper coarse node (nz+1 entries)
+  const T *gR, *gZ, *Ak;     // node arrays: r-face and z-face Poisson conductances, (e/eps0) A
   T *cr[NCOEF], *cz[NCOEF];  // face coefficients
+  T *fac[NFAC], *dia[NDIA];  // diagonal-block factors (rebuilt with the coefficients)
   T *du[3], *f[3], *r[3];
 };
 using Level = LevelT<double>;
@@ -46,22 +53,43 @@ struct StateView {           // nonlinear state on one level (FP64)
   const double *S[2];
 };
 
+// Device-resident control block of one linear solve (device-side V-cycle loop in a CUDA graph).
+constexpr int kMaxHist = 512;
+struct SolveCtl {
+  double w[3];      // per-field weights (norms of the Newton residual's absolute terms)
+  double eta;       // relative tolerance of the weighted residual
+  double r0;        // weighted residual at du = 0
+  double rel;       // last relative weighted residual
+  int max_cycles;
+  int ncyc;         // V-cycles run
+  double hist[kMaxHist];
+};
+
 // ---- launch wrappers (mg_kernels.cu) ------------------------------------------------------
-// All take the stream last and return cudaGetLastError() of the launch.
+// All take the stream last and return cudaGetLastError() of the launch.  While a stream capture
+// is being recorded (set_capturing(true)) launches are not counted: graph replays are counted
+// by the host after they ran.
 void count_launch(int n = 1);
+void set_capturing(bool on);
+int captured_launches();  // launches recorded since set_capturing(true)
+cudaError_t launch_solve_init(SolveCtl *ctl, const double *norm3, cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t launch_solve_check(SolveCtl *ctl, const double *norm3, cudaGraphConditionalHandle h, cudaStream_t st);
 
 cudaError_t launch_coef(const Level &L, const StateView &sv, const Transport &tr, cudaStream_t st);
+// Diagonal-block factors of every unknown node from the FP64 face coefficients at step dt; with
+// M non-null also the FP32 copies in n0-scaled unknowns (mixed form).
+cudaError_t launch_factor(const Level &L, const LevelT<float> *M, double dt, double n0, cudaStream_t st);
 // Residual rows F at the state; writes f = -F into L.f (if write_f) and F into Fout (may be null);
 // partial sums of F^2 and T^2 per field reduced to out6[0..5] (F2 e,p,V ; T2 e,p,V).
 cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport &tr, double dt,
                             bool write_f, double *Fout[3], double *partials, unsigned *counter,
                             double *out6, cudaStream_t st);
 template <typename T>
-cudaError_t launch_smooth(const LevelT<T> &L, double dt, double kap, int color, cudaStream_t st);
+cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st);
 // r = f - J v (or out = J v when f == nullptr); optional per-field norms (sum of squares) -> out3
 template <typename T>
-cudaError_t launch_linres(const LevelT<T> &L, double dt, double kap, T *const v[3], T *const f[3], T *out[3],
-                          double *partials, unsigned *counter, double *out3, cudaStream_t st);
+cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,
+                          unsigned *counter, double *out3, cudaStream_t st);
 template <typename T>
 cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st);
 template <typename T>
@@ -84,7 +112,7 @@ cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st);
 // mixed form
 cudaError_t launch_coef_to32(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);
 cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);
-cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double dt, double n0, double *partials,
+cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double n0, double *partials,
                                   unsigned *counter, double *out3, cudaStream_t st);
 cudaError_t launch_dirichlet(const Level &L, const StateView &sv, double Vc, double Va, cudaStream_t st);
 unsigned long long total_launches();

@@ -18,7 +18,14 @@
 namespace mgk {
 
 static unsigned long long g_launches = 0;
-void count_launch(int n) { __atomic_add_fetch(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+static thread_local bool g_capturing = false;
+static thread_local int g_captured = 0;
+void set_capturing(bool on) { g_capturing = on; g_captured = 0; }
+int captured_launches() { return g_captured; }
+void count_launch(int n) {
+  if (g_capturing) g_captured += n;
+  else __atomic_add_fetch(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED);
+}
 unsigned long long total_launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 constexpr int BX = 32, BY = 8, NT = BX * BY;
@@ -308,109 +315,137 @@ cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport
 }
 
 // ------------------------------------------------------------------------------------------
-// Stencil of eq. 14 at node (j, i): diagonal block a (7 nonzeros) and the products of the
-// four off-diagonal blocks with a vector v (off-diagonal blocks have 5 nonzeros).  T is the
-// arithmetic type (double: FP64 path; float: inner V-cycle of the mixed form, whose density
-// unknowns and rows are scaled by n0 so that kap = (e/eps0) n0 and cV carries 1/n0).
-template <typename T>
-struct Stencil {
-  T a11, a13, a22, a23, a31, a32, a33;  // diagonal block
-  T oe, op, oV;                         // sum over neighbours of (off-diagonal block) * v_nb
-};
-
-template <typename T>
-__device__ __forceinline__ Stencil<T> stencil(const LevelT<T> &L, T dt_inv, T kap, int j, int i, const T *ve,
-                                              const T *vp, const T *vV) {
+// Diagonal-block factors (once per Newton iteration and level).  The diagonal block of eq. 14
+// at an unknown node is [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]] with
+//   a11 = A/dt + sum(cG over faces where the node is the lower end) + sum(cF where upper),
+//   a13 = -sum(cV_e over the four faces), a33 = -sum(g), ak = A e/eps0 (ions likewise),
+// and is solved through its Schur complement in V:
+//   xV = (rV - q1 re - q2 rp) / s,  s = a33 - q1 a13 - q2 a23,  q1 = -ak/a11,  q2 = ak/a22.
+__global__ void k_factor(Level L, LevelT<float> M, int mixed, double dt_inv, double n0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > L.nr || j >= L.nz) return;
   const int P = L.P;
   const size_t k = (size_t)j * P + i;
-  const T A = L.volr[i] * L.dzc[j];
-  Stencil<T> s;
-  s.a11 = A * dt_inv; s.a22 = A * dt_inv;
-  s.a13 = 0; s.a23 = 0; s.a33 = 0;
-  s.a31 = -A * kap; s.a32 = A * kap;
-  s.oe = 0; s.op = 0; s.oV = 0;
-  if (i < L.nr) {  // east: this node is L
-    const T cGe = L.cr[CGE][k], cFe = L.cr[CFE][k], cVe = L.cr[CVE][k];
-    const T cGp = L.cr[CGP][k], cFp = L.cr[CFP][k], cVp = L.cr[CVP][k];
-    const T g = (T(i) + T(0.5)) * L.dzc[j];
-    s.a11 += cGe; s.a13 -= cVe; s.a22 += cGp; s.a23 -= cVp; s.a33 -= g;
-    const T we = ve[k + 1], wp = vp[k + 1], wV = vV[k + 1];
-    s.oe += -cFe * we + cVe * wV; s.op += -cFp * wp + cVp * wV; s.oV += g * wV;
+  const double A = L.volr[i] * L.dzc[j];
+  double a11 = A * dt_inv, a22 = A * dt_inv, a13 = 0.0, a23 = 0.0, a33 = 0.0;
+  if (i < L.nr) {
+    a11 += L.cr[CGE][k]; a22 += L.cr[CGP][k]; a13 -= L.cr[CVE][k]; a23 -= L.cr[CVP][k]; a33 -= L.gR[k];
   }
-  if (i > 0) {     // west: this node is R
-    const size_t kw = k - 1;
-    const T cGe = L.cr[CGE][kw], cFe = L.cr[CFE][kw], cVe = L.cr[CVE][kw];
-    const T cGp = L.cr[CGP][kw], cFp = L.cr[CFP][kw], cVp = L.cr[CVP][kw];
-    const T g = (T(i) - T(0.5)) * L.dzc[j];
-    s.a11 += cFe; s.a13 -= cVe; s.a22 += cFp; s.a23 -= cVp; s.a33 -= g;
-    const T we = ve[kw], wp = vp[kw], wV = vV[kw];
-    s.oe += -cGe * we + cVe * wV; s.op += -cGp * wp + cVp * wV; s.oV += g * wV;
+  if (i > 0) {
+    a11 += L.cr[CFE][k - 1]; a22 += L.cr[CFP][k - 1]; a13 -= L.cr[CVE][k - 1]; a23 -= L.cr[CVP][k - 1];
+    a33 -= L.gR[k - 1];
   }
-  {                // north: this node is L (the neighbour may be an electrode node: v = 0 there)
-    const T cGe = L.cz[CGE][k], cFe = L.cz[CFE][k], cVe = L.cz[CVE][k];
-    const T cGp = L.cz[CGP][k], cFp = L.cz[CFP][k], cVp = L.cz[CVP][k];
-    const T g = L.volr[i] / L.dz[j];
-    s.a11 += cGe; s.a13 -= cVe; s.a22 += cGp; s.a23 -= cVp; s.a33 -= g;
-    const size_t kn = k + P;
-    const T we = ve[kn], wp = vp[kn], wV = vV[kn];
-    s.oe += -cFe * we + cVe * wV; s.op += -cFp * wp + cVp * wV; s.oV += g * wV;
+  a11 += L.cz[CGE][k]; a22 += L.cz[CGP][k]; a13 -= L.cz[CVE][k]; a23 -= L.cz[CVP][k]; a33 -= L.gZ[k];
+  a11 += L.cz[CFE][k - P]; a22 += L.cz[CFP][k - P]; a13 -= L.cz[CVE][k - P]; a23 -= L.cz[CVP][k - P];
+  a33 -= L.gZ[k - P];
+  const double ak = L.Ak[k];
+  const double i11 = 1.0 / a11, i22 = 1.0 / a22;
+  const double q1 = -ak * i11, q2 = ak * i22;
+  const double is = 1.0 / (a33 - q1 * a13 - q2 * a23);
+  L.fac[FI11][k] = i11; L.fac[FI22][k] = i22; L.fac[FQ1][k] = q1; L.fac[FQ2][k] = q2; L.fac[FIS][k] = is;
+  L.fac[FA13][k] = a13; L.fac[FA23][k] = a23;
+  L.dia[DA11][k] = a11; L.dia[DA22][k] = a22; L.dia[DA33][k] = a33;
+  if (mixed) {  // density unknowns and rows in units of n0: a13, a23 / n0; q1, q2 * n0
+    M.fac[FI11][k] = (float)i11; M.fac[FI22][k] = (float)i22;
+    M.fac[FQ1][k] = (float)(q1 * n0); M.fac[FQ2][k] = (float)(q2 * n0); M.fac[FIS][k] = (float)is;
+    M.fac[FA13][k] = (float)(a13 / n0); M.fac[FA23][k] = (float)(a23 / n0);
+    M.dia[DA11][k] = (float)a11; M.dia[DA22][k] = (float)a22; M.dia[DA33][k] = (float)a33;
   }
-  {                // south: this node is R
-    const size_t ks = k - P;
-    const T cGe = L.cz[CGE][ks], cFe = L.cz[CFE][ks], cVe = L.cz[CVE][ks];
-    const T cGp = L.cz[CGP][ks], cFp = L.cz[CFP][ks], cVp = L.cz[CVP][ks];
-    const T g = L.volr[i] / L.dz[j - 1];
-    s.a11 += cFe; s.a13 -= cVe; s.a22 += cFp; s.a23 -= cVp; s.a33 -= g;
-    const T we = ve[ks], wp = vp[ks], wV = vV[ks];
-    s.oe += -cGe * we + cVe * wV; s.op += -cGp * wp + cVp * wV; s.oV += g * wV;
-  }
-  return s;
 }
 
-// K3: red-black collective Gauss-Seidel half sweep: solve the 3x3 diagonal block of every node of
-// one colour (red = (i + j) even) against the current neighbours.  The block has the pattern
-// [[a11, 0, a13], [0, a22, a23], [a31, a32, a33]] and is solved through its Schur complement in V.
-template <typename T>
-__global__ void k_smooth(LevelT<T> L, T dt_inv, T kap, int color) {
-  const int j = blockIdx.y * BY + threadIdx.y + 1;
-  const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + color) & 1);
-  if (j >= L.nz || i > L.nr) return;
-  const size_t k = (size_t)j * L.P + i;
-  const Stencil<T> s = stencil<T>(L, dt_inv, kap, j, i, L.du[NE], L.du[NP], L.du[NV]);
-  const T re = L.f[NE][k] - s.oe, rp = L.f[NP][k] - s.op, rV = L.f[NV][k] - s.oV;
-  const T i11 = T(1) / s.a11, i22 = T(1) / s.a22;
-  const T sch = s.a33 - s.a31 * s.a13 * i11 - s.a32 * s.a23 * i22;
-  const T xV = (rV - s.a31 * re * i11 - s.a32 * rp * i22) / sch;
-  L.du[NE][k] = (re - s.a13 * xV) * i11;
-  L.du[NP][k] = (rp - s.a23 * xV) * i22;
-  L.du[NV][k] = xV;
-}
-
-template <typename T>
-cudaError_t launch_smooth(const LevelT<T> &L, double dt, double kap, int color, cudaStream_t st) {
-  dim3 b(BX, BY), g(((L.nr + 2) / 2 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
-  k_smooth<T><<<g, b, 0, st>>>(L, T(dt > 0 ? 1.0 / dt : 0.0), T(kap), color);
+cudaError_t launch_factor(const Level &L, const LevelT<float> *M, double dt, double n0, cudaStream_t st) {
+  dim3 b(32, 4), g((L.nr + 1 + 31) / 32, (L.nz - 1 + 3) / 4);
+  k_factor<<<g, b, 0, st>>>(L, M ? *M : LevelT<float>(), M ? 1 : 0, dt > 0 ? 1.0 / dt : 0.0, n0);
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_smooth<double>(const LevelT<double> &, double, double, int, cudaStream_t);
-template cudaError_t launch_smooth<float>(const LevelT<float> &, double, double, int, cudaStream_t);
+
+// Sum over the four neighbours of (off-diagonal block of eq. 14) x v at node k = (j, i).  The
+// off-diagonal blocks have 5 nonzeros: towards a neighbour across a face where this node is the
+// lower end: [-cF, cV] for each species, g for V; where it is the upper end: [-cG, cV], g.
+// Electrode-row neighbours carry v = 0.
+template <typename T>
+__device__ __forceinline__ void offdiag(const LevelT<T> &L, int i, size_t k, const T *ve, const T *vp,
+                                        const T *vV, T &oe, T &op, T &oV) {
+  const int P = L.P;
+  T e = 0, p = 0, V = 0;
+  if (i < L.nr) {
+    const size_t n = k + 1;
+    const T w = vV[n];
+    e += L.cr[CVE][k] * w - L.cr[CFE][k] * ve[n];
+    p += L.cr[CVP][k] * w - L.cr[CFP][k] * vp[n];
+    V += L.gR[k] * w;
+  }
+  if (i > 0) {
+    const size_t n = k - 1;
+    const T w = vV[n];
+    e += L.cr[CVE][n] * w - L.cr[CGE][n] * ve[n];
+    p += L.cr[CVP][n] * w - L.cr[CGP][n] * vp[n];
+    V += L.gR[n] * w;
+  }
+  {
+    const size_t n = k + P;
+    const T w = vV[n];
+    e += L.cz[CVE][k] * w - L.cz[CFE][k] * ve[n];
+    p += L.cz[CVP][k] * w - L.cz[CFP][k] * vp[n];
+    V += L.gZ[k] * w;
+  }
+  {
+    const size_t n = k - P;
+    const T w = vV[n];
+    e += L.cz[CVE][n] * w - L.cz[CGE][n] * ve[n];
+    p += L.cz[CVP][n] * w - L.cz[CGP][n] * vp[n];
+    V += L.gZ[n] * w;
+  }
+  oe = e; op = p; oV = V;
+}
+
+// K3: red-black collective Gauss-Seidel half sweep: every node of one colour (red = (i + j)
+// even) solves its 3x3 diagonal block (stored factors) against the current neighbours.
+template <typename T>
+__global__ void k_smooth(LevelT<T> L, int color) {
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
+  if (j >= L.nz || i > L.nr) return;
+  const size_t k = (size_t)j * L.P + i;
+  T oe, op, oV;
+  offdiag<T>(L, i, k, L.du[NE], L.du[NP], L.du[NV], oe, op, oV);
+  const T re = L.f[NE][k] - oe, rp = L.f[NP][k] - op, rV = L.f[NV][k] - oV;
+  const T xV = (rV - L.fac[FQ1][k] * re - L.fac[FQ2][k] * rp) * L.fac[FIS][k];
+  L.du[NE][k] = (re - L.fac[FA13][k] * xV) * L.fac[FI11][k];
+  L.du[NP][k] = (rp - L.fac[FA23][k] * xV) * L.fac[FI22][k];
+  L.du[NV][k] = xV;
+}
+
+constexpr int SBX = 32, SBY = 2;  // stencil kernels: small blocks so that coarse levels spread over the SMs
+
+template <typename T>
+cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st) {
+  dim3 b(SBX, SBY), g(((L.nr + 2) / 2 + SBX - 1) / SBX, (L.nz - 1 + SBY - 1) / SBY);
+  k_smooth<T><<<g, b, 0, st>>>(L, color);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t);
+template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t);
 
 // K4: linear residual r = f - J v (or J v when f is null), optional per-field sums of squares
 // (accumulated in FP64).
 template <typename T>
-__global__ void k_linres(LevelT<T> L, T dt_inv, T kap, const T *v0, const T *v1, const T *v2, const T *f0,
-                         const T *f1, const T *f2, T *o0, T *o1, T *o2, double *partials, unsigned *counter,
-                         double *out3) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y + 1;
+__global__ void k_linres(LevelT<T> L, const T *v0, const T *v1, const T *v2, const T *f0, const T *f1, const T *f2,
+                         T *o0, T *o1, T *o2, double *partials, unsigned *counter, double *out3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
   if (i <= L.nr && j < L.nz) {
     const size_t k = (size_t)j * L.P + i;
-    const Stencil<T> s = stencil<T>(L, dt_inv, kap, j, i, v0, v1, v2);
-    T je = s.a11 * v0[k] + s.a13 * v2[k] + s.oe;
-    T jp = s.a22 * v1[k] + s.a23 * v2[k] + s.op;
-    T jV = s.a31 * v0[k] + s.a32 * v1[k] + s.a33 * v2[k] + s.oV;
+    T oe, op, oV;
+    offdiag<T>(L, i, k, v0, v1, v2, oe, op, oV);
+    const T ak = L.Ak[k];
+    T je = L.dia[DA11][k] * v0[k] + L.fac[FA13][k] * v2[k] + oe;
+    T jp = L.dia[DA22][k] * v1[k] + L.fac[FA23][k] * v2[k] + op;
+    T jV = ak * (v1[k] - v0[k]) + L.dia[DA33][k] * v2[k] + oV;
     if (f0) { je = f0[k] - je; jp = f1[k] - jp; jV = f2[k] - jV; }
     o0[k] = je; o1[k] = jp; o2[k] = jV;
     acc[0] = (double)je * je; acc[1] = (double)jp * jp; acc[2] = (double)jV * jV;
@@ -419,26 +454,25 @@ __global__ void k_linres(LevelT<T> L, T dt_inv, T kap, const T *v0, const T *v1,
 }
 
 template <typename T>
-cudaError_t launch_linres(const LevelT<T> &L, double dt, double kap, T *const v[3], T *const f[3], T *out[3],
-                          double *partials, unsigned *counter, double *out3, cudaStream_t st) {
-  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
-  k_linres<T><<<g, b, 0, st>>>(L, T(dt > 0 ? 1.0 / dt : 0.0), T(kap), v[0], v[1], v[2], f ? f[0] : nullptr,
-                               f ? f[1] : nullptr, f ? f[2] : nullptr, out[0], out[1], out[2], partials, counter,
-                               out3);
+cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,
+                          unsigned *counter, double *out3, cudaStream_t st) {
+  const int bx = 32, by = out3 ? BY : SBY;
+  dim3 b(bx, by), g((L.nr + 1 + bx - 1) / bx, (L.nz - 1 + by - 1) / by);
+  k_linres<T><<<g, b, 0, st>>>(L, v[0], v[1], v[2], f ? f[0] : nullptr, f ? f[1] : nullptr, f ? f[2] : nullptr,
+                               out[0], out[1], out[2], partials, counter, out3);
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_linres<double>(const LevelT<double> &, double, double, double *const[3],
-                                           double *const[3], double *[3], double *, unsigned *, double *,
-                                           cudaStream_t);
-template cudaError_t launch_linres<float>(const LevelT<float> &, double, double, float *const[3], float *const[3],
-                                          float *[3], double *, unsigned *, double *, cudaStream_t);
+template cudaError_t launch_linres<double>(const LevelT<double> &, double *const[3], double *const[3], double *[3],
+                                           double *, unsigned *, double *, cudaStream_t);
+template cudaError_t launch_linres<float>(const LevelT<float> &, float *const[3], float *const[3], float *[3],
+                                          double *, unsigned *, double *, cudaStream_t);
 
 // K5: restriction f_c = P^T r (full weighting in the node coordinates), and du_c = 0.
 template <typename T>
 __global__ void k_restrict(LevelT<T> F, LevelT<T> C) {
-  const int I = blockIdx.x * BX + threadIdx.x;
-  const int J = blockIdx.y * BY + threadIdx.y + 1;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
   if (I > C.nr || J >= C.nz) return;
   const size_t kc = (size_t)J * C.P + I;
   T s0 = 0, s1 = 0, s2 = 0;
@@ -461,7 +495,7 @@ __global__ void k_restrict(LevelT<T> F, LevelT<T> C) {
 
 template <typename T>
 cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st) {
-  dim3 b(BX, BY), g((C.nr + 1 + BX - 1) / BX, (C.nz - 1 + BY - 1) / BY);
+  dim3 b(SBX, SBY), g((C.nr + 1 + SBX - 1) / SBX, (C.nz - 1 + SBY - 1) / SBY);
   k_restrict<T><<<g, b, 0, st>>>(F, C);
   count_launch();
   return cudaGetLastError();
@@ -472,8 +506,8 @@ template cudaError_t launch_restrict<float>(const LevelT<float> &, const LevelT<
 // K6: prolongation and correction du_f += P du_c (bilinear in (r, z)).
 template <typename T>
 __global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   if (i > F.nr || j >= F.nz) return;
   const size_t kf = (size_t)j * F.P + i;
   int J0, J1;
@@ -495,7 +529,7 @@ __global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
 
 template <typename T>
 cudaError_t launch_prolong_add(const LevelT<T> &C, const LevelT<T> &F, cudaStream_t st) {
-  dim3 b(BX, BY), g((F.nr + 1 + BX - 1) / BX, (F.nz - 1 + BY - 1) / BY);
+  dim3 b(SBX, SBY), g((F.nr + 1 + SBX - 1) / SBX, (F.nz - 1 + SBY - 1) / SBY);
   k_prolong_add<T><<<g, b, 0, st>>>(C, F);
   count_launch();
   return cudaGetLastError();
@@ -565,6 +599,7 @@ cudaError_t launch_prolong_state(const Level &C, const StateView &cs, const Leve
 // node = (j - 1) * (nr + 1) + i), scale columns then rows to unit max-abs entry, and invert the
 // scaled matrix by Gauss-Jordan elimination with partial pivoting.  One CTA.
 constexpr int CT = 256;
+constexpr int kSmemGJ = 48;
 
 __global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, double *M, double *Minv,
                                                       double *rs, double *cs, int *flag) {
@@ -646,6 +681,58 @@ __global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, do
     Minv[e] = (r == c) ? 1.0 : 0.0;
   }
   __syncthreads();
+  if (n <= kSmemGJ) {
+    // Gauss-Jordan in shared memory (the usual 5^2-node coarsest level has n = 45)
+    __shared__ double sA[kSmemGJ * kSmemGJ], sB[kSmemGJ * kSmemGJ];
+    __shared__ int sp;
+    for (int e = tid; e < n * n; e += CT) { sA[e] = M[e]; sB[e] = Minv[e]; }
+    __syncthreads();
+    for (int col = 0; col < n; ++col) {
+      if (tid < 32) {  // pivot search by one warp, ties: lowest row index
+        double best = -1.0;
+        int bi = col;
+        for (int r = col + tid; r < n; r += 32) {
+          const double v = fabs(sA[r * n + col]);
+          if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) sp = best > 0.0 ? bi : -1;
+      }
+      __syncthreads();
+      const int p = sp;
+      if (p < 0) { if (tid == 0) *flag = 1; return; }
+      if (p != col) {
+        for (int c = tid; c < n; c += CT) {
+          double t = sA[p * n + c]; sA[p * n + c] = sA[col * n + c]; sA[col * n + c] = t;
+          t = sB[p * n + c]; sB[p * n + c] = sB[col * n + c]; sB[col * n + c] = t;
+        }
+      }
+      __syncthreads();
+      const double piv = 1.0 / sA[col * n + col];
+      __syncthreads();
+      for (int c = tid; c < n; c += CT) { sA[col * n + c] *= piv; sB[col * n + c] *= piv; }
+      __syncthreads();
+      for (int r = tid; r < n; r += CT) fac[r] = (r == col) ? 0.0 : sA[r * n + col];
+      __syncthreads();
+      for (int e = tid; e < n * n; e += CT) {
+        const int r = e / n, c = e % n;
+        const double fr = fac[r];
+        if (fr != 0.0) {
+          sA[e] -= fr * sA[col * n + c];
+          sB[e] -= fr * sB[col * n + c];
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += CT) Minv[e] = sB[e];
+    if (tid == 0) *flag = 0;
+    return;
+  }
+  // larger coarsest levels: the same elimination in global memory
   // Gauss-Jordan with partial pivoting (ties: lowest row index)
   for (int col = 0; col < n; ++col) {
     double best = -1.0;
@@ -838,18 +925,20 @@ cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n
   return cudaGetLastError();
 }
 
-__global__ void k_outer_residual(Level L, LevelT<float> M, double dt_inv, double inv_n0, double *partials,
-                                 unsigned *counter, double *out3) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y + 1;
+__global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double *partials, unsigned *counter,
+                                 double *out3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
   if (i <= L.nr && j < L.nz) {
     const size_t k = (size_t)j * L.P + i;
     const double *v0 = L.du[NE], *v1 = L.du[NP], *v2 = L.du[NV];
-    const Stencil<double> s = stencil<double>(L, dt_inv, kKappa, j, i, v0, v1, v2);
-    const double re = L.f[NE][k] - (s.a11 * v0[k] + s.a13 * v2[k] + s.oe);
-    const double rp = L.f[NP][k] - (s.a22 * v1[k] + s.a23 * v2[k] + s.op);
-    const double rV = L.f[NV][k] - (s.a31 * v0[k] + s.a32 * v1[k] + s.a33 * v2[k] + s.oV);
+    double oe, op, oV;
+    offdiag<double>(L, i, k, v0, v1, v2, oe, op, oV);
+    const double ak = L.Ak[k];
+    const double re = L.f[NE][k] - (L.dia[DA11][k] * v0[k] + L.fac[FA13][k] * v2[k] + oe);
+    const double rp = L.f[NP][k] - (L.dia[DA22][k] * v1[k] + L.fac[FA23][k] * v2[k] + op);
+    const double rV = L.f[NV][k] - (ak * (v1[k] - v0[k]) + L.dia[DA33][k] * v2[k] + oV);
     M.f[NE][k] = (float)(re * inv_n0);
     M.f[NP][k] = (float)(rp * inv_n0);
     M.f[NV][k] = (float)rV;
@@ -858,10 +947,57 @@ __global__ void k_outer_residual(Level L, LevelT<float> M, double dt_inv, double
   reduce_finish<3>(acc, partials, counter, out3, 0);
 }
 
-cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double dt, double n0, double *partials,
+cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double n0, double *partials,
                                   unsigned *counter, double *out3, cudaStream_t st) {
   dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
-  k_outer_residual<<<g, b, 0, st>>>(L, M, dt > 0 ? 1.0 / dt : 0.0, 1.0 / n0, partials, counter, out3);
+  k_outer_residual<<<g, b, 0, st>>>(L, M, 1.0 / n0, partials, counter, out3);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Cycle control on the device (row a7): the V-cycle loop of a linear solve runs inside a CUDA
+// graph as a conditional WHILE node; these one-thread kernels evaluate the stopping test
+//   max_f ||r_f|| / w_f  <=  eta * (the same at du = 0)
+// from the per-field sums of squares norm3, record the history and set the loop condition.
+__device__ __forceinline__ double weighted_norm(const SolveCtl *c, const double *norm3) {
+  double m = 0.0;
+  for (int q = 0; q < 3; ++q) {
+    const double v = sqrt(norm3[q]) / c->w[q];
+    if (!(v == v)) return NAN;
+    m = fmax(m, v);
+  }
+  return m;
+}
+
+__global__ void k_solve_init(SolveCtl *c, const double *norm3, cudaGraphConditionalHandle h) {
+  const double r0 = weighted_norm(c, norm3);
+  c->r0 = r0;
+  c->ncyc = 0;
+  c->rel = r0 > 0.0 ? 1.0 : 0.0;
+  c->hist[0] = c->rel;
+  const bool go = r0 > 0.0 && isfinite(r0) && c->rel > c->eta && c->max_cycles > 0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_solve_check(SolveCtl *c, const double *norm3, cudaGraphConditionalHandle h) {
+  const double rel = weighted_norm(c, norm3) / c->r0;
+  const int n = c->ncyc + 1;
+  c->ncyc = n;
+  c->rel = rel;
+  if (n < kMaxHist) c->hist[n] = rel;
+  const bool go = isfinite(rel) && rel > c->eta && n < c->max_cycles;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t launch_solve_init(SolveCtl *ctl, const double *norm3, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_solve_init<<<1, 1, 0, st>>>(ctl, norm3, h);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_check(SolveCtl *ctl, const double *norm3, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_solve_check<<<1, 1, 0, st>>>(ctl, norm3, h);
   count_launch();
   return cudaGetLastError();
 }

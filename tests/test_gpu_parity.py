@@ -287,3 +287,31 @@ def test_mixed_steady_257_matches_fp64(mg):
     # both are the same discrete steady state to the solve tolerance
     for q in range(3):
         assert np.abs(a[q] - b[q]).max() <= 1e-6 * np.abs(a[q]).max(), q
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_and_host_driven_solves_agree(mg, precision):
+    """The device-side V-cycle loop (CUDA graph with a conditional node) and the host-driven
+    loop launch the same kernels in the same order: identical iterates and histories."""
+    d = W.make_discharge(64, seed=2, V_cathode=-300.0, use_table=True)
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    out = []
+    for graphs in (1, 0):
+        s = mg.from_discharge(d, precision=prec, use_graphs=graphs)
+        F, _ = s.residual(1e-7)
+        x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-10, 100)
+        assert rc == mg.MG_OK
+        out.append((x, h))
+    (xa, ha), (xb, hb) = out
+    assert len(ha) == len(hb)
+    assert np.array_equal(ha, hb)
+    for q in range(3):
+        assert np.array_equal(xa[q], xb[q])
+
+
+def test_graph_solve_respects_cycle_cap(mg):
+    d = W.make_discharge(64, seed=2, V_cathode=-300.0)
+    s = mg.from_discharge(d)
+    F, _ = s.residual(1e-7)
+    x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-30, 3)
+    assert rc == mg.MG_ENOCONV and len(h) == 4
