@@ -324,6 +324,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roofline,
     }
+    if not args.no_forms:
+        line["forms"] = measure_forms(args, dev, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, sample_s, detail, counts = oracle_estimate(sample_vcycles=args.ref_vcycles)
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -340,6 +342,83 @@ def run_ours(args):
     return 0
 
 
+def measure_forms(args, dev, peaks):
+    """The other forms of the hot path, measured once each after the headline steps:
+    mixed-precision steady 257^2 solve, FP32 inner V-cycle at 1025^2 (HBM roofline of its
+    smoother), and the 64-instance batch of uneven discharges (solves/s, p50/p99)."""
+    import torch
+    import workloads as W
+    from paper_0811_4446_gb300 import mg
+    out = {}
+    # mixed-precision steady solve of the same 257^2 workload
+    d = W.steady_257()
+    s = mg.from_discharge(d, precision=mg.MG_MIXED)
+    ins = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (d.ne0, d.np0, d.V0)]
+    times = []
+    for k in range(4):
+        s.set_state(*ins)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = s.solve_steady(TOL)
+        torch.cuda.synchronize()
+        if rc != mg.MG_OK:
+            raise RuntimeError("mixed steady solve failed")
+        if k > 0:
+            times.append(time.perf_counter() - t0)
+    out["mixed_steady_257"] = {"solves_per_s": 1.0 / statistics.median(times), "ms": 1000 * statistics.median(times),
+                               "vcycles": st["vcycles"], "newton": st["newton_iterations"]}
+    s.close()
+    # FP32 inner V-cycle of the mixed form at 1025^2 (transient physics, dt = 1 ns)
+    d = W.transient_1025()
+    nodes = (d.nr + 1) * (d.nz - 1)
+    s = mg.from_discharge(d, precision=mg.MG_MIXED)
+    F, _ = s.residual(1e-9)
+    f = [-a for a in F]
+    s.linear_solve(1e-9, f, 0.0, 0)
+    t0 = time.perf_counter()
+    s.linear_solve(1e-9, f, 0.0, 0)
+    t1 = time.perf_counter()
+    x, hist, _ = s.linear_solve(1e-9, f, 0.0, 30)
+    t2 = time.perf_counter()
+    vc = ((t2 - t1) - (t1 - t0)) / 30
+    s.profile_begin(mg.MG_PROF_SMOOTH, 0)
+    s.linear_solve(1e-9, f, 0.0, 10)
+    n, ms = s.profile_end()
+    avg = ms / n / 1000.0
+    byt = 88 * nodes       # FP32: 12 coefficients + 2 conductances per node, 7 factors + f + du for the colour
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out["mixed_vcycle_1025"] = {"vcycle_us": vc * 1e6, "mpts_per_s": (d.nr + 1) * (d.nz + 1) / vc / 1e6,
+                                "residual_drop_30_cycles": float(hist[-1]),
+                                "roofline": {"bound": "hbm", "kernel": "k_smooth<float> (1025x1025 level)",
+                                             "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
+                                             "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6,
+                                             "algorithmic_bytes_per_launch": byt, "traffic": None}}
+    s.close()
+    # batched form: 64 independent discharges of seeded sizes 65^2..513^2, mixed precision
+    ds = W.batch_64()
+    solvers = [mg.from_discharge(dd, precision=mg.MG_MIXED, stream=torch.cuda.Stream(device=dev)) for dd in ds]
+    inits = [[np.ascontiguousarray(a) for a in (dd.ne0, dd.np0, dd.V0)] for dd in ds]
+    for sv in solvers:
+        sv.autotune()
+    for rep in range(2):
+        for sv, ini in zip(solvers, inits):
+            sv.set_state(*ini)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, ms_i, rcs = mg.solve_steady_batch(solvers, TOL, workers=args.batch_workers)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if rc != mg.MG_OK:
+            raise RuntimeError(f"batched solve failed: {rcs}")
+    sizes = sorted(set(dd.nr + 1 for dd in ds))
+    out["batch_64"] = {"solves_per_s": len(ds) / wall, "wall_s": wall, "p50_ms": float(np.percentile(ms_i, 50)),
+                       "p99_ms": float(np.percentile(ms_i, 99)), "instances": len(ds), "sizes": sizes,
+                       "workers": args.batch_workers, "precision": "mixed"}
+    for sv in solvers:
+        sv.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,6 +427,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-vcycles", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the mixed / batched form measurements")
+    ap.add_argument("--batch-workers", type=int, default=16)
     ap.add_argument("--no-extras", action="store_true",
                     help="timed steps only (used for the ncu launch-list pass)")
     args = ap.parse_args()

@@ -184,6 +184,22 @@ int mg_march(mg_state *s, double dt_start, double tol, mg_stats *stats);
  * with the long step dt_max, until the steady residual <= tol. */
 int mg_solve_steady(mg_state *s, double tol, mg_stats *stats);
 
+/* Batched form: solve n independent discharges to their steady states (mg_solve_steady on
+ * each) concurrently.  `workers` host threads take instances from a shared queue; every state
+ * runs on its own stream (give each state a distinct stream at mg_create so that the GPU can
+ * overlap them) and every linear solve is a device-side CUDA-graph loop.  ms_out[k] (may be
+ * NULL) receives instance k's wall time from its start to its stream being idle, rc_out[k]
+ * (may be NULL) its status.  Returns MG_OK or the first failing instance's status.  The
+ * states must live on the calling thread's current device. */
+int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, double *ms_out, int *rc_out);
+
+/* Autotuner of the smoother's launch shape: times the red-black half sweep of every level
+ * (FP64 and, in the mixed form, FP32) over a fixed set of thread-block shapes and keeps the
+ * fastest per level.  Leaves the solution state untouched.  shapes_out (may be NULL) receives
+ * 4 ints per level: FP64 (bx, by), FP32 (bx, by). */
+int mg_autotune(mg_state *s, int32_t *shapes_out);
+int mg_num_levels(const mg_state *s);
+
 /* Statistics accumulated since creation (or the last mg_reset_stats). */
 int mg_get_stats(const mg_state *s, mg_stats *out);
 void mg_reset_stats(mg_state *s);

@@ -7,7 +7,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <chrono>
 #include <new>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -34,6 +37,8 @@ struct LevelBuf {
   StateView sv;          // FP64 nonlinear state on this level
   double *geo;           // device geometry block
   float *geo32;
+  int sbx = 32, sby = 2;         // smoother launch shape, FP64 view (autotuned)
+  int sbx32 = 32, sby32 = 2;     // smoother launch shape, FP32 view (autotuned)
 };
 
 }  // namespace
@@ -285,10 +290,16 @@ template <typename T> double nscale_of(const mg_state *s);
 template <> double nscale_of<double>(const mg_state *) { return 1.0; }
 template <> double nscale_of<float>(const mg_state *s) { return s->prm.n0; }
 
+template <typename T> void shape_of(const LevelBuf &b, int &bx, int &by);
+template <> void shape_of<double>(const LevelBuf &b, int &bx, int &by) { bx = b.sbx; by = b.sby; }
+template <> void shape_of<float>(const LevelBuf &b, int &bx, int &by) { bx = b.sbx32; by = b.sby32; }
+
 template <typename T>
 int smooth(mg_state *s, int l, int color, cudaStream_t st) {
   ProfScope ps(s, MG_PROF_SMOOTH, l);
-  CK(launch_smooth<T>(view<T>(s->lv[l]), color, st));
+  int bx, by;
+  shape_of<T>(s->lv[l], bx, by);
+  CK(launch_smooth<T>(view<T>(s->lv[l]), color, st, bx, by));
   return MG_OK;
 }
 
@@ -584,6 +595,23 @@ int check_where(mg_state *s, int where) {
   return MG_OK;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------- autotuner
+namespace {
+// Mean device time of `reps` launches of the smoother with shape (bx, by) on level l.
+template <typename T>
+int time_shape(mg_state *s, int l, int bx, int by, int reps, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+  const LevelT<T> &L = view<T>(s->lv[l]);
+  for (int r = 0; r < 2; ++r) CK(launch_smooth<T>(L, r & 1, s->stream, bx, by));
+  CK(cudaEventRecord(e0, s->stream));
+  for (int r = 0; r < reps; ++r) CK(launch_smooth<T>(L, r & 1, s->stream, bx, by));
+  CK(cudaEventRecord(e1, s->stream));
+  CK(cudaEventSynchronize(e1));
+  CK(cudaEventElapsedTime(ms, e0, e1));
+  *ms /= reps;
+  return MG_OK;
+}
 }  // namespace
 
 // ================================================================ C ABI
@@ -976,5 +1004,81 @@ int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms) {
 }
 
 double mg_probe_fp64_gflops(void *stream) { return probe_fp64_gflops((cudaStream_t)stream); }
+
+
+int mg_autotune(mg_state *s, int32_t *shapes_out) {
+  if (!s) return MG_EINVAL;
+  static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+  const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = MG_OK;
+  // the smoother only rewrites the correction arrays, so tuning leaves the state untouched
+  for (int l = 0; l < s->nlev - 1 && rc == MG_OK; ++l) {
+    for (int prec = 0; prec < (mixed(s) ? 2 : 1) && rc == MG_OK; ++prec) {
+      float best = 1e30f;
+      int bi = 1;
+      for (int c = 0; c < nc && rc == MG_OK; ++c) {
+        float ms = 0.f;
+        rc = prec == 0 ? time_shape<double>(s, l, cand[c][0], cand[c][1], 10, e0, e1, &ms)
+                       : time_shape<float>(s, l, cand[c][0], cand[c][1], 10, e0, e1, &ms);
+        if (ms < best) { best = ms; bi = c; }
+      }
+      LevelBuf &b = s->lv[l];
+      if (prec == 0) { b.sbx = cand[bi][0]; b.sby = cand[bi][1]; }
+      else { b.sbx32 = cand[bi][0]; b.sby32 = cand[bi][1]; }
+      if (shapes_out) {
+        shapes_out[4 * l + 2 * prec] = cand[bi][0];
+        shapes_out[4 * l + 2 * prec + 1] = cand[bi][1];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // graphs recorded the old launch shapes
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (s->vexec[l]) { cudaGraphExecDestroy(s->vexec[l]); s->vexec[l] = nullptr; }
+  CK(launch_zero_du<double>(s->lv[0].L, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return rc;
+}
+
+int mg_num_levels(const mg_state *s) { return s ? s->nlev : 0; }
+
+// ---------------------------------------------------------------- batched steady solves
+int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, double *ms_out, int *rc_out) {
+  if (!states || n < 0 || !(tol > 0.0)) return MG_EINVAL;
+  for (int k = 0; k < n; ++k)
+    if (!states[k]) return MG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MG_ECUDA;
+  workers = std::max(1, std::min(workers, n));
+  std::atomic<int> next(0);
+  std::vector<int> rcs(n, MG_OK);
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      const auto t0 = std::chrono::steady_clock::now();
+      int rc = mg_solve_steady(states[k], tol, nullptr);
+      if (cudaStreamSynchronize(states[k]->stream) != cudaSuccess && rc == MG_OK) rc = MG_ECUDA;
+      const auto t1 = std::chrono::steady_clock::now();
+      rcs[k] = rc;
+      if (ms_out) ms_out[k] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+  int first = MG_OK;
+  for (int k = 0; k < n; ++k) {
+    if (rc_out) rc_out[k] = rcs[k];
+    if (first == MG_OK && rcs[k] != MG_OK) first = rcs[k];
+  }
+  return first;
+}
 
 }  // extern "C"

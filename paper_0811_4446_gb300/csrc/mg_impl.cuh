@@ -85,7 +85,7 @@ cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport
                             bool write_f, double *Fout[3], double *partials, unsigned *counter,
                             double *out6, cudaStream_t st);
 template <typename T>
-cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st);
+cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx = 32, int by = 2);
 // r = f - J v (or out = J v when f == nullptr); optional per-field norms (sum of squares) -> out3
 template <typename T>
 cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,

@@ -420,15 +420,16 @@ __global__ void k_smooth(LevelT<T> L, int color) {
 
 constexpr int SBX = 32, SBY = 2;  // stencil kernels: small blocks so that coarse levels spread over the SMs
 
+// Launch shape (bx, by) is a tuning knob: one thread per node of the colour, bx along r.
 template <typename T>
-cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st) {
-  dim3 b(SBX, SBY), g(((L.nr + 2) / 2 + SBX - 1) / SBX, (L.nz - 1 + SBY - 1) / SBY);
+cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx, int by) {
+  dim3 b(bx, by), g(((L.nr + 2) / 2 + bx - 1) / bx, (L.nz - 1 + by - 1) / by);
   k_smooth<T><<<g, b, 0, st>>>(L, color);
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t);
-template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t);
+template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t, int, int);
+template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t, int, int);
 
 // K4: linear residual r = f - J v (or J v when f is null), optional per-field sums of squares
 // (accumulated in FP64).

@@ -80,6 +80,9 @@ SIGNATURES = {
     "mg_profile_begin": (_i, [_vp, _i, _i]),
     "mg_profile_end": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "mg_probe_fp64_gflops": (ctypes.c_double, [_vp]),
+    "mg_solve_steady_batch": (_i, [ctypes.POINTER(_vp), _i, _d, _i, _vp, _vp]),
+    "mg_autotune": (_i, [_vp, _vp]),
+    "mg_num_levels": (_i, [_vp]),
     "mg_residual_noalloc": (_i, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_params), _vp, _vp, _vp, _vp, _vp, _vp,
                                  _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp]),
 }
@@ -277,6 +280,12 @@ class Solver:
     def reset_stats(self):
         self.lib.mg_reset_stats(self.h)
 
+    def autotune(self):
+        n = self.lib.mg_num_levels(self.h)
+        out = np.zeros(4 * n, dtype=np.int32)
+        self._check(self.lib.mg_autotune(self.h, out.ctypes.data))
+        return out.reshape(n, 4)
+
     def profile_begin(self, kernel: int, level: int = 0):
         self._check(self.lib.mg_profile_begin(self.h, int(kernel), int(level)))
 
@@ -285,6 +294,17 @@ class Solver:
         ms = ctypes.c_double(0.0)
         self._check(self.lib.mg_profile_end(self.h, ctypes.byref(n), ctypes.byref(ms)))
         return int(n.value), float(ms.value)
+
+
+def solve_steady_batch(solvers, tol: float, workers: int = 8):
+    """Steady solves of independent Solver objects concurrently; returns (rc, ms[n], rc[n])."""
+    lib = load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.h for s in solvers])
+    ms = np.zeros(n)
+    rcs = np.zeros(n, dtype=np.int32)
+    rc = lib.mg_solve_steady_batch(hs, n, float(tol), int(workers), ms.ctypes.data, rcs.ctypes.data)
+    return rc, ms, rcs
 
 
 def residual_noalloc(nr: int, nz: int, R: float, z, params: mg_params, state, old_state, sources, dt: float,
@@ -326,11 +346,11 @@ def probe_fp64_gflops() -> float:
     return float(load().mg_probe_fp64_gflops(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
 
-def from_discharge(d, **param_overrides) -> Solver:
+def from_discharge(d, stream=None, **param_overrides) -> Solver:
     """Solver for a workloads.Discharge (sources and initial state loaded)."""
     p = default_params(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p,
                        D_p=d.D_p, pressure_factor=d.pressure_factor, **param_overrides)
-    s = Solver(d.nr, d.nz, d.R, d.z, p, table=d.table)
+    s = Solver(d.nr, d.nz, d.R, d.z, p, table=d.table, stream=stream)
     s.set_sources(np.ascontiguousarray(d.S_e), np.ascontiguousarray(d.S_p))
     s.set_state(np.ascontiguousarray(d.ne0), np.ascontiguousarray(d.np0), np.ascontiguousarray(d.V0))
     return s

@@ -315,3 +315,37 @@ def test_graph_solve_respects_cycle_cap(mg):
     F, _ = s.residual(1e-7)
     x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-30, 3)
     assert rc == mg.MG_ENOCONV and len(h) == 4
+
+
+# ---------------------------------------------------------------- batched form, autotuner
+def test_batched_steady_solves_equal_individual_solves(mg):
+    ds = W.batch_64(seed=4, count=6, sizes=(16, 32, 64))
+    solvers = [mg.from_discharge(d, precision=mg.MG_MIXED, stream=torch.cuda.Stream()) for d in ds]
+    rc, ms, rcs = mg.solve_steady_batch(solvers, 1e-8, workers=4)
+    assert rc == mg.MG_OK, rcs
+    assert np.all(ms > 0)
+    for d, sb in zip(ds, solvers):
+        si = mg.from_discharge(d, precision=mg.MG_MIXED)
+        assert si.solve_steady(1e-8)[0] == mg.MG_OK
+        a, b = sb.get_state(), si.get_state()
+        for q in range(3):
+            assert np.array_equal(a[q], b[q])     # deterministic kernels: concurrency changes nothing
+        g, phys = _oracle(d)
+        F, T = disc.residual(g, np.stack(a), None, d.S_e, d.S_p, None, phys, with_terms=True)
+        assert disc.rho(F, T).max() <= 1.05e-8
+
+
+def test_autotune_keeps_results(mg):
+    d = W.make_discharge(128, seed=3, V_cathode=-300.0, use_table=True)
+    res = []
+    for tune in (False, True):
+        s = mg.from_discharge(d, precision=mg.MG_MIXED)
+        if tune:
+            shapes = s.autotune()
+            assert shapes.shape[1] == 4 and np.all(shapes[:-1, 0] >= 32)
+        F, _ = s.residual(1e-7)
+        x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-10, 100)
+        res.append((x, h))
+    assert np.array_equal(res[0][1], res[1][1])
+    for q in range(3):
+        assert np.array_equal(res[0][0][q], res[1][0][q])
