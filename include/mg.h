@@ -184,6 +184,14 @@ int mg_march(mg_state *s, double dt_start, double tol, mg_stats *stats);
  * with the long step dt_max, until the steady residual <= tol. */
 int mg_solve_steady(mg_state *s, double tol, mg_stats *stats);
 
+/* Steady state from an initial guess of the full-grid state (the learned-guess form, see
+ * unet.h): the current state is saved, (ne, np, V) become the state (electrode rows set to
+ * their Dirichlet values) and the march starts with the long step dt_max.  If that march
+ * fails or needs more than 60 steps, the saved state is restored and mg_solve_steady's
+ * continuation runs instead (*used_fallback = 1). */
+int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const double *V, int where, double tol,
+                          mg_stats *stats, int *used_fallback);
+
 /* Batched form: solve n independent discharges to their steady states (mg_solve_steady on
  * each) concurrently.  `workers` host threads take instances from a shared queue; every state
  * runs on its own stream (give each state a distinct stream at mg_create so that the GPU can

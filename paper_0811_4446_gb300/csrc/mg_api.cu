@@ -37,6 +37,7 @@ struct LevelBuf {
   StateView sv;          // FP64 nonlinear state on this level
   double *geo;           // device geometry block
   float *geo32;
+  double *ubak[3];       // copy of the state (fallback of the learned-guess solve)
   int sbx = 32, sby = 2;         // smoother launch shape, FP64 view (autotuned)
   int sbx32 = 32, sby32 = 2;     // smoother launch shape, FP32 view (autotuned)
 };
@@ -119,7 +120,7 @@ struct Carver {
   }
 };
 
-constexpr int kFieldsPerLevel = 42;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3
+constexpr int kFieldsPerLevel = 45;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, ubak 3
 constexpr int kGeoPerLevel = 4;      // dz, dzc, volr, wz (each up to max(nr, nz) + 1)
 
 size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz + 1 + 7) / 8); }
@@ -147,6 +148,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
     b.L.gR = f[q++]; b.L.gZ = f[q++]; b.L.Ak = f[q++];
     for (int a = 0; a < NFAC; ++a) b.L.fac[a] = f[q++];
     for (int a = 0; a < NDIA; ++a) b.L.dia[a] = f[q++];
+    for (int a = 0; a < 3; ++a) b.ubak[a] = f[q++];
     b.L.nr = b.nr; b.L.nz = b.nz; b.L.P = b.P;
     if (b.geo) {
       b.L.dz = b.geo;
@@ -955,6 +957,37 @@ int mg_solve_steady(mg_state *s, double tol, mg_stats *st) {
     CK(launch_prolong_state(c.L, c.sv, f.L, f.sv, s->stream));
     CK(launch_dirichlet(f.L, f.sv, s->prm.V_cathode, s->prm.V_anode, s->stream));
     rc = march(s, 0, s->prm.dt_max, tol);
+  }
+  if (st) *st = s->stats;
+  return rc;
+}
+
+int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const double *V, int where, double tol,
+                          mg_stats *st, int *used_fallback) {
+  if (!s || !ne || !np || !V || !(tol > 0.0)) return MG_EINVAL;
+  int rc = check_where(s, where);
+  if (rc) return rc;
+  if (used_fallback) *used_fallback = 0;
+  LevelBuf &b = s->lv[0];
+  for (int q = 0; q < 3; ++q)
+    CK(cudaMemcpyAsync(b.ubak[q], b.sv.u[q], b.nodes * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  const double *src[3] = {ne, np, V};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_in(s, b, b.sv.u[q], src[q], where, 0, b.nz))) return rc;
+  CK(launch_dirichlet(b.L, b.sv, s->prm.V_cathode, s->prm.V_anode, s->stream));
+  // march from the guess with the long step; a march that needs more than kGuessSteps steps or
+  // fails counts as divergence, and the continuation from the saved state takes over
+  constexpr int kGuessSteps = 60;
+  const int saved = s->prm.max_steps;
+  s->prm.max_steps = std::min(saved, kGuessSteps);
+  rc = march(s, 0, s->prm.dt_max, tol);
+  s->prm.max_steps = saved;
+  if (rc == MG_ECUDA) return rc;
+  if (rc != MG_OK) {
+    for (int q = 0; q < 3; ++q)
+      CK(cudaMemcpyAsync(b.sv.u[q], b.ubak[q], b.nodes * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    if (used_fallback) *used_fallback = 1;
+    rc = mg_solve_steady(s, tol, nullptr);
   }
   if (st) *st = s->stats;
   return rc;

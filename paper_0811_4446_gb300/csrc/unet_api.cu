@@ -1,0 +1,364 @@
+// Host side of include/unet.h: the learned-initial-guess network (a U-Net on the node grid)
+// on BF16 tensor-core convolution kernels (unet_kernels.cu).  The network maps per-node problem
+// features (cathode voltage, pressure factor, source map, r, z) to a guess of the steady state
+// (log n_e, log n_p, V) that replaces the coarse-grid part of the continuation of Sec. 2 of
+// arXiv:0811.4446; the paper itself has no learned component.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/mg.h"
+#include "../../include/unet.h"
+#include "unet_impl.cuh"
+
+using namespace unk;
+
+namespace {
+
+struct LayerDef {
+  int ks, stride, ci, co, relu;
+};
+// e0a e0b e1a e1b e2a e2b e3a e3b d2 d1 d0 head (same order as the parameter vector)
+constexpr int NL = 12;
+constexpr LayerDef kL[NL] = {{3, 1, 8, 32, 1},   {3, 1, 32, 32, 1},   {3, 2, 32, 64, 1},  {3, 1, 64, 64, 1},
+                             {3, 2, 64, 96, 1},  {3, 1, 96, 96, 1},   {3, 2, 96, 128, 1}, {3, 1, 128, 128, 1},
+                             {3, 1, 224, 64, 1}, {3, 1, 128, 32, 1}, {3, 1, 64, 32, 1},  {1, 1, 32, 3, 0}};
+enum { E0A, E0B, E1A, E1B, E2A, E2B, E3A, E3B, D2, D1, D0, HEAD };
+
+int pad8(int c) { return (c + 7) & ~7; }
+
+struct Act {
+  __nv_bfloat16 *a = nullptr;  // activation, NHWC bf16
+  float *g = nullptr;          // gradient, NHWC FP32
+  int H = 0, W = 0, C = 0;
+  size_t elems(int B) const { return (size_t)B * H * W * C; }
+};
+
+}  // namespace
+
+struct mg_unet {
+  int Bmax = 0, H = 0;
+  cudaStream_t st = nullptr;
+  size_t nparam = 0, woff[NL], boff[NL];
+  float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  __nv_bfloat16 *wf[NL], *wd[NL];
+  float *dwpad = nullptr;
+  Act x, e0a, e0b, e1a, e1b, e2a, e2b, e3a, e3b, u3, d2, u2, d1, u1, d0;
+  float *out = nullptr, *dout = nullptr, *tgt = nullptr, *xin = nullptr;
+  __nv_bfloat16 *dpre = nullptr;
+  double *loss_d = nullptr, *loss_h = nullptr;
+  int step = 0;
+  void *block = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(mg_unet *n, int code, const char *fmt, ...) {
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (n) n->err = buf;
+  return code;
+}
+
+#define UK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(n, MG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t param_count() {
+  size_t p = 0;
+  for (const auto &l : kL) p += (size_t)l.ks * l.ks * l.ci * l.co + l.co;
+  return p;
+}
+
+// one carve of the device block (sizes only when base == nullptr)
+struct Carve {
+  char *base;
+  size_t off;
+  template <typename T>
+  T *take(size_t count) {
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += (count * sizeof(T) + 255) & ~size_t(255);
+    return p;
+  }
+};
+
+void layout(mg_unet *n, Carve &c) {
+  const int B = n->Bmax, H0 = n->H, H1 = (H0 - 1) / 2 + 1, H2 = (H1 - 1) / 2 + 1, H3 = (H2 - 1) / 2 + 1;
+  n->nparam = param_count();
+  size_t o = 0;
+  size_t maxw = 0;
+  for (int l = 0; l < NL; ++l) {
+    n->woff[l] = o;
+    o += (size_t)kL[l].ks * kL[l].ks * kL[l].ci * kL[l].co;
+    n->boff[l] = o;
+    o += kL[l].co;
+    maxw = std::max(maxw, (size_t)kL[l].ks * kL[l].ks * kL[l].ci * pad8(kL[l].co));
+  }
+  n->master = c.take<float>(n->nparam);
+  n->grad = c.take<float>(n->nparam);
+  n->m = c.take<float>(n->nparam);
+  n->v = c.take<float>(n->nparam);
+  for (int l = 0; l < NL; ++l) {
+    const size_t e = (size_t)kL[l].ks * kL[l].ks * kL[l].ci * pad8(kL[l].co);
+    n->wf[l] = c.take<__nv_bfloat16>(e);
+    n->wd[l] = c.take<__nv_bfloat16>(e);
+  }
+  n->dwpad = c.take<float>(maxw);
+  auto act = [&](Act &t, int Hh, int C) {
+    t.H = t.W = Hh;
+    t.C = C;
+    t.a = c.take<__nv_bfloat16>(t.elems(B));
+    t.g = c.take<float>(t.elems(B));
+  };
+  act(n->x, H0, 8);
+  act(n->e0a, H0, 32); act(n->e0b, H0, 32);
+  act(n->e1a, H1, 64); act(n->e1b, H1, 64);
+  act(n->e2a, H2, 96); act(n->e2b, H2, 96);
+  act(n->e3a, H3, 128); act(n->e3b, H3, 128);
+  act(n->u3, H2, 128); act(n->d2, H2, 64);
+  act(n->u2, H1, 64); act(n->d1, H1, 32);
+  act(n->u1, H0, 32); act(n->d0, H0, 32);
+  const size_t P0 = (size_t)B * H0 * H0;
+  n->out = c.take<float>(P0 * 8);
+  n->dout = c.take<float>(P0 * 8);
+  n->tgt = c.take<float>(P0 * 3);
+  n->xin = c.take<float>(P0 * 8);
+  n->dpre = c.take<__nv_bfloat16>(P0 * 32);
+  n->loss_d = c.take<double>(1);
+}
+
+ConvArgs conv_args(const mg_unet *n, int l, int B, const Act &in1, const Act *in2) {
+  ConvArgs a;
+  std::memset(&a, 0, sizeof(a));
+  const LayerDef &L = kL[l];
+  a.Bn = B;
+  a.Hin = in1.H; a.Win = in1.W;
+  a.ks = L.ks; a.stride = L.stride; a.pad = (L.ks - 1) / 2;
+  a.Hout = (a.Hin + 2 * a.pad - a.ks) / a.stride + 1;
+  a.Wout = (a.Win + 2 * a.pad - a.ks) / a.stride + 1;
+  a.C1 = in1.C; a.C2 = in2 ? in2->C : 0;
+  a.Cout = pad8(L.co);
+  a.Pout = B * a.Hout * a.Wout;
+  a.Kf = a.ks * a.ks * (a.C1 + a.C2);
+  a.x1 = in1.a; a.x2 = in2 ? in2->a : nullptr;
+  a.bias = n->master + n->boff[l];
+  a.Nreal = L.co;
+  a.relu = L.relu;
+  return a;
+}
+
+int conv_fwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, Act *out, float *out32) {
+  ConvArgs a = conv_args(n, l, B, in1, in2);
+  a.M = a.Pout; a.N = a.Cout; a.K = a.Kf;
+  a.w = n->wf[l];
+  a.y = out ? out->a : nullptr;
+  a.y32 = out32;
+  UK(launch_conv(a, MODE_FWD, 1, n->st));
+  return MG_OK;
+}
+
+// Backward of layer l given the FP32 gradient of its output (out.g, or dout32 for the head):
+// ReLU mask, weight and bias gradients, and (if want_dx) the data gradient added into the
+// inputs' gradients.
+int conv_bwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, const Act *out, const float *dout32,
+             bool want_dx) {
+  ConvArgs a = conv_args(n, l, B, in1, in2);
+  const size_t P = (size_t)a.Pout;
+  const int cop = a.Cout;
+  UK(launch_relu_bwd(out ? out->g : dout32, out ? out->a : nullptr, n->dpre, P * cop, out ? kL[l].relu : 0, n->st));
+  UK(launch_bias_grad(n->dpre, n->grad + n->boff[l], (int)P, cop, kL[l].co, n->st));
+  // weight gradient: GEMM (kh, kw, ci) x cop over the output pixels, split over pixel ranges
+  ConvArgs w = a;
+  w.M = a.Kf; w.N = cop; w.K = a.Pout;
+  w.dy = n->dpre;
+  w.dw = n->dwpad;
+  UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), n->st));
+  const int tiles = ((w.M + 63) / 64) * ((w.N + 63) / 64);
+  const int splits = std::max(1, std::min((w.K + 255) / 256, 2 * 152 * 2 / std::max(1, tiles)));
+  UK(launch_conv(w, MODE_WGRAD, splits, n->st));
+  UK(launch_unpad_grad(n->dwpad, n->grad + n->woff[l], (size_t)a.Kf, kL[l].co, cop, n->st));
+  if (want_dx) {
+    ConvArgs d = a;
+    d.M = B * a.Hin * a.Win; d.N = a.C1 + a.C2; d.K = a.ks * a.ks * cop;
+    d.w = n->wd[l];
+    d.dy = n->dpre;
+    d.dx1 = in1.g;
+    d.dx2 = in2 ? in2->g : nullptr;
+    UK(launch_conv(d, MODE_DGRAD, 1, n->st));
+  }
+  return MG_OK;
+}
+
+int refresh_weights(mg_unet *n) {
+  for (int l = 0; l < NL; ++l)
+    UK(launch_weight_copies(n->master + n->woff[l], n->wf[l], n->wd[l], kL[l].ks, kL[l].ci, kL[l].co, pad8(kL[l].co),
+                            n->st));
+  return MG_OK;
+}
+
+int forward(mg_unet *n, int B) {
+  int rc;
+  const Act &x = n->x;
+  if ((rc = conv_fwd(n, E0A, B, x, nullptr, &n->e0a, nullptr))) return rc;
+  if ((rc = conv_fwd(n, E0B, B, n->e0a, nullptr, &n->e0b, nullptr))) return rc;
+  if ((rc = conv_fwd(n, E1A, B, n->e0b, nullptr, &n->e1a, nullptr))) return rc;
+  if ((rc = conv_fwd(n, E1B, B, n->e1a, nullptr, &n->e1b, nullptr))) return rc;
+  if ((rc = conv_fwd(n, E2A, B, n->e1b, nullptr, &n->e2a, nullptr))) return rc;
+  if ((rc = conv_fwd(n, E2B, B, n->e2a, nullptr, &n->e2b, nullptr))) return rc;
+  if ((rc = conv_fwd(n, E3A, B, n->e2b, nullptr, &n->e3a, nullptr))) return rc;
+  if ((rc = conv_fwd(n, E3B, B, n->e3a, nullptr, &n->e3b, nullptr))) return rc;
+  UK(launch_upsample(n->e3b.a, n->u3.a, B, n->e3b.H, n->e3b.W, n->e3b.C, n->st));
+  if ((rc = conv_fwd(n, D2, B, n->u3, &n->e2b, &n->d2, nullptr))) return rc;
+  UK(launch_upsample(n->d2.a, n->u2.a, B, n->d2.H, n->d2.W, n->d2.C, n->st));
+  if ((rc = conv_fwd(n, D1, B, n->u2, &n->e1b, &n->d1, nullptr))) return rc;
+  UK(launch_upsample(n->d1.a, n->u1.a, B, n->d1.H, n->d1.W, n->d1.C, n->st));
+  if ((rc = conv_fwd(n, D0, B, n->u1, &n->e0b, &n->d0, nullptr))) return rc;
+  return conv_fwd(n, HEAD, B, n->d0, nullptr, nullptr, n->out);
+}
+
+int backward(mg_unet *n, int B) {
+  int rc;
+  Act *all[] = {&n->x, &n->e0a, &n->e0b, &n->e1a, &n->e1b, &n->e2a, &n->e2b, &n->e3a,
+                &n->e3b, &n->u3, &n->d2, &n->u2, &n->d1, &n->u1, &n->d0};
+  for (Act *t : all) UK(cudaMemsetAsync(t->g, 0, t->elems(B) * sizeof(float), n->st));
+  UK(cudaMemsetAsync(n->grad, 0, n->nparam * sizeof(float), n->st));
+  if ((rc = conv_bwd(n, HEAD, B, n->d0, nullptr, nullptr, n->dout, true))) return rc;
+  if ((rc = conv_bwd(n, D0, B, n->u1, &n->e0b, &n->d0, nullptr, true))) return rc;
+  UK(launch_upsample_bwd(n->u1.g, n->d1.g, B, n->d1.H, n->d1.W, n->d1.C, n->st));
+  if ((rc = conv_bwd(n, D1, B, n->u2, &n->e1b, &n->d1, nullptr, true))) return rc;
+  UK(launch_upsample_bwd(n->u2.g, n->d2.g, B, n->d2.H, n->d2.W, n->d2.C, n->st));
+  if ((rc = conv_bwd(n, D2, B, n->u3, &n->e2b, &n->d2, nullptr, true))) return rc;
+  UK(launch_upsample_bwd(n->u3.g, n->e3b.g, B, n->e3b.H, n->e3b.W, n->e3b.C, n->st));
+  if ((rc = conv_bwd(n, E3B, B, n->e3a, nullptr, &n->e3b, nullptr, true))) return rc;
+  if ((rc = conv_bwd(n, E3A, B, n->e2b, nullptr, &n->e3a, nullptr, true))) return rc;
+  if ((rc = conv_bwd(n, E2B, B, n->e2a, nullptr, &n->e2b, nullptr, true))) return rc;
+  if ((rc = conv_bwd(n, E2A, B, n->e1b, nullptr, &n->e2a, nullptr, true))) return rc;
+  if ((rc = conv_bwd(n, E1B, B, n->e1a, nullptr, &n->e1b, nullptr, true))) return rc;
+  if ((rc = conv_bwd(n, E1A, B, n->e0b, nullptr, &n->e1a, nullptr, true))) return rc;
+  if ((rc = conv_bwd(n, E0B, B, n->e0a, nullptr, &n->e0b, nullptr, true))) return rc;
+  return conv_bwd(n, E0A, B, n->x, nullptr, &n->e0a, nullptr, false);
+}
+
+cudaMemcpyKind kin(int where) { return where == MG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kout(int where) { return where == MG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+int load_input(mg_unet *n, const float *x, int B, int where) {
+  const size_t e = (size_t)B * n->H * n->H * 8;
+  UK(cudaMemcpyAsync(n->xin, x, e * sizeof(float), kin(where), n->st));
+  UK(launch_f32_to_bf16(n->xin, n->x.a, e, n->st));
+  return MG_OK;
+}
+
+int loss_grad(mg_unet *n, const float *x, const float *t, int B, double *loss, int where) {
+  if (!n || !x || !t || B < 1 || B > n->Bmax) return MG_EINVAL;
+  int rc;
+  if ((rc = load_input(n, x, B, where)) || (rc = forward(n, B))) return rc;
+  const size_t P = (size_t)B * n->H * n->H;
+  UK(cudaMemcpyAsync(n->tgt, t, P * 3 * sizeof(float), kin(where), n->st));
+  UK(cudaMemsetAsync(n->loss_d, 0, sizeof(double), n->st));
+  UK(launch_mse(n->out, n->tgt, n->dout, P, 8, 3, n->loss_d, n->st));
+  if ((rc = backward(n, B))) return rc;
+  UK(cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, n->st));
+  UK(cudaStreamSynchronize(n->st));
+  if (loss) *loss = *n->loss_h;
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t mg_unet_param_count(void) { return (int64_t)param_count(); }
+
+int mg_unet_create(int batch_max, int n_intervals, void *stream, mg_unet **out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  if (batch_max < 1 || n_intervals < 8 || n_intervals % 8) return MG_EINVAL;
+  mg_unet *n = new (std::nothrow) mg_unet();
+  if (!n) return MG_ENOMEM;
+  n->Bmax = batch_max;
+  n->H = n_intervals + 1;
+  n->st = (cudaStream_t)stream;
+  Carve sz{nullptr, 0};
+  layout(n, sz);
+  if (cudaMalloc(&n->block, sz.off) != cudaSuccess) { delete n; return MG_ENOMEM; }
+  if (cudaMallocHost(&n->loss_h, sizeof(double)) != cudaSuccess) { cudaFree(n->block); delete n; return MG_ECUDA; }
+  Carve c{(char *)n->block, 0};
+  layout(n, c);
+  if (cudaMemsetAsync(n->block, 0, sz.off, n->st) != cudaSuccess || cudaStreamSynchronize(n->st) != cudaSuccess) {
+    mg_unet_destroy(n);
+    return MG_ECUDA;
+  }
+  *out = n;
+  return MG_OK;
+}
+
+void mg_unet_destroy(mg_unet *n) {
+  if (!n) return;
+  if (n->st) cudaStreamSynchronize(n->st);
+  if (n->block) cudaFree(n->block);
+  if (n->loss_h) cudaFreeHost(n->loss_h);
+  delete n;
+}
+
+const char *mg_unet_last_error(const mg_unet *n) { return n ? n->err.c_str() : "null network"; }
+
+int mg_unet_set_params(mg_unet *n, const float *p, int where) {
+  if (!n || !p) return MG_EINVAL;
+  UK(cudaMemcpyAsync(n->master, p, n->nparam * sizeof(float), kin(where), n->st));
+  UK(cudaMemsetAsync(n->m, 0, n->nparam * sizeof(float), n->st));
+  UK(cudaMemsetAsync(n->v, 0, n->nparam * sizeof(float), n->st));
+  n->step = 0;
+  int rc = refresh_weights(n);
+  if (rc) return rc;
+  UK(cudaStreamSynchronize(n->st));
+  return MG_OK;
+}
+
+int mg_unet_get_params(mg_unet *n, float *p, int where) {
+  if (!n || !p) return MG_EINVAL;
+  UK(cudaMemcpyAsync(p, n->master, n->nparam * sizeof(float), kout(where), n->st));
+  UK(cudaStreamSynchronize(n->st));
+  return MG_OK;
+}
+
+int mg_unet_get_grads(mg_unet *n, float *g, int where) {
+  if (!n || !g) return MG_EINVAL;
+  UK(cudaMemcpyAsync(g, n->grad, n->nparam * sizeof(float), kout(where), n->st));
+  UK(cudaStreamSynchronize(n->st));
+  return MG_OK;
+}
+
+int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where) {
+  if (!n || !x || !y || B < 1 || B > n->Bmax) return MG_EINVAL;
+  int rc;
+  if ((rc = load_input(n, x, B, where)) || (rc = forward(n, B))) return rc;
+  // out is [P][8]; copy the 3 real channels with a pitched copy
+  const size_t P = (size_t)B * n->H * n->H;
+  UK(cudaMemcpy2DAsync(y, 3 * sizeof(float), n->out, 8 * sizeof(float), 3 * sizeof(float), P, kout(where), n->st));
+  UK(cudaStreamSynchronize(n->st));
+  return MG_OK;
+}
+
+int mg_unet_loss_grad(mg_unet *n, const float *x, const float *t, int B, double *loss, int where) {
+  return loss_grad(n, x, t, B, loss, where);
+}
+
+int mg_unet_train_step(mg_unet *n, const float *x, const float *t, int B, float lr, double *loss, int where) {
+  int rc = loss_grad(n, x, t, B, loss, where);
+  if (rc) return rc;
+  n->step++;
+  UK(launch_adam(n->master, n->grad, n->m, n->v, n->nparam, lr, n->step, n->st));
+  return refresh_weights(n);
+}
+
+}  // extern "C"

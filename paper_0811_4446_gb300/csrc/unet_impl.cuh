@@ -1,0 +1,45 @@
+// Internal declarations of the learned-initial-guess network kernels (not part of the C ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+
+namespace unk {
+
+enum { MODE_FWD = 0, MODE_DGRAD = 1, MODE_WGRAD = 2 };
+
+// One implicit-GEMM convolution launch (see unet_kernels.cu for the three GEMM shapes).
+struct ConvArgs {
+  int M, N, K;                    // GEMM sizes of this launch
+  int Pout, Kf;                   // output pixels B*Hout*Wout; forward reduction ks*ks*(C1+C2)
+  int Bn, Hin, Win, Hout, Wout, ks, stride, pad;
+  int C1, C2, Cout;               // input channels (two concatenated tensors), padded output channels
+  const __nv_bfloat16 *x1, *x2;   // NHWC inputs
+  const __nv_bfloat16 *w;         // [N][K] bf16 operand (forward: wf, data gradient: wd)
+  const __nv_bfloat16 *dy;        // NHWC output gradient (bf16), channel stride Cout
+  const float *bias;               // Nreal entries (the padded output channels get no bias)
+  int Nreal, relu;
+  __nv_bfloat16 *y;               // forward output, bf16, channel stride N
+  float *y32;                     // or FP32 (network head)
+  float *dx1, *dx2;               // data gradient of the two input parts (FP32, accumulated)
+  float *dw;                      // weight gradient [M][N] (FP32, atomically accumulated)
+};
+
+cudaError_t launch_conv(const ConvArgs &a, int mode, int splits, cudaStream_t st);
+cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
+                            cudaStream_t st);
+cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st);
+cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C, cudaStream_t st);
+cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C, cudaStream_t st);
+cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,
+                       cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, int step, cudaStream_t st);
+cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, int ks, int ci, int co, int cop,
+                                 cudaStream_t st);
+cudaError_t launch_unpad_grad(const float *gp, float *g, size_t rows, int co, int cop, cudaStream_t st);
+cudaError_t launch_f32_to_bf16(const float *a, __nv_bfloat16 *b, size_t n, cudaStream_t st);
+
+}  // namespace unk

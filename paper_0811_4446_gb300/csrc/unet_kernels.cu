@@ -1,0 +1,396 @@
+// BF16 tensor-core kernels of the learned initial guess (a U-Net on the node grid).
+//
+// Convolutions are implicit GEMMs on NHWC bf16 tensors with FP32 accumulation:
+//   forward        Y[m][n]  = sum_k A[m][k] W[k][n],   m = output pixel, k = (kh, kw, c_in), n = c_out
+//   data gradient  dX[m][n] = sum_k dY'[m][k] W'[k][n], m = input pixel,  k = (kh, kw, c_out), n = c_in
+//   weight grad.   dW[m][n] = sum_k A[k][m] dY[k][n],   m = (kh, kw, c_in), k = output pixel, n = c_out
+// The A operand is gathered on the fly (zero padding, stride, and the channel concatenation of
+// two tensors); tiles are staged in shared memory and multiplied with mma.sync m16n8k16 bf16.
+// Channel counts are multiples of 8 so every 16-byte chunk lies in one (kh, kw) tap and one
+// source tensor.
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "unet_impl.cuh"
+
+namespace unk {
+
+namespace {
+
+constexpr int BK = 32;          // GEMM k per shared-memory stage
+constexpr int SK = BK + 8;      // padded row (bank-conflict-free 32-bit fragment reads)
+constexpr int NTHREADS = 128;   // 4 warps, each a 32 x 32 block of the output tile
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// 8 bf16 values of one source pixel (zero outside the image), channels [c, c + 8) of the
+// concatenation [x1 (C1 channels), x2 (C2 channels)].
+__device__ __forceinline__ uint4 load8(const ConvArgs &a, int b, int y, int x, int H, int W, int c) {
+  if (y < 0 || y >= H || x < 0 || x >= W) return make_uint4(0, 0, 0, 0);
+  const size_t pix = ((size_t)b * H + y) * W + x;
+  if (c < a.C1) return *reinterpret_cast<const uint4 *>(a.x1 + pix * a.C1 + c);
+  return *reinterpret_cast<const uint4 *>(a.x2 + pix * a.C2 + (c - a.C1));
+}
+
+// Forward gather: A[m][k0 .. k0+7], m = output pixel, k = (kh * ks + kw) * C + ci.
+__device__ __forceinline__ uint4 gather_fwd(const ConvArgs &a, int m, int k0) {
+  const int C = a.C1 + a.C2;
+  if (m >= a.Pout || k0 >= a.Kf) return make_uint4(0, 0, 0, 0);
+  const int tap = k0 / C, ci = k0 - tap * C;
+  const int kh = tap / a.ks, kw = tap - kh * a.ks;
+  const int xo = m % a.Wout, t = m / a.Wout, yo = t % a.Hout, b = t / a.Hout;
+  return load8(a, b, yo * a.stride + kh - a.pad, xo * a.stride + kw - a.pad, a.Hin, a.Win, ci);
+}
+
+// Data-gradient gather: A[m][k0 .. k0+7], m = input pixel, k = (kh * ks + kw) * Cout + co:
+// dY at the output pixel that tap (kh, kw) of m feeds (zero if none).
+__device__ __forceinline__ uint4 gather_dgrad(const ConvArgs &a, int m, int k0) {
+  if (m >= a.M || k0 >= a.K) return make_uint4(0, 0, 0, 0);
+  const int tap = k0 / a.Cout, co = k0 - tap * a.Cout;
+  const int kh = tap / a.ks, kw = tap - kh * a.ks;
+  const int xi = m % a.Win, t = m / a.Win, yi = t % a.Hin, b = t / a.Hin;
+  const int ys = yi + a.pad - kh, xs = xi + a.pad - kw;
+  if (ys < 0 || xs < 0 || ys % a.stride || xs % a.stride) return make_uint4(0, 0, 0, 0);
+  const int yo = ys / a.stride, xo = xs / a.stride;
+  if (yo >= a.Hout || xo >= a.Wout) return make_uint4(0, 0, 0, 0);
+  return *reinterpret_cast<const uint4 *>(a.dy + (((size_t)b * a.Hout + yo) * a.Wout + xo) * a.Cout + co);
+}
+
+template <int BM, int BN, int MODE>
+__global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
+  __shared__ __align__(16) __nv_bfloat16 As[BM][SK];
+  __shared__ __align__(16) __nv_bfloat16 Bs[BN][SK];
+  constexpr int WN = BN / 32;  // warps along n
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp / WN, wn = warp % WN;
+  const int g = lane >> 2, tq = lane & 3;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // k range of this block (split-k over output pixels for the weight gradient)
+  int kbeg = 0, kend = a.K;
+  if (MODE == MODE_WGRAD) {
+    const int per = ((a.K + gridDim.z - 1) / gridDim.z + BK - 1) / BK * BK;
+    kbeg = blockIdx.z * per;
+    kend = min(a.K, kbeg + per);
+  }
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    if (MODE != MODE_WGRAD) {
+      // A tile: BM rows x 4 chunks of 8 along k
+      for (int c = tid; c < BM * (BK / 8); c += NTHREADS) {
+        const int r = c / (BK / 8), kc = (c % (BK / 8)) * 8;
+        const uint4 v = MODE == MODE_FWD ? gather_fwd(a, m0 + r, k0 + kc) : gather_dgrad(a, m0 + r, k0 + kc);
+        *reinterpret_cast<uint4 *>(&As[r][kc]) = v;
+      }
+      // B tile from the [N][K] weight copy (k contiguous)
+      for (int c = tid; c < BN * (BK / 8); c += NTHREADS) {
+        const int r = c / (BK / 8), kc = (c % (BK / 8)) * 8;
+        const int n = n0 + r, k = k0 + kc;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (n < a.N && k < a.K) v = *reinterpret_cast<const uint4 *>(a.w + (size_t)n * a.K + k);
+        *reinterpret_cast<uint4 *>(&Bs[r][kc]) = v;
+      }
+    } else {
+      // weight gradient: GEMM k = output pixel.  A[m][k] = input gather for pixel k, rows
+      // m = (kh, kw, ci) -> 8 consecutive rows per 16-byte chunk, scattered into column k.
+      for (int c = tid; c < (BM / 8) * BK; c += NTHREADS) {
+        const int kk = c % BK, rc = (c / BK) * 8;
+        const int p = k0 + kk, row = m0 + rc;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (p < kend) v = gather_fwd(a, p, row);  // forward A element (pixel p, k = row)
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) As[rc + j][kk] = e[j];
+      }
+      for (int c = tid; c < (BN / 8) * BK; c += NTHREADS) {
+        const int kk = c % BK, nc = (c / BK) * 8;
+        const int p = k0 + kk, n = n0 + nc;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (p < kend && n < a.N) v = *reinterpret_cast<const uint4 *>(a.dy + (size_t)p * a.Cout + n);
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) Bs[nc + j][kk] = e[j];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int r = wm * 32 + mt * 16 + g;
+        af[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r][ks + tq * 2]);
+        af[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + tq * 2]);
+        af[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r][ks + tq * 2 + 8]);
+        af[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + tq * 2 + 8]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int n = wn * 32 + nt * 8 + g;
+        bfr[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][ks + tq * 2]);
+        bfr[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][ks + tq * 2 + 8]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+          mma_bf16(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], bfr[nt][0], bfr[nt][1]);
+    }
+    __syncthreads();
+  }
+  // epilogue
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + wm * 32 + mt * 16 + g + h * 8;
+        const int n = n0 + wn * 32 + nt * 8 + tq * 2;
+        if (m >= a.M) continue;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int nn = n + e;
+          if (nn >= a.N) continue;
+          float v = acc[mt][nt][2 * h + e];
+          if (MODE == MODE_FWD) {
+            if (nn < a.Nreal) v += a.bias[nn];
+            if (a.relu) v = fmaxf(v, 0.f);
+            if (a.y32) a.y32[(size_t)m * a.N + nn] = v;
+            else a.y[(size_t)m * a.N + nn] = __float2bfloat16(v);
+          } else if (MODE == MODE_DGRAD) {
+            // accumulate into the FP32 gradient of the concatenated input's two parts
+            if (nn < a.C1) a.dx1[(size_t)m * a.C1 + nn] += v;
+            else a.dx2[(size_t)m * a.C2 + (nn - a.C1)] += v;
+          } else {
+            atomicAdd(&a.dw[(size_t)m * a.N + nn], v);
+          }
+        }
+      }
+}
+
+template <int BM, int BN, int MODE>
+cudaError_t launch_conv_t(const ConvArgs &a, int splits, cudaStream_t st) {
+  dim3 g((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, MODE == MODE_WGRAD ? splits : 1);
+  k_conv<BM, BN, MODE><<<g, NTHREADS, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_conv(const ConvArgs &a, int mode, int splits, cudaStream_t st) {
+  const bool narrow = a.N <= 32;
+  if (mode == MODE_FWD) return narrow ? launch_conv_t<128, 32, MODE_FWD>(a, 1, st) : launch_conv_t<64, 64, MODE_FWD>(a, 1, st);
+  if (mode == MODE_DGRAD) return narrow ? launch_conv_t<128, 32, MODE_DGRAD>(a, 1, st) : launch_conv_t<64, 64, MODE_DGRAD>(a, 1, st);
+  return narrow ? launch_conv_t<128, 32, MODE_WGRAD>(a, splits, st) : launch_conv_t<64, 64, MODE_WGRAD>(a, splits, st);
+}
+
+// ------------------------------------------------------------------------------------------
+// elementwise and reduction kernels
+
+// dPre = dOut * (out > 0) for ReLU layers (relu = 0: plain copy), converted to bf16.
+__global__ void k_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float v = dout[i];
+    if (relu && !(__bfloat162float(out[i]) > 0.f)) v = 0.f;
+    dpre[i] = __float2bfloat16(v);
+  }
+}
+
+cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
+                            cudaStream_t st) {
+  k_relu_bwd<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(dout, out, dpre, n, relu);
+  return cudaGetLastError();
+}
+
+// db[c] += sum over pixels of dpre[p][c] for c < Creal (C = channel stride); blocks of 32
+// channels x 8 pixel rows, pixel-strided.
+__global__ void k_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal) {
+  const int c = blockIdx.y * 32 + threadIdx.x;
+  float s = 0.f;
+  if (c < Creal)
+    for (int p = blockIdx.x * blockDim.y + threadIdx.y; p < P; p += gridDim.x * blockDim.y)
+      s += __bfloat162float(dpre[(size_t)p * C + c]);
+  __shared__ float sh[8][33];
+  sh[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < Creal) {
+    float t = 0.f;
+    for (int r = 0; r < blockDim.y; ++r) t += sh[r][threadIdx.x];
+    atomicAdd(&db[c], t);
+  }
+}
+
+cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st) {
+  dim3 b(32, 8), g(std::min(256, (P + 7) / 8), (C + 31) / 32);
+  k_bias_grad<<<g, b, 0, st>>>(dpre, db, P, C, Creal);
+  return cudaGetLastError();
+}
+
+// Node-aligned bilinear upsampling of NHWC bf16: (h, w) -> (2h - 1, 2w - 1).
+__global__ void k_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C) {
+  const int H = 2 * h - 1, W = 2 * w - 1;
+  const size_t n = (size_t)B * H * W * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = i % C;
+    size_t t = i / C;
+    const int x = t % W;
+    t /= W;
+    const int y = t % H;
+    const int b = t / H;
+    const int y0 = y >> 1, y1 = (y + 1) >> 1, x0 = x >> 1, x1 = (x + 1) >> 1;
+    auto at = [&](int yy, int xx) { return __bfloat162float(in[(((size_t)b * h + yy) * w + xx) * C + c]); };
+    const float v = 0.25f * (at(y0, x0) + at(y0, x1) + at(y1, x0) + at(y1, x1));
+    out[i] = __float2bfloat16(v);
+  }
+}
+
+cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C, cudaStream_t st) {
+  const size_t n = (size_t)B * (2 * h - 1) * (2 * w - 1) * C;
+  k_upsample<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(in, out, B, h, w, C);
+  return cudaGetLastError();
+}
+
+// Transpose of the upsampling on FP32 gradients: dc[Y][X] += sum of fine gradients weighted
+// by the interpolation weights of node (Y, X).
+__global__ void k_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C) {
+  const int H = 2 * h - 1, W = 2 * w - 1;
+  const size_t n = (size_t)B * h * w * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = i % C;
+    size_t t = i / C;
+    const int X = t % w;
+    t /= w;
+    const int Y = t % h;
+    const int b = t / h;
+    float s = 0.f;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = 2 * Y + dy;
+      if (y < 0 || y >= H) continue;
+      const float wy = dy == 0 ? 1.f : 0.5f;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = 2 * X + dx;
+        if (x < 0 || x >= W) continue;
+        const float wx = dx == 0 ? 1.f : 0.5f;
+        s += wy * wx * dfine[(((size_t)b * H + y) * W + x) * C + c];
+      }
+    }
+    dcoarse[i] += s;
+  }
+}
+
+cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C, cudaStream_t st) {
+  const size_t n = (size_t)B * h * w * C;
+  k_upsample_bwd<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(dfine, dcoarse, B, h, w, C);
+  return cudaGetLastError();
+}
+
+// Mean-squared-error loss on the first `nc` of `ld` output channels; writes dL/dy and
+// accumulates the loss sum (double) into loss[0].
+__global__ void k_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double scale, double *loss) {
+  double s = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+    for (int c = 0; c < ld; ++c) {
+      float g = 0.f;
+      if (c < nc) {
+        const float d = y[p * ld + c] - t[p * nc + c];
+        s += (double)d * d;
+        g = (float)(2.0 * scale) * d;
+      }
+      dy[p * ld + c] = g;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * scale);
+}
+
+cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,
+                       cudaStream_t st) {
+  const double scale = 1.0 / ((double)P * nc);
+  k_mse<<<(unsigned)std::min<size_t>((P + 255) / 256, 2048), 256, 0, st>>>(y, t, dy, P, ld, nc, scale, loss);
+  return cudaGetLastError();
+}
+
+// Adam (Kingma & Ba) on FP32 master parameters.
+__global__ void k_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, int step, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  k_adam<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2);
+  return cudaGetLastError();
+}
+
+// bf16 operand copies of one layer's FP32 master weights w[kh][kw][ci][co]:
+//   wf[co][(kh, kw, ci)]  (forward B operand, k contiguous)
+//   wd[ci][(kh, kw, co)]  (data-gradient B operand)
+// co is padded to cop (zero rows) so that every operand dimension is a multiple of 8.
+__global__ void k_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, int ks, int ci, int co, int cop) {
+  const int taps = ks * ks;
+  const size_t n = (size_t)taps * ci * cop;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int o = i % cop;
+    size_t t = i / cop;
+    const int c = t % ci;
+    const int tap = t / ci;
+    const float v = o < co ? w[((size_t)tap * ci + c) * co + o] : 0.f;
+    const __nv_bfloat16 b = __float2bfloat16(v);
+    wf[(size_t)o * taps * ci + (size_t)tap * ci + c] = b;
+    wd[(size_t)c * taps * cop + (size_t)tap * cop + o] = b;
+  }
+}
+
+cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, int ks, int ci, int co, int cop,
+                                 cudaStream_t st) {
+  const size_t n = (size_t)ks * ks * ci * cop;
+  k_weight_copies<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(w, wf, wd, ks, ci, co, cop);
+  return cudaGetLastError();
+}
+
+// Weight gradient in the padded [(kh, kw, ci)][cop] layout -> master layout [(kh, kw, ci)][co].
+__global__ void k_unpad_grad(const float *gp, float *g, size_t rows, int co, int cop) {
+  const size_t n = rows * co;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    g[i] = gp[(i / co) * cop + i % co];
+}
+
+cudaError_t launch_unpad_grad(const float *gp, float *g, size_t rows, int co, int cop, cudaStream_t st) {
+  const size_t n = rows * co;
+  k_unpad_grad<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(gp, g, rows, co, cop);
+  return cudaGetLastError();
+}
+
+__global__ void k_f32_to_bf16(const float *a, __nv_bfloat16 *b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16(a[i]);
+}
+
+cudaError_t launch_f32_to_bf16(const float *a, __nv_bfloat16 *b, size_t n, cudaStream_t st) {
+  k_f32_to_bf16<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace unk

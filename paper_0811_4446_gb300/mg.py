@@ -82,6 +82,7 @@ SIGNATURES = {
     "mg_probe_fp64_gflops": (ctypes.c_double, [_vp]),
     "mg_solve_steady_batch": (_i, [ctypes.POINTER(_vp), _i, _d, _i, _vp, _vp]),
     "mg_autotune": (_i, [_vp, _vp]),
+    "mg_solve_steady_guess": (_i, [_vp, _vp, _vp, _vp, _i, _d, ctypes.POINTER(mg_stats), ctypes.POINTER(_i)]),
     "mg_num_levels": (_i, [_vp]),
     "mg_residual_noalloc": (_i, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_params), _vp, _vp, _vp, _vp, _vp, _vp,
                                  _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp]),
@@ -271,6 +272,16 @@ class Solver:
         rc = self.lib.mg_solve_steady(self.h, float(tol), ctypes.byref(st))
         self._check(rc, allow=(MG_EREJECT,))
         return rc, st.as_dict()
+
+    def solve_steady_guess(self, ne, np_, V, tol: float):
+        """Steady solve from a full-grid guess; returns (rc, stats, used_fallback)."""
+        st = mg_stats()
+        fb = ctypes.c_int(0)
+        w = _where(ne, np_, V)
+        rc = self.lib.mg_solve_steady_guess(self.h, _ptr(ne)[0], _ptr(np_)[0], _ptr(V)[0], w, float(tol),
+                                            ctypes.byref(st), ctypes.byref(fb))
+        self._check(rc, allow=(MG_EREJECT,))
+        return rc, st.as_dict(), bool(fb.value)
 
     def stats(self):
         st = mg_stats()

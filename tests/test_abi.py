@@ -35,8 +35,15 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_binding_signatures_cover_header():
-    from paper_0811_4446_gb300 import mg
-    assert _declared() == set(mg.SIGNATURES)
+    from paper_0811_4446_gb300 import mg, unet
+    assert _declared() == set(mg.SIGNATURES) | set(unet.SIGNATURES)
+
+
+def test_unet_param_count_matches_oracle(lib):
+    from oracle import unet as ou
+    from paper_0811_4446_gb300 import unet
+    assert unet.param_count() == ou.param_count()
+    assert unet.init_params(0).size == ou.param_count()
 
 
 def test_workspace_sizing_without_gpu(lib):

@@ -1,0 +1,182 @@
+"""GPU tests of the learned initial guess: the BF16 tensor-core U-Net kernels against the FP64
+CPU oracle (oracle/unet.py), training on the device, and the guess-then-refine steady solve.
+
+Tolerances: BF16 activations and weights (8-bit mantissa) through 12 layers -> the forward
+output agrees with the FP64 oracle (on BF16-rounded weights and inputs) to 3 % relative L2;
+each layer's weight gradient to 10 % relative L2 with cosine similarity >= 0.995.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import discretization as disc
+from oracle import unet as ou
+from oracle.grid import Grid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def un():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0811_4446_gb300 import build, unet
+    build.build()
+    return unet
+
+
+def _bf16(a: np.ndarray) -> np.ndarray:
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _setup(un, seed=1, B=2, n=32):
+    rng = np.random.default_rng(seed)
+    p = un.init_params(seed)
+    # non-zero biases so that their gradients and the bias path are exercised
+    off = 0
+    for name, k, _, ci, co, _ in ou.LAYERS:
+        off += k * k * ci * co
+        p[off:off + co] = 0.05 * rng.standard_normal(co)
+        off += co
+    x = np.zeros((B, n + 1, n + 1, 8), np.float32)
+    x[..., :5] = rng.standard_normal((B, n + 1, n + 1, 5)).astype(np.float32)
+    t = rng.standard_normal((B, n + 1, n + 1, 3)).astype(np.float32) * 0.5
+    return p, x, t
+
+
+def _oracle_params(p):
+    v = torch.from_numpy(_bf16(p))
+    d = ou.unflatten(v)
+    for name, *_ in ou.LAYERS:      # biases stay FP32 on the GPU (added in the FP32 epilogue)
+        pass
+    return d
+
+
+def test_forward_matches_oracle(un):
+    p, x, _ = _setup(un)
+    net = un.UNet(2, 32)
+    net.set_params(p)
+    y = net.forward(x)
+    po = ou.unflatten(torch.from_numpy(p.astype(np.float64)))
+    for name, *_ in ou.LAYERS:
+        po[name + ".w"] = torch.from_numpy(_bf16(po[name + ".w"].numpy()))
+    xo = torch.from_numpy(_bf16(x)).permute(0, 3, 1, 2)
+    yo = ou.forward(po, xo).permute(0, 2, 3, 1).numpy()
+    rel = np.linalg.norm(y - yo) / np.linalg.norm(yo)
+    assert rel <= 3e-2, rel
+
+
+def test_gradients_match_oracle(un):
+    p, x, t = _setup(un, seed=2)
+    net = un.UNet(2, 32)
+    net.set_params(p)
+    loss, g = net.loss_grad(x, t)
+    po = ou.unflatten(torch.from_numpy(p.astype(np.float64)))
+    for name, *_ in ou.LAYERS:
+        po[name + ".w"] = torch.from_numpy(_bf16(po[name + ".w"].numpy()))
+    xo = torch.from_numpy(_bf16(x)).permute(0, 3, 1, 2)
+    to = torch.from_numpy(t.astype(np.float64)).permute(0, 3, 1, 2)
+    lo, go = ou.loss_and_grads(po, xo, to)
+    assert abs(loss - lo) <= 3e-2 * lo, (loss, lo)
+    gg = ou.unflatten(torch.from_numpy(g.astype(np.float64)))
+    for name, *_ in ou.LAYERS:
+        for part in (".w", ".b"):
+            a, b = gg[name + part].numpy().ravel(), go[name + part].numpy().ravel()
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+            assert rel <= 0.1 and cos >= 0.995, (name + part, rel, cos)
+
+
+def test_training_reduces_loss(un):
+    p, x, _ = _setup(un, seed=3, B=4)
+    # a smooth target that depends on the inputs
+    t = np.stack([np.tanh(x[..., 0] + 0.5 * x[..., 3]), 0.5 * x[..., 1] * x[..., 4], np.sin(x[..., 2])], -1)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    net = un.UNet(4, 32)
+    net.set_params(p)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    first = net.train_step(xd, td, 1e-3)
+    for _ in range(80):
+        last = net.train_step(xd, td, 1e-3)
+    assert last < 0.2 * first, (first, last)
+
+
+def test_guess_then_refine_small_grid(un):
+    """33 x 33 family: train on solver-generated steady states, then solve held-out instances
+    from the network's guess; the result is the same discrete steady state as the continuation."""
+    from paper_0811_4446_gb300 import mg
+    X, T = un.generate(list(range(1000, 1032)), n=32, workers=8)
+    assert X.shape[0] >= 30
+    net = un.UNet(8, 32)
+    net.set_params(un.init_params(0))
+    hist = un.train(net, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), epochs=40, batch=8, lr=2e-3)
+    assert hist[-1] < 0.25 * hist[0], hist
+    for seed in (5000, 5001):
+        d = un.guess_discharge(seed, 32)
+        y = net.forward(un.features(d)[None])[0]
+        guess = un.state_from_output(y, d.V_cathode)
+        s = mg.from_discharge(d, precision=mg.MG_MIXED)
+        rc, st, fb = s.solve_steady_guess(*guess, 1e-8)
+        assert rc == mg.MG_OK
+        ug = np.stack(s.get_state())
+        ref = mg.from_discharge(d, precision=mg.MG_MIXED)
+        assert ref.solve_steady(1e-8)[0] == mg.MG_OK
+        ur = np.stack(ref.get_state())
+        for q in range(3):
+            assert np.abs(ug[q] - ur[q]).max() <= 1e-6 * np.abs(ur[q]).max(), q
+        g = Grid(d.nr, d.nz, d.R, d.z)
+        phys = disc.Physics(V_cathode=d.V_cathode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p,
+                            pressure_factor=d.pressure_factor)
+        F, Tm = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
+        assert disc.rho(F, Tm).max() <= 1.05e-8
+
+
+def test_bad_guess_falls_back_to_continuation(un):
+    from paper_0811_4446_gb300 import mg
+    d = un.guess_discharge(7000, 32)
+    s = mg.from_discharge(d, precision=mg.MG_MIXED)
+    shape = d.shape
+    # a nonsensical guess (huge densities, reversed field): the march from it must not be trusted
+    bad = [np.full(shape, 1e22), np.full(shape, 1e22), np.full(shape, 500.0)]
+    rc, st, fb = s.solve_steady_guess(*bad, 1e-8)
+    assert rc == mg.MG_OK
+    ref = mg.from_discharge(d, precision=mg.MG_MIXED)
+    assert ref.solve_steady(1e-8)[0] == mg.MG_OK
+    a, b = np.stack(s.get_state()), np.stack(ref.get_state())
+    for q in range(3):
+        assert np.abs(a[q] - b[q]).max() <= 1e-6 * np.abs(b[q]).max(), (q, fb)
+
+
+def test_trained_network_beats_continuation_at_257(un):
+    """With the committed weights (trained by paper_0811_4446_gb300.train_guess on the device):
+    held-out 257 x 257 instances reach rho <= 1e-8 faster from the guess than by the plain
+    129 -> 257 continuation."""
+    from paper_0811_4446_gb300 import mg
+    w = un.load_weights()
+    if w is None:
+        pytest.skip("no trained weights committed")
+    net = un.UNet(1, 256)
+    net.set_params(w)
+    t_guess, t_cont, fallbacks = [], [], 0
+    for seed in range(9000, 9006):
+        d = un.guess_discharge(seed, 256)
+        s = mg.from_discharge(d, precision=mg.MG_MIXED)
+        c = mg.from_discharge(d, precision=mg.MG_MIXED)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y = net.forward(un.features(d)[None])[0]
+        rc, st, fb = s.solve_steady_guess(*un.state_from_output(y, d.V_cathode), 1e-8)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        assert rc == mg.MG_OK
+        rc2, _ = c.solve_steady(1e-8)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        assert rc2 == mg.MG_OK
+        t_guess.append(t1 - t0)
+        t_cont.append(t2 - t1)
+        fallbacks += int(fb)
+    assert np.median(t_guess) < np.median(t_cont), (t_guess, t_cont, fallbacks)
