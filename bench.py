@@ -290,17 +290,18 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (red-black smoother half sweep on the finest level)
     peaks = _peaks()
     nodes = (d.nr + 1) * (d.nz - 1)            # unknown nodes of the 257 x 257 level
-    # per half-sweep launch: all face coefficients (12 x 8 B) and Poisson conductances (2 x 8 B) once,
-    # and for the updated colour 7 block factors, f and du (8 B each), the other colour's du read
-    bytes_per_launch = 176 * nodes
-    flops_per_launch = 52 * (nodes / 2)         # per updated node: 20 FMA off-diagonal + block solve
+    # per fused red-black sweep launch (both colours): the 12 face coefficients, 2 Poisson
+    # conductances, 7 block factors and 3 right-hand sides of every node once (8 B each), the old
+    # black corrections read (3 x 8 B per black node) and both colours' corrections written
+    bytes_per_launch = 228 * nodes
+    flops_per_launch = 52 * nodes               # per node: 20 FMA off-diagonal + block solve
     avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
     fp64_peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12 * 1000.0   # GFLOP/s: SMs x DFMA/clk x 2 x GHz
     fp64_probe = mg.probe_fp64_gflops()
     achieved_flops = flops_per_launch / avg_s / 1e9
     achieved_bw = bytes_per_launch / avg_s / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "kernel": "k_smooth (FP64, 257x257 level)", "achieved": achieved_flops,
+    roofline = {"bound": "alu", "kernel": "k_sweep<double> (fused red-black sweep, 257x257 level)", "achieved": achieved_flops,
                 "peak": fp64_peak_nominal, "unit": "GFLOP/s", "frac": achieved_flops / fp64_peak_nominal,
                 "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "peak_probe_gflops": fp64_probe, "traffic": None,
@@ -385,11 +386,11 @@ def measure_forms(args, dev, peaks):
     s.linear_solve(1e-9, f, 0.0, 10)
     n, ms = s.profile_end()
     avg = ms / n / 1000.0
-    byt = 88 * nodes       # FP32: 12 coefficients + 2 conductances per node, 7 factors + f + du for the colour
+    byt = 114 * nodes      # FP32 fused sweep: the FP64 per-node bytes halved
     hbm = peaks.get("hbm_gbs", 6800.0)
     out["mixed_vcycle_1025"] = {"vcycle_us": vc * 1e6, "mpts_per_s": (d.nr + 1) * (d.nz + 1) / vc / 1e6,
                                 "residual_drop_30_cycles": float(hist[-1]),
-                                "roofline": {"bound": "hbm", "kernel": "k_smooth<float> (1025x1025 level)",
+                                "roofline": {"bound": "hbm", "kernel": "k_sweep<float> (fused red-black sweep, 1025x1025 level)",
                                              "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
                                              "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6,
                                              "algorithmic_bytes_per_launch": byt, "traffic": None}}

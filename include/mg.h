@@ -91,6 +91,12 @@ typedef struct mg_params {
   double n0;              /* density unit of the FP32 inner cycle (eq. 12's n0), m^-3 */
   int32_t use_graphs;     /* 1: each linear solve is one CUDA-graph launch whose V-cycle loop
                              and stopping test run on the device; 0: host-driven loop */
+  int32_t fused_sweep;    /* 1: one launch per red-black sweep (tiled, both colours);
+                             0: one launch per colour.  Same result bit for bit. */
+  double guess_dt_max;    /* cap of the Delta-t ramp when marching from a learned guess: the
+                             ramp starts at dt_max and grows by dt_growth up to this value */
+  int32_t guess_level;    /* 0: march the full grid from the guess; 1: the guess (injected)
+                             starts the coarse-grid march of the continuation instead */
 } mg_params;
 
 /* Per-call statistics. */
@@ -114,7 +120,7 @@ typedef struct mg_state mg_state;
  * V_cathode = -200, V_anode = 0, nu1 = nu2 = 2, coarsest = 4, eta = 1e-3,
  * max_newton = 10, max_vcycles = 60, max_steps = 400, dt1 = 1e-9,
  * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14,
- * use_graphs = 1.
+ * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 0.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on
@@ -186,9 +192,10 @@ int mg_solve_steady(mg_state *s, double tol, mg_stats *stats);
 
 /* Steady state from an initial guess of the full-grid state (the learned-guess form, see
  * unet.h): the current state is saved, (ne, np, V) become the state (electrode rows set to
- * their Dirichlet values) and the march starts with the long step dt_max.  If that march
- * fails or needs more than 60 steps, the saved state is restored and mg_solve_steady's
- * continuation runs instead (*used_fallback = 1). */
+ * their Dirichlet values) and the march starts with the long step dt_max, growing by
+ * dt_growth up to guess_dt_max (the paper's growing ramp, Sec. 2).  If that march fails or
+ * needs more than 60 steps, the saved state is restored and mg_solve_steady's continuation
+ * runs instead (*used_fallback = 1). */
 int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const double *V, int where, double tol,
                           mg_stats *stats, int *used_fallback);
 
@@ -201,10 +208,11 @@ int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const
  * states must live on the calling thread's current device. */
 int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, double *ms_out, int *rc_out);
 
-/* Autotuner of the smoother's launch shape: times the red-black half sweep of every level
- * (FP64 and, in the mixed form, FP32) over a fixed set of thread-block shapes and keeps the
- * fastest per level.  Leaves the solution state untouched.  shapes_out (may be NULL) receives
- * 4 ints per level: FP64 (bx, by), FP32 (bx, by). */
+/* Autotuner of the smoother's launch shapes: times the red-black half sweep and the fused
+ * sweep of every level (FP64 and, in the mixed form, FP32) over fixed sets of thread-block /
+ * tile shapes and keeps the fastest per level.  Leaves the solution state untouched (only
+ * the correction work buffers are written).  shapes_out (may be NULL) receives 4 ints per
+ * level: FP64 half-sweep (bx, by), FP32 half-sweep (bx, by). */
 int mg_autotune(mg_state *s, int32_t *shapes_out);
 int mg_num_levels(const mg_state *s);
 

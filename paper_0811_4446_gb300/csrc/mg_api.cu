@@ -38,8 +38,9 @@ struct LevelBuf {
   double *geo;           // device geometry block
   float *geo32;
   double *ubak[3];       // copy of the state (fallback of the learned-guess solve)
-  int sbx = 32, sby = 2;         // smoother launch shape, FP64 view (autotuned)
-  int sbx32 = 32, sby32 = 2;     // smoother launch shape, FP32 view (autotuned)
+  int sbx = 32, sby = 2;         // half-sweep launch shape, FP64 view (autotuned)
+  int sbx32 = 32, sby32 = 2;     // half-sweep launch shape, FP32 view (autotuned)
+  int sw = 1, sw32 = 1;          // fused-sweep tile shape index, FP64 / FP32 (autotuned)
 };
 
 }  // namespace
@@ -120,12 +121,12 @@ struct Carver {
   }
 };
 
-constexpr int kFieldsPerLevel = 45;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, ubak 3
+constexpr int kFieldsPerLevel = 48;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, ubak 3, du2 3
 constexpr int kGeoPerLevel = 4;      // dz, dzc, volr, wz (each up to max(nr, nz) + 1)
 
 size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz + 1 + 7) / 8); }
 
-constexpr int kFields32PerLevel = 34;  // cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3
+constexpr int kFields32PerLevel = 37;  // cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, du2 3
 
 void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int table_rows, bool mixed) {
   for (int l = 0; l < nlev; ++l) {
@@ -149,6 +150,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
     for (int a = 0; a < NFAC; ++a) b.L.fac[a] = f[q++];
     for (int a = 0; a < NDIA; ++a) b.L.dia[a] = f[q++];
     for (int a = 0; a < 3; ++a) b.ubak[a] = f[q++];
+    for (int a = 0; a < 3; ++a) b.L.du2[a] = f[q++];
     b.L.nr = b.nr; b.L.nz = b.nz; b.L.P = b.P;
     if (b.geo) {
       b.L.dz = b.geo;
@@ -171,6 +173,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
       b.M.gR = g[w++]; b.M.gZ = g[w++]; b.M.Ak = g[w++];
       for (int a = 0; a < NFAC; ++a) b.M.fac[a] = g[w++];
       for (int a = 0; a < NDIA; ++a) b.M.dia[a] = g[w++];
+      for (int a = 0; a < 3; ++a) b.M.du2[a] = g[w++];
       b.M.nr = b.nr; b.M.nz = b.nz; b.M.P = b.P;
       if (b.geo32) {
         b.M.dz = b.geo32;
@@ -305,6 +308,38 @@ int smooth(mg_state *s, int l, int color, cudaStream_t st) {
   return MG_OK;
 }
 
+template <typename T> int sweep_shape(const LevelBuf &b);
+template <> int sweep_shape<double>(const LevelBuf &b) { return b.sw; }
+template <> int sweep_shape<float>(const LevelBuf &b) { return b.sw32; }
+
+// nu red-black sweeps on level l: fused sweeps alternate between du and du2 (the last one
+// lands in du; odd counts end with a copy), or pairs of half-sweep launches.
+template <typename T>
+int smooth_sweeps(mg_state *s, int l, int nu, cudaStream_t st) {
+  const LevelT<T> &b = view<T>(s->lv[l]);
+  int rc;
+  if (!s->prm.fused_sweep) {
+    for (int k = 0; k < nu; ++k)
+      for (int col = 0; col < 2; ++col)
+        if ((rc = smooth<T>(s, l, col, st))) return rc;
+    return MG_OK;
+  }
+  SweepIO<T> io;
+  for (int k = 0; k < nu; ++k) {
+    const bool fwd = (k % 2 == 0);
+    for (int q = 0; q < 3; ++q) {
+      io.in[q] = fwd ? b.du[q] : b.du2[q];
+      io.out[q] = fwd ? b.du2[q] : b.du[q];
+    }
+    ProfScope ps(s, MG_PROF_SMOOTH, l);
+    CK(launch_sweep<T>(b, io, sweep_shape<T>(s->lv[l]), st));
+  }
+  if (nu % 2)
+    for (int q = 0; q < 3; ++q)
+      CK(cudaMemcpyAsync(b.du[q], b.du2[q], s->lv[l].nodes * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  return MG_OK;
+}
+
 template <typename T>
 int vcycle(mg_state *s, int l, cudaStream_t st) {
   const LevelT<T> &b = view<T>(s->lv[l]);
@@ -314,9 +349,7 @@ int vcycle(mg_state *s, int l, cudaStream_t st) {
   }
   const LevelT<T> &c = view<T>(s->lv[l + 1]);
   int rc;
-  for (int k = 0; k < s->prm.nu1; ++k)
-    for (int col = 0; col < 2; ++col)
-      if ((rc = smooth<T>(s, l, col, st))) return rc;
+  if ((rc = smooth_sweeps<T>(s, l, s->prm.nu1, st))) return rc;
   {
     ProfScope ps(s, MG_PROF_LINRES, l);
     CK(launch_linres<T>(b, b.du, b.f, const_cast<T **>(b.r), nullptr, nullptr, nullptr, st));
@@ -330,10 +363,7 @@ int vcycle(mg_state *s, int l, cudaStream_t st) {
     ProfScope ps(s, MG_PROF_PROLONG, l);
     CK(launch_prolong_add<T>(c, b, st));
   }
-  for (int k = 0; k < s->prm.nu2; ++k)
-    for (int col = 0; col < 2; ++col)
-      if ((rc = smooth<T>(s, l, col, st))) return rc;
-  return MG_OK;
+  return smooth_sweeps<T>(s, l, s->prm.nu2, st);
 }
 
 // Per-field sums of squares of the linear residual f - J du on level l0 into dout[0..2]; in the
@@ -614,6 +644,21 @@ int time_shape(mg_state *s, int l, int bx, int by, int reps, cudaEvent_t e0, cud
   *ms /= reps;
   return MG_OK;
 }
+
+template <typename T>
+int time_sweep(mg_state *s, int l, int shape, int reps, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+  const LevelT<T> &L = view<T>(s->lv[l]);
+  SweepIO<T> io;
+  for (int q = 0; q < 3; ++q) { io.in[q] = L.du[q]; io.out[q] = L.du2[q]; }
+  for (int r = 0; r < 2; ++r) CK(launch_sweep<T>(L, io, shape, s->stream));
+  CK(cudaEventRecord(e0, s->stream));
+  for (int r = 0; r < reps; ++r) CK(launch_sweep<T>(L, io, shape, s->stream));
+  CK(cudaEventRecord(e1, s->stream));
+  CK(cudaEventSynchronize(e1));
+  CK(cudaEventElapsedTime(ms, e0, e1));
+  *ms /= reps;
+  return MG_OK;
+}
 }  // namespace
 
 // ================================================================ C ABI
@@ -632,6 +677,9 @@ void mg_params_default(mg_params *p) {
   p->dt1 = 1e-9; p->dt_growth = 5.0; p->dt_max = 1e-6;
   p->n0 = 1e14;
   p->use_graphs = 1;
+  p->fused_sweep = 1;
+  p->guess_dt_max = 1e-3;
+  p->guess_level = 0;
 }
 
 static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
@@ -979,9 +1027,25 @@ int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const
   // fails counts as divergence, and the continuation from the saved state takes over
   constexpr int kGuessSteps = 60;
   const int saved = s->prm.max_steps;
+  const double saved_dt = s->prm.dt_max;
   s->prm.max_steps = std::min(saved, kGuessSteps);
-  rc = march(s, 0, s->prm.dt_max, tol);
+  s->prm.dt_max = std::max(saved_dt, s->prm.guess_dt_max);
+  if (s->prm.guess_level == 1 && s->nlev >= 2) {
+    // the guess replaces the initial state of the coarse march (long step from the start),
+    // then the continuation proceeds as usual
+    LevelBuf &c = s->lv[1];
+    CK(launch_inject(b.L, b.sv, c.L, c.sv, false, true, s->stream));
+    rc = march(s, 1, saved_dt, tol);
+    if (rc == MG_OK) {
+      CK(launch_prolong_state(c.L, c.sv, b.L, b.sv, s->stream));
+      CK(launch_dirichlet(b.L, b.sv, s->prm.V_cathode, s->prm.V_anode, s->stream));
+      rc = march(s, 0, saved_dt, tol);
+    }
+  } else {
+    rc = march(s, 0, saved_dt, tol);
+  }
   s->prm.max_steps = saved;
+  s->prm.dt_max = saved_dt;
   if (rc == MG_ECUDA) return rc;
   if (rc != MG_OK) {
     for (int q = 0; q < 3; ++q)
@@ -1042,6 +1106,7 @@ double mg_probe_fp64_gflops(void *stream) { return probe_fp64_gflops((cudaStream
 int mg_autotune(mg_state *s, int32_t *shapes_out) {
   if (!s) return MG_EINVAL;
   static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+  // the tuning launches write only the correction buffers du and du2 of each level
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1061,6 +1126,15 @@ int mg_autotune(mg_state *s, int32_t *shapes_out) {
       LevelBuf &b = s->lv[l];
       if (prec == 0) { b.sbx = cand[bi][0]; b.sby = cand[bi][1]; }
       else { b.sbx32 = cand[bi][0]; b.sby32 = cand[bi][1]; }
+      // fused-sweep tile shape
+      float bestf = 1e30f;
+      int bf = 1;
+      for (int c = 0; c < kSweepShapes && rc == MG_OK; ++c) {
+        float ms = 0.f;
+        rc = prec == 0 ? time_sweep<double>(s, l, c, 10, e0, e1, &ms) : time_sweep<float>(s, l, c, 10, e0, e1, &ms);
+        if (ms < bestf) { bestf = ms; bf = c; }
+      }
+      if (prec == 0) b.sw = bf; else b.sw32 = bf;
       if (shapes_out) {
         shapes_out[4 * l + 2 * prec] = cand[bi][0];
         shapes_out[4 * l + 2 * prec + 1] = cand[bi][1];

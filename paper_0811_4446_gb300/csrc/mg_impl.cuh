@@ -45,8 +45,17 @@ struct LevelT {
   T *cr[NCOEF], *cz[NCOEF];  // face coefficients
   T *fac[NFAC], *dia[NDIA];  // diagonal-block factors (rebuilt with the coefficients)
   T *du[3], *f[3], *r[3];
+  T *du2[3];                 // second correction buffer (ping-pong of the fused sweep)
 };
 using Level = LevelT<double>;
+
+// Ping-pong correction buffers of one fused red-black sweep (read previous, write next).
+template <typename T>
+struct SweepIO {
+  T *in[3];
+  T *out[3];
+};
+constexpr int kSweepShapes = 6;  // tile shapes of the fused sweep: 32x2 32x4 32x8 64x2 64x4 128x2
 
 struct StateView {           // nonlinear state on one level (FP64)
   double *u[3], *uold[3];
@@ -86,6 +95,8 @@ cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport
                             double *out6, cudaStream_t st);
 template <typename T>
 cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx = 32, int by = 2);
+template <typename T>
+cudaError_t launch_sweep(const LevelT<T> &L, const SweepIO<T> &io, int shape, cudaStream_t st);
 // r = f - J v (or out = J v when f == nullptr); optional per-field norms (sum of squares) -> out3
 template <typename T>
 cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,

@@ -431,6 +431,127 @@ cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx
 template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t, int, int);
 template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t, int, int);
 
+// K3 fused: one full red-black sweep per launch.  A block owns a TX x TY tile of nodes.
+// Phase 1 updates the red nodes of the tile and of a one-node ring around it (ring nodes are
+// also updated by the neighbouring tiles, with identical inputs and arithmetic), keeping them
+// in shared memory; phase 2 updates the tile's black nodes from those red values and writes
+// both colours.  The black values of the previous sweep are read from `in`, the new ones go
+// to `out` (ping-pong buffers), so no block reads what another block writes in the same
+// launch and the result equals two half-sweep launches bit for bit.  Coefficients of a face
+// are read by its red end in phase 1 and by its black end in phase 2 (an L1/L2 hit).
+template <typename T>
+struct Triple {
+  T e, p, V;
+};
+
+template <typename T>
+__device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, size_t k, const Triple<T> &vE,
+                                                 const Triple<T> &vW, const Triple<T> &vN, const Triple<T> &vS) {
+  const int P = L.P;
+  T e = 0, p = 0, V = 0;
+  if (i < L.nr) {
+    e += L.cr[CVE][k] * vE.V - L.cr[CFE][k] * vE.e;
+    p += L.cr[CVP][k] * vE.V - L.cr[CFP][k] * vE.p;
+    V += L.gR[k] * vE.V;
+  }
+  if (i > 0) {
+    const size_t n = k - 1;
+    e += L.cr[CVE][n] * vW.V - L.cr[CGE][n] * vW.e;
+    p += L.cr[CVP][n] * vW.V - L.cr[CGP][n] * vW.p;
+    V += L.gR[n] * vW.V;
+  }
+  {
+    e += L.cz[CVE][k] * vN.V - L.cz[CFE][k] * vN.e;
+    p += L.cz[CVP][k] * vN.V - L.cz[CFP][k] * vN.p;
+    V += L.gZ[k] * vN.V;
+  }
+  {
+    const size_t n = k - P;
+    e += L.cz[CVE][n] * vS.V - L.cz[CGE][n] * vS.e;
+    p += L.cz[CVP][n] * vS.V - L.cz[CGP][n] * vS.p;
+    V += L.gZ[n] * vS.V;
+  }
+  const T re = L.f[NE][k] - e, rp = L.f[NP][k] - p, rV = L.f[NV][k] - V;
+  Triple<T> x;
+  x.V = (rV - L.fac[FQ1][k] * re - L.fac[FQ2][k] * rp) * L.fac[FIS][k];
+  x.e = (re - L.fac[FA13][k] * x.V) * L.fac[FI11][k];
+  x.p = (rp - L.fac[FA23][k] * x.V) * L.fac[FI22][k];
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ Triple<T> gload(T *const v[3], size_t k) {
+  Triple<T> t;
+  t.e = v[NE][k]; t.p = v[NP][k]; t.V = v[NV][k];
+  return t;
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
+  constexpr int EX = TX + 2, EY = TY + 2;
+  __shared__ T sr[3][EY][EX];
+  const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY;  // extended-tile origin (node coords)
+  const int nr = L.nr, nz = L.nz, P = L.P;
+  // phase 1: red nodes of the extended tile from the old black values
+  for (int q = threadIdx.x; q < EX * EY; q += TX * TY) {
+    const int li = q % EX, lj = q / EX;
+    const int i = i0 + li, j = j0 + lj;
+    T ve = 0, vp = 0, vV = 0;
+    if (i >= 0 && i <= nr && j >= 1 && j < nz && ((i + j) & 1) == 0) {
+      const size_t k = (size_t)j * P + i;
+      const Triple<T> z = {0, 0, 0};
+      const Triple<T> x = node_update<T>(L, i, k, i < nr ? gload<T>(io.in, k + 1) : z,
+                                         i > 0 ? gload<T>(io.in, k - 1) : z, gload<T>(io.in, k + P),
+                                         gload<T>(io.in, k - P));
+      ve = x.e; vp = x.p; vV = x.V;
+    }
+    sr[NE][lj][li] = ve; sr[NP][lj][li] = vp; sr[NV][lj][li] = vV;
+  }
+  __syncthreads();
+  // phase 2: black nodes of the tile from the new red values; both colours written
+  {
+    const int li = threadIdx.x % TX + 1, lj = threadIdx.x / TX + 1;
+    const int i = i0 + li, j = j0 + lj;
+    if (i <= nr && j >= 1 && j < nz) {
+      const size_t k = (size_t)j * P + i;
+      Triple<T> x;
+      if (((i + j) & 1) == 0) {
+        x.e = sr[NE][lj][li]; x.p = sr[NP][lj][li]; x.V = sr[NV][lj][li];
+      } else {
+        auto at = [&](int a, int b) {
+          Triple<T> t;
+          t.e = sr[NE][b][a]; t.p = sr[NP][b][a]; t.V = sr[NV][b][a];
+          return t;
+        };
+        x = node_update<T>(L, i, k, at(li + 1, lj), at(li - 1, lj), at(li, lj + 1), at(li, lj - 1));
+      }
+      io.out[NE][k] = x.e; io.out[NP][k] = x.p; io.out[NV][k] = x.V;
+    }
+  }
+}
+
+template <typename T, int TX, int TY>
+cudaError_t launch_sweep_t(const LevelT<T> &L, const SweepIO<T> &io, cudaStream_t st) {
+  dim3 g((L.nr + 1 + TX - 1) / TX, (L.nz + TY - 1) / TY);  // rows 1..nz-1 live in [0, nz)
+  k_sweep<T, TX, TY><<<g, TX * TY, 0, st>>>(L, io);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep(const LevelT<T> &L, const SweepIO<T> &io, int shape, cudaStream_t st) {
+  switch (shape) {
+    case 0: return launch_sweep_t<T, 32, 2>(L, io, st);
+    case 1: return launch_sweep_t<T, 32, 4>(L, io, st);
+    case 2: return launch_sweep_t<T, 32, 8>(L, io, st);
+    case 3: return launch_sweep_t<T, 64, 2>(L, io, st);
+    case 4: return launch_sweep_t<T, 64, 4>(L, io, st);
+    default: return launch_sweep_t<T, 128, 2>(L, io, st);
+  }
+}
+template cudaError_t launch_sweep<double>(const LevelT<double> &, const SweepIO<double> &, int, cudaStream_t);
+template cudaError_t launch_sweep<float>(const LevelT<float> &, const SweepIO<float> &, int, cudaStream_t);
+
 // K4: linear residual r = f - J v (or J v when f is null), optional per-field sums of squares
 // (accumulated in FP64).
 template <typename T>

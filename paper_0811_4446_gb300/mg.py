@@ -39,7 +39,8 @@ class mg_params(ctypes.Structure):
                 ("max_vcycles", ctypes.c_int32), ("max_newton", ctypes.c_int32), ("max_steps", ctypes.c_int32),
                 ("eta", ctypes.c_double), ("newton_tol", ctypes.c_double), ("corr_limit_frac", ctypes.c_double),
                 ("dt1", ctypes.c_double), ("dt_growth", ctypes.c_double), ("dt_max", ctypes.c_double),
-                ("n0", ctypes.c_double), ("use_graphs", ctypes.c_int32)]
+                ("n0", ctypes.c_double), ("use_graphs", ctypes.c_int32), ("fused_sweep", ctypes.c_int32),
+                ("guess_dt_max", ctypes.c_double), ("guess_level", ctypes.c_int32)]
 
 
 class mg_stats(ctypes.Structure):

@@ -62,22 +62,33 @@ def main():
     rows = []
     for seed in range(9000, 9000 + args.eval):
         d = unet.guess_discharge(seed, args.n)
-        s = mg.from_discharge(d, precision=mg.MG_MIXED)
         c = mg.from_discharge(d, precision=mg.MG_MIXED)
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        y = net1.forward(unet.features(d)[None])[0]
-        rc, st, fb = s.solve_steady_guess(*unet.state_from_output(y, d.V_cathode), 1e-8)
         torch.cuda.synchronize()
         b = time.perf_counter()
         rc2, st2 = c.solve_steady(1e-8)
         torch.cuda.synchronize()
         e = time.perf_counter()
-        rows.append({"seed": seed, "guess_ms": 1e3 * (b - a), "continuation_ms": 1e3 * (e - b), "fallback": fb,
-                     "guess_steps": st["steps_accepted"], "cont_steps": st2["steps_accepted"], "rc": [rc, rc2]})
-        print(rows[-1], flush=True)
+        ref = np.stack(c.get_state())
+        row = {"seed": seed, "continuation_ms": 1e3 * (e - b), "cont_steps": st2["steps_accepted"]}
+        y = net1.forward(unet.features(d)[None])[0]
+        g = unet.state_from_output(y, d.V_cathode)
+        row["guess_max_rel_err"] = [float(np.abs(g[q] - ref[q]).max() / np.abs(ref[q]).max()) for q in range(3)]
+        for level in (0, 1):
+            s = mg.from_discharge(d, precision=mg.MG_MIXED, guess_level=level, guess_dt_max=1e-6)
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            y = net1.forward(unet.features(d)[None])[0]
+            rc, st, fb = s.solve_steady_guess(*unet.state_from_output(y, d.V_cathode), 1e-8)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - a
+            row[f"guess_level{level}"] = {"ms": 1e3 * t, "fallback": fb, "steps": st["steps_accepted"],
+                                         "rejected": st["steps_rejected"], "rc": rc}
+        rows.append(row)
+        print(row, flush=True)
     report["eval"] = rows
-    report["median_speedup"] = float(np.median([r["continuation_ms"] / r["guess_ms"] for r in rows]))
+    for level in (0, 1):
+        report[f"median_speedup_level{level}"] = float(np.median(
+            [r["continuation_ms"] / r[f"guess_level{level}"]["ms"] for r in rows]))
     print(json.dumps(report), flush=True)
 
 

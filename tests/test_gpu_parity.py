@@ -349,3 +349,37 @@ def test_autotune_keeps_results(mg):
     assert np.array_equal(res[0][1], res[1][1])
     for q in range(3):
         assert np.array_equal(res[0][0][q], res[1][0][q])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [16, 64, 256])
+def test_fused_sweep_equals_half_sweeps(mg, precision, n):
+    """One launch per red-black sweep (tiles with a recomputed red ring, ping-pong buffers)
+    gives the same iterates as one launch per colour, bit for bit."""
+    d = W.make_discharge(n, seed=6, V_cathode=-300.0, use_table=(n == 64))
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    out = []
+    for fused in (1, 0):
+        s = mg.from_discharge(d, precision=prec, fused_sweep=fused)
+        if fused:
+            s.autotune()
+        F, _ = s.residual(1e-7)
+        x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-10, 100)
+        assert rc == mg.MG_OK
+        out.append((x, h))
+    (xa, ha), (xb, hb) = out
+    assert np.array_equal(ha, hb)
+    for q in range(3):
+        assert np.array_equal(xa[q], xb[q])
+
+
+def test_odd_sweep_counts(mg):
+    d = W.make_discharge(32, seed=6, V_cathode=-300.0)
+    res = []
+    for fused in (1, 0):
+        s = mg.from_discharge(d, nu1=1, nu2=3, fused_sweep=fused)
+        F, _ = s.residual(1e-8)
+        x, h, rc = s.linear_solve(1e-8, [-a for a in F], 1e-11, 100)
+        assert rc == mg.MG_OK
+        res.append((x, h))
+    assert np.array_equal(res[0][1], res[1][1])
