@@ -180,6 +180,8 @@ def run_ours(args):
 
     d = W.steady_257()
     s = mg.from_discharge(d)
+    shapes = s.autotune()                         # launch shapes per level (set-up, untimed)
+    fused0 = bool(shapes[0, 2])
     N0 = (d.nr + 1) * (d.nz + 1)
     inputs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (d.ne0, d.np0, d.V0, d.S_e, d.S_p)]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -290,18 +292,20 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (red-black smoother half sweep on the finest level)
     peaks = _peaks()
     nodes = (d.nr + 1) * (d.nz - 1)            # unknown nodes of the 257 x 257 level
-    # per fused red-black sweep launch (both colours): the 12 face coefficients, 2 Poisson
+    # fused red-black sweep launch (both colours): the 12 face coefficients, 2 Poisson
     # conductances, 7 block factors and 3 right-hand sides of every node once (8 B each), the old
-    # black corrections read (3 x 8 B per black node) and both colours' corrections written
-    bytes_per_launch = 228 * nodes
-    flops_per_launch = 52 * nodes               # per node: 20 FMA off-diagonal + block solve
+    # black corrections read (3 x 8 B per black node) and both colours' corrections written.
+    # Half-sweep launch (one colour): all face coefficients and conductances once, the colour's
+    # factors, f and du (8 B each) and the other colour's du read.
+    bytes_per_launch = (228 if fused0 else 176) * nodes
+    flops_per_launch = 52 * nodes if fused0 else 52 * (nodes / 2)   # 20 FMA off-diagonal + block solve per updated node
     avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
     fp64_peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12 * 1000.0   # GFLOP/s: SMs x DFMA/clk x 2 x GHz
     fp64_probe = mg.probe_fp64_gflops()
     achieved_flops = flops_per_launch / avg_s / 1e9
     achieved_bw = bytes_per_launch / avg_s / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "kernel": "k_sweep<double> (fused red-black sweep, 257x257 level)", "achieved": achieved_flops,
+    roofline = {"bound": "alu", "kernel": ("k_sweep<double> (fused red-black sweep" if fused0 else "k_smooth<double> (red-black half sweep") + ", 257x257 level)", "achieved": achieved_flops,
                 "peak": fp64_peak_nominal, "unit": "GFLOP/s", "frac": achieved_flops / fp64_peak_nominal,
                 "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "peak_probe_gflops": fp64_probe, "traffic": None,
@@ -354,6 +358,7 @@ def measure_forms(args, dev, peaks):
     # mixed-precision steady solve of the same 257^2 workload
     d = W.steady_257()
     s = mg.from_discharge(d, precision=mg.MG_MIXED)
+    s.autotune()
     ins = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (d.ne0, d.np0, d.V0)]
     times = []
     for k in range(4):
@@ -373,6 +378,7 @@ def measure_forms(args, dev, peaks):
     d = W.transient_1025()
     nodes = (d.nr + 1) * (d.nz - 1)
     s = mg.from_discharge(d, precision=mg.MG_MIXED)
+    fused32 = bool(s.autotune()[0, 5])
     F, _ = s.residual(1e-9)
     f = [-a for a in F]
     s.linear_solve(1e-9, f, 0.0, 0)
@@ -386,11 +392,11 @@ def measure_forms(args, dev, peaks):
     s.linear_solve(1e-9, f, 0.0, 10)
     n, ms = s.profile_end()
     avg = ms / n / 1000.0
-    byt = 114 * nodes      # FP32 fused sweep: the FP64 per-node bytes halved
+    byt = (114 if fused32 else 88) * nodes   # FP32: the FP64 per-launch bytes halved
     hbm = peaks.get("hbm_gbs", 6800.0)
     out["mixed_vcycle_1025"] = {"vcycle_us": vc * 1e6, "mpts_per_s": (d.nr + 1) * (d.nz + 1) / vc / 1e6,
                                 "residual_drop_30_cycles": float(hist[-1]),
-                                "roofline": {"bound": "hbm", "kernel": "k_sweep<float> (fused red-black sweep, 1025x1025 level)",
+                                "roofline": {"bound": "hbm", "kernel": ("k_sweep<float> (fused red-black sweep" if fused32 else "k_smooth<float> (red-black half sweep") + ", 1025x1025 level)",
                                              "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
                                              "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6,
                                              "algorithmic_bytes_per_launch": byt, "traffic": None}}
@@ -417,6 +423,49 @@ def measure_forms(args, dev, peaks):
                        "workers": args.batch_workers, "precision": "mixed"}
     for sv in solvers:
         sv.close()
+    # learned initial guess (committed weights, trained on the device): time to rho <= 1e-8 on
+    # held-out 257^2 instances against the plain continuation, both mixed precision
+    from paper_0811_4446_gb300 import unet
+    w = unet.load_weights()
+    if w is not None:
+        net = unet.UNet(1, 256)
+        net.set_params(w)
+        rows = []
+        variants = (("continuation", None, None),
+                    ("continuation_ramp_1e-3", None, dict(dt_max=1e-3)),
+                    ("guess_coarse_ramp_1e-3", dict(guess_level=1, guess_dt_max=1e-3), None),
+                    ("guess_coarse_capped", dict(guess_level=1, guess_dt_max=1e-6), None),
+                    ("guess_fine_capped", dict(guess_level=0, guess_dt_max=1e-6), None))
+        for seed in range(9000, 9008):
+            dd = unet.guess_discharge(seed, 256)
+            row = {}
+            for name, gkw, ckw in variants:
+                sv = mg.from_discharge(dd, precision=mg.MG_MIXED, **(gkw or ckw or {}))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if gkw is None:
+                    rc, _ = sv.solve_steady(TOL)
+                    fb = False
+                else:
+                    y = net.forward(unet.features(dd)[None])[0]
+                    rc, _, fb = sv.solve_steady_guess(*unet.state_from_output(y, dd.V_cathode), TOL)
+                torch.cuda.synchronize()
+                row[name] = (time.perf_counter() - t0) * 1e3
+                row[name + "_fallback"] = fb
+                if rc != mg.MG_OK:
+                    raise RuntimeError("learned-guess comparison failed")
+                sv.close()
+            rows.append(row)
+        cont = np.array([r["continuation"] for r in rows])
+        lg = {"instances": len(rows), "weights": "paper_0811_4446_gb300/weights/unet_guess_257.f32",
+              "fallbacks": int(sum(r[v[0] + "_fallback"] for r in rows for v in variants))}
+        for name, _, _ in variants:
+            t = np.array([r[name] for r in rows])
+            lg[name + "_ms_median"] = float(np.median(t))
+            if name != "continuation":
+                lg["gain_" + name] = float(np.median(cont / t))
+        out["learned_guess_257"] = lg
+        net.close()
     return out
 
 

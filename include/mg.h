@@ -97,6 +97,13 @@ typedef struct mg_params {
                              ramp starts at dt_max and grows by dt_growth up to this value */
   int32_t guess_level;    /* 0: march the full grid from the guess; 1: the guess (injected)
                              starts the coarse-grid march of the continuation instead */
+  double guess_dt_start;  /* first Delta t of the march from a learned guess (then x dt_growth) */
+  int32_t coarse_kernel_n;      /* levels whose larger side has <= this many intervals run as
+                                   one persistent cluster launch per V-cycle (0: off) */
+  int32_t coarse_kernel_ctas;   /* CTAs of that cluster (1..8) */
+  int32_t coarse_kernel_threads;/* threads per CTA (32..1024, multiple of 32) */
+  int32_t eta_adapt;      /* 1: Newton iteration k solves to eta_k = max(eta, min(0.1,
+                             tol / (2 rho_k))) instead of eta (inexact-Newton forcing term) */
 } mg_params;
 
 /* Per-call statistics. */
@@ -120,7 +127,9 @@ typedef struct mg_state mg_state;
  * V_cathode = -200, V_anode = 0, nu1 = nu2 = 2, coarsest = 4, eta = 1e-3,
  * max_newton = 10, max_vcycles = 60, max_steps = 400, dt1 = 1e-9,
  * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14,
- * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 0.
+ * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 1, guess_dt_start = 1e-8,
+ * coarse_kernel_n = 16,
+ * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on
@@ -192,8 +201,8 @@ int mg_solve_steady(mg_state *s, double tol, mg_stats *stats);
 
 /* Steady state from an initial guess of the full-grid state (the learned-guess form, see
  * unet.h): the current state is saved, (ne, np, V) become the state (electrode rows set to
- * their Dirichlet values) and the march starts with the long step dt_max, growing by
- * dt_growth up to guess_dt_max (the paper's growing ramp, Sec. 2).  If that march fails or
+ * their Dirichlet values) and the march starts at guess_dt_start, growing by dt_growth up to
+ * guess_dt_max (the paper's growing ramp, Sec. 2).  If that march fails or
  * needs more than 60 steps, the saved state is restored and mg_solve_steady's continuation
  * runs instead (*used_fallback = 1). */
 int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const double *V, int where, double tol,
@@ -211,8 +220,9 @@ int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, dou
 /* Autotuner of the smoother's launch shapes: times the red-black half sweep and the fused
  * sweep of every level (FP64 and, in the mixed form, FP32) over fixed sets of thread-block /
  * tile shapes and keeps the fastest per level.  Leaves the solution state untouched (only
- * the correction work buffers are written).  shapes_out (may be NULL) receives 4 ints per
- * level: FP64 half-sweep (bx, by), FP32 half-sweep (bx, by). */
+ * the correction work buffers are written); on each level the fused sweep is kept only where
+ * it beats two half sweeps.  shapes_out (may be NULL) receives 6 ints per level: FP64 half-sweep
+ * (bx, by), FP64 fused flag, FP32 half-sweep (bx, by), FP32 fused flag. */
 int mg_autotune(mg_state *s, int32_t *shapes_out);
 int mg_num_levels(const mg_state *s);
 

@@ -42,6 +42,7 @@ class SolverOptions:
     dt_max: float = 1e-6
     max_steps: int = 400
     newton_tol: Optional[float] = None   # per-step Newton tolerance; default 0.1 * steady tol
+    eta_adapt: bool = True          # relax eta when the Newton residual is near its target
 
 
 @dataclasses.dataclass
@@ -51,6 +52,15 @@ class StepStats:
     vcycles: List[int]
     rho: np.ndarray
     reason: str = ""
+
+
+def forcing_term(opt: SolverOptions, rho_k: float, tol: float) -> float:
+    """Linear tolerance of Newton iteration k: opt.eta, relaxed (up to 0.1) so that the linear
+    residual is only driven to half the Newton target, eta_k = max(eta, min(0.1, tol / (2 rho_k)))
+    (an inexact-Newton forcing term; the paper does not specify one)."""
+    if not opt.eta_adapt:
+        return opt.eta
+    return max(opt.eta, min(0.1, 0.5 * tol / rho_k))
 
 
 def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: float,
@@ -71,9 +81,10 @@ def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: f
             break
         H = mg.Hierarchy(g, x, dt, phys, opt.coarsest, opt.nu1, opt.nu2)
         tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
-        du, hist = H.solve(-disc.to_vec(g, F), opt.eta, opt.max_vcycles, scale=tn)
+        eta = forcing_term(opt, r.max(), tol)
+        du, hist = H.solve(-disc.to_vec(g, F), eta, opt.max_vcycles, scale=tn)
         vcyc.append(len(hist) - 1)
-        if not np.isfinite(hist[-1]) or hist[-1] > opt.eta:
+        if not np.isfinite(hist[-1]) or hist[-1] > eta:
             return u, StepStats(False, it + 1, vcyc, r, "linear solve failed")
         d = disc.from_vec(g, du)
         if np.abs(d[2]).max() > limit:

@@ -41,6 +41,7 @@ struct LevelBuf {
   int sbx = 32, sby = 2;         // half-sweep launch shape, FP64 view (autotuned)
   int sbx32 = 32, sby32 = 2;     // half-sweep launch shape, FP32 view (autotuned)
   int sw = 1, sw32 = 1;          // fused-sweep tile shape index, FP64 / FP32 (autotuned)
+  int fuse = 1, fuse32 = 1;      // fused sweep faster than two half sweeps on this level (autotuned)
 };
 
 }  // namespace
@@ -77,6 +78,10 @@ struct mg_state {
   SolveCtl *ctl = nullptr, *hctl = nullptr;
   cudaGraphExec_t vexec[kMaxLevels] = {};
   int vprefix[kMaxLevels] = {}, vbody[kMaxLevels] = {};
+  // persistent coarse-cycle kernel: levels cc_from .. nlev-1 in one cluster launch
+  int cc_from = -1;
+  CoarseSet<double> *cset64 = nullptr;
+  CoarseSet<float> *cset32 = nullptr;
 };
 
 namespace {
@@ -193,6 +198,8 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
   s->cs = c.take<double>(kMaxCoarse);
   s->flag = c.take<int>(4);
   s->ctl = c.take<SolveCtl>(1);
+  s->cset64 = c.take<CoarseSet<double>>(1);
+  s->cset32 = c.take<CoarseSet<float>>(1);
   s->table_d = table_rows > 0 ? c.take<double>((size_t)table_rows * 5) : nullptr;
 }
 
@@ -308,6 +315,10 @@ int smooth(mg_state *s, int l, int color, cudaStream_t st) {
   return MG_OK;
 }
 
+template <typename T> int level_fused(const LevelBuf &b);
+template <> int level_fused<double>(const LevelBuf &b) { return b.fuse; }
+template <> int level_fused<float>(const LevelBuf &b) { return b.fuse32; }
+
 template <typename T> int sweep_shape(const LevelBuf &b);
 template <> int sweep_shape<double>(const LevelBuf &b) { return b.sw; }
 template <> int sweep_shape<float>(const LevelBuf &b) { return b.sw32; }
@@ -318,7 +329,7 @@ template <typename T>
 int smooth_sweeps(mg_state *s, int l, int nu, cudaStream_t st) {
   const LevelT<T> &b = view<T>(s->lv[l]);
   int rc;
-  if (!s->prm.fused_sweep) {
+  if (!s->prm.fused_sweep || !level_fused<T>(s->lv[l])) {
     for (int k = 0; k < nu; ++k)
       for (int col = 0; col < 2; ++col)
         if ((rc = smooth<T>(s, l, col, st))) return rc;
@@ -340,9 +351,17 @@ int smooth_sweeps(mg_state *s, int l, int nu, cudaStream_t st) {
   return MG_OK;
 }
 
+template <typename T> const CoarseSet<T> *coarse_set(const mg_state *s);
+template <> const CoarseSet<double> *coarse_set<double>(const mg_state *s) { return s->cset64; }
+template <> const CoarseSet<float> *coarse_set<float>(const mg_state *s) { return s->cset32; }
+
 template <typename T>
 int vcycle(mg_state *s, int l, cudaStream_t st) {
   const LevelT<T> &b = view<T>(s->lv[l]);
+  if (l == s->cc_from && l < s->nlev - 1) {
+    CK(launch_coarse_cycle<T>(coarse_set<T>(s), s->prm.coarse_kernel_ctas, s->prm.coarse_kernel_threads, st));
+    return MG_OK;
+  }
   if (l == s->nlev - 1) {
     CK(launch_coarse_solve<T>(b, s->Minv, s->rs, s->cs, nscale_of<T>(s), st));
     return MG_OK;
@@ -573,7 +592,9 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out) {
     if (rc) return rc;
     int ncyc;
     bool ok;
-    rc = linear_solve(s, l0, s->prm.eta, s->prm.max_vcycles, tn, nullptr, &ncyc, &ok);
+    // inexact-Newton forcing term: drive the linear residual only to half the Newton target
+    const double eta = s->prm.eta_adapt ? std::max(s->prm.eta, std::min(0.1, 0.5 * tol / rmax)) : s->prm.eta;
+    rc = linear_solve(s, l0, eta, s->prm.max_vcycles, tn, nullptr, &ncyc, &ok);
     if (rc) return rc;
     if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
     CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout, s->stream));
@@ -620,6 +641,33 @@ int march(mg_state *s, int l0, double dt_start, double tol) {
     }
   }
   return fail(s, MG_EREJECT, "march: steady residual not reached in %d steps", s->prm.max_steps);
+}
+
+// Choose the first level handled by the persistent coarse-cycle kernel (all levels whose
+// larger side has at most coarse_kernel_n intervals) and upload the level views it needs.
+int setup_coarse_kernel(mg_state *s) {
+  s->cc_from = -1;
+  if (s->prm.coarse_kernel_n <= 0) return MG_OK;
+  for (int l = 1; l < s->nlev - 1; ++l)
+    if (std::max(s->lv[l].nr, s->lv[l].nz) <= s->prm.coarse_kernel_n) { s->cc_from = l; break; }
+  if (s->cc_from < 0 || s->nlev - s->cc_from > kMaxCoarseSet) { s->cc_from = -1; return MG_OK; }
+  CoarseSet<double> h64 = {};
+  CoarseSet<float> h32 = {};
+  h64.n = h32.n = s->nlev - s->cc_from;
+  h64.nu1 = h32.nu1 = s->prm.nu1;
+  h64.nu2 = h32.nu2 = s->prm.nu2;
+  h64.Minv = h32.Minv = s->Minv;
+  h64.rs = h32.rs = s->rs;
+  h64.cs = h32.cs = s->cs;
+  h64.nscale = 1.0;
+  h32.nscale = s->prm.n0;
+  for (int q = 0; q < h64.n; ++q) {
+    h64.lv[q] = s->lv[s->cc_from + q].L;
+    h32.lv[q] = s->lv[s->cc_from + q].M;
+  }
+  CK(cudaMemcpy(s->cset64, &h64, sizeof(h64), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->cset32, &h32, sizeof(h32), cudaMemcpyHostToDevice));
+  return MG_OK;
 }
 
 int check_where(mg_state *s, int where) {
@@ -679,7 +727,12 @@ void mg_params_default(mg_params *p) {
   p->use_graphs = 1;
   p->fused_sweep = 1;
   p->guess_dt_max = 1e-3;
-  p->guess_level = 0;
+  p->guess_level = 1;
+  p->guess_dt_start = 1e-8;
+  p->eta_adapt = 1;
+  p->coarse_kernel_n = 16;
+  p->coarse_kernel_ctas = 1;
+  p->coarse_kernel_threads = 512;
 }
 
 static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
@@ -702,6 +755,12 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
   }
   if (p->precision != MG_FP64 && p->precision != MG_MIXED) { *why = "unknown precision"; return MG_EINVAL; }
   if (p->precision == MG_MIXED && !(p->n0 > 0.0)) { *why = "n0 must be positive"; return MG_EINVAL; }
+  if (p->coarse_kernel_n > 0 && (p->coarse_kernel_ctas < 1 || p->coarse_kernel_ctas > 8 ||
+                                 p->coarse_kernel_threads < 32 || p->coarse_kernel_threads > 1024 ||
+                                 p->coarse_kernel_threads % 32)) {
+    *why = "coarse kernel: 1..8 CTAs of 32..1024 threads (multiple of 32)";
+    return MG_EINVAL;
+  }
   int lnr[kMaxLevels], lnz[kMaxLevels];
   const int n = plan_levels(g->nr, g->nz, p->coarsest, lnr, lnz);
   if (3 * (lnr[n - 1] + 1) * (lnz[n - 1] - 1) > kMaxCoarse) { *why = "coarsest level too large (too anisotropic grid)"; return MG_EINVAL; }
@@ -838,6 +897,7 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     if (rc == MG_OK) copy_state_async(s, 0, true);
     if (rc == MG_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = fail(s, MG_ECUDA, "init sync");
   }
+  if (rc == MG_OK) rc = setup_coarse_kernel(s);
   if (rc != MG_OK) {
     mg_destroy(s);
     return rc;
@@ -1035,14 +1095,14 @@ int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const
     // then the continuation proceeds as usual
     LevelBuf &c = s->lv[1];
     CK(launch_inject(b.L, b.sv, c.L, c.sv, false, true, s->stream));
-    rc = march(s, 1, saved_dt, tol);
+    rc = march(s, 1, std::min(saved_dt, s->prm.guess_dt_start), tol);
     if (rc == MG_OK) {
       CK(launch_prolong_state(c.L, c.sv, b.L, b.sv, s->stream));
       CK(launch_dirichlet(b.L, b.sv, s->prm.V_cathode, s->prm.V_anode, s->stream));
       rc = march(s, 0, saved_dt, tol);
     }
   } else {
-    rc = march(s, 0, saved_dt, tol);
+    rc = march(s, 0, std::min(saved_dt, s->prm.guess_dt_start), tol);
   }
   s->prm.max_steps = saved;
   s->prm.dt_max = saved_dt;
@@ -1135,10 +1195,15 @@ int mg_autotune(mg_state *s, int32_t *shapes_out) {
         if (ms < bestf) { bestf = ms; bf = c; }
       }
       if (prec == 0) b.sw = bf; else b.sw32 = bf;
+      // keep the fused sweep only where it beats two half sweeps of the best shape
+      const int fz = bestf < 2.0f * best ? 1 : 0;
+      if (prec == 0) b.fuse = fz; else b.fuse32 = fz;
       if (shapes_out) {
-        shapes_out[4 * l + 2 * prec] = cand[bi][0];
-        shapes_out[4 * l + 2 * prec + 1] = cand[bi][1];
+        shapes_out[6 * l + 3 * prec] = cand[bi][0];
+        shapes_out[6 * l + 3 * prec + 1] = cand[bi][1];
+        shapes_out[6 * l + 3 * prec + 2] = fz;
       }
+
     }
   }
   cudaEventDestroy(e0);

@@ -49,6 +49,17 @@ struct LevelT {
 };
 using Level = LevelT<double>;
 
+// The coarse levels handled by one launch of the persistent coarse-cycle kernel (K8).
+constexpr int kMaxCoarseSet = 8;
+template <typename T>
+struct CoarseSet {
+  LevelT<T> lv[kMaxCoarseSet];
+  int n;                            // levels in the set; the last one is the coarsest
+  int nu1, nu2;
+  const double *Minv, *rs, *cs;     // dense inverse of the coarsest level (FP64)
+  double nscale;                    // density unit of the view (1 or n0)
+};
+
 // Ping-pong correction buffers of one fused red-black sweep (read previous, write next).
 template <typename T>
 struct SweepIO {
@@ -97,6 +108,9 @@ template <typename T>
 cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx = 32, int by = 2);
 template <typename T>
 cudaError_t launch_sweep(const LevelT<T> &L, const SweepIO<T> &io, int shape, cudaStream_t st);
+// Coarse part of a V-cycle in one launch of a cluster of `cluster` CTAs (1..8) x `threads`.
+template <typename T>
+cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, cudaStream_t st);
 // r = f - J v (or out = J v when f == nullptr); optional per-field norms (sum of squares) -> out3
 template <typename T>
 cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,

@@ -11,6 +11,8 @@
 //
 // Thread mapping: one thread per node (or per node of one colour), 32 x 8 blocks,
 // x = radial index (coalesced), y = axial index.
+#include <cooperative_groups.h>
+
 #include <cstdio>
 
 #include "mg_impl.cuh"
@@ -361,6 +363,11 @@ cudaError_t launch_factor(const Level &L, const LevelT<float> *M, double dt, dou
   return cudaGetLastError();
 }
 
+template <typename T>
+struct Triple {
+  T e, p, V;
+};
+
 // Sum over the four neighbours of (off-diagonal block of eq. 14) x v at node k = (j, i).  The
 // off-diagonal blocks have 5 nonzeros: towards a neighbour across a face where this node is the
 // lower end: [-cF, cV] for each species, g for V; where it is the upper end: [-cG, cV], g.
@@ -404,10 +411,7 @@ __device__ __forceinline__ void offdiag(const LevelT<T> &L, int i, size_t k, con
 // K3: red-black collective Gauss-Seidel half sweep: every node of one colour (red = (i + j)
 // even) solves its 3x3 diagonal block (stored factors) against the current neighbours.
 template <typename T>
-__global__ void k_smooth(LevelT<T> L, int color) {
-  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
-  if (j >= L.nz || i > L.nr) return;
+__device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   const size_t k = (size_t)j * L.P + i;
   T oe, op, oV;
   offdiag<T>(L, i, k, L.du[NE], L.du[NP], L.du[NV], oe, op, oV);
@@ -416,6 +420,14 @@ __global__ void k_smooth(LevelT<T> L, int color) {
   L.du[NE][k] = (re - L.fac[FA13][k] * xV) * L.fac[FI11][k];
   L.du[NP][k] = (rp - L.fac[FA23][k] * xV) * L.fac[FI22][k];
   L.du[NV][k] = xV;
+}
+
+template <typename T>
+__global__ void k_smooth(LevelT<T> L, int color) {
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
+  if (j >= L.nz || i > L.nr) return;
+  smooth_node<T>(L, i, j);
 }
 
 constexpr int SBX = 32, SBY = 2;  // stencil kernels: small blocks so that coarse levels spread over the SMs
@@ -439,11 +451,6 @@ template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream
 // to `out` (ping-pong buffers), so no block reads what another block writes in the same
 // launch and the result equals two half-sweep launches bit for bit.  Coefficients of a face
 // are read by its red end in phase 1 and by its black end in phase 2 (an L1/L2 hit).
-template <typename T>
-struct Triple {
-  T e, p, V;
-};
-
 template <typename T>
 __device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, size_t k, const Triple<T> &vE,
                                                  const Triple<T> &vW, const Triple<T> &vN, const Triple<T> &vS) {
@@ -555,22 +562,30 @@ template cudaError_t launch_sweep<float>(const LevelT<float> &, const SweepIO<fl
 // K4: linear residual r = f - J v (or J v when f is null), optional per-field sums of squares
 // (accumulated in FP64).
 template <typename T>
+__device__ __forceinline__ Triple<T> linres_node(const LevelT<T> &L, int i, int j, const T *v0, const T *v1,
+                                                 const T *v2, const T *f0, const T *f1, const T *f2, T *o0, T *o1,
+                                                 T *o2) {
+  const size_t k = (size_t)j * L.P + i;
+  T oe, op, oV;
+  offdiag<T>(L, i, k, v0, v1, v2, oe, op, oV);
+  const T ak = L.Ak[k];
+  T je = L.dia[DA11][k] * v0[k] + L.fac[FA13][k] * v2[k] + oe;
+  T jp = L.dia[DA22][k] * v1[k] + L.fac[FA23][k] * v2[k] + op;
+  T jV = ak * (v1[k] - v0[k]) + L.dia[DA33][k] * v2[k] + oV;
+  if (f0) { je = f0[k] - je; jp = f1[k] - jp; jV = f2[k] - jV; }
+  o0[k] = je; o1[k] = jp; o2[k] = jV;
+  return Triple<T>{je, jp, jV};
+}
+
+template <typename T>
 __global__ void k_linres(LevelT<T> L, const T *v0, const T *v1, const T *v2, const T *f0, const T *f1, const T *f2,
                          T *o0, T *o1, T *o2, double *partials, unsigned *counter, double *out3) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
   if (i <= L.nr && j < L.nz) {
-    const size_t k = (size_t)j * L.P + i;
-    T oe, op, oV;
-    offdiag<T>(L, i, k, v0, v1, v2, oe, op, oV);
-    const T ak = L.Ak[k];
-    T je = L.dia[DA11][k] * v0[k] + L.fac[FA13][k] * v2[k] + oe;
-    T jp = L.dia[DA22][k] * v1[k] + L.fac[FA23][k] * v2[k] + op;
-    T jV = ak * (v1[k] - v0[k]) + L.dia[DA33][k] * v2[k] + oV;
-    if (f0) { je = f0[k] - je; jp = f1[k] - jp; jV = f2[k] - jV; }
-    o0[k] = je; o1[k] = jp; o2[k] = jV;
-    acc[0] = (double)je * je; acc[1] = (double)jp * jp; acc[2] = (double)jV * jV;
+    const Triple<T> r = linres_node<T>(L, i, j, v0, v1, v2, f0, f1, f2, o0, o1, o2);
+    acc[0] = (double)r.e * r.e; acc[1] = (double)r.p * r.p; acc[2] = (double)r.V * r.V;
   }
   if (out3) reduce_finish<3>(acc, partials, counter, out3, 0);
 }
@@ -592,10 +607,7 @@ template cudaError_t launch_linres<float>(const LevelT<float> &, float *const[3]
 
 // K5: restriction f_c = P^T r (full weighting in the node coordinates), and du_c = 0.
 template <typename T>
-__global__ void k_restrict(LevelT<T> F, LevelT<T> C) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (I > C.nr || J >= C.nz) return;
+__device__ __forceinline__ void restrict_node(const LevelT<T> &F, const LevelT<T> &C, int I, int J) {
   const size_t kc = (size_t)J * C.P + I;
   T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
@@ -616,6 +628,14 @@ __global__ void k_restrict(LevelT<T> F, LevelT<T> C) {
 }
 
 template <typename T>
+__global__ void k_restrict(LevelT<T> F, LevelT<T> C) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (I > C.nr || J >= C.nz) return;
+  restrict_node<T>(F, C, I, J);
+}
+
+template <typename T>
 cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st) {
   dim3 b(SBX, SBY), g((C.nr + 1 + SBX - 1) / SBX, (C.nz - 1 + SBY - 1) / SBY);
   k_restrict<T><<<g, b, 0, st>>>(F, C);
@@ -627,10 +647,7 @@ template cudaError_t launch_restrict<float>(const LevelT<float> &, const LevelT<
 
 // K6: prolongation and correction du_f += P du_c (bilinear in (r, z)).
 template <typename T>
-__global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i > F.nr || j >= F.nz) return;
+__device__ __forceinline__ void prolong_node(const LevelT<T> &C, const LevelT<T> &F, int i, int j) {
   const size_t kf = (size_t)j * F.P + i;
   int J0, J1;
   T w0, w1;
@@ -647,6 +664,14 @@ __global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
     const T b = v0 * c[(size_t)J1 * C.P + I0] + v1 * c[(size_t)J1 * C.P + I1];
     F.du[q][kf] += w0 * a + w1 * b;
   }
+}
+
+template <typename T>
+__global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > F.nr || j >= F.nz) return;
+  prolong_node<T>(C, F, i, j);
 }
 
 template <typename T>
@@ -913,19 +938,19 @@ cudaError_t launch_coarse_factor(const Level &L, double dt, double *M, double *M
 // cycle of the mixed form the density entries of f and du are in units of n0 (nscale = n0):
 // the FP64 inverse acts on unscaled values.
 template <typename T>
-__global__ void __launch_bounds__(CT) k_coarse_solve(LevelT<T> L, const double *Minv, const double *rs,
-                                                     const double *cs, double nscale) {
+__device__ __forceinline__ void coarse_solve_block(const LevelT<T> &L, const double *Minv, const double *rs,
+                                                   const double *cs, double nscale, int nthreads) {
   const int nn = (L.nr + 1) * (L.nz - 1);
   const int n = 3 * nn;
   __shared__ double fs[3 * 9 * 9];
-  for (int q = threadIdx.x; q < n; q += CT) {
+  for (int q = threadIdx.x; q < n; q += nthreads) {
     const int node = q / 3, fld = q % 3;
     const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
     const double sc = fld == NV ? 1.0 : nscale;
     fs[q] = rs[q] * sc * (double)L.f[fld][(size_t)j * L.P + i];
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < n; q += CT) {
+  for (int q = threadIdx.x; q < n; q += nthreads) {
     double x = 0.0;
     for (int c = 0; c < n; ++c) x += Minv[(size_t)q * n + c] * fs[c];
     const int node = q / 3, fld = q % 3;
@@ -934,6 +959,91 @@ __global__ void __launch_bounds__(CT) k_coarse_solve(LevelT<T> L, const double *
     L.du[fld][(size_t)j * L.P + i] = (T)(cs[q] * x * sc);
   }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(CT) k_coarse_solve(LevelT<T> L, const double *Minv, const double *rs,
+                                                     const double *cs, double nscale) {
+  coarse_solve_block<T>(L, Minv, rs, cs, nscale, CT);
+}
+
+// ------------------------------------------------------------------------------------------
+// K8: the coarse part of a V-cycle (levels S.lv[0] .. S.lv[n-1], the last one solved by the
+// dense inverse) in one launch of a thread-block cluster: every phase (a half sweep, the
+// residual, the restriction, the coarsest solve, a prolongation) is a loop over the level's
+// nodes strided across all threads of the cluster, separated by cluster-wide barriers.  It
+// calls the same per-node functions in the same order as the per-level kernels, so the result
+// is identical to launching them one by one.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__restrict__ sp) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const CoarseSet<T> &S = *sp;
+  const int nth = (int)(cl.num_blocks() * blockDim.x);
+  const int tid = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
+  // barrier.cluster.arrive / wait default to release / acquire at cluster scope, which orders
+  // the global-memory writes of one phase before the reads of the next for every CTA of the
+  // cluster; a single-CTA set uses the block barrier
+  const bool one = cl.num_blocks() == 1;
+  auto bar = [&]() {
+    if (one) __syncthreads();
+    else cl.sync();
+  };
+  auto sweeps = [&](const LevelT<T> &L, int nu) {
+    const int half = (L.nr + 2) / 2;
+    for (int it = 0; it < nu; ++it)
+      for (int color = 0; color < 2; ++color) {
+        for (int t = tid; t < (L.nz - 1) * half; t += nth) {
+          const int j = t / half + 1, i = 2 * (t % half) + ((j + color) & 1);
+          if (i <= L.nr) smooth_node<T>(L, i, j);
+        }
+        bar();
+      }
+  };
+  for (int q = 0; q + 1 < S.n; ++q) {
+    const LevelT<T> &L = S.lv[q];
+    const LevelT<T> &C = S.lv[q + 1];
+    sweeps(L, S.nu1);
+    const int W = L.nr + 1;
+    for (int t = tid; t < (L.nz - 1) * W; t += nth) {
+      const int j = t / W + 1, i = t % W;
+      linres_node<T>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP], L.f[NV], L.r[NE], L.r[NP], L.r[NV]);
+    }
+    bar();
+    const int Wc = C.nr + 1;
+    for (int t = tid; t < (C.nz - 1) * Wc; t += nth) restrict_node<T>(L, C, t % Wc, t / Wc + 1);
+    bar();
+  }
+  if (cl.block_rank() == 0) coarse_solve_block<T>(S.lv[S.n - 1], S.Minv, S.rs, S.cs, S.nscale, blockDim.x);
+  bar();
+  for (int q = S.n - 2; q >= 0; --q) {
+    const LevelT<T> &F = S.lv[q];
+    const int W = F.nr + 1;
+    for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(S.lv[q + 1], F, t % W, t / W + 1);
+    bar();
+    sweeps(F, S.nu2);
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_coarse_cycle<T>, dev_set);
+  count_launch();
+  return e;
+}
+template cudaError_t launch_coarse_cycle<double>(const CoarseSet<double> *, int, int, cudaStream_t);
+template cudaError_t launch_coarse_cycle<float>(const CoarseSet<float> *, int, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_coarse_solve(const LevelT<T> &L, const double *Minv, const double *rs, const double *cs,

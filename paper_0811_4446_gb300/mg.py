@@ -40,7 +40,10 @@ class mg_params(ctypes.Structure):
                 ("eta", ctypes.c_double), ("newton_tol", ctypes.c_double), ("corr_limit_frac", ctypes.c_double),
                 ("dt1", ctypes.c_double), ("dt_growth", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("n0", ctypes.c_double), ("use_graphs", ctypes.c_int32), ("fused_sweep", ctypes.c_int32),
-                ("guess_dt_max", ctypes.c_double), ("guess_level", ctypes.c_int32)]
+                ("guess_dt_max", ctypes.c_double), ("guess_level", ctypes.c_int32),
+                ("guess_dt_start", ctypes.c_double),
+                ("coarse_kernel_n", ctypes.c_int32), ("coarse_kernel_ctas", ctypes.c_int32),
+                ("coarse_kernel_threads", ctypes.c_int32), ("eta_adapt", ctypes.c_int32)]
 
 
 class mg_stats(ctypes.Structure):
@@ -294,9 +297,9 @@ class Solver:
 
     def autotune(self):
         n = self.lib.mg_num_levels(self.h)
-        out = np.zeros(4 * n, dtype=np.int32)
+        out = np.zeros(6 * n, dtype=np.int32)
         self._check(self.lib.mg_autotune(self.h, out.ctypes.data))
-        return out.reshape(n, 4)
+        return out.reshape(n, 6)
 
     def profile_begin(self, kernel: int, level: int = 0):
         self._check(self.lib.mg_profile_begin(self.h, int(kernel), int(level)))

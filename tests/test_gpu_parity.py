@@ -342,7 +342,7 @@ def test_autotune_keeps_results(mg):
         s = mg.from_discharge(d, precision=mg.MG_MIXED)
         if tune:
             shapes = s.autotune()
-            assert shapes.shape[1] == 4 and np.all(shapes[:-1, 0] >= 32)
+            assert shapes.shape[1] == 6 and np.all(shapes[:-1, 0] >= 32)
         F, _ = s.residual(1e-7)
         x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-10, 100)
         res.append((x, h))
@@ -383,3 +383,24 @@ def test_odd_sweep_counts(mg):
         assert rc == mg.MG_OK
         res.append((x, h))
     assert np.array_equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("ctas,threads", [(1, 1024), (2, 256), (8, 512)])
+def test_persistent_coarse_cycle_equals_level_kernels(mg, precision, ctas, threads):
+    """The coarse levels of a V-cycle in one cluster launch give the same iterates as the
+    per-level kernels, bit for bit."""
+    d = W.make_discharge(128, seed=8, V_cathode=-300.0, use_table=True)
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    out = []
+    for kn in (64, 0):
+        s = mg.from_discharge(d, precision=prec, coarse_kernel_n=kn, coarse_kernel_ctas=ctas,
+                              coarse_kernel_threads=threads)
+        F, _ = s.residual(1e-7)
+        x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-10, 100)
+        assert rc == mg.MG_OK
+        out.append((x, h))
+    (xa, ha), (xb, hb) = out
+    assert np.array_equal(ha, hb)
+    for q in range(3):
+        assert np.array_equal(xa[q], xb[q])
