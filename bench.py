@@ -466,7 +466,64 @@ def measure_forms(args, dev, peaks):
                 lg["gain_" + name] = float(np.median(cont / t))
         out["learned_guess_257"] = lg
         net.close()
+    # tensor-core convolutions of the network: forward and training step on a batch of 16 at 257^2
+    out["unet_257"] = measure_unet(dev, peaks)
     return out
+
+
+def unet_conv_flops(n: int = 256) -> float:
+    """Multiply-add FLOPs (2 per MAC) of the network's convolutions for one sample."""
+    H = [n + 1]
+    for _ in range(3):
+        H.append((H[-1] - 1) // 2 + 1)
+    layers = [(0, 9 * 8, 32), (0, 9 * 32, 32), (1, 9 * 32, 64), (1, 9 * 64, 64), (2, 9 * 64, 96), (2, 9 * 96, 96),
+              (3, 9 * 96, 128), (3, 9 * 128, 128), (2, 9 * 224, 64), (1, 9 * 128, 32), (0, 9 * 64, 32), (0, 32, 8)]
+    return float(sum(2.0 * H[lv] ** 2 * k * co for lv, k, co in layers))
+
+
+def measure_unet(dev, peaks, B: int = 16, reps: int = 10):
+    import torch
+    from paper_0811_4446_gb300 import unet
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.standard_normal((B, 257, 257, 8)).astype(np.float32)).to(dev)
+    x[..., 5:] = 0
+    t = torch.from_numpy(rng.standard_normal((B, 257, 257, 3)).astype(np.float32)).to(dev)
+    y = torch.empty((B, 257, 257, 3), dtype=torch.float32, device=dev)
+    res = {}
+    fl = unet_conv_flops() * B
+    for name, path in (("tcgen05", 1), ("mma_sync", 0)):
+        net = unet.UNet(B, 256)
+        net.set_tensor_path(path)
+        net.set_params(unet.init_params(0))
+        # the network launches on torch's current stream: events there bracket its kernels
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for _ in range(3):
+            net.forward(x, y)
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            net.forward(x, y)
+        ev[1].record()
+        for _ in range(3):
+            net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        ev[2].record()
+        for _ in range(reps):
+            net.train_step(x, t, 1e-4)
+        ev[3].record()
+        torch.cuda.synchronize()
+        fwd = ev[0].elapsed_time(ev[1]) * 1e-3 / reps
+        stp = ev[2].elapsed_time(ev[3]) * 1e-3 / reps
+        res[name] = {"forward_ms": fwd * 1e3, "forward_tflops": fl / fwd / 1e12,
+                     "train_step_ms": stp * 1e3, "train_tflops": 3 * fl / stp / 1e12}
+        net.close()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    res["roofline"] = {"bound": "tensor", "kernel": "U-Net forward (all convolutions, batch 16, 257^2)",
+                       "achieved": res["tcgen05"]["forward_tflops"], "peak": peak, "unit": "TFLOP/s",
+                       "frac": res["tcgen05"]["forward_tflops"] / peak,
+                       "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
+                       "flops_per_sample": unet_conv_flops(), "traffic": None}
+    return res
 
 
 def main():

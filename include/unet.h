@@ -52,6 +52,13 @@ int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where);
 int mg_unet_loss_grad(mg_unet *n, const float *x, const float *t, int B, double *loss, int where);
 int mg_unet_get_grads(mg_unet *n, float *g, int where);
 
+/* Tensor-core path of the convolutions: 1 (default) = tcgen05.mma with the accumulator in
+ * tensor memory for the forward and data-gradient convolutions whose output width is a
+ * multiple of 16 (<= 256); 0 = mma.sync for every convolution.  The weight gradient and the
+ * 8-wide head always use mma.sync.  A tcgen05 kernel whose bounded wait expires makes the
+ * next call return MG_ETIMEOUT. */
+int mg_unet_set_tensor_path(mg_unet *n, int path);
+
 /* One training step: loss and gradients as above, then an Adam update (beta1 0.9,
  * beta2 0.999, eps 1e-8) with learning rate lr. */
 int mg_unet_train_step(mg_unet *n, const float *x, const float *t, int B, float lr, double *loss, int where);

@@ -1,6 +1,7 @@
 """Small fixed workloads for profiling runs (ncu captures of single kernels).
 
     python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager]
+    python -m paper_0811_4446_gb300.cases unet B N [REPS] [--mma]
 
 builds the N x N-node discharge of the benchmark family (table transport for N = 256),
 evaluates the Newton residual at the initial state and runs CYCLES multigrid V-cycles
@@ -8,6 +9,10 @@ evaluates the Newton residual at the initial state and runs CYCLES multigrid V-c
 V-cycle: 4 per level on the way down, 4 per level on the way up, finest level first.
 --eager launches the V-cycle kernels from the host instead of the device-side graph loop
 (kernel profilers cannot attribute kernels inside graphs with conditional nodes).
+
+unet: REPS (default 2) forward passes plus one training step of the learned-guess network
+on a batch of B random (N+1) x (N+1) inputs; --mma selects the mma.sync convolutions instead
+of the tcgen05 ones.
 """
 from __future__ import annotations
 
@@ -32,7 +37,30 @@ def vcycles(n: int, cycles: int = 3, mixed: bool = False, eager: bool = False) -
     return float(hist[-1])
 
 
+def unet_case(B: int, n: int, reps: int = 2, mma: bool = False) -> float:
+    import numpy as np
+    import torch
+    from . import unet
+
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.standard_normal((B, n + 1, n + 1, 8)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((B, n + 1, n + 1, 3)).astype(np.float32)).cuda()
+    net = unet.UNet(B, n)
+    net.set_tensor_path(0 if mma else 1)
+    net.set_params(unet.init_params(0))
+    for _ in range(reps):
+        y = net.forward(x)
+    loss = net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    net.close()
+    return float(loss) + float(y.abs().mean())
+
+
 if __name__ == "__main__":
+    if len(sys.argv) >= 4 and sys.argv[1] == "unet":
+        R = int(sys.argv[4]) if len(sys.argv) > 4 and not sys.argv[4].startswith("--") else 2
+        print("ok", unet_case(int(sys.argv[2]), int(sys.argv[3]), R, "--mma" in sys.argv))
+        sys.exit(0)
     if len(sys.argv) < 3 or sys.argv[1] != "vcycles":
         print(__doc__)
         sys.exit(2)

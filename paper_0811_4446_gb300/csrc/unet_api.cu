@@ -50,6 +50,8 @@ struct mg_unet {
   float *out = nullptr, *dout = nullptr, *tgt = nullptr, *xin = nullptr;
   __nv_bfloat16 *dpre = nullptr;
   double *loss_d = nullptr, *loss_h = nullptr;
+  int *tc_err = nullptr;   // set by a tcgen05 kernel whose bounded wait expired
+  int use_tc = 1;          // tcgen05 path where the layer shape allows it
   int step = 0;
   void *block = nullptr;
   std::string err;
@@ -134,6 +136,7 @@ void layout(mg_unet *n, Carve &c) {
   n->xin = c.take<float>(P0 * 8);
   n->dpre = c.take<__nv_bfloat16>(P0 * 32);
   n->loss_d = c.take<double>(1);
+  n->tc_err = c.take<int>(4);
 }
 
 ConvArgs conv_args(const mg_unet *n, int l, int B, const Act &in1, const Act *in2) {
@@ -162,7 +165,8 @@ int conv_fwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, Act *out,
   a.w = n->wf[l];
   a.y = out ? out->a : nullptr;
   a.y32 = out32;
-  UK(launch_conv(a, MODE_FWD, 1, n->st));
+  if (n->use_tc && conv_tc_supported(a, MODE_FWD)) UK(launch_conv_tc(a, MODE_FWD, n->tc_err, n->st));
+  else UK(launch_conv(a, MODE_FWD, 1, n->st));
   return MG_OK;
 }
 
@@ -193,7 +197,8 @@ int conv_bwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, const Act
     d.dy = n->dpre;
     d.dx1 = in1.g;
     d.dx2 = in2 ? in2->g : nullptr;
-    UK(launch_conv(d, MODE_DGRAD, 1, n->st));
+    if (n->use_tc && conv_tc_supported(d, MODE_DGRAD)) UK(launch_conv_tc(d, MODE_DGRAD, n->tc_err, n->st));
+    else UK(launch_conv(d, MODE_DGRAD, 1, n->st));
   }
   return MG_OK;
 }
@@ -251,6 +256,17 @@ int backward(mg_unet *n, int B) {
 cudaMemcpyKind kin(int where) { return where == MG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kout(int where) { return where == MG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
+// a tcgen05 kernel that gave up on a bounded wait leaves the flag set
+int check_tc(mg_unet *n) {
+  int h = 0;
+  UK(cudaMemcpy(&h, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    cudaMemset(n->tc_err, 0, sizeof(int));
+    return fail(n, MG_ETIMEOUT, "tensor-core convolution: bounded wait expired");
+  }
+  return MG_OK;
+}
+
 int load_input(mg_unet *n, const float *x, int B, int where) {
   const size_t e = (size_t)B * n->H * n->H * 8;
   UK(cudaMemcpyAsync(n->xin, x, e * sizeof(float), kin(where), n->st));
@@ -270,7 +286,7 @@ int loss_grad(mg_unet *n, const float *x, const float *t, int B, double *loss, i
   UK(cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, n->st));
   UK(cudaStreamSynchronize(n->st));
   if (loss) *loss = *n->loss_h;
-  return MG_OK;
+  return check_tc(n);
 }
 
 }  // namespace
@@ -346,6 +362,12 @@ int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where) {
   const size_t P = (size_t)B * n->H * n->H;
   UK(cudaMemcpy2DAsync(y, 3 * sizeof(float), n->out, 8 * sizeof(float), 3 * sizeof(float), P, kout(where), n->st));
   UK(cudaStreamSynchronize(n->st));
+  return check_tc(n);
+}
+
+int mg_unet_set_tensor_path(mg_unet *n, int path) {
+  if (!n || (path != 0 && path != 1)) return MG_EINVAL;
+  n->use_tc = path;
   return MG_OK;
 }
 

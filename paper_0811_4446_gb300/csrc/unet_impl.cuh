@@ -29,6 +29,9 @@ struct ConvArgs {
 };
 
 cudaError_t launch_conv(const ConvArgs &a, int mode, int splits, cudaStream_t st);
+// tcgen05 / TMEM path (forward and data gradient with 16 <= N <= 256, N % 16 == 0)
+bool conv_tc_supported(const ConvArgs &a, int mode);
+cudaError_t launch_conv_tc(const ConvArgs &a, int mode, int *err, cudaStream_t st);
 cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
                             cudaStream_t st);
 cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st);

@@ -32,6 +32,7 @@ SIGNATURES = {
     "mg_unet_loss_grad": (_i, [_vp, _vp, _vp, _i, _c.POINTER(_d), _i]),
     "mg_unet_get_grads": (_i, [_vp, _vp, _i]),
     "mg_unet_train_step": (_i, [_vp, _vp, _vp, _i, _f, _c.POINTER(_d), _i]),
+    "mg_unet_set_tensor_path": (_i, [_vp, _i]),
 }
 
 WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
@@ -88,6 +89,10 @@ class UNet:
     def _check(self, rc):
         if rc != mg.MG_OK:
             raise mg.MGError(rc, self.lib.mg_unet_last_error(self.h).decode())
+
+    def set_tensor_path(self, path: int):
+        """1: tcgen05 / TMEM convolutions where the shape allows, 0: mma.sync everywhere."""
+        self._check(self.lib.mg_unet_set_tensor_path(self.h, int(path)))
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32) if isinstance(p, np.ndarray) else p

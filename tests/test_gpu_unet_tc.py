@@ -1,0 +1,56 @@
+"""GPU tests of the tcgen05 / TMEM convolution path of the learned-guess network: the forward
+pass and every parameter gradient agree with the mma.sync path (itself checked against the
+FP64 CPU oracle in test_gpu_unet.py) up to the rounding of BF16 outputs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def un():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0811_4446_gb300 import build, unet
+    build.build()
+    return unet
+
+
+def _inputs(un, B, n, seed):
+    rng = np.random.default_rng(seed)
+    p = un.init_params(seed)
+    p += (0.01 * rng.standard_normal(p.size)).astype(np.float32)
+    x = np.zeros((B, n + 1, n + 1, 8), np.float32)
+    x[..., :5] = rng.standard_normal((B, n + 1, n + 1, 5)).astype(np.float32)
+    t = (0.5 * rng.standard_normal((B, n + 1, n + 1, 3))).astype(np.float32)
+    return p, x, t
+
+
+@pytest.mark.parametrize("B,n", [(2, 32), (3, 64)])
+def test_tc_forward_matches_mma_sync(un, B, n):
+    p, x, _ = _inputs(un, B, n, 11)
+    ys = []
+    for path in (0, 1):
+        net = un.UNet(B, n)
+        net.set_tensor_path(path)
+        net.set_params(p)
+        ys.append(net.forward(x))
+        net.close()
+    rel = np.linalg.norm(ys[1] - ys[0]) / np.linalg.norm(ys[0])
+    assert rel <= 1e-2, rel
+
+
+def test_tc_gradients_match_mma_sync(un):
+    p, x, t = _inputs(un, 2, 32, 12)
+    out = []
+    for path in (0, 1):
+        net = un.UNet(2, 32)
+        net.set_tensor_path(path)
+        net.set_params(p)
+        out.append(net.loss_grad(x, t))
+        net.close()
+    (l0, g0), (l1, g1) = out
+    assert abs(l1 - l0) <= 1e-2 * abs(l0)
+    rel = np.linalg.norm(g1 - g0) / np.linalg.norm(g0)
+    assert rel <= 3e-2, rel
