@@ -236,9 +236,14 @@ uint64_t mg_kernel_launches(void);
 /* Kernel timing for measurement: between mg_profile_begin and mg_profile_end every launch
  * of `kernel` on multigrid level `level` (0 = finest) is bracketed by CUDA events recorded on
  * the state's stream (up to 16384 launches).  mg_profile_end synchronises the stream and
- * returns the number of bracketed launches and their summed device time in milliseconds. */
+ * returns the number of bracketed launches and their summed device time in milliseconds.
+ * MG_PROF_RESIDUAL brackets the face-coefficient and residual launches of a residual
+ * evaluation on `level`; MG_PROF_COEF the hierarchy set-up below a Newton iteration on root
+ * level `level` (injection, coarse-level coefficients and the diagonal factors of every level,
+ * one launch each); MG_PROF_COARSE the launches of the coarse-cycle kernel that starts on
+ * `level`. */
 enum { MG_PROF_SMOOTH = 1, MG_PROF_LINRES = 2, MG_PROF_COEF = 3, MG_PROF_RESIDUAL = 4,
-       MG_PROF_RESTRICT = 5, MG_PROF_PROLONG = 6 };
+       MG_PROF_RESTRICT = 5, MG_PROF_PROLONG = 6, MG_PROF_COARSE = 7 };
 int mg_profile_begin(mg_state *s, int kernel, int level);
 int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms);
 
@@ -251,7 +256,8 @@ double mg_probe_fp64_gflops(void *stream);
  * callers that cannot allocate device memory (code running inside another framework's memory
  * pool, real-time loops where cudaMalloc is forbidden or would synchronise the device, plug-ins
  * that may only use the buffers their host hands them).  It evaluates the same residual rows
- * and scale-free norms rho[3] as mg_residual, with the same kernel, without creating a state:
+ * and scale-free norms rho[3] as mg_residual (up to rounding: it evaluates every face directly
+ * instead of through stored face coefficients), without creating a state:
  * every array argument is caller-owned DEVICE memory of (nz + 1) x (nr + 1) doubles (dense
  * rows, i fastest) and rho is host memory.  ne_old, np_old, V_old are read only when dt > 0
  * (dt <= 0: steady residual).  F_ne, F_np, F_V receive the rows when non-NULL (all three or

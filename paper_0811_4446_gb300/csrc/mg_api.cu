@@ -82,6 +82,8 @@ struct mg_state {
   int cc_from = -1;
   CoarseSet<double> *cset64 = nullptr;
   CoarseSet<float> *cset32 = nullptr;
+  size_t cc_smem64 = 0, cc_smem32 = 0;  // shared memory of the single-CTA form (0: global-memory form)
+  LevelSet *lset = nullptr;   // device copy of every level's views (multi-level set-up kernels)
 };
 
 namespace {
@@ -127,9 +129,10 @@ struct Carver {
 };
 
 constexpr int kFieldsPerLevel = 48;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, ubak 3, du2 3
-constexpr int kGeoPerLevel = 4;      // dz, dzc, volr, wz (each up to max(nr, nz) + 1)
+constexpr int kGeoPerLevel = 5;      // dz, dzc, volr, wz, 1/dz (each up to max(nr, nz) + 1)
 
-size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz + 1 + 7) / 8); }
+// blocks of the largest reduction launch (32 x 2 threads per block)
+size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz + 1 + 1) / 2); }
 
 constexpr int kFields32PerLevel = 37;  // cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, du2 3
 
@@ -162,6 +165,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
       b.L.dzc = b.geo + glen;
       b.L.volr = b.geo + 2 * glen;
       b.L.wz = b.geo + 3 * glen;
+      b.L.idz = b.geo + 4 * glen;
     }
     b.M = LevelT<float>();
     b.geo32 = nullptr;
@@ -185,6 +189,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
         b.M.dzc = b.geo32 + glen;
         b.M.volr = b.geo32 + 2 * glen;
         b.M.wz = b.geo32 + 3 * glen;
+        b.M.idz = b.geo32 + 4 * glen;
       }
     }
   }
@@ -200,16 +205,18 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
   s->ctl = c.take<SolveCtl>(1);
   s->cset64 = c.take<CoarseSet<double>>(1);
   s->cset32 = c.take<CoarseSet<float>>(1);
-  s->table_d = table_rows > 0 ? c.take<double>((size_t)table_rows * 5) : nullptr;
+  s->table_d = table_rows > 0 ? c.take<double>((size_t)table_rows * 6) : nullptr;  // rows x 5, then 1/dE
+  s->lset = c.take<LevelSet>(1);
 }
 
 // Geometry of one level (finite-volume control volumes of eqs. 12-13, per radian).
 void host_geometry(const std::vector<double> &zl, int nr, double R, std::vector<double> &out, int glen) {
   const int nz = (int)zl.size() - 1;
   out.assign((size_t)kGeoPerLevel * glen, 0.0);
-  double *dz = out.data(), *dzc = dz + glen, *volr = dz + 2 * glen, *wz = dz + 3 * glen;
+  double *dz = out.data(), *dzc = dz + glen, *volr = dz + 2 * glen, *wz = dz + 3 * glen, *idz = dz + 4 * glen;
   const double dr = R / nr;
   for (int j = 0; j < nz; ++j) dz[j] = zl[j + 1] - zl[j];
+  for (int j = 0; j < nz; ++j) idz[j] = 1.0 / dz[j];
   for (int j = 1; j < nz; ++j) dzc[j] = 0.5 * (dz[j - 1] + dz[j]);
   for (int i = 0; i <= nr; ++i) volr[i] = i * dr * dr;
   volr[0] = dr * dr / 8.0;
@@ -268,7 +275,10 @@ int residual(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], doub
   LevelBuf &b = s->lv[l0];
   {
     ProfScope ps(s, MG_PROF_RESIDUAL, l0);
-    CK(launch_residual(b.L, b.sv, s->tr, dt, write_f, Fout, s->partials, s->counter, s->dout, s->stream));
+    // face coefficients at the state (also the Jacobian's, reused by build_hierarchy), then
+    // the rows from them
+    CK(launch_coef(b.L, b.sv, s->tr, s->stream));
+    CK(launch_resid_coef(b.L, b.sv, dt, write_f, Fout, s->partials, s->counter, s->dout, s->stream));
   }
   int rc = sync_read(s, 6);
   if (rc) return rc;
@@ -281,14 +291,18 @@ int residual(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], doub
 }
 
 // Coefficients on levels l0..nlev-1 at the state of l0 injected downward; coarsest inverse.
+// The face coefficients of level l0 itself come from residual() at the same state, which every
+// caller runs first.  All coarser levels are treated by one launch per phase (their kernels are
+// latency-bound one by one).
 int build_hierarchy(mg_state *s, int l0, double dt) {
-  for (int l = l0; l < s->nlev; ++l) {
-    LevelBuf &b = s->lv[l];
-    if (l > l0) CK(launch_inject(s->lv[l - 1].L, s->lv[l - 1].sv, b.L, b.sv, false, false, s->stream));
-    ProfScope ps(s, MG_PROF_COEF, l);
-    CK(launch_coef(b.L, b.sv, s->tr, s->stream));
-    if (mixed(s)) CK(launch_coef_to32(b.L, b.M, s->prm.n0, s->stream));
-    CK(launch_factor(b.L, mixed(s) ? &b.M : nullptr, dt, s->prm.n0, s->stream));
+  const int last = s->nlev - 1;
+  {
+    ProfScope ps(s, MG_PROF_COEF, l0);
+    if (l0 < last) {
+      CK(launch_inject_levels(s->lset, s->lv[l0].L, l0, last, s->stream));
+      CK(launch_coef_levels(s->lset, s->lv[l0 + 1].L, l0 + 1, last, s->tr, s->stream));
+    }
+    CK(launch_factor_levels(s->lset, s->lv[l0].L, l0, last, mixed(s), dt, s->prm.n0, s->stream));
   }
   LevelBuf &c = s->lv[s->nlev - 1];
   CK(launch_coarse_factor(c.L, dt, s->M, s->Minv, s->rs, s->cs, s->flag, s->stream));
@@ -354,12 +368,17 @@ int smooth_sweeps(mg_state *s, int l, int nu, cudaStream_t st) {
 template <typename T> const CoarseSet<T> *coarse_set(const mg_state *s);
 template <> const CoarseSet<double> *coarse_set<double>(const mg_state *s) { return s->cset64; }
 template <> const CoarseSet<float> *coarse_set<float>(const mg_state *s) { return s->cset32; }
+template <typename T> size_t coarse_smem(const mg_state *s);
+template <> size_t coarse_smem<double>(const mg_state *s) { return s->cc_smem64; }
+template <> size_t coarse_smem<float>(const mg_state *s) { return s->cc_smem32; }
 
 template <typename T>
 int vcycle(mg_state *s, int l, cudaStream_t st) {
   const LevelT<T> &b = view<T>(s->lv[l]);
   if (l == s->cc_from && l < s->nlev - 1) {
-    CK(launch_coarse_cycle<T>(coarse_set<T>(s), s->prm.coarse_kernel_ctas, s->prm.coarse_kernel_threads, st));
+    ProfScope ps(s, MG_PROF_COARSE, l);
+    CK(launch_coarse_cycle<T>(coarse_set<T>(s), s->prm.coarse_kernel_ctas, s->prm.coarse_kernel_threads,
+                              coarse_smem<T>(s), st));
     return MG_OK;
   }
   if (l == s->nlev - 1) {
@@ -643,6 +662,20 @@ int march(mg_state *s, int l0, double dt_start, double tol) {
   return fail(s, MG_EREJECT, "march: steady residual not reached in %d steps", s->prm.max_steps);
 }
 
+// Device copy of every level's views (pointers and geometry scalars are fixed after mg_create).
+int upload_level_set(mg_state *s) {
+  if (s->nlev > kMaxLevelSet) return fail(s, MG_EINVAL, "too many levels (%d)", s->nlev);
+  LevelSet h;
+  std::memset(&h, 0, sizeof(h));
+  for (int l = 0; l < s->nlev; ++l) {
+    h.L[l] = s->lv[l].L;
+    h.M[l] = s->lv[l].M;
+    h.sv[l] = s->lv[l].sv;
+  }
+  CK(cudaMemcpy(s->lset, &h, sizeof(h), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
 // Choose the first level handled by the persistent coarse-cycle kernel (all levels whose
 // larger side has at most coarse_kernel_n intervals) and upload the level views it needs.
 int setup_coarse_kernel(mg_state *s) {
@@ -667,6 +700,9 @@ int setup_coarse_kernel(mg_state *s) {
   }
   CK(cudaMemcpy(s->cset64, &h64, sizeof(h64), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->cset32, &h32, sizeof(h32), cudaMemcpyHostToDevice));
+  constexpr size_t kCoarseSmemLimit = 200 * 1024;
+  s->cc_smem64 = prepare_coarse_smem(h64, kCoarseSmemLimit);
+  s->cc_smem32 = mixed(s) ? prepare_coarse_smem(h32, kCoarseSmemLimit) : 0;
   return MG_OK;
 }
 
@@ -833,6 +869,8 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     host_geometry(zl, b.nr, g->R, geo, glen);
     b.L.dr = g->R / b.nr;
     b.M.dr = (float)(g->R / b.nr);
+    b.L.idr = 1.0 / b.L.dr;
+    b.M.idr = (float)b.L.idr;
     if (cudaMemcpyAsync(b.geo, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream) !=
         cudaSuccess)
       rc = fail(s, MG_ECUDA, "geometry copy");
@@ -877,12 +915,16 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
   s->tr.mu_e = p->mu_e / p->pressure_factor; s->tr.D_e = p->D_e / p->pressure_factor;
   s->tr.mu_p = p->mu_p / p->pressure_factor; s->tr.D_p = p->D_p / p->pressure_factor;
   s->tr.inv_pf = 1.0 / p->pressure_factor;
-  s->tr.table = nullptr; s->tr.rows = 0;
+  s->tr.table = nullptr; s->tr.rows = 0; s->tr.inv_dE = nullptr;
   if (p->table && rc == MG_OK) {
-    if (cudaMemcpy(s->table_d, s->table_h.data(), s->table_h.size() * sizeof(double), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
+    // the table, then the reciprocal width of each |E| interval (the lookup multiplies by it)
+    const int rows = p->table_rows;
+    std::vector<double> t6(s->table_h);
+    t6.resize((size_t)rows * 6, 0.0);
+    for (int k = 0; k + 1 < rows; ++k) t6[(size_t)rows * 5 + k] = 1.0 / (s->table_h[5 * (k + 1)] - s->table_h[5 * k]);
+    if (cudaMemcpy(s->table_d, t6.data(), t6.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
       rc = fail(s, MG_ECUDA, "table copy");
-    s->tr.table = s->table_d; s->tr.rows = p->table_rows;
+    s->tr.table = s->table_d; s->tr.rows = rows; s->tr.inv_dE = s->table_d + (size_t)rows * 5;
   }
   if (rc == MG_OK) {
     // initial state: n = 0, V linear in z; old level = state
@@ -897,6 +939,7 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     if (rc == MG_OK) copy_state_async(s, 0, true);
     if (rc == MG_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = fail(s, MG_ECUDA, "init sync");
   }
+  if (rc == MG_OK) rc = upload_level_set(s);
   if (rc == MG_OK) rc = setup_coarse_kernel(s);
   if (rc != MG_OK) {
     mg_destroy(s);
@@ -1130,7 +1173,7 @@ void mg_reset_stats(mg_state *s) {
 uint64_t mg_kernel_launches(void) { return (uint64_t)total_launches(); }
 
 int mg_profile_begin(mg_state *s, int kernel, int level) {
-  if (!s || kernel < MG_PROF_SMOOTH || kernel > MG_PROF_PROLONG || level < 0 || level >= s->nlev)
+  if (!s || kernel < MG_PROF_SMOOTH || kernel > MG_PROF_COARSE || level < 0 || level >= s->nlev)
     return fail(s, MG_EINVAL, "mg_profile_begin: bad kernel or level");
   if (s->prof_ev.empty()) {
     s->prof_ev.resize(2 * kProfMax);

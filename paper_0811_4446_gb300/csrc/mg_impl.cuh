@@ -32,6 +32,7 @@ struct Transport {
   const double *table;  // device, rows x 5 (|E|, mu_e, D_e, mu_p, D_p), or nullptr
   int rows;
   double inv_pf;        // 1 / pressure factor (applied to tabulated values)
+  const double *inv_dE; // device, 1 / (|E|_{k+1} - |E|_k) per table interval, or nullptr (divide)
 };
 
 // One multigrid level: geometry, state and work arrays (device pointers).
@@ -40,6 +41,8 @@ struct LevelT {
   int nr, nz, P;
   T dr;
   const T *dz, *dzc, *volr;  // nz, nz+1, nr+1 (geometry in the level's arithmetic type)
+  const T *idz;              // 1 / dz (nz entries)
+  T idr;                     // 1 / dr
   const T *wz;               // odd fine row j: weight of the upper coarse node (nz+1 entries)
   const T *gR, *gZ, *Ak;     // node arrays: r-face and z-face Poisson conductances, (e/eps0) A
   T *cr[NCOEF], *cz[NCOEF];  // face coefficients
@@ -73,6 +76,15 @@ struct StateView {           // nonlinear state on one level (FP64)
   const double *S[2];
 };
 
+// Views of every level in device memory, for the kernels that treat all levels of the
+// hierarchy in one launch (blockIdx.z selects the level).
+constexpr int kMaxLevelSet = 16;
+struct LevelSet {
+  LevelT<double> L[kMaxLevelSet];
+  LevelT<float> M[kMaxLevelSet];
+  StateView sv[kMaxLevelSet];
+};
+
 // Device-resident control block of one linear solve (device-side V-cycle loop in a CUDA graph).
 constexpr int kMaxHist = 512;
 struct SolveCtl {
@@ -96,6 +108,19 @@ cudaError_t launch_solve_init(SolveCtl *ctl, const double *norm3, cudaGraphCondi
 cudaError_t launch_solve_check(SolveCtl *ctl, const double *norm3, cudaGraphConditionalHandle h, cudaStream_t st);
 
 cudaError_t launch_coef(const Level &L, const StateView &sv, const Transport &tr, cudaStream_t st);
+// Residual rows from the face coefficients of the same state (launch_coef first): F, f = -F and
+// the norms as launch_residual, without re-evaluating the Scharfetter-Gummel faces.
+cudaError_t launch_resid_coef(const Level &L, const StateView &sv, double dt, bool write_f, double *Fout[3],
+                              double *partials, unsigned *counter, double *out6, cudaStream_t st);
+// Hierarchy set-up over levels of the device LevelSet in one launch each (L0 = the level whose
+// dimensions size the grid): injection of the state of level l0 into levels l0+1 .. l1, face
+// coefficients of levels a .. b, diagonal factors (and, mixed, the FP32 coefficient copies) of
+// levels a .. b.
+cudaError_t launch_inject_levels(const LevelSet *S, const Level &L0, int l0, int l1, cudaStream_t st);
+cudaError_t launch_coef_levels(const LevelSet *S, const Level &La, int a, int b, const Transport &tr,
+                               cudaStream_t st);
+cudaError_t launch_factor_levels(const LevelSet *S, const Level &La, int a, int b, bool mixed, double dt, double n0,
+                                 cudaStream_t st);
 // Diagonal-block factors of every unknown node from the FP64 face coefficients at step dt; with
 // M non-null also the FP32 copies in n0-scaled unknowns (mixed form).
 cudaError_t launch_factor(const Level &L, const LevelT<float> *M, double dt, double n0, cudaStream_t st);
@@ -109,8 +134,13 @@ cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx
 template <typename T>
 cudaError_t launch_sweep(const LevelT<T> &L, const SweepIO<T> &io, int shape, cudaStream_t st);
 // Coarse part of a V-cycle in one launch of a cluster of `cluster` CTAs (1..8) x `threads`.
+// smem_bytes > 0 with cluster == 1: the single-CTA form with every coarse array in shared
+// memory (prepare_coarse_smem gives the size, 0 if the set does not fit in `limit` bytes).
 template <typename T>
-cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, cudaStream_t st);
+cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, size_t smem_bytes,
+                                cudaStream_t st);
+template <typename T>
+size_t prepare_coarse_smem(const CoarseSet<T> &host_set, size_t limit);
 // r = f - J v (or out = J v when f == nullptr); optional per-field norms (sum of squares) -> out3
 template <typename T>
 cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,

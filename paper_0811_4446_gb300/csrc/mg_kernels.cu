@@ -129,6 +129,119 @@ __device__ __forceinline__ FaceTr tr_zface(const Level &L, const Transport &tr, 
   return lookup(tr, eabs_zface(L, V, j, i));
 }
 
+// ---- coefficient path with few FP64 divisions and transcendentals -----------------------------
+// FP64 arithmetic is the scarce resource of the face evaluation (the FP64 pipe issues one warp
+// instruction per SM sub-partition every 64 cycles on this part): the faces below use stored
+// reciprocals of the spacings and table intervals, and one exponential and one division per
+// Bernoulli pair.  For y = |x| >= 0.1: e = 1 - e^{-y} from expm1 when y < 0.5 (then e^{-y} =
+// 1 - e > 0.6 is exact to an ulp) and from exp otherwise (then e > 0.39 is), so both keep full
+// relative accuracy; B(y) = y e^{-y} / e, B'(y) = e^{-y} (e - y) / e^2.
+__device__ __forceinline__ Bern bernoulli1(double x) {
+  const double y = fabs(x);
+  double by, dby;
+  if (y < 0.1) {
+    const double y2 = y * y;
+    const double even =
+        1.0 + y2 * (1.0 / 12.0 +
+                    y2 * (-1.0 / 720.0 + y2 * (1.0 / 30240.0 + y2 * (-1.0 / 1209600.0 + y2 * (1.0 / 47900160.0)))));
+    by = even - 0.5 * y;
+    const double odd =
+        y * (1.0 / 6.0 + y2 * (-1.0 / 180.0 + y2 * (1.0 / 5040.0 + y2 * (-1.0 / 151200.0 + y2 * (1.0 / 4790016.0)))));
+    dby = odd - 0.5;
+  } else {
+    double t, em;
+    if (y < 0.5) { em = -expm1(-y); t = 1.0 - em; }
+    else { t = exp(-y); em = 1.0 - t; }
+    const double ie = 1.0 / em;
+    const double tie = t * ie;
+    by = y * tie;
+    dby = tie * (em - y) * ie;
+  }
+  Bern b;
+  if (x >= 0.0) {
+    b.Bp = by; b.Bm = by + y; b.dBp = dby; b.dBm = -dby - 1.0;
+  } else {
+    b.Bp = by + y; b.Bm = by; b.dBp = -dby - 1.0; b.dBm = dby;
+  }
+  return b;
+}
+
+__device__ __forceinline__ FaceTr lookup1(const Transport &tr, double Eabs) {
+  const double *T = tr.table;
+  const int n = tr.rows;
+  const double x = fmin(fmax(Eabs, __ldg(T)), __ldg(T + 5 * (n - 1)));
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(T + 5 * mid) <= x) lo = mid; else hi = mid;
+  }
+  const double *a = T + 5 * lo, *b = a + 5;
+  const double t = (x - __ldg(a)) * __ldg(tr.inv_dE + lo);
+  FaceTr f;
+  f.mu_e = (__ldg(a + 1) + t * (__ldg(b + 1) - __ldg(a + 1))) * tr.inv_pf;
+  f.D_e = (__ldg(a + 2) + t * (__ldg(b + 2) - __ldg(a + 2))) * tr.inv_pf;
+  f.mu_p = (__ldg(a + 3) + t * (__ldg(b + 3) - __ldg(a + 3))) * tr.inv_pf;
+  f.D_p = (__ldg(a + 4) + t * (__ldg(b + 4) - __ldg(a + 4))) * tr.inv_pf;
+  return f;
+}
+
+// |E| on the r-face (i+1/2, j) and the z-face (i, j+1/2), as eabs_rface / eabs_zface.
+__device__ __forceinline__ double eabs_r1(const Level &L, const double *V, int j, size_t k) {
+  const int P = L.P;
+  const double En = (V[k] - V[k + 1]) * L.idr;
+  const double lo = (V[k - P] - V[k]) + (V[k + 1 - P] - V[k + 1]);
+  const double up = (V[k] - V[k + P]) + (V[k + 1] - V[k + 1 + P]);
+  const double Et = 0.25 * (lo * L.idz[j - 1] + up * L.idz[j]);
+  return sqrt(En * En + Et * Et);
+}
+__device__ __forceinline__ double eabs_z1(const Level &L, const double *V, int j, int i, size_t k) {
+  const int P = L.P;
+  const double En = (V[k] - V[k + P]) * L.idz[j];
+  double Et = 0.0;
+  if (i > 0 && i < L.nr)
+    Et = 0.25 * L.idr * ((V[k - 1] - V[k + 1]) + (V[k + P - 1] - V[k + P + 1]));
+  return sqrt(En * En + Et * Et);
+}
+
+// Face coefficients (cG, cF, cV) of both species on one face.
+__device__ __forceinline__ void face_coefs(const Transport &tr, bool table, double Eabs, double g, double dV,
+                                           double neL, double neR, double npL, double npR, double (&c)[NCOEF]) {
+  const FaceTr t = table ? lookup1(tr, Eabs) : FaceTr{tr.mu_e, tr.D_e, tr.mu_p, tr.D_p};
+  {
+    const Bern b = bernoulli1((t.mu_e / t.D_e) * dV);  // electrons: s = -1
+    const double gD = g * t.D_e;
+    c[CGE] = gD * b.Bm; c[CFE] = gD * b.Bp;
+    c[CVE] = -g * t.mu_e * (neL * b.dBm + neR * b.dBp);
+  }
+  {
+    const Bern b = bernoulli1(-(t.mu_p / t.D_p) * dV);  // ions: s = +1
+    const double gD = g * t.D_p;
+    c[CGP] = gD * b.Bm; c[CFP] = gD * b.Bp;
+    c[CVP] = g * t.mu_p * (npL * b.dBm + npR * b.dBp);
+  }
+}
+
+// East r-face and north z-face coefficients of node (i, j) of level L (face conductances g:
+// the stored Poisson ones, (i + 1/2) dz_c and vol_r / dz).
+__device__ __forceinline__ void coef_node(const Level &L, const StateView &sv, const Transport &tr, int i, int j) {
+  const size_t k = (size_t)j * L.P + i;
+  const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
+  const bool table = tr.table != nullptr;
+  double c[NCOEF];
+  if (i < L.nr && j >= 1 && j < L.nz) {
+    face_coefs(tr, table, table ? eabs_r1(L, V, j, k) : 0.0, L.gR[k], V[k + 1] - V[k], ne[k], ne[k + 1], np[k],
+               np[k + 1], c);
+#pragma unroll
+    for (int a = 0; a < NCOEF; ++a) L.cr[a][k] = c[a];
+  }
+  if (j < L.nz) {
+    face_coefs(tr, table, table ? eabs_z1(L, V, j, i, k) : 0.0, L.gZ[k], V[k + L.P] - V[k], ne[k], ne[k + L.P],
+               np[k], np[k + L.P], c);
+#pragma unroll
+    for (int a = 0; a < NCOEF; ++a) L.cz[a][k] = c[a];
+  }
+}
+
 // SG flux through a face from L to R (eqs. 8-11): alpha = -s (mu/D)(V_R - V_L),
 // flux = g D (n_L G(alpha) - n_R F(alpha)).
 __device__ __forceinline__ double sg_flux(double g, double mu, double D, double s, double nL, double nR,
@@ -214,37 +327,116 @@ __device__ void reduce_finish(double (&v)[K], double *partials, unsigned *counte
 
 // ------------------------------------------------------------------------------------------
 // K1: face coefficients (eqs. 8-11 differentiated) for the east r-face and north z-face of each node.
-__global__ void k_coef(Level L, StateView sv, Transport tr) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+constexpr int CBY = 2;  // 32 x 2 threads: the FP64-bound set-up kernels spread over every SM
+
+__global__ void __launch_bounds__(32 * CBY) k_coef(Level L, StateView sv, Transport tr) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * CBY + threadIdx.y;
   if (i > L.nr || j > L.nz) return;
-  const size_t k = (size_t)j * L.P + i;
-  const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
-  if (i < L.nr && j >= 1 && j < L.nz) {
-    const double g = (i + 0.5) * L.dzc[j];
-    const FaceTr t = tr_rface(L, tr, V, j, i);
-    const double dV = V[k + 1] - V[k];
-    double cG, cF, cV;
-    sg_coef(g, t.mu_e, t.D_e, -1.0, ne[k], ne[k + 1], dV, cG, cF, cV);
-    L.cr[CGE][k] = cG; L.cr[CFE][k] = cF; L.cr[CVE][k] = cV;
-    sg_coef(g, t.mu_p, t.D_p, 1.0, np[k], np[k + 1], dV, cG, cF, cV);
-    L.cr[CGP][k] = cG; L.cr[CFP][k] = cF; L.cr[CVP][k] = cV;
-  }
-  if (j < L.nz) {
-    const double g = L.volr[i] / L.dz[j];
-    const FaceTr t = tr_zface(L, tr, V, j, i);
-    const double dV = V[k + L.P] - V[k];
-    double cG, cF, cV;
-    sg_coef(g, t.mu_e, t.D_e, -1.0, ne[k], ne[k + L.P], dV, cG, cF, cV);
-    L.cz[CGE][k] = cG; L.cz[CFE][k] = cF; L.cz[CVE][k] = cV;
-    sg_coef(g, t.mu_p, t.D_p, 1.0, np[k], np[k + L.P], dV, cG, cF, cV);
-    L.cz[CGP][k] = cG; L.cz[CFP][k] = cF; L.cz[CVP][k] = cV;
-  }
+  coef_node(L, sv, tr, i, j);
 }
 
 cudaError_t launch_coef(const Level &L, const StateView &sv, const Transport &tr, cudaStream_t st) {
-  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
+  dim3 b(32, CBY), g((L.nr + 1 + 31) / 32, (L.nz + 1 + CBY - 1) / CBY);
   k_coef<<<g, b, 0, st>>>(L, sv, tr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// All levels a .. b in one launch (grid sized by level a, the largest).
+__global__ void __launch_bounds__(32 * CBY) k_coef_levels(const LevelSet *__restrict__ S, int a, Transport tr) {
+  const int l = a + blockIdx.z;
+  const Level &L = S->L[l];
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * CBY + threadIdx.y;
+  if (i > L.nr || j > L.nz) return;
+  coef_node(L, S->sv[l], tr, i, j);
+}
+
+cudaError_t launch_coef_levels(const LevelSet *S, const Level &La, int a, int b, const Transport &tr,
+                               cudaStream_t st) {
+  if (b < a) return cudaSuccess;
+  dim3 bl(32, CBY), g((La.nr + 1 + 31) / 32, (La.nz + 1 + CBY - 1) / CBY, b - a + 1);
+  k_coef_levels<<<g, bl, 0, st>>>(S, a, tr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Injection of the state of level l0 into levels l0 + 1 .. l1 (node (I, J) of level l is node
+// (I, J) x 2^(l - l0) of level l0 on the nested grids).
+__global__ void k_inject_levels(const LevelSet *__restrict__ S, int l0) {
+  const int l = l0 + 1 + blockIdx.z;
+  const Level &C = S->L[l];
+  const int I = blockIdx.x * 32 + threadIdx.x;
+  const int J = blockIdx.y * CBY + threadIdx.y;
+  if (I > C.nr || J > C.nz) return;
+  const int sh = l - l0;
+  const size_t kc = (size_t)J * C.P + I, kf = ((size_t)J << sh) * S->L[l0].P + ((size_t)I << sh);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) S->sv[l].u[q][kc] = S->sv[l0].u[q][kf];
+}
+
+cudaError_t launch_inject_levels(const LevelSet *S, const Level &L0, int l0, int l1, cudaStream_t st) {
+  if (l1 <= l0) return cudaSuccess;
+  const int nr = L0.nr / 2, nz = L0.nz / 2;
+  dim3 bl(32, CBY), g((nr + 1 + 31) / 32, (nz + 1 + CBY - 1) / CBY, l1 - l0);
+  k_inject_levels<<<g, bl, 0, st>>>(S, l0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// K2': nonlinear residual from the face coefficients of the same state: the SG flux through a
+// face is cG n_L - cF n_R (cG = g D G(alpha), cF = g D F(alpha)), the Poisson flux g dV.
+__global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, double dt_inv, int write_f,
+                                                         double *F0, double *F1, double *F2, double *partials,
+                                                         unsigned *counter, double *out6) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (i <= L.nr && j < L.nz) {
+    const int P = L.P;
+    const size_t k = (size_t)j * P + i;
+    const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
+    const double A = L.volr[i] * L.dzc[j];
+    double Fe = 0, Fp = 0, FV = 0, Te = 0, Tp = 0, TV = 0;
+    if (dt_inv > 0.0) {
+      Fe += A * (ne[k] - sv.uold[NE][k]) * dt_inv;
+      Fp += A * (np[k] - sv.uold[NP][k]) * dt_inv;
+      Te += A * (fabs(ne[k]) + fabs(sv.uold[NE][k])) * dt_inv;
+      Tp += A * (fabs(np[k]) + fabs(sv.uold[NP][k])) * dt_inv;
+    }
+    Fe -= A * sv.S[0][k];
+    Fp -= A * sv.S[1][k];
+    Te += A * fabs(sv.S[0][k]);
+    Tp += A * fabs(sv.S[1][k]);
+    auto face = [&](double *const *c, const double *gp, size_t kL, size_t kR, size_t kc, double sgn) {
+      const double pe = c[CGE][kc] * ne[kL] - c[CFE][kc] * ne[kR];
+      const double pp = c[CGP][kc] * np[kL] - c[CFP][kc] * np[kR];
+      const double ps = gp[kc] * (V[kR] - V[kL]);
+      Fe += sgn * pe; Fp += sgn * pp; FV += sgn * ps;
+      Te += fabs(pe); Tp += fabs(pp); TV += fabs(ps);
+    };
+    if (i < L.nr) face(L.cr, L.gR, k, k + 1, k, 1.0);
+    if (i > 0) face(L.cr, L.gR, k - 1, k, k - 1, -1.0);
+    face(L.cz, L.gZ, k, k + P, k, 1.0);
+    face(L.cz, L.gZ, k - P, k, k - P, -1.0);
+    const double ak = L.Ak[k];
+    FV += ak * (np[k] - ne[k]);
+    TV += ak * (fabs(np[k]) + fabs(ne[k]));
+    if (write_f) { L.f[NE][k] = -Fe; L.f[NP][k] = -Fp; L.f[NV][k] = -FV; }
+    if (F0) { F0[k] = Fe; F1[k] = Fp; F2[k] = FV; }
+    acc[0] = Fe * Fe; acc[1] = Fp * Fp; acc[2] = FV * FV;
+    acc[3] = Te * Te; acc[4] = Tp * Tp; acc[5] = TV * TV;
+  }
+  reduce_finish<6>(acc, partials, counter, out6, 0);
+}
+
+cudaError_t launch_resid_coef(const Level &L, const StateView &sv, double dt, bool write_f, double *Fout[3],
+                              double *partials, unsigned *counter, double *out6, cudaStream_t st) {
+  dim3 b(32, CBY), g((L.nr + 1 + 31) / 32, (L.nz - 1 + CBY - 1) / CBY);
+  k_resid_coef<<<g, b, 0, st>>>(L, sv, dt > 0 ? 1.0 / dt : 0.0, write_f ? 1 : 0, Fout ? Fout[0] : nullptr,
+                                Fout ? Fout[1] : nullptr, Fout ? Fout[2] : nullptr, partials, counter, out6);
   count_launch();
   return cudaGetLastError();
 }
@@ -323,10 +515,8 @@ cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport
 //   a13 = -sum(cV_e over the four faces), a33 = -sum(g), ak = A e/eps0 (ions likewise),
 // and is solved through its Schur complement in V:
 //   xV = (rV - q1 re - q2 rp) / s,  s = a33 - q1 a13 - q2 a23,  q1 = -ak/a11,  q2 = ak/a22.
-__global__ void k_factor(Level L, LevelT<float> M, int mixed, double dt_inv, double n0) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i > L.nr || j >= L.nz) return;
+__device__ __forceinline__ void factor_node(const Level &L, const LevelT<float> &M, int mixed, double dt_inv,
+                                            double n0, int i, int j) {
   const int P = L.P;
   const size_t k = (size_t)j * P + i;
   const double A = L.volr[i] * L.dzc[j];
@@ -354,6 +544,46 @@ __global__ void k_factor(Level L, LevelT<float> M, int mixed, double dt_inv, dou
     M.fac[FA13][k] = (float)(a13 / n0); M.fac[FA23][k] = (float)(a23 / n0);
     M.dia[DA11][k] = (float)a11; M.dia[DA22][k] = (float)a22; M.dia[DA33][k] = (float)a33;
   }
+}
+
+__global__ void k_factor(Level L, LevelT<float> M, int mixed, double dt_inv, double n0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (i > L.nr || j >= L.nz) return;
+  factor_node(L, M, mixed, dt_inv, n0, i, j);
+}
+
+// Mixed form: FP64 face coefficients of node (i, j) -> FP32 copies in the n0-scaled unknowns
+// (density unknowns and density rows divided by n0: cG, cF unchanged, cV / n0).
+__device__ __forceinline__ void coef_to32_node(const Level &L, const LevelT<float> &M, double inv_n0, size_t k) {
+#pragma unroll
+  for (int c = 0; c < NCOEF; ++c) {
+    const double sc = (c == CVE || c == CVP) ? inv_n0 : 1.0;
+    M.cr[c][k] = (float)(L.cr[c][k] * sc);
+    M.cz[c][k] = (float)(L.cz[c][k] * sc);
+  }
+}
+
+// Levels a .. b in one launch: diagonal factors of the unknown rows and, mixed, the FP32
+// coefficient copies of every row.
+__global__ void __launch_bounds__(32 * CBY) k_factor_levels(const LevelSet *__restrict__ S, int a, int mixed,
+                                                            double dt_inv, double n0) {
+  const int l = a + blockIdx.z;
+  const Level &L = S->L[l];
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * CBY + threadIdx.y;
+  if (i > L.nr || j > L.nz) return;
+  if (mixed) coef_to32_node(L, S->M[l], 1.0 / n0, (size_t)j * L.P + i);
+  if (j >= 1 && j < L.nz) factor_node(L, S->M[l], mixed, dt_inv, n0, i, j);
+}
+
+cudaError_t launch_factor_levels(const LevelSet *S, const Level &La, int a, int b, bool mixed, double dt, double n0,
+                                 cudaStream_t st) {
+  if (b < a) return cudaSuccess;
+  dim3 bl(32, CBY), g((La.nr + 1 + 31) / 32, (La.nz + 1 + CBY - 1) / CBY, b - a + 1);
+  k_factor_levels<<<g, bl, 0, st>>>(S, a, mixed ? 1 : 0, dt > 0 ? 1.0 / dt : 0.0, n0);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_factor(const Level &L, const LevelT<float> *M, double dt, double n0, cudaStream_t st) {
@@ -748,23 +978,17 @@ cudaError_t launch_prolong_state(const Level &C, const StateView &cs, const Leve
 constexpr int CT = 256;
 constexpr int kSmemGJ = 48;
 
-__global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, double *M, double *Minv,
-                                                      double *rs, double *cs, int *flag) {
+// Adds the Jacobian entries of the coarsest level into A (row-major, leading dimension ld,
+// zeroed by the caller); thread tid of nthr assembles the rows of nodes tid, tid + nthr, ...
+__device__ void assemble_coarse(const Level &L, double dt_inv, double *A, int ld, int tid, int nthr) {
   const int nn = (L.nr + 1) * (L.nz - 1);
-  const int n = 3 * nn;
-  const int tid = threadIdx.x;
-  __shared__ double fac[3 * 9 * 9];
-  __shared__ double pv[CT];
-  __shared__ int pi[CT];
-  for (int e = tid; e < n * n; e += CT) { M[e] = 0.0; Minv[e] = 0.0; }
-  __syncthreads();
-  for (int node = tid; node < nn; node += CT) {
+  for (int node = tid; node < nn; node += nthr) {
     const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
     const size_t k = (size_t)j * L.P + i;
-    const double A = L.volr[i] * L.dzc[j];
-    double a11 = A * dt_inv, a22 = A * dt_inv, a13 = 0, a23 = 0, a33 = 0;
+    const double Av = L.volr[i] * L.dzc[j];
+    double a11 = Av * dt_inv, a22 = Av * dt_inv, a13 = 0, a23 = 0, a33 = 0;
     const int re = 3 * node, rp = re + 1, rv = re + 2;
-    auto put = [&](int row, int col, double v) { M[(size_t)row * n + col] += v; };
+    auto put = [&](int row, int col, double v) { A[(size_t)row * ld + col] += v; };
     // east
     if (i < L.nr) {
       const int nb = 3 * (node + 1);
@@ -806,8 +1030,106 @@ __global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, do
     }
     put(re, re, a11); put(re, rv, a13);
     put(rp, rp, a22); put(rp, rv, a23);
-    put(rv, re, -A * kKappa); put(rv, rp, A * kKappa); put(rv, rv, a33);
+    put(rv, re, -Av * kKappa); put(rv, rp, Av * kKappa); put(rv, rv, a33);
   }
+}
+
+// n <= 48 unknowns (the usual 5^2-node coarsest level has n = 45): the augmented matrix
+// [A | I] (n x 2n) lives in shared memory from assembly to the inverse.  Per pivot column one
+// warp finds the pivot, swaps and scales the pivot row, then four threads per row eliminate
+// the remaining columns; entries left of the pivot column are never read again and are not
+// updated, so the multiplier A[r][col] stays intact during its step (two barriers per column).
+__global__ void __launch_bounds__(CT) k_coarse_factor_smem(Level L, double dt_inv, double *Minv, double *rs,
+                                                           double *cs, int *flag) {
+  const int n = 3 * (L.nr + 1) * (L.nz - 1);
+  const int W = 2 * n;
+  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ double sAB[kSmemGJ * 2 * kSmemGJ];
+  __shared__ double srs[kSmemGJ], scs[kSmemGJ];
+  __shared__ int sp;
+  for (int e = tid; e < n * W; e += CT) sAB[e] = 0.0;
+  __syncthreads();
+  assemble_coarse(L, dt_inv, sAB, W, tid, CT);
+  __syncthreads();
+  // equilibration: columns, then rows; identity on the right
+  if (tid < n) {
+    double m = 0.0;
+    for (int r = 0; r < n; ++r) m = fmax(m, fabs(sAB[r * W + tid]));
+    scs[tid] = m > 0.0 ? 1.0 / m : 1.0;
+  }
+  __syncthreads();
+  if (tid < n) {
+    double m = 0.0;
+    for (int c = 0; c < n; ++c) m = fmax(m, fabs(sAB[tid * W + c] * scs[c]));
+    srs[tid] = m > 0.0 ? 1.0 / m : 1.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += CT) {
+    const int r = e / n, c = e - r * n;
+    sAB[r * W + c] *= srs[r] * scs[c];
+    sAB[r * W + n + c] = (r == c) ? 1.0 : 0.0;
+  }
+  if (tid < n) { rs[tid] = srs[tid]; cs[tid] = scs[tid]; }
+  __syncthreads();
+  const int er = tid >> 2, ec = tid & 3;  // elimination: row er, columns col+1+ec, +4, ...
+  for (int col = 0; col < n; ++col) {
+    if (tid < 32) {  // pivot search, ties: lowest row index
+      double best = -1.0;
+      int bi = col;
+      for (int r = col + lane; r < n; r += 32) {
+        const double v = fabs(sAB[r * W + col]);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (best > 0.0) {
+        if (bi != col)
+          for (int c = col + lane; c < W; c += 32) {
+            const double t = sAB[bi * W + c];
+            sAB[bi * W + c] = sAB[col * W + c];
+            sAB[col * W + c] = t;
+          }
+        __syncwarp();
+        const double piv = 1.0 / sAB[col * W + col];
+        __syncwarp();
+        for (int c = col + 1 + lane; c < W; c += 32) sAB[col * W + c] *= piv;
+      }
+      if (lane == 0) sp = best > 0.0 ? bi : -1;
+    }
+    __syncthreads();
+    if (sp < 0) {
+      if (tid == 0) *flag = 1;
+      return;
+    }
+    if (er < n && er != col) {
+      const double fr = sAB[er * W + col];
+      if (fr != 0.0)
+        for (int c = col + 1 + ec; c < W; c += 4) sAB[er * W + c] -= fr * sAB[col * W + c];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * n; e += CT) {
+    const int r = e / n, c = e - r * n;
+    Minv[e] = sAB[r * W + n + c];
+  }
+  if (tid == 0) *flag = 0;
+}
+
+// Larger coarsest levels: the same steps in global memory (M is n x n scratch).
+__global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, double *M, double *Minv,
+                                                      double *rs, double *cs, int *flag) {
+  const int nn = (L.nr + 1) * (L.nz - 1);
+  const int n = 3 * nn;
+  const int tid = threadIdx.x;
+  __shared__ double fac[3 * 9 * 9];
+  __shared__ double pv[CT];
+  __shared__ int pi[CT];
+  for (int e = tid; e < n * n; e += CT) { M[e] = 0.0; Minv[e] = 0.0; }
+  __syncthreads();
+  assemble_coarse(L, dt_inv, M, n, tid, CT);
   __syncthreads();
   // equilibration: columns, then rows
   for (int c = tid; c < n; c += CT) {
@@ -828,58 +1150,6 @@ __global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, do
     Minv[e] = (r == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  if (n <= kSmemGJ) {
-    // Gauss-Jordan in shared memory (the usual 5^2-node coarsest level has n = 45)
-    __shared__ double sA[kSmemGJ * kSmemGJ], sB[kSmemGJ * kSmemGJ];
-    __shared__ int sp;
-    for (int e = tid; e < n * n; e += CT) { sA[e] = M[e]; sB[e] = Minv[e]; }
-    __syncthreads();
-    for (int col = 0; col < n; ++col) {
-      if (tid < 32) {  // pivot search by one warp, ties: lowest row index
-        double best = -1.0;
-        int bi = col;
-        for (int r = col + tid; r < n; r += 32) {
-          const double v = fabs(sA[r * n + col]);
-          if (v > best) { best = v; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_down_sync(0xffffffffu, best, o);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (tid == 0) sp = best > 0.0 ? bi : -1;
-      }
-      __syncthreads();
-      const int p = sp;
-      if (p < 0) { if (tid == 0) *flag = 1; return; }
-      if (p != col) {
-        for (int c = tid; c < n; c += CT) {
-          double t = sA[p * n + c]; sA[p * n + c] = sA[col * n + c]; sA[col * n + c] = t;
-          t = sB[p * n + c]; sB[p * n + c] = sB[col * n + c]; sB[col * n + c] = t;
-        }
-      }
-      __syncthreads();
-      const double piv = 1.0 / sA[col * n + col];
-      __syncthreads();
-      for (int c = tid; c < n; c += CT) { sA[col * n + c] *= piv; sB[col * n + c] *= piv; }
-      __syncthreads();
-      for (int r = tid; r < n; r += CT) fac[r] = (r == col) ? 0.0 : sA[r * n + col];
-      __syncthreads();
-      for (int e = tid; e < n * n; e += CT) {
-        const int r = e / n, c = e % n;
-        const double fr = fac[r];
-        if (fr != 0.0) {
-          sA[e] -= fr * sA[col * n + c];
-          sB[e] -= fr * sB[col * n + c];
-        }
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < n * n; e += CT) Minv[e] = sB[e];
-    if (tid == 0) *flag = 0;
-    return;
-  }
-  // larger coarsest levels: the same elimination in global memory
   // Gauss-Jordan with partial pivoting (ties: lowest row index)
   for (int col = 0; col < n; ++col) {
     double best = -1.0;
@@ -929,7 +1199,9 @@ cudaError_t launch_coarse_factor(const Level &L, double dt, double *M, double *M
                                  int *flag, cudaStream_t st) {
   const int n = 3 * (L.nr + 1) * (L.nz - 1);
   if (n > 3 * 9 * 9) return cudaErrorInvalidValue;
-  k_coarse_factor<<<1, CT, 0, st>>>(L, dt > 0 ? 1.0 / dt : 0.0, M, Minv, rs, cs, flag);
+  const double dti = dt > 0 ? 1.0 / dt : 0.0;
+  if (n <= kSmemGJ) k_coarse_factor_smem<<<1, CT, 0, st>>>(L, dti, Minv, rs, cs, flag);
+  else k_coarse_factor<<<1, CT, 0, st>>>(L, dti, M, Minv, rs, cs, flag);
   count_launch();
   return cudaGetLastError();
 }
@@ -1024,8 +1296,119 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
   }
 }
 
+// Single-CTA form of K8 with every array of the coarse levels in shared memory: the
+// coefficient, factor and conductance arrays are copied in at the start (constant during a
+// linear solve), so are the corrections and the right-hand side of the first level, and its
+// correction is copied back at the end (the prolongation to the next finer level reads it).  The phases are those of k_coarse_cycle; what changes is only where the
+// arrays live, which turns each phase's dependent global-memory reads into shared-memory ones.
+constexpr int kCoarseFields = 2 * NCOEF + NFAC + NDIA + 3 + 9;  // + gR gZ Ak, du f r
+
 template <typename T>
-cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, cudaStream_t st) {
+size_t coarse_smem_bytes(const CoarseSet<T> &S) {
+  size_t n = 0;
+  for (int q = 0; q < S.n; ++q) n += (size_t)(S.lv[q].nz + 1) * S.lv[q].P;
+  return n * kCoarseFields * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *__restrict__ sp) {
+  extern __shared__ __align__(16) unsigned char cc_smem[];
+  __shared__ LevelT<T> lv[kMaxCoarseSet];
+  const CoarseSet<T> &G = *sp;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) {
+    T *p = reinterpret_cast<T *>(cc_smem);
+    for (int q = 0; q < G.n; ++q) {
+      LevelT<T> v = G.lv[q];
+      const size_t nodes = (size_t)(v.nz + 1) * v.P;
+      auto take = [&]() { T *r = p; p += nodes; return r; };
+      for (int a = 0; a < NCOEF; ++a) v.cr[a] = take();
+      for (int a = 0; a < NCOEF; ++a) v.cz[a] = take();
+      for (int a = 0; a < NFAC; ++a) v.fac[a] = take();
+      for (int a = 0; a < NDIA; ++a) v.dia[a] = take();
+      v.gR = take(); v.gZ = take(); v.Ak = take();
+      for (int a = 0; a < 3; ++a) { v.du[a] = take(); v.f[a] = take(); v.r[a] = take(); v.du2[a] = nullptr; }
+      lv[q] = v;
+    }
+  }
+  __syncthreads();
+  // copy-in with asynchronous 16-byte copies (every array is a multiple of 16 bytes long and
+  // 16-byte aligned at both ends), all issued before one wait
+  for (int q = 0; q < G.n; ++q) {
+    const LevelT<T> &g = G.lv[q];
+    const LevelT<T> &v = lv[q];
+    const int chunks = (int)((size_t)(g.nz + 1) * g.P * sizeof(T) / 16);
+    auto copy = [&](const T *dst, const T *src) {
+      const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+      const char *sp = reinterpret_cast<const char *>(src);
+      for (int c = tid; c < chunks; c += nth)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * c), "l"(sp + 16 * (size_t)c)
+                     : "memory");
+    };
+    for (int a = 0; a < NCOEF; ++a) { copy(v.cr[a], g.cr[a]); copy(v.cz[a], g.cz[a]); }
+    for (int a = 0; a < NFAC; ++a) copy(v.fac[a], g.fac[a]);
+    for (int a = 0; a < NDIA; ++a) copy(v.dia[a], g.dia[a]);
+    copy(v.gR, g.gR); copy(v.gZ, g.gZ); copy(v.Ak, g.Ak);
+    // the first level's correction is the current iterate when the set's first level is the
+    // root of the solve; the coarser ones are overwritten by the restriction except for their
+    // (zero) electrode rows
+    for (int a = 0; a < 3; ++a) {
+      if (q == 0) copy(v.f[a], g.f[a]);
+      copy(v.du[a], g.du[a]);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  auto sweeps = [&](const LevelT<T> &L, int nu) {
+    const int half = (L.nr + 2) / 2;
+    for (int it = 0; it < nu; ++it)
+      for (int color = 0; color < 2; ++color) {
+        for (int t = tid; t < (L.nz - 1) * half; t += nth) {
+          const int j = t / half + 1, i = 2 * (t % half) + ((j + color) & 1);
+          if (i <= L.nr) smooth_node<T>(L, i, j);
+        }
+        __syncthreads();
+      }
+  };
+  for (int q = 0; q + 1 < G.n; ++q) {
+    const LevelT<T> &L = lv[q];
+    const LevelT<T> &C = lv[q + 1];
+    sweeps(L, G.nu1);
+    const int W = L.nr + 1;
+    for (int t = tid; t < (L.nz - 1) * W; t += nth) {
+      const int j = t / W + 1, i = t % W;
+      linres_node<T>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP], L.f[NV], L.r[NE], L.r[NP], L.r[NV]);
+    }
+    __syncthreads();
+    const int Wc = C.nr + 1;
+    for (int t = tid; t < (C.nz - 1) * Wc; t += nth) restrict_node<T>(L, C, t % Wc, t / Wc + 1);
+    __syncthreads();
+  }
+  coarse_solve_block<T>(lv[G.n - 1], G.Minv, G.rs, G.cs, G.nscale, nth);
+  __syncthreads();
+  for (int q = G.n - 2; q >= 0; --q) {
+    const LevelT<T> &F = lv[q];
+    const int W = F.nr + 1;
+    for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(lv[q + 1], F, t % W, t / W + 1);
+    __syncthreads();
+    sweeps(F, G.nu2);
+  }
+  {
+    const LevelT<T> &g = G.lv[0];
+    const int nodes = (g.nz + 1) * g.P;
+    for (int a = 0; a < 3; ++a)
+      for (int e = tid; e < nodes; e += nth) g.du[a][e] = lv[0].du[a][e];
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, size_t smem_bytes,
+                                cudaStream_t st) {
+  if (cluster == 1 && smem_bytes > 0) {
+    k_coarse_cycle_smem<T><<<1, threads, smem_bytes, st>>>(dev_set);
+    count_launch();
+    return cudaGetLastError();
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
@@ -1042,8 +1425,22 @@ cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int th
   count_launch();
   return e;
 }
-template cudaError_t launch_coarse_cycle<double>(const CoarseSet<double> *, int, int, cudaStream_t);
-template cudaError_t launch_coarse_cycle<float>(const CoarseSet<float> *, int, int, cudaStream_t);
+template cudaError_t launch_coarse_cycle<double>(const CoarseSet<double> *, int, int, size_t, cudaStream_t);
+template cudaError_t launch_coarse_cycle<float>(const CoarseSet<float> *, int, int, size_t, cudaStream_t);
+
+// Shared memory of the single-CTA coarse cycle for a set (0 when it does not fit); sets the
+// kernel's dynamic shared-memory limit.
+template <typename T>
+size_t prepare_coarse_smem(const CoarseSet<T> &S, size_t limit) {
+  const size_t b = coarse_smem_bytes(S);
+  if (b > limit) return 0;
+  if (cudaFuncSetAttribute(k_coarse_cycle_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) !=
+      cudaSuccess)
+    return 0;
+  return b;
+}
+template size_t prepare_coarse_smem<double>(const CoarseSet<double> &, size_t);
+template size_t prepare_coarse_smem<float>(const CoarseSet<float> &, size_t);
 
 template <typename T>
 cudaError_t launch_coarse_solve(const LevelT<T> &L, const double *Minv, const double *rs, const double *cs,
@@ -1115,19 +1512,12 @@ template cudaError_t launch_zero_du<double>(const LevelT<double> &, cudaStream_t
 template cudaError_t launch_zero_du<float>(const LevelT<float> &, cudaStream_t);
 
 // ------------------------------------------------------------------------------------------
-// Mixed form.  FP64 face coefficients of one level -> FP32 copies in the n0-scaled unknowns
-// (density unknowns and density rows divided by n0: cG, cF unchanged, cV / n0).
+// Mixed form.  FP64 face coefficients of one level -> FP32 copies (coef_to32_node).
 __global__ void k_coef_to32(Level L, LevelT<float> M, double inv_n0) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i > L.nr || j > L.nz) return;
-  const size_t k = (size_t)j * L.P + i;
-#pragma unroll
-  for (int c = 0; c < NCOEF; ++c) {
-    const double sc = (c == CVE || c == CVP) ? inv_n0 : 1.0;
-    M.cr[c][k] = (float)(L.cr[c][k] * sc);
-    M.cz[c][k] = (float)(L.cz[c][k] * sc);
-  }
+  coef_to32_node(L, M, inv_n0, (size_t)j * L.P + i);
 }
 
 cudaError_t launch_coef_to32(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st) {
@@ -1284,8 +1674,9 @@ double probe_fp64_gflops(cudaStream_t st) {
 // Some callers cannot allocate device memory: code that runs inside another framework's
 // memory pool or a real-time loop where cudaMalloc is forbidden or would synchronise the
 // device, and plug-ins that may only use the buffers their host hands them.  For them this
-// entry point evaluates the same residual rows and norms as mg_residual with the same kernel
-// (k_residual) on caller-owned input and output arrays, and keeps its own scratch (geometry,
+// entry point evaluates the same residual rows and norms as mg_residual (up to rounding: it
+// evaluates every face directly with k_residual instead of through stored face coefficients)
+// on caller-owned input and output arrays, and keeps its own scratch (geometry,
 // transport table, block partial sums, reduction counter and results) in the file-scope
 // device array below.  Every GPU that loads this library holds that array until the process
 // exits.  All calls share it and it keeps the last call's contents: calls that overlap on the
@@ -1388,6 +1779,7 @@ extern "C" int mg_residual_noalloc(const mg_grid *g, const mg_params *p, const d
   tr.inv_pf = 1.0 / p->pressure_factor;
   tr.table = p->table ? base + kOffTable : nullptr;
   tr.rows = p->table ? p->table_rows : 0;
+  tr.inv_dE = nullptr;
   double *Fo[3] = {F_ne, F_np, F_V};
   if (launch_residual(L, sv, tr, dt, false, F_ne ? Fo : nullptr, base + kOffPartials,
                       reinterpret_cast<unsigned *>(base + kOffCounter), base + kOffOut, st) != cudaSuccess)

@@ -3,10 +3,11 @@
 // Implicit-GEMM convolution, one CTA per 128-row output tile:
 //   * four warps gather the A tile (128 rows x 64 k of bf16, im2col on the fly, zero padding)
 //     and the B tile (N rows x 64 k of the [N][K] weight copy) into shared memory with
-//     cp.async, in the 128-byte-swizzled K-major layout the tensor core reads;
+//     cp.async, in the 128-byte-swizzled K-major layout the tensor core reads; two k blocks
+//     are in flight while the tensor core works on a third;
 //   * one thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> fp32, M = 128, N = tile width,
 //     K = 16 per instruction) with the accumulator in tensor memory (TMEM), and tcgen05.commit
-//     arrives on an mbarrier per shared-memory stage (3 stages, so gathering overlaps the MMAs);
+//     arrives on an mbarrier per shared-memory stage, which releases that stage for refilling;
 //   * the epilogue reads the accumulator back with tcgen05.ld (each warp its 32 TMEM lanes)
 //     and applies bias + ReLU (forward) or accumulates the data gradient (FP32).
 // Every mbarrier wait is bounded; on a timeout the kernel records an error flag, frees its
@@ -52,9 +53,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -82,29 +80,76 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // byte offset of 16-byte chunk c (0..7) of row r inside a 1024-byte-aligned swizzled tile
 __device__ __forceinline__ uint32_t sw128_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
-// source pointer of the forward / data-gradient A chunk (nullptr: zero padding)
-__device__ __forceinline__ const __nv_bfloat16 *src_fwd(const ConvArgs &a, int m, int k0) {
-  const int C = a.C1 + a.C2;
-  if (m >= a.Pout || k0 >= a.Kf) return nullptr;
-  const int tap = k0 / C, ci = k0 - tap * C;
-  const int kh = tap / a.ks, kw = tap - kh * a.ks;
-  const int xo = m % a.Wout, t = m / a.Wout, yo = t % a.Hout, b = t / a.Hout;
-  const int y = yo * a.stride + kh - a.pad, x = xo * a.stride + kw - a.pad;
-  if (y < 0 || y >= a.Hin || x < 0 || x >= a.Win) return nullptr;
-  const size_t pix = ((size_t)b * a.Hin + y) * a.Win + x;
-  return ci < a.C1 ? a.x1 + pix * a.C1 + ci : a.x2 + pix * a.C2 + (ci - a.C1);
+// Per-thread gather plan.  Thread t always fills 16-byte chunk column c = t % 8 of rows
+// t / 8 + 16 i (i = 0..7) of the A tile, so the pixel coordinates of those eight rows are
+// computed once per CTA; per k block only the tap and channel of column c change.
+struct RowPlan {
+  int yb[8], xb[8], pb[8];  // forward: yo*stride-pad, xo*stride-pad, b*Hin; dgrad: yi+pad, xi+pad, b*Hout
+};
+
+template <int MODE>
+__device__ __forceinline__ void plan_rows(const ConvArgs &a, int m0, int tid, RowPlan &P) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (tid >> 3) + 16 * i;
+    if (MODE == MODE_FWD) {
+      const int xo = m % a.Wout, t = m / a.Wout, yo = t % a.Hout, b = t / a.Hout;
+      P.yb[i] = m < a.Pout ? yo * a.stride - a.pad : -(1 << 28);
+      P.xb[i] = xo * a.stride - a.pad;
+      P.pb[i] = b * a.Hin;
+    } else {
+      const int xi = m % a.Win, t = m / a.Win, yi = t % a.Hin, b = t / a.Hin;
+      P.yb[i] = m < a.M ? yi + a.pad : -(1 << 28);
+      P.xb[i] = xi + a.pad;
+      P.pb[i] = b * a.Hout;
+    }
+  }
 }
 
-__device__ __forceinline__ const __nv_bfloat16 *src_dgrad(const ConvArgs &a, int m, int k0) {
-  if (m >= a.M || k0 >= a.K) return nullptr;
-  const int tap = k0 / a.Cout, co = k0 - tap * a.Cout;
-  const int kh = tap / a.ks, kw = tap - kh * a.ks;
-  const int xi = m % a.Win, t = m / a.Win, yi = t % a.Hin, b = t / a.Hin;
-  const int ys = yi + a.pad - kh, xs = xi + a.pad - kw;
-  if (ys < 0 || xs < 0 || ys % a.stride || xs % a.stride) return nullptr;
-  const int yo = ys / a.stride, xo = xs / a.stride;
-  if (yo >= a.Hout || xo >= a.Wout) return nullptr;
-  return a.dy + (((size_t)b * a.Hout + yo) * a.Wout + xo) * a.Cout + co;
+// cp.async the A and B chunks of k block kt into stage tiles sa / sb, then commit one group
+template <int MODE>
+__device__ __forceinline__ void gather_stage(const ConvArgs &a, const RowPlan &P, int tid, int kt, int BN, uint32_t sa,
+                                             uint32_t sb) {
+  const int c = tid & 7, r0 = tid >> 3;
+  const int k = kt * TC_BK + c * 8;
+  if (MODE == MODE_FWD) {
+    const int C = a.C1 + a.C2;
+    const bool kv = k < a.Kf;
+    const int tap = kv ? k / C : 0, ci = k - tap * C;
+    const int kh = tap / a.ks, kw = tap - kh * a.ks;
+    const __nv_bfloat16 *base = ci < a.C1 ? a.x1 + ci : a.x2 + (ci - a.C1);
+    const int ch = ci < a.C1 ? a.C1 : a.C2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int y = P.yb[i] + kh, x = P.xb[i] + kw;
+      const bool v = kv && y >= 0 && y < a.Hin && x >= 0 && x < a.Win;
+      const __nv_bfloat16 *src = v ? base + ((size_t)(P.pb[i] + y) * a.Win + x) * ch : a.w;
+      cp_async16(sa + sw128_off(r0 + 16 * i, c), src, v);
+    }
+  } else {
+    const bool kv = k < a.K;
+    const int tap = kv ? k / a.Cout : 0, co = k - tap * a.Cout;
+    const int kh = tap / a.ks, kw = tap - kh * a.ks;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int ys = P.yb[i] - kh, xs = P.xb[i] - kw;
+      bool v = kv && ys >= 0 && xs >= 0;
+      int yo = ys, xo = xs;
+      if (a.stride == 2) {
+        v = v && !(ys & 1) && !(xs & 1);
+        yo = ys >> 1;
+        xo = xs >> 1;
+      }
+      v = v && yo < a.Hout && xo < a.Wout;
+      const __nv_bfloat16 *src = v ? a.dy + ((size_t)(P.pb[i] + yo) * a.Wout + xo) * a.Cout + co : a.w;
+      cp_async16(sa + sw128_off(r0 + 16 * i, c), src, v);
+    }
+  }
+  for (int r = r0; r < BN; r += 16) {
+    const bool v = r < a.N && k < a.K;
+    cp_async16(sb + sw128_off(r, c), v ? (const void *)(a.w + (size_t)r * a.K + k) : (const void *)a.w, v);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <int MODE>
@@ -127,39 +172,33 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int BN, int 
   if (tid == 0)
     for (int s = 0; s < TC_STAGES; ++s) mbar_init(&bars[s], 1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  RowPlan P;
+  plan_rows<MODE>(a, m0, tid, P);
+  const int KT = (a.K + TC_BK - 1) / TC_BK;
+  auto stage_a = [&](int kt) { return base + (uint32_t)(kt % TC_STAGES) * a_bytes; };
+  auto stage_b = [&](int kt) { return base + TC_STAGES * a_bytes + (uint32_t)(kt % TC_STAGES) * b_bytes; };
+  // prologue: k blocks 0 .. STAGES-2 in flight (one cp.async group each, empty past the end)
+#pragma unroll
+  for (int p = 0; p < TC_STAGES - 1; ++p) {
+    if (p < KT) gather_stage<MODE>(a, P, tid, p, BN, stage_a(p), stage_b(p));
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
   const uint32_t idesc = idesc_bf16(TC_BM, BN);
-  const int KT = (a.K + TC_BK - 1) / TC_BK;
   bool ok = true;
 
-  for (int kt = 0; kt < KT && ok; ++kt) {
-    const int s = kt % TC_STAGES;
-    if (kt >= TC_STAGES) ok = mbar_wait(&bars[s], (uint32_t)((kt / TC_STAGES - 1) & 1));
-    ok = __syncthreads_and(ok);  // one decision for the whole CTA
-    if (!ok) break;
-    const uint32_t sa = base + (uint32_t)s * a_bytes;
-    const uint32_t sb = base + TC_STAGES * a_bytes + (uint32_t)s * b_bytes;
-    const int k0 = kt * TC_BK;
-    for (int q = tid; q < TC_BM * 8; q += TC_THREADS) {
-      const int r = q >> 3, c = q & 7;
-      const __nv_bfloat16 *src = MODE == MODE_FWD ? src_fwd(a, m0 + r, k0 + c * 8) : src_dgrad(a, m0 + r, k0 + c * 8);
-      cp_async16(sa + sw128_off(r, c), src ? (const void *)src : (const void *)a.w, src != nullptr);
-    }
-    for (int q = tid; q < BN * 8; q += TC_THREADS) {
-      const int r = q >> 3, c = q & 7;
-      const int k = k0 + c * 8;
-      const bool v = r < a.N && k < a.K;
-      cp_async16(sb + sw128_off(r, c), v ? (const void *)(a.w + (size_t)r * a.K + k) : (const void *)a.w, v);
-    }
-    cp_async_commit_wait_all();
+  for (int kt = 0; kt < KT; ++kt) {
+    // this thread's chunks of block kt have landed; make them visible to the tensor core
+    asm volatile("cp.async.wait_group %0;" ::"n"(TC_STAGES - 2) : "memory");
     fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+    ok = __syncthreads_and(ok);  // every thread's chunks landed, and no wait has timed out
+    if (!ok) break;
     if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sa = stage_a(kt), sb = stage_b(kt);
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 16; ++kk) {
         const uint64_t da = sw128_desc(sa + kk * 32), db = sw128_desc(sb + kk * 32);
@@ -170,10 +209,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int BN, int 
             "l"(da), "l"(db), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&bars[s]))
+                       smem_u32(&bars[kt % TC_STAGES]))
                    : "memory");
     }
+    // refill the stage that block kt-1 used, once its MMAs have read it
+    const int nk = kt + TC_STAGES - 1;
+    if (nk < KT) {
+      if (kt >= 1) ok = mbar_wait(&bars[(kt - 1) % TC_STAGES], (uint32_t)(((kt - 1) / TC_STAGES) & 1));
+      if (ok) gather_stage<MODE>(a, P, tid, nk, BN, stage_a(nk), stage_b(nk));
+      else asm volatile("cp.async.commit_group;" ::: "memory");
+    } else {
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   // the last commit covers every MMA issued
   if (ok && KT > 0) {
     const int kl = KT - 1;
@@ -183,28 +232,51 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, int BN, int 
   tc_fence_after();
   if (ok) {
     const int m = m0 + warp * 32 + lane;
-    for (int n0 = 0; n0 < BN; n0 += 8) {
-      uint32_t r[8];
+    for (int n0 = 0; n0 < BN; n0 += 16) {
+      uint32_t r[16];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                   : "r"(taddr));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (m < a.M) {
+      if (m >= a.M) continue;
+      float v[16];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int n = n0 + e;
-          if (n >= a.N) continue;
-          float v = __uint_as_float(r[e]);
-          if (MODE == MODE_FWD) {
-            if (n < a.Nreal) v += a.bias[n];
-            if (a.relu) v = fmaxf(v, 0.f);
-            if (a.y32) a.y32[(size_t)m * a.N + n] = v;
-            else a.y[(size_t)m * a.N + n] = __float2bfloat16(v);
-          } else {
-            if (n < a.C1) a.dx1[(size_t)m * a.C1 + n] += v;
-            else a.dx2[(size_t)m * a.C2 + (n - a.C1)] += v;
+      for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+      if (MODE == MODE_FWD) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          if (n0 + e < a.Nreal) v[e] += a.bias[n0 + e];
+          if (a.relu) v[e] = fmaxf(v[e], 0.f);
+        }
+        if (a.y32) {
+          for (int e = 0; e < 16; ++e)
+            if (n0 + e < a.N) a.y32[(size_t)m * a.N + n0 + e] = v[e];
+        } else {
+          // N % 16 == 0: the 16 outputs are one aligned 32-byte run of the row
+          uint32_t pk[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+            pk[e] = *reinterpret_cast<const uint32_t *>(&h);
           }
+          uint4 *dst = reinterpret_cast<uint4 *>(a.y + (size_t)m * a.N + n0);
+          dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      } else {
+        // channel groups of 4 lie wholly in one input part (C1 % 8 == 0)
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int n = n0 + 4 * g;
+          if (n >= a.N) break;
+          float4 *dst = n < a.C1 ? reinterpret_cast<float4 *>(a.dx1 + (size_t)m * a.C1 + n)
+                                 : reinterpret_cast<float4 *>(a.dx2 + (size_t)m * a.C2 + (n - a.C1));
+          float4 t = *dst;
+          t.x += v[4 * g]; t.y += v[4 * g + 1]; t.z += v[4 * g + 2]; t.w += v[4 * g + 3];
+          *dst = t;
         }
       }
     }
@@ -228,6 +300,8 @@ size_t conv_tc_smem(int BN) { return 1024 + (size_t)TC_STAGES * (TC_BM * 128 + (
 
 bool conv_tc_supported(const ConvArgs &a, int mode) {
   if (mode == MODE_WGRAD) return false;
+  // 16-byte gather chunks must not straddle a tap or the two concatenated inputs
+  if (a.C1 % 8 || a.C2 % 8 || a.Cout % 8 || (a.stride != 1 && a.stride != 2)) return false;
   return a.N % 16 == 0 && a.N >= 16 && a.N <= 256;
 }
 

@@ -92,6 +92,7 @@ SIGNATURES = {
                                  _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp]),
 }
 MG_PROF_SMOOTH, MG_PROF_LINRES, MG_PROF_COEF, MG_PROF_RESIDUAL, MG_PROF_RESTRICT, MG_PROF_PROLONG = 1, 2, 3, 4, 5, 6
+MG_PROF_COARSE = 7
 
 
 def lib_path() -> str:

@@ -386,14 +386,16 @@ def test_odd_sweep_counts(mg):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("ctas,threads", [(1, 1024), (2, 256), (8, 512)])
-def test_persistent_coarse_cycle_equals_level_kernels(mg, precision, ctas, threads):
+@pytest.mark.parametrize("ctas,threads", [(1, 1024), (1, 512), (2, 256), (8, 512)])
+@pytest.mark.parametrize("kn", [16, 64])
+def test_persistent_coarse_cycle_equals_level_kernels(mg, precision, ctas, threads, kn):
     """The coarse levels of a V-cycle in one cluster launch give the same iterates as the
-    per-level kernels, bit for bit."""
+    per-level kernels, bit for bit (kn = 16 with one CTA: the shared-memory form; kn = 64: the
+    levels do not fit in shared memory and the global-memory form runs)."""
     d = W.make_discharge(128, seed=8, V_cathode=-300.0, use_table=True)
     prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
     out = []
-    for kn in (64, 0):
+    for kn in (kn, 0):
         s = mg.from_discharge(d, precision=prec, coarse_kernel_n=kn, coarse_kernel_ctas=ctas,
                               coarse_kernel_threads=threads)
         F, _ = s.residual(1e-7)
