@@ -124,7 +124,7 @@ typedef struct mg_stats {
 typedef struct mg_state mg_state;
 
 /* Fill *p with the defaults: mu_e = 30, D_e = 60, mu_p = 0.15, D_p = 0.0038,
- * V_cathode = -200, V_anode = 0, nu1 = nu2 = 2, coarsest = 4, eta = 1e-3,
+ * V_cathode = -200, V_anode = 0, nu1 = nu2 = 4, coarsest = 4, eta = 1e-3,
  * max_newton = 10, max_vcycles = 60, max_steps = 400, dt1 = 1e-9,
  * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14,
  * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 1, guess_dt_start = 1e-8,

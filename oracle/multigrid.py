@@ -107,7 +107,7 @@ class Hierarchy:
     """Levels 0 (finest) .. L-1 built at the state u (injected downward)."""
 
     def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics,
-                 coarsest: int = 4, nu1: int = 2, nu2: int = 2):
+                 coarsest: int = 4, nu1: int = 4, nu2: int = 4):
         self.levels: List[Level] = []
         self.P: List[sp.csr_matrix] = []
         self.nu1, self.nu2 = nu1, nu2

@@ -30,8 +30,8 @@ from .grid import Grid
 
 @dataclasses.dataclass
 class SolverOptions:
-    nu1: int = 2
-    nu2: int = 2
+    nu1: int = 4
+    nu2: int = 4
     eta: float = 1e-3               # inexact-Newton linear tolerance
     max_vcycles: int = 60
     coarsest: int = 4

@@ -6,7 +6,8 @@
 builds the N x N-node discharge of the benchmark family (table transport for N = 256),
 evaluates the Newton residual at the initial state and runs CYCLES multigrid V-cycles
 (default 3) on the linearised system (eq. 14) at Delta t = 1e-6 s.  Smoother launches per
-V-cycle: 4 per level on the way down, 4 per level on the way up, finest level first.
+V-cycle and level: nu1 sweeps on the way down and nu2 on the way up (one launch per fused
+sweep, two per half-sweep pair, as the autotuner chose for the level), finest level first.
 --eager launches the V-cycle kernels from the host instead of the device-side graph loop
 (kernel profilers cannot attribute kernels inside graphs with conditional nodes).
 

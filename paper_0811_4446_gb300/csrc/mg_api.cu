@@ -755,7 +755,7 @@ void mg_params_default(mg_params *p) {
   p->table = nullptr; p->table_rows = 0;
   p->precision = MG_FP64;
   p->pressure_factor = 1.0;
-  p->nu1 = 2; p->nu2 = 2; p->coarsest = 4;
+  p->nu1 = 4; p->nu2 = 4; p->coarsest = 4;
   p->max_vcycles = 60; p->max_newton = 10; p->max_steps = 400;
   p->eta = 1e-3; p->newton_tol = 0.0; p->corr_limit_frac = 0.5;
   p->dt1 = 1e-9; p->dt_growth = 5.0; p->dt_max = 1e-6;

@@ -62,5 +62,5 @@ def test_workspace_sizing_without_gpu(lib):
 def test_params_default_values(lib):
     from paper_0811_4446_gb300 import mg
     p = mg.default_params()
-    assert (p.dt1, p.dt_growth, p.max_newton, p.nu1, p.nu2) == (1e-9, 5.0, 10, 2, 2)
+    assert (p.dt1, p.dt_growth, p.max_newton, p.nu1, p.nu2) == (1e-9, 5.0, 10, 4, 4)
     assert np.isclose(p.mu_p, 0.15) and np.isclose(p.D_p, 0.0038)
