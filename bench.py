@@ -288,6 +288,21 @@ def run_ours(args):
     tc = time.perf_counter()
     vcycle_s = ((tc - tb) - (tb - ta)) / nvc
     vcycle_mpts = N0 / vcycle_s / 1e6
+    # the same with V(2,2) cycles (the lighter cycle the V-cycle rate is often quoted for)
+    s22 = mg.from_discharge(d, nu1=2, nu2=2)
+    s22.autotune()
+    s22.set_state(inputs[0], inputs[1], inputs[2])
+    F22, _ = s22.residual(1e-6)
+    f22 = [-a for a in F22]
+    s22.linear_solve(1e-6, f22, 0.0, 2)
+    torch.cuda.synchronize()
+    ta = time.perf_counter()
+    s22.linear_solve(1e-6, f22, 0.0, 0)
+    tb = time.perf_counter()
+    s22.linear_solve(1e-6, f22, 0.0, nvc)
+    tc = time.perf_counter()
+    vcycle22_s = ((tc - tb) - (tb - ta)) / nvc
+    s22.close()
 
     # ---- roofline of the dominant kernel (red-black smoother half sweep on the finest level)
     peaks = _peaks()
@@ -321,7 +336,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "vcycle_mpts_per_s": vcycle_mpts, "vcycle_us_257": vcycle_s * 1e6,
+        "vcycle_mpts_per_s": vcycle_mpts, "vcycle_us_257": vcycle_s * 1e6, "vcycle_kind": "V(4,4)",
+        "vcycle_v22_mpts_per_s": N0 / vcycle22_s / 1e6, "vcycle_v22_us_257": vcycle22_s * 1e6,
         "solve_stats": {k: st[k] for k in ("steps_accepted", "steps_rejected", "newton_iterations", "vcycles",
                                            "coarse_steps", "coarse_newton", "coarse_vcycles", "steady_rho")},
         "wall_s": wall_max, "clocks": clocks,

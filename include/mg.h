@@ -237,6 +237,8 @@ uint64_t mg_kernel_launches(void);
  * of `kernel` on multigrid level `level` (0 = finest) is bracketed by CUDA events recorded on
  * the state's stream (up to 16384 launches).  mg_profile_end synchronises the stream and
  * returns the number of bracketed launches and their summed device time in milliseconds.
+ * MG_PROF_RESTRICT brackets the fused linear-residual + restriction launch from `level`,
+ * MG_PROF_LINRES the residual-norm launch of each cycle of a linear solve rooted at `level`.
  * MG_PROF_RESIDUAL brackets the face-coefficient and residual launches of a residual
  * evaluation on `level`; MG_PROF_COEF the hierarchy set-up below a Newton iteration on root
  * level `level` (injection, coarse-level coefficients and the diagonal factors of every level,

@@ -389,12 +389,8 @@ int vcycle(mg_state *s, int l, cudaStream_t st) {
   int rc;
   if ((rc = smooth_sweeps<T>(s, l, s->prm.nu1, st))) return rc;
   {
-    ProfScope ps(s, MG_PROF_LINRES, l);
-    CK(launch_linres<T>(b, b.du, b.f, const_cast<T **>(b.r), nullptr, nullptr, nullptr, st));
-  }
-  {
     ProfScope ps(s, MG_PROF_RESTRICT, l);
-    CK(launch_restrict<T>(b, c, st));
+    CK(launch_linres_restrict<T>(b, c, st));
   }
   if ((rc = vcycle<T>(s, l + 1, st))) return rc;
   {
@@ -408,6 +404,7 @@ int vcycle(mg_state *s, int l, cudaStream_t st) {
 // mixed form this is the FP64 outer defect, also written as the next FP32 right-hand side.
 int launch_norm(mg_state *s, int l0, cudaStream_t st) {
   LevelBuf &b = s->lv[l0];
+  ProfScope ps(s, MG_PROF_LINRES, l0);
   if (mixed(s)) {
     CK(launch_outer_residual(b.L, b.M, s->prm.n0, s->partials, s->counter, s->dout, st));
   } else {

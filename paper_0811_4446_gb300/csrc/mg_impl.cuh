@@ -147,6 +147,9 @@ cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *o
                           unsigned *counter, double *out3, cudaStream_t st);
 template <typename T>
 cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st);
+// r = f - J du on level F and its restriction to C in one launch (r stays on chip)
+template <typename T>
+cudaError_t launch_linres_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st);
 template <typename T>
 cudaError_t launch_prolong_add(const LevelT<T> &C, const LevelT<T> &F, cudaStream_t st);
 cudaError_t launch_inject(const Level &F, const StateView &fs, const Level &C, const StateView &cs,

@@ -601,54 +601,76 @@ struct Triple {
 // Sum over the four neighbours of (off-diagonal block of eq. 14) x v at node k = (j, i).  The
 // off-diagonal blocks have 5 nonzeros: towards a neighbour across a face where this node is the
 // lower end: [-cF, cV] for each species, g for V; where it is the upper end: [-cG, cV], g.
-// Electrode-row neighbours carry v = 0.
+// Electrode-row neighbours carry v = 0.  No branches: the face arrays hold zeros on the r-faces
+// at i = nr and in the pitch padding (never written), so the east term of an i = nr node and
+// the west term of an i = 0 node add exact zeros, and every load can be issued at once.
 template <typename T>
 __device__ __forceinline__ void offdiag(const LevelT<T> &L, int i, size_t k, const T *ve, const T *vp,
                                         const T *vV, T &oe, T &op, T &oV) {
+  (void)i;
   const int P = L.P;
+  const size_t kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
   T e = 0, p = 0, V = 0;
-  if (i < L.nr) {
-    const size_t n = k + 1;
-    const T w = vV[n];
-    e += L.cr[CVE][k] * w - L.cr[CFE][k] * ve[n];
-    p += L.cr[CVP][k] * w - L.cr[CFP][k] * vp[n];
+  {
+    const T w = vV[kE];
+    e += L.cr[CVE][k] * w - L.cr[CFE][k] * ve[kE];
+    p += L.cr[CVP][k] * w - L.cr[CFP][k] * vp[kE];
     V += L.gR[k] * w;
   }
-  if (i > 0) {
-    const size_t n = k - 1;
-    const T w = vV[n];
-    e += L.cr[CVE][n] * w - L.cr[CGE][n] * ve[n];
-    p += L.cr[CVP][n] * w - L.cr[CGP][n] * vp[n];
-    V += L.gR[n] * w;
+  {
+    const T w = vV[kW];
+    e += L.cr[CVE][kW] * w - L.cr[CGE][kW] * ve[kW];
+    p += L.cr[CVP][kW] * w - L.cr[CGP][kW] * vp[kW];
+    V += L.gR[kW] * w;
   }
   {
-    const size_t n = k + P;
-    const T w = vV[n];
-    e += L.cz[CVE][k] * w - L.cz[CFE][k] * ve[n];
-    p += L.cz[CVP][k] * w - L.cz[CFP][k] * vp[n];
+    const T w = vV[kN];
+    e += L.cz[CVE][k] * w - L.cz[CFE][k] * ve[kN];
+    p += L.cz[CVP][k] * w - L.cz[CFP][k] * vp[kN];
     V += L.gZ[k] * w;
   }
   {
-    const size_t n = k - P;
-    const T w = vV[n];
-    e += L.cz[CVE][n] * w - L.cz[CGE][n] * ve[n];
-    p += L.cz[CVP][n] * w - L.cz[CGP][n] * vp[n];
-    V += L.gZ[n] * w;
+    const T w = vV[kS];
+    e += L.cz[CVE][kS] * w - L.cz[CGE][kS] * ve[kS];
+    p += L.cz[CVP][kS] * w - L.cz[CGP][kS] * vp[kS];
+    V += L.gZ[kS] * w;
   }
   oe = e; op = p; oV = V;
 }
 
 // K3: red-black collective Gauss-Seidel half sweep: every node of one colour (red = (i + j)
 // even) solves its 3x3 diagonal block (stored factors) against the current neighbours.
+// Every operand is loaded before the arithmetic starts (the compiler barrier keeps the loads
+// together), so one node costs one round of memory latency; the arithmetic is offdiag's and
+// node_update's, term for term.
 template <typename T>
 __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
-  const size_t k = (size_t)j * L.P + i;
-  T oe, op, oV;
-  offdiag<T>(L, i, k, L.du[NE], L.du[NP], L.du[NV], oe, op, oV);
-  const T re = L.f[NE][k] - oe, rp = L.f[NP][k] - op, rV = L.f[NV][k] - oV;
-  const T xV = (rV - L.fac[FQ1][k] * re - L.fac[FQ2][k] * rp) * L.fac[FIS][k];
-  L.du[NE][k] = (re - L.fac[FA13][k] * xV) * L.fac[FI11][k];
-  L.du[NP][k] = (rp - L.fac[FA23][k] * xV) * L.fac[FI22][k];
+  (void)i;
+  const int P = L.P;
+  const size_t k = (size_t)j * P + i;
+  const size_t kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
+  const T *ve = L.du[NE], *vp = L.du[NP], *vV = L.du[NV];
+  const T eE = ve[kE], pE = vp[kE], wE = vV[kE];
+  const T eW = ve[kW], pW = vp[kW], wW = vV[kW];
+  const T eN = ve[kN], pN = vp[kN], wN = vV[kN];
+  const T eS = ve[kS], pS = vp[kS], wS = vV[kS];
+  const T aE0 = L.cr[CVE][k], aE1 = L.cr[CFE][k], aE2 = L.cr[CVP][k], aE3 = L.cr[CFP][k], gE = L.gR[k];
+  const T aW0 = L.cr[CVE][kW], aW1 = L.cr[CGE][kW], aW2 = L.cr[CVP][kW], aW3 = L.cr[CGP][kW], gW = L.gR[kW];
+  const T aN0 = L.cz[CVE][k], aN1 = L.cz[CFE][k], aN2 = L.cz[CVP][k], aN3 = L.cz[CFP][k], gN = L.gZ[k];
+  const T aS0 = L.cz[CVE][kS], aS1 = L.cz[CGE][kS], aS2 = L.cz[CVP][kS], aS3 = L.cz[CGP][kS], gS = L.gZ[kS];
+  const T f0 = L.f[NE][k], f1 = L.f[NP][k], f2 = L.f[NV][k];
+  const T q1 = L.fac[FQ1][k], q2 = L.fac[FQ2][k], is = L.fac[FIS][k];
+  const T a13 = L.fac[FA13][k], a23 = L.fac[FA23][k], i11 = L.fac[FI11][k], i22 = L.fac[FI22][k];
+  asm volatile("" ::: "memory");
+  T e = 0, p = 0, V = 0;
+  e += aE0 * wE - aE1 * eE; p += aE2 * wE - aE3 * pE; V += gE * wE;
+  e += aW0 * wW - aW1 * eW; p += aW2 * wW - aW3 * pW; V += gW * wW;
+  e += aN0 * wN - aN1 * eN; p += aN2 * wN - aN3 * pN; V += gN * wN;
+  e += aS0 * wS - aS1 * eS; p += aS2 * wS - aS3 * pS; V += gS * wS;
+  const T re = f0 - e, rp = f1 - p, rV = f2 - V;
+  const T xV = (rV - q1 * re - q2 * rp) * is;
+  L.du[NE][k] = (re - a13 * xV) * i11;
+  L.du[NP][k] = (rp - a23 * xV) * i22;
   L.du[NV][k] = xV;
 }
 
@@ -684,14 +706,15 @@ template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream
 template <typename T>
 __device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, size_t k, const Triple<T> &vE,
                                                  const Triple<T> &vW, const Triple<T> &vN, const Triple<T> &vS) {
+  (void)i;
   const int P = L.P;
   T e = 0, p = 0, V = 0;
-  if (i < L.nr) {
+  {  // no branches at i = 0, nr: see offdiag
     e += L.cr[CVE][k] * vE.V - L.cr[CFE][k] * vE.e;
     p += L.cr[CVP][k] * vE.V - L.cr[CFP][k] * vE.p;
     V += L.gR[k] * vE.V;
   }
-  if (i > 0) {
+  {
     const size_t n = k - 1;
     e += L.cr[CVE][n] * vW.V - L.cr[CGE][n] * vW.e;
     p += L.cr[CVP][n] * vW.V - L.cr[CGP][n] * vW.p;
@@ -736,10 +759,8 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
     T ve = 0, vp = 0, vV = 0;
     if (i >= 0 && i <= nr && j >= 1 && j < nz && ((i + j) & 1) == 0) {
       const size_t k = (size_t)j * P + i;
-      const Triple<T> z = {0, 0, 0};
-      const Triple<T> x = node_update<T>(L, i, k, i < nr ? gload<T>(io.in, k + 1) : z,
-                                         i > 0 ? gload<T>(io.in, k - 1) : z, gload<T>(io.in, k + P),
-                                         gload<T>(io.in, k - P));
+      const Triple<T> x = node_update<T>(L, i, k, gload<T>(io.in, k + 1), gload<T>(io.in, k - 1),
+                                         gload<T>(io.in, k + P), gload<T>(io.in, k - P));
       ve = x.e; vp = x.p; vV = x.V;
     }
     sr[NE][lj][li] = ve; sr[NP][lj][li] = vp; sr[NV][lj][li] = vV;
@@ -792,9 +813,8 @@ template cudaError_t launch_sweep<float>(const LevelT<float> &, const SweepIO<fl
 // K4: linear residual r = f - J v (or J v when f is null), optional per-field sums of squares
 // (accumulated in FP64).
 template <typename T>
-__device__ __forceinline__ Triple<T> linres_node(const LevelT<T> &L, int i, int j, const T *v0, const T *v1,
-                                                 const T *v2, const T *f0, const T *f1, const T *f2, T *o0, T *o1,
-                                                 T *o2) {
+__device__ __forceinline__ Triple<T> linres_val(const LevelT<T> &L, int i, int j, const T *v0, const T *v1,
+                                                const T *v2, const T *f0, const T *f1, const T *f2) {
   const size_t k = (size_t)j * L.P + i;
   T oe, op, oV;
   offdiag<T>(L, i, k, v0, v1, v2, oe, op, oV);
@@ -803,8 +823,17 @@ __device__ __forceinline__ Triple<T> linres_node(const LevelT<T> &L, int i, int 
   T jp = L.dia[DA22][k] * v1[k] + L.fac[FA23][k] * v2[k] + op;
   T jV = ak * (v1[k] - v0[k]) + L.dia[DA33][k] * v2[k] + oV;
   if (f0) { je = f0[k] - je; jp = f1[k] - jp; jV = f2[k] - jV; }
-  o0[k] = je; o1[k] = jp; o2[k] = jV;
   return Triple<T>{je, jp, jV};
+}
+
+template <typename T>
+__device__ __forceinline__ Triple<T> linres_node(const LevelT<T> &L, int i, int j, const T *v0, const T *v1,
+                                                 const T *v2, const T *f0, const T *f1, const T *f2, T *o0, T *o1,
+                                                 T *o2) {
+  const Triple<T> r = linres_val<T>(L, i, j, v0, v1, v2, f0, f1, f2);
+  const size_t k = (size_t)j * L.P + i;
+  o0[k] = r.e; o1[k] = r.p; o2[k] = r.V;
+  return r;
 }
 
 template <typename T>
@@ -823,7 +852,7 @@ __global__ void k_linres(LevelT<T> L, const T *v0, const T *v1, const T *v2, con
 template <typename T>
 cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,
                           unsigned *counter, double *out3, cudaStream_t st) {
-  const int bx = 32, by = out3 ? BY : SBY;
+  const int bx = 32, by = SBY;
   dim3 b(bx, by), g((L.nr + 1 + bx - 1) / bx, (L.nz - 1 + by - 1) / by);
   k_linres<T><<<g, b, 0, st>>>(L, v[0], v[1], v[2], f ? f[0] : nullptr, f ? f[1] : nullptr, f ? f[2] : nullptr,
                                out[0], out[1], out[2], partials, counter, out3);
@@ -874,6 +903,59 @@ cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t
 }
 template cudaError_t launch_restrict<double>(const LevelT<double> &, const LevelT<double> &, cudaStream_t);
 template cudaError_t launch_restrict<float>(const LevelT<float> &, const LevelT<float> &, cudaStream_t);
+
+// K4+K5 in one launch: a block computes r = f - J du on the fine nodes under a CX x CY tile of
+// coarse nodes (plus the one-node ring the full weighting reaches) into shared memory and
+// restricts them; r never goes to global memory.  Same per-node arithmetic and summation order
+// as linres_node followed by restrict_node.
+template <typename T, int CX, int CY>
+__global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) k_linres_restrict(LevelT<T> F,
+                                                                                                 LevelT<T> C) {
+  constexpr int FW = 2 * CX + 1, FH = 2 * CY + 1;
+  __shared__ T sr[3][FH * FW];
+  const int I0 = blockIdx.x * CX, J0 = 1 + blockIdx.y * CY;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < FW * FH; t += blockDim.x) {
+    const int fi = 2 * I0 - 1 + t % FW, fj = 2 * J0 - 1 + t / FW;
+    Triple<T> r{T(0), T(0), T(0)};
+    if (fi >= 0 && fi <= F.nr && fj < F.nz)
+      r = linres_val<T>(F, fi, fj, F.du[NE], F.du[NP], F.du[NV], F.f[NE], F.f[NP], F.f[NV]);
+    sr[0][t] = r.e; sr[1][t] = r.p; sr[2][t] = r.V;
+  }
+  __syncthreads();
+  for (int t = tid; t < CX * CY; t += blockDim.x) {
+    const int I = I0 + t % CX, J = J0 + t / CX;
+    if (I > C.nr || J >= C.nz) continue;
+    const size_t kc = (size_t)J * C.P + I;
+    T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int j = 2 * J + dj;
+      const T wz = dj == 0 ? T(1) : (dj < 0 ? F.wz[j] : T(1) - F.wz[j]);
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int i = 2 * I + di;
+        if (i < 0 || i > F.nr) continue;
+        const T w = wz * (di == 0 ? T(1) : T(0.5));
+        const int ls = (j - (2 * J0 - 1)) * FW + (i - (2 * I0 - 1));
+        s0 += w * sr[0][ls]; s1 += w * sr[1][ls]; s2 += w * sr[2][ls];
+      }
+    }
+    C.f[NE][kc] = s0; C.f[NP][kc] = s1; C.f[NV][kc] = s2;
+    C.du[NE][kc] = T(0); C.du[NP][kc] = T(0); C.du[NV][kc] = T(0);
+  }
+}
+
+template <typename T>
+cudaError_t launch_linres_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st) {
+  constexpr int CX = 16, CY = 4;  // 33 x 9 fine nodes, one per thread
+  dim3 b(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32), g((C.nr + 1 + CX - 1) / CX, (C.nz - 1 + CY - 1) / CY);
+  k_linres_restrict<T, CX, CY><<<g, b, 0, st>>>(F, C);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_linres_restrict<double>(const LevelT<double> &, const LevelT<double> &, cudaStream_t);
+template cudaError_t launch_linres_restrict<float>(const LevelT<float> &, const LevelT<float> &, cudaStream_t);
 
 // K6: prolongation and correction du_f += P du_c (bilinear in (r, z)).
 template <typename T>
