@@ -323,7 +323,10 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": ("k_sweep<double> (fused red-black sweep" if fused0 else "k_smooth<double> (red-black half sweep") + ", 257x257 level)", "achieved": achieved_flops,
                 "peak": fp64_peak_nominal, "unit": "GFLOP/s", "frac": achieved_flops / fp64_peak_nominal,
                 "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "peak_probe_gflops": fp64_probe, "traffic": None,
+                "peak_probe_gflops": fp64_probe,
+                # DRAM bytes read + written per launch in one ncu capture of this kernel (cold
+                # caches; profiles/k_smooth_fp64_257.md); no capture of the fused FP64 form
+                "traffic": None if fused0 else 14347904,
                 "launches": prof_n, "avg_launch_us": avg_s * 1e6,
                 "algorithmic_flops_per_launch": flops_per_launch,
                 "hbm": {"achieved": achieved_bw, "peak": hbm_peak, "unit": "GB/s",
@@ -415,7 +418,10 @@ def measure_forms(args, dev, peaks):
                                 "roofline": {"bound": "hbm", "kernel": ("k_sweep<float> (fused red-black sweep" if fused32 else "k_smooth<float> (red-black half sweep") + ", 1025x1025 level)",
                                              "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
                                              "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6,
-                                             "algorithmic_bytes_per_launch": byt, "traffic": None}}
+                                             "algorithmic_bytes_per_launch": byt,
+                                             # ncu DRAM read + write per launch, cold caches
+                                             # (profiles/k_smooth_fp32_1025_mixed.md)
+                                             "traffic": None if fused32 else 117228672}}
     s.close()
     # batched form: 64 independent discharges of seeded sizes 65^2..513^2, mixed precision
     ds = W.batch_64()

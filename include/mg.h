@@ -221,7 +221,7 @@ int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, dou
  * sweep of every level (FP64 and, in the mixed form, FP32) over fixed sets of thread-block /
  * tile shapes and keeps the fastest per level.  Leaves the solution state untouched (only
  * the correction work buffers are written); on each level the fused sweep is kept only where
- * it beats two half sweeps.  shapes_out (may be NULL) receives 6 ints per level: FP64 half-sweep
+ * it beats two half sweeps by more than 3 %.  shapes_out (may be NULL) receives 6 ints per level: FP64 half-sweep
  * (bx, by), FP64 fused flag, FP32 half-sweep (bx, by), FP32 fused flag. */
 int mg_autotune(mg_state *s, int32_t *shapes_out);
 int mg_num_levels(const mg_state *s);

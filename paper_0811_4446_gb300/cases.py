@@ -1,6 +1,6 @@
 """Small fixed workloads for profiling runs (ncu captures of single kernels).
 
-    python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager]
+    python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager] [--autotune] [--half]
     python -m paper_0811_4446_gb300.cases unet B N [REPS] [--mma]
 
 builds the N x N-node discharge of the benchmark family (table transport for N = 256),
@@ -10,6 +10,10 @@ V-cycle and level: nu1 sweeps on the way down and nu2 on the way up (one launch 
 sweep, two per half-sweep pair, as the autotuner chose for the level), finest level first.
 --eager launches the V-cycle kernels from the host instead of the device-side graph loop
 (kernel profilers cannot attribute kernels inside graphs with conditional nodes).
+--autotune picks the smoother launch shapes and fused / half sweeps per level as the
+benchmark does (its timing launches come before the V-cycles).  The linear solve (its
+residual, hierarchy set-up and V-cycles) runs inside the NVTX range "measure".  --half
+smooths with two half-sweep launches per sweep on every level (no fused sweeps).
 
 unet: REPS (default 2) forward passes plus one training step of the learned-guess network
 on a batch of B random (N+1) x (N+1) inputs; --mma selects the mma.sync convolutions instead
@@ -21,7 +25,8 @@ import os
 import sys
 
 
-def vcycles(n: int, cycles: int = 3, mixed: bool = False, eager: bool = False) -> float:
+def vcycles(n: int, cycles: int = 3, mixed: bool = False, eager: bool = False, autotune: bool = False,
+            half: bool = False) -> float:
     import torch
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -31,10 +36,16 @@ def vcycles(n: int, cycles: int = 3, mixed: bool = False, eager: bool = False) -
     from . import mg
 
     d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=(n == 256))
-    s = mg.from_discharge(d, precision=mg.MG_MIXED if mixed else mg.MG_FP64, use_graphs=0 if eager else 1)
+    s = mg.from_discharge(d, precision=mg.MG_MIXED if mixed else mg.MG_FP64, use_graphs=0 if eager else 1,
+                          fused_sweep=0 if half else 1)
+    if autotune:
+        s.autotune()
     F, _ = s.residual(1e-6)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("measure")  # profilers can select the launches inside this range
     _, hist, _ = s.linear_solve(1e-6, [-a for a in F], 0.0, cycles)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     return float(hist[-1])
 
 
@@ -67,4 +78,5 @@ if __name__ == "__main__":
         sys.exit(2)
     N = int(sys.argv[2])
     C = int(sys.argv[3]) if len(sys.argv) > 3 and not sys.argv[3].startswith("--") else 3
-    print("ok", N, vcycles(N, C, "--mixed" in sys.argv, "--eager" in sys.argv))
+    print("ok", N, vcycles(N, C, "--mixed" in sys.argv, "--eager" in sys.argv, "--autotune" in sys.argv,
+                           "--half" in sys.argv))

@@ -1235,8 +1235,9 @@ int mg_autotune(mg_state *s, int32_t *shapes_out) {
         if (ms < bestf) { bestf = ms; bf = c; }
       }
       if (prec == 0) b.sw = bf; else b.sw32 = bf;
-      // keep the fused sweep only where it beats two half sweeps of the best shape
-      const int fz = bestf < 2.0f * best ? 1 : 0;
+      // keep the fused sweep only where it beats two half sweeps of the best shape by more
+      // than the timing noise (3 %), so that near-ties give the same choice run after run
+      const int fz = bestf < 0.97f * 2.0f * best ? 1 : 0;
       if (prec == 0) b.fuse = fz; else b.fuse32 = fz;
       if (shapes_out) {
         shapes_out[6 * l + 3 * prec] = cand[bi][0];
