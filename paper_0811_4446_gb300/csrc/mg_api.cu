@@ -270,23 +270,33 @@ struct ProfScope {
 };
 
 // ---------------------------------------------------------------- building blocks
-// Nonlinear residual on root level l0; rho[3] and the term norms tn[3]; f = -F written if write_f.
-int residual(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], double rho[3], double tn[3]) {
+// Nonlinear residual on root level l0: launches only.  with_coef: the face coefficients are
+// (re)computed at the current state first; callers pass false only right after a residual at
+// the same state (the coefficients are also the Jacobian's, reused by build_hierarchy).  The six
+// sums of squares land in dout[0..5].
+int residual_launch(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], bool with_coef) {
   LevelBuf &b = s->lv[l0];
-  {
-    ProfScope ps(s, MG_PROF_RESIDUAL, l0);
-    // face coefficients at the state (also the Jacobian's, reused by build_hierarchy), then
-    // the rows from them
-    CK(launch_coef(b.L, b.sv, s->tr, s->stream));
-    CK(launch_resid_coef(b.L, b.sv, dt, write_f, Fout, s->partials, s->counter, s->dout, s->stream));
-  }
-  int rc = sync_read(s, 6);
-  if (rc) return rc;
+  ProfScope ps(s, MG_PROF_RESIDUAL, l0);
+  if (with_coef) CK(launch_coef(b.L, b.sv, s->tr, s->stream));
+  CK(launch_resid_coef(b.L, b.sv, dt, write_f, Fout, s->partials, s->counter, s->dout, s->stream));
+  return MG_OK;
+}
+
+// rho[3] and the term norms tn[3] from the sums read back into hout[0..5]
+void residual_norms(const mg_state *s, double rho[3], double tn[3]) {
   for (int q = 0; q < 3; ++q) {
     const double fn = std::sqrt(s->hout[q]), t = std::sqrt(s->hout[3 + q]);
     if (tn) tn[q] = t;
     if (rho) rho[q] = fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
   }
+}
+
+// Nonlinear residual on root level l0; rho[3] and the term norms tn[3]; f = -F written if write_f.
+int residual(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], double rho[3], double tn[3],
+             bool with_coef = true) {
+  int rc = residual_launch(s, l0, dt, write_f, Fout, with_coef);
+  if (rc || (rc = sync_read(s, 6))) return rc;
+  residual_norms(s, rho, tn);
   return MG_OK;
 }
 
@@ -535,8 +545,10 @@ done:
   return MG_OK;
 }
 
-int linear_solve_graph(mg_state *s, int l0, double eta, int max_cycles, const double w[3], double *hist, int *ncyc,
-                       bool *ok) {
+// Device-side solve: the control block goes in, the graph runs, the control block comes back
+// into the pinned host mirror, all on the state's stream without waiting.  The caller
+// synchronises the stream and then calls linear_solve_graph_end.
+int linear_solve_graph_begin(mg_state *s, int l0, double eta, int max_cycles, const double w[3]) {
   if (!s->vexec[l0]) {
     int rc = build_solve_graph(s, l0);
     if (rc) return rc;
@@ -551,13 +563,33 @@ int linear_solve_graph(mg_state *s, int l0, double eta, int max_cycles, const do
   CK(cudaMemcpyAsync(s->ctl, h, offsetof(SolveCtl, hist), cudaMemcpyHostToDevice, s->stream));
   CK(cudaGraphLaunch(s->vexec[l0], s->stream));
   CK(cudaMemcpyAsync(h, s->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+void linear_solve_graph_end(mg_state *s, int l0, double eta, double *hist, int *ncyc, bool *ok) {
+  const SolveCtl *h = s->hctl;
   *ncyc = h->ncyc;
   count_launch(s->vprefix[l0] + h->ncyc * s->vbody[l0]);
   if (hist)
     for (int k = 0; k <= h->ncyc; ++k) hist[k] = h->hist[k];
   *ok = (h->r0 == 0.0) || (h->rel <= eta);
+}
+
+int linear_solve_graph(mg_state *s, int l0, double eta, int max_cycles, const double w[3], double *hist, int *ncyc,
+                       bool *ok) {
+  int rc = linear_solve_graph_begin(s, l0, eta, max_cycles, w);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  linear_solve_graph_end(s, l0, eta, hist, ncyc, ok);
   return MG_OK;
+}
+
+bool use_graph(const mg_state *s, int max_cycles) {
+  return s->prm.use_graphs && s->prof_kernel == 0 && max_cycles < kMaxHist;
+}
+
+void solve_weights(const double tn[3], double w[3]) {
+  for (int q = 0; q < 3; ++q) w[q] = tn[q] > 0.0 ? tn[q] : 1.0;
 }
 
 // V-cycles on level l0 from du = 0 until the weighted residual drops by eta (tn: the per-field
@@ -565,10 +597,9 @@ int linear_solve_graph(mg_state *s, int l0, double eta, int max_cycles, const do
 int linear_solve(mg_state *s, int l0, double eta, int max_cycles, const double tn[3], double *hist, int *ncyc,
                  bool *ok) {
   double w[3];
-  for (int q = 0; q < 3; ++q) w[q] = tn[q] > 0.0 ? tn[q] : 1.0;
-  const bool graphs = s->prm.use_graphs && s->prof_kernel == 0 && max_cycles < kMaxHist;
-  const int rc = graphs ? linear_solve_graph(s, l0, eta, max_cycles, w, hist, ncyc, ok)
-                        : linear_solve_eager(s, l0, eta, max_cycles, w, hist, ncyc, ok);
+  solve_weights(tn, w);
+  const int rc = use_graph(s, max_cycles) ? linear_solve_graph(s, l0, eta, max_cycles, w, hist, ncyc, ok)
+                                          : linear_solve_eager(s, l0, eta, max_cycles, w, hist, ncyc, ok);
   if (rc == MG_OK) s->stats.vcycles += *ncyc;
   return rc;
 }
@@ -583,17 +614,22 @@ void copy_state_async(mg_state *s, int l0, bool to_old) {
 
 // One backward-Euler step on level l0 (eq. 7 by Newton-Raphson on eq. 14).
 // Returns MG_OK (accepted), MG_ENOCONV or MG_ENONFINITE (rejected; state restored).
-int step(mg_state *s, int l0, double dt, double tol, int *newton_out) {
+// coef_current: the face coefficients of level l0 are those of the current state (the caller
+// evaluated a residual at this state and changed nothing since).
+// A Newton iteration enqueues the hierarchy set-up, the device-side linear solve, the update
+// and the next residual, then waits once and reads the solve's control block, the update's
+// checks and the new residual norms together.
+int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_current = false) {
   LevelBuf &b = s->lv[l0];
   copy_state_async(s, l0, true);
   CK(cudaGetLastError());
   const double limit = s->prm.corr_limit_frac * std::fabs(s->prm.V_cathode);
   int rc;
   int reason = MG_ENOCONV;
+  double rho[3], tn[3];
+  rc = residual(s, l0, dt, true, nullptr, rho, tn, !coef_current);
+  if (rc) return rc;
   for (int it = 0; it <= s->prm.max_newton; ++it) {
-    double rho[3], tn[3];
-    rc = residual(s, l0, dt, true, nullptr, rho, tn);
-    if (rc) return rc;
     for (int q = 0; q < 3; ++q) s->stats.rho[q] = rho[q];
     const double rmax = std::max(rho[0], std::max(rho[1], rho[2]));
     if (!(rmax == rmax) || std::isinf(rmax)) { reason = MG_ENONFINITE; *newton_out = it; break; }
@@ -610,14 +646,24 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out) {
     bool ok;
     // inexact-Newton forcing term: drive the linear residual only to half the Newton target
     const double eta = s->prm.eta_adapt ? std::max(s->prm.eta, std::min(0.1, 0.5 * tol / rmax)) : s->prm.eta;
-    rc = linear_solve(s, l0, eta, s->prm.max_vcycles, tn, nullptr, &ncyc, &ok);
+    double w[3];
+    solve_weights(tn, w);
+    const bool graph = use_graph(s, s->prm.max_vcycles);
+    if (graph) rc = linear_solve_graph_begin(s, l0, eta, s->prm.max_vcycles, w);
+    else rc = linear_solve_eager(s, l0, eta, s->prm.max_vcycles, w, nullptr, &ncyc, &ok);
     if (rc) return rc;
+    // u += du (max |dV| and the non-finite flag into dout[8..9]), then the residual at the new
+    // state (into dout[0..5]); used only if the update is accepted
+    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout + 8, s->stream));
+    if ((rc = residual_launch(s, l0, dt, true, nullptr, true))) return rc;
+    rc = sync_read(s, 10);
+    if (rc) return rc;
+    if (graph) linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
+    s->stats.vcycles += ncyc;
     if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
-    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout, s->stream));
-    rc = sync_read(s, 2);
-    if (rc) return rc;
-    if (s->hout[1] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
-    if (s->hout[0] > limit) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
+    if (s->hout[9] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
+    if (s->hout[8] > limit) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
+    residual_norms(s, rho, tn);
   }
   s->stats.newton_iterations += *newton_out;
   s->stats.last_newton = *newton_out;
@@ -630,17 +676,22 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out) {
 int march(mg_state *s, int l0, double dt_start, double tol) {
   double dt = dt_start, dt_prev = -1.0;
   const double ntol = s->prm.newton_tol > 0.0 ? s->prm.newton_tol : 0.1 * tol;
+  bool coef_current = false;  // face coefficients of level l0 at the current state
   for (int n = 0; n < s->prm.max_steps; ++n) {
     int newton = 0;
-    int rc = step(s, l0, dt, ntol, &newton);
+    int rc = step(s, l0, dt, ntol, &newton, coef_current);
+    coef_current = false;
     if (rc == MG_ECUDA) return rc;
     s->stats.dt_last = dt;
     if (rc == MG_OK) {
       s->stats.steps_accepted++;
       s->stats.sim_time += dt;
+      // the accepted step ended on a residual at this very state: its coefficients stand, and
+      // they serve the next step's first residual too
       double rho[3];
-      rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr);
+      rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr, false);
       if (rc) return rc;
+      coef_current = true;
       const double r = std::max(rho[0], std::max(rho[1], rho[2]));
       s->stats.steady_rho = r;
       if (r <= tol) return MG_OK;
