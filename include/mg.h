@@ -104,6 +104,9 @@ typedef struct mg_params {
   int32_t coarse_kernel_threads;/* threads per CTA (32..1024, multiple of 32) */
   int32_t eta_adapt;      /* 1: Newton iteration k solves to eta_k = max(eta, min(0.1,
                              tol / (2 rho_k))) instead of eta (inexact-Newton forcing term) */
+  int32_t nu_coarse_n;    /* levels whose larger side has <= this many intervals smooth with
+                             nu_coarse1 / nu_coarse2 sweeps instead of nu1 / nu2 (0: off) */
+  int32_t nu_coarse1, nu_coarse2;
 } mg_params;
 
 /* Per-call statistics. */
@@ -129,7 +132,8 @@ typedef struct mg_state mg_state;
  * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14,
  * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 1, guess_dt_start = 1e-8,
  * coarse_kernel_n = 16,
- * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1.
+ * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1, nu_coarse_n = 64,
+ * nu_coarse1 = nu_coarse2 = 2 (V(4,4) smoothing on levels larger than 65^2, V(2,2) below).
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on

@@ -14,7 +14,8 @@ names no component.  The components below are this project's readings:
   z by distance weights), identity across the three fields; electrode rows carry 0;
 * restriction R = P^T acting on the finite-volume-integrated residual;
 * coarsest level: dense LU with partial pivoting of the whole (equilibrated) 3-field system;
-* V(nu1, nu2) cycles until the field-weighted residual norm has dropped by eta.
+* V(nu1, nu2) cycles (V(nu_coarse1, nu_coarse2) smoothing on the small levels) until the
+  field-weighted residual norm has dropped by eta.
 """
 from __future__ import annotations
 
@@ -107,12 +108,18 @@ class Hierarchy:
     """Levels 0 (finest) .. L-1 built at the state u (injected downward)."""
 
     def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics,
-                 coarsest: int = 4, nu1: int = 4, nu2: int = 4):
+                 coarsest: int = 4, nu1: int = 4, nu2: int = 4, nu_coarse_n: int = 64,
+                 nu_coarse1: int = 2, nu_coarse2: int = 2):
+        """Smoothing: nu1 / nu2 sweeps before / after the coarse-grid correction, except on
+        levels whose larger side has at most nu_coarse_n intervals (0: none), which take
+        nu_coarse1 / nu_coarse2."""
         self.levels: List[Level] = []
         self.P: List[sp.csr_matrix] = []
-        self.nu1, self.nu2 = nu1, nu2
+        self.nus: List[tuple] = []
         while True:
             self.levels.append(Level(g, u, dt, phys))
+            small = nu_coarse_n > 0 and max(g.nr, g.nz) <= nu_coarse_n
+            self.nus.append((nu_coarse1, nu_coarse2) if small else (nu1, nu2))
             if min(g.nr, g.nz) <= coarsest or g.nr % 2 or g.nz % 2:
                 break
             gc = g.coarse()
@@ -124,12 +131,13 @@ class Hierarchy:
         lev = self.levels[l]
         if l == len(self.levels) - 1:
             return lev.direct(f)
-        x = lev.smooth(x, f, self.nu1)
+        nu1, nu2 = self.nus[l]
+        x = lev.smooth(x, f, nu1)
         r = f - lev.J @ x
         fc = self.P[l].T @ r
         xc = self.vcycle(l + 1, np.zeros_like(fc), fc)
         x = x + self.P[l] @ xc
-        return lev.smooth(x, f, self.nu2)
+        return lev.smooth(x, f, nu2)
 
     def solve(self, f: np.ndarray, eta: float, max_cycles: int = 100, x0: Optional[np.ndarray] = None,
               scale: Optional[np.ndarray] = None):

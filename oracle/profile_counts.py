@@ -50,7 +50,8 @@ def unit_times(d, level_n, dt=1e-6, vcycles=3, opt=None):
     F, T = disc.residual(g, u, u, S_e, S_p, dt, phys, with_terms=True)
     t_res = time.perf_counter() - t0
     t0 = time.perf_counter()
-    H = mg.Hierarchy(g, u, dt, phys, opt.coarsest, opt.nu1, opt.nu2)
+    H = mg.Hierarchy(g, u, dt, phys, opt.coarsest, opt.nu1, opt.nu2, opt.nu_coarse_n, opt.nu_coarse1,
+                     opt.nu_coarse2)
     t_hier = time.perf_counter() - t0
     f = -disc.to_vec(g, F)
     x = np.zeros_like(f)

@@ -32,6 +32,9 @@ from .grid import Grid
 class SolverOptions:
     nu1: int = 4
     nu2: int = 4
+    nu_coarse_n: int = 64     # levels with at most this many intervals per side smooth with
+    nu_coarse1: int = 2       # nu_coarse1 / nu_coarse2 sweeps (0: nu1 / nu2 everywhere)
+    nu_coarse2: int = 2
     eta: float = 1e-3               # inexact-Newton linear tolerance
     max_vcycles: int = 60
     coarsest: int = 4
@@ -79,7 +82,8 @@ def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: f
             return x, StepStats(True, it, vcyc, r)
         if it == opt.max_newton:
             break
-        H = mg.Hierarchy(g, x, dt, phys, opt.coarsest, opt.nu1, opt.nu2)
+        H = mg.Hierarchy(g, x, dt, phys, opt.coarsest, opt.nu1, opt.nu2, opt.nu_coarse_n, opt.nu_coarse1,
+                         opt.nu_coarse2)
         tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
         eta = forcing_term(opt, r.max(), tol)
         du, hist = H.solve(-disc.to_vec(g, F), eta, opt.max_vcycles, scale=tn)

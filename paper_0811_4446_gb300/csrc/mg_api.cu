@@ -382,6 +382,13 @@ template <typename T> size_t coarse_smem(const mg_state *s);
 template <> size_t coarse_smem<double>(const mg_state *s) { return s->cc_smem64; }
 template <> size_t coarse_smem<float>(const mg_state *s) { return s->cc_smem32; }
 
+// pre- (which = 1) or post-smoothing (2) sweeps on level l
+int nu_of(const mg_state *s, int l, int which) {
+  const bool small = s->prm.nu_coarse_n > 0 && std::max(s->lv[l].nr, s->lv[l].nz) <= s->prm.nu_coarse_n;
+  if (which == 1) return small ? s->prm.nu_coarse1 : s->prm.nu1;
+  return small ? s->prm.nu_coarse2 : s->prm.nu2;
+}
+
 template <typename T>
 int vcycle(mg_state *s, int l, cudaStream_t st) {
   const LevelT<T> &b = view<T>(s->lv[l]);
@@ -397,7 +404,7 @@ int vcycle(mg_state *s, int l, cudaStream_t st) {
   }
   const LevelT<T> &c = view<T>(s->lv[l + 1]);
   int rc;
-  if ((rc = smooth_sweeps<T>(s, l, s->prm.nu1, st))) return rc;
+  if ((rc = smooth_sweeps<T>(s, l, nu_of(s, l, 1), st))) return rc;
   {
     ProfScope ps(s, MG_PROF_RESTRICT, l);
     CK(launch_linres_restrict<T>(b, c, st));
@@ -407,7 +414,7 @@ int vcycle(mg_state *s, int l, cudaStream_t st) {
     ProfScope ps(s, MG_PROF_PROLONG, l);
     CK(launch_prolong_add<T>(c, b, st));
   }
-  return smooth_sweeps<T>(s, l, s->prm.nu2, st);
+  return smooth_sweeps<T>(s, l, nu_of(s, l, 2), st);
 }
 
 // Per-field sums of squares of the linear residual f - J du on level l0 into dout[0..2]; in the
@@ -735,8 +742,10 @@ int setup_coarse_kernel(mg_state *s) {
   CoarseSet<double> h64 = {};
   CoarseSet<float> h32 = {};
   h64.n = h32.n = s->nlev - s->cc_from;
-  h64.nu1 = h32.nu1 = s->prm.nu1;
-  h64.nu2 = h32.nu2 = s->prm.nu2;
+  for (int q = 0; q < h64.n; ++q) {
+    h64.nu1[q] = h32.nu1[q] = nu_of(s, s->cc_from + q, 1);
+    h64.nu2[q] = h32.nu2[q] = nu_of(s, s->cc_from + q, 2);
+  }
   h64.Minv = h32.Minv = s->Minv;
   h64.rs = h32.rs = s->rs;
   h64.cs = h32.cs = s->cs;
@@ -814,6 +823,7 @@ void mg_params_default(mg_params *p) {
   p->guess_level = 1;
   p->guess_dt_start = 1e-8;
   p->eta_adapt = 1;
+  p->nu_coarse_n = 64; p->nu_coarse1 = 2; p->nu_coarse2 = 2;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
   p->coarse_kernel_threads = 512;
@@ -827,6 +837,11 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
     if (!(g->z[j + 1] > g->z[j])) { *why = "z must increase strictly"; return MG_EINVAL; }
   if (p->coarsest < 2 || p->coarsest > 8) { *why = "coarsest must be in 2..8"; return MG_EINVAL; }
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) { *why = "need at least one smoothing sweep"; return MG_EINVAL; }
+  if (p->nu_coarse_n < 0 || (p->nu_coarse_n > 0 && (p->nu_coarse1 < 0 || p->nu_coarse2 < 0 ||
+                                                     p->nu_coarse1 + p->nu_coarse2 < 1))) {
+    *why = "nu_coarse_n >= 0 and, when set, at least one coarse smoothing sweep";
+    return MG_EINVAL;
+  }
   if (!(p->pressure_factor > 0.0) || !(p->D_e > 0.0) || !(p->D_p > 0.0) || p->mu_e < 0 || p->mu_p < 0) {
     *why = "transport coefficients must be positive"; return MG_EINVAL;
   }

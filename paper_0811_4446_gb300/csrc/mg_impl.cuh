@@ -58,7 +58,7 @@ template <typename T>
 struct CoarseSet {
   LevelT<T> lv[kMaxCoarseSet];
   int n;                            // levels in the set; the last one is the coarsest
-  int nu1, nu2;
+  int nu1[kMaxCoarseSet], nu2[kMaxCoarseSet];  // pre- / post-smoothing sweeps per level
   const double *Minv, *rs, *cs;     // dense inverse of the coarsest level (FP64)
   double nscale;                    // density unit of the view (1 or n0)
 };

@@ -1356,7 +1356,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
   for (int q = 0; q + 1 < S.n; ++q) {
     const LevelT<T> &L = S.lv[q];
     const LevelT<T> &C = S.lv[q + 1];
-    sweeps(L, S.nu1);
+    sweeps(L, S.nu1[q]);
     const int W = L.nr + 1;
     for (int t = tid; t < (L.nz - 1) * W; t += nth) {
       const int j = t / W + 1, i = t % W;
@@ -1374,7 +1374,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
     const int W = F.nr + 1;
     for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(S.lv[q + 1], F, t % W, t / W + 1);
     bar();
-    sweeps(F, S.nu2);
+    sweeps(F, S.nu2[q]);
   }
 }
 
@@ -1455,7 +1455,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
   for (int q = 0; q + 1 < G.n; ++q) {
     const LevelT<T> &L = lv[q];
     const LevelT<T> &C = lv[q + 1];
-    sweeps(L, G.nu1);
+    sweeps(L, G.nu1[q]);
     const int W = L.nr + 1;
     for (int t = tid; t < (L.nz - 1) * W; t += nth) {
       const int j = t / W + 1, i = t % W;
@@ -1473,7 +1473,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
     const int W = F.nr + 1;
     for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(lv[q + 1], F, t % W, t / W + 1);
     __syncthreads();
-    sweeps(F, G.nu2);
+    sweeps(F, G.nu2[q]);
   }
   {
     const LevelT<T> &g = G.lv[0];
