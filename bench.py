@@ -181,7 +181,6 @@ def run_ours(args):
     d = W.steady_257()
     s = mg.from_discharge(d)
     shapes = s.autotune()                         # launch shapes per level (set-up, untimed)
-    fused0 = bool(shapes[0, 2])
     N0 = (d.nr + 1) * (d.nz + 1)
     inputs = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (d.ne0, d.np0, d.V0, d.S_e, d.S_p)]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -228,14 +227,17 @@ def run_ours(args):
         dev_ms, wall, launches, clocks, st = timed()
         clocks["remeasured"] = True
 
-    # Kernel timing of the finest-level smoother: CUDA events around every launch of that kernel
-    # (on the launching stream) during one more solve of the same workload.  Per-launch events
-    # cannot sit inside the device-side V-cycle loop of the graphs used above, so this solve
-    # launches the same kernels with the same data from the host.
-    flush.zero_()
-    s.profile_begin(mg.MG_PROF_SMOOTH, 0)
-    step()
-    prof_n, prof_ms = s.profile_end()
+    # Kernel timing of the smoother on each level: CUDA events around every launch of it (on the
+    # launching stream) during one more solve of the same workload per level.  Per-launch events
+    # cannot sit inside the device-side V-cycle loop of the graphs used above, so these solves
+    # launch the same kernels with the same data from the host.
+    nlev = s.lib.mg_num_levels(s.h)
+    smooth_prof = []
+    for lev in range(nlev - 1):
+        flush.zero_()
+        s.profile_begin(mg.MG_PROF_SMOOTH, lev)
+        step()
+        smooth_prof.append(s.profile_end())
 
     t = torch.tensor([dev_ms, wall], dtype=torch.float64, device=dev)
     if world > 1:
@@ -304,34 +306,51 @@ def run_ours(args):
     vcycle22_s = ((tc - tb) - (tb - ta)) / nvc
     s22.close()
 
-    # ---- roofline of the dominant kernel (red-black smoother half sweep on the finest level)
+    # ---- roofline of the dominant kernel: the smoother on the level where it took the most
+    # device time in the profiled solves (launches x average duration)
     peaks = _peaks()
-    nodes = (d.nr + 1) * (d.nz - 1)            # unknown nodes of the 257 x 257 level
-    # fused red-black sweep launch (both colours): the 12 face coefficients, 2 Poisson
-    # conductances, 7 block factors and 3 right-hand sides of every node once (8 B each), the old
-    # black corrections read (3 x 8 B per black node) and both colours' corrections written.
-    # Half-sweep launch (one colour): all face coefficients and conductances once, the colour's
-    # factors, f and du (8 B each) and the other colour's du read.
-    bytes_per_launch = (228 if fused0 else 176) * nodes
-    flops_per_launch = 52 * nodes if fused0 else 52 * (nodes / 2)   # 20 FMA off-diagonal + block solve per updated node
-    avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
     fp64_peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12 * 1000.0   # GFLOP/s: SMs x DFMA/clk x 2 x GHz
     fp64_probe = mg.probe_fp64_gflops()
-    achieved_flops = flops_per_launch / avg_s / 1e9
-    achieved_bw = bytes_per_launch / avg_s / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "kernel": ("k_sweep<double> (fused red-black sweep" if fused0 else "k_smooth<double> (red-black half sweep") + ", 257x257 level)", "achieved": achieved_flops,
-                "peak": fp64_peak_nominal, "unit": "GFLOP/s", "frac": achieved_flops / fp64_peak_nominal,
+    # DRAM bytes read + written per launch in one ncu capture of the kernel (cold caches): the
+    # half sweep of the 257^2 level (profiles/k_smooth_fp64_257.md); the other levels and the
+    # fused FP64 form have no committed capture
+    traffic_ncu = {(256, False): 14347904}
+    levels = []
+    for lev, (n_l, ms_l) in enumerate(smooth_prof):
+        if not n_l:
+            continue          # levels inside the coarse-cycle kernel (no smoother launches of their own)
+        n_iv = d.nr >> lev
+        nodes = (n_iv + 1) * (n_iv - 1)        # unknown nodes of the level
+        fused = bool(shapes[lev, 2])
+        # fused red-black sweep launch (both colours): the 12 face coefficients, 2 Poisson
+        # conductances, 7 block factors and 3 right-hand sides of every node once (8 B each), the
+        # old black corrections read (3 x 8 B per black node) and both colours' corrections
+        # written.  Half-sweep launch (one colour): all face coefficients and conductances once,
+        # the colour's factors, f and du (8 B each) and the other colour's du read.
+        byt = (228 if fused else 176) * nodes
+        flo = 52 * nodes if fused else 52 * (nodes / 2)   # 20 FMA off-diagonal + block solve per updated node
+        avg = (ms_l / n_l) / 1000.0
+        levels.append({"level": lev, "nodes_per_side": n_iv + 1, "fused": fused, "launches": n_l,
+                       "total_ms": ms_l, "avg_launch_us": avg * 1e6, "gflops": flo / avg / 1e9,
+                       "frac_fp64": flo / avg / 1e9 / fp64_peak_nominal, "gbs": byt / avg / 1e9,
+                       "flops_per_launch": flo, "bytes_per_launch": byt,
+                       "traffic": traffic_ncu.get((n_iv, fused))})
+    dom = max(levels, key=lambda r: r["total_ms"])
+    roofline = {"bound": "alu",
+                "kernel": ("k_sweep<double> (fused red-black sweep" if dom["fused"] else
+                           "k_smooth<double> (red-black half sweep")
+                + f", {dom['nodes_per_side']}x{dom['nodes_per_side']} level, the largest smoother share)",
+                "achieved": dom["gflops"], "peak": fp64_peak_nominal, "unit": "GFLOP/s", "frac": dom["frac_fp64"],
                 "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "peak_probe_gflops": fp64_probe,
-                # DRAM bytes read + written per launch in one ncu capture of this kernel (cold
-                # caches; profiles/k_smooth_fp64_257.md); no capture of the fused FP64 form
-                "traffic": None if fused0 else 14347904,
-                "launches": prof_n, "avg_launch_us": avg_s * 1e6,
-                "algorithmic_flops_per_launch": flops_per_launch,
-                "hbm": {"achieved": achieved_bw, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": achieved_bw / hbm_peak, "algorithmic_bytes_per_launch": bytes_per_launch,
-                        "peak_source": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback"}}
+                "peak_probe_gflops": fp64_probe, "traffic": dom["traffic"],
+                "launches": dom["launches"], "avg_launch_us": dom["avg_launch_us"],
+                "algorithmic_flops_per_launch": dom["flops_per_launch"],
+                "hbm": {"achieved": dom["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": dom["gbs"] / hbm_peak,
+                        "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+                        "peak_source": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+                "smoother_levels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+                                    for r in levels]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -339,7 +358,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "vcycle_mpts_per_s": vcycle_mpts, "vcycle_us_257": vcycle_s * 1e6, "vcycle_kind": "V(4,4)",
+        "vcycle_mpts_per_s": vcycle_mpts, "vcycle_us_257": vcycle_s * 1e6, "vcycle_kind": "V(4,4) above 65^2, V(2,2) from 65^2 down",
         "vcycle_v22_mpts_per_s": N0 / vcycle22_s / 1e6, "vcycle_v22_us_257": vcycle22_s * 1e6,
         "solve_stats": {k: st[k] for k in ("steps_accepted", "steps_rejected", "newton_iterations", "vcycles",
                                            "coarse_steps", "coarse_newton", "coarse_vcycles", "steady_rho")},
