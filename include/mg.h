@@ -107,6 +107,10 @@ typedef struct mg_params {
   int32_t nu_coarse_n;    /* levels whose larger side has <= this many intervals smooth with
                              nu_coarse1 / nu_coarse2 sweeps instead of nu1 / nu2 (0: off) */
   int32_t nu_coarse1, nu_coarse2;
+  int32_t chain_from;     /* mg_solve_steady starts its march on level chain_from (the grid
+                             coarsened 2^chain_from times; 1 <= chain_from < levels) and goes
+                             back up one level at a time: prolongation, then a march from
+                             dt_max on each finer level (Sec. 2: finer and finer grids) */
 } mg_params;
 
 /* Per-call statistics. */
@@ -133,7 +137,8 @@ typedef struct mg_state mg_state;
  * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 1, guess_dt_start = 1e-8,
  * coarse_kernel_n = 16,
  * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1, nu_coarse_n = 64,
- * nu_coarse1 = nu_coarse2 = 2 (V(4,4) smoothing on levels larger than 65^2, V(2,2) below).
+ * nu_coarse1 = nu_coarse2 = 2 (V(4,4) smoothing on levels larger than 65^2, V(2,2) below),
+ * chain_from = 1 (the two-level 129^2 -> 257^2 continuation).
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on

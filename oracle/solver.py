@@ -35,6 +35,7 @@ class SolverOptions:
     nu_coarse_n: int = 64     # levels with at most this many intervals per side smooth with
     nu_coarse1: int = 2       # nu_coarse1 / nu_coarse2 sweeps (0: nu1 / nu2 everywhere)
     nu_coarse2: int = 2
+    chain_from: int = 1       # continuation starts on the grid coarsened this many times
     eta: float = 1e-3               # inexact-Newton linear tolerance
     max_vcycles: int = 60
     coarsest: int = 4
@@ -146,12 +147,29 @@ def prolong_state(gc: Grid, gf: Grid, uc: np.ndarray) -> np.ndarray:
 
 
 def solve_steady(g: Grid, u0, S_e, S_p, phys, tol, opt: SolverOptions, log=None):
-    """Coarse (N/2) steady solve from u0 injected, prolong, fine steady solve from dt_max."""
-    gc = g.coarse()
-    uc = disc.apply_dirichlet(mg.inject(g, u0), phys)
-    uc, okc, rec_c = march(gc, uc, mg.inject(g, S_e), mg.inject(g, S_p), phys, tol, opt, opt.dt1, log)
-    if not okc:
+    """Multilevel continuation (abstract and Sec. 2): steady solve on the grid coarsened
+    opt.chain_from times (u0 and the sources injected, march from dt1), then on each finer grid
+    the prolonged steady state marched from dt_max.  Returns (u, ok, coarse records, fine
+    records); the coarse records hold every level but the finest."""
+    grids, us, Se, Sp = [g], [u0], [S_e], [S_p]
+    for _ in range(opt.chain_from):
+        gc = grids[-1].coarse()
+        us.append(mg.inject(grids[-1], us[-1]))
+        Se.append(mg.inject(grids[-1], Se[-1]))
+        Sp.append(mg.inject(grids[-1], Sp[-1]))
+        grids.append(gc)
+    k = opt.chain_from
+    u = disc.apply_dirichlet(us[k], phys)
+    u, ok, rec_c = march(grids[k], u, Se[k], Sp[k], phys, tol, opt, opt.dt1, log)
+    if not ok:
         return u0, False, rec_c, []
-    uf = disc.apply_dirichlet(prolong_state(gc, g, uc), phys)
-    uf, okf, rec_f = march(g, uf, S_e, S_p, phys, tol, opt, opt.dt_max, log)
-    return uf, okf, rec_c, rec_f
+    for k in range(opt.chain_from - 1, -1, -1):
+        u = disc.apply_dirichlet(prolong_state(grids[k + 1], grids[k], u), phys)
+        u, ok, rec = march(grids[k], u, Se[k], Sp[k], phys, tol, opt, opt.dt_max, log)
+        if k > 0:
+            rec_c = rec_c + rec
+            if not ok:
+                return u0, False, rec_c, []
+        else:
+            return u, ok, rec_c, rec
+    raise AssertionError("unreachable")

@@ -824,6 +824,7 @@ void mg_params_default(mg_params *p) {
   p->guess_dt_start = 1e-8;
   p->eta_adapt = 1;
   p->nu_coarse_n = 64; p->nu_coarse1 = 2; p->nu_coarse2 = 2;
+  p->chain_from = 1;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
   p->coarse_kernel_threads = 512;
@@ -1156,22 +1157,35 @@ int mg_march(mg_state *s, double dt_start, double tol, mg_stats *st) {
   return rc;
 }
 
+// Multilevel continuation (abstract and Sec. 2): steady state on level `from` (state and
+// sources injected from the finest level, march from dt1), then on each finer level the
+// prolonged steady state and a march from dt_max.  The coarse_* statistics count every level
+// but the finest.
 int mg_solve_steady(mg_state *s, double tol, mg_stats *st) {
   if (!s || !(tol > 0.0)) return MG_EINVAL;
   if (s->nlev < 2) return fail(s, MG_EINVAL, "continuation needs at least two grid levels");
-  LevelBuf &f = s->lv[0], &c = s->lv[1];
-  CK(launch_inject(f.L, f.sv, c.L, c.sv, false, true, s->stream));
+  const int from = s->prm.chain_from;
+  if (from < 1 || from >= s->nlev)
+    return fail(s, MG_EINVAL, "chain_from = %d outside 1 .. %d", from, s->nlev - 1);
+  for (int l = 1; l <= from; ++l)
+    CK(launch_inject(s->lv[l - 1].L, s->lv[l - 1].sv, s->lv[l].L, s->lv[l].sv, false, true, s->stream));
   const mg_stats before = s->stats;
-  int rc = march(s, 1, s->prm.dt1, tol);
-  s->stats.coarse_steps += s->stats.steps_accepted + s->stats.steps_rejected - before.steps_accepted -
-                           before.steps_rejected;
-  s->stats.coarse_newton += s->stats.newton_iterations - before.newton_iterations;
-  s->stats.coarse_vcycles += s->stats.vcycles - before.vcycles;
-  if (rc == MG_OK) {
+  auto count_coarse = [&]() {
+    s->stats.coarse_steps += s->stats.steps_accepted + s->stats.steps_rejected - before.steps_accepted -
+                             before.steps_rejected;
+    s->stats.coarse_newton += s->stats.newton_iterations - before.newton_iterations;
+    s->stats.coarse_vcycles += s->stats.vcycles - before.vcycles;
+  };
+  int rc = march(s, from, s->prm.dt1, tol);
+  bool counted = false;
+  for (int l = from - 1; l >= 0 && rc == MG_OK; --l) {
+    if (l == 0) { count_coarse(); counted = true; }
+    LevelBuf &f = s->lv[l], &c = s->lv[l + 1];
     CK(launch_prolong_state(c.L, c.sv, f.L, f.sv, s->stream));
     CK(launch_dirichlet(f.L, f.sv, s->prm.V_cathode, s->prm.V_anode, s->stream));
-    rc = march(s, 0, s->prm.dt_max, tol);
+    rc = march(s, l, s->prm.dt_max, tol);
   }
+  if (!counted) count_coarse();
   if (st) *st = s->stats;
   return rc;
 }

@@ -44,7 +44,8 @@ class mg_params(ctypes.Structure):
                 ("guess_dt_start", ctypes.c_double),
                 ("coarse_kernel_n", ctypes.c_int32), ("coarse_kernel_ctas", ctypes.c_int32),
                 ("coarse_kernel_threads", ctypes.c_int32), ("eta_adapt", ctypes.c_int32),
-                ("nu_coarse_n", ctypes.c_int32), ("nu_coarse1", ctypes.c_int32), ("nu_coarse2", ctypes.c_int32)]
+                ("nu_coarse_n", ctypes.c_int32), ("nu_coarse1", ctypes.c_int32), ("nu_coarse2", ctypes.c_int32),
+                ("chain_from", ctypes.c_int32)]
 
 
 class mg_stats(ctypes.Structure):

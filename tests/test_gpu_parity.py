@@ -154,6 +154,39 @@ def test_solve_steady_continuation_parity_33(mg):
         assert np.abs(ug[q] - uo[q]).max() <= 1e-7 * np.abs(uo[q]).max(), q
 
 
+@pytest.mark.parametrize("chain_from,dt_max", [(2, 1e-6), (3, 1.0)])
+def test_solve_steady_chain_parity_65(mg, chain_from, dt_max):
+    """Multilevel continuation from the grid coarsened chain_from times (17^2 or 9^2 up to 65^2),
+    capped and uncapped Delta-t ramp: the oracle's schedule, step for step, and its steady state."""
+    d = W.make_discharge(64, seed=1, V_cathode=-300.0, use_table=True)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-10, max_vcycles=200, chain_from=chain_from, dt_max=dt_max)
+    rc, st = s.solve_steady(1e-9)
+    assert rc == mg.MG_OK
+    opt = osv.SolverOptions(eta=1e-10, max_vcycles=200, chain_from=chain_from, dt_max=dt_max)
+    uo, ok, rec_c, rec_f = osv.solve_steady(g, u, d.S_e, d.S_p, phys, 1e-9, opt)
+    assert ok
+    assert st["coarse_steps"] == len(rec_c) and st["steps_accepted"] + st["steps_rejected"] == len(rec_c) + len(rec_f)
+    ug = s.get_state()
+    for q in range(3):
+        assert np.abs(ug[q] - uo[q]).max() <= 1e-7 * np.abs(uo[q]).max(), q
+
+
+def test_steady_257_chain_uncapped_residual_property(mg):
+    """257 x 257 from 33^2 up with the uncapped ramp (the paper's own schedule): the oracle's
+    residual of the result."""
+    d = W.steady_257()
+    g, phys = _oracle(d)
+    s = mg.from_discharge(d, chain_from=3, dt_max=1.0)
+    rc, st = s.solve_steady(1e-8)
+    assert rc == mg.MG_OK, st
+    ug = np.stack(s.get_state())
+    F, T = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
+    assert disc.rho(F, T).max() <= 1.05e-8
+    assert np.all(np.isfinite(ug))
+
+
 def test_steady_257_full_size_residual_property(mg):
     """257 x 257, table transport, continuation to rho <= 1e-8: the oracle's residual of the result."""
     d = W.steady_257()

@@ -140,3 +140,42 @@ def test_transient_33_regression_golden():
     for k, name in enumerate(("ne", "np", "V")):
         assert np.isclose(np.abs(u[k]).sum(), gold[name + "_l1"], rtol=1e-10)
         assert np.isclose(u[k][gold["probe_j"], gold["probe_i"]], gold[name + "_probe"], rtol=1e-10)
+
+
+def _steady_problem(n, seed=0):
+    d = W.make_discharge(n, seed=seed, V_cathode=-300.0)
+    g = Grid(d.nr, d.nz, d.R, d.z)
+    phys = disc.Physics(V_cathode=d.V_cathode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p)
+    return d, g, phys, np.stack([d.ne0, d.np0, d.V0])
+
+
+def test_chain_from_one_is_the_two_level_continuation():
+    """chain_from = 1 is the printed two-level schedule: inject to N/2, march from dt1,
+    prolong, march from dt_max (written out here step by step)."""
+    d, g, phys, u0 = _steady_problem(16)
+    opt = so.SolverOptions(eta=1e-10)
+    u, ok, rc, rf = so.solve_steady(g, u0, d.S_e, d.S_p, phys, 1e-8, opt)
+    assert ok
+    gc = g.coarse()
+    uc = disc.apply_dirichlet(mg.inject(g, u0), phys)
+    uc, okc, _ = so.march(gc, uc, mg.inject(g, d.S_e), mg.inject(g, d.S_p), phys, 1e-8, opt, opt.dt1)
+    uf = disc.apply_dirichlet(so.prolong_state(gc, g, uc), phys)
+    uf, okf, _ = so.march(g, uf, d.S_e, d.S_p, phys, 1e-8, opt, opt.dt_max)
+    assert okc and okf
+    assert np.array_equal(u, uf)
+
+
+@pytest.mark.parametrize("dt_max", [1e-6, 1.0])
+def test_chain_reaches_the_same_steady_state(dt_max):
+    """Starting the continuation two levels further down (and with the paper's uncapped ramp)
+    ends on the same discrete steady state: rho <= tol on the finest grid and the state of the
+    two-level schedule to the accuracy the tolerance allows."""
+    d, g, phys, u0 = _steady_problem(16, seed=3)
+    base, ok0, _, _ = so.solve_steady(g, u0, d.S_e, d.S_p, phys, 1e-9, so.SolverOptions(eta=1e-10))
+    assert ok0
+    opt = so.SolverOptions(eta=1e-10, chain_from=2, dt_max=dt_max)
+    u, ok, rc, rf = so.solve_steady(g, u0, d.S_e, d.S_p, phys, 1e-9, opt)
+    assert ok and len(rf) >= 1
+    assert so.steady_rho(g, u, d.S_e, d.S_p, phys).max() <= 1e-9
+    for q in range(3):
+        assert np.abs(u[q] - base[q]).max() <= 1e-6 * np.abs(base[q]).max(), q
