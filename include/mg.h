@@ -91,8 +91,10 @@ typedef struct mg_params {
   double n0;              /* density unit of the FP32 inner cycle (eq. 12's n0), m^-3 */
   int32_t use_graphs;     /* 1: each linear solve is one CUDA-graph launch whose V-cycle loop
                              and stopping test run on the device; 0: host-driven loop */
-  int32_t fused_sweep;    /* 1: one launch per red-black sweep (tiled, both colours);
-                             0: one launch per colour.  Same result bit for bit. */
+  int32_t fused_sweep;    /* 1: levels may run one launch per red-black sweep (tiled, both
+                             colours) where their choice says so (mg_autotune, mg_set_smoother;
+                             by default the FP32 view); 0: one launch per colour everywhere.
+                             Same result bit for bit. */
   double guess_dt_max;    /* cap of the Delta-t ramp when marching from a learned guess: the
                              ramp starts at dt_max and grows by dt_growth up to this value */
   int32_t guess_level;    /* 0: march the full grid from the guess; 1: the guess (injected)
@@ -229,10 +231,18 @@ int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, dou
 /* Autotuner of the smoother's launch shapes: times the red-black half sweep and the fused
  * sweep of every level (FP64 and, in the mixed form, FP32) over fixed sets of thread-block /
  * tile shapes and keeps the fastest per level.  Leaves the solution state untouched (only
- * the correction work buffers are written); on each level the fused sweep is kept only where
- * it beats two half sweeps by more than 3 %.  shapes_out (may be NULL) receives 6 ints per level: FP64 half-sweep
+ * the correction work buffers are written); on each level the FP32 fused sweep is kept only
+ * where it beats two half sweeps by more than 3 %, and the FP64 view always uses half sweeps
+ * (their ring recompute makes fused FP64 sweeps slower inside a V-cycle).  shapes_out (may be NULL) receives 6 ints per level: FP64 half-sweep
  * (bx, by), FP64 fused flag, FP32 half-sweep (bx, by), FP32 fused flag. */
 int mg_autotune(mg_state *s, int32_t *shapes_out);
+
+/* Sets the smoother's launch on one level by hand (what mg_autotune chooses): precision 0 for
+ * the FP64 view, 1 for the FP32 view (mixed form); half-sweep block (bx, by) with bx in
+ * {32, 64, 128} and bx * by <= 1024; fused = 1 for one tiled launch per sweep with tile shape
+ * `tile` (0: 32x2, 1: 32x4, 2: 32x8, 3: 64x2, 4: 64x4, 5: 128x2), 0 for two half sweeps.
+ * Results are the same bit for bit whatever the choice.  MG_EINVAL on a bad level or shape. */
+int mg_set_smoother(mg_state *s, int level, int precision, int bx, int by, int fused, int tile);
 int mg_num_levels(const mg_state *s);
 
 /* Statistics accumulated since creation (or the last mg_reset_stats). */

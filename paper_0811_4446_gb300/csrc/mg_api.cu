@@ -41,7 +41,7 @@ struct LevelBuf {
   int sbx = 32, sby = 2;         // half-sweep launch shape, FP64 view (autotuned)
   int sbx32 = 32, sby32 = 2;     // half-sweep launch shape, FP32 view (autotuned)
   int sw = 1, sw32 = 1;          // fused-sweep tile shape index, FP64 / FP32 (autotuned)
-  int fuse = 1, fuse32 = 1;      // fused sweep faster than two half sweeps on this level (autotuned)
+  int fuse = 0, fuse32 = 1;      // fused sweep on this level (FP64: off, see mg_autotune; FP32: autotuned)
 };
 
 }  // namespace
@@ -1315,9 +1315,13 @@ int mg_autotune(mg_state *s, int32_t *shapes_out) {
         if (ms < bestf) { bestf = ms; bf = c; }
       }
       if (prec == 0) b.sw = bf; else b.sw32 = bf;
-      // keep the fused sweep only where it beats two half sweeps of the best shape by more
-      // than the timing noise (3 %), so that near-ties give the same choice run after run
-      const int fz = bestf < 0.97f * 2.0f * best ? 1 : 0;
+      // FP32: keep the fused sweep only where it beats two half sweeps of the best shape by
+      // more than the timing noise (3 %), so that near-ties give the same choice run after run.
+      // FP64: never.  Back-to-back launches of one kernel favour the fused sweep, but inside the
+      // V-cycle its red ring recompute costs FP64 work that two half sweeps do not: on the 257^2
+      // steady solve every FP64 level ran as fast or faster with half sweeps (129^2: 5 % of the
+      // solve), while the FP32 choices were within noise of each other.
+      const int fz = (prec == 1 && bestf < 0.97f * 2.0f * best) ? 1 : 0;
       if (prec == 0) b.fuse = fz; else b.fuse32 = fz;
       if (shapes_out) {
         shapes_out[6 * l + 3 * prec] = cand[bi][0];
@@ -1335,6 +1339,21 @@ int mg_autotune(mg_state *s, int32_t *shapes_out) {
   CK(launch_zero_du<double>(s->lv[0].L, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return rc;
+}
+
+int mg_set_smoother(mg_state *s, int level, int precision, int bx, int by, int fused, int tile) {
+  if (!s) return MG_EINVAL;
+  if (level < 0 || level >= s->nlev || (precision != 0 && precision != 1) || (fused != 0 && fused != 1))
+    return fail(s, MG_EINVAL, "mg_set_smoother: bad level / precision / fused flag");
+  if ((bx != 32 && bx != 64 && bx != 128) || by < 1 || bx * by > 1024 || tile < 0 || tile >= kSweepShapes)
+    return fail(s, MG_EINVAL, "mg_set_smoother: bad block (%d, %d) or tile %d", bx, by, tile);
+  LevelBuf &b = s->lv[level];
+  if (precision == 0) { b.sbx = bx; b.sby = by; b.fuse = fused; b.sw = tile; }
+  else { b.sbx32 = bx; b.sby32 = by; b.fuse32 = fused; b.sw32 = tile; }
+  // graphs recorded the old launch shapes
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (s->vexec[l]) { cudaGraphExecDestroy(s->vexec[l]); s->vexec[l] = nullptr; }
+  return MG_OK;
 }
 
 int mg_num_levels(const mg_state *s) { return s ? s->nlev : 0; }

@@ -83,6 +83,7 @@ SIGNATURES = {
     "mg_get_stats": (_i, [_vp, ctypes.POINTER(mg_stats)]),
     "mg_reset_stats": (None, [_vp]),
     "mg_kernel_launches": (ctypes.c_uint64, []),
+    "mg_set_smoother": (_i, [_vp, _i, _i, _i, _i, _i, _i]),
     "mg_profile_begin": (_i, [_vp, _i, _i]),
     "mg_profile_end": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "mg_probe_fp64_gflops": (ctypes.c_double, [_vp]),
@@ -297,6 +298,10 @@ class Solver:
 
     def reset_stats(self):
         self.lib.mg_reset_stats(self.h)
+
+    def set_smoother(self, level: int, precision: int, bx: int, by: int, fused: int, tile: int):
+        """Smoother launch of one level by hand (see mg_set_smoother in include/mg.h)."""
+        self._check(self.lib.mg_set_smoother(self.h, level, precision, bx, by, fused, tile))
 
     def autotune(self):
         n = self.lib.mg_num_levels(self.h)

@@ -384,9 +384,17 @@ def test_autotune_keeps_results(mg):
         assert np.array_equal(res[0][0][q], res[1][0][q])
 
 
+def _force_fused(s, tile):
+    """Fused sweeps with the given tile on every level of both views."""
+    for lev in range(s.lib.mg_num_levels(s.h)):
+        for view in (0, 1):
+            s.set_smoother(lev, view, 32, 2, 1, tile)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("n", [16, 64, 256])
-def test_fused_sweep_equals_half_sweeps(mg, precision, n):
+@pytest.mark.parametrize("tile", ["autotuned", 0, 4, 5])
+def test_fused_sweep_equals_half_sweeps(mg, precision, n, tile):
     """One launch per red-black sweep (tiles with a recomputed red ring, ping-pong buffers)
     gives the same iterates as one launch per colour, bit for bit."""
     d = W.make_discharge(n, seed=6, V_cathode=-300.0, use_table=(n == 64))
@@ -396,6 +404,8 @@ def test_fused_sweep_equals_half_sweeps(mg, precision, n):
         s = mg.from_discharge(d, precision=prec, fused_sweep=fused)
         if fused:
             s.autotune()
+            if tile != "autotuned":
+                _force_fused(s, tile)
         F, _ = s.residual(1e-7)
         x, h, rc = s.linear_solve(1e-7, [-a for a in F], 1e-10, 100)
         assert rc == mg.MG_OK
@@ -411,6 +421,8 @@ def test_odd_sweep_counts(mg):
     res = []
     for fused in (1, 0):
         s = mg.from_discharge(d, nu1=1, nu2=3, fused_sweep=fused)
+        if fused:
+            _force_fused(s, 1)
         F, _ = s.residual(1e-8)
         x, h, rc = s.linear_solve(1e-8, [-a for a in F], 1e-11, 100)
         assert rc == mg.MG_OK
