@@ -133,7 +133,7 @@ typedef struct mg_stats {
 typedef struct mg_state mg_state;
 
 /* Fill *p with the defaults: mu_e = 30, D_e = 60, mu_p = 0.15, D_p = 0.0038,
- * V_cathode = -200, V_anode = 0, nu1 = nu2 = 4, coarsest = 4, eta = 1e-3,
+ * V_cathode = -200, V_anode = 0, nu1 = nu2 = 4, coarsest = 2, eta = 1e-3,
  * max_newton = 10, max_vcycles = 60, max_steps = 400, dt1 = 1e-9,
  * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14,
  * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 1, guess_dt_start = 1e-8,
@@ -262,9 +262,10 @@ uint64_t mg_kernel_launches(void);
  * evaluation on `level`; MG_PROF_COEF the hierarchy set-up below a Newton iteration on root
  * level `level` (injection, coarse-level coefficients and the diagonal factors of every level,
  * one launch each); MG_PROF_COARSE the launches of the coarse-cycle kernel that starts on
- * `level`. */
+ * `level`; MG_PROF_COARSE_FACTOR the coarsest-level inverse below a Newton iteration on root
+ * level `level`. */
 enum { MG_PROF_SMOOTH = 1, MG_PROF_LINRES = 2, MG_PROF_COEF = 3, MG_PROF_RESIDUAL = 4,
-       MG_PROF_RESTRICT = 5, MG_PROF_PROLONG = 6, MG_PROF_COARSE = 7 };
+       MG_PROF_RESTRICT = 5, MG_PROF_PROLONG = 6, MG_PROF_COARSE = 7, MG_PROF_COARSE_FACTOR = 8 };
 int mg_profile_begin(mg_state *s, int kernel, int level);
 int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms);
 

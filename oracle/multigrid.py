@@ -108,7 +108,7 @@ class Hierarchy:
     """Levels 0 (finest) .. L-1 built at the state u (injected downward)."""
 
     def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics,
-                 coarsest: int = 4, nu1: int = 4, nu2: int = 4, nu_coarse_n: int = 64,
+                 coarsest: int = 2, nu1: int = 4, nu2: int = 4, nu_coarse_n: int = 64,
                  nu_coarse1: int = 2, nu_coarse2: int = 2):
         """Smoothing: nu1 / nu2 sweeps before / after the coarse-grid correction, except on
         levels whose larger side has at most nu_coarse_n intervals (0: none), which take

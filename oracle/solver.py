@@ -38,7 +38,7 @@ class SolverOptions:
     chain_from: int = 1       # continuation starts on the grid coarsened this many times
     eta: float = 1e-3               # inexact-Newton linear tolerance
     max_vcycles: int = 60
-    coarsest: int = 4
+    coarsest: int = 2
     max_newton: int = 10
     corr_limit_frac: float = 0.5    # reject if max|dV| > frac * |V_cathode|
     dt1: float = 1e-9

@@ -315,6 +315,7 @@ int build_hierarchy(mg_state *s, int l0, double dt) {
     CK(launch_factor_levels(s->lset, s->lv[l0].L, l0, last, mixed(s), dt, s->prm.n0, s->stream));
   }
   LevelBuf &c = s->lv[s->nlev - 1];
+  ProfScope ps(s, MG_PROF_COARSE_FACTOR, l0);
   CK(launch_coarse_factor(c.L, dt, s->M, s->Minv, s->rs, s->cs, s->flag, s->stream));
   return MG_OK;
 }
@@ -812,7 +813,7 @@ void mg_params_default(mg_params *p) {
   p->table = nullptr; p->table_rows = 0;
   p->precision = MG_FP64;
   p->pressure_factor = 1.0;
-  p->nu1 = 4; p->nu2 = 4; p->coarsest = 4;
+  p->nu1 = 4; p->nu2 = 4; p->coarsest = 2;
   p->max_vcycles = 60; p->max_newton = 10; p->max_steps = 400;
   p->eta = 1e-3; p->newton_tol = 0.0; p->corr_limit_frac = 0.5;
   p->dt1 = 1e-9; p->dt_growth = 5.0; p->dt_max = 1e-6;
@@ -1250,7 +1251,7 @@ void mg_reset_stats(mg_state *s) {
 uint64_t mg_kernel_launches(void) { return (uint64_t)total_launches(); }
 
 int mg_profile_begin(mg_state *s, int kernel, int level) {
-  if (!s || kernel < MG_PROF_SMOOTH || kernel > MG_PROF_COARSE || level < 0 || level >= s->nlev)
+  if (!s || kernel < MG_PROF_SMOOTH || kernel > MG_PROF_COARSE_FACTOR || level < 0 || level >= s->nlev)
     return fail(s, MG_EINVAL, "mg_profile_begin: bad kernel or level");
   if (s->prof_ev.empty()) {
     s->prof_ev.resize(2 * kProfMax);

@@ -95,7 +95,7 @@ SIGNATURES = {
                                  _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp]),
 }
 MG_PROF_SMOOTH, MG_PROF_LINRES, MG_PROF_COEF, MG_PROF_RESIDUAL, MG_PROF_RESTRICT, MG_PROF_PROLONG = 1, 2, 3, 4, 5, 6
-MG_PROF_COARSE = 7
+MG_PROF_COARSE, MG_PROF_COARSE_FACTOR = 7, 8
 
 
 def lib_path() -> str:
