@@ -109,6 +109,9 @@ typedef struct mg_params {
   int32_t nu_coarse_n;    /* levels whose larger side has <= this many intervals smooth with
                              nu_coarse1 / nu_coarse2 sweeps instead of nu1 / nu2 (0: off) */
   int32_t nu_coarse1, nu_coarse2;
+  int32_t nu_tiny_n;      /* levels whose larger side has <= this many intervals (a subset of the
+                             nu_coarse_n levels) smooth with nu_tiny1 / nu_tiny2 sweeps (0: off) */
+  int32_t nu_tiny1, nu_tiny2;
   int32_t chain_from;     /* mg_solve_steady starts its march on level chain_from (the grid
                              coarsened 2^chain_from times; 1 <= chain_from < levels) and goes
                              back up one level at a time: prolongation, then a march from
@@ -139,7 +142,8 @@ typedef struct mg_state mg_state;
  * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 1, guess_dt_start = 1e-8,
  * coarse_kernel_n = 16,
  * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1, nu_coarse_n = 64,
- * nu_coarse1 = nu_coarse2 = 2 (V(4,4) smoothing on levels larger than 65^2, V(2,2) below),
+ * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels
+ * larger than 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down),
  * chain_from = 1 (the two-level 129^2 -> 257^2 continuation).
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
@@ -243,6 +247,11 @@ int mg_autotune(mg_state *s, int32_t *shapes_out);
  * `tile` (0: 32x2, 1: 32x4, 2: 32x8, 3: 64x2, 4: 64x4, 5: 128x2), 0 for two half sweeps.
  * Results are the same bit for bit whatever the choice.  MG_EINVAL on a bad level or shape. */
 int mg_set_smoother(mg_state *s, int level, int precision, int bx, int by, int fused, int tile);
+
+/* Pre- and post-smoothing sweeps of one level by hand, instead of the rule of the parameters
+ * (nu1 / nu2, nu_coarse_n / nu_coarse1 / nu_coarse2); nu1 = nu2 = -1 restores the rule.
+ * MG_EINVAL on a bad level or counts (both set or both -1, at least one sweep). */
+int mg_set_level_sweeps(mg_state *s, int level, int nu1, int nu2);
 int mg_num_levels(const mg_state *s);
 
 /* Statistics accumulated since creation (or the last mg_reset_stats). */

@@ -109,17 +109,23 @@ class Hierarchy:
 
     def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics,
                  coarsest: int = 2, nu1: int = 4, nu2: int = 4, nu_coarse_n: int = 64,
-                 nu_coarse1: int = 2, nu_coarse2: int = 2):
+                 nu_coarse1: int = 2, nu_coarse2: int = 2, nu_tiny_n: int = 8, nu_tiny1: int = 1,
+                 nu_tiny2: int = 1):
         """Smoothing: nu1 / nu2 sweeps before / after the coarse-grid correction, except on
-        levels whose larger side has at most nu_coarse_n intervals (0: none), which take
-        nu_coarse1 / nu_coarse2."""
+        levels whose larger side has at most nu_tiny_n intervals (nu_tiny1 / nu_tiny2) or else at
+        most nu_coarse_n intervals (nu_coarse1 / nu_coarse2); 0 switches a tier off."""
         self.levels: List[Level] = []
         self.P: List[sp.csr_matrix] = []
         self.nus: List[tuple] = []
         while True:
             self.levels.append(Level(g, u, dt, phys))
-            small = nu_coarse_n > 0 and max(g.nr, g.nz) <= nu_coarse_n
-            self.nus.append((nu_coarse1, nu_coarse2) if small else (nu1, nu2))
+            side = max(g.nr, g.nz)
+            if nu_tiny_n > 0 and side <= nu_tiny_n:
+                self.nus.append((nu_tiny1, nu_tiny2))
+            elif nu_coarse_n > 0 and side <= nu_coarse_n:
+                self.nus.append((nu_coarse1, nu_coarse2))
+            else:
+                self.nus.append((nu1, nu2))
             if min(g.nr, g.nz) <= coarsest or g.nr % 2 or g.nz % 2:
                 break
             gc = g.coarse()

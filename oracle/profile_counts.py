@@ -51,7 +51,7 @@ def unit_times(d, level_n, dt=1e-6, vcycles=3, opt=None):
     t_res = time.perf_counter() - t0
     t0 = time.perf_counter()
     H = mg.Hierarchy(g, u, dt, phys, opt.coarsest, opt.nu1, opt.nu2, opt.nu_coarse_n, opt.nu_coarse1,
-                     opt.nu_coarse2)
+                     opt.nu_coarse2, opt.nu_tiny_n, opt.nu_tiny1, opt.nu_tiny2)
     t_hier = time.perf_counter() - t0
     f = -disc.to_vec(g, F)
     x = np.zeros_like(f)

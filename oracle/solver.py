@@ -35,6 +35,9 @@ class SolverOptions:
     nu_coarse_n: int = 64     # levels with at most this many intervals per side smooth with
     nu_coarse1: int = 2       # nu_coarse1 / nu_coarse2 sweeps (0: nu1 / nu2 everywhere)
     nu_coarse2: int = 2
+    nu_tiny_n: int = 8        # levels with at most this many intervals per side smooth with
+    nu_tiny1: int = 1         # nu_tiny1 / nu_tiny2 sweeps (checked before nu_coarse_n)
+    nu_tiny2: int = 1
     chain_from: int = 1       # continuation starts on the grid coarsened this many times
     eta: float = 1e-3               # inexact-Newton linear tolerance
     max_vcycles: int = 60
@@ -84,7 +87,7 @@ def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: f
         if it == opt.max_newton:
             break
         H = mg.Hierarchy(g, x, dt, phys, opt.coarsest, opt.nu1, opt.nu2, opt.nu_coarse_n, opt.nu_coarse1,
-                         opt.nu_coarse2)
+                         opt.nu_coarse2, opt.nu_tiny_n, opt.nu_tiny1, opt.nu_tiny2)
         tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
         eta = forcing_term(opt, r.max(), tol)
         du, hist = H.solve(-disc.to_vec(g, F), eta, opt.max_vcycles, scale=tn)

@@ -42,6 +42,7 @@ struct LevelBuf {
   int sbx32 = 32, sby32 = 2;     // half-sweep launch shape, FP32 view (autotuned)
   int sw = 1, sw32 = 1;          // fused-sweep tile shape index, FP64 / FP32 (autotuned)
   int fuse = 0, fuse32 = 1;      // fused sweep on this level (FP64: off, see mg_autotune; FP32: autotuned)
+  int nu1 = -1, nu2 = -1;        // sweeps set by mg_set_level_sweeps (-1: the parameters' rule)
 };
 
 }  // namespace
@@ -385,7 +386,11 @@ template <> size_t coarse_smem<float>(const mg_state *s) { return s->cc_smem32; 
 
 // pre- (which = 1) or post-smoothing (2) sweeps on level l
 int nu_of(const mg_state *s, int l, int which) {
-  const bool small = s->prm.nu_coarse_n > 0 && std::max(s->lv[l].nr, s->lv[l].nz) <= s->prm.nu_coarse_n;
+  const int set = which == 1 ? s->lv[l].nu1 : s->lv[l].nu2;
+  if (set >= 0) return set;
+  const int side = std::max(s->lv[l].nr, s->lv[l].nz);
+  if (s->prm.nu_tiny_n > 0 && side <= s->prm.nu_tiny_n) return which == 1 ? s->prm.nu_tiny1 : s->prm.nu_tiny2;
+  const bool small = s->prm.nu_coarse_n > 0 && side <= s->prm.nu_coarse_n;
   if (which == 1) return small ? s->prm.nu_coarse1 : s->prm.nu1;
   return small ? s->prm.nu_coarse2 : s->prm.nu2;
 }
@@ -825,6 +830,7 @@ void mg_params_default(mg_params *p) {
   p->guess_dt_start = 1e-8;
   p->eta_adapt = 1;
   p->nu_coarse_n = 64; p->nu_coarse1 = 2; p->nu_coarse2 = 2;
+  p->nu_tiny_n = 8; p->nu_tiny1 = 1; p->nu_tiny2 = 1;
   p->chain_from = 1;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
@@ -842,6 +848,10 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
   if (p->nu_coarse_n < 0 || (p->nu_coarse_n > 0 && (p->nu_coarse1 < 0 || p->nu_coarse2 < 0 ||
                                                      p->nu_coarse1 + p->nu_coarse2 < 1))) {
     *why = "nu_coarse_n >= 0 and, when set, at least one coarse smoothing sweep";
+    return MG_EINVAL;
+  }
+  if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
+    *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";
     return MG_EINVAL;
   }
   if (!(p->pressure_factor > 0.0) || !(p->D_e > 0.0) || !(p->D_p > 0.0) || p->mu_e < 0 || p->mu_p < 0) {
@@ -1355,6 +1365,18 @@ int mg_set_smoother(mg_state *s, int level, int precision, int bx, int by, int f
   for (int l = 0; l < kMaxLevels; ++l)
     if (s->vexec[l]) { cudaGraphExecDestroy(s->vexec[l]); s->vexec[l] = nullptr; }
   return MG_OK;
+}
+
+int mg_set_level_sweeps(mg_state *s, int level, int nu1, int nu2) {
+  if (!s) return MG_EINVAL;
+  if (level < 0 || level >= s->nlev || nu1 < -1 || nu2 < -1 || (nu1 >= 0) != (nu2 >= 0) ||
+      (nu1 >= 0 && nu1 + nu2 < 1))
+    return fail(s, MG_EINVAL, "mg_set_level_sweeps: bad level %d or sweeps (%d, %d)", level, nu1, nu2);
+  s->lv[level].nu1 = nu1;
+  s->lv[level].nu2 = nu2;
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (s->vexec[l]) { cudaGraphExecDestroy(s->vexec[l]); s->vexec[l] = nullptr; }
+  return setup_coarse_kernel(s);  // the coarse-cycle kernel carries its levels' sweep counts
 }
 
 int mg_num_levels(const mg_state *s) { return s ? s->nlev : 0; }

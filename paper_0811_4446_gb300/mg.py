@@ -45,6 +45,7 @@ class mg_params(ctypes.Structure):
                 ("coarse_kernel_n", ctypes.c_int32), ("coarse_kernel_ctas", ctypes.c_int32),
                 ("coarse_kernel_threads", ctypes.c_int32), ("eta_adapt", ctypes.c_int32),
                 ("nu_coarse_n", ctypes.c_int32), ("nu_coarse1", ctypes.c_int32), ("nu_coarse2", ctypes.c_int32),
+                ("nu_tiny_n", ctypes.c_int32), ("nu_tiny1", ctypes.c_int32), ("nu_tiny2", ctypes.c_int32),
                 ("chain_from", ctypes.c_int32)]
 
 
@@ -84,6 +85,7 @@ SIGNATURES = {
     "mg_reset_stats": (None, [_vp]),
     "mg_kernel_launches": (ctypes.c_uint64, []),
     "mg_set_smoother": (_i, [_vp, _i, _i, _i, _i, _i, _i]),
+    "mg_set_level_sweeps": (_i, [_vp, _i, _i, _i]),
     "mg_profile_begin": (_i, [_vp, _i, _i]),
     "mg_profile_end": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "mg_probe_fp64_gflops": (ctypes.c_double, [_vp]),
@@ -302,6 +304,10 @@ class Solver:
     def set_smoother(self, level: int, precision: int, bx: int, by: int, fused: int, tile: int):
         """Smoother launch of one level by hand (see mg_set_smoother in include/mg.h)."""
         self._check(self.lib.mg_set_smoother(self.h, level, precision, bx, by, fused, tile))
+
+    def set_level_sweeps(self, level: int, nu1: int, nu2: int):
+        """Sweeps of one level by hand (see mg_set_level_sweeps in include/mg.h)."""
+        self._check(self.lib.mg_set_level_sweeps(self.h, level, nu1, nu2))
 
     def autotune(self):
         n = self.lib.mg_num_levels(self.h)
