@@ -1356,7 +1356,7 @@ int mg_set_smoother(mg_state *s, int level, int precision, int bx, int by, int f
   if (!s) return MG_EINVAL;
   if (level < 0 || level >= s->nlev || (precision != 0 && precision != 1) || (fused != 0 && fused != 1))
     return fail(s, MG_EINVAL, "mg_set_smoother: bad level / precision / fused flag");
-  if ((bx != 32 && bx != 64 && bx != 128) || by < 1 || bx * by > 1024 || tile < 0 || tile >= kSweepShapes)
+  if ((bx != 32 && bx != 64 && bx != 128) || by < 1 || bx * by > 256 || tile < 0 || tile >= kSweepShapes)
     return fail(s, MG_EINVAL, "mg_set_smoother: bad block (%d, %d) or tile %d", bx, by, tile);
   LevelBuf &b = s->lv[level];
   if (precision == 0) { b.sbx = bx; b.sby = by; b.fuse = fused; b.sw = tile; }
