@@ -313,9 +313,9 @@ def run_ours(args):
     fp64_probe = mg.probe_fp64_gflops()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     # DRAM bytes read + written per launch in one ncu capture of the kernel (cold caches): the
-    # half sweep of the 257^2 level (profiles/k_smooth_fp64_257.md); the other levels and the
-    # fused FP64 form have no committed capture
-    traffic_ncu = {(256, False): 14347904}
+    # half sweeps of the 257^2 level (k_smooth, profiles/k_smooth_fp64_257.md) and of the 129^2
+    # level (k_smooth_ilp, profiles/smoother_fp64_129.md); the other levels have no capture
+    traffic_ncu = {(256, False): 14347904, (128, False): 3639296}
     levels = []
     for lev, (n_l, ms_l) in enumerate(smooth_prof):
         if not n_l:
@@ -337,9 +337,10 @@ def run_ours(args):
                        "flops_per_launch": flo, "bytes_per_launch": byt,
                        "traffic": traffic_ncu.get((n_iv, fused))})
     dom = max(levels, key=lambda r: r["total_ms"])
+    half_name = "k_smooth_ilp<double>" if dom["nodes_per_side"] <= 129 else "k_smooth<double>"
     roofline = {"bound": "alu",
                 "kernel": ("k_sweep<double> (fused red-black sweep" if dom["fused"] else
-                           "k_smooth<double> (red-black half sweep")
+                           half_name + " (red-black half sweep")
                 + f", {dom['nodes_per_side']}x{dom['nodes_per_side']} level, the largest smoother share)",
                 "achieved": dom["gflops"], "peak": fp64_peak_nominal, "unit": "GFLOP/s", "frac": dom["frac_fp64"],
                 "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",

@@ -1296,7 +1296,9 @@ double mg_probe_fp64_gflops(void *stream) { return probe_fp64_gflops((cudaStream
 
 int mg_autotune(mg_state *s, int32_t *shapes_out) {
   if (!s) return MG_EINVAL;
-  static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+  // half-sweep blocks of at most 128 threads: on the small levels larger blocks leave most SMs
+  // idle (32 x 8 on 129^2: 48 blocks, 11 % slower steady solves), and they never won on 257^2
+  static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
   // the tuning launches write only the correction buffers du and du2 of each level
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
   cudaEvent_t e0, e1;
@@ -1310,8 +1312,8 @@ int mg_autotune(mg_state *s, int32_t *shapes_out) {
       int bi = 1;
       for (int c = 0; c < nc && rc == MG_OK; ++c) {
         float ms = 0.f;
-        rc = prec == 0 ? time_shape<double>(s, l, cand[c][0], cand[c][1], 10, e0, e1, &ms)
-                       : time_shape<float>(s, l, cand[c][0], cand[c][1], 10, e0, e1, &ms);
+        rc = prec == 0 ? time_shape<double>(s, l, cand[c][0], cand[c][1], 20, e0, e1, &ms)
+                       : time_shape<float>(s, l, cand[c][0], cand[c][1], 20, e0, e1, &ms);
         if (ms < best) { best = ms; bi = c; }
       }
       LevelBuf &b = s->lv[l];
