@@ -145,8 +145,6 @@ size_t prepare_coarse_smem(const CoarseSet<T> &host_set, size_t limit);
 template <typename T>
 cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *out[3], double *partials,
                           unsigned *counter, double *out3, cudaStream_t st);
-template <typename T>
-cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st);
 // r = f - J du on level F and its restriction to C in one launch (r stays on chip)
 template <typename T>
 cudaError_t launch_linres_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st);
@@ -168,7 +166,6 @@ cudaError_t launch_update(const Level &L, const StateView &sv, double *partials,
 template <typename T>
 cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st);
 // mixed form
-cudaError_t launch_coef_to32(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);
 cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);
 cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double n0, double *partials,
                                   unsigned *counter, double *out3, cudaStream_t st);

@@ -900,23 +900,6 @@ __device__ __forceinline__ void restrict_node(const LevelT<T> &F, const LevelT<T
   C.du[NE][kc] = T(0); C.du[NP][kc] = T(0); C.du[NV][kc] = T(0);
 }
 
-template <typename T>
-__global__ void k_restrict(LevelT<T> F, LevelT<T> C) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (I > C.nr || J >= C.nz) return;
-  restrict_node<T>(F, C, I, J);
-}
-
-template <typename T>
-cudaError_t launch_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st) {
-  dim3 b(SBX, SBY), g((C.nr + 1 + SBX - 1) / SBX, (C.nz - 1 + SBY - 1) / SBY);
-  k_restrict<T><<<g, b, 0, st>>>(F, C);
-  count_launch();
-  return cudaGetLastError();
-}
-template cudaError_t launch_restrict<double>(const LevelT<double> &, const LevelT<double> &, cudaStream_t);
-template cudaError_t launch_restrict<float>(const LevelT<float> &, const LevelT<float> &, cudaStream_t);
 
 // K4+K5 in one launch: a block computes r = f - J du on the fine nodes under a CX x CY tile of
 // coarse nodes (plus the one-node ring the full weighting reaches) into shared memory and
@@ -1607,21 +1590,6 @@ cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st) {
 template cudaError_t launch_zero_du<double>(const LevelT<double> &, cudaStream_t);
 template cudaError_t launch_zero_du<float>(const LevelT<float> &, cudaStream_t);
 
-// ------------------------------------------------------------------------------------------
-// Mixed form.  FP64 face coefficients of one level -> FP32 copies (coef_to32_node).
-__global__ void k_coef_to32(Level L, LevelT<float> M, double inv_n0) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  if (i > L.nr || j > L.nz) return;
-  coef_to32_node(L, M, inv_n0, (size_t)j * L.P + i);
-}
-
-cudaError_t launch_coef_to32(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st) {
-  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
-  k_coef_to32<<<g, b, 0, st>>>(L, M, 1.0 / n0);
-  count_launch();
-  return cudaGetLastError();
-}
 
 // Outer FP64 defect of the mixed solve: x += e (e from the FP32 cycle, densities x n0), then
 // r = f - J x in FP64, written as the next FP32 right-hand side (densities / n0), with FP64
