@@ -83,8 +83,11 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int c) { return (uint32_t)(
 // Per-thread gather plan.  Thread t always fills 16-byte chunk column c = t % 8 of rows
 // t / 8 + 16 i (i = 0..7) of the A tile, so the pixel coordinates of those eight rows are
 // computed once per CTA; per k block only the tap and channel of column c change.
+// Forward: yb, xb = input row and column of tap (0, 0) (in the padding for border pixels;
+// rows past the output are marked by a huge negative yb), pb = that tap's input pixel index;
+// dgrad: yb, xb, pb = yi + pad, xi + pad, b * Hout.
 struct RowPlan {
-  int yb[8], xb[8], pb[8];  // forward: yo*stride-pad, xo*stride-pad, b*Hin; dgrad: yi+pad, xi+pad, b*Hout
+  int yb[8], xb[8], pb[8];
 };
 
 template <int MODE>
@@ -94,9 +97,10 @@ __device__ __forceinline__ void plan_rows(const ConvArgs &a, int m0, int tid, Ro
     const int m = m0 + (tid >> 3) + 16 * i;
     if (MODE == MODE_FWD) {
       const int xo = m % a.Wout, t = m / a.Wout, yo = t % a.Hout, b = t / a.Hout;
-      P.yb[i] = m < a.Pout ? yo * a.stride - a.pad : -(1 << 28);
-      P.xb[i] = xo * a.stride - a.pad;
-      P.pb[i] = b * a.Hin;
+      const int y0 = yo * a.stride - a.pad, x0 = xo * a.stride - a.pad;
+      P.yb[i] = m < a.Pout ? y0 : -(1 << 28);
+      P.xb[i] = x0;
+      P.pb[i] = (b * a.Hin + y0) * a.Win + x0;
     } else {
       const int xi = m % a.Win, t = m / a.Win, yi = t % a.Hin, b = t / a.Hin;
       P.yb[i] = m < a.M ? yi + a.pad : -(1 << 28);
@@ -117,13 +121,13 @@ __device__ __forceinline__ void gather_stage(const ConvArgs &a, const RowPlan &P
     const bool kv = k < a.Kf;
     const int tap = kv ? k / C : 0, ci = k - tap * C;
     const int kh = tap / a.ks, kw = tap - kh * a.ks;
+    const int toff = kh * a.Win + kw;
     const __nv_bfloat16 *base = ci < a.C1 ? a.x1 + ci : a.x2 + (ci - a.C1);
-    const int ch = ci < a.C1 ? a.C1 : a.C2;
+    const size_t ch = ci < a.C1 ? a.C1 : a.C2;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int y = P.yb[i] + kh, x = P.xb[i] + kw;
-      const bool v = kv && y >= 0 && y < a.Hin && x >= 0 && x < a.Win;
-      const __nv_bfloat16 *src = v ? base + ((size_t)(P.pb[i] + y) * a.Win + x) * ch : a.w;
+      const bool v = kv && (unsigned)(P.yb[i] + kh) < (unsigned)a.Hin && (unsigned)(P.xb[i] + kw) < (unsigned)a.Win;
+      const __nv_bfloat16 *src = v ? base + (size_t)(P.pb[i] + toff) * ch : a.w;
       cp_async16(sa + sw128_off(r0 + 16 * i, c), src, v);
     }
   } else {
