@@ -86,7 +86,7 @@ typedef struct mg_params {
   int32_t max_steps;      /* per march                                         */
   double eta;             /* linear tolerance relative to the Newton residual  */
   double newton_tol;      /* per-step tolerance in a march; 0 -> 0.1 * tol     */
-  double corr_limit_frac; /* reject a step if max|dV| > frac * |V_cathode|     */
+  double corr_limit_frac; /* reject a step if max|dV| > frac * |V_anode - V_cathode| */
   double dt1, dt_growth, dt_max; /* Delta-t ramp of Sec. 2                     */
   double n0;              /* density unit of the FP32 inner cycle (eq. 12's n0), m^-3 */
   int32_t use_graphs;     /* 1: each linear solve is one CUDA-graph launch whose V-cycle loop

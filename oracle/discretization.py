@@ -48,13 +48,17 @@ class Physics:
     pressure_factor: float = 1.0
 
 
-def apply_dirichlet(u: np.ndarray, phys: Physics) -> np.ndarray:
-    """Electrode rows: n_e = n_p = 0, V(z=0) = V_cathode, V(z=d) = V_anode."""
+def apply_dirichlet(u: np.ndarray, phys: Physics, g: Optional[Grid] = None) -> np.ndarray:
+    """Electrode rows: n_e = n_p = 0, V(z=0) = V_cathode, V(z=d) = V_anode; with a grid whose
+    wall is Dirichlet (Sec. 3) also the wall column: n_e = n_p = 0, V linear in z between them."""
     u = u.copy()
     u[0:2, 0, :] = 0.0
     u[0:2, -1, :] = 0.0
     u[2, 0, :] = phys.V_cathode
     u[2, -1, :] = phys.V_anode
+    if g is not None and g.wall_dirichlet:
+        u[0:2, :, -1] = 0.0
+        u[2, :, -1] = phys.V_cathode + (phys.V_anode - phys.V_cathode) * (g.z - g.z[0]) / (g.z[-1] - g.z[0])
     return u
 
 
@@ -153,6 +157,9 @@ def residual(g: Grid, u: np.ndarray, u_old: Optional[np.ndarray], S_e, S_p, dt: 
     F[:, -1, :] = 0.0
     T[:, 0, :] = 0.0
     T[:, -1, :] = 0.0
+    if g.wall_dirichlet:
+        F[:, :, -1] = 0.0
+        T[:, :, -1] = 0.0
     return (F, T) if with_terms else F
 
 
@@ -229,11 +236,11 @@ def jacobian(g: Grid, u: np.ndarray, dt: Optional[float], phys: Physics) -> sp.c
 
 def to_vec(g: Grid, a: np.ndarray) -> np.ndarray:
     """(3, nz+1, nr+1) -> unknown vector (node-major, 3 per node)."""
-    return np.ascontiguousarray(np.moveaxis(a[:, 1:-1, :], 0, -1)).reshape(-1)
+    return np.ascontiguousarray(np.moveaxis(a[:, 1:-1, :g.ni], 0, -1)).reshape(-1)
 
 
 def from_vec(g: Grid, x: np.ndarray) -> np.ndarray:
-    """Unknown vector -> (3, nz+1, nr+1) with zero electrode rows."""
+    """Unknown vector -> (3, nz+1, nr+1) with zeros on the Dirichlet nodes."""
     out = np.zeros((3,) + g.shape)
-    out[:, 1:-1, :] = np.moveaxis(x.reshape(g.nz - 1, g.nr + 1, 3), -1, 0)
+    out[:, 1:-1, :g.ni] = np.moveaxis(x.reshape(g.nz - 1, g.ni, 3), -1, 0)
     return out

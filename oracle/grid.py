@@ -19,6 +19,9 @@ coefficients of eq. 12 (interior) and eq. 13 (axis); the tests check this.
 
 Unknown rows are j = 1..N_z-1 (electrode rows j = 0, N_z carry Dirichlet data),
 i = 0..N_r (axis row: natural finite-volume row; wall row: half cell, zero outer flux).
+With wall_dirichlet (the paper's argon case, Sec. 3: n_e = n_p = 0 on the wall and V
+interpolated linearly along it) the wall column i = N_r carries Dirichlet data too and the
+unknowns are i = 0..N_r-1.
 """
 from __future__ import annotations
 
@@ -26,7 +29,7 @@ import numpy as np
 
 
 class Grid:
-    def __init__(self, nr: int, nz: int, R: float, z: np.ndarray):
+    def __init__(self, nr: int, nz: int, R: float, z: np.ndarray, wall_dirichlet: bool = False):
         z = np.asarray(z, dtype=np.float64)
         if z.shape != (nz + 1,):
             raise ValueError("z must have nz + 1 entries")
@@ -51,17 +54,19 @@ class Grid:
         # z-face conductance (i, j+1/2): volr_i / dz_j, shape (nz, nr+1)
         self.gz = self.volr[None, :] / self.dz[:, None]
         self.shape = (self.nz + 1, self.nr + 1)
-        self.n_nodes_unknown = (self.nz - 1) * (self.nr + 1)
+        self.wall_dirichlet = bool(wall_dirichlet)
+        self.ni = self.nr if self.wall_dirichlet else self.nr + 1   # unknown columns
+        self.n_nodes_unknown = (self.nz - 1) * self.ni
 
     def coarse(self) -> "Grid":
         """Vertex-centred coarsening by two in both directions (nested node subset)."""
         if self.nr % 2 or self.nz % 2:
             raise ValueError("cannot coarsen an odd grid")
-        return Grid(self.nr // 2, self.nz // 2, self.R, self.z[::2])
+        return Grid(self.nr // 2, self.nz // 2, self.R, self.z[::2], self.wall_dirichlet)
 
     # unknown numbering: node-major, three fields per node (n_e, n_p, V)
     def node_index(self):
-        """(nz+1, nr+1) int array of unknown-node numbers (-1 on electrode rows)."""
+        """(nz+1, nr+1) int array of unknown-node numbers (-1 on Dirichlet nodes)."""
         idx = -np.ones(self.shape, dtype=np.int64)
-        idx[1:-1, :] = np.arange(self.n_nodes_unknown).reshape(self.nz - 1, self.nr + 1)
+        idx[1:-1, :self.ni] = np.arange(self.n_nodes_unknown).reshape(self.nz - 1, self.ni)
         return idx

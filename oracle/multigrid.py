@@ -46,6 +46,8 @@ def prolongation(gf: Grid, gc: Grid) -> sp.csr_matrix:
                 if Jc < 1 or Jc > gc.nz - 1:
                     continue
                 for Ic, wr in rw:
+                    if idf[j, i] < 0 or idc[Jc, Ic] < 0:
+                        continue   # Dirichlet wall nodes carry no correction
                     for f in range(3):
                         rows.append(3 * idf[j, i] + f)
                         cols.append(3 * idc[Jc, Ic] + f)
@@ -64,8 +66,8 @@ class Level:
         self.g = g
         self.J = disc.jacobian(g, u, dt, phys)
         nodes = np.arange(g.n_nodes_unknown)
-        jj = nodes // (g.nr + 1) + 1
-        ii = nodes % (g.nr + 1)
+        jj = nodes // g.ni + 1
+        ii = nodes % g.ni
         self.colors = []
         for c in (0, 1):
             nc = nodes[(ii + jj) % 2 == c]

@@ -5,7 +5,8 @@
   u += du, until every field's scale-free residual rho_f <= tol.  The step is
   rejected when Newton needs more than ``max_newton`` iterations (the paper
   observed fewer than 10), when max |dV| exceeds ``corr_limit`` (the "upper
-  limit" on the Newton correction norm of Sec. 2, read as 0.5 |V_cathode|), when
+  limit" on the Newton correction norm of Sec. 2, read as half the applied voltage
+  0.5 |V_anode - V_cathode|), when
   the linear solve fails, or on non-finite values.
 * ``march``: Delta t_1, then Delta t_{k+1} = n Delta t_k (n = 5) capped at dt_max;
   after a rejection go back and retry with the previous accepted Delta t, and
@@ -43,7 +44,7 @@ class SolverOptions:
     max_vcycles: int = 60
     coarsest: int = 2
     max_newton: int = 10
-    corr_limit_frac: float = 0.5    # reject if max|dV| > frac * |V_cathode|
+    corr_limit_frac: float = 0.5    # reject if max|dV| > frac * |V_anode - V_cathode|
     dt1: float = 1e-9
     dt_growth: float = 5.0
     dt_max: float = 1e-6
@@ -74,9 +75,9 @@ def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: f
          opt: SolverOptions):
     """One backward-Euler step; returns (u_new, StepStats).  u is not modified."""
     u_old = u
-    x = disc.apply_dirichlet(u, phys)
+    x = disc.apply_dirichlet(u, phys, g)
     vcyc = []
-    limit = opt.corr_limit_frac * abs(phys.V_cathode)
+    limit = opt.corr_limit_frac * abs(phys.V_anode - phys.V_cathode)
     for it in range(opt.max_newton + 1):
         F, T = disc.residual(g, x, u_old, S_e, S_p, dt, phys, with_terms=True)
         r = disc.rho(F, T)
@@ -162,12 +163,12 @@ def solve_steady(g: Grid, u0, S_e, S_p, phys, tol, opt: SolverOptions, log=None)
         Sp.append(mg.inject(grids[-1], Sp[-1]))
         grids.append(gc)
     k = opt.chain_from
-    u = disc.apply_dirichlet(us[k], phys)
+    u = disc.apply_dirichlet(us[k], phys, grids[k])
     u, ok, rec_c = march(grids[k], u, Se[k], Sp[k], phys, tol, opt, opt.dt1, log)
     if not ok:
         return u0, False, rec_c, []
     for k in range(opt.chain_from - 1, -1, -1):
-        u = disc.apply_dirichlet(prolong_state(grids[k + 1], grids[k], u), phys)
+        u = disc.apply_dirichlet(prolong_state(grids[k + 1], grids[k], u), phys, grids[k])
         u, ok, rec = march(grids[k], u, Se[k], Sp[k], phys, tol, opt, opt.dt_max, log)
         if k > 0:
             rec_c = rec_c + rec

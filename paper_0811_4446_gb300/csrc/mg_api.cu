@@ -636,7 +636,7 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
   LevelBuf &b = s->lv[l0];
   copy_state_async(s, l0, true);
   CK(cudaGetLastError());
-  const double limit = s->prm.corr_limit_frac * std::fabs(s->prm.V_cathode);
+  const double limit = s->prm.corr_limit_frac * std::fabs(s->prm.V_anode - s->prm.V_cathode);
   int rc;
   int reason = MG_ENOCONV;
   double rho[3], tn[3];

@@ -199,3 +199,69 @@ def test_block_structure_of_eq14():
     off = J[3 * k:3 * k + 3, 3 * kn:3 * kn + 3]
     assert (diag != 0).sum() == 7 and diag[0, 1] == 0 and diag[1, 0] == 0
     assert (off != 0).sum() == 5 and off[2, 0] == 0 and off[2, 1] == 0
+
+
+# ---------------------------------------------------------------- Dirichlet wall (Sec. 3)
+def _wall_grid(n):
+    return Grid(n, n, 1e-2, W.z_nodes(n, 1e-2), wall_dirichlet=True)
+
+
+def test_dirichlet_wall_values_and_unknowns():
+    """The argon case's wall (Sec. 3): n_e = n_p = 0 and V linear in z along r = R; the wall
+    column carries no unknowns and no residual rows."""
+    g = _wall_grid(8)
+    phys = disc.Physics(V_cathode=0.0, V_anode=255.9)
+    u = disc.apply_dirichlet(np.ones((3,) + g.shape), phys, g)
+    assert np.all(u[0:2, :, -1] == 0.0)
+    assert np.allclose(u[2, :, -1], 255.9 * (g.z - g.z[0]) / (g.z[-1] - g.z[0]), rtol=1e-15, atol=0)
+    assert g.n_nodes_unknown == (g.nz - 1) * g.nr and (g.node_index()[:, -1] == -1).all()
+    F = disc.residual(g, u, None, np.ones(g.shape), np.ones(g.shape), None, phys)
+    assert np.all(F[:, :, -1] == 0.0)
+    x = np.arange(3.0 * g.n_nodes_unknown)
+    assert np.array_equal(disc.to_vec(g, disc.from_vec(g, x)), x)
+
+
+def test_flux_divergence_telescopes_with_dirichlet_wall():
+    """Summed over the unknown rows the flux divergence equals the flux through the electrode
+    faces of the unknown columns plus the flux into the wall."""
+    rng = np.random.default_rng(11)
+    g = _wall_grid(16)
+    phys = disc.Physics(V_cathode=0.0, V_anode=255.9)
+    u = _random_state(g, rng, V_c=-255.9)
+    u = disc.apply_dirichlet(u, phys, g)
+    S = 1e20 * rng.random(g.shape)
+    F = disc.residual(g, u, None, S, S, None, phys)
+    (mer, der, mpr, dpr), (mez, dez, mpz, dpz) = disc.face_transport(g, u[2], phys)
+    ni = g.ni
+    for fi, s, (mr, dr_), (mz, dz_) in ((0, -1.0, (mer, der), (mez, dez)), (1, 1.0, (mpr, dpr), (mpz, dpz))):
+        n, V = u[fi], u[2]
+        cath = disc.sg_flux(g.gz[0, :ni], mz[0, :ni], dz_[0, :ni], s, n[0, :ni], n[1, :ni], V[0, :ni], V[1, :ni])
+        anod = disc.sg_flux(g.gz[-1, :ni], mz[-1, :ni], dz_[-1, :ni], s, n[-2, :ni], n[-1, :ni], V[-2, :ni],
+                            V[-1, :ni])
+        wall = disc.sg_flux(g.gr[1:-1, -1], mr[1:-1, -1], dr_[1:-1, -1], s, n[1:-1, -2], n[1:-1, -1], V[1:-1, -2],
+                            V[1:-1, -1])
+        net_out = anod.sum() - cath.sum() + wall.sum()
+        lhs = (F[fi, 1:-1, :ni] + g.A[1:-1, :ni] * S[1:-1, :ni]).sum()
+        assert np.isclose(lhs, net_out, rtol=1e-10, atol=1e-12 * np.abs(F[fi]).sum()), (lhs, net_out)
+
+
+@pytest.mark.parametrize("dt", [1e-9, None])
+def test_jacobian_matches_finite_differences_dirichlet_wall(dt):
+    rng = np.random.default_rng(4)
+    g = _wall_grid(8)
+    phys = disc.Physics(V_cathode=0.0, V_anode=255.9)
+    u = disc.apply_dirichlet(_random_state(g, rng), phys, g)
+    u_old = disc.apply_dirichlet(_random_state(g, rng), phys, g)
+    S = 1e20 * rng.random(g.shape)
+    J = disc.jacobian(g, u, dt, phys)
+    assert J.shape == (3 * g.n_nodes_unknown,) * 2
+    F0 = lambda x: disc.to_vec(g, disc.residual(g, x, u_old, S, S, dt, phys))
+    for _ in range(4):
+        v = disc.from_vec(g, rng.standard_normal(3 * g.n_nodes_unknown))
+        v[0:2] *= 1e12
+        eps = 1e-4
+        fd = (F0(u + eps * v) - F0(u - eps * v)) / (2 * eps)
+        jv = J @ disc.to_vec(g, v)
+        for f in range(3):
+            a, b = fd[f::3], jv[f::3]
+            assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), (f, np.linalg.norm(a - b), np.linalg.norm(b))

@@ -113,3 +113,21 @@ def test_vcycle_factor_independent_of_grid_size():
     facs = [_factor(n, 1e-9) for n in (16, 32, 64, 128)]
     assert max(facs) < 0.15, facs
     assert facs[-1] < 2.0 * facs[1] + 0.02, facs
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_vcycle_with_dirichlet_wall_matches_dense_solve(n):
+    """The argon case's boundary (Sec. 3): Dirichlet wall; the V-cycle still converges to the
+    equilibrated dense solution of the smaller unknown set."""
+    d = W.argon(n, a=30.0, b=24.0)
+    g = Grid(d.nr, d.nz, d.R, d.z, wall_dirichlet=True)
+    phys = disc.Physics(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, 1e-9, phys, with_terms=True)
+    H = mg.Hierarchy(g, u, 1e-9, phys)
+    f = -disc.to_vec(g, F)
+    scale = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    x, hist = H.solve(f, 1e-13, 80, scale=scale)
+    xd = _dense_reference(H.levels[0].J, f)
+    for k in range(3):
+        assert np.abs(x[k::3] - xd[k::3]).max() <= 1e-9 * np.abs(xd[k::3]).max(), k

@@ -76,6 +76,7 @@ class Discharge:
     np0: np.ndarray
     V0: np.ndarray
     seed: int
+    wall_dirichlet: bool = False   # the argon case: n = 0 and V linear in z on the wall r = R
 
     @property
     def r(self) -> np.ndarray:
@@ -144,6 +145,44 @@ def make_discharge(n: int, *, seed: int = 0, V_cathode: float = -200.0, use_tabl
                      pressure_factor=pressure_factor,
                      table=transport_table(table_seed) if use_table else None,
                      S_e=S.copy(), S_p=S.copy(), ne0=ne0, np0=np0, V0=V0, seed=seed)
+
+
+# --- the paper's argon discharge (Sec. 3) ----------------------------------------------
+ARGON_P_TORR = 0.514           # pd = 75 Pa cm at d = 1.1 cm
+ARGON_MU_P = 0.22              # stand-in ion mobility (m^2 / V s): the paper's value comes from
+                               # its ref. [7] and is not printed
+
+
+def argon_sources(r, z, R, L, a, b):
+    """The analytic source terms of Sec. 3 (m^-3 s^-1) with the length scale L = d."""
+    rr, zz = np.meshgrid(r, z)
+    x = zz / L
+    radial = 1.0 / (1.0 + np.exp(a * rr / R - b))
+    S_p = 0.35e22 * x ** 2 * np.exp(-50.0 * x ** 8) * radial
+    S_e = 1.75e22 * (x - 0.5) * np.exp(-40.0 * (x - 0.5) ** 2) * (x > 0.5) * radial
+    return S_e, S_p
+
+
+def argon(n: int, a: float = 30.0, b: float = 24.0) -> Discharge:
+    """The glow discharge of Sec. 3 on an (n+1)^2 node grid: d = 1.1 cm, R = 2.7 cm, p = 0.514
+    torr, V = 0 at z = 0 (cathode) and 255.9 V at z = d, Dirichlet walls (n = 0, V linear in z),
+    mu_e = 30 / p, D_e = mu_e x 1 V, D_p = mu_p x 0.026 V (the printed "D_e" of the ion line read
+    as D_p), the analytic sources with (a, b) = (30, 24) or (10, 1); z stretched as the other
+    workloads; initial densities the other workloads' Gaussian, zero on the wall."""
+    if n < 2 or (n & (n - 1)):
+        raise ValueError("N must be a power of two >= 2")
+    R, d = 2.7e-2, 1.1e-2
+    z = z_nodes(n, d)
+    r = r_nodes(n, R)
+    S_e, S_p = argon_sources(r, z, R, d, a, b)
+    ne0, np0, V0 = initial_state(r, z, R, d, 0.0, 255.9)
+    ne0[:, -1] = 0.0
+    np0[:, -1] = 0.0
+    mu_e = 30.0 / ARGON_P_TORR
+    return Discharge(nr=n, nz=n, R=R, d=d, z=z, V_cathode=0.0, V_anode=255.9,
+                     mu_e=mu_e, D_e=mu_e * 1.0, mu_p=ARGON_MU_P, D_p=ARGON_MU_P * 0.026,
+                     pressure_factor=1.0, table=None, S_e=S_e, S_p=S_p, ne0=ne0, np0=np0, V0=V0,
+                     seed=0, wall_dirichlet=True)
 
 
 # --- the five workloads -------------------------------------------------------------
