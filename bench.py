@@ -439,6 +439,36 @@ def measure_forms(args, dev, peaks):
         s.close()
     chain["schedule"] = "33^2 -> 65^2 -> 129^2 -> 257^2, dt1 = 1 ns x5 per step, dt_max = 1 s"
     out["chain_uncapped_257"] = chain
+    # the paper's own argon discharge (Dirichlet walls, analytic sources; the ion mobility is a
+    # stand-in) at 257^2, FP64, with the two-level capped schedule and the paper's schedule
+    argon = {}
+    for a, b in ((30.0, 24.0), (10.0, 1.0)):
+        da = W.argon(256, a=a, b=b)
+        ins_a = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (da.ne0, da.np0, da.V0)]
+        row = {}
+        for name, kw in (("two_level_capped", {}), ("chain_uncapped", dict(chain_from=3, dt_max=1.0))):
+            s = mg.from_discharge(da, **kw)
+            s.autotune()
+            times = []
+            for k in range(3):
+                s.set_state(*ins_a)
+                s.reset_stats()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, st = s.solve_steady(TOL)
+                torch.cuda.synchronize()
+                if rc != mg.MG_OK:
+                    raise RuntimeError("argon steady solve failed")
+                if k > 0:
+                    times.append(time.perf_counter() - t0)
+            row[name] = {"solves_per_s": 1.0 / statistics.median(times), "ms": 1000 * statistics.median(times),
+                         "steps": st["steps_accepted"] + st["steps_rejected"], "newton": st["newton_iterations"],
+                         "vcycles": st["vcycles"]}
+            s.close()
+        argon[f"a{a:g}_b{b:g}"] = row
+    argon["workload"] = ("257x257 nodes, d = 1.1 cm, R = 2.7 cm, 0 V / 255.9 V, Dirichlet walls, "
+                         "mu_e = 30/p at 0.514 torr, stand-in mu_p = 0.22 m^2/Vs, FP64, rho <= 1e-8")
+    out["argon_257"] = argon
     # FP32 inner V-cycle of the mixed form at 1025^2 (transient physics, dt = 1 ns)
     d = W.transient_1025()
     nodes = (d.nr + 1) * (d.nz - 1)

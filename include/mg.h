@@ -116,6 +116,9 @@ typedef struct mg_params {
                              coarsened 2^chain_from times; 1 <= chain_from < levels) and goes
                              back up one level at a time: prolongation, then a march from
                              dt_max on each finer level (Sec. 2: finer and finer grids) */
+  int32_t wall_dirichlet; /* 0: zero normal flux and dV/dr = 0 on the wall r = R (half-cell rows);
+                             1: the argon case of Sec. 3: n_e = n_p = 0 and V linear in z between
+                             the electrodes on the wall, which then carries no unknowns */
 } mg_params;
 
 /* Per-call statistics. */
@@ -144,7 +147,7 @@ typedef struct mg_state mg_state;
  * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1, nu_coarse_n = 64,
  * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels
  * larger than 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down),
- * chain_from = 1 (the two-level 129^2 -> 257^2 continuation).
+ * chain_from = 1 (the two-level 129^2 -> 257^2 continuation), wall_dirichlet = 0.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on
@@ -293,8 +296,8 @@ double mg_probe_fp64_gflops(void *stream);
  * rows, i fastest) and rho is host memory.  ne_old, np_old, V_old are read only when dt > 0
  * (dt <= 0: steady residual).  F_ne, F_np, F_V receive the rows when non-NULL (all three or
  * none).  The electrode rows of the inputs must hold the Dirichlet values.
- * Limits: nr, nz powers of two with 2 <= nr, nz <= 1024; at most 64 table rows; larger
- * inputs return MG_EINVAL.  It calls no cudaMalloc, cudaFree or allocating library routine:
+ * Limits: nr, nz powers of two with 2 <= nr, nz <= 1024; at most 64 table rows; the zero-flux
+ * wall only (wall_dirichlet = 1 returns MG_EINVAL); larger inputs return MG_EINVAL.  It calls no cudaMalloc, cudaFree or allocating library routine:
  * its scratch (about 232 KB: geometry, table, block partial sums, a reduction counter and the
  * results) is one file-scope device array that every GPU loading the library holds until
  * the process exits.  All calls share that array and it keeps the last call's contents, so

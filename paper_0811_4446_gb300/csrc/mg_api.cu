@@ -130,7 +130,7 @@ struct Carver {
 };
 
 constexpr int kFieldsPerLevel = 48;  // u 3, uold 3, S 2, cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, ubak 3, du2 3
-constexpr int kGeoPerLevel = 5;      // dz, dzc, volr, wz, 1/dz (each up to max(nr, nz) + 1)
+constexpr int kGeoPerLevel = 6;      // dz, dzc, volr, wz, 1/dz, z fraction (each up to max(nr, nz) + 1)
 
 // blocks of the largest reduction launch (32 x 2 threads per block)
 size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz + 1 + 1) / 2); }
@@ -167,6 +167,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
       b.L.volr = b.geo + 2 * glen;
       b.L.wz = b.geo + 3 * glen;
       b.L.idz = b.geo + 4 * glen;
+      b.L.zf = b.geo + 5 * glen;
     }
     b.M = LevelT<float>();
     b.geo32 = nullptr;
@@ -191,6 +192,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
         b.M.volr = b.geo32 + 2 * glen;
         b.M.wz = b.geo32 + 3 * glen;
         b.M.idz = b.geo32 + 4 * glen;
+        b.M.zf = b.geo32 + 5 * glen;
       }
     }
   }
@@ -214,10 +216,12 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
 void host_geometry(const std::vector<double> &zl, int nr, double R, std::vector<double> &out, int glen) {
   const int nz = (int)zl.size() - 1;
   out.assign((size_t)kGeoPerLevel * glen, 0.0);
-  double *dz = out.data(), *dzc = dz + glen, *volr = dz + 2 * glen, *wz = dz + 3 * glen, *idz = dz + 4 * glen;
+  double *dz = out.data(), *dzc = dz + glen, *volr = dz + 2 * glen, *wz = dz + 3 * glen, *idz = dz + 4 * glen,
+         *zf = dz + 5 * glen;
   const double dr = R / nr;
   for (int j = 0; j < nz; ++j) dz[j] = zl[j + 1] - zl[j];
   for (int j = 0; j < nz; ++j) idz[j] = 1.0 / dz[j];
+  for (int j = 0; j <= nz; ++j) zf[j] = (zl[j] - zl[0]) / (zl[nz] - zl[0]);
   for (int j = 1; j < nz; ++j) dzc[j] = 0.5 * (dz[j - 1] + dz[j]);
   for (int i = 0; i <= nr; ++i) volr[i] = i * dr * dr;
   volr[0] = dr * dr / 8.0;
@@ -832,6 +836,7 @@ void mg_params_default(mg_params *p) {
   p->nu_coarse_n = 64; p->nu_coarse1 = 2; p->nu_coarse2 = 2;
   p->nu_tiny_n = 8; p->nu_tiny1 = 1; p->nu_tiny2 = 1;
   p->chain_from = 1;
+  p->wall_dirichlet = 0;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
   p->coarse_kernel_threads = 512;
@@ -850,6 +855,7 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
     *why = "nu_coarse_n >= 0 and, when set, at least one coarse smoothing sweep";
     return MG_EINVAL;
   }
+  if (p->wall_dirichlet != 0 && p->wall_dirichlet != 1) { *why = "wall_dirichlet must be 0 or 1"; return MG_EINVAL; }
   if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
     *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";
     return MG_EINVAL;
@@ -946,6 +952,7 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     b.M.dr = (float)(g->R / b.nr);
     b.L.idr = 1.0 / b.L.dr;
     b.M.idr = (float)b.L.idr;
+    b.L.ni = b.M.ni = p->wall_dirichlet ? b.nr : b.nr + 1;
     if (cudaMemcpyAsync(b.geo, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream) !=
         cudaSuccess)
       rc = fail(s, MG_ECUDA, "geometry copy");
@@ -1114,8 +1121,12 @@ int mg_jacobian_apply(mg_state *s, double dt, const double *v_ne, const double *
   CK(launch_coef(b.L, b.sv, s->tr, s->stream));
   CK(launch_factor(b.L, nullptr, dt, s->prm.n0, s->stream));
   const double *src[3] = {v_ne, v_np, v_V};
-  for (int q = 0; q < 3; ++q)
+  for (int q = 0; q < 3; ++q) {
     if ((rc = copy_in(s, b, b.L.du[q], src[q], where, 1, b.nz - 1))) return rc;
+    // a Dirichlet wall carries no unknowns: its entries of v do not enter J v
+    if (b.L.ni == b.nr)
+      CK(cudaMemset2DAsync(b.L.du[q] + b.nr, b.P * sizeof(double), 0, sizeof(double), b.nz + 1, s->stream));
+  }
   CK(launch_linres<double>(b.L, b.L.du, nullptr, b.L.r, nullptr, nullptr, nullptr, s->stream));
   double *dst[3] = {o_ne, o_np, o_V};
   for (int q = 0; q < 3; ++q)

@@ -39,9 +39,11 @@ struct Transport {
 template <typename T>
 struct LevelT {
   int nr, nz, P;
+  int ni;                    // unknown columns: nr + 1, or nr with a Dirichlet wall
   T dr;
   const T *dz, *dzc, *volr;  // nz, nz+1, nr+1 (geometry in the level's arithmetic type)
   const T *idz;              // 1 / dz (nz entries)
+  const T *zf;               // (z_j - z_0) / (z_nz - z_0) (nz + 1 entries; the wall's V profile)
   T idr;                     // 1 / dr
   const T *wz;               // odd fine row j: weight of the upper coarse node (nz+1 entries)
   const T *gR, *gZ, *Ak;     // node arrays: r-face and z-face Poisson conductances, (e/eps0) A

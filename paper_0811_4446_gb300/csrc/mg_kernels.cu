@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * CBY + threadIdx.y + 1;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  if (i <= L.nr && j < L.nz) {
+  if (i < L.ni && j < L.nz) {
     const int P = L.P;
     const size_t k = (size_t)j * P + i;
     const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
@@ -549,7 +549,7 @@ __device__ __forceinline__ void factor_node(const Level &L, const LevelT<float> 
 __global__ void k_factor(Level L, LevelT<float> M, int mixed, double dt_inv, double n0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i > L.nr || j >= L.nz) return;
+  if (i >= L.ni || j >= L.nz) return;
   factor_node(L, M, mixed, dt_inv, n0, i, j);
 }
 
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(32 * CBY) k_factor_levels(const LevelSet *__re
   const int j = blockIdx.y * CBY + threadIdx.y;
   if (i > L.nr || j > L.nz) return;
   if (mixed) coef_to32_node(L, S->M[l], 1.0 / n0, (size_t)j * L.P + i);
-  if (j >= 1 && j < L.nz) factor_node(L, S->M[l], mixed, dt_inv, n0, i, j);
+  if (j >= 1 && j < L.nz && i < L.ni) factor_node(L, S->M[l], mixed, dt_inv, n0, i, j);
 }
 
 cudaError_t launch_factor_levels(const LevelSet *S, const Level &La, int a, int b, bool mixed, double dt, double n0,
@@ -678,7 +678,7 @@ template <typename T>
 __global__ void k_smooth(LevelT<T> L, int color) {
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
-  if (j >= L.nz || i > L.nr) return;
+  if (j >= L.nz || i >= L.ni) return;
   smooth_node<T>(L, i, j);
 }
 
@@ -691,7 +691,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, 1) k_smooth_ilp(LevelT<T> L, int color) {
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
-  if (j >= L.nz || i > L.nr) return;
+  if (j >= L.nz || i >= L.ni) return;
   smooth_node<T>(L, i, j);
 }
 
@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
     const int li = q % EX, lj = q / EX;
     const int i = i0 + li, j = j0 + lj;
     T ve = 0, vp = 0, vV = 0;
-    if (i >= 0 && i <= nr && j >= 1 && j < nz && ((i + j) & 1) == 0) {
+    if (i >= 0 && i < L.ni && j >= 1 && j < nz && ((i + j) & 1) == 0) {
       const size_t k = (size_t)j * P + i;
       const Triple<T> x = node_update<T>(L, i, k, gload<T>(io.in, k + 1), gload<T>(io.in, k - 1),
                                          gload<T>(io.in, k + P), gload<T>(io.in, k - P));
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
   {
     const int li = threadIdx.x % TX + 1, lj = threadIdx.x / TX + 1;
     const int i = i0 + li, j = j0 + lj;
-    if (i <= nr && j >= 1 && j < nz) {
+    if (i < L.ni && j >= 1 && j < nz) {
       const size_t k = (size_t)j * P + i;
       Triple<T> x;
       if (((i + j) & 1) == 0) {
@@ -856,7 +856,7 @@ __global__ void k_linres(LevelT<T> L, const T *v0, const T *v1, const T *v2, con
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
-  if (i <= L.nr && j < L.nz) {
+  if (i < L.ni && j < L.nz) {
     const Triple<T> r = linres_node<T>(L, i, j, v0, v1, v2, f0, f1, f2, o0, o1, o2);
     acc[0] = (double)r.e * r.e; acc[1] = (double)r.p * r.p; acc[2] = (double)r.V * r.V;
   }
@@ -890,7 +890,7 @@ __device__ __forceinline__ void restrict_node(const LevelT<T> &F, const LevelT<T
 #pragma unroll
     for (int di = -1; di <= 1; ++di) {
       const int i = 2 * I + di;
-      if (i < 0 || i > F.nr) continue;
+      if (i < 0 || i >= F.ni) continue;   // Dirichlet wall nodes carry no residual
       const T w = wz * (di == 0 ? T(1) : T(0.5));
       const size_t kf = (size_t)j * F.P + i;
       s0 += w * F.r[NE][kf]; s1 += w * F.r[NP][kf]; s2 += w * F.r[NV][kf];
@@ -915,14 +915,14 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) 
   for (int t = tid; t < FW * FH; t += blockDim.x) {
     const int fi = 2 * I0 - 1 + t % FW, fj = 2 * J0 - 1 + t / FW;
     Triple<T> r{T(0), T(0), T(0)};
-    if (fi >= 0 && fi <= F.nr && fj < F.nz)
+    if (fi >= 0 && fi < F.ni && fj < F.nz)
       r = linres_val<T>(F, fi, fj, F.du[NE], F.du[NP], F.du[NV], F.f[NE], F.f[NP], F.f[NV]);
     sr[0][t] = r.e; sr[1][t] = r.p; sr[2][t] = r.V;
   }
   __syncthreads();
   for (int t = tid; t < CX * CY; t += blockDim.x) {
     const int I = I0 + t % CX, J = J0 + t / CX;
-    if (I > C.nr || J >= C.nz) continue;
+    if (I >= C.ni || J >= C.nz) continue;
     const size_t kc = (size_t)J * C.P + I;
     T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) 
 #pragma unroll
       for (int di = -1; di <= 1; ++di) {
         const int i = 2 * I + di;
-        if (i < 0 || i > F.nr) continue;
+        if (i < 0 || i >= F.ni) continue;
         const T w = wz * (di == 0 ? T(1) : T(0.5));
         const int ls = (j - (2 * J0 - 1)) * FW + (i - (2 * I0 - 1));
         s0 += w * sr[0][ls]; s1 += w * sr[1][ls]; s2 += w * sr[2][ls];
@@ -979,7 +979,7 @@ template <typename T>
 __global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i > F.nr || j >= F.nz) return;
+  if (i >= F.ni || j >= F.nz) return;
   prolong_node<T>(C, F, i, j);
 }
 
@@ -1060,22 +1060,25 @@ constexpr int kSmemGJ = 48;
 // Adds the Jacobian entries of the coarsest level into A (row-major, leading dimension ld,
 // zeroed by the caller); thread tid of nthr assembles the rows of nodes tid, tid + nthr, ...
 __device__ void assemble_coarse(const Level &L, double dt_inv, double *A, int ld, int tid, int nthr) {
-  const int nn = (L.nr + 1) * (L.nz - 1);
+  const int W = L.ni;  // unknown columns (node = (j - 1) * W + i)
+  const int nn = W * (L.nz - 1);
   for (int node = tid; node < nn; node += nthr) {
-    const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
+    const int j = node / W + 1, i = node % W;
     const size_t k = (size_t)j * L.P + i;
     const double Av = L.volr[i] * L.dzc[j];
     double a11 = Av * dt_inv, a22 = Av * dt_inv, a13 = 0, a23 = 0, a33 = 0;
     const int re = 3 * node, rp = re + 1, rv = re + 2;
     auto put = [&](int row, int col, double v) { A[(size_t)row * ld + col] += v; };
-    // east
+    // east (towards a Dirichlet wall node only the diagonal terms remain)
     if (i < L.nr) {
       const int nb = 3 * (node + 1);
       const double g = (i + 0.5) * L.dzc[j];
       a11 += L.cr[CGE][k]; a13 -= L.cr[CVE][k]; a22 += L.cr[CGP][k]; a23 -= L.cr[CVP][k]; a33 -= g;
-      put(re, nb, -L.cr[CFE][k]); put(re, nb + 2, L.cr[CVE][k]);
-      put(rp, nb + 1, -L.cr[CFP][k]); put(rp, nb + 2, L.cr[CVP][k]);
-      put(rv, nb + 2, g);
+      if (i + 1 < W) {
+        put(re, nb, -L.cr[CFE][k]); put(re, nb + 2, L.cr[CVE][k]);
+        put(rp, nb + 1, -L.cr[CFP][k]); put(rp, nb + 2, L.cr[CVP][k]);
+        put(rv, nb + 2, g);
+      }
     }
     if (i > 0) {
       const int nb = 3 * (node - 1);
@@ -1090,7 +1093,7 @@ __device__ void assemble_coarse(const Level &L, double dt_inv, double *A, int ld
       const double g = L.volr[i] / L.dz[j];
       a11 += L.cz[CGE][k]; a13 -= L.cz[CVE][k]; a22 += L.cz[CGP][k]; a23 -= L.cz[CVP][k]; a33 -= g;
       if (j + 1 < L.nz) {
-        const int nb = 3 * (node + L.nr + 1);
+        const int nb = 3 * (node + W);
         put(re, nb, -L.cz[CFE][k]); put(re, nb + 2, L.cz[CVE][k]);
         put(rp, nb + 1, -L.cz[CFP][k]); put(rp, nb + 2, L.cz[CVP][k]);
         put(rv, nb + 2, g);
@@ -1101,7 +1104,7 @@ __device__ void assemble_coarse(const Level &L, double dt_inv, double *A, int ld
       const double g = L.volr[i] / L.dz[j - 1];
       a11 += L.cz[CFE][ks]; a13 -= L.cz[CVE][ks]; a22 += L.cz[CFP][ks]; a23 -= L.cz[CVP][ks]; a33 -= g;
       if (j - 1 >= 1) {
-        const int nb = 3 * (node - L.nr - 1);
+        const int nb = 3 * (node - W);
         put(re, nb, -L.cz[CGE][ks]); put(re, nb + 2, L.cz[CVE][ks]);
         put(rp, nb + 1, -L.cz[CGP][ks]); put(rp, nb + 2, L.cz[CVP][ks]);
         put(rv, nb + 2, g);
@@ -1120,7 +1123,7 @@ __device__ void assemble_coarse(const Level &L, double dt_inv, double *A, int ld
 // updated, so the multiplier A[r][col] stays intact during its step (two barriers per column).
 __global__ void __launch_bounds__(CT) k_coarse_factor_smem(Level L, double dt_inv, double *Minv, double *rs,
                                                            double *cs, int *flag) {
-  const int n = 3 * (L.nr + 1) * (L.nz - 1);
+  const int n = 3 * L.ni * (L.nz - 1);
   const int W = 2 * n;
   const int tid = threadIdx.x, lane = tid & 31;
   __shared__ double sAB[kSmemGJ * 2 * kSmemGJ];
@@ -1200,7 +1203,7 @@ __global__ void __launch_bounds__(CT) k_coarse_factor_smem(Level L, double dt_in
 // Larger coarsest levels: the same steps in global memory (M is n x n scratch).
 __global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, double *M, double *Minv,
                                                       double *rs, double *cs, int *flag) {
-  const int nn = (L.nr + 1) * (L.nz - 1);
+  const int nn = L.ni * (L.nz - 1);
   const int n = 3 * nn;
   const int tid = threadIdx.x;
   __shared__ double fac[3 * 9 * 9];
@@ -1276,7 +1279,7 @@ __global__ void __launch_bounds__(CT) k_coarse_factor(Level L, double dt_inv, do
 
 cudaError_t launch_coarse_factor(const Level &L, double dt, double *M, double *Minv, double *rs, double *cs,
                                  int *flag, cudaStream_t st) {
-  const int n = 3 * (L.nr + 1) * (L.nz - 1);
+  const int n = 3 * L.ni * (L.nz - 1);
   if (n > 3 * 9 * 9) return cudaErrorInvalidValue;
   const double dti = dt > 0 ? 1.0 / dt : 0.0;
   if (n <= kSmemGJ) k_coarse_factor_smem<<<1, CT, 0, st>>>(L, dti, Minv, rs, cs, flag);
@@ -1291,12 +1294,12 @@ cudaError_t launch_coarse_factor(const Level &L, double dt, double *M, double *M
 template <typename T>
 __device__ __forceinline__ void coarse_solve_block(const LevelT<T> &L, const double *Minv, const double *rs,
                                                    const double *cs, double nscale, int nthreads) {
-  const int nn = (L.nr + 1) * (L.nz - 1);
+  const int nn = L.ni * (L.nz - 1);
   const int n = 3 * nn;
   __shared__ double fs[3 * 9 * 9];
   for (int q = threadIdx.x; q < n; q += nthreads) {
     const int node = q / 3, fld = q % 3;
-    const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
+    const int j = node / L.ni + 1, i = node % L.ni;
     const double sc = fld == NV ? 1.0 : nscale;
     fs[q] = rs[q] * sc * (double)L.f[fld][(size_t)j * L.P + i];
   }
@@ -1305,7 +1308,7 @@ __device__ __forceinline__ void coarse_solve_block(const LevelT<T> &L, const dou
     double x = 0.0;
     for (int c = 0; c < n; ++c) x += Minv[(size_t)q * n + c] * fs[c];
     const int node = q / 3, fld = q % 3;
-    const int j = node / (L.nr + 1) + 1, i = node % (L.nr + 1);
+    const int j = node / L.ni + 1, i = node % L.ni;
     const double sc = fld == NV ? 1.0 : 1.0 / nscale;
     L.du[fld][(size_t)j * L.P + i] = (T)(cs[q] * x * sc);
   }
@@ -1345,7 +1348,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
       for (int color = 0; color < 2; ++color) {
         for (int t = tid; t < (L.nz - 1) * half; t += nth) {
           const int j = t / half + 1, i = 2 * (t % half) + ((j + color) & 1);
-          if (i <= L.nr) smooth_node<T>(L, i, j);
+          if (i < L.ni) smooth_node<T>(L, i, j);
         }
         bar();
       }
@@ -1354,13 +1357,13 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
     const LevelT<T> &L = S.lv[q];
     const LevelT<T> &C = S.lv[q + 1];
     sweeps(L, S.nu1[q]);
-    const int W = L.nr + 1;
+    const int W = L.ni;
     for (int t = tid; t < (L.nz - 1) * W; t += nth) {
       const int j = t / W + 1, i = t % W;
       linres_node<T>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP], L.f[NV], L.r[NE], L.r[NP], L.r[NV]);
     }
     bar();
-    const int Wc = C.nr + 1;
+    const int Wc = C.ni;
     for (int t = tid; t < (C.nz - 1) * Wc; t += nth) restrict_node<T>(L, C, t % Wc, t / Wc + 1);
     bar();
   }
@@ -1368,7 +1371,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
   bar();
   for (int q = S.n - 2; q >= 0; --q) {
     const LevelT<T> &F = S.lv[q];
-    const int W = F.nr + 1;
+    const int W = F.ni;
     for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(S.lv[q + 1], F, t % W, t / W + 1);
     bar();
     sweeps(F, S.nu2[q]);
@@ -1444,7 +1447,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
       for (int color = 0; color < 2; ++color) {
         for (int t = tid; t < (L.nz - 1) * half; t += nth) {
           const int j = t / half + 1, i = 2 * (t % half) + ((j + color) & 1);
-          if (i <= L.nr) smooth_node<T>(L, i, j);
+          if (i < L.ni) smooth_node<T>(L, i, j);
         }
         __syncthreads();
       }
@@ -1453,13 +1456,13 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
     const LevelT<T> &L = lv[q];
     const LevelT<T> &C = lv[q + 1];
     sweeps(L, G.nu1[q]);
-    const int W = L.nr + 1;
+    const int W = L.ni;
     for (int t = tid; t < (L.nz - 1) * W; t += nth) {
       const int j = t / W + 1, i = t % W;
       linres_node<T>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP], L.f[NV], L.r[NE], L.r[NP], L.r[NV]);
     }
     __syncthreads();
-    const int Wc = C.nr + 1;
+    const int Wc = C.ni;
     for (int t = tid; t < (C.nz - 1) * Wc; t += nth) restrict_node<T>(L, C, t % Wc, t / Wc + 1);
     __syncthreads();
   }
@@ -1467,7 +1470,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
   __syncthreads();
   for (int q = G.n - 2; q >= 0; --q) {
     const LevelT<T> &F = lv[q];
-    const int W = F.nr + 1;
+    const int W = F.ni;
     for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(lv[q + 1], F, t % W, t / W + 1);
     __syncthreads();
     sweeps(F, G.nu2[q]);
@@ -1538,7 +1541,7 @@ __global__ void k_update(Level L, StateView sv, double *partials, unsigned *coun
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y + 1;
   double acc[2] = {0.0, 0.0};
-  if (i <= L.nr && j < L.nz) {
+  if (i < L.ni && j < L.nz) {
     const size_t k = (size_t)j * L.P + i;
     const double a = L.du[NE][k], b = L.du[NP][k], c = L.du[NV][k];
     sv.u[NE][k] += a; sv.u[NP][k] += b; sv.u[NV][k] += c;
@@ -1557,16 +1560,24 @@ cudaError_t launch_update(const Level &L, const StateView &sv, double *partials,
 }
 
 // Dirichlet electrode rows: n_e = n_p = 0, V = V_cathode (j = 0) and V_anode (j = nz).
+// Boundary values: electrode rows (n = 0, V = Vc at z = 0 and Va at z = d) and, with a
+// Dirichlet wall (Sec. 3), the wall column (n = 0, V linear in z between Vc and Va).
 __global__ void k_dirichlet(Level L, StateView sv, double Vc, double Va) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  if (i > L.nr) return;
-  const size_t k0 = i, k1 = (size_t)L.nz * L.P + i;
-  sv.u[NE][k0] = 0.0; sv.u[NP][k0] = 0.0; sv.u[NV][k0] = Vc;
-  sv.u[NE][k1] = 0.0; sv.u[NP][k1] = 0.0; sv.u[NV][k1] = Va;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= L.nr) {
+    const size_t k0 = t, k1 = (size_t)L.nz * L.P + t;
+    sv.u[NE][k0] = 0.0; sv.u[NP][k0] = 0.0; sv.u[NV][k0] = Vc;
+    sv.u[NE][k1] = 0.0; sv.u[NP][k1] = 0.0; sv.u[NV][k1] = Va;
+  }
+  if (L.ni == L.nr && t <= L.nz) {
+    const size_t kw = (size_t)t * L.P + L.nr;
+    sv.u[NE][kw] = 0.0; sv.u[NP][kw] = 0.0; sv.u[NV][kw] = Vc + (Va - Vc) * L.zf[t];
+  }
 }
 
 cudaError_t launch_dirichlet(const Level &L, const StateView &sv, double Vc, double Va, cudaStream_t st) {
-  k_dirichlet<<<(L.nr + 1 + 127) / 128, 128, 0, st>>>(L, sv, Vc, Va);
+  const int n = (L.nr > L.nz ? L.nr : L.nz) + 1;
+  k_dirichlet<<<(n + 127) / 128, 128, 0, st>>>(L, sv, Vc, Va);
   count_launch();
   return cudaGetLastError();
 }
@@ -1597,7 +1608,7 @@ template cudaError_t launch_zero_du<float>(const LevelT<float> &, cudaStream_t);
 __global__ void k_mixed_update(Level L, LevelT<float> M, double n0) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y + 1;
-  if (i > L.nr || j >= L.nz) return;
+  if (i >= L.ni || j >= L.nz) return;
   const size_t k = (size_t)j * L.P + i;
   L.du[NE][k] += n0 * (double)M.du[NE][k];
   L.du[NP][k] += n0 * (double)M.du[NP][k];
@@ -1616,7 +1627,7 @@ __global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
-  if (i <= L.nr && j < L.nz) {
+  if (i < L.ni && j < L.nz) {
     const size_t k = (size_t)j * L.P + i;
     const double *v0 = L.du[NE], *v1 = L.du[NP], *v2 = L.du[NV];
     double oe, op, oV;
@@ -1804,6 +1815,7 @@ extern "C" int mg_residual_noalloc(const mg_grid *g, const mg_params *p, const d
   if ((F_ne || F_np || F_V) && !(F_ne && F_np && F_V)) return MG_EINVAL;
   if (!(p->pressure_factor > 0.0) || !(p->D_e > 0.0) || !(p->D_p > 0.0)) return MG_EINVAL;
   if (p->table && (p->table_rows < 2 || p->table_rows > kNoallocTableRows)) return MG_EINVAL;
+  if (p->wall_dirichlet) return MG_EINVAL;  // wall rows are those of the zero-flux wall
   for (int j = 0; j < nz; ++j)
     if (!(g->z[j + 1] > g->z[j])) return MG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1830,6 +1842,7 @@ extern "C" int mg_residual_noalloc(const mg_grid *g, const mg_params *p, const d
 
   Level L = Level();
   L.nr = nr; L.nz = nz; L.P = nr + 1;  // caller arrays are dense rows of nr + 1 nodes
+  L.ni = nr + 1;
   L.dr = dr;
   L.dz = base + kOffDz; L.dzc = base + kOffDzc; L.volr = base + kOffVolr;
   StateView sv;

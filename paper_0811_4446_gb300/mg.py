@@ -46,7 +46,7 @@ class mg_params(ctypes.Structure):
                 ("coarse_kernel_threads", ctypes.c_int32), ("eta_adapt", ctypes.c_int32),
                 ("nu_coarse_n", ctypes.c_int32), ("nu_coarse1", ctypes.c_int32), ("nu_coarse2", ctypes.c_int32),
                 ("nu_tiny_n", ctypes.c_int32), ("nu_tiny1", ctypes.c_int32), ("nu_tiny2", ctypes.c_int32),
-                ("chain_from", ctypes.c_int32)]
+                ("chain_from", ctypes.c_int32), ("wall_dirichlet", ctypes.c_int32)]
 
 
 class mg_stats(ctypes.Structure):
@@ -377,8 +377,10 @@ def probe_fp64_gflops() -> float:
 
 def from_discharge(d, stream=None, **param_overrides) -> Solver:
     """Solver for a workloads.Discharge (sources and initial state loaded)."""
-    p = default_params(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p,
-                       D_p=d.D_p, pressure_factor=d.pressure_factor, **param_overrides)
+    kw = dict(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p,
+              pressure_factor=d.pressure_factor, wall_dirichlet=int(getattr(d, "wall_dirichlet", False)))
+    kw.update(param_overrides)
+    p = default_params(**kw)
     s = Solver(d.nr, d.nz, d.R, d.z, p, table=d.table, stream=stream)
     s.set_sources(np.ascontiguousarray(d.S_e), np.ascontiguousarray(d.S_p))
     s.set_state(np.ascontiguousarray(d.ne0), np.ascontiguousarray(d.np0), np.ascontiguousarray(d.V0))

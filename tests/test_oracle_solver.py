@@ -179,3 +179,30 @@ def test_chain_reaches_the_same_steady_state(dt_max):
     assert so.steady_rho(g, u, d.S_e, d.S_p, phys).max() <= 1e-9
     for q in range(3):
         assert np.abs(u[q] - base[q]).max() <= 1e-6 * np.abs(base[q]).max(), q
+
+
+def _cathode_ion_current(g, u, phys):
+    _, (mez, dez, mpz, dpz) = disc.face_transport(g, u[2], phys)
+    phi = disc.sg_flux(g.gz[0], mpz[0], dpz[0], 1.0, u[1][0], u[1][1], u[2][0], u[2][1])
+    return -2.0 * np.pi * 1.602176634e-19 * phi.sum()
+
+
+@pytest.mark.parametrize("a,b,key,rtol", [(30.0, 24.0, "a30_b24", 0.06), (10.0, 1.0, "a10_b1", 0.02)])
+def test_argon_ion_current_matches_the_paper(a, b, key, rtol):
+    """The paper's argon discharge (Sec. 3) on 33^2 nodes: the steady ion current into the
+    cathode is the printed one (0.59 mA and 0.035 mA, two significant digits).  At steady state
+    it equals e times the total ion production, nearly independent of the ion mobility the
+    paper does not print (here a stand-in), so the printed currents pin the Dirichlet-wall
+    discretisation, the sources and the continuation together."""
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as fh:
+        ref = json.load(fh)["argon_ion_current_mA"][key]
+    d = W.argon(32, a=a, b=b)
+    g = Grid(d.nr, d.nz, d.R, d.z, wall_dirichlet=True)
+    phys = disc.Physics(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p)
+    u, ok, _, _ = so.solve_steady(g, np.stack([d.ne0, d.np0, d.V0]), d.S_e, d.S_p, phys, 1e-8, so.SolverOptions())
+    assert ok
+    I_mA = _cathode_ion_current(g, u, phys) * 1e3
+    assert abs(I_mA - ref) <= rtol * ref, (I_mA, ref)
+    # and it is the ion production, whatever the ion mobility (within the losses to the walls)
+    prod = 2.0 * np.pi * 1.602176634e-19 * (g.A[1:-1, :g.ni] * d.S_p[1:-1, :g.ni]).sum() * 1e3
+    assert abs(I_mA - prod) <= 0.01 * prod
