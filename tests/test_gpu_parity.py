@@ -242,6 +242,27 @@ def test_invalid_arguments_are_rejected(mg):
     s = mg.Solver(32, 32, 1e-2, z)
     rc = s.lib.mg_step(s.h, -1.0, 1e-8, None)
     assert rc == mg.MG_EINVAL
+    # parameters of the later forms
+    for bad_params in (dict(wall_dirichlet=2), dict(nu_coarse_n=-1), dict(nu_tiny_n=8, nu_tiny1=0, nu_tiny2=0),
+                       dict(coarse_kernel_threads=2048), dict(nu1=0, nu2=0)):
+        with pytest.raises(mg.MGError):
+            mg.Solver(32, 32, 1e-2, z, mg.default_params(**bad_params))
+    for chain_from in (0, 99):                                 # chain_from outside 1 .. levels - 1
+        sc = mg.Solver(32, 32, 1e-2, z, mg.default_params(chain_from=chain_from))
+        assert sc.lib.mg_solve_steady(sc.h, 1e-8, None) == mg.MG_EINVAL
+    nl = s.lib.mg_num_levels(s.h)
+    for args in ((nl, 0, 32, 2, 0, 0), (0, 2, 32, 2, 0, 0), (0, 0, 48, 2, 0, 0), (0, 0, 128, 4, 0, 0),
+                 (0, 0, 32, 2, 2, 0), (0, 0, 32, 2, 1, 6)):
+        assert s.lib.mg_set_smoother(s.h, *args) == mg.MG_EINVAL, args
+    for args in ((nl, 2, 2), (0, 0, 0), (0, 2, -1), (0, -2, -2)):
+        assert s.lib.mg_set_level_sweeps(s.h, *args) == mg.MG_EINVAL, args
+    assert s.lib.mg_set_level_sweeps(s.h, 1, 3, 1) == mg.MG_OK
+    assert s.lib.mg_set_level_sweeps(s.h, 1, -1, -1) == mg.MG_OK
+    # the allocation-free residual covers the zero-flux wall only
+    p = mg.default_params(wall_dirichlet=1)
+    zz = torch.zeros((33, 33), dtype=torch.float64, device="cuda")
+    with pytest.raises(mg.MGError):
+        mg.residual_noalloc(32, 32, 1e-2, z, p, [zz, zz, zz], None, [zz, zz], 0.0)
 
 
 def test_rejected_step_leaves_state_unchanged(mg):
