@@ -405,7 +405,7 @@ int vcycle(mg_state *s, int l, cudaStream_t st) {
   if (l == s->cc_from && l < s->nlev - 1) {
     ProfScope ps(s, MG_PROF_COARSE, l);
     CK(launch_coarse_cycle<T>(coarse_set<T>(s), s->prm.coarse_kernel_ctas, s->prm.coarse_kernel_threads,
-                              coarse_smem<T>(s), st));
+                              coarse_smem<T>(s), (s->prm.pdl & PDL_COARSE) != 0, st));
     return MG_OK;
   }
   if (l == s->nlev - 1) {
@@ -836,6 +836,7 @@ void mg_params_default(mg_params *p) {
   p->nu_coarse_n = 64; p->nu_coarse1 = 2; p->nu_coarse2 = 2;
   p->nu_tiny_n = 8; p->nu_tiny1 = 1; p->nu_tiny2 = 1;
   p->chain_from = 1;
+  p->pdl = PDL_SMOOTH | PDL_COARSE;
   p->wall_dirichlet = 0;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
@@ -856,6 +857,7 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
     return MG_EINVAL;
   }
   if (p->wall_dirichlet != 0 && p->wall_dirichlet != 1) { *why = "wall_dirichlet must be 0 or 1"; return MG_EINVAL; }
+  if (p->pdl < 0 || p->pdl > PDL_ALL) { *why = "pdl: a combination of the PDL kernel-kind bits"; return MG_EINVAL; }
   if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
     *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";
     return MG_EINVAL;
@@ -953,6 +955,7 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     b.L.idr = 1.0 / b.L.dr;
     b.M.idr = (float)b.L.idr;
     b.L.ni = b.M.ni = p->wall_dirichlet ? b.nr : b.nr + 1;
+    b.L.pdl = b.M.pdl = p->pdl;
     if (cudaMemcpyAsync(b.geo, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream) !=
         cudaSuccess)
       rc = fail(s, MG_ECUDA, "geometry copy");

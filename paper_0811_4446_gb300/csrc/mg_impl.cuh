@@ -18,6 +18,8 @@ constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kKappa = kECharge / kEps0;
 
 enum { NE = 0, NP = 1, NV = 2 };
+// kernel kinds that may use programmatic dependent launch (mg_params.pdl bits)
+enum { PDL_SMOOTH = 1, PDL_TRANSFER = 2, PDL_NORM = 4, PDL_COARSE = 8, PDL_OTHER = 16, PDL_ALL = 31 };
 // face-coefficient slots: per species s (0 = electrons, 1 = ions): G-term, F-term, V-derivative
 enum { CGE = 0, CFE = 1, CVE = 2, CGP = 3, CFP = 4, CVP = 5, NCOEF = 6 };
 // per-node factors of the 3x3 diagonal block [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]]
@@ -40,6 +42,8 @@ template <typename T>
 struct LevelT {
   int nr, nz, P;
   int ni;                    // unknown columns: nr + 1, or nr with a Dirichlet wall
+  int pdl;                   // host side: PDL_* bits of the kernel kinds launched with programmatic
+                             // dependent launch (they start while the previous kernel finishes)
   T dr;
   const T *dz, *dzc, *volr;  // nz, nz+1, nr+1 (geometry in the level's arithmetic type)
   const T *idz;              // 1 / dz (nz entries)
@@ -139,7 +143,7 @@ cudaError_t launch_sweep(const LevelT<T> &L, const SweepIO<T> &io, int shape, cu
 // smem_bytes > 0 with cluster == 1: the single-CTA form with every coarse array in shared
 // memory (prepare_coarse_smem gives the size, 0 if the set does not fit in `limit` bytes).
 template <typename T>
-cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, size_t smem_bytes,
+cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, size_t smem_bytes, bool pdl,
                                 cudaStream_t st);
 template <typename T>
 size_t prepare_coarse_smem(const CoarseSet<T> &host_set, size_t limit);

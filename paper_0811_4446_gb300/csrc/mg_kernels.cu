@@ -32,6 +32,35 @@ unsigned long long total_launches() { return __atomic_load_n(&g_launches, __ATOM
 
 constexpr int BX = 32, BY = 8, NT = BX * BY;
 
+// ---- programmatic dependent launch ----------------------------------------------------------
+// A kernel launched with programmatic stream serialization may start while the kernel before it
+// in the stream is still running, once every CTA of that kernel has executed
+// griddepcontrol.launch_dependents; griddepcontrol.wait then blocks until the previous kernel
+// has completed and its memory is visible.  The V-cycle kernels signal their dependents at once
+// and read only data that no kernel of the linear solve writes (face coefficients, factors,
+// conductances) before they wait.  Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t st, Args... args) {
+  if (!pdl) {
+    kern<<<g, b, smem, st>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ------------------------------------------------------------------------------------------
 // Bernoulli function B(x) = x / (e^x - 1): F(x) = B(x), G(x) = B(-x) (definitions after eq. 11).
 // Returns B(x), B(-x), B'(x), B'(-x).  |x| < 0.1: Bernoulli-number series
@@ -643,24 +672,27 @@ __device__ __forceinline__ void offdiag(const LevelT<T> &L, int i, size_t k, con
 // Every operand is loaded before the arithmetic starts (the compiler barrier keeps the loads
 // together), so one node costs one round of memory latency; the arithmetic is offdiag's and
 // node_update's, term for term.
-template <typename T>
+// PDL: the operator data (constant during a linear solve) is requested before waiting for the
+// previous kernel, the corrections and right-hand sides after.
+template <typename T, bool PDL = false>
 __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   (void)i;
   const int P = L.P;
   const size_t k = (size_t)j * P + i;
   const size_t kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
+  const T aE0 = L.cr[CVE][k], aE1 = L.cr[CFE][k], aE2 = L.cr[CVP][k], aE3 = L.cr[CFP][k], gE = L.gR[k];
+  const T aW0 = L.cr[CVE][kW], aW1 = L.cr[CGE][kW], aW2 = L.cr[CVP][kW], aW3 = L.cr[CGP][kW], gW = L.gR[kW];
+  const T aN0 = L.cz[CVE][k], aN1 = L.cz[CFE][k], aN2 = L.cz[CVP][k], aN3 = L.cz[CFP][k], gN = L.gZ[k];
+  const T aS0 = L.cz[CVE][kS], aS1 = L.cz[CGE][kS], aS2 = L.cz[CVP][kS], aS3 = L.cz[CGP][kS], gS = L.gZ[kS];
+  const T q1 = L.fac[FQ1][k], q2 = L.fac[FQ2][k], is = L.fac[FIS][k];
+  const T a13 = L.fac[FA13][k], a23 = L.fac[FA23][k], i11 = L.fac[FI11][k], i22 = L.fac[FI22][k];
+  if (PDL) pdl_wait();
   const T *ve = L.du[NE], *vp = L.du[NP], *vV = L.du[NV];
   const T eE = ve[kE], pE = vp[kE], wE = vV[kE];
   const T eW = ve[kW], pW = vp[kW], wW = vV[kW];
   const T eN = ve[kN], pN = vp[kN], wN = vV[kN];
   const T eS = ve[kS], pS = vp[kS], wS = vV[kS];
-  const T aE0 = L.cr[CVE][k], aE1 = L.cr[CFE][k], aE2 = L.cr[CVP][k], aE3 = L.cr[CFP][k], gE = L.gR[k];
-  const T aW0 = L.cr[CVE][kW], aW1 = L.cr[CGE][kW], aW2 = L.cr[CVP][kW], aW3 = L.cr[CGP][kW], gW = L.gR[kW];
-  const T aN0 = L.cz[CVE][k], aN1 = L.cz[CFE][k], aN2 = L.cz[CVP][k], aN3 = L.cz[CFP][k], gN = L.gZ[k];
-  const T aS0 = L.cz[CVE][kS], aS1 = L.cz[CGE][kS], aS2 = L.cz[CVP][kS], aS3 = L.cz[CGP][kS], gS = L.gZ[kS];
   const T f0 = L.f[NE][k], f1 = L.f[NP][k], f2 = L.f[NV][k];
-  const T q1 = L.fac[FQ1][k], q2 = L.fac[FQ2][k], is = L.fac[FIS][k];
-  const T a13 = L.fac[FA13][k], a23 = L.fac[FA23][k], i11 = L.fac[FI11][k], i22 = L.fac[FI22][k];
   asm volatile("" ::: "memory");
   T e = 0, p = 0, V = 0;
   e += aE0 * wE - aE1 * eE; p += aE2 * wE - aE3 * pE; V += gE * wE;
@@ -676,10 +708,11 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
 
 template <typename T>
 __global__ void k_smooth(LevelT<T> L, int color) {
+  pdl_launch_dependents();
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
   if (j >= L.nz || i >= L.ni) return;
-  smooth_node<T>(L, i, j);
+  smooth_node<T, true>(L, i, j);
 }
 
 // The same half sweep for small levels (FP64, N <= 128): at most 256 threads per block (the
@@ -689,10 +722,11 @@ __global__ void k_smooth(LevelT<T> L, int color) {
 // many warps share each SM, the default allocation is faster.
 template <typename T>
 __global__ void __launch_bounds__(256, 1) k_smooth_ilp(LevelT<T> L, int color) {
+  pdl_launch_dependents();
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
   if (j >= L.nz || i >= L.ni) return;
-  smooth_node<T>(L, i, j);
+  smooth_node<T, true>(L, i, j);
 }
 
 constexpr int SBX = 32, SBY = 2;  // stencil kernels: small blocks so that coarse levels spread over the SMs
@@ -701,10 +735,11 @@ constexpr int SBX = 32, SBY = 2;  // stencil kernels: small blocks so that coars
 template <typename T>
 cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx, int by) {
   dim3 b(bx, by), g(((L.nr + 2) / 2 + bx - 1) / bx, (L.nz - 1 + by - 1) / by);
-  if (sizeof(T) == 8 && L.nr <= 128 && bx * by <= 256) k_smooth_ilp<T><<<g, b, 0, st>>>(L, color);
-  else k_smooth<T><<<g, b, 0, st>>>(L, color);
+  cudaError_t e;
+  if (sizeof(T) == 8 && L.nr <= 128 && bx * by <= 256) e = launch_k((L.pdl & PDL_SMOOTH) != 0, k_smooth_ilp<T>, g, b, 0, st, L, color);
+  else e = launch_k((L.pdl & PDL_SMOOTH) != 0, k_smooth<T>, g, b, 0, st, L, color);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t, int, int);
 template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t, int, int);
@@ -762,6 +797,8 @@ __device__ __forceinline__ Triple<T> gload(T *const v[3], size_t k) {
 
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
+  pdl_launch_dependents();
+  pdl_wait();
   constexpr int EX = TX + 2, EY = TY + 2;
   __shared__ T sr[3][EY][EX];
   const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY;  // extended-tile origin (node coords)
@@ -805,9 +842,9 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
 template <typename T, int TX, int TY>
 cudaError_t launch_sweep_t(const LevelT<T> &L, const SweepIO<T> &io, cudaStream_t st) {
   dim3 g((L.nr + 1 + TX - 1) / TX, (L.nz + TY - 1) / TY);  // rows 1..nz-1 live in [0, nz)
-  k_sweep<T, TX, TY><<<g, TX * TY, 0, st>>>(L, io);
+  const cudaError_t e = launch_k((L.pdl & PDL_SMOOTH) != 0, k_sweep<T, TX, TY>, g, dim3(TX * TY), 0, st, L, io);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 template <typename T>
@@ -853,6 +890,8 @@ __device__ __forceinline__ Triple<T> linres_node(const LevelT<T> &L, int i, int 
 template <typename T>
 __global__ void k_linres(LevelT<T> L, const T *v0, const T *v1, const T *v2, const T *f0, const T *f1, const T *f2,
                          T *o0, T *o1, T *o2, double *partials, unsigned *counter, double *out3) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
@@ -868,10 +907,11 @@ cudaError_t launch_linres(const LevelT<T> &L, T *const v[3], T *const f[3], T *o
                           unsigned *counter, double *out3, cudaStream_t st) {
   const int bx = 32, by = SBY;
   dim3 b(bx, by), g((L.nr + 1 + bx - 1) / bx, (L.nz - 1 + by - 1) / by);
-  k_linres<T><<<g, b, 0, st>>>(L, v[0], v[1], v[2], f ? f[0] : nullptr, f ? f[1] : nullptr, f ? f[2] : nullptr,
-                               out[0], out[1], out[2], partials, counter, out3);
+  const cudaError_t e = launch_k((L.pdl & PDL_NORM) != 0, k_linres<T>, g, b, 0, st, L, (const T *)v[0], (const T *)v[1],
+                                 (const T *)v[2], (const T *)(f ? f[0] : nullptr), (const T *)(f ? f[1] : nullptr),
+                                 (const T *)(f ? f[2] : nullptr), out[0], out[1], out[2], partials, counter, out3);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 template cudaError_t launch_linres<double>(const LevelT<double> &, double *const[3], double *const[3], double *[3],
                                            double *, unsigned *, double *, cudaStream_t);
@@ -910,6 +950,8 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) 
                                                                                                  LevelT<T> C) {
   constexpr int FW = 2 * CX + 1, FH = 2 * CY + 1;
   __shared__ T sr[3][FH * FW];
+  pdl_launch_dependents();
+  pdl_wait();
   const int I0 = blockIdx.x * CX, J0 = 1 + blockIdx.y * CY;
   const int tid = threadIdx.x;
   for (int t = tid; t < FW * FH; t += blockDim.x) {
@@ -947,9 +989,9 @@ template <typename T>
 cudaError_t launch_linres_restrict(const LevelT<T> &F, const LevelT<T> &C, cudaStream_t st) {
   constexpr int CX = 16, CY = 4;  // 33 x 9 fine nodes, one per thread
   dim3 b(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32), g((C.nr + 1 + CX - 1) / CX, (C.nz - 1 + CY - 1) / CY);
-  k_linres_restrict<T, CX, CY><<<g, b, 0, st>>>(F, C);
+  const cudaError_t e = launch_k((F.pdl & PDL_TRANSFER) != 0, k_linres_restrict<T, CX, CY>, g, b, 0, st, F, C);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 template cudaError_t launch_linres_restrict<double>(const LevelT<double> &, const LevelT<double> &, cudaStream_t);
 template cudaError_t launch_linres_restrict<float>(const LevelT<float> &, const LevelT<float> &, cudaStream_t);
@@ -977,6 +1019,8 @@ __device__ __forceinline__ void prolong_node(const LevelT<T> &C, const LevelT<T>
 
 template <typename T>
 __global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   if (i >= F.ni || j >= F.nz) return;
@@ -986,9 +1030,9 @@ __global__ void k_prolong_add(LevelT<T> C, LevelT<T> F) {
 template <typename T>
 cudaError_t launch_prolong_add(const LevelT<T> &C, const LevelT<T> &F, cudaStream_t st) {
   dim3 b(SBX, SBY), g((F.nr + 1 + SBX - 1) / SBX, (F.nz - 1 + SBY - 1) / SBY);
-  k_prolong_add<T><<<g, b, 0, st>>>(C, F);
+  const cudaError_t e = launch_k((F.pdl & PDL_TRANSFER) != 0, k_prolong_add<T>, g, b, 0, st, C, F);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 template cudaError_t launch_prolong_add<double>(const LevelT<double> &, const LevelT<double> &, cudaStream_t);
 template cudaError_t launch_prolong_add<float>(const LevelT<float> &, const LevelT<float> &, cudaStream_t);
@@ -1398,6 +1442,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
   __shared__ LevelT<T> lv[kMaxCoarseSet];
   const CoarseSet<T> &G = *sp;
   const int tid = threadIdx.x, nth = blockDim.x;
+  pdl_launch_dependents();
   if (tid == 0) {
     T *p = reinterpret_cast<T *>(cc_smem);
     for (int q = 0; q < G.n; ++q) {
@@ -1415,28 +1460,37 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
   }
   __syncthreads();
   // copy-in with asynchronous 16-byte copies (every array is a multiple of 16 bytes long and
-  // 16-byte aligned at both ends), all issued before one wait
+  // 16-byte aligned at both ends), all issued before one wait: the operator arrays (constant
+  // during a linear solve) before waiting for the previous kernel, corrections and right-hand
+  // side after
+  auto copy = [&](const T *dst, const T *src, int chunks) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const char *sp = reinterpret_cast<const char *>(src);
+    for (int c = tid; c < chunks; c += nth)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * c), "l"(sp + 16 * (size_t)c)
+                   : "memory");
+  };
+  auto chunks_of = [&](const LevelT<T> &g) { return (int)((size_t)(g.nz + 1) * g.P * sizeof(T) / 16); };
   for (int q = 0; q < G.n; ++q) {
     const LevelT<T> &g = G.lv[q];
     const LevelT<T> &v = lv[q];
-    const int chunks = (int)((size_t)(g.nz + 1) * g.P * sizeof(T) / 16);
-    auto copy = [&](const T *dst, const T *src) {
-      const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-      const char *sp = reinterpret_cast<const char *>(src);
-      for (int c = tid; c < chunks; c += nth)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * c), "l"(sp + 16 * (size_t)c)
-                     : "memory");
-    };
-    for (int a = 0; a < NCOEF; ++a) { copy(v.cr[a], g.cr[a]); copy(v.cz[a], g.cz[a]); }
-    for (int a = 0; a < NFAC; ++a) copy(v.fac[a], g.fac[a]);
-    for (int a = 0; a < NDIA; ++a) copy(v.dia[a], g.dia[a]);
-    copy(v.gR, g.gR); copy(v.gZ, g.gZ); copy(v.Ak, g.Ak);
+    const int ch = chunks_of(g);
+    for (int a = 0; a < NCOEF; ++a) { copy(v.cr[a], g.cr[a], ch); copy(v.cz[a], g.cz[a], ch); }
+    for (int a = 0; a < NFAC; ++a) copy(v.fac[a], g.fac[a], ch);
+    for (int a = 0; a < NDIA; ++a) copy(v.dia[a], g.dia[a], ch);
+    copy(v.gR, g.gR, ch); copy(v.gZ, g.gZ, ch); copy(v.Ak, g.Ak, ch);
+  }
+  pdl_wait();
+  for (int q = 0; q < G.n; ++q) {
+    const LevelT<T> &g = G.lv[q];
+    const LevelT<T> &v = lv[q];
+    const int ch = chunks_of(g);
     // the first level's correction is the current iterate when the set's first level is the
     // root of the solve; the coarser ones are overwritten by the restriction except for their
     // (zero) electrode rows
     for (int a = 0; a < 3; ++a) {
-      if (q == 0) copy(v.f[a], g.f[a]);
-      copy(v.du[a], g.du[a]);
+      if (q == 0) copy(v.f[a], g.f[a], ch);
+      copy(v.du[a], g.du[a], ch);
     }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -1484,12 +1538,12 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
 }
 
 template <typename T>
-cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, size_t smem_bytes,
+cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int threads, size_t smem_bytes, bool pdl,
                                 cudaStream_t st) {
   if (cluster == 1 && smem_bytes > 0) {
-    k_coarse_cycle_smem<T><<<1, threads, smem_bytes, st>>>(dev_set);
+    const cudaError_t e = launch_k(pdl, k_coarse_cycle_smem<T>, dim3(1), dim3(threads), smem_bytes, st, dev_set);
     count_launch();
-    return cudaGetLastError();
+    return e;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, 1, 1);
@@ -1507,8 +1561,8 @@ cudaError_t launch_coarse_cycle(const CoarseSet<T> *dev_set, int cluster, int th
   count_launch();
   return e;
 }
-template cudaError_t launch_coarse_cycle<double>(const CoarseSet<double> *, int, int, size_t, cudaStream_t);
-template cudaError_t launch_coarse_cycle<float>(const CoarseSet<float> *, int, int, size_t, cudaStream_t);
+template cudaError_t launch_coarse_cycle<double>(const CoarseSet<double> *, int, int, size_t, bool, cudaStream_t);
+template cudaError_t launch_coarse_cycle<float>(const CoarseSet<float> *, int, int, size_t, bool, cudaStream_t);
 
 // Shared memory of the single-CTA coarse cycle for a set (0 when it does not fit); sets the
 // kernel's dynamic shared-memory limit.
@@ -1584,6 +1638,8 @@ cudaError_t launch_dirichlet(const Level &L, const StateView &sv, double Vc, dou
 
 template <typename T>
 __global__ void k_zero_du(LevelT<T> L) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i > L.nr || j > L.nz) return;
@@ -1594,9 +1650,9 @@ __global__ void k_zero_du(LevelT<T> L) {
 template <typename T>
 cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st) {
   dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
-  k_zero_du<T><<<g, b, 0, st>>>(L);
+  const cudaError_t e = launch_k((L.pdl & PDL_OTHER) != 0, k_zero_du<T>, g, b, 0, st, L);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 template cudaError_t launch_zero_du<double>(const LevelT<double> &, cudaStream_t);
 template cudaError_t launch_zero_du<float>(const LevelT<float> &, cudaStream_t);
@@ -1606,6 +1662,8 @@ template cudaError_t launch_zero_du<float>(const LevelT<float> &, cudaStream_t);
 // r = f - J x in FP64, written as the next FP32 right-hand side (densities / n0), with FP64
 // per-field sums of squares.  Two passes: the update must be complete before J x is applied.
 __global__ void k_mixed_update(Level L, LevelT<float> M, double n0) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y + 1;
   if (i >= L.ni || j >= L.nz) return;
@@ -1617,13 +1675,15 @@ __global__ void k_mixed_update(Level L, LevelT<float> M, double n0) {
 
 cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st) {
   dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
-  k_mixed_update<<<g, b, 0, st>>>(L, M, n0);
+  const cudaError_t e = launch_k((L.pdl & PDL_OTHER) != 0, k_mixed_update, g, b, 0, st, L, M, n0);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 __global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double *partials, unsigned *counter,
                                  double *out3) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
@@ -1647,9 +1707,9 @@ __global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double
 cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double n0, double *partials,
                                   unsigned *counter, double *out3, cudaStream_t st) {
   dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
-  k_outer_residual<<<g, b, 0, st>>>(L, M, 1.0 / n0, partials, counter, out3);
+  const cudaError_t e = launch_k((L.pdl & PDL_NORM) != 0, k_outer_residual, g, b, 0, st, L, M, 1.0 / n0, partials, counter, out3);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 // ------------------------------------------------------------------------------------------
