@@ -37,6 +37,57 @@ TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20
 
 
+# DRAM bytes read + written by one k_smooth<double> half sweep at 1025^2 in an ncu capture
+TRAFFIC_K_SMOOTH_FP64_1025 = None
+
+
+def _vcycle_1025(precision, peaks):
+    """V-cycle time at 1025^2 and the roofline of its finest-level smoother launch."""
+    import workloads as W
+    from paper_0811_4446_gb300 import mg
+    d = W.transient_1025()
+    nodes = (d.nr + 1) * (d.nz - 1)
+    fp64 = precision == mg.MG_FP64
+    s = mg.from_discharge(d, precision=precision)
+    tuned = s.autotune()
+    fused = bool(tuned[0, 2] if fp64 else tuned[0, 5])
+    F, _ = s.residual(1e-9)
+    f = [-a for a in F]
+    s.linear_solve(1e-9, f, 0.0, 0)
+    t0 = time.perf_counter()
+    s.linear_solve(1e-9, f, 0.0, 0)
+    t1 = time.perf_counter()
+    x, hist, _ = s.linear_solve(1e-9, f, 0.0, 30)
+    t2 = time.perf_counter()
+    vc = ((t2 - t1) - (t1 - t0)) / 30
+    s.profile_begin(mg.MG_PROF_SMOOTH, 0)
+    s.linear_solve(1e-9, f, 0.0, 10)
+    n, ms = s.profile_end()
+    s.close()
+    avg = ms / n / 1000.0
+    # algorithmic bytes of one launch (FP64 figures; FP32 halves them): a half sweep reads all
+    # face coefficients and conductances once, the colour's factors, f and du and the other
+    # colour's du, and writes the colour's du (176 B per unknown node); a fused sweep 228 B
+    byt = (228 if fused else 176) * nodes // (1 if fp64 else 2)
+    flo = 52 * nodes if fused else 26 * nodes
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    name = ("k_sweep" if fused else "k_smooth") + ("<double>" if fp64 else "<float>")
+    # ncu DRAM read + write per launch, cold caches (profiles/k_smooth_fp32_1025_mixed.md,
+    # profiles/k_smooth_fp64_1025.md)
+    traffic = None if fused else (117228672 if not fp64 else TRAFFIC_K_SMOOTH_FP64_1025)
+    roof = {"bound": "hbm", "kernel": name + (" (fused red-black sweep" if fused else " (red-black half sweep")
+            + ", 1025x1025 level)", "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6, "algorithmic_bytes_per_launch": byt,
+            "traffic": traffic, "peak_source": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    if fp64:
+        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e9
+        roof["fp64"] = {"achieved": flo / avg / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+                        "frac": flo / avg / 1e9 / fp64_peak, "algorithmic_flops_per_launch": flo,
+                        "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    return {"vcycle_us": vc * 1e6, "mpts_per_s": (d.nr + 1) * (d.nz + 1) / vc / 1e6,
+            "residual_drop_30_cycles": float(hist[-1]), "roofline": roof}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -469,36 +520,10 @@ def measure_forms(args, dev, peaks):
     argon["workload"] = ("257x257 nodes, d = 1.1 cm, R = 2.7 cm, 0 V / 255.9 V, Dirichlet walls, "
                          "mu_e = 30/p at 0.514 torr, stand-in mu_p = 0.22 m^2/Vs, FP64, rho <= 1e-8")
     out["argon_257"] = argon
-    # FP32 inner V-cycle of the mixed form at 1025^2 (transient physics, dt = 1 ns)
-    d = W.transient_1025()
-    nodes = (d.nr + 1) * (d.nz - 1)
-    s = mg.from_discharge(d, precision=mg.MG_MIXED)
-    fused32 = bool(s.autotune()[0, 5])
-    F, _ = s.residual(1e-9)
-    f = [-a for a in F]
-    s.linear_solve(1e-9, f, 0.0, 0)
-    t0 = time.perf_counter()
-    s.linear_solve(1e-9, f, 0.0, 0)
-    t1 = time.perf_counter()
-    x, hist, _ = s.linear_solve(1e-9, f, 0.0, 30)
-    t2 = time.perf_counter()
-    vc = ((t2 - t1) - (t1 - t0)) / 30
-    s.profile_begin(mg.MG_PROF_SMOOTH, 0)
-    s.linear_solve(1e-9, f, 0.0, 10)
-    n, ms = s.profile_end()
-    avg = ms / n / 1000.0
-    byt = (114 if fused32 else 88) * nodes   # FP32: the FP64 per-launch bytes halved
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    out["mixed_vcycle_1025"] = {"vcycle_us": vc * 1e6, "mpts_per_s": (d.nr + 1) * (d.nz + 1) / vc / 1e6,
-                                "residual_drop_30_cycles": float(hist[-1]),
-                                "roofline": {"bound": "hbm", "kernel": ("k_sweep<float> (fused red-black sweep" if fused32 else "k_smooth<float> (red-black half sweep") + ", 1025x1025 level)",
-                                             "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
-                                             "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6,
-                                             "algorithmic_bytes_per_launch": byt,
-                                             # ncu DRAM read + write per launch, cold caches
-                                             # (profiles/k_smooth_fp32_1025_mixed.md)
-                                             "traffic": None if fused32 else 117228672}}
-    s.close()
+    # V-cycles at 1025^2 (transient physics, dt = 1 ns): the FP32 inner cycle of the mixed form
+    # and the plain FP64 cycle, each with the roofline of its finest-level smoother
+    out["mixed_vcycle_1025"] = _vcycle_1025(mg.MG_MIXED, peaks)
+    out["fp64_vcycle_1025"] = _vcycle_1025(mg.MG_FP64, peaks)
     # batched form: 64 independent discharges of seeded sizes 65^2..513^2, mixed precision
     ds = W.batch_64()
     solvers = [mg.from_discharge(dd, precision=mg.MG_MIXED, stream=torch.cuda.Stream(device=dev)) for dd in ds]

@@ -627,51 +627,40 @@ struct Triple {
   T e, p, V;
 };
 
-// Sum over the four neighbours of (off-diagonal block of eq. 14) x v at node k = (j, i).  The
-// off-diagonal blocks have 5 nonzeros: towards a neighbour across a face where this node is the
-// lower end: [-cF, cV] for each species, g for V; where it is the upper end: [-cG, cV], g.
-// Electrode-row neighbours carry v = 0.  No branches: the face arrays hold zeros on the r-faces
-// at i = nr and in the pitch padding (never written), so the east term of an i = nr node and
-// the west term of an i = 0 node add exact zeros, and every load can be issued at once.
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// One face's share of r = f - (off-diagonal block of eq. 14) x v at a node.  The off-diagonal
+// blocks have 5 nonzeros: towards a neighbour across a face where this node is the lower end:
+// [-cF, cV] for each species, g for V; where it is the upper end: [-cG, cV], g (cx below is
+// cF or cG).  Each product goes into its row with one fused multiply-add: five per face, the
+// FP64 pipe being the scarce unit on this GPU.  Electrode-row neighbours carry v = 0.  No
+// branches at i = 0, nr: the face arrays hold zeros on the r-faces at i = nr and in the pitch
+// padding (never written), so those terms add exact zeros and every load can be issued at once.
 template <typename T>
-__device__ __forceinline__ void offdiag(const LevelT<T> &L, int i, size_t k, const T *ve, const T *vp,
-                                        const T *vV, T &oe, T &op, T &oV) {
-  (void)i;
-  const int P = L.P;
-  const size_t kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
-  T e = 0, p = 0, V = 0;
-  {
-    const T w = vV[kE];
-    e += L.cr[CVE][k] * w - L.cr[CFE][k] * ve[kE];
-    p += L.cr[CVP][k] * w - L.cr[CFP][k] * vp[kE];
-    V += L.gR[k] * w;
-  }
-  {
-    const T w = vV[kW];
-    e += L.cr[CVE][kW] * w - L.cr[CGE][kW] * ve[kW];
-    p += L.cr[CVP][kW] * w - L.cr[CGP][kW] * vp[kW];
-    V += L.gR[kW] * w;
-  }
-  {
-    const T w = vV[kN];
-    e += L.cz[CVE][k] * w - L.cz[CFE][k] * ve[kN];
-    p += L.cz[CVP][k] * w - L.cz[CFP][k] * vp[kN];
-    V += L.gZ[k] * w;
-  }
-  {
-    const T w = vV[kS];
-    e += L.cz[CVE][kS] * w - L.cz[CGE][kS] * ve[kS];
-    p += L.cz[CVP][kS] * w - L.cz[CGP][kS] * vp[kS];
-    V += L.gZ[kS] * w;
-  }
-  oe = e; op = p; oV = V;
+__device__ __forceinline__ void acc_face(T &re, T &rp, T &rV, T cve, T cxe, T cvp, T cxp, T g, T e, T p, T w) {
+  re = fmadd(-cve, w, re); re = fmadd(cxe, e, re);
+  rp = fmadd(-cvp, w, rp); rp = fmadd(cxp, p, rp);
+  rV = fmadd(-g, w, rV);
+}
+
+// Solve of the diagonal block through its Schur complement in V (stored factors, see
+// factor_node): seven operations.
+template <typename T>
+__device__ __forceinline__ Triple<T> block_solve(T re, T rp, T rV, T q1, T q2, T is, T a13, T a23, T i11,
+                                                 T i22) {
+  Triple<T> x;
+  x.V = fmadd(-q2, rp, fmadd(-q1, re, rV)) * is;
+  x.e = fmadd(-a13, x.V, re) * i11;
+  x.p = fmadd(-a23, x.V, rp) * i22;
+  return x;
 }
 
 // K3: red-black collective Gauss-Seidel half sweep: every node of one colour (red = (i + j)
 // even) solves its 3x3 diagonal block (stored factors) against the current neighbours.
 // Every operand is loaded before the arithmetic starts (the compiler barrier keeps the loads
-// together), so one node costs one round of memory latency; the arithmetic is offdiag's and
-// node_update's, term for term.
+// together), so one node costs one round of memory latency; the arithmetic is node_update's,
+// term for term: 20 fused multiply-adds for the four faces, 7 for the block solve.
 // PDL: the operator data (constant during a linear solve) is requested before waiting for the
 // previous kernel, the corrections and right-hand sides after.
 template <typename T, bool PDL = false>
@@ -694,16 +683,15 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   const T eS = ve[kS], pS = vp[kS], wS = vV[kS];
   const T f0 = L.f[NE][k], f1 = L.f[NP][k], f2 = L.f[NV][k];
   asm volatile("" ::: "memory");
-  T e = 0, p = 0, V = 0;
-  e += aE0 * wE - aE1 * eE; p += aE2 * wE - aE3 * pE; V += gE * wE;
-  e += aW0 * wW - aW1 * eW; p += aW2 * wW - aW3 * pW; V += gW * wW;
-  e += aN0 * wN - aN1 * eN; p += aN2 * wN - aN3 * pN; V += gN * wN;
-  e += aS0 * wS - aS1 * eS; p += aS2 * wS - aS3 * pS; V += gS * wS;
-  const T re = f0 - e, rp = f1 - p, rV = f2 - V;
-  const T xV = (rV - q1 * re - q2 * rp) * is;
-  L.du[NE][k] = (re - a13 * xV) * i11;
-  L.du[NP][k] = (rp - a23 * xV) * i22;
-  L.du[NV][k] = xV;
+  T re = f0, rp = f1, rV = f2;
+  acc_face(re, rp, rV, aE0, aE1, aE2, aE3, gE, eE, pE, wE);
+  acc_face(re, rp, rV, aW0, aW1, aW2, aW3, gW, eW, pW, wW);
+  acc_face(re, rp, rV, aN0, aN1, aN2, aN3, gN, eN, pN, wN);
+  acc_face(re, rp, rV, aS0, aS1, aS2, aS3, gS, eS, pS, wS);
+  const Triple<T> x = block_solve(re, rp, rV, q1, q2, is, a13, a23, i11, i22);
+  L.du[NE][k] = x.e;
+  L.du[NP][k] = x.p;
+  L.du[NV][k] = x.V;
 }
 
 template <typename T>
@@ -757,35 +745,14 @@ __device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, size
                                                  const Triple<T> &vW, const Triple<T> &vN, const Triple<T> &vS) {
   (void)i;
   const int P = L.P;
-  T e = 0, p = 0, V = 0;
-  {  // no branches at i = 0, nr: see offdiag
-    e += L.cr[CVE][k] * vE.V - L.cr[CFE][k] * vE.e;
-    p += L.cr[CVP][k] * vE.V - L.cr[CFP][k] * vE.p;
-    V += L.gR[k] * vE.V;
-  }
-  {
-    const size_t n = k - 1;
-    e += L.cr[CVE][n] * vW.V - L.cr[CGE][n] * vW.e;
-    p += L.cr[CVP][n] * vW.V - L.cr[CGP][n] * vW.p;
-    V += L.gR[n] * vW.V;
-  }
-  {
-    e += L.cz[CVE][k] * vN.V - L.cz[CFE][k] * vN.e;
-    p += L.cz[CVP][k] * vN.V - L.cz[CFP][k] * vN.p;
-    V += L.gZ[k] * vN.V;
-  }
-  {
-    const size_t n = k - P;
-    e += L.cz[CVE][n] * vS.V - L.cz[CGE][n] * vS.e;
-    p += L.cz[CVP][n] * vS.V - L.cz[CGP][n] * vS.p;
-    V += L.gZ[n] * vS.V;
-  }
-  const T re = L.f[NE][k] - e, rp = L.f[NP][k] - p, rV = L.f[NV][k] - V;
-  Triple<T> x;
-  x.V = (rV - L.fac[FQ1][k] * re - L.fac[FQ2][k] * rp) * L.fac[FIS][k];
-  x.e = (re - L.fac[FA13][k] * x.V) * L.fac[FI11][k];
-  x.p = (rp - L.fac[FA23][k] * x.V) * L.fac[FI22][k];
-  return x;
+  const size_t kW = k - 1, kS = k - P;
+  T re = L.f[NE][k], rp = L.f[NP][k], rV = L.f[NV][k];
+  acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], vE.e, vE.p, vE.V);
+  acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], vW.e, vW.p, vW.V);
+  acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], vN.e, vN.p, vN.V);
+  acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], vS.e, vS.p, vS.V);
+  return block_solve(re, rp, rV, L.fac[FQ1][k], L.fac[FQ2][k], L.fac[FIS][k], L.fac[FA13][k], L.fac[FA23][k],
+                     L.fac[FI11][k], L.fac[FI22][k]);
 }
 
 template <typename T>
@@ -866,15 +833,23 @@ template cudaError_t launch_sweep<float>(const LevelT<float> &, const SweepIO<fl
 template <typename T>
 __device__ __forceinline__ Triple<T> linres_val(const LevelT<T> &L, int i, int j, const T *v0, const T *v1,
                                                 const T *v2, const T *f0, const T *f1, const T *f2) {
-  const size_t k = (size_t)j * L.P + i;
-  T oe, op, oV;
-  offdiag<T>(L, i, k, v0, v1, v2, oe, op, oV);
-  const T ak = L.Ak[k];
-  T je = L.dia[DA11][k] * v0[k] + L.fac[FA13][k] * v2[k] + oe;
-  T jp = L.dia[DA22][k] * v1[k] + L.fac[FA23][k] * v2[k] + op;
-  T jV = ak * (v1[k] - v0[k]) + L.dia[DA33][k] * v2[k] + oV;
-  if (f0) { je = f0[k] - je; jp = f1[k] - jp; jV = f2[k] - jV; }
-  return Triple<T>{je, jp, jV};
+  (void)i;
+  const int P = L.P;
+  const size_t k = (size_t)j * P + i, kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
+  T re = f0 ? f0[k] : T(0), rp = f0 ? f1[k] : T(0), rV = f0 ? f2[k] : T(0);
+  // diagonal block (eq. 14): [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]]
+  re = fmadd(-L.dia[DA11][k], v0[k], re); re = fmadd(-L.fac[FA13][k], v2[k], re);
+  rp = fmadd(-L.dia[DA22][k], v1[k], rp); rp = fmadd(-L.fac[FA23][k], v2[k], rp);
+  rV = fmadd(-L.Ak[k], v1[k] - v0[k], rV); rV = fmadd(-L.dia[DA33][k], v2[k], rV);
+  acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], v0[kE], v1[kE], v2[kE]);
+  acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], v0[kW], v1[kW],
+           v2[kW]);
+  acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], v0[kN], v1[kN], v2[kN]);
+  acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], v0[kS], v1[kS],
+           v2[kS]);
+  // without f the result is -(J v); negation is exact
+  if (!f0) { re = -re; rp = -rp; rV = -rV; }
+  return Triple<T>{re, rp, rV};
 }
 
 template <typename T>
@@ -1689,13 +1664,8 @@ __global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double
   double acc[3] = {0, 0, 0};
   if (i < L.ni && j < L.nz) {
     const size_t k = (size_t)j * L.P + i;
-    const double *v0 = L.du[NE], *v1 = L.du[NP], *v2 = L.du[NV];
-    double oe, op, oV;
-    offdiag<double>(L, i, k, v0, v1, v2, oe, op, oV);
-    const double ak = L.Ak[k];
-    const double re = L.f[NE][k] - (L.dia[DA11][k] * v0[k] + L.fac[FA13][k] * v2[k] + oe);
-    const double rp = L.f[NP][k] - (L.dia[DA22][k] * v1[k] + L.fac[FA23][k] * v2[k] + op);
-    const double rV = L.f[NV][k] - (ak * (v1[k] - v0[k]) + L.dia[DA33][k] * v2[k] + oV);
+    const Triple<double> r = linres_val<double>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP], L.f[NV]);
+    const double re = r.e, rp = r.p, rV = r.V;
     M.f[NE][k] = (float)(re * inv_n0);
     M.f[NP][k] = (float)(rp * inv_n0);
     M.f[NV][k] = (float)rV;
