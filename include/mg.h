@@ -249,8 +249,8 @@ int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, dou
 int mg_autotune(mg_state *s, int32_t *shapes_out);
 
 /* Sets the smoother's launch on one level by hand (what mg_autotune chooses): precision 0 for
- * the FP64 view, 1 for the FP32 view (mixed form); half-sweep block (bx, by) with bx in
- * {32, 64, 128} and bx * by <= 256; fused = 1 for one tiled launch per sweep with tile shape
+ * the FP64 view, 1 for the FP32 view (mixed form); half sweeps in blocks of bx * by threads
+ * (one per node of the colour) with bx in {32, 64, 128} and bx * by <= 256; fused = 1 for one tiled launch per sweep with tile shape
  * `tile` (0: 32x2, 1: 32x4, 2: 32x8, 3: 64x2, 4: 64x4, 5: 128x2), 0 for two half sweeps.
  * Results are the same bit for bit whatever the choice.  MG_EINVAL on a bad level or shape. */
 int mg_set_smoother(mg_state *s, int level, int precision, int bx, int by, int fused, int tile);

@@ -1310,9 +1310,10 @@ double mg_probe_fp64_gflops(void *stream) { return probe_fp64_gflops((cudaStream
 
 int mg_autotune(mg_state *s, int32_t *shapes_out) {
   if (!s) return MG_EINVAL;
-  // half-sweep blocks of at most 128 threads: on the small levels larger blocks leave most SMs
-  // idle (32 x 8 on 129^2: 48 blocks, 11 % slower steady solves), and they never won on 257^2
-  static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
+  // half-sweep blocks (bx * by threads over the colour's nodes) of at most 128 threads: on the
+  // small levels larger blocks leave most SMs idle (256 threads on 129^2: 11 % slower steady
+  // solves), and they never won on 257^2
+  static const int cand[][2] = {{32, 1}, {64, 1}, {128, 1}};
   // the tuning launches write only the correction buffers du and du2 of each level
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
   cudaEvent_t e0, e1;

@@ -694,12 +694,26 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   L.du[NV][k] = x.V;
 }
 
+// The t-th unknown node of one colour (red: i + j even), row by row: two consecutive rows
+// hold ni nodes of each colour together, so threads map onto the colour's nodes with no idle
+// lanes inside a row (one row's colour nodes rarely fill whole warps).  False past the end.
+__device__ __forceinline__ bool colour_node(int t, int ni, int nz, int color, int &i, int &j) {
+  const int p = t / ni, r = t - p * ni;
+  const int j0 = 1 + 2 * p;
+  const int par0 = (j0 + color) & 1;   // first i of the colour in row j0
+  const int n0 = (ni - par0 + 1) >> 1; // colour nodes in row j0
+  if (r < n0) { j = j0; i = 2 * r + par0; }
+  else { j = j0 + 1; i = 2 * (r - n0) + (par0 ^ 1); }
+  return j < nz;
+}
+// thread slots of colour_node for a level: nz / 2 row pairs of ni
+__host__ __device__ __forceinline__ int colour_slots(int ni, int nz) { return (nz / 2) * ni; }
+
 template <typename T>
 __global__ void k_smooth(LevelT<T> L, int color) {
   pdl_launch_dependents();
-  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
-  if (j >= L.nz || i >= L.ni) return;
+  int i, j;
+  if (!colour_node(blockIdx.x * blockDim.x + threadIdx.x, L.ni, L.nz, color, i, j)) return;
   smooth_node<T, true>(L, i, j);
 }
 
@@ -711,18 +725,19 @@ __global__ void k_smooth(LevelT<T> L, int color) {
 template <typename T>
 __global__ void __launch_bounds__(256, 1) k_smooth_ilp(LevelT<T> L, int color) {
   pdl_launch_dependents();
-  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + color) & 1);
-  if (j >= L.nz || i >= L.ni) return;
+  int i, j;
+  if (!colour_node(blockIdx.x * blockDim.x + threadIdx.x, L.ni, L.nz, color, i, j)) return;
   smooth_node<T, true>(L, i, j);
 }
 
 constexpr int SBX = 32, SBY = 2;  // stencil kernels: small blocks so that coarse levels spread over the SMs
 
-// Launch shape (bx, by) is a tuning knob: one thread per node of the colour, bx along r.
+// Launch shape (bx, by) is a tuning knob: one thread per node of the colour (colour_node),
+// blocks of bx * by threads.
 template <typename T>
 cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx, int by) {
-  dim3 b(bx, by), g(((L.nr + 2) / 2 + bx - 1) / bx, (L.nz - 1 + by - 1) / by);
+  const int nb = bx * by;
+  dim3 b(nb), g((colour_slots(L.ni, L.nz) + nb - 1) / nb);
   cudaError_t e;
   if (sizeof(T) == 8 && L.nr <= 128 && bx * by <= 256) e = launch_k((L.pdl & PDL_SMOOTH) != 0, k_smooth_ilp<T>, g, b, 0, st, L, color);
   else e = launch_k((L.pdl & PDL_SMOOTH) != 0, k_smooth<T>, g, b, 0, st, L, color);
@@ -1362,12 +1377,12 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
     else cl.sync();
   };
   auto sweeps = [&](const LevelT<T> &L, int nu) {
-    const int half = (L.nr + 2) / 2;
+    const int slots = colour_slots(L.ni, L.nz);
     for (int it = 0; it < nu; ++it)
       for (int color = 0; color < 2; ++color) {
-        for (int t = tid; t < (L.nz - 1) * half; t += nth) {
-          const int j = t / half + 1, i = 2 * (t % half) + ((j + color) & 1);
-          if (i < L.ni) smooth_node<T>(L, i, j);
+        for (int t = tid; t < slots; t += nth) {
+          int i, j;
+          if (colour_node(t, L.ni, L.nz, color, i, j)) smooth_node<T>(L, i, j);
         }
         bar();
       }
@@ -1470,13 +1485,15 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
+  // colour nodes packed onto the first warps (colour_node): on 17^2 each colour fills exactly
+  // four warps, one per sub-partition, and FP64 issue time goes by warps, not by active lanes
   auto sweeps = [&](const LevelT<T> &L, int nu) {
-    const int half = (L.nr + 2) / 2;
+    const int slots = colour_slots(L.ni, L.nz);
     for (int it = 0; it < nu; ++it)
       for (int color = 0; color < 2; ++color) {
-        for (int t = tid; t < (L.nz - 1) * half; t += nth) {
-          const int j = t / half + 1, i = 2 * (t % half) + ((j + color) & 1);
-          if (i < L.ni) smooth_node<T>(L, i, j);
+        for (int t = tid; t < slots; t += nth) {
+          int i, j;
+          if (colour_node(t, L.ni, L.nz, color, i, j)) smooth_node<T>(L, i, j);
         }
         __syncthreads();
       }
