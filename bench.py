@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 # DRAM bytes read + written by one k_smooth<double> half sweep at 1025^2 in an ncu capture
-TRAFFIC_K_SMOOTH_FP64_1025 = None
+TRAFFIC_K_SMOOTH_FP64_1025 = 242450176
 
 
 def _vcycle_1025(precision, peaks):
@@ -366,7 +366,7 @@ def run_ours(args):
     # DRAM bytes read + written per launch in one ncu capture of the kernel (cold caches): the
     # half sweeps of the 257^2 level (k_smooth, profiles/k_smooth_fp64_257.md) and of the 129^2
     # level (k_smooth_ilp, profiles/smoother_fp64_129.md); the other levels have no capture
-    traffic_ncu = {(256, False): 14347904, (128, False): 3639296}
+    traffic_ncu = {(256, False): 14348288, (128, False): 3639552}
     levels = []
     for lev, (n_l, ms_l) in enumerate(smooth_prof):
         if not n_l:
