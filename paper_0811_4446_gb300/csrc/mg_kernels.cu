@@ -326,16 +326,39 @@ __device__ void reduce_finish(double (&v)[K], double *partials, unsigned *counte
   if (!last) return;
   __threadfence();
   const int nthr = blockDim.x * blockDim.y;
+  // each thread folds blocks tid, tid + nthr, ... in that order, four blocks' partials per
+  // round with all their loads in flight (L2 reads, .cg: the other blocks' writes are visible
+  // after their fence and the counter); a dependent load per block made this pass the longest
+  // part of a norm launch
+  double xs[K];
+  bool first = true;
+#pragma unroll
+  for (int q = 0; q < K; ++q) xs[q] = 0.0;
+  int b = tid;
+  for (; b + 3 * nthr < nblocks; b += 4 * nthr) {
+    double y[4][K];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q) y[u][q] = __ldcg(partials + (size_t)(b + u * nthr) * K + q);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        xs[q] = (first && u == 0) ? y[u][q] : (op ? fmax(xs[q], y[u][q]) : xs[q] + y[u][q]);
+    first = false;
+  }
+  for (; b < nblocks; b += nthr) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const double y = __ldcg(partials + (size_t)b * K + q);
+      xs[q] = first ? y : (op ? fmax(xs[q], y) : xs[q] + y);
+    }
+    first = false;
+  }
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    double x = op ? 0.0 : 0.0;
-    bool first = true;
-    for (int b = tid; b < nblocks; b += nthr) {
-      const double y = ((volatile double *)partials)[(size_t)b * K + q];
-      x = first ? y : (op ? fmax(x, y) : x + y);
-      first = false;
-    }
-    if (first) x = op ? -1.0 : 0.0;
+    double x = first ? (op ? -1.0 : 0.0) : xs[q];
     for (int o = 16; o > 0; o >>= 1) {
       const double y = __shfl_down_sync(0xffffffffu, x, o);
       x = op ? fmax(x, y) : x + y;
