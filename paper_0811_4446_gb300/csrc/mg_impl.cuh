@@ -26,6 +26,13 @@ enum { CGE = 0, CFE = 1, CVE = 2, CGP = 3, CFP = 4, CVP = 5, NCOEF = 6 };
 // (ak = A e/eps0): inverse pivots, Schur-complement multipliers q1 = -ak/a11, q2 = ak/a22,
 // inverse Schur complement, and the two couplings to V
 enum { FI11 = 0, FI22 = 1, FQ1 = 2, FQ2 = 3, FIS = 4, FA13 = 5, FA23 = 6, NFAC = 7 };
+// The factor arrays are stored colour-split within each row of pitch P: node (i, j) with i + j
+// even at i / 2, the other colour at P / 2 + i / 2 (P is a multiple of 4 and exceeds nr, so
+// both halves hold their row's nodes).  A half sweep then reads its colour's factors as one
+// contiguous run per row instead of every other element.
+__host__ __device__ __forceinline__ size_t fac_idx(int P, int i, int j) {
+  return (size_t)j * P + (((i + j) & 1) ? (P >> 1) : 0) + (i >> 1);
+}
 enum { DA11 = 0, DA22 = 1, DA33 = 2, NDIA = 3 };
 
 // Transport inputs (mu, D constant or tabulated in |E|), already divided by the pressure factor.

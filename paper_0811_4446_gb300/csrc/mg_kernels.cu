@@ -587,13 +587,14 @@ __device__ __forceinline__ void factor_node(const Level &L, const LevelT<float> 
   const double i11 = 1.0 / a11, i22 = 1.0 / a22;
   const double q1 = -ak * i11, q2 = ak * i22;
   const double is = 1.0 / (a33 - q1 * a13 - q2 * a23);
-  L.fac[FI11][k] = i11; L.fac[FI22][k] = i22; L.fac[FQ1][k] = q1; L.fac[FQ2][k] = q2; L.fac[FIS][k] = is;
-  L.fac[FA13][k] = a13; L.fac[FA23][k] = a23;
+  const size_t kf = fac_idx(P, i, j);
+  L.fac[FI11][kf] = i11; L.fac[FI22][kf] = i22; L.fac[FQ1][kf] = q1; L.fac[FQ2][kf] = q2; L.fac[FIS][kf] = is;
+  L.fac[FA13][kf] = a13; L.fac[FA23][kf] = a23;
   L.dia[DA11][k] = a11; L.dia[DA22][k] = a22; L.dia[DA33][k] = a33;
   if (mixed) {  // density unknowns and rows in units of n0: a13, a23 / n0; q1, q2 * n0
-    M.fac[FI11][k] = (float)i11; M.fac[FI22][k] = (float)i22;
-    M.fac[FQ1][k] = (float)(q1 * n0); M.fac[FQ2][k] = (float)(q2 * n0); M.fac[FIS][k] = (float)is;
-    M.fac[FA13][k] = (float)(a13 / n0); M.fac[FA23][k] = (float)(a23 / n0);
+    M.fac[FI11][kf] = (float)i11; M.fac[FI22][kf] = (float)i22;
+    M.fac[FQ1][kf] = (float)(q1 * n0); M.fac[FQ2][kf] = (float)(q2 * n0); M.fac[FIS][kf] = (float)is;
+    M.fac[FA13][kf] = (float)(a13 / n0); M.fac[FA23][kf] = (float)(a23 / n0);
     M.dia[DA11][k] = (float)a11; M.dia[DA22][k] = (float)a22; M.dia[DA33][k] = (float)a33;
   }
 }
@@ -688,7 +689,6 @@ __device__ __forceinline__ Triple<T> block_solve(T re, T rp, T rV, T q1, T q2, T
 // previous kernel, the corrections and right-hand sides after.
 template <typename T, bool PDL = false>
 __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
-  (void)i;
   const int P = L.P;
   const size_t k = (size_t)j * P + i;
   const size_t kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
@@ -696,8 +696,9 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   const T aW0 = L.cr[CVE][kW], aW1 = L.cr[CGE][kW], aW2 = L.cr[CVP][kW], aW3 = L.cr[CGP][kW], gW = L.gR[kW];
   const T aN0 = L.cz[CVE][k], aN1 = L.cz[CFE][k], aN2 = L.cz[CVP][k], aN3 = L.cz[CFP][k], gN = L.gZ[k];
   const T aS0 = L.cz[CVE][kS], aS1 = L.cz[CGE][kS], aS2 = L.cz[CVP][kS], aS3 = L.cz[CGP][kS], gS = L.gZ[kS];
-  const T q1 = L.fac[FQ1][k], q2 = L.fac[FQ2][k], is = L.fac[FIS][k];
-  const T a13 = L.fac[FA13][k], a23 = L.fac[FA23][k], i11 = L.fac[FI11][k], i22 = L.fac[FI22][k];
+  const size_t kf = fac_idx(P, i, j);
+  const T q1 = L.fac[FQ1][kf], q2 = L.fac[FQ2][kf], is = L.fac[FIS][kf];
+  const T a13 = L.fac[FA13][kf], a23 = L.fac[FA23][kf], i11 = L.fac[FI11][kf], i22 = L.fac[FI22][kf];
   if (PDL) pdl_wait();
   const T *ve = L.du[NE], *vp = L.du[NP], *vV = L.du[NV];
   const T eE = ve[kE], pE = vp[kE], wE = vV[kE];
@@ -779,9 +780,8 @@ template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream
 // launch and the result equals two half-sweep launches bit for bit.  Coefficients of a face
 // are read by its red end in phase 1 and by its black end in phase 2 (an L1/L2 hit).
 template <typename T>
-__device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, size_t k, const Triple<T> &vE,
+__device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, int j, size_t k, const Triple<T> &vE,
                                                  const Triple<T> &vW, const Triple<T> &vN, const Triple<T> &vS) {
-  (void)i;
   const int P = L.P;
   const size_t kW = k - 1, kS = k - P;
   T re = L.f[NE][k], rp = L.f[NP][k], rV = L.f[NV][k];
@@ -789,8 +789,9 @@ __device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, size
   acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], vW.e, vW.p, vW.V);
   acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], vN.e, vN.p, vN.V);
   acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], vS.e, vS.p, vS.V);
-  return block_solve(re, rp, rV, L.fac[FQ1][k], L.fac[FQ2][k], L.fac[FIS][k], L.fac[FA13][k], L.fac[FA23][k],
-                     L.fac[FI11][k], L.fac[FI22][k]);
+  const size_t kf = fac_idx(P, i, j);
+  return block_solve(re, rp, rV, L.fac[FQ1][kf], L.fac[FQ2][kf], L.fac[FIS][kf], L.fac[FA13][kf],
+                     L.fac[FA23][kf], L.fac[FI11][kf], L.fac[FI22][kf]);
 }
 
 template <typename T>
@@ -815,7 +816,7 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
     T ve = 0, vp = 0, vV = 0;
     if (i >= 0 && i < L.ni && j >= 1 && j < nz && ((i + j) & 1) == 0) {
       const size_t k = (size_t)j * P + i;
-      const Triple<T> x = node_update<T>(L, i, k, gload<T>(io.in, k + 1), gload<T>(io.in, k - 1),
+      const Triple<T> x = node_update<T>(L, i, j, k, gload<T>(io.in, k + 1), gload<T>(io.in, k - 1),
                                          gload<T>(io.in, k + P), gload<T>(io.in, k - P));
       ve = x.e; vp = x.p; vV = x.V;
     }
@@ -837,7 +838,7 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
           t.e = sr[NE][b][a]; t.p = sr[NP][b][a]; t.V = sr[NV][b][a];
           return t;
         };
-        x = node_update<T>(L, i, k, at(li + 1, lj), at(li - 1, lj), at(li, lj + 1), at(li, lj - 1));
+        x = node_update<T>(L, i, j, k, at(li + 1, lj), at(li - 1, lj), at(li, lj + 1), at(li, lj - 1));
       }
       io.out[NE][k] = x.e; io.out[NP][k] = x.p; io.out[NV][k] = x.V;
     }
@@ -871,13 +872,13 @@ template cudaError_t launch_sweep<float>(const LevelT<float> &, const SweepIO<fl
 template <typename T>
 __device__ __forceinline__ Triple<T> linres_val(const LevelT<T> &L, int i, int j, const T *v0, const T *v1,
                                                 const T *v2, const T *f0, const T *f1, const T *f2) {
-  (void)i;
   const int P = L.P;
   const size_t k = (size_t)j * P + i, kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
   T re = f0 ? f0[k] : T(0), rp = f0 ? f1[k] : T(0), rV = f0 ? f2[k] : T(0);
   // diagonal block (eq. 14): [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]]
-  re = fmadd(-L.dia[DA11][k], v0[k], re); re = fmadd(-L.fac[FA13][k], v2[k], re);
-  rp = fmadd(-L.dia[DA22][k], v1[k], rp); rp = fmadd(-L.fac[FA23][k], v2[k], rp);
+  const size_t kf = fac_idx(P, i, j);
+  re = fmadd(-L.dia[DA11][k], v0[k], re); re = fmadd(-L.fac[FA13][kf], v2[k], re);
+  rp = fmadd(-L.dia[DA22][k], v1[k], rp); rp = fmadd(-L.fac[FA23][kf], v2[k], rp);
   rV = fmadd(-L.Ak[k], v1[k] - v0[k], rV); rV = fmadd(-L.dia[DA33][k], v2[k], rV);
   acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], v0[kE], v1[kE], v2[kE]);
   acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], v0[kW], v1[kW],
