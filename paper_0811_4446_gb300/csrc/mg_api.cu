@@ -1149,8 +1149,10 @@ int mg_linear_solve(mg_state *s, double dt, const double *f_ne, const double *f_
   if ((rc = residual(s, 0, dt, false, nullptr, nullptr, tn))) return rc;
   if ((rc = build_hierarchy(s, 0, dt))) return rc;
   const double *src[3] = {f_ne, f_np, f_V};
+  // caller rows -> the residual scratch (row layout) -> f (colour-split layout)
   for (int q = 0; q < 3; ++q)
-    if ((rc = copy_in(s, b, b.L.f[q], src[q], where, 1, b.nz - 1))) return rc;
+    if ((rc = copy_in(s, b, b.L.r[q], src[q], where, 1, b.nz - 1))) return rc;
+  CK(launch_split_rows(b.L, b.L.r, b.L.f, s->stream));
   int nc = 0;
   bool ok;
   if ((rc = linear_solve(s, 0, eta, max_cycles, tn, history, &nc, &ok))) return rc;

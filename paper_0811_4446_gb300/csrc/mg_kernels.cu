@@ -476,7 +476,10 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
     const double ak = L.Ak[k];
     FV += ak * (np[k] - ne[k]);
     TV += ak * (fabs(np[k]) + fabs(ne[k]));
-    if (write_f) { L.f[NE][k] = -Fe; L.f[NP][k] = -Fp; L.f[NV][k] = -FV; }
+    if (write_f) {
+      const size_t kf = cidx(P, i, j);
+      L.f[NE][kf] = -Fe; L.f[NP][kf] = -Fp; L.f[NV][kf] = -FV;
+    }
     if (F0) { F0[k] = Fe; F1[k] = Fp; F2[k] = FV; }
     acc[0] = Fe * Fe; acc[1] = Fp * Fp; acc[2] = FV * FV;
     acc[3] = Te * Te; acc[4] = Tp * Tp; acc[5] = TV * TV;
@@ -543,7 +546,10 @@ __global__ void k_residual(Level L, StateView sv, Transport tr, double dt_inv, i
     }
     FV += A * kKappa * (np[k] - ne[k]);
     TV += A * kKappa * (fabs(np[k]) + fabs(ne[k]));
-    if (write_f) { L.f[NE][k] = -Fe; L.f[NP][k] = -Fp; L.f[NV][k] = -FV; }
+    if (write_f) {
+      const size_t kf = cidx(P, i, j);
+      L.f[NE][kf] = -Fe; L.f[NP][kf] = -Fp; L.f[NV][kf] = -FV;
+    }
     if (F0) { F0[k] = Fe; F1[k] = Fp; F2[k] = FV; }
     acc[0] = Fe * Fe; acc[1] = Fp * Fp; acc[2] = FV * FV;
     acc[3] = Te * Te; acc[4] = Tp * Tp; acc[5] = TV * TV;
@@ -587,7 +593,7 @@ __device__ __forceinline__ void factor_node(const Level &L, const LevelT<float> 
   const double i11 = 1.0 / a11, i22 = 1.0 / a22;
   const double q1 = -ak * i11, q2 = ak * i22;
   const double is = 1.0 / (a33 - q1 * a13 - q2 * a23);
-  const size_t kf = fac_idx(P, i, j);
+  const size_t kf = cidx(P, i, j);
   L.fac[FI11][kf] = i11; L.fac[FI22][kf] = i22; L.fac[FQ1][kf] = q1; L.fac[FQ2][kf] = q2; L.fac[FIS][kf] = is;
   L.fac[FA13][kf] = a13; L.fac[FA23][kf] = a23;
   L.dia[DA11][k] = a11; L.dia[DA22][k] = a22; L.dia[DA33][k] = a33;
@@ -696,7 +702,7 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   const T aW0 = L.cr[CVE][kW], aW1 = L.cr[CGE][kW], aW2 = L.cr[CVP][kW], aW3 = L.cr[CGP][kW], gW = L.gR[kW];
   const T aN0 = L.cz[CVE][k], aN1 = L.cz[CFE][k], aN2 = L.cz[CVP][k], aN3 = L.cz[CFP][k], gN = L.gZ[k];
   const T aS0 = L.cz[CVE][kS], aS1 = L.cz[CGE][kS], aS2 = L.cz[CVP][kS], aS3 = L.cz[CGP][kS], gS = L.gZ[kS];
-  const size_t kf = fac_idx(P, i, j);
+  const size_t kf = cidx(P, i, j);
   const T q1 = L.fac[FQ1][kf], q2 = L.fac[FQ2][kf], is = L.fac[FIS][kf];
   const T a13 = L.fac[FA13][kf], a23 = L.fac[FA23][kf], i11 = L.fac[FI11][kf], i22 = L.fac[FI22][kf];
   if (PDL) pdl_wait();
@@ -705,7 +711,7 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   const T eW = ve[kW], pW = vp[kW], wW = vV[kW];
   const T eN = ve[kN], pN = vp[kN], wN = vV[kN];
   const T eS = ve[kS], pS = vp[kS], wS = vV[kS];
-  const T f0 = L.f[NE][k], f1 = L.f[NP][k], f2 = L.f[NV][k];
+  const T f0 = L.f[NE][kf], f1 = L.f[NP][kf], f2 = L.f[NV][kf];
   asm volatile("" ::: "memory");
   T re = f0, rp = f1, rV = f2;
   acc_face(re, rp, rV, aE0, aE1, aE2, aE3, gE, eE, pE, wE);
@@ -784,12 +790,12 @@ __device__ __forceinline__ Triple<T> node_update(const LevelT<T> &L, int i, int 
                                                  const Triple<T> &vW, const Triple<T> &vN, const Triple<T> &vS) {
   const int P = L.P;
   const size_t kW = k - 1, kS = k - P;
-  T re = L.f[NE][k], rp = L.f[NP][k], rV = L.f[NV][k];
+  const size_t kf = cidx(P, i, j);
+  T re = L.f[NE][kf], rp = L.f[NP][kf], rV = L.f[NV][kf];
   acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], vE.e, vE.p, vE.V);
   acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], vW.e, vW.p, vW.V);
   acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], vN.e, vN.p, vN.V);
   acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], vS.e, vS.p, vS.V);
-  const size_t kf = fac_idx(P, i, j);
   return block_solve(re, rp, rV, L.fac[FQ1][kf], L.fac[FQ2][kf], L.fac[FIS][kf], L.fac[FA13][kf],
                      L.fac[FA23][kf], L.fac[FI11][kf], L.fac[FI22][kf]);
 }
@@ -874,9 +880,9 @@ __device__ __forceinline__ Triple<T> linres_val(const LevelT<T> &L, int i, int j
                                                 const T *v2, const T *f0, const T *f1, const T *f2) {
   const int P = L.P;
   const size_t k = (size_t)j * P + i, kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
-  T re = f0 ? f0[k] : T(0), rp = f0 ? f1[k] : T(0), rV = f0 ? f2[k] : T(0);
+  const size_t kf = cidx(P, i, j);
+  T re = f0 ? f0[kf] : T(0), rp = f0 ? f1[kf] : T(0), rV = f0 ? f2[kf] : T(0);
   // diagonal block (eq. 14): [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]]
-  const size_t kf = fac_idx(P, i, j);
   re = fmadd(-L.dia[DA11][k], v0[k], re); re = fmadd(-L.fac[FA13][kf], v2[k], re);
   rp = fmadd(-L.dia[DA22][k], v1[k], rp); rp = fmadd(-L.fac[FA23][kf], v2[k], rp);
   rV = fmadd(-L.Ak[k], v1[k] - v0[k], rV); rV = fmadd(-L.dia[DA33][k], v2[k], rV);
@@ -950,7 +956,8 @@ __device__ __forceinline__ void restrict_node(const LevelT<T> &F, const LevelT<T
       s0 += w * F.r[NE][kf]; s1 += w * F.r[NP][kf]; s2 += w * F.r[NV][kf];
     }
   }
-  C.f[NE][kc] = s0; C.f[NP][kc] = s1; C.f[NV][kc] = s2;
+  const size_t kcf = cidx(C.P, I, J);
+  C.f[NE][kcf] = s0; C.f[NP][kcf] = s1; C.f[NV][kcf] = s2;
   C.du[NE][kc] = T(0); C.du[NP][kc] = T(0); C.du[NV][kc] = T(0);
 }
 
@@ -994,7 +1001,8 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) 
         s0 += w * sr[0][ls]; s1 += w * sr[1][ls]; s2 += w * sr[2][ls];
       }
     }
-    C.f[NE][kc] = s0; C.f[NP][kc] = s1; C.f[NV][kc] = s2;
+    const size_t kcf = cidx(C.P, I, J);
+    C.f[NE][kcf] = s0; C.f[NP][kcf] = s1; C.f[NV][kcf] = s2;
     C.du[NE][kc] = T(0); C.du[NP][kc] = T(0); C.du[NV][kc] = T(0);
   }
 }
@@ -1359,7 +1367,7 @@ __device__ __forceinline__ void coarse_solve_block(const LevelT<T> &L, const dou
     const int node = q / 3, fld = q % 3;
     const int j = node / L.ni + 1, i = node % L.ni;
     const double sc = fld == NV ? 1.0 : nscale;
-    fs[q] = rs[q] * sc * (double)L.f[fld][(size_t)j * L.P + i];
+    fs[q] = rs[q] * sc * (double)L.f[fld][cidx(L.P, i, j)];
   }
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += nthreads) {
@@ -1696,6 +1704,24 @@ cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n
   return e;
 }
 
+// Right-hand sides given in the natural row layout (pitch P) -> the colour-split layout of f,
+// rows 1 .. nz-1.
+__global__ void k_split_rows(Level L, const double *i0, const double *i1, const double *i2, double *o0,
+                             double *o1, double *o2) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (i > L.nr || j >= L.nz) return;
+  const size_t k = (size_t)j * L.P + i, kf = cidx(L.P, i, j);
+  o0[kf] = i0[k]; o1[kf] = i1[k]; o2[kf] = i2[k];
+}
+
+cudaError_t launch_split_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
+  k_split_rows<<<g, b, 0, st>>>(L, in[0], in[1], in[2], out[0], out[1], out[2]);
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double *partials, unsigned *counter,
                                  double *out3) {
   pdl_launch_dependents();
@@ -1704,12 +1730,12 @@ __global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double
   const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
   double acc[3] = {0, 0, 0};
   if (i < L.ni && j < L.nz) {
-    const size_t k = (size_t)j * L.P + i;
     const Triple<double> r = linres_val<double>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP], L.f[NV]);
     const double re = r.e, rp = r.p, rV = r.V;
-    M.f[NE][k] = (float)(re * inv_n0);
-    M.f[NP][k] = (float)(rp * inv_n0);
-    M.f[NV][k] = (float)rV;
+    const size_t kf = cidx(L.P, i, j);
+    M.f[NE][kf] = (float)(re * inv_n0);
+    M.f[NP][kf] = (float)(rp * inv_n0);
+    M.f[NV][kf] = (float)rV;
     acc[0] = re * re; acc[1] = rp * rp; acc[2] = rV * rV;
   }
   reduce_finish<3>(acc, partials, counter, out3, 0);
