@@ -1124,12 +1124,14 @@ int mg_jacobian_apply(mg_state *s, double dt, const double *v_ne, const double *
   CK(launch_coef(b.L, b.sv, s->tr, s->stream));
   CK(launch_factor(b.L, nullptr, dt, s->prm.n0, s->stream));
   const double *src[3] = {v_ne, v_np, v_V};
-  for (int q = 0; q < 3; ++q) {
-    if ((rc = copy_in(s, b, b.L.du[q], src[q], where, 1, b.nz - 1))) return rc;
-    // a Dirichlet wall carries no unknowns: its entries of v do not enter J v
-    if (b.L.ni == b.nr)
-      CK(cudaMemset2DAsync(b.L.du[q] + b.nr, b.P * sizeof(double), 0, sizeof(double), b.nz + 1, s->stream));
-  }
+  // caller rows -> the residual scratch -> du (colour-split); a Dirichlet wall carries no
+  // unknowns, so its entries of v are zeroed and do not enter J v
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_in(s, b, b.L.r[q], src[q], where, 1, b.nz - 1))) return rc;
+  CK(launch_zero_du<double>(b.L, s->stream));
+  CK(launch_split_rows(b.L, b.L.r, b.L.du, s->stream));
+  // J v is written on the unknown rows and columns only: the rest of the output is zero
+  for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(b.L.r[q], 0, b.nodes * sizeof(double), s->stream));
   CK(launch_linres<double>(b.L, b.L.du, nullptr, b.L.r, nullptr, nullptr, nullptr, s->stream));
   double *dst[3] = {o_ne, o_np, o_V};
   for (int q = 0; q < 3; ++q)
@@ -1153,13 +1155,15 @@ int mg_linear_solve(mg_state *s, double dt, const double *f_ne, const double *f_
   for (int q = 0; q < 3; ++q)
     if ((rc = copy_in(s, b, b.L.r[q], src[q], where, 1, b.nz - 1))) return rc;
   CK(launch_split_rows(b.L, b.L.r, b.L.f, s->stream));
+  for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(b.L.r[q], 0, b.nodes * sizeof(double), s->stream));
   int nc = 0;
   bool ok;
   if ((rc = linear_solve(s, 0, eta, max_cycles, tn, history, &nc, &ok))) return rc;
   if (cycles) *cycles = nc;
   double *dst[3] = {x_ne, x_np, x_V};
+  CK(launch_join_rows(b.L, b.L.du, b.L.r, s->stream));
   for (int q = 0; q < 3; ++q)
-    if ((rc = copy_out(s, b, dst[q], b.L.du[q], where))) return rc;
+    if ((rc = copy_out(s, b, dst[q], b.L.r[q], where))) return rc;
   CK(cudaStreamSynchronize(s->stream));
   return ok ? MG_OK : fail(s, MG_ENOCONV, "linear solve: tolerance not reached in %d V-cycles", nc);
 }

@@ -26,13 +26,32 @@ enum { CGE = 0, CFE = 1, CVE = 2, CGP = 3, CFP = 4, CVP = 5, NCOEF = 6 };
 // (ak = A e/eps0): inverse pivots, Schur-complement multipliers q1 = -ak/a11, q2 = ak/a22,
 // inverse Schur complement, and the two couplings to V
 enum { FI11 = 0, FI22 = 1, FQ1 = 2, FQ2 = 3, FIS = 4, FA13 = 5, FA23 = 6, NFAC = 7 };
-// The factor arrays and the right-hand sides f are stored colour-split within each row of
-// pitch P: node (i, j) with i + j even at i / 2, the other colour at P / 2 + i / 2 (P is a
+// The factor arrays, the right-hand sides f and the corrections du are stored colour-split
+// within each row of pitch P: node (i, j) with i + j even at i / 2, the other colour at P / 2 + i / 2 (P is a
 // multiple of 4 and exceeds nr, so both halves hold their row's nodes).  A half sweep then
-// reads its colour's factors and right-hand sides as one contiguous run per row instead of
-// every other element.
+// reads its colour's factors and right-hand sides and the other colour's corrections as
+// contiguous runs per row, and writes its own corrections as one, instead of every other
+// element.  Slots past nr stay zero (multiplied by zero face coefficients at i = 0 and nr).
 __host__ __device__ __forceinline__ size_t cidx(int P, int i, int j) {
   return (size_t)j * P + (((i + j) & 1) ? (P >> 1) : 0) + (i >> 1);
+}
+// Colour-split positions of node (i, j) (self) and of its four neighbours, which are all of
+// the other colour: E and W are adjacent slots of that colour's half of row j, N and S the
+// slot i / 2 of its half of rows j + 1 and j - 1.
+struct SplitNb {
+  size_t self, E, W, N, S;
+};
+__host__ __device__ __forceinline__ SplitNb split_nb(int P, int i, int j) {
+  const int half = P >> 1, h = i >> 1;
+  const int other = ((i + j) & 1) ? 0 : half;          // the other colour's half
+  const size_t row = (size_t)j * P;
+  SplitNb n;
+  n.self = row + (half - other) + h;
+  n.E = row + other + h + (i & 1);
+  n.W = n.E - 1;
+  n.N = row + P + other + h;
+  n.S = row - P + other + h;
+  return n;
 }
 enum { DA11 = 0, DA22 = 1, DA33 = 2, NDIA = 3 };
 
@@ -181,6 +200,7 @@ template <typename T>
 cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st);
 // mixed form
 cudaError_t launch_split_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);
+cudaError_t launch_join_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);
 cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);
 cudaError_t launch_outer_residual(const Level &L, const LevelT<float> &M, double n0, double *partials,
                                   unsigned *counter, double *out3, cudaStream_t st);

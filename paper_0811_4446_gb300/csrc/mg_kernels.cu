@@ -697,20 +697,23 @@ template <typename T, bool PDL = false>
 __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   const int P = L.P;
   const size_t k = (size_t)j * P + i;
-  const size_t kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
+  const size_t kW = k - 1, kS = k - P;
   const T aE0 = L.cr[CVE][k], aE1 = L.cr[CFE][k], aE2 = L.cr[CVP][k], aE3 = L.cr[CFP][k], gE = L.gR[k];
   const T aW0 = L.cr[CVE][kW], aW1 = L.cr[CGE][kW], aW2 = L.cr[CVP][kW], aW3 = L.cr[CGP][kW], gW = L.gR[kW];
   const T aN0 = L.cz[CVE][k], aN1 = L.cz[CFE][k], aN2 = L.cz[CVP][k], aN3 = L.cz[CFP][k], gN = L.gZ[k];
   const T aS0 = L.cz[CVE][kS], aS1 = L.cz[CGE][kS], aS2 = L.cz[CVP][kS], aS3 = L.cz[CGP][kS], gS = L.gZ[kS];
-  const size_t kf = cidx(P, i, j);
+  const SplitNb d = split_nb(P, i, j);
+  const size_t kf = d.self;
   const T q1 = L.fac[FQ1][kf], q2 = L.fac[FQ2][kf], is = L.fac[FIS][kf];
   const T a13 = L.fac[FA13][kf], a23 = L.fac[FA23][kf], i11 = L.fac[FI11][kf], i22 = L.fac[FI22][kf];
   if (PDL) pdl_wait();
+  // corrections in the colour-split layout: the four neighbours are of the other colour
+  const size_t dE = d.E, dW = d.W, dN = d.N, dS = d.S;
   const T *ve = L.du[NE], *vp = L.du[NP], *vV = L.du[NV];
-  const T eE = ve[kE], pE = vp[kE], wE = vV[kE];
-  const T eW = ve[kW], pW = vp[kW], wW = vV[kW];
-  const T eN = ve[kN], pN = vp[kN], wN = vV[kN];
-  const T eS = ve[kS], pS = vp[kS], wS = vV[kS];
+  const T eE = ve[dE], pE = vp[dE], wE = vV[dE];
+  const T eW = ve[dW], pW = vp[dW], wW = vV[dW];
+  const T eN = ve[dN], pN = vp[dN], wN = vV[dN];
+  const T eS = ve[dS], pS = vp[dS], wS = vV[dS];
   const T f0 = L.f[NE][kf], f1 = L.f[NP][kf], f2 = L.f[NV][kf];
   asm volatile("" ::: "memory");
   T re = f0, rp = f1, rV = f2;
@@ -719,9 +722,9 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   acc_face(re, rp, rV, aN0, aN1, aN2, aN3, gN, eN, pN, wN);
   acc_face(re, rp, rV, aS0, aS1, aS2, aS3, gS, eS, pS, wS);
   const Triple<T> x = block_solve(re, rp, rV, q1, q2, is, a13, a23, i11, i22);
-  L.du[NE][k] = x.e;
-  L.du[NP][k] = x.p;
-  L.du[NV][k] = x.V;
+  L.du[NE][kf] = x.e;
+  L.du[NP][kf] = x.p;
+  L.du[NV][kf] = x.V;
 }
 
 // The t-th unknown node of one colour (red: i + j even), row by row: two consecutive rows
@@ -822,8 +825,9 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
     T ve = 0, vp = 0, vV = 0;
     if (i >= 0 && i < L.ni && j >= 1 && j < nz && ((i + j) & 1) == 0) {
       const size_t k = (size_t)j * P + i;
-      const Triple<T> x = node_update<T>(L, i, j, k, gload<T>(io.in, k + 1), gload<T>(io.in, k - 1),
-                                         gload<T>(io.in, k + P), gload<T>(io.in, k - P));
+      const SplitNb d = split_nb(P, i, j);
+      const Triple<T> x = node_update<T>(L, i, j, k, gload<T>(io.in, d.E), gload<T>(io.in, d.W),
+                                         gload<T>(io.in, d.N), gload<T>(io.in, d.S));
       ve = x.e; vp = x.p; vV = x.V;
     }
     sr[NE][lj][li] = ve; sr[NP][lj][li] = vp; sr[NV][lj][li] = vV;
@@ -846,7 +850,8 @@ __global__ void __launch_bounds__(TX * TY) k_sweep(LevelT<T> L, SweepIO<T> io) {
         };
         x = node_update<T>(L, i, j, k, at(li + 1, lj), at(li - 1, lj), at(li, lj + 1), at(li, lj - 1));
       }
-      io.out[NE][k] = x.e; io.out[NP][k] = x.p; io.out[NV][k] = x.V;
+      const size_t kd = cidx(P, i, j);
+      io.out[NE][kd] = x.e; io.out[NP][kd] = x.p; io.out[NV][kd] = x.V;
     }
   }
 }
@@ -879,19 +884,21 @@ template <typename T>
 __device__ __forceinline__ Triple<T> linres_val(const LevelT<T> &L, int i, int j, const T *v0, const T *v1,
                                                 const T *v2, const T *f0, const T *f1, const T *f2) {
   const int P = L.P;
-  const size_t k = (size_t)j * P + i, kE = k + 1, kW = k - 1, kN = k + P, kS = k - P;
-  const size_t kf = cidx(P, i, j);
+  const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
+  // f, the factors and v (a correction) in the colour-split layout, the face arrays by row
+  const SplitNb d = split_nb(P, i, j);
+  const size_t kf = d.self, dE = d.E, dW = d.W, dN = d.N, dS = d.S;
   T re = f0 ? f0[kf] : T(0), rp = f0 ? f1[kf] : T(0), rV = f0 ? f2[kf] : T(0);
   // diagonal block (eq. 14): [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]]
-  re = fmadd(-L.dia[DA11][k], v0[k], re); re = fmadd(-L.fac[FA13][kf], v2[k], re);
-  rp = fmadd(-L.dia[DA22][k], v1[k], rp); rp = fmadd(-L.fac[FA23][kf], v2[k], rp);
-  rV = fmadd(-L.Ak[k], v1[k] - v0[k], rV); rV = fmadd(-L.dia[DA33][k], v2[k], rV);
-  acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], v0[kE], v1[kE], v2[kE]);
-  acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], v0[kW], v1[kW],
-           v2[kW]);
-  acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], v0[kN], v1[kN], v2[kN]);
-  acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], v0[kS], v1[kS],
-           v2[kS]);
+  re = fmadd(-L.dia[DA11][k], v0[kf], re); re = fmadd(-L.fac[FA13][kf], v2[kf], re);
+  rp = fmadd(-L.dia[DA22][k], v1[kf], rp); rp = fmadd(-L.fac[FA23][kf], v2[kf], rp);
+  rV = fmadd(-L.Ak[k], v1[kf] - v0[kf], rV); rV = fmadd(-L.dia[DA33][k], v2[kf], rV);
+  acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], v0[dE], v1[dE], v2[dE]);
+  acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], v0[dW], v1[dW],
+           v2[dW]);
+  acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], v0[dN], v1[dN], v2[dN]);
+  acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], v0[dS], v1[dS],
+           v2[dS]);
   // without f the result is -(J v); negation is exact
   if (!f0) { re = -re; rp = -rp; rV = -rV; }
   return Triple<T>{re, rp, rV};
@@ -958,7 +965,7 @@ __device__ __forceinline__ void restrict_node(const LevelT<T> &F, const LevelT<T
   }
   const size_t kcf = cidx(C.P, I, J);
   C.f[NE][kcf] = s0; C.f[NP][kcf] = s1; C.f[NV][kcf] = s2;
-  C.du[NE][kc] = T(0); C.du[NP][kc] = T(0); C.du[NV][kc] = T(0);
+  C.du[NE][kcf] = T(0); C.du[NP][kcf] = T(0); C.du[NV][kcf] = T(0);
 }
 
 
@@ -1003,7 +1010,7 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) 
     }
     const size_t kcf = cidx(C.P, I, J);
     C.f[NE][kcf] = s0; C.f[NP][kcf] = s1; C.f[NV][kcf] = s2;
-    C.du[NE][kc] = T(0); C.du[NP][kc] = T(0); C.du[NV][kc] = T(0);
+    C.du[NE][kcf] = T(0); C.du[NP][kcf] = T(0); C.du[NV][kcf] = T(0);
   }
 }
 
@@ -1021,7 +1028,7 @@ template cudaError_t launch_linres_restrict<float>(const LevelT<float> &, const 
 // K6: prolongation and correction du_f += P du_c (bilinear in (r, z)).
 template <typename T>
 __device__ __forceinline__ void prolong_node(const LevelT<T> &C, const LevelT<T> &F, int i, int j) {
-  const size_t kf = (size_t)j * F.P + i;
+  const size_t kf = cidx(F.P, i, j);  // corrections in the colour-split layout
   int J0, J1;
   T w0, w1;
   if (j & 1) { J0 = (j - 1) >> 1; J1 = J0 + 1; w1 = F.wz[j]; w0 = T(1) - w1; }
@@ -1033,8 +1040,8 @@ __device__ __forceinline__ void prolong_node(const LevelT<T> &C, const LevelT<T>
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const T *c = C.du[q];
-    const T a = v0 * c[(size_t)J0 * C.P + I0] + v1 * c[(size_t)J0 * C.P + I1];
-    const T b = v0 * c[(size_t)J1 * C.P + I0] + v1 * c[(size_t)J1 * C.P + I1];
+    const T a = v0 * c[cidx(C.P, I0, J0)] + v1 * c[cidx(C.P, I1, J0)];
+    const T b = v0 * c[cidx(C.P, I0, J1)] + v1 * c[cidx(C.P, I1, J1)];
     F.du[q][kf] += w0 * a + w1 * b;
   }
 }
@@ -1376,7 +1383,7 @@ __device__ __forceinline__ void coarse_solve_block(const LevelT<T> &L, const dou
     const int node = q / 3, fld = q % 3;
     const int j = node / L.ni + 1, i = node % L.ni;
     const double sc = fld == NV ? 1.0 : 1.0 / nscale;
-    L.du[fld][(size_t)j * L.P + i] = (T)(cs[q] * x * sc);
+    L.du[fld][cidx(L.P, i, j)] = (T)(cs[q] * x * sc);
   }
 }
 
@@ -1620,8 +1627,8 @@ __global__ void k_update(Level L, StateView sv, double *partials, unsigned *coun
   const int j = blockIdx.y * BY + threadIdx.y + 1;
   double acc[2] = {0.0, 0.0};
   if (i < L.ni && j < L.nz) {
-    const size_t k = (size_t)j * L.P + i;
-    const double a = L.du[NE][k], b = L.du[NP][k], c = L.du[NV][k];
+    const size_t k = (size_t)j * L.P + i, kd = cidx(L.P, i, j);
+    const double a = L.du[NE][kd], b = L.du[NP][kd], c = L.du[NV][kd];
     sv.u[NE][k] += a; sv.u[NP][k] += b; sv.u[NV][k] += c;
     acc[0] = fabs(c);
     acc[1] = (isfinite(a) && isfinite(b) && isfinite(c)) ? 0.0 : 1.0;
@@ -1664,16 +1671,16 @@ template <typename T>
 __global__ void k_zero_du(LevelT<T> L) {
   pdl_launch_dependents();
   pdl_wait();
-  const int i = blockIdx.x * BX + threadIdx.x;
+  const int i = blockIdx.x * BX + threadIdx.x;  // every slot of the row (colour-split layout)
   const int j = blockIdx.y * BY + threadIdx.y;
-  if (i > L.nr || j > L.nz) return;
+  if (i >= L.P || j > L.nz) return;
   const size_t k = (size_t)j * L.P + i;
   L.du[NE][k] = T(0); L.du[NP][k] = T(0); L.du[NV][k] = T(0);
 }
 
 template <typename T>
 cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st) {
-  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
+  dim3 b(BX, BY), g((L.P + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
   const cudaError_t e = launch_k((L.pdl & PDL_OTHER) != 0, k_zero_du<T>, g, b, 0, st, L);
   count_launch();
   return e;
@@ -1691,7 +1698,7 @@ __global__ void k_mixed_update(Level L, LevelT<float> M, double n0) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y + 1;
   if (i >= L.ni || j >= L.nz) return;
-  const size_t k = (size_t)j * L.P + i;
+  const size_t k = cidx(L.P, i, j);
   L.du[NE][k] += n0 * (double)M.du[NE][k];
   L.du[NP][k] += n0 * (double)M.du[NP][k];
   L.du[NV][k] += (double)M.du[NV][k];
@@ -1704,20 +1711,38 @@ cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n
   return e;
 }
 
-// Right-hand sides given in the natural row layout (pitch P) -> the colour-split layout of f,
-// rows 1 .. nz-1.
+// Vectors given in the natural row layout (pitch P) -> the colour-split layout of f and du,
+// rows 1 .. nz-1; columns i >= ni (a Dirichlet wall) get zero.
 __global__ void k_split_rows(Level L, const double *i0, const double *i1, const double *i2, double *o0,
                              double *o1, double *o2) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y + 1;
   if (i > L.nr || j >= L.nz) return;
   const size_t k = (size_t)j * L.P + i, kf = cidx(L.P, i, j);
-  o0[kf] = i0[k]; o1[kf] = i1[k]; o2[kf] = i2[k];
+  const bool in = i < L.ni;
+  o0[kf] = in ? i0[k] : 0.0; o1[kf] = in ? i1[k] : 0.0; o2[kf] = in ? i2[k] : 0.0;
 }
 
 cudaError_t launch_split_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st) {
   dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz - 1 + BY - 1) / BY);
   k_split_rows<<<g, b, 0, st>>>(L, in[0], in[1], in[2], out[0], out[1], out[2]);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// The colour-split layout -> natural rows, every row 0 .. nz.
+__global__ void k_join_rows(Level L, const double *i0, const double *i1, const double *i2, double *o0, double *o1,
+                            double *o2) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.nr || j > L.nz) return;
+  const size_t k = (size_t)j * L.P + i, kf = cidx(L.P, i, j);
+  o0[k] = i0[kf]; o1[k] = i1[kf]; o2[k] = i2[kf];
+}
+
+cudaError_t launch_join_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st) {
+  dim3 b(BX, BY), g((L.nr + 1 + BX - 1) / BX, (L.nz + 1 + BY - 1) / BY);
+  k_join_rows<<<g, b, 0, st>>>(L, in[0], in[1], in[2], out[0], out[1], out[2]);
   count_launch();
   return cudaGetLastError();
 }
