@@ -37,8 +37,10 @@ TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20
 
 
-# DRAM bytes read + written by one k_smooth<double> half sweep at 1025^2 in an ncu capture
-TRAFFIC_K_SMOOTH_FP64_1025 = 242450176
+# DRAM bytes read + written by one half sweep at 1025^2 in an ncu capture (cold caches):
+# k_smooth<double> (profiles/k_smooth_fp64_1025.md), k_smooth<float> (k_smooth_fp32_1025_mixed.md)
+TRAFFIC_K_SMOOTH_FP64_1025 = 182969344
+TRAFFIC_K_SMOOTH_FP32_1025 = 90871296
 
 
 def _vcycle_1025(precision, peaks):
@@ -74,7 +76,7 @@ def _vcycle_1025(precision, peaks):
     name = ("k_sweep" if fused else "k_smooth") + ("<double>" if fp64 else "<float>")
     # ncu DRAM read + write per launch, cold caches (profiles/k_smooth_fp32_1025_mixed.md,
     # profiles/k_smooth_fp64_1025.md)
-    traffic = None if fused else (117228672 if not fp64 else TRAFFIC_K_SMOOTH_FP64_1025)
+    traffic = None if fused else (TRAFFIC_K_SMOOTH_FP32_1025 if not fp64 else TRAFFIC_K_SMOOTH_FP64_1025)
     roof = {"bound": "hbm", "kernel": name + (" (fused red-black sweep" if fused else " (red-black half sweep")
             + ", 1025x1025 level)", "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6, "algorithmic_bytes_per_launch": byt,
@@ -366,7 +368,7 @@ def run_ours(args):
     # DRAM bytes read + written per launch in one ncu capture of the kernel (cold caches): the
     # half sweeps of the 257^2 level (k_smooth, profiles/k_smooth_fp64_257.md) and of the 129^2
     # level (k_smooth_ilp, profiles/smoother_fp64_129.md); the other levels have no capture
-    traffic_ncu = {(256, False): 14348288, (128, False): 3639552}
+    traffic_ncu = {(256, False): 11266560, (128, False): 2949632}
     levels = []
     for lev, (n_l, ms_l) in enumerate(smooth_prof):
         if not n_l:
