@@ -1374,7 +1374,9 @@ __device__ __forceinline__ void coarse_solve_block(const LevelT<T> &L, const dou
     const int node = q / 3, fld = q % 3;
     const int j = node / L.ni + 1, i = node % L.ni;
     const double sc = fld == NV ? 1.0 : nscale;
-    fs[q] = rs[q] * sc * (double)L.f[fld][cidx(L.P, i, j)];
+    // the field's array chosen by selects, not by a runtime index into the view
+    const T *fp = fld == NE ? L.f[NE] : (fld == NP ? L.f[NP] : L.f[NV]);
+    fs[q] = rs[q] * sc * (double)fp[cidx(L.P, i, j)];
   }
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += nthreads) {
@@ -1383,7 +1385,8 @@ __device__ __forceinline__ void coarse_solve_block(const LevelT<T> &L, const dou
     const int node = q / 3, fld = q % 3;
     const int j = node / L.ni + 1, i = node % L.ni;
     const double sc = fld == NV ? 1.0 : 1.0 / nscale;
-    L.du[fld][cidx(L.P, i, j)] = (T)(cs[q] * x * sc);
+    T *dp = fld == NE ? L.du[NE] : (fld == NP ? L.du[NP] : L.du[NV]);
+    dp[cidx(L.P, i, j)] = (T)(cs[q] * x * sc);
   }
 }
 
@@ -1468,26 +1471,48 @@ size_t coarse_smem_bytes(const CoarseSet<T> &S) {
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *__restrict__ sp) {
   extern __shared__ __align__(16) unsigned char cc_smem[];
-  __shared__ LevelT<T> lv[kMaxCoarseSet];
+  // per level: offset of its block of kCoarseFields arrays in cc_smem (elements), array length,
+  // sizes; the views below derive every array pointer from cc_smem itself, so the compiler
+  // addresses them as shared memory (no pointer loads, no generic loads)
+  __shared__ int s_off[kMaxCoarseSet], s_len[kMaxCoarseSet], s_nr[kMaxCoarseSet], s_nz[kMaxCoarseSet],
+      s_P[kMaxCoarseSet], s_ni[kMaxCoarseSet];
+  __shared__ const T *s_wz[kMaxCoarseSet];
+  // the coarsest level's dense inverse and scalings when they fit (constant per Newton iteration)
+  constexpr int kInvMax = 27;
+  __shared__ double s_minv[kInvMax * kInvMax], s_rs[kInvMax], s_cs[kInvMax];
   const CoarseSet<T> &G = *sp;
   const int tid = threadIdx.x, nth = blockDim.x;
   pdl_launch_dependents();
   if (tid == 0) {
-    T *p = reinterpret_cast<T *>(cc_smem);
+    int off = 0;
     for (int q = 0; q < G.n; ++q) {
-      LevelT<T> v = G.lv[q];
-      const size_t nodes = (size_t)(v.nz + 1) * v.P;
-      auto take = [&]() { T *r = p; p += nodes; return r; };
-      for (int a = 0; a < NCOEF; ++a) v.cr[a] = take();
-      for (int a = 0; a < NCOEF; ++a) v.cz[a] = take();
-      for (int a = 0; a < NFAC; ++a) v.fac[a] = take();
-      for (int a = 0; a < NDIA; ++a) v.dia[a] = take();
-      v.gR = take(); v.gZ = take(); v.Ak = take();
-      for (int a = 0; a < 3; ++a) { v.du[a] = take(); v.f[a] = take(); v.r[a] = take(); v.du2[a] = nullptr; }
-      lv[q] = v;
+      const LevelT<T> &g = G.lv[q];
+      const int len = (g.nz + 1) * g.P;
+      s_off[q] = off; s_len[q] = len; s_nr[q] = g.nr; s_nz[q] = g.nz; s_P[q] = g.P; s_ni[q] = g.ni;
+      s_wz[q] = g.wz;
+      off += kCoarseFields * len;
     }
   }
   __syncthreads();
+  auto view = [&](int q) {
+    LevelT<T> v = {};
+    v.nr = s_nr[q]; v.nz = s_nz[q]; v.P = s_P[q]; v.ni = s_ni[q]; v.wz = s_wz[q];
+    T *b = reinterpret_cast<T *>(cc_smem) + s_off[q];
+    const int n = s_len[q];
+#pragma unroll
+    for (int a = 0; a < NCOEF; ++a) { v.cr[a] = b + a * n; v.cz[a] = b + (NCOEF + a) * n; }
+#pragma unroll
+    for (int a = 0; a < NFAC; ++a) v.fac[a] = b + (2 * NCOEF + a) * n;
+#pragma unroll
+    for (int a = 0; a < NDIA; ++a) v.dia[a] = b + (2 * NCOEF + NFAC + a) * n;
+    constexpr int g0 = 2 * NCOEF + NFAC + NDIA;
+    v.gR = b + g0 * n; v.gZ = b + (g0 + 1) * n; v.Ak = b + (g0 + 2) * n;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      v.du[a] = b + (g0 + 3 + 3 * a) * n; v.f[a] = b + (g0 + 4 + 3 * a) * n; v.r[a] = b + (g0 + 5 + 3 * a) * n;
+    }
+    return v;
+  };
   // copy-in with asynchronous 16-byte copies (every array is a multiple of 16 bytes long and
   // 16-byte aligned at both ends), all issued before one wait: the operator arrays (constant
   // during a linear solve) before waiting for the previous kernel, corrections and right-hand
@@ -1502,21 +1527,32 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
   auto chunks_of = [&](const LevelT<T> &g) { return (int)((size_t)(g.nz + 1) * g.P * sizeof(T) / 16); };
   for (int q = 0; q < G.n; ++q) {
     const LevelT<T> &g = G.lv[q];
-    const LevelT<T> &v = lv[q];
+    const LevelT<T> v = view(q);
     const int ch = chunks_of(g);
+#pragma unroll
     for (int a = 0; a < NCOEF; ++a) { copy(v.cr[a], g.cr[a], ch); copy(v.cz[a], g.cz[a], ch); }
+#pragma unroll
     for (int a = 0; a < NFAC; ++a) copy(v.fac[a], g.fac[a], ch);
+#pragma unroll
     for (int a = 0; a < NDIA; ++a) copy(v.dia[a], g.dia[a], ch);
     copy(v.gR, g.gR, ch); copy(v.gZ, g.gZ, ch); copy(v.Ak, g.Ak, ch);
+  }
+  const LevelT<T> &gc = G.lv[G.n - 1];
+  const int nc = 3 * gc.ni * (gc.nz - 1);   // unknowns of the coarsest level
+  const bool inv_smem = nc <= kInvMax;
+  if (inv_smem) {
+    for (int e = tid; e < nc * nc; e += nth) s_minv[e] = G.Minv[e];
+    for (int e = tid; e < nc; e += nth) { s_rs[e] = G.rs[e]; s_cs[e] = G.cs[e]; }
   }
   pdl_wait();
   for (int q = 0; q < G.n; ++q) {
     const LevelT<T> &g = G.lv[q];
-    const LevelT<T> &v = lv[q];
+    const LevelT<T> v = view(q);
     const int ch = chunks_of(g);
     // the first level's correction is the current iterate when the set's first level is the
     // root of the solve; the coarser ones are overwritten by the restriction except for their
     // (zero) electrode rows
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (q == 0) copy(v.f[a], g.f[a], ch);
       copy(v.du[a], g.du[a], ch);
@@ -1538,8 +1574,8 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
       }
   };
   for (int q = 0; q + 1 < G.n; ++q) {
-    const LevelT<T> &L = lv[q];
-    const LevelT<T> &C = lv[q + 1];
+    const LevelT<T> L = view(q);
+    const LevelT<T> C = view(q + 1);
     sweeps(L, G.nu1[q]);
     const int W = L.ni;
     for (int t = tid; t < (L.nz - 1) * W; t += nth) {
@@ -1551,20 +1587,27 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle_smem(const CoarseSet<T> *
     for (int t = tid; t < (C.nz - 1) * Wc; t += nth) restrict_node<T>(L, C, t % Wc, t / Wc + 1);
     __syncthreads();
   }
-  coarse_solve_block<T>(lv[G.n - 1], G.Minv, G.rs, G.cs, G.nscale, nth);
+  {
+    const LevelT<T> Lc = view(G.n - 1);
+    if (inv_smem) coarse_solve_block<T>(Lc, s_minv, s_rs, s_cs, G.nscale, nth);
+    else coarse_solve_block<T>(Lc, G.Minv, G.rs, G.cs, G.nscale, nth);
+  }
   __syncthreads();
   for (int q = G.n - 2; q >= 0; --q) {
-    const LevelT<T> &F = lv[q];
+    const LevelT<T> F = view(q);
+    const LevelT<T> C = view(q + 1);
     const int W = F.ni;
-    for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(lv[q + 1], F, t % W, t / W + 1);
+    for (int t = tid; t < (F.nz - 1) * W; t += nth) prolong_node<T>(C, F, t % W, t / W + 1);
     __syncthreads();
     sweeps(F, G.nu2[q]);
   }
   {
     const LevelT<T> &g = G.lv[0];
+    const LevelT<T> v = view(0);
     const int nodes = (g.nz + 1) * g.P;
+#pragma unroll
     for (int a = 0; a < 3; ++a)
-      for (int e = tid; e < nodes; e += nth) g.du[a][e] = lv[0].du[a][e];
+      for (int e = tid; e < nodes; e += nth) g.du[a][e] = v.du[a][e];
   }
 }
 
