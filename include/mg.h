@@ -290,6 +290,19 @@ int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms);
  * FP64 path.  Returns a negative value on a CUDA error. */
 double mg_probe_fp64_gflops(void *stream);
 
+/* Smoother timing as the V-cycle graphs run it: `sweeps` red-black sweeps of level `level`
+ * (0 = finest, below the last level) in the precision view `precision` (0 FP64, 1 the FP32
+ * view of the mixed form), issued exactly as a V-cycle issues them (the level's launch shape,
+ * half or fused sweeps, programmatic dependent launch), are captured into one CUDA graph on
+ * the state's stream and replayed twice; the second replay is timed with CUDA events.
+ * *us_per_launch receives its device time divided by the number of launches,
+ * *launches_per_sweep (may be NULL) 2 for half sweeps, 1 for fused ones.  Only the level's
+ * correction buffers are written, and they are zeroed afterwards; the solution state is not
+ * touched.  Synchronises the stream.  MG_EINVAL on a bad level, precision (1 needs the mixed
+ * form) or sweep count (1 .. 4096); MG_ECUDA on a CUDA error. */
+int mg_time_smoother(mg_state *s, int level, int precision, int sweeps, double *us_per_launch,
+                     int *launches_per_sweep);
+
 /* Allocation-free residual norms.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory (code running inside another framework's memory
  * pool, real-time loops where cudaMalloc is forbidden or would synchronise the device, plug-ins

@@ -1313,6 +1313,51 @@ int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms) {
 
 double mg_probe_fp64_gflops(void *stream) { return probe_fp64_gflops((cudaStream_t)stream); }
 
+int mg_time_smoother(mg_state *s, int level, int precision, int sweeps, double *us_per_launch,
+                     int *launches_per_sweep) {
+  if (!s || !us_per_launch || level < 0 || level >= s->nlev - 1 || (precision != 0 && precision != 1) ||
+      (precision == 1 && !mixed(s)) || sweeps < 1 || sweeps > 4096)
+    return fail(s, MG_EINVAL, "mg_time_smoother: bad level, precision or sweep count");
+  cudaStream_t st = s->stream, cs = s->cap_stream;
+  // the sweeps, as a V-cycle issues them, captured into one graph on the private capture
+  // stream and replayed on the state's stream; only the level's correction buffers are
+  // written, and they are zeroed afterwards
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaStreamSynchronize(st));
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  set_capturing(true);
+  const int rc = precision == 0 ? smooth_sweeps<double>(s, level, sweeps, cs) : smooth_sweeps<float>(s, level, sweeps, cs);
+  const int64_t launches = captured_launches();
+  set_capturing(false);
+  const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+  if (rc != MG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+  CK(ec);
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float ms = 0.f;
+  e = cudaGraphLaunch(exec, st);                 // warm-up replay
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(exec);
+  CK(e);
+  if (precision == 0) CK(launch_zero_du<double>(s->lv[level].L, st));
+  else CK(launch_zero_du<float>(s->lv[level].M, st));
+  CK(cudaStreamSynchronize(st));
+  *us_per_launch = launches > 0 ? 1000.0 * ms / (double)launches : 0.0;
+  if (launches_per_sweep) *launches_per_sweep = (int)(launches / sweeps);
+  return MG_OK;
+}
+
 
 int mg_autotune(mg_state *s, int32_t *shapes_out) {
   if (!s) return MG_EINVAL;

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mg_profile_begin": (_i, [_vp, _i, _i]),
     "mg_profile_end": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "mg_probe_fp64_gflops": (ctypes.c_double, [_vp]),
+    "mg_time_smoother": (_i, [_vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "mg_solve_steady_batch": (_i, [ctypes.POINTER(_vp), _i, _d, _i, _vp, _vp]),
     "mg_autotune": (_i, [_vp, _vp]),
     "mg_solve_steady_guess": (_i, [_vp, _vp, _vp, _vp, _i, _d, ctypes.POINTER(mg_stats), ctypes.POINTER(_i)]),
@@ -314,6 +315,15 @@ class Solver:
         out = np.zeros(6 * n, dtype=np.int32)
         self._check(self.lib.mg_autotune(self.h, out.ctypes.data))
         return out.reshape(n, 6)
+
+    def time_smoother(self, level: int, precision: int = 0, sweeps: int = 200):
+        """(device us per smoother launch, launches per sweep) with the level's sweeps replayed
+        from a captured graph (see mg_time_smoother in include/mg.h)."""
+        us = ctypes.c_double(0.0)
+        lps = ctypes.c_int(0)
+        self._check(self.lib.mg_time_smoother(self.h, int(level), int(precision), int(sweeps), ctypes.byref(us),
+                                              ctypes.byref(lps)))
+        return us.value, lps.value
 
     def profile_begin(self, kernel: int, level: int = 0):
         self._check(self.lib.mg_profile_begin(self.h, int(kernel), int(level)))

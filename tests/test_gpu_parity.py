@@ -5,6 +5,8 @@ tolerances: residual rows and Jacobian products agree to 1e-12 of the row
 scale (rounding order only); linear and Newton solves to 1e-10 relative
 max-norm per field (both sides solved to 1e-12 or tighter).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -263,6 +265,37 @@ def test_invalid_arguments_are_rejected(mg):
     zz = torch.zeros((33, 33), dtype=torch.float64, device="cuda")
     with pytest.raises(mg.MGError):
         mg.residual_noalloc(32, 32, 1e-2, z, p, [zz, zz, zz], None, [zz, zz], 0.0)
+
+
+def test_time_smoother(mg):
+    """mg_time_smoother: a positive device time per launch, two launches per sweep for half
+    sweeps, the state untouched, a linear solve afterwards unchanged bit for bit; bad
+    arguments rejected."""
+    d = W.make_discharge(64, seed=0, V_cathode=-300.0)
+    s = mg.from_discharge(d, precision=mg.MG_MIXED)
+    F, _ = s.residual(1e-9)
+    f = [-a for a in F]
+    xa, ha, _ = s.linear_solve(1e-9, f, 0.0, 3)
+    before = s.get_state()
+    for prec in (0, 1):
+        us, lps = s.time_smoother(0, prec, 20)
+        assert us > 0.0 and lps in (1, 2)
+    s.set_smoother(1, 0, 32, 1, 0, 0)
+    us, lps = s.time_smoother(1, 0, 5)
+    assert us > 0.0 and lps == 2
+    after = s.get_state()
+    for q in range(3):
+        assert np.array_equal(before[q], after[q])
+    xb, hb, _ = s.linear_solve(1e-9, f, 0.0, 3)
+    assert np.array_equal(ha, hb)
+    for q in range(3):
+        assert np.array_equal(xa[q], xb[q])
+    us = ctypes.c_double(0.0)
+    nl = s.lib.mg_num_levels(s.h)
+    for args in ((nl - 1, 0, 10), (-1, 0, 10), (0, 2, 10), (0, 0, 0), (0, 0, 5000)):
+        assert s.lib.mg_time_smoother(s.h, *args, ctypes.byref(us), None) == mg.MG_EINVAL, args
+    s64 = mg.from_discharge(d)
+    assert s64.lib.mg_time_smoother(s64.h, 0, 1, 10, ctypes.byref(us), None) == mg.MG_EINVAL
 
 
 def test_rejected_step_leaves_state_unchanged(mg):
