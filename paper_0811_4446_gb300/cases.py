@@ -2,6 +2,7 @@
 
     python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager] [--autotune] [--half]
     python -m paper_0811_4446_gb300.cases unet B N [REPS] [--mma]
+    python -m paper_0811_4446_gb300.cases steady [--mixed] [--eager]
 
 builds the N x N-node discharge of the benchmark family (table transport for N = 256),
 evaluates the Newton residual at the initial state and runs CYCLES multigrid V-cycles
@@ -14,6 +15,11 @@ sweep, two per half-sweep pair, as the autotuner chose for the level), finest le
 benchmark does (its timing launches come before the V-cycles).  The linear solve (its
 residual, hierarchy set-up and V-cycles) runs inside the NVTX range "measure".  --half
 smooths with two half-sweep launches per sweep on every level (no fused sweeps).
+
+steady: one steady solve of the benchmark's 257 x 257 workload (129 -> 257 continuation,
+table transport, rho <= 1e-8) after one untimed solve, autotuned as the benchmark does, inside
+the NVTX range "measure"; --eager launches every kernel from the host (no graphs), so that a
+kernel profiler sees each launch of the solve.
 
 unet: REPS (default 2) forward passes plus one training step of the learned-guess network
 on a batch of B random (N+1) x (N+1) inputs; --mma selects the mma.sync convolutions instead
@@ -49,6 +55,33 @@ def vcycles(n: int, cycles: int = 3, mixed: bool = False, eager: bool = False, a
     return float(hist[-1])
 
 
+def steady(mixed: bool = False, eager: bool = False) -> float:
+    import numpy as np
+    import torch
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import workloads as W
+    from . import mg
+
+    d = W.steady_257()
+    s = mg.from_discharge(d, precision=mg.MG_MIXED if mixed else mg.MG_FP64, use_graphs=0 if eager else 1)
+    s.autotune()
+    ins = [np.ascontiguousarray(a) for a in (d.ne0, d.np0, d.V0)]
+    s.set_state(*ins)
+    s.solve_steady(1e-8)
+    s.set_state(*ins)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("measure")
+    rc, st = s.solve_steady(1e-8)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if rc != mg.MG_OK:
+        raise RuntimeError(f"steady solve failed: {rc}")
+    return float(st["steady_rho"])
+
+
 def unet_case(B: int, n: int, reps: int = 2, mma: bool = False) -> float:
     import numpy as np
     import torch
@@ -72,6 +105,9 @@ if __name__ == "__main__":
     if len(sys.argv) >= 4 and sys.argv[1] == "unet":
         R = int(sys.argv[4]) if len(sys.argv) > 4 and not sys.argv[4].startswith("--") else 2
         print("ok", unet_case(int(sys.argv[2]), int(sys.argv[3]), R, "--mma" in sys.argv))
+        sys.exit(0)
+    if len(sys.argv) >= 2 and sys.argv[1] == "steady":
+        print("ok", steady("--mixed" in sys.argv, "--eager" in sys.argv))
         sys.exit(0)
     if len(sys.argv) < 3 or sys.argv[1] != "vcycles":
         print(__doc__)
