@@ -202,6 +202,52 @@ def test_steady_257_full_size_residual_property(mg):
     assert np.all(np.isfinite(ug))
 
 
+def test_transient_1025_full_size(mg):
+    """1025 x 1025 (the mixed-precision workload at full size), autotuned as the benchmark runs
+    it: one backward-Euler step of 1 ns in FP64 and in the mixed form.  The oracle's residual of
+    each result meets the step tolerance, and the two results agree to 1e-8 relative per field."""
+    d = W.transient_1025()
+    g, phys = _oracle(d)
+    u0 = np.stack([d.ne0, d.np0, d.V0])
+    out = []
+    for prec in (mg.MG_FP64, mg.MG_MIXED):
+        s = mg.from_discharge(d, precision=prec)
+        s.autotune()
+        rc, st = s.step(1e-9, 1e-10)
+        assert rc == mg.MG_OK, st
+        ug = np.stack(s.get_state())
+        assert np.all(np.isfinite(ug))
+        F, T = disc.residual(g, ug, u0, d.S_e, d.S_p, 1e-9, phys, with_terms=True)
+        assert disc.rho(F, T).max() <= 1.05e-10, (prec, disc.rho(F, T))
+        out.append(ug)
+        s.close()
+    for q in range(3):
+        assert np.abs(out[0][q] - out[1][q]).max() <= 1e-8 * np.abs(out[0][q]).max(), q
+
+
+def test_batched_full_sizes_residual_property(mg):
+    """The batched form at its full instance sizes (one instance of each of 65^2, 129^2, 257^2
+    and 513^2 from the 64-discharge workload), autotuned: the oracle's steady residual of every
+    result."""
+    ds = W.batch_64()
+    pick, seen = [], set()
+    for d in ds:
+        if d.nr not in seen:
+            seen.add(d.nr)
+            pick.append(d)
+    assert sorted(seen) == [64, 128, 256, 512]
+    solvers = [mg.from_discharge(d, precision=mg.MG_MIXED, stream=torch.cuda.Stream()) for d in pick]
+    for sv in solvers:
+        sv.autotune()
+    rc, ms, rcs = mg.solve_steady_batch(solvers, 1e-8, workers=4)
+    assert rc == mg.MG_OK, rcs
+    for d, sv in zip(pick, solvers):
+        g, phys = _oracle(d)
+        ug = np.stack(sv.get_state())
+        F, T = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
+        assert disc.rho(F, T).max() <= 1.05e-8, (d.nr, disc.rho(F, T))
+
+
 def test_device_and_host_io_agree(mg):
     d = W.make_discharge(32, seed=2)
     s = mg.from_discharge(d)
