@@ -187,8 +187,11 @@ def run_reference(args):
         oracle_estimate(sample_vcycles=1)
     ests, samples = [], []
     detail = counts = None
+    # each step is one bounded sample; with many steps the sample shrinks to one V-cycle per
+    # grid so that the whole run stays within a few minutes
+    nv = args.ref_vcycles if args.steps <= 5 else 1
     for _ in range(args.steps):
-        est, sample_s, detail, counts = oracle_estimate(sample_vcycles=args.ref_vcycles)
+        est, sample_s, detail, counts = oracle_estimate(sample_vcycles=nv)
         ests.append(est)
         samples.append(sample_s)
     ms = 1000.0 * sum(ests) / len(ests)
@@ -200,7 +203,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "n/a (host CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": (f"per step: oracle residual, Jacobian hierarchy and {args.ref_vcycles} "
+                         "sample": (f"per step: oracle residual, Jacobian hierarchy and {nv} "
                                     f"V-cycles timed on 129^2 and 257^2 ({statistics.mean(samples):.1f} s of CPU), "
                                     "scaled by the oracle's own counts for the full continuation "
                                     f"({counts['levels']})"),
@@ -456,23 +459,37 @@ def measure_forms(args, dev, peaks):
     import workloads as W
     from paper_0811_4446_gb300 import mg
     out = {}
-    # mixed-precision steady solve of the same 257^2 workload
     d = W.steady_257()
+    ins = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (d.ne0, d.np0, d.V0)]
+
+    def timed_steady(s, what):
+        times = []
+        for k in range(4):
+            s.set_state(*ins)
+            s.reset_stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = s.solve_steady(TOL)
+            torch.cuda.synchronize()
+            if rc != mg.MG_OK:
+                raise RuntimeError(what + " steady solve failed")
+            if k > 0:
+                times.append(time.perf_counter() - t0)
+        return times, st
+
+    # the same FP64 schedule with every step solved to 0.1 x the steady tolerance (no relative
+    # per-step tolerance): the stricter reading of the per-step Newton stop
+    s = mg.from_discharge(d, newton_tol_rel=0.0)
+    s.autotune()
+    times, st = timed_steady(s, "strict-step")
+    out["strict_steps_257"] = {"solves_per_s": 1.0 / statistics.median(times), "ms": 1000 * statistics.median(times),
+                               "steps": st["steps_accepted"] + st["steps_rejected"], "newton": st["newton_iterations"],
+                               "vcycles": st["vcycles"]}
+    s.close()
+    # mixed-precision steady solve of the same 257^2 workload
     s = mg.from_discharge(d, precision=mg.MG_MIXED)
     s.autotune()
-    ins = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (d.ne0, d.np0, d.V0)]
-    times = []
-    for k in range(4):
-        s.set_state(*ins)
-        s.reset_stats()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, st = s.solve_steady(TOL)
-        torch.cuda.synchronize()
-        if rc != mg.MG_OK:
-            raise RuntimeError("mixed steady solve failed")
-        if k > 0:
-            times.append(time.perf_counter() - t0)
+    times, st = timed_steady(s, "mixed")
     out["mixed_steady_257"] = {"solves_per_s": 1.0 / statistics.median(times), "ms": 1000 * statistics.median(times),
                                "vcycles": st["vcycles"], "newton": st["newton_iterations"]}
     s.close()
@@ -663,7 +680,7 @@ def measure_unet(dev, peaks, B: int = 16, reps: int = 10):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-vcycles", type=int, default=40)

@@ -123,6 +123,10 @@ typedef struct mg_params {
   int32_t wall_dirichlet; /* 0: zero normal flux and dV/dr = 0 on the wall r = R (half-cell rows);
                              1: the argon case of Sec. 3: n_e = n_p = 0 and V linear in z between
                              the electrodes on the wall, which then carries no unknowns */
+  double newton_tol_rel;  /* > 0: a march step's Newton tolerance is max(the per-step tolerance,
+                             newton_tol_rel x the steady residual at the step's start): steps far
+                             from the steady state are solved only as far as they can matter for
+                             it (0: off; 0 <= newton_tol_rel < 1) */
 } mg_params;
 
 /* Per-call statistics. */
@@ -151,7 +155,8 @@ typedef struct mg_state mg_state;
  * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1, nu_coarse_n = 64,
  * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels
  * larger than 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down),
- * chain_from = 1 (the two-level 129^2 -> 257^2 continuation), pdl = 9 (smoothers and the coarse-cycle kernel), wall_dirichlet = 0.
+ * chain_from = 1 (the two-level 129^2 -> 257^2 continuation), pdl = 9 (smoothers and the coarse-cycle kernel), wall_dirichlet = 0,
+ * newton_tol_rel = 0.1.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on

@@ -50,6 +50,8 @@ class SolverOptions:
     dt_max: float = 1e-6
     max_steps: int = 400
     newton_tol: Optional[float] = None   # per-step Newton tolerance; default 0.1 * steady tol
+    newton_tol_rel: float = 0.1     # > 0: a step's tolerance is max(newton_tol, this x the steady
+                                    # residual at the step's start); 0: every step to newton_tol
     eta_adapt: bool = True          # relax eta when the Newton residual is near its target
 
 
@@ -116,11 +118,15 @@ def march(g: Grid, u, S_e, S_p, phys, tol, opt: SolverOptions, dt_start: float, 
     dt_prev = None
     records = []
     newton_tol = 0.1 * tol if opt.newton_tol is None else opt.newton_tol
+    # Sec. 2: the time accuracy of the march does not matter for the steady state, so a step may
+    # be solved only to a fraction of the steady residual it starts from
+    r_start = steady_rho(g, u, S_e, S_p, phys).max() if opt.newton_tol_rel > 0 else 0.0
     for _ in range(opt.max_steps):
-        u_new, st = step(g, u, S_e, S_p, dt, phys, newton_tol, opt)
+        u_new, st = step(g, u, S_e, S_p, dt, phys, max(newton_tol, opt.newton_tol_rel * r_start), opt)
         if st.accepted:
             u = u_new
             rs = steady_rho(g, u, S_e, S_p, phys)
+            r_start = rs.max()
             records.append((dt, True, st.newton, sum(st.vcycles), rs.max()))
             if log:
                 log(records[-1])

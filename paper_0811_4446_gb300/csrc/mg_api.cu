@@ -689,14 +689,27 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
   return reason;
 }
 
-// March on level l0 with the Delta-t ramp until the steady residual <= tol.
+// March on level l0 with the Delta-t ramp until the steady residual <= tol.  Each step is
+// solved to the per-step tolerance (default 0.1 tol: a step's residual measure includes the
+// time-derivative terms, the steady one does not) or, with newton_tol_rel > 0, to
+// newton_tol_rel x the steady residual at the step's start when that is larger.
 int march(mg_state *s, int l0, double dt_start, double tol) {
   double dt = dt_start, dt_prev = -1.0;
   const double ntol = s->prm.newton_tol > 0.0 ? s->prm.newton_tol : 0.1 * tol;
+  const double rel = s->prm.newton_tol_rel;
   bool coef_current = false;  // face coefficients of level l0 at the current state
+  double r_start = 0.0;       // steady residual of the current state (used when rel > 0)
+  if (rel > 0.0) {
+    double rho[3];
+    const int rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr, true);
+    if (rc) return rc;
+    coef_current = true;
+    r_start = std::max(rho[0], std::max(rho[1], rho[2]));
+  }
   for (int n = 0; n < s->prm.max_steps; ++n) {
     int newton = 0;
-    int rc = step(s, l0, dt, ntol, &newton, coef_current);
+    const double step_tol = std::max(ntol, rel * r_start);
+    int rc = step(s, l0, dt, step_tol, &newton, coef_current);
     coef_current = false;
     if (rc == MG_ECUDA) return rc;
     s->stats.dt_last = dt;
@@ -711,6 +724,7 @@ int march(mg_state *s, int l0, double dt_start, double tol) {
       coef_current = true;
       const double r = std::max(rho[0], std::max(rho[1], rho[2]));
       s->stats.steady_rho = r;
+      r_start = r;
       if (r <= tol) return MG_OK;
       dt_prev = dt;
       dt = std::min(dt * s->prm.dt_growth, s->prm.dt_max);
@@ -838,6 +852,7 @@ void mg_params_default(mg_params *p) {
   p->chain_from = 1;
   p->pdl = PDL_SMOOTH | PDL_COARSE;
   p->wall_dirichlet = 0;
+  p->newton_tol_rel = 0.1;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
   p->coarse_kernel_threads = 512;
@@ -857,6 +872,7 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
     return MG_EINVAL;
   }
   if (p->wall_dirichlet != 0 && p->wall_dirichlet != 1) { *why = "wall_dirichlet must be 0 or 1"; return MG_EINVAL; }
+  if (!(p->newton_tol_rel >= 0.0 && p->newton_tol_rel < 1.0)) { *why = "newton_tol_rel must be in [0, 1)"; return MG_EINVAL; }
   if (p->pdl < 0 || p->pdl > PDL_ALL) { *why = "pdl: a combination of the PDL kernel-kind bits"; return MG_EINVAL; }
   if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
     *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";

@@ -46,7 +46,8 @@ class mg_params(ctypes.Structure):
                 ("coarse_kernel_threads", ctypes.c_int32), ("eta_adapt", ctypes.c_int32),
                 ("nu_coarse_n", ctypes.c_int32), ("nu_coarse1", ctypes.c_int32), ("nu_coarse2", ctypes.c_int32),
                 ("nu_tiny_n", ctypes.c_int32), ("nu_tiny1", ctypes.c_int32), ("nu_tiny2", ctypes.c_int32),
-                ("chain_from", ctypes.c_int32), ("pdl", ctypes.c_int32), ("wall_dirichlet", ctypes.c_int32)]
+                ("chain_from", ctypes.c_int32), ("pdl", ctypes.c_int32), ("wall_dirichlet", ctypes.c_int32),
+                ("newton_tol_rel", ctypes.c_double)]
 
 
 class mg_stats(ctypes.Structure):

@@ -65,4 +65,5 @@ def test_params_default_values(lib):
     assert (p.dt1, p.dt_growth, p.max_newton, p.nu1, p.nu2) == (1e-9, 5.0, 10, 4, 4)
     assert (p.nu_coarse_n, p.nu_coarse1, p.nu_coarse2, p.chain_from) == (64, 2, 2, 1)
     assert (p.nu_tiny_n, p.nu_tiny1, p.nu_tiny2, p.pdl, p.wall_dirichlet) == (8, 1, 1, 9, 0)
+    assert p.newton_tol_rel == 0.1 and p.newton_tol == 0.0
     assert np.isclose(p.mu_p, 0.15) and np.isclose(p.D_p, 0.0038)

@@ -127,16 +127,22 @@ def test_transient_33_ten_steps_parity(mg):
         assert np.abs(ug[q] - u[q]).max() <= 1e-10 * np.abs(u[q]).max(), q
 
 
-def test_steady_march_parity_small(mg):
+@pytest.mark.parametrize("rel", [0.1, 0.0])
+def test_steady_march_parity_small(mg, rel):
+    """March to the steady state, with the relative per-step Newton tolerance (default) and with
+    every step solved to 0.1 x the steady tolerance: the oracle's steps, Newton iterations and
+    state."""
     d = W.make_discharge(16, seed=1, V_cathode=-300.0, use_table=True)
     g, phys = _oracle(d)
     u = np.stack([d.ne0, d.np0, d.V0])
-    s = mg.from_discharge(d, eta=1e-10, max_vcycles=200)
+    s = mg.from_discharge(d, eta=1e-10, max_vcycles=200, newton_tol_rel=rel)
     rc, st = s.march(1e-9, 1e-10)
     assert rc == mg.MG_OK
-    uo, ok, rec = osv.march(g, u, d.S_e, d.S_p, phys, 1e-10, osv.SolverOptions(eta=1e-10, max_vcycles=200), 1e-9)
+    uo, ok, rec = osv.march(g, u, d.S_e, d.S_p, phys, 1e-10,
+                            osv.SolverOptions(eta=1e-10, max_vcycles=200, newton_tol_rel=rel), 1e-9)
     assert ok
     assert st["steps_accepted"] == sum(1 for r in rec if r[1])
+    assert st["newton_iterations"] == sum(r[2] for r in rec)
     ug = s.get_state()
     for q in range(3):
         assert np.abs(ug[q] - uo[q]).max() <= 1e-8 * np.abs(uo[q]).max(), q

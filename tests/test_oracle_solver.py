@@ -181,6 +181,45 @@ def test_chain_reaches_the_same_steady_state(dt_max):
         assert np.abs(u[q] - base[q]).max() <= 1e-6 * np.abs(base[q]).max(), q
 
 
+def test_march_step_tolerances(monkeypatch):
+    """The per-step Newton tolerance of a march: 0.1 x the steady tolerance with newton_tol_rel = 0,
+    and with newton_tol_rel = theta the larger of it and theta x the steady residual of the state
+    the step starts from (the initial state, then each accepted step's result)."""
+    d, g, phys, u0 = _steady_problem(8, seed=2)
+    tol, theta = 1e-9, 0.05
+    seen = []
+    real_step = so.step
+
+    def spy(g_, u_, Se, Sp, dt, phys_, ntol, opt_):
+        seen.append((ntol, so.steady_rho(g_, u_, Se, Sp, phys_).max()))
+        return real_step(g_, u_, Se, Sp, dt, phys_, ntol, opt_)
+
+    monkeypatch.setattr(so, "step", spy)
+    _, ok, rec = so.march(g, u0, d.S_e, d.S_p, phys, tol, so.SolverOptions(eta=1e-10, newton_tol_rel=0.0), 1e-9)
+    assert ok and len(seen) == len(rec) and all(t == 0.1 * tol for t, _ in seen)
+    seen.clear()
+    _, ok, rec = so.march(g, u0, d.S_e, d.S_p, phys, tol, so.SolverOptions(eta=1e-10, newton_tol_rel=theta), 1e-9)
+    assert ok and len(seen) == len(rec)
+    for t, r_start in seen:
+        assert t == max(0.1 * tol, theta * r_start)
+    assert seen[0][0] > 0.1 * tol    # the first steps, far from the steady state, are solved loosely
+
+
+def test_relative_step_tolerance_reaches_the_same_steady_state():
+    """Loose steps far from the steady state (newton_tol_rel) end on the same discrete steady
+    state as steps each solved to 0.1 x the steady tolerance, with fewer Newton iterations."""
+    d, g, phys, u0 = _steady_problem(16, seed=3)
+    base, ok0, rc0, rf0 = so.solve_steady(g, u0, d.S_e, d.S_p, phys, 1e-9,
+                                          so.SolverOptions(eta=1e-10, newton_tol_rel=0.0))
+    u, ok, rc, rf = so.solve_steady(g, u0, d.S_e, d.S_p, phys, 1e-9, so.SolverOptions(eta=1e-10, newton_tol_rel=0.1))
+    assert ok0 and ok
+    assert so.steady_rho(g, u, d.S_e, d.S_p, phys).max() <= 1e-9
+    for q in range(3):
+        assert np.abs(u[q] - base[q]).max() <= 1e-6 * np.abs(base[q]).max(), q
+    newton = lambda recs: sum(r[2] for r in recs)
+    assert newton(rc) + newton(rf) < newton(rc0) + newton(rf0)
+
+
 def _cathode_ion_current(g, u, phys):
     _, (mez, dez, mpz, dpz) = disc.face_transport(g, u[2], phys)
     phi = disc.sg_flux(g.gz[0], mpz[0], dpz[0], 1.0, u[1][0], u[1][1], u[2][0], u[2][1])
