@@ -196,7 +196,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
       }
     }
   }
-  s->partials_cap = 8 * max_blocks(lnr[0], lnz[0]) + 64;
+  s->partials_cap = 12 * max_blocks(lnr[0], lnz[0]) + 64;
   s->partials = c.take<double>(s->partials_cap);
   s->counter = c.take<unsigned>(4);
   s->dout = c.take<double>(16);
@@ -278,12 +278,14 @@ struct ProfScope {
 // Nonlinear residual on root level l0: launches only.  with_coef: the face coefficients are
 // (re)computed at the current state first; callers pass false only right after a residual at
 // the same state (the coefficients are also the Jacobian's, reused by build_hierarchy).  The six
-// sums of squares land in dout[0..5].
-int residual_launch(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], bool with_coef) {
+// sums of squares land in dout[0..5]; with steady_too those of the steady rows (no
+// time-derivative terms) in dout[6..11] as well.
+int residual_launch(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], bool with_coef,
+                    bool steady_too = false) {
   LevelBuf &b = s->lv[l0];
   ProfScope ps(s, MG_PROF_RESIDUAL, l0);
   if (with_coef) CK(launch_coef(b.L, b.sv, s->tr, s->stream));
-  CK(launch_resid_coef(b.L, b.sv, dt, write_f, Fout, s->partials, s->counter, s->dout, s->stream));
+  CK(launch_resid_coef(b.L, b.sv, dt, write_f, steady_too, Fout, s->partials, s->counter, s->dout, s->stream));
   return MG_OK;
 }
 
@@ -636,7 +638,10 @@ void copy_state_async(mg_state *s, int l0, bool to_old) {
 // A Newton iteration enqueues the hierarchy set-up, the device-side linear solve, the update
 // and the next residual, then waits once and reads the solve's control block, the update's
 // checks and the new residual norms together.
-int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_current = false) {
+// steady_rho (may be NULL): on acceptance after at least one Newton iteration, the steady
+// residual of the new state (from the same residual launch), else -1.
+int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_current = false,
+         double *steady_rho = nullptr) {
   LevelBuf &b = s->lv[l0];
   copy_state_async(s, l0, true);
   CK(cudaGetLastError());
@@ -644,6 +649,8 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
   int rc;
   int reason = MG_ENOCONV;
   double rho[3], tn[3];
+  if (steady_rho) *steady_rho = -1.0;
+  double rho_steady[3] = {-1.0, -1.0, -1.0};
   rc = residual(s, l0, dt, true, nullptr, rho, tn, !coef_current);
   if (rc) return rc;
   for (int it = 0; it <= s->prm.max_newton; ++it) {
@@ -651,6 +658,7 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
     const double rmax = std::max(rho[0], std::max(rho[1], rho[2]));
     if (!(rmax == rmax) || std::isinf(rmax)) { reason = MG_ENONFINITE; *newton_out = it; break; }
     if (rmax <= tol) {
+      if (steady_rho && it > 0) *steady_rho = std::max(rho_steady[0], std::max(rho_steady[1], rho_steady[2]));
       *newton_out = it;
       s->stats.newton_iterations += it;
       s->stats.last_newton = it;
@@ -669,18 +677,23 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
     if (graph) rc = linear_solve_graph_begin(s, l0, eta, s->prm.max_vcycles, w);
     else rc = linear_solve_eager(s, l0, eta, s->prm.max_vcycles, w, nullptr, &ncyc, &ok);
     if (rc) return rc;
-    // u += du (max |dV| and the non-finite flag into dout[8..9]), then the residual at the new
-    // state (into dout[0..5]); used only if the update is accepted
-    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout + 8, s->stream));
-    if ((rc = residual_launch(s, l0, dt, true, nullptr, true))) return rc;
-    rc = sync_read(s, 10);
+    // u += du (max |dV| and the non-finite flag into dout[12..13]), then the residual at the new
+    // state (into dout[0..5], its steady rows' sums into dout[6..11]); used only if the update
+    // is accepted
+    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout + 12, s->stream));
+    if ((rc = residual_launch(s, l0, dt, true, nullptr, true, true))) return rc;
+    rc = sync_read(s, 14);
     if (rc) return rc;
     if (graph) linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
     s->stats.vcycles += ncyc;
     if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
-    if (s->hout[9] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
-    if (s->hout[8] > limit) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
+    if (s->hout[13] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
+    if (s->hout[12] > limit) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
     residual_norms(s, rho, tn);
+    for (int q = 0; q < 3; ++q) {
+      const double fn = std::sqrt(s->hout[6 + q]), t = std::sqrt(s->hout[9 + q]);
+      rho_steady[q] = fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
+    }
   }
   s->stats.newton_iterations += *newton_out;
   s->stats.last_newton = *newton_out;
@@ -709,7 +722,8 @@ int march(mg_state *s, int l0, double dt_start, double tol) {
   for (int n = 0; n < s->prm.max_steps; ++n) {
     int newton = 0;
     const double step_tol = std::max(ntol, rel * r_start);
-    int rc = step(s, l0, dt, step_tol, &newton, coef_current);
+    double r_step = -1.0;
+    int rc = step(s, l0, dt, step_tol, &newton, coef_current, &r_step);
     coef_current = false;
     if (rc == MG_ECUDA) return rc;
     s->stats.dt_last = dt;
@@ -717,12 +731,16 @@ int march(mg_state *s, int l0, double dt_start, double tol) {
       s->stats.steps_accepted++;
       s->stats.sim_time += dt;
       // the accepted step ended on a residual at this very state: its coefficients stand, and
-      // they serve the next step's first residual too
-      double rho[3];
-      rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr, false);
-      if (rc) return rc;
+      // they serve the next step's first residual too; that launch also summed the steady rows
+      // (after at least one Newton iteration), otherwise evaluate them here
+      double r = r_step;
+      if (r < 0.0) {
+        double rho[3];
+        rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr, false);
+        if (rc) return rc;
+        r = std::max(rho[0], std::max(rho[1], rho[2]));
+      }
       coef_current = true;
-      const double r = std::max(rho[0], std::max(rho[1], rho[2]));
       s->stats.steady_rho = r;
       r_start = r;
       if (r <= tol) return MG_OK;

@@ -440,24 +440,21 @@ cudaError_t launch_inject_levels(const LevelSet *S, const Level &L0, int l0, int
 // ------------------------------------------------------------------------------------------
 // K2': nonlinear residual from the face coefficients of the same state: the SG flux through a
 // face is cG n_L - cF n_R (cG = g D G(alpha), cF = g D F(alpha)), the Poisson flux g dV.
+// The steady rows (sources, fluxes, space charge) are summed first and the time-derivative
+// terms added last, so with steady_too the same launch also reduces the steady rows' sums
+// (into out[6..11]), equal bit for bit to a launch with dt_inv = 0.
 __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, double dt_inv, int write_f,
-                                                         double *F0, double *F1, double *F2, double *partials,
-                                                         unsigned *counter, double *out6) {
+                                                         int steady_too, double *F0, double *F1, double *F2,
+                                                         double *partials, unsigned *counter, double *out) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * CBY + threadIdx.y + 1;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (i < L.ni && j < L.nz) {
     const int P = L.P;
     const size_t k = (size_t)j * P + i;
     const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
     const double A = L.volr[i] * L.dzc[j];
     double Fe = 0, Fp = 0, FV = 0, Te = 0, Tp = 0, TV = 0;
-    if (dt_inv > 0.0) {
-      Fe += A * (ne[k] - sv.uold[NE][k]) * dt_inv;
-      Fp += A * (np[k] - sv.uold[NP][k]) * dt_inv;
-      Te += A * (fabs(ne[k]) + fabs(sv.uold[NE][k])) * dt_inv;
-      Tp += A * (fabs(np[k]) + fabs(sv.uold[NP][k])) * dt_inv;
-    }
     Fe -= A * sv.S[0][k];
     Fp -= A * sv.S[1][k];
     Te += A * fabs(sv.S[0][k]);
@@ -476,6 +473,14 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
     const double ak = L.Ak[k];
     FV += ak * (np[k] - ne[k]);
     TV += ak * (fabs(np[k]) + fabs(ne[k]));
+    acc[6] = Fe * Fe; acc[7] = Fp * Fp; acc[8] = FV * FV;
+    acc[9] = Te * Te; acc[10] = Tp * Tp; acc[11] = TV * TV;
+    if (dt_inv > 0.0) {
+      Fe += A * (ne[k] - sv.uold[NE][k]) * dt_inv;
+      Fp += A * (np[k] - sv.uold[NP][k]) * dt_inv;
+      Te += A * (fabs(ne[k]) + fabs(sv.uold[NE][k])) * dt_inv;
+      Tp += A * (fabs(np[k]) + fabs(sv.uold[NP][k])) * dt_inv;
+    }
     if (write_f) {
       const size_t kf = cidx(P, i, j);
       L.f[NE][kf] = -Fe; L.f[NP][kf] = -Fp; L.f[NV][kf] = -FV;
@@ -484,14 +489,20 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
     acc[0] = Fe * Fe; acc[1] = Fp * Fp; acc[2] = FV * FV;
     acc[3] = Te * Te; acc[4] = Tp * Tp; acc[5] = TV * TV;
   }
-  reduce_finish<6>(acc, partials, counter, out6, 0);
+  if (steady_too) {
+    reduce_finish<12>(acc, partials, counter, out, 0);
+  } else {
+    double a6[6] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5]};
+    reduce_finish<6>(a6, partials, counter, out, 0);
+  }
 }
 
-cudaError_t launch_resid_coef(const Level &L, const StateView &sv, double dt, bool write_f, double *Fout[3],
-                              double *partials, unsigned *counter, double *out6, cudaStream_t st) {
+cudaError_t launch_resid_coef(const Level &L, const StateView &sv, double dt, bool write_f, bool steady_too,
+                              double *Fout[3], double *partials, unsigned *counter, double *out, cudaStream_t st) {
   dim3 b(32, CBY), g((L.nr + 1 + 31) / 32, (L.nz - 1 + CBY - 1) / CBY);
-  k_resid_coef<<<g, b, 0, st>>>(L, sv, dt > 0 ? 1.0 / dt : 0.0, write_f ? 1 : 0, Fout ? Fout[0] : nullptr,
-                                Fout ? Fout[1] : nullptr, Fout ? Fout[2] : nullptr, partials, counter, out6);
+  k_resid_coef<<<g, b, 0, st>>>(L, sv, dt > 0 ? 1.0 / dt : 0.0, write_f ? 1 : 0, steady_too ? 1 : 0,
+                                Fout ? Fout[0] : nullptr, Fout ? Fout[1] : nullptr, Fout ? Fout[2] : nullptr,
+                                partials, counter, out);
   count_launch();
   return cudaGetLastError();
 }
