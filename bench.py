@@ -179,6 +179,23 @@ def oracle_estimate(sample_vcycles: int = 4):
     return total, sample_s, detail, counts
 
 
+def max_over_ranks(vals, world, device):
+    """Element-wise maximum of per-rank values over all ranks (the slowest rank's times);
+    the values themselves on a single rank."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_rate(world, steps, seconds):
+    """Solves per second of the whole job: every rank solved `steps` replicas of the workload,
+    and the job took the slowest rank's time."""
+    return world * steps / seconds
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -297,11 +314,8 @@ def run_ours(args):
         step()
         smooth_prof.append(s.profile_end())
 
-    t = torch.tensor([dev_ms, wall], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms_max, wall_max = float(t[0]), float(t[1])
-    value = world * args.steps / (dev_ms_max / 1000.0)
+    dev_ms_max, wall_max = max_over_ranks([dev_ms, wall], world, dev)
+    value = whole_job_rate(world, args.steps, dev_ms_max / 1000.0)
 
     if args.no_extras:
         if rank == 0:
@@ -331,10 +345,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_wall = time.perf_counter() - t0
-    te = torch.tensor([e2e_wall], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / float(te[0])
+    e2e_value = whole_job_rate(world, args.steps, max_over_ranks([e2e_wall], world, dev)[0])
 
     # ---- V-cycle rate on the 257 x 257 Newton system (cycle control included: one norm per cycle)
     F, _ = s.residual(1e-6)
