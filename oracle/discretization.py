@@ -63,14 +63,15 @@ def apply_dirichlet(u: np.ndarray, phys: Physics, g: Optional[Grid] = None) -> n
 
 
 # --------------------------------------------------------------------------- fields
-def face_fields(g: Grid, V: np.ndarray):
-    """|E| on r-faces (nz+1, nr) and z-faces (nz, nr+1), E = -grad V (eq. 6).
+def face_field_components(g: Grid, V: np.ndarray):
+    """Components of E = -grad V (eq. 6) on the faces: (Er, Ez_t) on r-faces (nz+1, nr) and
+    (Ez, Er_t) on z-faces (nz, nr+1).
 
     The face-normal component is the two-point difference across the face; the
     transverse component is the mean of the four adjacent perpendicular face
     fields.  On the axis and the outer wall the perpendicular field is taken as
     zero (dV/dr = 0 there by symmetry).  Electrode-row r-faces get no transverse
-    part (they never enter a residual row).
+    part (they never enter a residual row).  Linear in V.
     """
     Er = -(V[:, 1:] - V[:, :-1]) / g.dr
     Ez = -(V[1:, :] - V[:-1, :]) / g.dz[:, None]
@@ -78,6 +79,12 @@ def face_fields(g: Grid, V: np.ndarray):
     Ez_t[1:-1, :] = 0.25 * (Ez[:-1, :-1] + Ez[1:, :-1] + Ez[:-1, 1:] + Ez[1:, 1:])
     Er_t = np.zeros_like(Ez)
     Er_t[:, 1:-1] = 0.25 * (Er[:-1, :-1] + Er[:-1, 1:] + Er[1:, :-1] + Er[1:, 1:])
+    return Er, Ez_t, Ez, Er_t
+
+
+def face_fields(g: Grid, V: np.ndarray):
+    """|E| on r-faces (nz+1, nr) and z-faces (nz, nr+1) (see face_field_components)."""
+    Er, Ez_t, Ez, Er_t = face_field_components(g, V)
     return np.sqrt(Er ** 2 + Ez_t ** 2), np.sqrt(Ez ** 2 + Er_t ** 2)
 
 
@@ -89,6 +96,17 @@ def table_lookup(table: np.ndarray, Eabs: np.ndarray):
     t = (x - E[k]) / (E[k + 1] - E[k])
     cols = [table[k, c] + t * (table[k + 1, c] - table[k, c]) for c in range(1, 5)]
     return cols  # mu_e, D_e, mu_p, D_p
+
+
+def table_slopes(table: np.ndarray, Eabs: np.ndarray):
+    """d/d|E| of each interpolated column at |E|: the slope of the segment table_lookup
+    interpolates on, zero where |E| lies outside the table (the lookup is clamped there)."""
+    E = table[:, 0]
+    inside = (Eabs >= E[0]) & (Eabs <= E[-1])
+    x = np.clip(Eabs, E[0], E[-1])
+    k = np.clip(np.searchsorted(E, x, side="right") - 1, 0, len(E) - 2)
+    h = E[k + 1] - E[k]
+    return [np.where(inside, (table[k + 1, c] - table[k, c]) / h, 0.0) for c in range(1, 5)]
 
 
 def face_transport(g: Grid, V: np.ndarray, phys: Physics):
@@ -232,6 +250,52 @@ def jacobian(g: Grid, u: np.ndarray, dt: Optional[float], phys: Physics) -> sp.c
     n = 3 * g.n_nodes_unknown
     J = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
     return J.tocsr()
+
+
+def transport_jv(g: Grid, u: np.ndarray, w: np.ndarray, phys: Physics) -> np.ndarray:
+    """The part of the residual's directional derivative along w (3, nz+1, nr+1) that the
+    Picard Jacobian leaves out: the flux change through mu(|E|), D(|E|) as the potential moves
+    by w[2] (Sec. 2: mobilities and diffusion coefficients are functions of the local field).
+
+    Per face and species, flux = g D (n_L G(a) - n_R F(a)) with a = -s (mu/D)(V_R - V_L)
+    (eqs. 8-11), so at fixed n, V_R - V_L:
+        d flux = g dD (n_L G(a) - n_R F(a)) + g D (n_L G'(a) - n_R F'(a)) da,
+        da = -s (V_R - V_L) (dmu D - mu dD) / D^2,
+    with dmu, dD the table slopes times d|E|, and d|E| = (E_n dE_n + E_t dE_t) / |E| from
+    the field components of w[2].  Rows as in residual (L += d flux, R -= d flux); zero
+    without a transport table.
+    """
+    out = np.zeros_like(u)
+    if phys.table is None:
+        return out
+    V, f = u[2], phys.pressure_factor
+    Er, Ezt, Ez, Ert = face_field_components(g, V)
+    dEr, dEzt, dEz, dErt = face_field_components(g, w[2])
+    sets = (("r", Er, Ezt, dEr, dEzt), ("z", Ez, Ert, dEz, dErt))
+    for (name, gf, _, _, Ls, Rs), (_, En, Et, dEn, dEt) in zip(_faces(g, u, phys), sets):
+        Em = np.sqrt(En ** 2 + Et ** 2)
+        dEm = np.divide(En * dEn + Et * dEt, Em, out=np.zeros_like(Em), where=Em > 0)
+        vals = [c / f for c in table_lookup(phys.table, Em)]
+        slopes = [c / f for c in table_slopes(phys.table, Em)]
+        dVf = V[Rs] - V[Ls]
+        for fi, s, (mu, D), (smu, sD) in ((0, -1.0, vals[0:2], slopes[0:2]), (1, 1.0, vals[2:4], slopes[2:4])):
+            n = u[fi]
+            a = -s * (mu / D) * dVf
+            dmu, dD = smu * dEm, sD * dEm
+            da = -s * dVf * (dmu * D - mu * dD) / D ** 2
+            dflux = (gf * dD * (n[Ls] * bernoulli.G(a) - n[Rs] * bernoulli.F(a))
+                     + gf * D * (n[Ls] * bernoulli.dG(a) - n[Rs] * bernoulli.dF(a)) * da)
+            out[fi][Ls] += dflux
+            out[fi][Rs] -= dflux
+    return out
+
+
+def jacobian_full_apply(g: Grid, u: np.ndarray, dt: Optional[float], phys: Physics, x: np.ndarray,
+                        J: Optional[sp.csr_matrix] = None) -> np.ndarray:
+    """Full Jacobian (field dependence of mu, D included) times an unknown vector x:
+    J x (Picard Jacobian, eq. 14) plus transport_jv along x."""
+    J = jacobian(g, u, dt, phys) if J is None else J
+    return J @ x + to_vec(g, transport_jv(g, u, from_vec(g, x), phys))
 
 
 def to_vec(g: Grid, a: np.ndarray) -> np.ndarray:

@@ -53,6 +53,8 @@ class SolverOptions:
     newton_tol_rel: float = 0.1     # > 0: a step's tolerance is max(newton_tol, this x the steady
                                     # residual at the step's start); 0: every step to newton_tol
     eta_adapt: bool = True          # relax eta when the Newton residual is near its target
+    full_jacobian: bool = False     # Newton with the field dependence of mu, D in the Jacobian
+    max_corrections: int = 20       # defect corrections per Newton iteration (full_jacobian)
 
 
 @dataclasses.dataclass
@@ -71,6 +73,33 @@ def forcing_term(opt: SolverOptions, rho_k: float, tol: float) -> float:
     if not opt.eta_adapt:
         return opt.eta
     return max(opt.eta, min(0.1, 0.5 * tol / rho_k))
+
+
+def full_jacobian_correct(g: Grid, x, dt, phys, H, fvec, du, eta, tn, opt: SolverOptions):
+    """Newton step of the full Jacobian J_F (mu, D functions of |E|) by defect correction with
+    the multigrid solver of the Picard Jacobian J_P: while
+        max_f ||fvec - J_F du||_f / tn_f  >  eta * max_f ||fvec||_f / tn_f,
+    solve J_P e = fvec - J_F du by V-cycles (same test, relative to the defect) and add e.
+    Returns (du, V-cycles spent, converged)."""
+    s = np.where(np.asarray(tn) > 0, tn, 1.0)
+
+    def wnorm(v):
+        return max(np.linalg.norm(v[k::3]) / s[k] for k in range(3))
+
+    J = H.levels[0].J
+    f0 = wnorm(fvec)
+    ncyc = 0
+    for _ in range(opt.max_corrections):
+        r = fvec - disc.jacobian_full_apply(g, x, dt, phys, du, J)
+        if wnorm(r) <= eta * f0:
+            return du, ncyc, True
+        e, hist = H.solve(r, eta, opt.max_vcycles, scale=tn)
+        ncyc += len(hist) - 1
+        if not np.isfinite(hist[-1]) or hist[-1] > eta:
+            return du, ncyc, False
+        du = du + e
+    r = fvec - disc.jacobian_full_apply(g, x, dt, phys, du, J)
+    return du, ncyc, bool(wnorm(r) <= eta * f0)
 
 
 def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: float,
@@ -93,10 +122,16 @@ def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: f
                          opt.nu_coarse2, opt.nu_tiny_n, opt.nu_tiny1, opt.nu_tiny2)
         tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
         eta = forcing_term(opt, r.max(), tol)
-        du, hist = H.solve(-disc.to_vec(g, F), eta, opt.max_vcycles, scale=tn)
+        fvec = -disc.to_vec(g, F)
+        du, hist = H.solve(fvec, eta, opt.max_vcycles, scale=tn)
         vcyc.append(len(hist) - 1)
         if not np.isfinite(hist[-1]) or hist[-1] > eta:
             return u, StepStats(False, it + 1, vcyc, r, "linear solve failed")
+        if opt.full_jacobian:
+            du, ncyc, ok = full_jacobian_correct(g, x, dt, phys, H, fvec, du, eta, tn, opt)
+            vcyc[-1] += ncyc
+            if not ok:
+                return u, StepStats(False, it + 1, vcyc, r, "full-Jacobian correction failed")
         d = disc.from_vec(g, du)
         if np.abs(d[2]).max() > limit:
             return u, StepStats(False, it + 1, vcyc, r, "correction limit")
