@@ -497,6 +497,18 @@ def measure_forms(args, dev, peaks):
                                "steps": st["steps_accepted"] + st["steps_rejected"], "newton": st["newton_iterations"],
                                "vcycles": st["vcycles"]}
     s.close()
+    # full Newton Jacobian (mu, D functions of |E|): defect corrections around the Picard
+    # multigrid solve, with the default step rule and with every step solved to 0.1 x tol
+    fj = {}
+    for name, kw in (("relative_steps", {}), ("strict_steps", dict(newton_tol_rel=0.0))):
+        s = mg.from_discharge(d, full_jacobian=1, **kw)
+        s.autotune()
+        times, st = timed_steady(s, "full-Jacobian")
+        fj[name] = {"solves_per_s": 1.0 / statistics.median(times), "ms": 1000 * statistics.median(times),
+                    "steps": st["steps_accepted"] + st["steps_rejected"], "newton": st["newton_iterations"],
+                    "vcycles": st["vcycles"]}
+        s.close()
+    out["full_jacobian_257"] = fj
     # mixed-precision steady solve of the same 257^2 workload
     s = mg.from_discharge(d, precision=mg.MG_MIXED)
     s.autotune()

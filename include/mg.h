@@ -127,6 +127,12 @@ typedef struct mg_params {
                              newton_tol_rel x the steady residual at the step's start): steps far
                              from the steady state are solved only as far as they can matter for
                              it (0: off; 0 <= newton_tol_rel < 1) */
+  int32_t full_jacobian;  /* 1: Newton with the field dependence of mu(|E|), D(|E|) in the
+                             Jacobian (Sec. 2): each Newton step solves the full-Jacobian system by
+                             defect correction around the multigrid solve of the Picard Jacobian
+                             (eq. 14, mu and D frozen); 0: the Picard Jacobian alone */
+  int32_t max_corrections; /* defect corrections per Newton iteration with full_jacobian (1..100);
+                             not converged -> the step is rejected like a failed linear solve */
 } mg_params;
 
 /* Per-call statistics. */
@@ -156,7 +162,7 @@ typedef struct mg_state mg_state;
  * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels
  * larger than 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down),
  * chain_from = 1 (the two-level 129^2 -> 257^2 continuation), pdl = 9 (smoothers and the coarse-cycle kernel), wall_dirichlet = 0,
- * newton_tol_rel = 0.1.
+ * newton_tol_rel = 0.1, full_jacobian = 0, max_corrections = 20.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on
@@ -197,7 +203,9 @@ int mg_set_sources(mg_state *s, const double *S_e, const double *S_p, int where)
 int mg_residual(mg_state *s, double dt, double *F_ne, double *F_np, double *F_V, double rho[3], int where);
 
 /* Jacobian-vector product (eq. 14) at the current state: out = J v.  v and out
- * are 3 node arrays each (electrode rows of v ignored, of out set to 0). */
+ * are 3 node arrays each (electrode rows of v ignored, of out set to 0).  With
+ * full_jacobian = 1 in the state's parameters the product includes the field dependence of
+ * mu(|E|), D(|E|) (the full Newton Jacobian); otherwise it is the Picard Jacobian. */
 int mg_jacobian_apply(mg_state *s, double dt, const double *v_ne, const double *v_np, const double *v_V,
                       double *o_ne, double *o_np, double *o_V, int where);
 

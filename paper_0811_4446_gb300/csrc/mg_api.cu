@@ -67,6 +67,7 @@ struct mg_state {
   double *dout;          // device outputs of reductions (16 doubles)
   double *hout;          // pinned host mirror (16 doubles)
   double *M, *Minv, *rs, *cs;
+  double *fj_f[3], *fj_d[3];  // full-Jacobian Newton: saved right-hand side and accumulated step
   int *flag;
   double *table_d;
   mg_stats stats;
@@ -210,6 +211,10 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
   s->cset32 = c.take<CoarseSet<float>>(1);
   s->table_d = table_rows > 0 ? c.take<double>((size_t)table_rows * 6) : nullptr;  // rows x 5, then 1/dE
   s->lset = c.take<LevelSet>(1);
+  {
+    const size_t n0 = (size_t)(lnz[0] + 1) * pitch_of(lnr[0]);
+    for (int q = 0; q < 3; ++q) { s->fj_f[q] = c.take<double>(n0); s->fj_d[q] = c.take<double>(n0); }
+  }
 }
 
 // Geometry of one level (finite-volume control volumes of eqs. 12-13, per radian).
@@ -638,6 +643,44 @@ void copy_state_async(mg_state *s, int l0, bool to_old) {
 // A Newton iteration enqueues the hierarchy set-up, the device-side linear solve, the update
 // and the next residual, then waits once and reads the solve's control block, the update's
 // checks and the new residual norms together.
+// Full-Jacobian Newton step on level l0 (mu, D functions of |E|): the multigrid solve of the
+// Picard system has left du; while the full defect  max_f ||f - J_full du||_f / w_f  exceeds
+// eta * f0 (f0 = the same for f, the Newton residual's weighted norm), solve the Picard system
+// for the defect and add the correction.  du ends as the accumulated step.
+int full_jacobian_correct(mg_state *s, int l0, double eta, const double tn[3], double f0, int *ncyc, bool *ok) {
+  LevelBuf &b = s->lv[l0];
+  cudaStream_t st = s->stream;
+  const size_t bytes = b.nodes * sizeof(double);
+  double w[3];
+  solve_weights(tn, w);
+  for (int q = 0; q < 3; ++q) {
+    CK(cudaMemcpyAsync(s->fj_f[q], b.L.f[q], bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(s->fj_d[q], b.L.du[q], bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  *ok = false;
+  *ncyc = 0;
+  for (int c = 0; c <= s->prm.max_corrections; ++c) {
+    CK(launch_full_defect(b.L, b.sv, s->tr, s->fj_f, s->fj_d, s->partials, s->counter, s->dout, st));
+    int rc = sync_read(s, 3);
+    if (rc) return rc;
+    const double r = weighted(s, w);
+    if (!(r == r)) break;
+    if (r <= eta * f0) { *ok = true; break; }
+    if (c == s->prm.max_corrections) break;
+    // the Picard solve of J_P e = defect, relative to the defect
+    int nc = 0;
+    bool lok = false;
+    rc = linear_solve(s, l0, eta, s->prm.max_vcycles, tn, nullptr, &nc, &lok);
+    if (rc) return rc;
+    *ncyc += nc;
+    s->stats.vcycles -= nc;  // counted by the caller with the first solve's cycles
+    if (!lok) break;
+    CK(launch_add3(s->fj_d, b.L.du, b.nodes, st));
+  }
+  for (int q = 0; q < 3; ++q) CK(cudaMemcpyAsync(b.L.du[q], s->fj_d[q], bytes, cudaMemcpyDeviceToDevice, st));
+  return MG_OK;
+}
+
 // steady_rho (may be NULL): on acceptance after at least one Newton iteration, the steady
 // residual of the new state (from the same residual launch), else -1.
 int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_current = false,
@@ -674,9 +717,22 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
     double w[3];
     solve_weights(tn, w);
     const bool graph = use_graph(s, s->prm.max_vcycles);
+    const bool full = s->prm.full_jacobian != 0;
     if (graph) rc = linear_solve_graph_begin(s, l0, eta, s->prm.max_vcycles, w);
     else rc = linear_solve_eager(s, l0, eta, s->prm.max_vcycles, w, nullptr, &ncyc, &ok);
     if (rc) return rc;
+    if (full) {
+      // the defect corrections need the Picard step first
+      if (graph) {
+        CK(cudaStreamSynchronize(s->stream));
+        linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
+      }
+      if (ok) {
+        int nc2 = 0;
+        if ((rc = full_jacobian_correct(s, l0, eta, tn, rmax, &nc2, &ok))) return rc;
+        ncyc += nc2;
+      }
+    }
     // u += du (max |dV| and the non-finite flag into dout[12..13]), then the residual at the new
     // state (into dout[0..5], its steady rows' sums into dout[6..11]); used only if the update
     // is accepted
@@ -684,7 +740,7 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
     if ((rc = residual_launch(s, l0, dt, true, nullptr, true, true))) return rc;
     rc = sync_read(s, 14);
     if (rc) return rc;
-    if (graph) linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
+    if (graph && !full) linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
     s->stats.vcycles += ncyc;
     if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
     if (s->hout[13] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
@@ -871,6 +927,8 @@ void mg_params_default(mg_params *p) {
   p->pdl = PDL_SMOOTH | PDL_COARSE;
   p->wall_dirichlet = 0;
   p->newton_tol_rel = 0.1;
+  p->full_jacobian = 0;
+  p->max_corrections = 20;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
   p->coarse_kernel_threads = 512;
@@ -891,6 +949,8 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
   }
   if (p->wall_dirichlet != 0 && p->wall_dirichlet != 1) { *why = "wall_dirichlet must be 0 or 1"; return MG_EINVAL; }
   if (!(p->newton_tol_rel >= 0.0 && p->newton_tol_rel < 1.0)) { *why = "newton_tol_rel must be in [0, 1)"; return MG_EINVAL; }
+  if (p->full_jacobian != 0 && p->full_jacobian != 1) { *why = "full_jacobian must be 0 or 1"; return MG_EINVAL; }
+  if (p->max_corrections < 1 || p->max_corrections > 100) { *why = "max_corrections must be in 1..100"; return MG_EINVAL; }
   if (p->pdl < 0 || p->pdl > PDL_ALL) { *why = "pdl: a combination of the PDL kernel-kind bits"; return MG_EINVAL; }
   if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
     *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";
@@ -1167,6 +1227,8 @@ int mg_jacobian_apply(mg_state *s, double dt, const double *v_ne, const double *
   // J v is written on the unknown rows and columns only: the rest of the output is zero
   for (int q = 0; q < 3; ++q) CK(cudaMemsetAsync(b.L.r[q], 0, b.nodes * sizeof(double), s->stream));
   CK(launch_linres<double>(b.L, b.L.du, nullptr, b.L.r, nullptr, nullptr, nullptr, s->stream));
+  // full_jacobian: add the field dependence of mu, D
+  if (s->prm.full_jacobian) CK(launch_add_transport(b.L, b.sv, s->tr, b.L.du[NV], b.L.r, s->stream));
   double *dst[3] = {o_ne, o_np, o_V};
   for (int q = 0; q < 3; ++q)
     if ((rc = copy_out(s, b, dst[q], b.L.r[q], where))) return rc;

@@ -199,6 +199,11 @@ cudaError_t launch_update(const Level &L, const StateView &sv, double *partials,
 template <typename T>
 cudaError_t launch_zero_du(const LevelT<T> &L, cudaStream_t st);
 // mixed form
+cudaError_t launch_full_defect(const Level &L, const StateView &sv, const Transport &tr, double *const fs[3],
+                               double *const d[3], double *partials, unsigned *counter, double *out3, cudaStream_t st);
+cudaError_t launch_add_transport(const Level &L, const StateView &sv, const Transport &tr, const double *w,
+                                 double *out[3], cudaStream_t st);
+cudaError_t launch_add3(double *const acc[3], double *const x[3], size_t n, cudaStream_t st);
 cudaError_t launch_split_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);
 cudaError_t launch_join_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);
 cudaError_t launch_mixed_update(const Level &L, const LevelT<float> &M, double n0, cudaStream_t st);

@@ -1784,6 +1784,179 @@ cudaError_t launch_split_rows(const Level &L, double *const in[3], double *const
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// Full Newton Jacobian (mu, D functions of |E|, Sec. 2): the residual's change through the
+// transport coefficients when the potential moves by w, which the Picard Jacobian of eq. 14
+// (mu, D frozen) leaves out.  Per face and species, flux = g D (n_L G(a) - n_R F(a)),
+// a = -s (mu/D)(V_R - V_L), so at fixed n and V_R - V_L
+//   d flux = g dD (n_L G(a) - n_R F(a)) + g D (n_L G'(a) - n_R F'(a)) da,
+//   da = -s (V_R - V_L) (dmu D - mu dD) / D^2,
+// dmu, dD = table segment slope x d|E| (zero where the lookup is clamped), and
+// d|E| = (E_n dE_n + E_t dE_t) / |E| with the face field components of w (the same stencils as
+// the face |E| of the coefficient kernel).  G = B(-a), F = B(a): n_L G' - n_R F' =
+// -(n_L B'(-a) + n_R B'(a)).
+
+// Table values and their |E| slopes (divided by the pressure factor).
+__device__ __forceinline__ void lookup_slope1(const Transport &tr, double Eabs, FaceTr &v, FaceTr &d) {
+  const double *T = tr.table;
+  const int n = tr.rows;
+  const double E0 = __ldg(T), E1 = __ldg(T + 5 * (n - 1));
+  const bool inside = Eabs >= E0 && Eabs <= E1;
+  const double x = fmin(fmax(Eabs, E0), E1);
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(T + 5 * mid) <= x) lo = mid; else hi = mid;
+  }
+  const double *a = T + 5 * lo, *b = a + 5;
+  const double ih = __ldg(tr.inv_dE + lo);
+  const double t = (x - __ldg(a)) * ih;
+  double sl[4], val[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double ya = __ldg(a + 1 + c), yb = __ldg(b + 1 + c);
+    val[c] = (ya + t * (yb - ya)) * tr.inv_pf;
+    sl[c] = inside ? (yb - ya) * ih * tr.inv_pf : 0.0;
+  }
+  v = FaceTr{val[0], val[1], val[2], val[3]};
+  d = FaceTr{sl[0], sl[1], sl[2], sl[3]};
+}
+
+// d flux of both species through one face; En, Et: the face field components of the state,
+// dEn, dEt: those of w; dV = V_R - V_L.
+__device__ __forceinline__ Triple<double> face_dflux(const Transport &tr, double g, double En, double Et, double dEn,
+                                                     double dEt, double dV, double neL, double neR, double npL,
+                                                     double npR) {
+  const double Em = sqrt(En * En + Et * Et);
+  const double dEm = Em > 0.0 ? (En * dEn + Et * dEt) / Em : 0.0;
+  FaceTr t, sl;
+  lookup_slope1(tr, Em, t, sl);
+  Triple<double> out{0.0, 0.0, 0.0};
+  {  // electrons, s = -1: a = (mu/D) dV
+    const double a = (t.mu_e / t.D_e) * dV;
+    const Bern b = bernoulli1(a);
+    const double dmu = sl.mu_e * dEm, dD = sl.D_e * dEm;
+    const double da = dV * (dmu * t.D_e - t.mu_e * dD) / (t.D_e * t.D_e);
+    out.e = g * dD * (neL * b.Bm - neR * b.Bp) - g * t.D_e * (neL * b.dBm + neR * b.dBp) * da;
+  }
+  {  // ions, s = +1: a = -(mu/D) dV
+    const double a = -(t.mu_p / t.D_p) * dV;
+    const Bern b = bernoulli1(a);
+    const double dmu = sl.mu_p * dEm, dD = sl.D_p * dEm;
+    const double da = -dV * (dmu * t.D_p - t.mu_p * dD) / (t.D_p * t.D_p);
+    out.p = g * dD * (npL * b.Bm - npR * b.Bp) - g * t.D_p * (npL * b.dBm + npR * b.dBp) * da;
+  }
+  return out;
+}
+
+// The transport part of (J w) in the two continuity rows of unknown node (i, j); w in the
+// colour-split layout of the corrections, the state in row order.
+__device__ __forceinline__ Triple<double> transport_row(const Level &L, const StateView &sv, const Transport &tr,
+                                                        const double *w, int i, int j) {
+  const int P = L.P;
+  const size_t k = (size_t)j * P + i;
+  const double *ne = sv.u[NE], *np = sv.u[NP], *V = sv.u[NV];
+  auto W = [&](int ii, int jj) { return w[cidx(P, ii, jj)]; };
+  Triple<double> r{0.0, 0.0, 0.0};
+  // r-face between columns c and c + 1 of row j (j interior)
+  auto rface = [&](int c) {
+    const size_t kL = (size_t)j * P + c, kR = kL + 1;
+    const double En = (V[kL] - V[kR]) * L.idr;
+    const double lo = (V[kL - P] - V[kL]) + (V[kR - P] - V[kR]);
+    const double up = (V[kL] - V[kL + P]) + (V[kR] - V[kR + P]);
+    const double Et = 0.25 * (lo * L.idz[j - 1] + up * L.idz[j]);
+    const double dEn = (W(c, j) - W(c + 1, j)) * L.idr;
+    const double dlo = (W(c, j - 1) - W(c, j)) + (W(c + 1, j - 1) - W(c + 1, j));
+    const double dup = (W(c, j) - W(c, j + 1)) + (W(c + 1, j) - W(c + 1, j + 1));
+    const double dEt = 0.25 * (dlo * L.idz[j - 1] + dup * L.idz[j]);
+    return face_dflux(tr, L.gR[kL], En, Et, dEn, dEt, V[kR] - V[kL], ne[kL], ne[kR], np[kL], np[kR]);
+  };
+  // z-face between rows q and q + 1 of column i
+  auto zface = [&](int q) {
+    const size_t kL = (size_t)q * P + i, kR = kL + P;
+    const double En = (V[kL] - V[kR]) * L.idz[q];
+    const double dEn = (W(i, q) - W(i, q + 1)) * L.idz[q];
+    double Et = 0.0, dEt = 0.0;
+    if (i > 0 && i < L.nr) {
+      Et = 0.25 * L.idr * ((V[kL - 1] - V[kL + 1]) + (V[kR - 1] - V[kR + 1]));
+      dEt = 0.25 * L.idr * ((W(i - 1, q) - W(i + 1, q)) + (W(i - 1, q + 1) - W(i + 1, q + 1)));
+    }
+    return face_dflux(tr, L.gZ[kL], En, Et, dEn, dEt, V[kR] - V[kL], ne[kL], ne[kR], np[kL], np[kR]);
+  };
+  if (i < L.nr) { const Triple<double> f = rface(i); r.e += f.e; r.p += f.p; }
+  if (i > 0) { const Triple<double> f = rface(i - 1); r.e -= f.e; r.p -= f.p; }
+  { const Triple<double> f = zface(j); r.e += f.e; r.p += f.p; }
+  { const Triple<double> f = zface(j - 1); r.e -= f.e; r.p -= f.p; }
+  (void)k;
+  return r;
+}
+
+// Defect of the full-Jacobian Newton step: f = fs - J_full d (J_full = the Picard operator of
+// level L plus the transport part), written as the right-hand side of the next correction
+// (colour-split), with its per-field sums of squares.
+__global__ void __launch_bounds__(32 * CBY) k_full_defect(Level L, StateView sv, Transport tr, const double *fs0,
+                                                          const double *fs1, const double *fs2, const double *d0,
+                                                          const double *d1, const double *d2, double *partials,
+                                                          unsigned *counter, double *out3) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  double acc[3] = {0, 0, 0};
+  if (i < L.ni && j < L.nz) {
+    Triple<double> r = linres_val<double>(L, i, j, d0, d1, d2, fs0, fs1, fs2);
+    if (tr.table) {
+      const Triple<double> t = transport_row(L, sv, tr, d2, i, j);
+      r.e -= t.e;
+      r.p -= t.p;
+    }
+    const size_t kf = cidx(L.P, i, j);
+    L.f[NE][kf] = r.e; L.f[NP][kf] = r.p; L.f[NV][kf] = r.V;
+    acc[0] = r.e * r.e; acc[1] = r.p * r.p; acc[2] = r.V * r.V;
+  }
+  reduce_finish<3>(acc, partials, counter, out3, 0);
+}
+
+cudaError_t launch_full_defect(const Level &L, const StateView &sv, const Transport &tr, double *const fs[3],
+                               double *const d[3], double *partials, unsigned *counter, double *out3, cudaStream_t st) {
+  dim3 b(32, CBY), g((L.nr + 1 + 31) / 32, (L.nz - 1 + CBY - 1) / CBY);
+  k_full_defect<<<g, b, 0, st>>>(L, sv, tr, fs[0], fs[1], fs[2], d[0], d[1], d[2], partials, counter, out3);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// out (row layout) += the transport part of J w on the unknown nodes (w colour-split)
+__global__ void __launch_bounds__(32 * CBY) k_add_transport(Level L, StateView sv, Transport tr, const double *w,
+                                                            double *o0, double *o1) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  if (i >= L.ni || j >= L.nz || !tr.table) return;
+  const Triple<double> t = transport_row(L, sv, tr, w, i, j);
+  const size_t k = (size_t)j * L.P + i;
+  o0[k] += t.e;
+  o1[k] += t.p;
+}
+
+cudaError_t launch_add_transport(const Level &L, const StateView &sv, const Transport &tr, const double *w,
+                                 double *out[3], cudaStream_t st) {
+  dim3 b(32, CBY), g((L.nr + 1 + 31) / 32, (L.nz - 1 + CBY - 1) / CBY);
+  k_add_transport<<<g, b, 0, st>>>(L, sv, tr, w, out[0], out[1]);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// acc += x over n elements of three arrays
+__global__ void k_add3(double *a0, double *a1, double *a2, const double *x0, const double *x1, const double *x2,
+                       size_t n) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  a0[e] += x0[e]; a1[e] += x1[e]; a2[e] += x2[e];
+}
+
+cudaError_t launch_add3(double *const acc[3], double *const x[3], size_t n, cudaStream_t st) {
+  k_add3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(acc[0], acc[1], acc[2], x[0], x[1], x[2], n);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // The colour-split layout -> natural rows, every row 0 .. nz.
 __global__ void k_join_rows(Level L, const double *i0, const double *i1, const double *i2, double *o0, double *o1,
                             double *o2) {

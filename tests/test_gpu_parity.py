@@ -88,6 +88,58 @@ def test_jacobian_apply_parity(mg, nr, nz, table):
             assert np.abs(Jg[f] - Jv[f]).max() <= 1e-12 * scale[f].max(), f
 
 
+@pytest.mark.parametrize("nr,nz", [(16, 16), (64, 64), (32, 16)])
+def test_full_jacobian_apply_parity(mg, nr, nz):
+    """f4: the full Jacobian (mu, D functions of |E|) times a random vector, FP64 GPU against
+    the oracle's J_P v + transport_jv, to 1e-12 of the row scale."""
+    d = W.make_discharge(nr, nz=nz, seed=5, V_cathode=-300.0, use_table=True)
+    g, phys = _oracle(d)
+    rng = np.random.default_rng(4)
+    u = _random_state(d, rng)
+    s = mg.from_discharge(d, full_jacobian=1)
+    s.set_state(*[np.ascontiguousarray(a) for a in u])
+    for dt in (1e-9, 0.0):
+        v = np.zeros((3,) + d.shape)
+        v[:, 1:-1] = rng.standard_normal((3, d.nz - 1, d.nr + 1))
+        v[0:2] *= 1e12
+        Jg = s.jacobian_apply(dt, list(v))
+        J = disc.jacobian(g, u, dt if dt > 0 else None, phys)
+        x = disc.to_vec(g, v)
+        Jv = disc.from_vec(g, disc.jacobian_full_apply(g, u, dt if dt > 0 else None, phys, x, J))
+        scale = disc.from_vec(g, abs(J) @ np.abs(x))
+        for f in range(3):
+            assert np.abs(Jg[f] - Jv[f]).max() <= 1e-12 * scale[f].max(), (dt, f)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_jacobian_newton_step_parity(mg, precision):
+    """f4: one backward-Euler step with the full-Jacobian Newton (defect corrections around the
+    Picard multigrid solve) from a 2 % density perturbation of a near-steady 17^2 state: the
+    oracle's Newton iterations (fewer than the Picard Newton's) and state."""
+    d = W.make_discharge(16, seed=1, V_cathode=-300.0, use_table=True)
+    g, phys = _oracle(d)
+    us, ok, _ = osv.march(g, np.stack([d.ne0, d.np0, d.V0]), d.S_e, d.S_p, phys, 1e-6,
+                          osv.SolverOptions(eta=1e-10), 1e-9)
+    assert ok
+    start = disc.apply_dirichlet(us * np.array([1.02, 1.02, 1.0])[:, None, None], phys, g)
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    counts = []
+    for full in (0, 1):
+        s = mg.from_discharge(d, precision=prec, eta=1e-10, max_vcycles=200, full_jacobian=full)
+        s.set_state(*[np.ascontiguousarray(a) for a in start])
+        rc, st = s.step(1e-5, 1e-11)
+        assert rc == mg.MG_OK, st
+        counts.append(st["newton_iterations"])
+        uo, so_ = osv.step(g, start, d.S_e, d.S_p, 1e-5, phys, 1e-11,
+                           osv.SolverOptions(eta=1e-10, max_vcycles=200, full_jacobian=bool(full)))
+        assert so_.accepted and so_.newton == st["newton_iterations"], (full, so_.newton, st)
+        ug = s.get_state()
+        tolr = 1e-8 if precision == "mixed" else 1e-10
+        for q in range(3):
+            assert np.abs(ug[q] - uo[q]).max() <= tolr * np.abs(uo[q]).max(), (full, q)
+    assert counts[1] < counts[0]
+
+
 @pytest.mark.parametrize("n,table,dt", [(4, False, 1e-9), (16, False, 1e-9), (32, True, 1e-7), (64, True, 1e-6)])
 def test_linear_solve_parity(mg, n, table, dt):
     d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=table)
