@@ -10,6 +10,9 @@ names no component.  The components below are this project's readings:
 * smoother: collective (3x3 point-block) Gauss-Seidel in red-black order,
   red = (i + j) even first; in a five-point stencil nodes of one colour do not
   couple, so a half sweep is an exact block solve of the colour's own rows;
+  or (line=True) z-line Gauss-Seidel in zebra order, even columns first: a half
+  sweep solves the block-tridiagonal system of every column of one parity
+  exactly, its r-neighbours (the other parity) held fixed;
 * prolongation P: bilinear interpolation in the node coordinates (r equidistant,
   z by distance weights), identity across the three fields; electrode rows carry 0;
 * restriction R = P^T acting on the finite-volume-integrated residual;
@@ -24,6 +27,7 @@ from typing import List, Optional
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import discretization as disc
 from .grid import Grid
@@ -62,8 +66,9 @@ def inject(gf: Grid, a: np.ndarray) -> np.ndarray:
 
 
 class Level:
-    def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics):
+    def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics, line: bool = False):
         self.g = g
+        self.line = line
         self.J = disc.jacobian(g, u, dt, phys)
         nodes = np.arange(g.n_nodes_unknown)
         jj = nodes // g.ni + 1
@@ -80,9 +85,25 @@ class Level:
             blocks = np.zeros((len(nc), 3, 3))
             blocks[Jcc.row // 3, Jcc.row % 3, Jcc.col % 3] = Jcc.data
             self.colors.append((U, O, blocks, self.J[U][:, O].tocsr()))
+        self.lines = []
+        if line:
+            for c in (0, 1):
+                nc = nodes[ii % 2 == c]
+                oc = nodes[ii % 2 != c]
+                U = (3 * nc[:, None] + np.arange(3)[None, :]).ravel()
+                O = (3 * oc[:, None] + np.arange(3)[None, :]).ravel()
+                JUU = self.J[U][:, U].tocoo()
+                if np.any(ii[nc[JUU.row // 3]] != ii[nc[JUU.col // 3]]):
+                    raise AssertionError("columns of one parity couple: not a five-point stencil")
+                self.lines.append((U, O, spla.splu(JUU.tocsc()), self.J[U][:, O].tocsr()))
         self.dense = None
 
     def smooth(self, x: np.ndarray, f: np.ndarray, sweeps: int) -> np.ndarray:
+        if self.line:
+            for _ in range(sweeps):
+                for U, O, lu, JUO in self.lines:
+                    x[U] = lu.solve(f[U] - JUO @ x[O])
+            return x
         for _ in range(sweeps):
             for U, O, blocks, JUO in self.colors:
                 rhs = (f[U] - JUO @ x[O]).reshape(-1, 3, 1)
@@ -112,7 +133,7 @@ class Hierarchy:
     def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics,
                  coarsest: int = 2, nu1: int = 4, nu2: int = 4, nu_coarse_n: int = 64,
                  nu_coarse1: int = 2, nu_coarse2: int = 2, nu_tiny_n: int = 8, nu_tiny1: int = 1,
-                 nu_tiny2: int = 1):
+                 nu_tiny2: int = 1, line: bool = False):
         """Smoothing: nu1 / nu2 sweeps before / after the coarse-grid correction, except on
         levels whose larger side has at most nu_tiny_n intervals (nu_tiny1 / nu_tiny2) or else at
         most nu_coarse_n intervals (nu_coarse1 / nu_coarse2); 0 switches a tier off."""
@@ -120,7 +141,7 @@ class Hierarchy:
         self.P: List[sp.csr_matrix] = []
         self.nus: List[tuple] = []
         while True:
-            self.levels.append(Level(g, u, dt, phys))
+            self.levels.append(Level(g, u, dt, phys, line))
             side = max(g.nr, g.nz)
             if nu_tiny_n > 0 and side <= nu_tiny_n:
                 self.nus.append((nu_tiny1, nu_tiny2))

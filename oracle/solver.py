@@ -55,6 +55,7 @@ class SolverOptions:
     eta_adapt: bool = True          # relax eta when the Newton residual is near its target
     full_jacobian: bool = False     # Newton with the field dependence of mu, D in the Jacobian
     max_corrections: int = 20       # defect corrections per Newton iteration (full_jacobian)
+    line_smoother: bool = False     # z-line zebra Gauss-Seidel instead of point red-black
 
 
 @dataclasses.dataclass
@@ -119,7 +120,7 @@ def step(g: Grid, u: np.ndarray, S_e, S_p, dt: float, phys: disc.Physics, tol: f
         if it == opt.max_newton:
             break
         H = mg.Hierarchy(g, x, dt, phys, opt.coarsest, opt.nu1, opt.nu2, opt.nu_coarse_n, opt.nu_coarse1,
-                         opt.nu_coarse2, opt.nu_tiny_n, opt.nu_tiny1, opt.nu_tiny2)
+                         opt.nu_coarse2, opt.nu_tiny_n, opt.nu_tiny1, opt.nu_tiny2, opt.line_smoother)
         tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
         eta = forcing_term(opt, r.max(), tol)
         fvec = -disc.to_vec(g, F)

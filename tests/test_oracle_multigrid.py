@@ -131,3 +131,53 @@ def test_vcycle_with_dirichlet_wall_matches_dense_solve(n):
     xd = _dense_reference(H.levels[0].J, f)
     for k in range(3):
         assert np.abs(x[k::3] - xd[k::3]).max() <= 1e-9 * np.abs(xd[k::3]).max(), k
+
+
+def _line_case(R, n=32):
+    d = W.make_discharge(n, seed=0, V_cathode=-300.0, R=R)
+    g = Grid(d.nr, d.nz, d.R, d.z)
+    phys = disc.Physics(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    F, T = disc.residual(g, u, 0.99 * u, d.S_e, d.S_p, 1e-7, phys, with_terms=True)
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    return g, u, phys, -disc.to_vec(g, F), tn
+
+
+def test_line_half_sweep_solves_its_columns():
+    """f1: a zebra half sweep leaves zero residual (to rounding) in every row of the columns of
+    its parity, whatever the other columns hold: each column's block-tridiagonal system is
+    solved exactly."""
+    g, u, phys, f, tn = _line_case(1e-2)
+    lev = mg.Level(g, u, 1e-7, phys, line=True)
+    rng = np.random.default_rng(0)
+    for c in (0, 1):
+        x = rng.standard_normal(f.shape) * np.tile([1e12, 1e12, 1.0], len(f) // 3)
+        U, O, lu, JUO = lev.lines[c]
+        x[U] = lu.solve(f[U] - JUO @ x[O])
+        r = f - lev.J @ x
+        sc = abs(lev.J) @ np.abs(x) + np.abs(f)
+        assert np.abs(r[U]).max() <= 1e-13 * sc[U].max(), c
+        assert np.abs(r[O]).max() > 1e-3 * sc[O].max()
+    # the two parities together cover every unknown once
+    assert sorted(np.concatenate([lev.lines[0][0], lev.lines[1][0]])) == list(range(len(f)))
+
+
+@pytest.mark.parametrize("R", [1e-2, 1e-1])
+def test_line_smoother_converges_and_resists_anisotropy(R):
+    """f1: V-cycles with the z-line smoother converge to the same solution as the point
+    smoother; with dr = 10 dz (R = 10 d, strong z-coupling) their convergence factor stays
+    below 0.05 while the point smoother's rises above 0.2 (and above ten times the line one's)."""
+    g, u, phys, f, tn = _line_case(R)
+    res = {}
+    for line in (False, True):
+        H = mg.Hierarchy(g, u, 1e-7, phys, line=line)
+        x, hist = H.solve(f, 1e-12, 100, scale=tn)
+        assert hist[-1] <= (1e-12 if line else 1e-10)   # the point smoother stalls at rounding level
+        fac = (hist[min(6, len(hist) - 1)] / hist[1]) ** (1.0 / (min(6, len(hist) - 1) - 1))
+        res[line] = (x, fac)
+    xp, xl = res[False][0], res[True][0]
+    for k in range(3):
+        assert np.abs(xl[k::3] - xp[k::3]).max() <= 1e-7 * np.abs(xp[k::3]).max(), k
+    assert res[True][1] < 0.05
+    if R >= 1e-1:
+        assert res[False][1] > 0.2 and res[False][1] > 10 * res[True][1]
