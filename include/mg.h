@@ -133,6 +133,11 @@ typedef struct mg_params {
                              (eq. 14, mu and D frozen); 0: the Picard Jacobian alone */
   int32_t max_corrections; /* defect corrections per Newton iteration with full_jacobian (1..100);
                              not converged -> the step is rejected like a failed linear solve */
+  int32_t line_smoother;  /* 0: point-block red-black Gauss-Seidel; 1: z-line Gauss-Seidel in
+                             zebra order (even columns, then odd; each column's block-tridiagonal
+                             system solved exactly, robust to strong z-coupling) on every level
+                             (the coarse levels then run as separate launches, no coarse-cycle
+                             kernel) */
 } mg_params;
 
 /* Per-call statistics. */
@@ -162,7 +167,7 @@ typedef struct mg_state mg_state;
  * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels
  * larger than 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down),
  * chain_from = 1 (the two-level 129^2 -> 257^2 continuation), pdl = 9 (smoothers and the coarse-cycle kernel), wall_dirichlet = 0,
- * newton_tol_rel = 0.1, full_jacobian = 0, max_corrections = 20.
+ * newton_tol_rel = 0.1, full_jacobian = 0, max_corrections = 20, line_smoother = 0.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on

@@ -68,6 +68,7 @@ struct mg_state {
   double *hout;          // pinned host mirror (16 doubles)
   double *M, *Minv, *rs, *cs;
   double *fj_f[3], *fj_d[3];  // full-Jacobian Newton: saved right-hand side and accumulated step
+  double *line_scr;           // z-line smoother: 12 planes of (nz + 1) x (nr + 2) / 2 of the finest level
   int *flag;
   double *table_d;
   mg_stats stats;
@@ -138,7 +139,8 @@ size_t max_blocks(int nr, int nz) { return (size_t)((nr + 1 + 31) / 32) * ((nz +
 
 constexpr int kFields32PerLevel = 37;  // cr 6, cz 6, du 3, f 3, r 3, gR gZ Ak 3, fac 7, dia 3, du2 3
 
-void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int table_rows, bool mixed) {
+void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int table_rows, bool mixed,
+           bool line) {
   for (int l = 0; l < nlev; ++l) {
     LevelBuf &b = s->lv[l];
     b.nr = lnr[l]; b.nz = lnz[l]; b.P = pitch_of(lnr[l]);
@@ -215,6 +217,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
     const size_t n0 = (size_t)(lnz[0] + 1) * pitch_of(lnr[0]);
     for (int q = 0; q < 3; ++q) { s->fj_f[q] = c.take<double>(n0); s->fj_d[q] = c.take<double>(n0); }
   }
+  s->line_scr = line ? c.take<double>((size_t)12 * (lnz[0] + 1) * ((lnr[0] + 2) / 2)) : nullptr;
 }
 
 // Geometry of one level (finite-volume control volumes of eqs. 12-13, per radian).
@@ -364,6 +367,15 @@ template <> int sweep_shape<float>(const LevelBuf &b) { return b.sw32; }
 // lands in du; odd counts end with a copy), or pairs of half-sweep launches.
 template <typename T>
 int smooth_sweeps(mg_state *s, int l, int nu, cudaStream_t st) {
+  if (s->prm.line_smoother) {
+    T *scr = reinterpret_cast<T *>(s->line_scr);
+    for (int k = 0; k < nu; ++k)
+      for (int col = 0; col < 2; ++col) {
+        ProfScope ps(s, MG_PROF_SMOOTH, l);
+        CK(launch_zline<T>(view<T>(s->lv[l]), col, scr, st));
+      }
+    return MG_OK;
+  }
   const LevelT<T> &b = view<T>(s->lv[l]);
   int rc;
   if (!s->prm.fused_sweep || !level_fused<T>(s->lv[l])) {
@@ -833,7 +845,7 @@ int upload_level_set(mg_state *s) {
 // larger side has at most coarse_kernel_n intervals) and upload the level views it needs.
 int setup_coarse_kernel(mg_state *s) {
   s->cc_from = -1;
-  if (s->prm.coarse_kernel_n <= 0) return MG_OK;
+  if (s->prm.coarse_kernel_n <= 0 || s->prm.line_smoother) return MG_OK;
   for (int l = 1; l < s->nlev - 1; ++l)
     if (std::max(s->lv[l].nr, s->lv[l].nz) <= s->prm.coarse_kernel_n) { s->cc_from = l; break; }
   if (s->cc_from < 0 || s->nlev - s->cc_from > kMaxCoarseSet) { s->cc_from = -1; return MG_OK; }
@@ -929,6 +941,7 @@ void mg_params_default(mg_params *p) {
   p->newton_tol_rel = 0.1;
   p->full_jacobian = 0;
   p->max_corrections = 20;
+  p->line_smoother = 0;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
   p->coarse_kernel_threads = 512;
@@ -951,6 +964,7 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
   if (!(p->newton_tol_rel >= 0.0 && p->newton_tol_rel < 1.0)) { *why = "newton_tol_rel must be in [0, 1)"; return MG_EINVAL; }
   if (p->full_jacobian != 0 && p->full_jacobian != 1) { *why = "full_jacobian must be 0 or 1"; return MG_EINVAL; }
   if (p->max_corrections < 1 || p->max_corrections > 100) { *why = "max_corrections must be in 1..100"; return MG_EINVAL; }
+  if (p->line_smoother != 0 && p->line_smoother != 1) { *why = "line_smoother must be 0 or 1"; return MG_EINVAL; }
   if (p->pdl < 0 || p->pdl > PDL_ALL) { *why = "pdl: a combination of the PDL kernel-kind bits"; return MG_EINVAL; }
   if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
     *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";
@@ -987,7 +1001,8 @@ size_t mg_workspace_bytes(const mg_grid *g, const mg_params *p) {
   const int n = plan_levels(g->nr, g->nz, p->coarsest, lnr, lnz);
   mg_state tmp;
   Carver c{nullptr, 0};
-  carve(c, &tmp, n, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED);
+  carve(c, &tmp, n, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED,
+        p->line_smoother != 0);
   return c.off;
 }
 
@@ -1011,7 +1026,8 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
   int lnr[kMaxLevels], lnz[kMaxLevels];
   s->nlev = plan_levels(g->nr, g->nz, p->coarsest, lnr, lnz);
   Carver sizer{nullptr, 0};
-  carve(sizer, s, s->nlev, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED);
+  carve(sizer, s, s->nlev, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED,
+        p->line_smoother != 0);
   const size_t need = sizer.off;
   if (workspace) {
     if (workspace_bytes < need || ((uintptr_t)workspace & (kAlign - 1))) {
@@ -1032,7 +1048,8 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     return MG_ECUDA;
   }
   Carver c{(char *)s->ws, 0};
-  carve(c, s, s->nlev, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED);
+  carve(c, s, s->nlev, lnr, lnz, p->table ? p->table_rows : 0, p->precision == MG_MIXED,
+        p->line_smoother != 0);
   int rc = MG_OK;
   // zero everything once (electrode rows of du stay zero forever)
   if (cudaMemsetAsync(s->ws, 0, need, s->stream) != cudaSuccess) rc = fail(s, MG_ECUDA, "memset workspace");

@@ -203,6 +203,8 @@ cudaError_t launch_full_defect(const Level &L, const StateView &sv, const Transp
                                double *const d[3], double *partials, unsigned *counter, double *out3, cudaStream_t st);
 cudaError_t launch_add_transport(const Level &L, const StateView &sv, const Transport &tr, const double *w,
                                  double *out[3], cudaStream_t st);
+template <typename T>
+cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st);
 cudaError_t launch_add3(double *const acc[3], double *const x[3], size_t n, cudaStream_t st);
 cudaError_t launch_split_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);
 cudaError_t launch_join_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);

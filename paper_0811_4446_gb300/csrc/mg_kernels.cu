@@ -791,6 +791,95 @@ cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx
 template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t, int, int);
 template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t, int, int);
 
+// ------------------------------------------------------------------------------------------
+// z-line Gauss-Seidel, zebra order (even columns, then odd): one thread per column of the
+// parity solves the column's block-tridiagonal system (rows 1 .. nz-1, 3x3 blocks of eq. 14)
+// exactly by block elimination, its r-neighbours (the other parity) held at their current
+// values.  Row j:  Lo_j x_{j-1} + D_j x_j + Up_j x_{j+1} = f_j - (E and W couplings),
+// D_j = [[a11, 0, a13], [0, a22, a23], [-ak, ak, a33]], Up_j / Lo_j the north / south face
+// blocks [[-c_xe, 0, c_ve], [0, -c_xp, c_vp], [0, 0, g]] (c_x = cF towards the north
+// neighbour, cG towards the south one).  Forward: M_j = D_j - Lo_j C_{j-1}, C_j = M_j^-1 Up_j,
+// y_j = M_j^-1 (rhs_j - Lo_j y_{j-1}) (kept in scr, 12 planes of (nz+1) x cstride);
+// backward: x_j = y_j - C_j x_{j+1}, the electrode rows held at zero.
+
+// inverse of a general 3x3 matrix (row-major) by its cofactors
+template <typename T>
+__device__ __forceinline__ void inv3(const T (&m)[9], T (&r)[9]) {
+  const T c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+  const T id = T(1) / (m[0] * c00 + m[1] * c01 + m[2] * c02);
+  r[0] = c00 * id; r[1] = (m[2] * m[7] - m[1] * m[8]) * id; r[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+  r[3] = c01 * id; r[4] = (m[0] * m[8] - m[2] * m[6]) * id; r[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+  r[6] = c02 * id; r[7] = (m[1] * m[6] - m[0] * m[7]) * id; r[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+}
+
+template <typename T>
+__global__ void k_zline(LevelT<T> L, int color, T *scr, int cstride) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = 2 * t + color;
+  if (i >= L.ni) return;
+  const int P = L.P, nz = L.nz;
+  const size_t plane = (size_t)(nz + 1) * cstride;
+  auto S = [&](int q, int j) -> T & { return scr[q * plane + (size_t)j * cstride + t]; };
+  T Cp[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}, yp[3] = {T(0), T(0), T(0)};
+  for (int j = 1; j < nz; ++j) {
+    const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
+    const SplitNb d = split_nb(P, i, j);
+    T re = L.f[NE][d.self], rp = L.f[NP][d.self], rV = L.f[NV][d.self];
+    acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], L.du[NE][d.E],
+             L.du[NP][d.E], L.du[NV][d.E]);
+    acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], L.du[NE][d.W],
+             L.du[NP][d.W], L.du[NV][d.W]);
+    const T ak = L.Ak[k];
+    T M[9] = {L.dia[DA11][k], T(0), L.fac[FA13][d.self], T(0), L.dia[DA22][k], L.fac[FA23][d.self], -ak, ak,
+              L.dia[DA33][k]};
+    // south block (nonzeros l00, l02, l11, l12, l22) times the previous row's C and y
+    const T l00 = -L.cz[CGE][kS], l02 = L.cz[CVE][kS], l11 = -L.cz[CGP][kS], l12 = L.cz[CVP][kS], l22 = L.gZ[kS];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      M[c] -= l00 * Cp[c] + l02 * Cp[6 + c];
+      M[3 + c] -= l11 * Cp[3 + c] + l12 * Cp[6 + c];
+      M[6 + c] -= l22 * Cp[6 + c];
+    }
+    re -= l00 * yp[0] + l02 * yp[2];
+    rp -= l11 * yp[1] + l12 * yp[2];
+    rV -= l22 * yp[2];
+    T Mi[9];
+    inv3(M, Mi);
+    // north block (nonzeros u00, u02, u11, u12, u22)
+    const T u00 = -L.cz[CFE][k], u02 = L.cz[CVE][k], u11 = -L.cz[CFP][k], u12 = L.cz[CVP][k], u22 = L.gZ[k];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      Cp[3 * r] = Mi[3 * r] * u00;
+      Cp[3 * r + 1] = Mi[3 * r + 1] * u11;
+      Cp[3 * r + 2] = Mi[3 * r] * u02 + Mi[3 * r + 1] * u12 + Mi[3 * r + 2] * u22;
+      yp[r] = Mi[3 * r] * re + Mi[3 * r + 1] * rp + Mi[3 * r + 2] * rV;
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) S(q, j) = Cp[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S(9 + q, j) = yp[q];
+  }
+  T xn[3] = {T(0), T(0), T(0)};
+  for (int j = nz - 1; j >= 1; --j) {
+    T x[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[r] = S(9 + r, j) - (S(3 * r, j) * xn[0] + S(3 * r + 1, j) * xn[1] + S(3 * r + 2, j) * xn[2]);
+    const size_t kd = cidx(P, i, j);
+    L.du[NE][kd] = x[0]; L.du[NP][kd] = x[1]; L.du[NV][kd] = x[2];
+    xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
+  }
+}
+
+template <typename T>
+cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st) {
+  const int cstride = (L.nr + 2) / 2, n = (L.ni - color + 1) / 2;
+  k_zline<T><<<(n + 63) / 64, 64, 0, st>>>(L, color, scr, cstride);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_zline<double>(const LevelT<double> &, int, double *, cudaStream_t);
+template cudaError_t launch_zline<float>(const LevelT<float> &, int, float *, cudaStream_t);
+
 // K3 fused: one full red-black sweep per launch.  A block owns a TX x TY tile of nodes.
 // Phase 1 updates the red nodes of the tile and of a one-node ring around it (ring nodes are
 // also updated by the neighbouring tiles, with identical inputs and arithmetic), keeping them

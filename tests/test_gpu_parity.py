@@ -163,6 +163,42 @@ def test_linear_solve_parity(mg, n, table, dt):
     assert np.allclose(hg[:k], ho[:k], rtol=1e-5, atol=1e-14)
 
 
+@pytest.mark.parametrize("n,R,table,precision", [(32, 1e-2, False, "fp64"), (64, 1e-1, True, "fp64"),
+                                                 (32, 1e-1, False, "mixed"), (16, 1e-2, True, "fp64")])
+def test_line_smoother_linear_solve_parity(mg, n, R, table, precision):
+    """f1: linear solves with the z-line zebra smoother on every level (block-tridiagonal
+    column solves on the GPU, exact sparse column solves in the oracle): the oracle's residual
+    history cycle by cycle and its solution; on the strongly z-coupled grid (R = 10 d) far
+    fewer cycles than the point smoother."""
+    d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=table, R=R)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    dt = 1e-7
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, dt, phys, with_terms=True)
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    s = mg.from_discharge(d, precision=prec, line_smoother=1)
+    s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+    eta = 1e-12 if precision == "fp64" else 1e-10
+    xg, hg, rc = s.linear_solve(dt, list(-F), eta, 200)
+    assert rc == mg.MG_OK
+    H = omg.Hierarchy(g, u, dt, phys, line=True)
+    x, ho = H.solve(disc.to_vec(g, -F), eta, 200, scale=tn)
+    xo = disc.from_vec(g, x)
+    tol = 1e-10 if precision == "fp64" else 1e-7
+    for q in range(3):
+        assert np.abs(xg[q] - xo[q]).max() <= tol * np.abs(xo[q]).max(), q
+    if precision == "fp64":
+        assert abs(len(hg) - len(ho)) <= 1
+        k = min(len(hg), len(ho), 6)
+        assert np.allclose(hg[:k], ho[:k], rtol=1e-5, atol=1e-14)
+    if R >= 1e-1:
+        sp_ = mg.from_discharge(d, precision=prec)
+        sp_.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+        _, hp, _ = sp_.linear_solve(dt, list(-F), eta, 200)
+        assert len(hg) * 2 < len(hp), (len(hg), len(hp))
+
+
 def test_transient_33_ten_steps_parity(mg):
     d = W.transient_33()
     g, phys = _oracle(d)
