@@ -870,10 +870,133 @@ __global__ void k_zline(LevelT<T> L, int color, T *scr, int cstride) {
   }
 }
 
+// The same column solves by parallel cyclic reduction: one CTA per column, thread t owns row
+// t + 1.  Each round (h = 1, 2, 4, ...) every row publishes D^-1 [Lo | Up | r] (21 values) in
+// shared memory and folds in its neighbours h rows away:
+//   D <- D - Lo (D^-1 Up)_{j-h} - Up (D^-1 Lo)_{j+h},  r <- r - Lo (D^-1 r)_{j-h} - Up (D^-1 r)_{j+h},
+//   Lo <- -Lo (D^-1 Lo)_{j-h},  Up <- -Up (D^-1 Up)_{j+h},
+// so the couplings move 2h rows away; after log2(nz) rounds the rows are decoupled and
+// x_j = D_j^-1 r_j.  Rows past the column ends couple to the electrode rows (x = 0) and are
+// dropped.  nz threads (a power of two, up to 512).
+template <typename T>
+__device__ __forceinline__ void mm3(const T (&a)[9], const T *b, T (&c)[9]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) c[3 * r + q] = a[3 * r] * b[q] + a[3 * r + 1] * b[3 + q] + a[3 * r + 2] * b[6 + q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_zline_pcr(LevelT<T> L, int color) {
+  extern __shared__ __align__(16) unsigned char zl_smem[];
+  T *X = reinterpret_cast<T *>(zl_smem);  // [21][nz]
+  const int nz = L.nz, P = L.P, tid = threadIdx.x;
+  const int i = 2 * blockIdx.x + color;
+  const int j = tid + 1;
+  const bool row = j < nz;
+  T D[9], Lo[9], Up[9], r[3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) { D[q] = T(0); Lo[q] = T(0); Up[q] = T(0); }
+  r[0] = r[1] = r[2] = T(0);
+  if (row) {
+    const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
+    const SplitNb d = split_nb(P, i, j);
+    T re = L.f[NE][d.self], rp = L.f[NP][d.self], rV = L.f[NV][d.self];
+    acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], L.du[NE][d.E],
+             L.du[NP][d.E], L.du[NV][d.E]);
+    acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], L.du[NE][d.W],
+             L.du[NP][d.W], L.du[NV][d.W]);
+    r[0] = re; r[1] = rp; r[2] = rV;
+    const T ak = L.Ak[k];
+    D[0] = L.dia[DA11][k]; D[2] = L.fac[FA13][d.self];
+    D[4] = L.dia[DA22][k]; D[5] = L.fac[FA23][d.self];
+    D[6] = -ak; D[7] = ak; D[8] = L.dia[DA33][k];
+    if (j > 1) {
+      Lo[0] = -L.cz[CGE][kS]; Lo[2] = L.cz[CVE][kS]; Lo[4] = -L.cz[CGP][kS]; Lo[5] = L.cz[CVP][kS];
+      Lo[8] = L.gZ[kS];
+    }
+    if (j < nz - 1) {
+      Up[0] = -L.cz[CFE][k]; Up[2] = L.cz[CVE][k]; Up[4] = -L.cz[CFP][k]; Up[5] = L.cz[CVP][k]; Up[8] = L.gZ[k];
+    }
+  }
+  for (int h = 1; h < nz; h <<= 1) {
+    if (row) {
+      T Di[9], t9[9];
+      inv3(D, Di);
+      mm3(Di, Lo, t9);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) X[q * nz + j] = t9[q];
+      mm3(Di, Up, t9);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) X[(9 + q) * nz + j] = t9[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) X[(18 + q) * nz + j] = Di[3 * q] * r[0] + Di[3 * q + 1] * r[1] + Di[3 * q + 2] * r[2];
+    }
+    __syncthreads();
+    if (row) {
+      const int m = j - h, p = j + h;
+      T nLo[9], nUp[9], a9[9], b9[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) { nLo[q] = T(0); nUp[q] = T(0); }
+      if (m >= 1) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { a9[q] = X[q * nz + m]; b9[q] = X[(9 + q) * nz + m]; }
+        T c9[9];
+        mm3(Lo, b9, c9);  // Lo (D^-1 Up)_m
+#pragma unroll
+        for (int q = 0; q < 9; ++q) D[q] -= c9[q];
+        mm3(Lo, a9, c9);  // Lo (D^-1 Lo)_m
+#pragma unroll
+        for (int q = 0; q < 9; ++q) nLo[q] = -c9[q];
+        const T y0 = X[18 * nz + m], y1 = X[19 * nz + m], y2 = X[20 * nz + m];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r[q] -= Lo[3 * q] * y0 + Lo[3 * q + 1] * y1 + Lo[3 * q + 2] * y2;
+      }
+      if (p < nz) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { a9[q] = X[q * nz + p]; b9[q] = X[(9 + q) * nz + p]; }
+        T c9[9];
+        mm3(Up, a9, c9);  // Up (D^-1 Lo)_p
+#pragma unroll
+        for (int q = 0; q < 9; ++q) D[q] -= c9[q];
+        mm3(Up, b9, c9);  // Up (D^-1 Up)_p
+#pragma unroll
+        for (int q = 0; q < 9; ++q) nUp[q] = -c9[q];
+        const T y0 = X[18 * nz + p], y1 = X[19 * nz + p], y2 = X[20 * nz + p];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r[q] -= Up[3 * q] * y0 + Up[3 * q + 1] * y1 + Up[3 * q + 2] * y2;
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) { Lo[q] = nLo[q]; Up[q] = nUp[q]; }
+    }
+    __syncthreads();
+  }
+  if (row) {
+    T Di[9];
+    inv3(D, Di);
+    const size_t kd = cidx(P, i, j);
+    L.du[NE][kd] = Di[0] * r[0] + Di[1] * r[1] + Di[2] * r[2];
+    L.du[NP][kd] = Di[3] * r[0] + Di[4] * r[1] + Di[5] * r[2];
+    L.du[NV][kd] = Di[6] * r[0] + Di[7] * r[1] + Di[8] * r[2];
+  }
+}
+
 template <typename T>
 cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st) {
-  const int cstride = (L.nr + 2) / 2, n = (L.ni - color + 1) / 2;
-  k_zline<T><<<(n + 63) / 64, 64, 0, st>>>(L, color, scr, cstride);
+  const int n = (L.ni - color + 1) / 2;
+  if (n <= 0) return cudaSuccess;
+  if (L.nz <= 512 && (L.nz & (L.nz - 1)) == 0) {
+    const size_t smem = (size_t)21 * L.nz * sizeof(T);
+    static bool raised = false;  // the 512-row FP64 case needs 86 KB of dynamic shared memory
+    if (!raised && smem > 48 * 1024) {
+      cudaFuncSetAttribute(k_zline_pcr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 21 * 512 * (int)sizeof(T));
+      raised = true;
+    }
+    k_zline_pcr<T><<<n, L.nz, smem, st>>>(L, color);
+  } else {
+    const int cstride = (L.nr + 2) / 2;
+    k_zline<T><<<(n + 63) / 64, 64, 0, st>>>(L, color, scr, cstride);
+  }
   count_launch();
   return cudaGetLastError();
 }
