@@ -64,10 +64,13 @@ struct mg_state {
   double *partials;
   size_t partials_cap;   // doubles
   unsigned *counter;
-  double *dout;          // device outputs of reductions (16 doubles)
-  double *hout;          // pinned host mirror (16 doubles)
+  double *dout;          // device outputs of reductions (24 doubles)
+  double *hout;          // pinned host mirror (24 doubles)
   double *M, *Minv, *rs, *cs;
   double *fj_f[3], *fj_d[3];  // full-Jacobian Newton: saved right-hand side and accumulated step
+  double *fss[3];             // -F of the steady rows at the current state (a march step's first f)
+  double start_sums[16];      // the residual sums of that launch (see k_resid_coef)
+  bool start_valid = false;   // fss and start_sums describe the current state of the march level
   double *line_scr;           // z-line smoother: 12 planes of (nz + 1) x (nr + 2) / 2 of the finest level
   int *flag;
   double *table_d;
@@ -199,10 +202,10 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
       }
     }
   }
-  s->partials_cap = 12 * max_blocks(lnr[0], lnz[0]) + 64;
+  s->partials_cap = 16 * max_blocks(lnr[0], lnz[0]) + 64;
   s->partials = c.take<double>(s->partials_cap);
   s->counter = c.take<unsigned>(4);
-  s->dout = c.take<double>(16);
+  s->dout = c.take<double>(24);
   s->M = c.take<double>((size_t)kMaxCoarse * kMaxCoarse);
   s->Minv = c.take<double>((size_t)kMaxCoarse * kMaxCoarse);
   s->rs = c.take<double>(kMaxCoarse);
@@ -216,6 +219,7 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
   {
     const size_t n0 = (size_t)(lnz[0] + 1) * pitch_of(lnr[0]);
     for (int q = 0; q < 3; ++q) { s->fj_f[q] = c.take<double>(n0); s->fj_d[q] = c.take<double>(n0); }
+    for (int q = 0; q < 3; ++q) s->fss[q] = c.take<double>(n0);
   }
   s->line_scr = line ? c.take<double>((size_t)12 * (lnz[0] + 1) * ((lnr[0] + 2) / 2)) : nullptr;
 }
@@ -293,7 +297,8 @@ int residual_launch(mg_state *s, int l0, double dt, bool write_f, double *Fout[3
   LevelBuf &b = s->lv[l0];
   ProfScope ps(s, MG_PROF_RESIDUAL, l0);
   if (with_coef) CK(launch_coef(b.L, b.sv, s->tr, s->stream));
-  CK(launch_resid_coef(b.L, b.sv, dt, write_f, steady_too, Fout, s->partials, s->counter, s->dout, s->stream));
+  CK(launch_resid_coef(b.L, b.sv, dt, write_f, steady_too, Fout, steady_too ? s->fss : nullptr, s->partials,
+                       s->counter, s->dout, s->stream));
   return MG_OK;
 }
 
@@ -313,6 +318,29 @@ int residual(mg_state *s, int l0, double dt, bool write_f, double *Fout[3], doub
   if (rc || (rc = sync_read(s, 6))) return rc;
   residual_norms(s, rho, tn);
   return MG_OK;
+}
+
+// Start data of a march step at the current state of level l0 (the steady rows' -F in fss and
+// the sums of k_resid_coef in start_sums), from one residual launch; with_coef as in
+// residual_launch.
+int start_data(mg_state *s, int l0, bool with_coef) {
+  int rc = residual_launch(s, l0, 0.0, false, nullptr, with_coef, true);
+  if (rc || (rc = sync_read(s, 16))) return rc;
+  for (int q = 0; q < 16; ++q) s->start_sums[q] = s->hout[q];
+  s->start_valid = true;
+  return MG_OK;
+}
+
+// rho[3] and tn[3] of a step of length dt that starts from the state start_sums describe (its F
+// is the steady one; its e and p term norms gain the time terms t / dt).
+void start_norms(const mg_state *s, double dt, double rho[3], double tn[3]) {
+  const double *S = s->start_sums, c = 1.0 / dt;
+  const double t2[3] = {S[9] + 2.0 * c * S[12] + c * c * S[13], S[10] + 2.0 * c * S[14] + c * c * S[15], S[11]};
+  for (int q = 0; q < 3; ++q) {
+    const double fn = std::sqrt(S[6 + q]), t = std::sqrt(t2[q]);
+    tn[q] = t;
+    rho[q] = fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
+  }
 }
 
 // Coefficients on levels l0..nlev-1 at the state of l0 injected downward; coarsest inverse.
@@ -695,8 +723,10 @@ int full_jacobian_correct(mg_state *s, int l0, double eta, const double tn[3], d
 
 // steady_rho (may be NULL): on acceptance after at least one Newton iteration, the steady
 // residual of the new state (from the same residual launch), else -1.
+// use_start: the state's start data (start_data, or the last residual launch of the previous
+// accepted step) stand in for the step's first residual launch (coefficients current too).
 int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_current = false,
-         double *steady_rho = nullptr) {
+         double *steady_rho = nullptr, bool use_start = false) {
   LevelBuf &b = s->lv[l0];
   copy_state_async(s, l0, true);
   CK(cudaGetLastError());
@@ -706,20 +736,32 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
   double rho[3], tn[3];
   if (steady_rho) *steady_rho = -1.0;
   double rho_steady[3] = {-1.0, -1.0, -1.0};
-  rc = residual(s, l0, dt, true, nullptr, rho, tn, !coef_current);
-  if (rc) return rc;
+  double cand[16];
+  if (use_start && s->start_valid) {
+    start_norms(s, dt, rho, tn);
+    for (int q = 0; q < 3; ++q)
+      CK(cudaMemcpyAsync(b.L.f[q], s->fss[q], b.nodes * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  } else {
+    rc = residual(s, l0, dt, true, nullptr, rho, tn, !coef_current);
+    if (rc) return rc;
+  }
   for (int it = 0; it <= s->prm.max_newton; ++it) {
     for (int q = 0; q < 3; ++q) s->stats.rho[q] = rho[q];
     const double rmax = std::max(rho[0], std::max(rho[1], rho[2]));
     if (!(rmax == rmax) || std::isinf(rmax)) { reason = MG_ENONFINITE; *newton_out = it; break; }
     if (rmax <= tol) {
       if (steady_rho && it > 0) *steady_rho = std::max(rho_steady[0], std::max(rho_steady[1], rho_steady[2]));
+      if (it > 0) {  // the accepted state's start data come from its residual launch
+        for (int q = 0; q < 16; ++q) s->start_sums[q] = cand[q];
+        s->start_valid = true;
+      }
       *newton_out = it;
       s->stats.newton_iterations += it;
       s->stats.last_newton = it;
       return MG_OK;
     }
     if (it == s->prm.max_newton) { *newton_out = it; break; }
+    s->start_valid = false;  // this iteration's residual launch overwrites fss and the sums
     rc = build_hierarchy(s, l0, dt);
     if (rc) return rc;
     int ncyc;
@@ -745,19 +787,20 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
         ncyc += nc2;
       }
     }
-    // u += du (max |dV| and the non-finite flag into dout[12..13]), then the residual at the new
-    // state (into dout[0..5], its steady rows' sums into dout[6..11]); used only if the update
-    // is accepted
-    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout + 12, s->stream));
+    // u += du (max |dV| and the non-finite flag into dout[16..17]), then the residual at the new
+    // state (into dout[0..5], its steady rows' sums and start data into dout[6..15] and fss);
+    // used only if the update is accepted
+    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout + 16, s->stream));
     if ((rc = residual_launch(s, l0, dt, true, nullptr, true, true))) return rc;
-    rc = sync_read(s, 14);
+    rc = sync_read(s, 18);
     if (rc) return rc;
     if (graph && !full) linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
     s->stats.vcycles += ncyc;
     if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
-    if (s->hout[13] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
-    if (s->hout[12] > limit) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
+    if (s->hout[17] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
+    if (s->hout[16] > limit) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
     residual_norms(s, rho, tn);
+    for (int q = 0; q < 16; ++q) cand[q] = s->hout[q];
     for (int q = 0; q < 3; ++q) {
       const double fn = std::sqrt(s->hout[6 + q]), t = std::sqrt(s->hout[9 + q]);
       rho_steady[q] = fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
@@ -779,19 +822,27 @@ int march(mg_state *s, int l0, double dt_start, double tol) {
   const double ntol = s->prm.newton_tol > 0.0 ? s->prm.newton_tol : 0.1 * tol;
   const double rel = s->prm.newton_tol_rel;
   bool coef_current = false;  // face coefficients of level l0 at the current state
-  double r_start = 0.0;       // steady residual of the current state (used when rel > 0)
-  if (rel > 0.0) {
-    double rho[3];
-    const int rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr, true);
+  double r_start = 0.0;       // steady residual of the current state
+  auto steady_of_start = [&]() {  // the steady residual of the start state
+    double m = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double fn = std::sqrt(s->start_sums[6 + q]), t = std::sqrt(s->start_sums[9 + q]);
+      m = std::max(m, fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY));
+    }
+    return m;
+  };
+  // one residual launch gives the first step's residual and the steady residual of the start
+  {
+    const int rc = start_data(s, l0, true);
     if (rc) return rc;
     coef_current = true;
-    r_start = std::max(rho[0], std::max(rho[1], rho[2]));
+    r_start = steady_of_start();
   }
   for (int n = 0; n < s->prm.max_steps; ++n) {
     int newton = 0;
     const double step_tol = std::max(ntol, rel * r_start);
     double r_step = -1.0;
-    int rc = step(s, l0, dt, step_tol, &newton, coef_current, &r_step);
+    int rc = step(s, l0, dt, step_tol, &newton, coef_current, &r_step, true);
     coef_current = false;
     if (rc == MG_ECUDA) return rc;
     s->stats.dt_last = dt;
@@ -803,10 +854,9 @@ int march(mg_state *s, int l0, double dt_start, double tol) {
       // (after at least one Newton iteration), otherwise evaluate them here
       double r = r_step;
       if (r < 0.0) {
-        double rho[3];
-        rc = residual(s, l0, 0.0, false, nullptr, rho, nullptr, false);
-        if (rc) return rc;
-        r = std::max(rho[0], std::max(rho[1], rho[2]));
+        // accepted without a Newton iteration: the state is the start state
+        if (!s->start_valid && (rc = start_data(s, l0, false))) return rc;
+        r = steady_of_start();
       }
       coef_current = true;
       s->stats.steady_rho = r;
@@ -1040,7 +1090,7 @@ int mg_create(const mg_grid *g, const mg_params *p, void *stream, void *workspac
     s->owns_ws = true;
   }
   s->ws_bytes = need;
-  if (cudaMallocHost(&s->hout, 16 * sizeof(double)) != cudaSuccess ||
+  if (cudaMallocHost(&s->hout, 24 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&s->hctl, sizeof(SolveCtl)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     if (s->owns_ws) cudaFree(s->ws);

@@ -144,7 +144,8 @@ cudaError_t launch_coef(const Level &L, const StateView &sv, const Transport &tr
 // Residual rows from the face coefficients of the same state (launch_coef first): F, f = -F and
 // the norms as launch_residual, without re-evaluating the Scharfetter-Gummel faces.
 cudaError_t launch_resid_coef(const Level &L, const StateView &sv, double dt, bool write_f, bool steady_too,
-                              double *Fout[3], double *partials, unsigned *counter, double *out, cudaStream_t st);
+                              double *Fout[3], double *const fsteady[3], double *partials, unsigned *counter,
+                              double *out, cudaStream_t st);
 // Hierarchy set-up over levels of the device LevelSet in one launch each (L0 = the level whose
 // dimensions size the grid): injection of the state of level l0 into levels l0+1 .. l1, face
 // coefficients of levels a .. b, diagonal factors (and, mixed, the FP32 coefficient copies) of

@@ -442,13 +442,18 @@ cudaError_t launch_inject_levels(const LevelSet *S, const Level &L0, int l0, int
 // face is cG n_L - cF n_R (cG = g D G(alpha), cF = g D F(alpha)), the Poisson flux g dV.
 // The steady rows (sources, fluxes, space charge) are summed first and the time-derivative
 // terms added last, so with steady_too the same launch also reduces the steady rows' sums
-// (into out[6..11]), equal bit for bit to a launch with dt_inv = 0.
+// (into out[6..11]), equal bit for bit to a launch with dt_inv = 0, writes -F of the steady
+// rows (colour-split) into fs, and reduces sum(Ts t) and sum(t^2) of both continuity rows
+// (out[12..15]), t = A (|n| + |n|): the residual of a step that starts from this state (u_old
+// = u, so the time term of F vanishes) has the steady F, and its term norms follow for any dt
+// from sum((Ts + t / dt)^2) = sum(Ts^2) + 2 sum(Ts t) / dt + sum(t^2) / dt^2.
 __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, double dt_inv, int write_f,
                                                          int steady_too, double *F0, double *F1, double *F2,
-                                                         double *partials, unsigned *counter, double *out) {
+                                                         double *fs0, double *fs1, double *fs2, double *partials,
+                                                         unsigned *counter, double *out) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * CBY + threadIdx.y + 1;
-  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (i < L.ni && j < L.nz) {
     const int P = L.P;
     const size_t k = (size_t)j * P + i;
@@ -475,6 +480,14 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
     TV += ak * (fabs(np[k]) + fabs(ne[k]));
     acc[6] = Fe * Fe; acc[7] = Fp * Fp; acc[8] = FV * FV;
     acc[9] = Te * Te; acc[10] = Tp * Tp; acc[11] = TV * TV;
+    if (steady_too) {
+      const double te = A * (fabs(ne[k]) + fabs(ne[k])), tp = A * (fabs(np[k]) + fabs(np[k]));
+      acc[12] = Te * te; acc[13] = te * te; acc[14] = Tp * tp; acc[15] = tp * tp;
+      if (fs0) {
+        const size_t kf = cidx(P, i, j);
+        fs0[kf] = -Fe; fs1[kf] = -Fp; fs2[kf] = -FV;
+      }
+    }
     if (dt_inv > 0.0) {
       Fe += A * (ne[k] - sv.uold[NE][k]) * dt_inv;
       Fp += A * (np[k] - sv.uold[NP][k]) * dt_inv;
@@ -490,7 +503,7 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
     acc[3] = Te * Te; acc[4] = Tp * Tp; acc[5] = TV * TV;
   }
   if (steady_too) {
-    reduce_finish<12>(acc, partials, counter, out, 0);
+    reduce_finish<16>(acc, partials, counter, out, 0);
   } else {
     double a6[6] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5]};
     reduce_finish<6>(a6, partials, counter, out, 0);
@@ -498,11 +511,13 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
 }
 
 cudaError_t launch_resid_coef(const Level &L, const StateView &sv, double dt, bool write_f, bool steady_too,
-                              double *Fout[3], double *partials, unsigned *counter, double *out, cudaStream_t st) {
+                              double *Fout[3], double *const fsteady[3], double *partials, unsigned *counter,
+                              double *out, cudaStream_t st) {
   dim3 b(32, CBY), g((L.nr + 1 + 31) / 32, (L.nz - 1 + CBY - 1) / CBY);
   k_resid_coef<<<g, b, 0, st>>>(L, sv, dt > 0 ? 1.0 / dt : 0.0, write_f ? 1 : 0, steady_too ? 1 : 0,
                                 Fout ? Fout[0] : nullptr, Fout ? Fout[1] : nullptr, Fout ? Fout[2] : nullptr,
-                                partials, counter, out);
+                                fsteady ? fsteady[0] : nullptr, fsteady ? fsteady[1] : nullptr,
+                                fsteady ? fsteady[2] : nullptr, partials, counter, out);
   count_launch();
   return cudaGetLastError();
 }
