@@ -1,6 +1,7 @@
 // Internal declarations of the learned-initial-guess network kernels (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -32,6 +33,14 @@ cudaError_t launch_conv(const ConvArgs &a, int mode, int splits, cudaStream_t st
 // tcgen05 / TMEM path (forward and data gradient with 16 <= N <= 256, N % 16 == 0)
 bool conv_tc_supported(const ConvArgs &a, int mode);
 cudaError_t launch_conv_tc(const ConvArgs &a, int mode, int *err, cudaStream_t st);
+// TMA-fed tcgen05 path (forward 3x3 stride-1 convolutions whose input parts have a multiple
+// of 32 channels): tensor maps of the two input parts and of the weight matrix
+struct ConvMaps {
+  CUtensorMap x1, x2, w;
+};
+bool conv_tma_supported(const ConvArgs &a, int mode);
+int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
+cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st);
 cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
                             cudaStream_t st);
 cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st);

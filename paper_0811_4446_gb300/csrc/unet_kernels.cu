@@ -201,100 +201,140 @@ cudaError_t launch_conv(const ConvArgs &a, int mode, int splits, cudaStream_t st
 // ------------------------------------------------------------------------------------------
 // elementwise and reduction kernels
 
-// dPre = dOut * (out > 0) for ReLU layers (relu = 0: plain copy), converted to bf16.
-__global__ void k_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    float v = dout[i];
-    if (relu && !(__bfloat162float(out[i]) > 0.f)) v = 0.f;
-    dpre[i] = __float2bfloat16(v);
+// dPre = dOut * (out > 0) for ReLU layers (relu = 0: plain copy), converted to bf16; eight
+// consecutive elements per thread (n8 = n / 8, n a multiple of 8: whole 8-channel groups).
+__global__ void k_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n8, int relu) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 d0 = reinterpret_cast<const float4 *>(dout)[2 * i], d1 = reinterpret_cast<const float4 *>(dout)[2 * i + 1];
+    float v[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+    if (relu) {
+      const uint4 o = reinterpret_cast<const uint4 *>(out)[i];
+      const __nv_bfloat16 *ob = reinterpret_cast<const __nv_bfloat16 *>(&o);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (!(__bfloat162float(ob[e]) > 0.f)) v[e] = 0.f;
+    }
+    uint32_t pk[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      pk[e] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    reinterpret_cast<uint4 *>(dpre)[i] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
 cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
                             cudaStream_t st) {
-  k_relu_bwd<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(dout, out, dpre, n, relu);
+  if (n % 8) return cudaErrorInvalidValue;
+  const size_t n8 = n / 8;
+  k_relu_bwd<<<(unsigned)std::min<size_t>((n8 + 255) / 256, 152 * 16), 256, 0, st>>>(dout, out, dpre, n8, relu);
   return cudaGetLastError();
 }
 
-// db[c] += sum over pixels of dpre[p][c] for c < Creal (C = channel stride); blocks of 32
-// channels x 8 pixel rows, pixel-strided.
-__global__ void k_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal) {
-  const int c = blockIdx.y * 32 + threadIdx.x;
-  float s = 0.f;
-  if (c < Creal)
-    for (int p = blockIdx.x * blockDim.y + threadIdx.y; p < P; p += gridDim.x * blockDim.y)
-      s += __bfloat162float(dpre[(size_t)p * C + c]);
-  __shared__ float sh[8][33];
-  sh[threadIdx.y][threadIdx.x] = s;
+// db[c] += sum over pixels of dpre[p][c] for c < Creal (C = channel stride, a multiple of 8,
+// at most 256).  A thread sums the 8 channels of one 16-byte group over a pixel-strided set of
+// rows; the block adds its rows up in shared memory and makes one atomic add per channel.
+__global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal) {
+  const int G = C / 8, rows = 256 / G;
+  const int g = threadIdx.x % G, r = threadIdx.x / G;
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (r < rows)
+    for (int p = blockIdx.x * rows + r; p < P; p += gridDim.x * rows) {
+      const uint4 q = *reinterpret_cast<const uint4 *>(dpre + (size_t)p * C + 8 * g);
+      const __nv_bfloat16 *hq = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) s[e] += __bfloat162float(hq[e]);
+    }
+  __shared__ float sh[256][9];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) sh[threadIdx.x][e] = s[e];
   __syncthreads();
-  if (threadIdx.y == 0 && c < Creal) {
+  if ((int)threadIdx.x < Creal) {
+    const int c = threadIdx.x, gg = c / 8, e = c % 8;
     float t = 0.f;
-    for (int r = 0; r < blockDim.y; ++r) t += sh[r][threadIdx.x];
+    for (int rr = 0; rr < rows; ++rr) t += sh[rr * G + gg][e];
     atomicAdd(&db[c], t);
   }
 }
 
 cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st) {
-  dim3 b(32, 8), g(std::min(256, (P + 7) / 8), (C + 31) / 32);
-  k_bias_grad<<<g, b, 0, st>>>(dpre, db, P, C, Creal);
+  if (C % 8 || C > 256 || Creal > C) return cudaErrorInvalidValue;
+  const int rows = 256 / (C / 8);
+  k_bias_grad<<<std::max(1, std::min(152 * 4, (P + rows - 1) / rows)), 256, 0, st>>>(dpre, db, P, C, Creal);
   return cudaGetLastError();
 }
 
-// Node-aligned bilinear upsampling of NHWC bf16: (h, w) -> (2h - 1, 2w - 1).
+// Node-aligned bilinear upsampling of NHWC bf16: (h, w) -> (2h - 1, 2w - 1); one 16-byte group
+// of 8 channels per thread (C a multiple of 8), 32-bit indices (host-checked).
 __global__ void k_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C) {
-  const int H = 2 * h - 1, W = 2 * w - 1;
-  const size_t n = (size_t)B * H * W * C;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % C;
-    size_t t = i / C;
-    const int x = t % W;
-    t /= W;
-    const int y = t % H;
-    const int b = t / H;
-    const int y0 = y >> 1, y1 = (y + 1) >> 1, x0 = x >> 1, x1 = (x + 1) >> 1;
-    auto at = [&](int yy, int xx) { return __bfloat162float(in[(((size_t)b * h + yy) * w + xx) * C + c]); };
-    const float v = 0.25f * (at(y0, x0) + at(y0, x1) + at(y1, x0) + at(y1, x1));
-    out[i] = __float2bfloat16(v);
+  const unsigned H = 2 * h - 1, W = 2 * w - 1, G = C / 8;
+  const unsigned n = (unsigned)B * H * W * G;
+  const uint4 *src = reinterpret_cast<const uint4 *>(in);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned g = i % G, t = i / G, x = t % W, t2 = t / W, y = t2 % H, b = t2 / H;
+    const unsigned y0 = y >> 1, y1 = (y + 1) >> 1, x0 = x >> 1, x1 = (x + 1) >> 1;
+    const uint4 q[4] = {src[((b * h + y0) * w + x0) * G + g], src[((b * h + y0) * w + x1) * G + g],
+                        src[((b * h + y1) * w + x0) * G + g], src[((b * h + y1) * w + x1) * G + g]};
+    const __nv_bfloat16 *hq = reinterpret_cast<const __nv_bfloat16 *>(q);
+    uint32_t pk[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float v[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int c = 2 * e + k;
+        v[k] = 0.25f * (__bfloat162float(hq[c]) + __bfloat162float(hq[8 + c]) + __bfloat162float(hq[16 + c]) +
+                        __bfloat162float(hq[24 + c]));
+      }
+      const __nv_bfloat162 hv = __floats2bfloat162_rn(v[0], v[1]);
+      pk[e] = *reinterpret_cast<const uint32_t *>(&hv);
+    }
+    reinterpret_cast<uint4 *>(out)[i] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
 cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C, cudaStream_t st) {
-  const size_t n = (size_t)B * (2 * h - 1) * (2 * w - 1) * C;
-  k_upsample<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(in, out, B, h, w, C);
+  const size_t n = (size_t)B * (2 * h - 1) * (2 * w - 1) * (C / 8);
+  if (C % 8 || n >= (1u << 31)) return cudaErrorInvalidValue;
+  k_upsample<<<(unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)), 256, 0, st>>>(in, out, B, h,
+                                                                                                      w, C);
   return cudaGetLastError();
 }
 
 // Transpose of the upsampling on FP32 gradients: dc[Y][X] += sum of fine gradients weighted
-// by the interpolation weights of node (Y, X).
+// by the interpolation weights of node (Y, X); four channels (one float4) per thread.
 __global__ void k_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C) {
-  const int H = 2 * h - 1, W = 2 * w - 1;
-  const size_t n = (size_t)B * h * w * C;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int c = i % C;
-    size_t t = i / C;
-    const int X = t % w;
-    t /= w;
-    const int Y = t % h;
-    const int b = t / h;
-    float s = 0.f;
+  const int H = 2 * h - 1, W = 2 * w - 1, G = C / 4;
+  const unsigned n = (unsigned)B * h * w * G;
+  const float4 *src = reinterpret_cast<const float4 *>(dfine);
+  float4 *dst = reinterpret_cast<float4 *>(dcoarse);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned g = i % G, t = i / G, X = t % w, t2 = t / w, Y = t2 % h, b = t2 / h;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int dy = -1; dy <= 1; ++dy) {
-      const int y = 2 * Y + dy;
+      const int y = 2 * (int)Y + dy;
       if (y < 0 || y >= H) continue;
       const float wy = dy == 0 ? 1.f : 0.5f;
       for (int dx = -1; dx <= 1; ++dx) {
-        const int x = 2 * X + dx;
+        const int x = 2 * (int)X + dx;
         if (x < 0 || x >= W) continue;
-        const float wx = dx == 0 ? 1.f : 0.5f;
-        s += wy * wx * dfine[(((size_t)b * H + y) * W + x) * C + c];
+        const float wt = wy * (dx == 0 ? 1.f : 0.5f);
+        const float4 f = src[(((unsigned)b * H + y) * W + x) * G + g];
+        s.x += wt * f.x; s.y += wt * f.y; s.z += wt * f.z; s.w += wt * f.w;
       }
     }
-    dcoarse[i] += s;
+    float4 d = dst[i];
+    d.x += s.x; d.y += s.y; d.z += s.z; d.w += s.w;
+    dst[i] = d;
   }
 }
 
 cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C, cudaStream_t st) {
-  const size_t n = (size_t)B * h * w * C;
-  k_upsample_bwd<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(dfine, dcoarse, B, h, w, C);
+  const size_t nf = (size_t)B * (2 * h - 1) * (2 * w - 1) * (C / 4), n = (size_t)B * h * w * (C / 4);
+  if (C % 4 || nf >= (1u << 31)) return cudaErrorInvalidValue;
+  k_upsample_bwd<<<(unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)), 256, 0, st>>>(
+      dfine, dcoarse, B, h, w, C);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,355 @@
+// tcgen05 convolutions of the learned-guess network fed by the Tensor Memory Accelerator.
+//
+// For the 3x3, stride-1 convolutions whose input parts have a multiple of 32 channels, the GEMM
+// rows are the output pixels in tiles of 16 x 8 pixels of one image (M = 128) and the columns all
+// output channels (N <= 128).  The reduction runs over (tap, input part, 32-channel chunk) in the
+// order of the weight matrix's K index (tap-major, then the channels of the concatenated inputs).
+// For each chunk one TMA tiled load brings the 16 x 8 input pixels shifted by the tap, 32
+// channels each, into shared memory (64-byte rows, 64-byte swizzle; coordinates outside the
+// image read zero, which is the convolution's padding) and one brings the N x 32 weight slice.
+//
+// The kernel is persistent (a CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...) and warp
+// specialised: lane 0 of warp 0 issues the TMA loads into an S-stage ring (mbarriers "full",
+// completed by the TMA byte count, and "empty", completed by tcgen05.commit once the MMAs that
+// read a stage are done); lane 0 of warp 1 issues tcgen05.mma (kind::f16, K = 16, two per chunk)
+// into one of two TMEM accumulators (columns [0, N) and [cols / 2, cols / 2 + N) of a
+// power-of-two allocation of at least 2N columns); warps 2-5 drain the other accumulator (tcgen05.ld, bias,
+// ReLU, bf16 stores) and hand it back ("acc_empty").  Every wait is bounded and also ends when
+// another role has given up; before the CTA leaves, the producer waits for its loads still in
+// flight and the MMA thread for its last MMAs, and warp 0 frees the TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+
+#include "unet_impl.cuh"
+
+namespace unk {
+
+namespace {
+
+constexpr int TM_X = 16, TM_Y = 8;     // output tile (x fastest): 128 GEMM rows
+constexpr int TM_CH = 32;              // channels per chunk: 64-byte rows
+constexpr int TM_MAXS = 8;             // most pipeline stages
+constexpr int TM_THREADS = 192;        // producer warp, MMA warp, 4 epilogue warps
+constexpr int TM_NMAX = 128;
+constexpr long kTmaWaitLimit = 1L << 22;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for the phase of the given parity; false after kTmaWaitLimit polls or once *abort is set
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort) {
+  for (long it = 0; it < kTmaWaitLimit; ++it) {
+    if (try_wait(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of 64 bytes, 8-row
+// groups 512 bytes apart.  Bits: [0,14) address >> 4, [16,30) LBO >> 4 (unused here),
+// [32,46) SBO >> 4, [46,48) descriptor version 1, [61,64) layout 4 = 64-byte swizzle.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t a) {
+  uint64_t d = 0;
+  d |= (uint64_t)((a >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
+__host__ __device__ constexpr uint32_t idesc_bf16_tma(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+struct TileGrid {
+  int tx, ty, per_img, ntiles;
+};
+
+__device__ __forceinline__ void tile_origin(const TileGrid &g, int t, int &x0, int &y0, int &b) {
+  b = t / g.per_img;
+  const int r = t - b * g.per_img;
+  y0 = (r / g.tx) * TM_Y;
+  x0 = (r % g.tx) * TM_X;
+}
+
+__global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__ CUtensorMap mx1,
+                                                         const __grid_constant__ CUtensorMap mx2,
+                                                         const __grid_constant__ CUtensorMap mw, ConvArgs a,
+                                                         TileGrid tg, int S, int tmem_cols, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int BN = a.N;
+  const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
+  const uint32_t a_bytes = TM_X * TM_Y * 64, st_bytes = a_bytes + (uint32_t)BN * 64;
+  __shared__ __align__(8) uint64_t full[TM_MAXS], empty[TM_MAXS], acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+  volatile int *abort = &abort_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_sh)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 32) {
+    abort_sh = 0;
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])) : "memory");
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&acc_full[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(saddr(&acc_empty[i])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mma_done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+
+  const int c1 = a.C1 / TM_CH, c2 = a.C2 / TM_CH, per_tap = c1 + c2;
+  const int nk = 9 * per_tap;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: TMA loads of every chunk of every tile of this CTA, in order
+    const uint64_t pm1 = reinterpret_cast<uint64_t>(&mx1), pm2 = reinterpret_cast<uint64_t>(&mx2),
+                   pmw = reinterpret_cast<uint64_t>(&mw);
+    long g = 0;  // chunks issued so far
+    for (int t = blockIdx.x; t < tg.ntiles && !*abort; t += gridDim.x) {
+      int x0, y0, b;
+      tile_origin(tg, t, x0, y0, b);
+      for (int k = 0; k < nk; ++k, ++g) {
+        const int s = (int)(g % S);
+        const uint32_t use = (uint32_t)(g / S);
+        if (use > 0 && !wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort)) break;
+        const int tap = k / per_tap, q = k - tap * per_tap;
+        const int kh = tap / 3, kw = tap - kh * 3;
+        const uint64_t mx = q < c1 ? pm1 : pm2;
+        const int cc = (q < c1 ? q : q - c1) * TM_CH;
+        const uint32_t sa = base + (uint32_t)s * st_bytes, sb = sa + a_bytes, bar = saddr(&full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+            ::"r"(sa), "l"(mx), "r"(cc), "r"(x0 + kw - 1), "r"(y0 + kh - 1), "r"(b), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(sb), "l"(pmw), "r"(tap * (a.C1 + a.C2) + q * TM_CH), "r"(0), "r"(bar)
+            : "memory");
+      }
+    }
+    // loads still in flight: the last min(S, g) issued, one per stage, each the latest on its stage
+    volatile int never = 0;
+    for (long j = g > S ? g - S : 0; j < g; ++j)
+      wait_bounded(saddr(&full[j % S]), (uint32_t)((j / S) & 1), &never);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = idesc_bf16_tma(TM_X * TM_Y, BN);
+    long g = 0;
+    int j = 0;  // tiles of this CTA so far
+    bool ok = true;
+    for (int t = blockIdx.x; t < tg.ntiles && ok; t += gridDim.x, ++j) {
+      const int ab = j & 1;
+      if (j >= 2 && !(ok = wait_bounded(saddr(&acc_empty[ab]), (uint32_t)(((j >> 1) - 1) & 1), abort))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc_t = tmem + (uint32_t)(ab * (tmem_cols >> 1));
+      for (int k = 0; k < nk; ++k, ++g) {
+        const int s = (int)(g % S);
+        if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / S) & 1), abort))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = base + (uint32_t)s * st_bytes, sb = sa + a_bytes;
+#pragma unroll
+        for (int kk = 0; kk < TM_CH / 16; ++kk) {
+          const uint64_t da = sw64_desc(sa + kk * 32), db = sw64_desc(sb + kk * 32);
+          const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_t),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        }
+        commit(saddr(&empty[s]));
+      }
+      if (ok) commit(saddr(&acc_full[ab]));
+    }
+    // every MMA issued has finished before the CTA goes on to free the TMEM
+    commit(saddr(&mma_done));
+    volatile int never = 0;
+    wait_bounded(saddr(&mma_done), 0, &never);
+  } else if (warp >= 2) {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = GEMM rows of the tile
+    const int quarter = warp & 3;
+    const int m = quarter * 32 + lane;
+    int j = 0;
+    for (int t = blockIdx.x; t < tg.ntiles; t += gridDim.x, ++j) {
+      const int ab = j & 1;
+      // every lane waits (acquire); the warp goes on only together, as tcgen05.ld is .aligned
+      const bool got = wait_bounded(saddr(&acc_full[ab]), (uint32_t)((j >> 1) & 1), abort);
+      if (!__all_sync(0xffffffffu, got)) {
+        *abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int x0, y0, b;
+      tile_origin(tg, t, x0, y0, b);
+      const int xx = x0 + (m % TM_X), yy = y0 + (m / TM_X);
+      const bool inside = xx < a.Wout && yy < a.Hout;
+      const size_t pix = ((size_t)b * a.Hout + yy) * a.Wout + xx;
+      for (int n0 = 0; n0 < BN; n0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * (tmem_cols >> 1) + n0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!inside) continue;
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          v[e] = __uint_as_float(r[e]);
+          if (n0 + e < a.Nreal) v[e] += a.bias[n0 + e];
+          if (a.relu) v[e] = fmaxf(v[e], 0.f);
+        }
+        uint32_t pk[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+          pk[e] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.N + n0);
+        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      arrive(saddr(&acc_empty[ab]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && abort_sh) atomicExch(err, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+int tmem_cols_of(int n) {
+  int c = 32;
+  while (c < n) c <<= 1;
+  return c;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool conv_tma_supported(const ConvArgs &a, int mode) {
+  return mode == MODE_FWD && a.ks == 3 && a.stride == 1 && a.pad == 1 && a.C1 > 0 && a.C1 % TM_CH == 0 &&
+         a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && a.y && !a.y32 && a.N % 16 == 0 && a.N >= 16 &&
+         a.N <= TM_NMAX && a.Nreal <= a.N && encoder() != nullptr;
+}
+
+// Tensor maps of one convolution: the input parts as 4-D (C, W, H, B) bf16 tensors with boxes
+// of 32 channels x 16 x 8 pixels x 1 image, the weight matrix [N][K] as a 2-D (K, N) tensor
+// with boxes of 32 x N; 64-byte swizzle, zero fill outside.
+int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
+  EncodeTiled enc = encoder();
+  if (!enc) return 1;
+  std::memset(m, 0, sizeof(*m));
+  auto act = [&](CUtensorMap *t, const __nv_bfloat16 *p, int C) {
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)Bmax};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)a.Win * C * 2, (cuuint64_t)a.Hin * a.Win * C * 2};
+    const cuuint32_t box[4] = {TM_CH, TM_X, TM_Y, 1}, es[4] = {1, 1, 1, 1};
+    return enc(t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!act(&m->x1, a.x1, a.C1)) return 2;
+  if (a.C2 > 0 ? !act(&m->x2, a.x2, a.C2) : !act(&m->x2, a.x1, a.C1)) return 3;
+  const cuuint64_t wd[2] = {(cuuint64_t)a.K, (cuuint64_t)a.N};
+  const cuuint64_t ws[1] = {(cuuint64_t)a.K * 2};
+  const cuuint32_t wbox[2] = {TM_CH, (cuuint32_t)a.N}, wes[2] = {1, 1};
+  if (enc(&m->w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(a.w), wd, ws, wbox, wes,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 4;
+  return 0;
+}
+
+namespace {
+
+// Four stages per CTA and several CTAs per SM: the loads in flight on an SM grow with the CTAs
+// it holds, each CTA's single producer thread keeps its own ring full.
+int stages_for(int BN) {
+  (void)BN;
+  return 4;
+}
+
+size_t smem_for(int BN) { return 1024 + (size_t)stages_for(BN) * (TM_X * TM_Y * 64 + (size_t)BN * 64); }
+
+}  // namespace
+
+cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st) {
+  const int BN = a.N, S = stages_for(BN), cols = tmem_cols_of(2 * BN);
+  const size_t smem = smem_for(BN);
+  cudaError_t e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, smem_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  // CTAs per SM: as many as the shared memory holds (the ring, the static barriers and the 1 KB
+  // each CTA reserves) and whose accumulators fit together in the 512 TMEM columns of an SM, so
+  // that a resident CTA never waits in tcgen05.alloc; a CTA that finds no room starts later.
+  const int occ = std::max(1, std::min(smem_sm / (int)(smem + 2048), 512 / cols));
+  TileGrid tg;
+  tg.tx = (a.Wout + TM_X - 1) / TM_X;
+  tg.ty = (a.Hout + TM_Y - 1) / TM_Y;
+  tg.per_img = tg.tx * tg.ty;
+  tg.ntiles = tg.per_img * a.Bn;
+  const int grid = std::max(1, std::min(tg.ntiles, sms * occ));
+  k_conv_tma<<<grid, TM_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, tg, S, cols, err);
+  return cudaGetLastError();
+}
+
+}  // namespace unk

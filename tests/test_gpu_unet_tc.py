@@ -1,6 +1,7 @@
 """GPU tests of the tcgen05 / TMEM convolution path of the learned-guess network: the forward
 pass and every parameter gradient agree with the mma.sync path (itself checked against the
-FP64 CPU oracle in test_gpu_unet.py) up to the rounding of BF16 outputs."""
+FP64 CPU oracle in test_gpu_unet.py) up to the rounding of BF16 outputs; the TMA-fed forward
+path (2) reads the same operands in the same reduction order as the gather path (1)."""
 import numpy as np
 import pytest
 
@@ -54,3 +55,34 @@ def test_tc_gradients_match_mma_sync(un):
     assert abs(l1 - l0) <= 1e-2 * abs(l0)
     rel = np.linalg.norm(g1 - g0) / np.linalg.norm(g0)
     assert rel <= 3e-2, rel
+
+
+@pytest.mark.parametrize("Bmax,B,n", [(2, 2, 32), (3, 2, 64), (1, 1, 128)])
+def test_tma_forward_matches_gather(un, Bmax, B, n):
+    # Bmax > B: the tensor maps span the allocated batch, the launch only the images given;
+    # 33, 65 and 129 node rows leave ragged 16 x 8 tiles on the right and bottom edges.
+    p, x, _ = _inputs(un, B, n, 13)
+    ys = []
+    for path in (1, 2):
+        net = un.UNet(Bmax, n)
+        net.set_tensor_path(path)
+        net.set_params(p)
+        ys.append(net.forward(x))
+        net.close()
+    rel = np.linalg.norm(ys[1] - ys[0]) / np.linalg.norm(ys[0])
+    assert rel <= 1e-5, rel
+
+
+def test_tma_gradients_match_gather(un):
+    p, x, t = _inputs(un, 2, 32, 14)
+    out = []
+    for path in (1, 2):
+        net = un.UNet(2, 32)
+        net.set_tensor_path(path)
+        net.set_params(p)
+        out.append(net.loss_grad(x, t))
+        net.close()
+    (l1, g1), (l2, g2) = out
+    assert abs(l2 - l1) <= 1e-5 * abs(l1)
+    rel = np.linalg.norm(g2 - g1) / np.linalg.norm(g1)
+    assert rel <= 1e-4, rel
