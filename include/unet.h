@@ -52,14 +52,17 @@ int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where);
 int mg_unet_loss_grad(mg_unet *n, const float *x, const float *t, int B, double *loss, int where);
 int mg_unet_get_grads(mg_unet *n, float *g, int where);
 
-/* Tensor-core path of the convolutions: 1 = tcgen05.mma with the accumulator in
- * tensor memory for the forward and data-gradient convolutions whose output width is a
- * multiple of 16 (<= 256); 0 = mma.sync for every convolution.  The weight gradient and the
- * 8-wide head always use mma.sync; 2 (default) = as 1, except that the forward 3x3 stride-1
- * convolutions whose input parts have a multiple of 32 channels take their operands by TMA
- * tiled loads (16 x 8 output pixels per CTA, the padding read as the loads' zero fill) instead
- * of a thread gather.  Any other value returns MG_EINVAL.  A tcgen05 kernel whose bounded wait
- * expires makes the next call return MG_ETIMEOUT. */
+/* Tensor-core path of the convolutions.
+ *   0 = mma.sync for every convolution.
+ *   1 = tcgen05.mma with the accumulator in tensor memory for the forward and data-gradient
+ *       convolutions whose output width is a multiple of 16 (<= 256), operands gathered by
+ *       threads; the 1x1 head's forward (8 FP32 outputs) on an FP32-accumulating CUDA-core
+ *       kernel; the rest on mma.sync.
+ *   2 (default) = as 1, except that the forward 3x3 stride-1 convolutions whose input parts
+ *       have a multiple of 32 channels take their operands by TMA tiled loads (tiles of 16 x 8
+ *       output pixels, the padding read as the loads' zero fill) in a persistent kernel.
+ * The weight gradient always uses mma.sync.  Any other value returns MG_EINVAL.  A tcgen05
+ * kernel whose bounded wait expires makes the next call return MG_ETIMEOUT. */
 int mg_unet_set_tensor_path(mg_unet *n, int path);
 
 /* One training step: loss and gradients as above, then an Adam update (beta1 0.9,

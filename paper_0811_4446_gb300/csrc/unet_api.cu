@@ -167,7 +167,9 @@ int conv_fwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, Act *out,
   a.w = n->wf[l];
   a.y = out ? out->a : nullptr;
   a.y32 = out32;
-  if (n->use_tc == 2 && conv_tma_supported(a, MODE_FWD)) {
+  if (n->use_tc && conv1x1_f32_supported(a)) {
+    UK(launch_conv1x1_f32(a, n->st));
+  } else if (n->use_tc == 2 && conv_tma_supported(a, MODE_FWD)) {
     const void *key[3] = {a.x1, a.x2, a.w};
     if (std::memcmp(key, n->map_key[l], sizeof(key)) != 0) {
       if (int rc = make_conv_maps(a, n->Bmax, &n->maps[l]))

@@ -41,6 +41,9 @@ struct ConvMaps {
 bool conv_tma_supported(const ConvArgs &a, int mode);
 int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
 cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st);
+// FP32-output 1x1 convolution to 8 channels (the head) on the CUDA cores
+bool conv1x1_f32_supported(const ConvArgs &a);
+cudaError_t launch_conv1x1_f32(const ConvArgs &a, cudaStream_t st);
 cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
                             cudaStream_t st);
 cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st);

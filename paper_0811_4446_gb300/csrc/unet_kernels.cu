@@ -423,6 +423,49 @@ cudaError_t launch_unpad_grad(const float *gp, float *g, size_t rows, int co, in
   return cudaGetLastError();
 }
 
+// 1x1 convolution to 8 FP32 output channels (the network head; memory-bound: C bf16 in and
+// 8 floats out per pixel): one pixel per thread, its C input channels (C % 8 == 0, C <= 64)
+// read as 16-byte groups, the 8 x C bf16 weights ([N][K] rows, the padded rows zero) and the
+// bias held in shared memory as FP32, FP32 accumulation in channel order, then the bias.
+__global__ void __launch_bounds__(256) k_conv1x1_f32(const __nv_bfloat16 *x, const __nv_bfloat16 *w,
+                                                     const float *bias, int Nreal, int C, int P, float *y) {
+  __shared__ float ws[8 * 64];
+  __shared__ float bs[8];
+  for (int i = threadIdx.x; i < 8 * C; i += blockDim.x) ws[i] = __bfloat162float(w[i]);
+  if (threadIdx.x < 8) bs[threadIdx.x] = (int)threadIdx.x < Nreal ? bias[threadIdx.x] : 0.f;
+  __syncthreads();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const uint4 *src = reinterpret_cast<const uint4 *>(x + (size_t)p * C);
+    for (int g = 0; g < C / 8; ++g) {
+      const uint4 q = src[g];
+      const __nv_bfloat16 *hq = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float v = __bfloat162float(hq[e]);
+        const int c = 8 * g + e;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[o] = fmaf(v, ws[o * C + c], acc[o]);
+      }
+    }
+    float4 *dst = reinterpret_cast<float4 *>(y + (size_t)p * 8);
+    dst[0] = make_float4(acc[0] + bs[0], acc[1] + bs[1], acc[2] + bs[2], acc[3] + bs[3]);
+    dst[1] = make_float4(acc[4] + bs[4], acc[5] + bs[5], acc[6] + bs[6], acc[7] + bs[7]);
+  }
+}
+
+bool conv1x1_f32_supported(const ConvArgs &a) {
+  return a.ks == 1 && a.stride == 1 && a.pad == 0 && a.y32 && a.N == 8 && a.C2 == 0 && a.C1 % 8 == 0 &&
+         a.C1 > 0 && a.C1 <= 64 && a.Nreal <= 8;
+}
+
+cudaError_t launch_conv1x1_f32(const ConvArgs &a, cudaStream_t st) {
+  if (!conv1x1_f32_supported(a)) return cudaErrorInvalidValue;
+  const int blocks = std::max(1, std::min((a.Pout + 255) / 256, 152 * 8));
+  k_conv1x1_f32<<<blocks, 256, 0, st>>>(a.x1, a.w, a.bias, a.Nreal, a.C1, a.Pout, a.y32);
+  return cudaGetLastError();
+}
+
 __global__ void k_f32_to_bf16(const float *a, __nv_bfloat16 *b, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     b[i] = __float2bfloat16(a[i]);
