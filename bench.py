@@ -28,6 +28,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# The oracle legs (cpu_baseline and --impl reference) run on one thread: the BLAS pools numpy and
+# scipy may start (the coarsest level's dense factorisation) are pinned to one thread before
+# numpy is first imported, so that the reported "cores": 1 is what they used.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import numpy as np  # noqa: E402
 
 METRIC = "V-cycle Mpts/s & steady solves/s at 257² to 1e-8 resid; % HBM roofline"
