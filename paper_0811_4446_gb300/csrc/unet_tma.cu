@@ -1,12 +1,13 @@
 // tcgen05 convolutions of the learned-guess network fed by the Tensor Memory Accelerator.
 //
-// For the 3x3, stride-1 convolutions whose input parts have a multiple of 32 channels, the GEMM
-// rows are the output pixels in tiles of 16 x 8 pixels of one image (M = 128) and the columns all
-// output channels (N <= 128).  The reduction runs over (tap, input part, 32-channel chunk) in the
-// order of the weight matrix's K index (tap-major, then the channels of the concatenated inputs).
-// For each chunk one TMA tiled load brings the 16 x 8 input pixels shifted by the tap, 32
-// channels each, into shared memory (64-byte rows, 64-byte swizzle; coordinates outside the
-// image read zero, which is the convolution's padding) and one brings the N x 32 weight slice.
+// For the 3x3 convolutions of stride 1 or 2 whose input parts have a multiple of 32 channels,
+// the GEMM rows are the output pixels in tiles of 16 x 8 pixels of one image (M = 128) and the
+// columns all output channels (N <= 128).  The reduction runs over (tap, input part, 32-channel
+// chunk) in the order of the weight matrix's K index (tap-major, then the channels of the
+// concatenated inputs).  For each chunk one TMA tiled load brings the 16 x 8 input pixels that
+// the tap reads (for stride 2 every second pixel, by the load's element strides), 32 channels
+// each, into shared memory (64-byte rows, 64-byte swizzle; coordinates outside the image read
+// zero, which is the convolution's padding) and one brings the N x 32 weight slice.
 //
 // The kernel is persistent (a CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...) and warp
 // specialised: lane 0 of warp 0 issues the TMA loads into an S-stage ring (mbarriers "full",
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes) : "memory");
         asm volatile(
             "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-            ::"r"(sa), "l"(mx), "r"(cc), "r"(x0 + kw - 1), "r"(y0 + kh - 1), "r"(b), "r"(bar)
+            ::"r"(sa), "l"(mx), "r"(cc), "r"(x0 * a.stride + kw - 1), "r"(y0 * a.stride + kh - 1), "r"(b), "r"(bar)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -281,14 +282,16 @@ EncodeTiled encoder() {
 }  // namespace
 
 bool conv_tma_supported(const ConvArgs &a, int mode) {
-  return mode == MODE_FWD && a.ks == 3 && a.stride == 1 && a.pad == 1 && a.C1 > 0 && a.C1 % TM_CH == 0 &&
+  return mode == MODE_FWD && a.ks == 3 && (a.stride == 1 || a.stride == 2) && a.pad == 1 && a.C1 > 0 &&
+         a.C1 % TM_CH == 0 &&
          a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && a.y && !a.y32 && a.N % 16 == 0 && a.N >= 16 &&
          a.N <= TM_NMAX && a.Nreal <= a.N && encoder() != nullptr;
 }
 
 // Tensor maps of one convolution: the input parts as 4-D (C, W, H, B) bf16 tensors with boxes
-// of 32 channels x 16 x 8 pixels x 1 image, the weight matrix [N][K] as a 2-D (K, N) tensor
-// with boxes of 32 x N; 64-byte swizzle, zero fill outside.
+// of 32 channels x 16 x 8 pixels x 1 image (stride s: s * 16 x s * 8 pixels traversed with
+// element strides s), the weight matrix [N][K] as a 2-D (K, N) tensor with boxes of 32 x N;
+// 64-byte swizzle, zero fill outside.
 int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
   EncodeTiled enc = encoder();
   if (!enc) return 1;
@@ -296,7 +299,10 @@ int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
   auto act = [&](CUtensorMap *t, const __nv_bfloat16 *p, int C) {
     const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)Bmax};
     const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)a.Win * C * 2, (cuuint64_t)a.Hin * a.Win * C * 2};
-    const cuuint32_t box[4] = {TM_CH, TM_X, TM_Y, 1}, es[4] = {1, 1, 1, 1};
+    // a stride-s convolution reads every s-th pixel: a box of s * 16 x s * 8 pixels traversed
+    // with element strides s loads the 16 x 8 pixels one tap of an output tile needs
+    const cuuint32_t sd = (cuuint32_t)a.stride;
+    const cuuint32_t box[4] = {TM_CH, TM_X * sd, TM_Y * sd, 1}, es[4] = {1, sd, sd, 1};
     return enc(t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
