@@ -138,6 +138,13 @@ typedef struct mg_params {
                              system solved exactly, robust to strong z-coupling) on every level
                              (the coarse levels then run as separate launches, no coarse-cycle
                              kernel) */
+  int32_t smooth_phase;   /* levels with at most this many intervals per side run each pre- or
+                             post-smoothing phase (all its red-black half sweeps) as one
+                             cooperative launch with grid barriers between the half sweeps
+                             instead of one launch per half sweep (0: off; 0..1024).  Results
+                             are bit for bit those of the half-sweep launches.  On GB300 it is
+                             slower: a grid barrier costs more than a kernel boundary inside a
+                             graph with programmatic dependent launch, hence off by default */
 } mg_params;
 
 /* Per-call statistics. */
@@ -167,7 +174,8 @@ typedef struct mg_state mg_state;
  * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels
  * larger than 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down),
  * chain_from = 1 (the two-level 129^2 -> 257^2 continuation), pdl = 9 (smoothers and the coarse-cycle kernel), wall_dirichlet = 0,
- * newton_tol_rel = 0.1, full_jacobian = 0, max_corrections = 20, line_smoother = 0.
+ * newton_tol_rel = 0.1, full_jacobian = 0, max_corrections = 20, line_smoother = 0,
+ * smooth_phase = 0.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on

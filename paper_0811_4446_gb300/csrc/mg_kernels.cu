@@ -719,7 +719,13 @@ __device__ __forceinline__ Triple<T> block_solve(T re, T rp, T rV, T q1, T q2, T
 // term for term: 20 fused multiply-adds for the four faces, 7 for the block solve.
 // PDL: the operator data (constant during a linear solve) is requested before waiting for the
 // previous kernel, the corrections and right-hand sides after.
-template <typename T, bool PDL = false>
+// a correction read: through L2 (CG) where another CTA of the same launch wrote it
+template <bool CG, typename T> __device__ __forceinline__ T ld_du(const T *p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+
+template <typename T, bool PDL = false, bool CG = false>
 __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   const int P = L.P;
   const size_t k = (size_t)j * P + i;
@@ -736,10 +742,10 @@ __device__ __forceinline__ void smooth_node(const LevelT<T> &L, int i, int j) {
   // corrections in the colour-split layout: the four neighbours are of the other colour
   const size_t dE = d.E, dW = d.W, dN = d.N, dS = d.S;
   const T *ve = L.du[NE], *vp = L.du[NP], *vV = L.du[NV];
-  const T eE = ve[dE], pE = vp[dE], wE = vV[dE];
-  const T eW = ve[dW], pW = vp[dW], wW = vV[dW];
-  const T eN = ve[dN], pN = vp[dN], wN = vV[dN];
-  const T eS = ve[dS], pS = vp[dS], wS = vV[dS];
+  const T eE = ld_du<CG>(ve + dE), pE = ld_du<CG>(vp + dE), wE = ld_du<CG>(vV + dE);
+  const T eW = ld_du<CG>(ve + dW), pW = ld_du<CG>(vp + dW), wW = ld_du<CG>(vV + dW);
+  const T eN = ld_du<CG>(ve + dN), pN = ld_du<CG>(vp + dN), wN = ld_du<CG>(vV + dN);
+  const T eS = ld_du<CG>(ve + dS), pS = ld_du<CG>(vp + dS), wS = ld_du<CG>(vV + dS);
   const T f0 = L.f[NE][kf], f1 = L.f[NP][kf], f2 = L.f[NV][kf];
   asm volatile("" ::: "memory");
   T re = f0, rp = f1, rV = f2;
@@ -805,6 +811,103 @@ cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx
 }
 template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t, int, int);
 template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t, int, int);
+
+// Grid barrier of a cooperative launch (every CTA resident): bar[0] counts arrivals, bar[1] is
+// the generation; the last CTA to arrive resets the count and advances the generation, the
+// others poll the generation.  Bounded: false after kGridWaitLimit polls.
+constexpr long kGridWaitLimit = 1L << 21;
+__device__ bool grid_barrier(unsigned *bar) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = bar + 1;
+    const unsigned g = *vgen;  // read before arriving: the generation cannot move before that
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      ok = 0;
+      for (long it = 0; it < kGridWaitLimit; ++it)
+        if (*vgen != g) {
+          ok = 1;
+          break;
+        }
+    }
+    __threadfence();
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// A whole pre- or post-smoothing phase of a small level (nu red-black sweeps) in one cooperative
+// launch: the half sweeps are separated by grid barriers, the corrections of the other colour
+// are read through L2 (CTAs of this launch wrote them), the arithmetic is smooth_node's.
+// A barrier that gives up marks the level's barrier as broken (bar[2]; later launches on it
+// stop at once) and writes NaN into the V correction of the CTA's nodes, which the Newton
+// update's non-finite check then reports.
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_smooth_phase(LevelT<T> L, int nu, unsigned *bar) {
+  pdl_launch_dependents();
+  const int slots = colour_slots(L.ni, L.nz);
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  bool ok = *reinterpret_cast<volatile unsigned *>(bar + 2) == 0;
+  for (int h = 0; h < 2 * nu && ok; ++h) {
+    for (int t = t0; t < slots; t += stride) {
+      int i, j;
+      if (colour_node(t, L.ni, L.nz, h & 1, i, j)) smooth_node<T, false, true>(L, i, j);
+    }
+    if (h + 1 < 2 * nu) ok = grid_barrier(bar);
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(bar + 2, 1u);
+    int i, j;
+    if (t0 < slots && colour_node(t0, L.ni, L.nz, 0, i, j)) L.du[NV][split_nb(L.P, i, j).self] = T(NAN);
+  }
+}
+
+template <typename T>
+int smooth_phase_block() {
+  return 128;
+}
+
+template <typename T>
+int smooth_phase_grid(const LevelT<T> &L) {
+  static int sms = 0, occ = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_smooth_phase<T>, smooth_phase_block<T>(), 0) != cudaSuccess)
+      sms = 0;
+  }
+  if (sms <= 0 || occ <= 0) return 0;
+  const int need = (colour_slots(L.ni, L.nz) + smooth_phase_block<T>() - 1) / smooth_phase_block<T>();
+  return std::max(1, std::min(need, sms * occ));
+}
+
+template <typename T>
+cudaError_t launch_smooth_phase(const LevelT<T> &L, int nu, unsigned *bar, cudaStream_t st) {
+  const int g = smooth_phase_grid(L);
+  if (g <= 0) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g);
+  cfg.blockDim = dim3(smooth_phase_block<T>());
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_smooth_phase<T>, L, nu, bar);
+  count_launch();
+  return e;
+}
+template cudaError_t launch_smooth_phase<double>(const LevelT<double> &, int, unsigned *, cudaStream_t);
+template cudaError_t launch_smooth_phase<float>(const LevelT<float> &, int, unsigned *, cudaStream_t);
 
 // ------------------------------------------------------------------------------------------
 // z-line Gauss-Seidel, zebra order (even columns, then odd): one thread per column of the
