@@ -115,7 +115,11 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the raw samples go to $BENCH_CLOCKS_DIR (default: the temporary directory); the JSON
+        # line carries their summary
+        import tempfile
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{device_index}.csv")
 
     def start(self):
         try:
