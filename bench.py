@@ -395,6 +395,17 @@ def run_ours(args):
     # half sweeps of the 257^2 level (k_smooth, profiles/k_smooth_fp64_257.md) and of the 129^2
     # level (k_smooth_ilp, profiles/smoother_fp64_129.md); the other levels have no capture
     traffic_ncu = {(256, False): 11266560, (128, False): 2949632}
+
+    def sweeps_of_level(n_iv):
+        """Sweeps of one smoothing phase on a level of n_iv intervals per side: the solver's
+        own rule (mg_params nu1 / nu_coarse1 / nu_tiny1 by level size)."""
+        p = s.params
+        if p.nu_tiny_n > 0 and n_iv <= p.nu_tiny_n:
+            return p.nu_tiny1
+        if p.nu_coarse_n > 0 and n_iv <= p.nu_coarse_n:
+            return p.nu_coarse1
+        return p.nu1
+
     levels = []
     for lev, (n_l, ms_l) in enumerate(smooth_prof):
         if not n_l:
@@ -409,15 +420,21 @@ def run_ours(args):
         # the colour's factors, f and du (8 B each) and the other colour's du read.
         byt = (228 if fused else 176) * nodes
         flo = 52 * nodes if fused else 52 * (nodes / 2)   # 20 FMA off-diagonal + block solve per updated node
-        # duration of one launch as the solve's graphs run it: the level's sweeps replayed from
-        # a captured graph (back to back, programmatic dependent launch, the level's arrays in
-        # L2 as in the V-cycle); the event-bracketed launches of the profiled solve above carry
-        # host launch gaps and serve only to rank the levels by their share of the solve
-        us_graph, _ = s.time_smoother(lev, 0, 200)
+        # duration of one launch as the solve's graphs run it: one smoothing phase of the level
+        # (its nu sweeps, as each V-cycle issues them) replayed from a captured graph (back to
+        # back, programmatic dependent launch, the level's arrays in L2 as in the V-cycle), the
+        # median of 7 replays; the per-launch time of a 200-sweep graph is reported beside it
+        # (longer chains of the same launches run slower per launch).  The event-bracketed
+        # launches of the profiled solve above carry host launch gaps and serve only to rank
+        # the levels by their share of the solve.
+        nu_l = sweeps_of_level(n_iv)
+        us_graph = statistics.median([s.time_smoother(lev, 0, nu_l)[0] for _ in range(7)])
+        us_long, _ = s.time_smoother(lev, 0, 200)
         avg = us_graph * 1e-6
         levels.append({"level": lev, "nodes_per_side": n_iv + 1, "fused": fused, "launches": n_l,
                        "profiled_total_ms": ms_l, "profiled_avg_launch_us": ms_l / n_l * 1000.0,
-                       "avg_launch_us": us_graph, "gflops": flo / avg / 1e9,
+                       "sweeps_per_phase": nu_l, "avg_launch_us": us_graph,
+                       "avg_launch_us_200_sweep_graph": us_long, "gflops": flo / avg / 1e9,
                        "frac_fp64": flo / avg / 1e9 / fp64_peak_nominal, "gbs": byt / avg / 1e9,
                        "flops_per_launch": flo, "bytes_per_launch": byt,
                        "traffic": traffic_ncu.get((n_iv, fused))})
@@ -431,7 +448,10 @@ def run_ours(args):
                 "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "peak_probe_gflops": fp64_probe, "traffic": dom["traffic"],
                 "launches": dom["launches"], "avg_launch_us": dom["avg_launch_us"],
-                "avg_launch_us_source": "CUDA events around a captured graph of 200 sweeps of the level (mg_time_smoother)",
+                "avg_launch_us_source": ("CUDA events around a captured graph of one smoothing phase of the level "
+                                         f"({dom['sweeps_per_phase']} sweeps, as each V-cycle issues them), median of "
+                                         "7 replays (mg_time_smoother)"),
+                "avg_launch_us_200_sweep_graph": dom["avg_launch_us_200_sweep_graph"],
                 "algorithmic_flops_per_launch": dom["flops_per_launch"],
                 "hbm": {"achieved": dom["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": dom["gbs"] / hbm_peak,
                         "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
