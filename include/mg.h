@@ -139,9 +139,11 @@ typedef struct mg_params {
                              (the coarse levels then run as separate launches, no coarse-cycle
                              kernel) */
   int32_t smooth_phase;   /* levels with at most this many intervals per side run each pre- or
-                             post-smoothing phase (all its red-black half sweeps) as one
-                             cooperative launch with grid barriers between the half sweeps
-                             instead of one launch per half sweep (0: off; 0..1024).  Results
+                             post-smoothing phase (all its red-black half sweeps) as one launch
+                             with barriers between the half sweeps (one thread-block cluster with
+                             the hardware cluster barrier up to 65^2 nodes, a cooperative launch
+                             with a bounded grid barrier above) instead of one launch per half
+                             sweep (0: off; 0..1024).  Results
                              are bit for bit those of the half-sweep launches.  On GB300 it is
                              slower: a grid barrier costs more than a kernel boundary inside a
                              graph with programmatic dependent launch, hence off by default */
