@@ -58,9 +58,12 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
  *       convolutions whose output width is a multiple of 16 (<= 256), operands gathered by
  *       threads; the 1x1 head's forward (8 FP32 outputs) on an FP32-accumulating CUDA-core
  *       kernel; the rest on mma.sync.
- *   2 (default) = as 1, except that the forward 3x3 convolutions (stride 1 or 2) whose input
+ *   2 = as 1, except that the forward 3x3 convolutions (stride 1 or 2) whose input
  *       parts have a multiple of 32 channels take their operands by TMA tiled loads (tiles of
  *       16 x 8 output pixels, the padding read as the loads' zero fill) in a persistent kernel.
+ *   3 (default) = as 2, except that the stride-1 ones whose weight matrix fits in 72 KB keep it
+ *       resident in shared memory and load one 10 x 18-pixel halo per 32-channel chunk for all
+ *       nine taps (tiles of 8 x 16 output pixels); their sums round in another order.
  * The weight gradient always uses mma.sync.  Any other value returns MG_EINVAL.  A tcgen05
  * kernel whose bounded wait expires makes the next call return MG_ETIMEOUT. */
 int mg_unet_set_tensor_path(mg_unet *n, int path);

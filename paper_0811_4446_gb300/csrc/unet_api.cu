@@ -51,9 +51,9 @@ struct mg_unet {
   __nv_bfloat16 *dpre = nullptr;
   double *loss_d = nullptr, *loss_h = nullptr;
   int *tc_err = nullptr;   // set by a tcgen05 kernel whose bounded wait expired
-  int use_tc = 2;          // 1: tcgen05 path where the layer shape allows it; 2: TMA-fed where it can
+  int use_tc = 3;          // 1: tcgen05 where the layer shape allows it; 2: TMA-fed where it can; 3: halo loads too
   ConvMaps maps[NL];       // tensor maps of the TMA-fed forward convolutions, built on first use
-  const void *map_key[NL][3] = {};
+  const void *map_key[NL][4] = {};  // inputs, weights and the kind of map (2: tile boxes, 3: halo boxes)
   int step = 0;
   void *block = nullptr;
   std::string err;
@@ -169,8 +169,16 @@ int conv_fwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, Act *out,
   a.y32 = out32;
   if (n->use_tc && conv1x1_f32_supported(a)) {
     UK(launch_conv1x1_f32(a, n->st));
-  } else if (n->use_tc == 2 && conv_tma_supported(a, MODE_FWD)) {
-    const void *key[3] = {a.x1, a.x2, a.w};
+  } else if (n->use_tc == 3 && conv_halo_supported(a, MODE_FWD)) {
+    const void *key[4] = {a.x1, a.x2, a.w, reinterpret_cast<const void *>(3)};
+    if (std::memcmp(key, n->map_key[l], sizeof(key)) != 0) {
+      if (int rc = make_halo_maps(a, n->Bmax, &n->maps[l]))
+        return fail(n, MG_ECUDA, "halo tensor maps of layer %d: encode step %d failed", l, rc);
+      std::memcpy(n->map_key[l], key, sizeof(key));
+    }
+    UK(launch_conv_halo(a, n->maps[l], n->tc_err, n->st));
+  } else if (n->use_tc >= 2 && conv_tma_supported(a, MODE_FWD)) {
+    const void *key[4] = {a.x1, a.x2, a.w, reinterpret_cast<const void *>(2)};
     if (std::memcmp(key, n->map_key[l], sizeof(key)) != 0) {
       if (int rc = make_conv_maps(a, n->Bmax, &n->maps[l]))
         return fail(n, MG_ECUDA, "tensor maps of layer %d: encode step %d failed", l, rc);
@@ -381,7 +389,7 @@ int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where) {
 }
 
 int mg_unet_set_tensor_path(mg_unet *n, int path) {
-  if (!n || path < 0 || path > 2) return MG_EINVAL;
+  if (!n || path < 0 || path > 3) return MG_EINVAL;
   n->use_tc = path;
   return MG_OK;
 }

@@ -41,6 +41,10 @@ struct ConvMaps {
 bool conv_tma_supported(const ConvArgs &a, int mode);
 int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
 cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st);
+// halo variant (3x3 stride 1, the weight matrix resident in shared memory, <= 72 KB)
+bool conv_halo_supported(const ConvArgs &a, int mode);
+int make_halo_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
+cudaError_t launch_conv_halo(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st);
 // FP32-output 1x1 convolution to 8 channels (the head) on the CUDA cores
 bool conv1x1_f32_supported(const ConvArgs &a);
 cudaError_t launch_conv1x1_f32(const ConvArgs &a, cudaStream_t st);

@@ -255,6 +255,213 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
+// ---- halo variant (tensor path 3): one load per 32-channel chunk serves all nine taps ----------
+//
+// For 3x3 stride-1 layers whose whole weight matrix fits in shared memory (at most 72 KB), the
+// weights are loaded once per CTA and stay resident, and a tile is 8 x 16 output pixels.  Per
+// 32-channel chunk four TMA loads (one per 8-channel group, 16-byte rows, no swizzle) bring the
+// 10 x 18-pixel halo of the tile; the nine taps are nine windows of it.  In the halo a group
+// plane holds pixel (x, y) at (y * 10 + x) * 16 bytes, so the 8 pixels of one output row at one
+// tap are a contiguous 128-byte core matrix (8 rows x 16 bytes), the next output row's core
+// matrix lies 160 bytes on (SBO) and the next 8 channels one plane slot, 2,944 bytes, on (LBO): an unswizzled
+// K-major operand whose start address moves with the tap.  A chunk takes 18 MMAs (9 taps x
+// K 32).  The reduction runs chunk by chunk, each chunk tap by tap (the thread-gather and the
+// path-2 kernels run tap by tap, each tap over all channels), so the FP32 sums round differently.
+constexpr int HX = 8, HY = 16;                   // output tile
+constexpr int HW = HX + 2, HH = HY + 2;          // halo
+constexpr uint32_t HPLANE = HW * HH * 16;        // one 8-channel group: 2,880 bytes loaded
+constexpr uint32_t HPITCH = 2944;                // its slot: rounded up to 128 bytes, as a TMA destination must be
+constexpr uint32_t HSTAGE = 4 * HPITCH;          // one 32-channel chunk: 11,776 bytes
+constexpr uint32_t HTX = 4 * HPLANE;             // bytes its four loads deliver
+constexpr int HSTAGES = 4;
+constexpr uint32_t HWMAX = 72 * 1024;            // largest resident weight matrix
+
+// Unswizzled K-major descriptor: core matrices of 8 rows x 16 bytes, LBO between K-adjacent and
+// SBO between M/N-adjacent core matrices; layout type 0 (no swizzle), descriptor version 1.
+__device__ __forceinline__ uint64_t nosw_desc(uint32_t a, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((a >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  return d;
+}
+
+__device__ __forceinline__ void halo_origin(const TileGrid &g, int t, int &x0, int &y0, int &b) {
+  b = t / g.per_img;
+  const int r = t - b * g.per_img;
+  y0 = (r / g.tx) * HY;
+  x0 = (r % g.tx) * HX;
+}
+
+__global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant__ CUtensorMap mx1,
+                                                          const __grid_constant__ CUtensorMap mx2,
+                                                          const __grid_constant__ CUtensorMap mw, ConvArgs a,
+                                                          TileGrid tg, int tmem_cols, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int BN = a.N;
+  const int Ctot = a.C1 + a.C2, nkb = 9 * Ctot / TM_CH;  // weight blocks of 32 K values
+  const uint32_t wblk = (uint32_t)BN * 64, wbytes = (uint32_t)nkb * wblk;
+  const uint32_t wbase = (saddr(smem_raw) + 1023u) & ~1023u, hbase = wbase + wbytes;
+  __shared__ __align__(8) uint64_t wfull, full[HSTAGES], empty[HSTAGES], acc_full[2], acc_empty[2], mma_done;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+  volatile int *abort = &abort_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_sh)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 32) {
+    abort_sh = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&wfull)) : "memory");
+    for (int s = 0; s < HSTAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])) : "memory");
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&acc_full[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(saddr(&acc_empty[i])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mma_done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  const int c1 = a.C1 / TM_CH, nch = Ctot / TM_CH;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: the weight matrix once, then the halo of every chunk of every tile
+    const uint64_t pm1 = reinterpret_cast<uint64_t>(&mx1), pm2 = reinterpret_cast<uint64_t>(&mx2),
+                   pmw = reinterpret_cast<uint64_t>(&mw);
+    const uint32_t wb = saddr(&wfull);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wb), "r"(wbytes) : "memory");
+    for (int i = 0; i < nkb; ++i)
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+          ::"r"(wbase + (uint32_t)i * wblk), "l"(pmw), "r"(i * TM_CH), "r"(0), "r"(wb)
+          : "memory");
+    long g = 0;
+    for (int t = blockIdx.x; t < tg.ntiles && !*abort; t += gridDim.x) {
+      int x0, y0, b;
+      halo_origin(tg, t, x0, y0, b);
+      for (int c = 0; c < nch; ++c, ++g) {
+        const int s = (int)(g % HSTAGES);
+        const uint32_t use = (uint32_t)(g / HSTAGES);
+        if (use > 0 && !wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort)) break;
+        const uint64_t mx = c < c1 ? pm1 : pm2;
+        const int cc = (c < c1 ? c : c - c1) * TM_CH;
+        const uint32_t sa = hbase + (uint32_t)s * HSTAGE, bar = saddr(&full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(HTX) : "memory");
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+              ::"r"(sa + (uint32_t)q * HPITCH), "l"(mx), "r"(cc + 8 * q), "r"(x0 - 1), "r"(y0 - 1), "r"(b), "r"(bar)
+              : "memory");
+      }
+    }
+    volatile int never = 0;
+    wait_bounded(wb, 0, &never);
+    for (long j = g > HSTAGES ? g - HSTAGES : 0; j < g; ++j)
+      wait_bounded(saddr(&full[j % HSTAGES]), (uint32_t)((j / HSTAGES) & 1), &never);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = idesc_bf16_tma(HX * HY, BN);
+    bool ok = wait_bounded(saddr(&wfull), 0, abort);
+    long g = 0;
+    int j = 0;
+    for (int t = blockIdx.x; t < tg.ntiles && ok; t += gridDim.x, ++j) {
+      const int ab = j & 1;
+      if (j >= 2 && !(ok = wait_bounded(saddr(&acc_empty[ab]), (uint32_t)(((j >> 1) - 1) & 1), abort))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc_t = tmem + (uint32_t)(ab * (tmem_cols >> 1));
+      for (int c = 0; c < nch; ++c, ++g) {
+        const int s = (int)(g % HSTAGES);
+        if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / HSTAGES) & 1), abort))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = hbase + (uint32_t)s * HSTAGE;
+        for (int tap = 0; tap < 9; ++tap) {
+          const int kh = tap / 3, kw = tap - kh * 3;
+          const uint32_t wblock = wbase + (uint32_t)((tap * Ctot + c * TM_CH) / TM_CH) * wblk;
+#pragma unroll
+          for (int kk = 0; kk < TM_CH / 16; ++kk) {
+            const uint64_t da = nosw_desc(sa + (uint32_t)(2 * kk) * HPITCH + (uint32_t)(kh * HW + kw) * 16, HPITCH,
+                                          HW * 16);
+            const uint64_t db = sw64_desc(wblock + kk * 32);
+            const uint32_t acc = (c > 0 || tap > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_t),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          }
+        }
+        commit(saddr(&empty[s]));
+      }
+      if (ok) commit(saddr(&acc_full[ab]));
+    }
+    commit(saddr(&mma_done));
+    volatile int never = 0;
+    wait_bounded(saddr(&mma_done), 0, &never);
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lane m = GEMM row = output pixel (x0 + m % 8, y0 + m / 8)
+    const int quarter = warp & 3;
+    const int m = quarter * 32 + lane;
+    int j = 0;
+    for (int t = blockIdx.x; t < tg.ntiles; t += gridDim.x, ++j) {
+      const int ab = j & 1;
+      const bool got = wait_bounded(saddr(&acc_full[ab]), (uint32_t)((j >> 1) & 1), abort);
+      if (!__all_sync(0xffffffffu, got)) {
+        *abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int x0, y0, b;
+      halo_origin(tg, t, x0, y0, b);
+      const int xx = x0 + (m % HX), yy = y0 + (m / HX);
+      const bool inside = xx < a.Wout && yy < a.Hout;
+      const size_t pix = ((size_t)b * a.Hout + yy) * a.Wout + xx;
+      for (int n0 = 0; n0 < BN; n0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * (tmem_cols >> 1) + n0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!inside) continue;
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          v[e] = __uint_as_float(r[e]);
+          if (n0 + e < a.Nreal) v[e] += a.bias[n0 + e];
+          if (a.relu) v[e] = fmaxf(v[e], 0.f);
+        }
+        uint32_t pk[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+          pk[e] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.N + n0);
+        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      arrive(saddr(&acc_empty[ab]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && abort_sh) atomicExch(err, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
 int tmem_cols_of(int n) {
   int c = 32;
   while (c < n) c <<= 1;
@@ -286,6 +493,65 @@ bool conv_tma_supported(const ConvArgs &a, int mode) {
          a.C1 % TM_CH == 0 &&
          a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && a.y && !a.y32 && a.N % 16 == 0 && a.N >= 16 &&
          a.N <= TM_NMAX && a.Nreal <= a.N && encoder() != nullptr;
+}
+
+bool conv_halo_supported(const ConvArgs &a, int mode) {
+  return mode == MODE_FWD && a.ks == 3 && a.stride == 1 && a.pad == 1 && a.C1 > 0 && a.C1 % TM_CH == 0 &&
+         a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && a.y && !a.y32 && a.N % 16 == 0 && a.N >= 16 &&
+         a.N <= TM_NMAX && a.Nreal <= a.N && (size_t)9 * (a.C1 + a.C2) * a.N * 2 <= HWMAX && encoder() != nullptr;
+}
+
+// Tensor maps of the halo variant: the input parts as 4-D (C, W, H, B) bf16 tensors with boxes
+// of 8 channels x 10 x 18 pixels x 1 image (16-byte rows, no swizzle, zero fill outside), the
+// weight matrix as for the path-2 kernel.
+int make_halo_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
+  EncodeTiled enc = encoder();
+  if (!enc) return 1;
+  std::memset(m, 0, sizeof(*m));
+  auto act = [&](CUtensorMap *t, const __nv_bfloat16 *p, int C) {
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)Bmax};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)a.Win * C * 2, (cuuint64_t)a.Hin * a.Win * C * 2};
+    const cuuint32_t box[4] = {8, HW, HH, 1}, es[4] = {1, 1, 1, 1};
+    return enc(t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!act(&m->x1, a.x1, a.C1)) return 2;
+  if (a.C2 > 0 ? !act(&m->x2, a.x2, a.C2) : !act(&m->x2, a.x1, a.C1)) return 3;
+  const cuuint64_t wd[2] = {(cuuint64_t)a.K, (cuuint64_t)a.N};
+  const cuuint64_t ws[1] = {(cuuint64_t)a.K * 2};
+  const cuuint32_t wbox[2] = {TM_CH, (cuuint32_t)a.N}, wes[2] = {1, 1};
+  if (enc(&m->w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(a.w), wd, ws, wbox, wes,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 4;
+  return 0;
+}
+
+cudaError_t launch_conv_halo(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st) {
+  const int BN = a.N, cols = tmem_cols_of(2 * BN);
+  const size_t wbytes = (size_t)9 * (a.C1 + a.C2) / TM_CH * BN * 64;
+  // the operand windows end inside their stage: the last tap's last core matrix of a plane ends
+  // at (2 * 10 + 2) * 16 + 15 * 160 + 128 = 2,880 bytes, the plane's end
+  const size_t smem = 1024 + wbytes + (size_t)HSTAGES * HSTAGE;
+  cudaError_t e = cudaFuncSetAttribute(k_conv_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_halo, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, smem_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  const int occ = std::max(1, std::min(smem_sm / (int)(smem + 2048), 512 / cols));
+  TileGrid tg;
+  tg.tx = (a.Wout + HX - 1) / HX;
+  tg.ty = (a.Hout + HY - 1) / HY;
+  tg.per_img = tg.tx * tg.ty;
+  tg.ntiles = tg.per_img * a.Bn;
+  const int grid = std::max(1, std::min(tg.ntiles, sms * occ));
+  k_conv_halo<<<grid, TM_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, tg, cols, err);
+  return cudaGetLastError();
 }
 
 // Tensor maps of one convolution: the input parts as 4-D (C, W, H, B) bf16 tensors with boxes

@@ -92,8 +92,9 @@ class UNet:
 
     def set_tensor_path(self, path: int):
         """1: tcgen05 / TMEM convolutions where the shape allows, 0: mma.sync everywhere,
-        2 (default): as 1 with TMA-fed operands for the 3x3 forward convolutions (stride 1 or 2)
-        whose input parts have a multiple of 32 channels."""
+        2: as 1 with TMA-fed operands for the 3x3 forward convolutions (stride 1 or 2)
+        whose input parts have a multiple of 32 channels, 3 (default): as 2 with one halo load
+        per 32-channel chunk for all nine taps where the weights fit in shared memory."""
         self._check(self.lib.mg_unet_set_tensor_path(self.h, int(path)))
 
     def set_params(self, p):

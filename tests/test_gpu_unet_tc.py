@@ -86,3 +86,20 @@ def test_tma_gradients_match_gather(un):
     assert abs(l2 - l1) <= 1e-5 * abs(l1)
     rel = np.linalg.norm(g2 - g1) / np.linalg.norm(g1)
     assert rel <= 1e-4, rel
+
+
+@pytest.mark.parametrize("Bmax,B,n", [(2, 2, 32), (3, 2, 64), (1, 1, 128)])
+def test_halo_forward_matches_tile_path(un, Bmax, B, n):
+    # path 3 sums each output chunk by chunk, each chunk tap by tap (path 2: tap by tap over all
+    # channels), so FP32 rounding differs, some BF16 activations round to the neighbouring value
+    # and the differences carry through the twelve layers: the bound of the mma.sync comparison
+    p, x, _ = _inputs(un, B, n, 15)
+    ys = []
+    for path in (2, 3):
+        net = un.UNet(Bmax, n)
+        net.set_tensor_path(path)
+        net.set_params(p)
+        ys.append(net.forward(x))
+        net.close()
+    rel = np.linalg.norm(ys[1] - ys[0]) / np.linalg.norm(ys[0])
+    assert rel <= 1e-2, rel
