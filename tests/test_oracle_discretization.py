@@ -320,3 +320,105 @@ def test_table_slopes_are_the_lerp_derivative():
     for c in range(4):
         fd = (up[c] - disc.table_lookup(d.table, x)[c]) / h
         assert np.allclose(fd, slopes[c], rtol=1e-5, atol=1e-12 * np.abs(d.table[:, c + 1]).max() / E[0]), c
+
+
+# ---------------------------------------------------------------- face |E| components (reading 7)
+def _bilinear_quadratic_field(g, a=0.3e-2, b=0.7e-2, c1=2.0e5, c2=-3.0e4):
+    """V = c1 r^2 (b + z) + c2 (a + r) z^2 on the grid nodes; its face differences have closed
+    forms in the node coordinates alone."""
+    r, z = g.r[None, :], g.z[:, None]
+    return c1 * r ** 2 * (b + z) + c2 * (a + r) * z ** 2
+
+
+def test_face_field_components_closed_forms():
+    """E = -grad V (eq. 6) on the faces of a stretched grid for V = c1 r^2 (b+z) + c2 (a+r) z^2,
+    against closed forms written from the node coordinates (no index arithmetic of the oracle):
+    * r-face (i+1/2, j): E_r = -[c1 (r_i + r_{i+1})(b + z_j) + c2 z_j^2];
+    * z-face (i, j+1/2): E_z = -[c1 r_i^2 + c2 (a + r_i)(z_j + z_{j+1})];
+    * transverse E_z on an interior r-face: the mean of the four z-faces at columns i, i+1 and
+      rows j-1/2, j+1/2, i.e. -[c1 (r_i^2 + r_{i+1}^2)/2 + c2 (a + r_{i+1/2})(z_{j-1} + 2 z_j + z_{j+1})/2];
+    * transverse E_r on a z-face of an inner column: the mean of the four r-faces at rows j, j+1
+      and columns i-1/2, i+1/2, i.e. -[c1 2 r_i (b + (z_j + z_{j+1})/2) + c2 (z_j^2 + z_{j+1}^2)/2];
+    * zero transverse part on the electrode-row r-faces and on the axis and wall z-faces.
+    A dropped term, a wrong neighbour index or a transposed average fails one of these."""
+    a, b, c1, c2 = 0.3e-2, 0.7e-2, 2.0e5, -3.0e4
+    g = _grid(8, 16, ratio=1.3)
+    V = _bilinear_quadratic_field(g, a, b, c1, c2)
+    Er, Ez_t, Ez, Er_t = disc.face_field_components(g, V)
+    r, z = g.r, g.z
+    rh = 0.5 * (r[:-1] + r[1:])
+    ex_Er = -(c1 * (r[:-1] + r[1:])[None, :] * (b + z)[:, None] + c2 * (z ** 2)[:, None] * np.ones(g.nr)[None, :])
+    ex_Ez = -(c1 * (r ** 2)[None, :] * np.ones(g.nz)[:, None] + c2 * (a + r)[None, :] * (z[:-1] + z[1:])[:, None])
+    ex_Ez_t = np.zeros((g.nz + 1, g.nr))
+    ex_Ez_t[1:-1] = -(c1 * 0.5 * (r[:-1] ** 2 + r[1:] ** 2)[None, :]
+                      + c2 * (a + rh)[None, :] * (0.5 * (z[:-2] + 2 * z[1:-1] + z[2:]))[:, None])
+    ex_Er_t = np.zeros((g.nz, g.nr + 1))
+    ex_Er_t[:, 1:-1] = -(c1 * 2 * r[1:-1][None, :] * (b + 0.5 * (z[:-1] + z[1:]))[:, None]
+                         + c2 * (0.5 * (z[:-1] ** 2 + z[1:] ** 2))[:, None])
+    for got, ex in ((Er, ex_Er), (Ez, ex_Ez), (Ez_t, ex_Ez_t), (Er_t, ex_Er_t)):
+        assert got.shape == ex.shape
+        assert np.abs(got - ex).max() <= 1e-11 * np.abs(ex).max()
+    # |E| combines the normal and the transverse component in quadrature
+    Eabs_r, Eabs_z = disc.face_fields(g, V)
+    assert np.allclose(Eabs_r, np.hypot(ex_Er, ex_Ez_t), rtol=1e-11)
+    assert np.allclose(Eabs_z, np.hypot(ex_Ez, ex_Er_t), rtol=1e-11)
+
+
+def test_face_field_components_hand_values():
+    """A 2 x 2-interval grid (r = 0, 1, 2 mm; z = 0, 1, 3 mm) and V with node values written out;
+    every face value below was computed by hand from E = -(V_R - V_L)/h."""
+    g = Grid(2, 2, 2e-3, np.array([0.0, 1e-3, 3e-3]))
+    V = np.array([[0.0, 1.0, 4.0],      # z = 0
+                  [2.0, 2.0, 8.0],      # z = 1 mm
+                  [6.0, 9.0, 3.0]])     # z = 3 mm
+    Er, Ez_t, Ez, Er_t = disc.face_field_components(g, V)
+    k = 1e3   # 1/mm
+    assert np.allclose(Er, -k * np.array([[1.0, 3.0], [0.0, 6.0], [3.0, -6.0]]), rtol=1e-14)
+    assert np.allclose(Ez, -k * np.array([[2.0, 1.0, 4.0], [2.0, 3.5, -2.5]]), rtol=1e-14)
+    # transverse E_z on the middle-row r-faces: (Ez[0,i] + Ez[1,i] + Ez[0,i+1] + Ez[1,i+1]) / 4
+    assert np.allclose(Ez_t, -k * np.array([[0.0, 0.0], [8.5 / 4, 6.0 / 4], [0.0, 0.0]]), rtol=1e-14)
+    # transverse E_r on the middle-column z-faces: (Er[j,0] + Er[j,1] + Er[j+1,0] + Er[j+1,1]) / 4
+    assert np.allclose(Er_t, -k * np.array([[0.0, 10.0 / 4, 0.0], [0.0, 3.0 / 4, 0.0]]), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- table lookup (reading 7)
+_HAND_TABLE = np.array([[1.0, 5.0, 1.0, 0.50, 10.0],
+                        [10.0, 3.0, 2.0, 0.25, 20.0],
+                        [100.0, 7.0, 3.0, 1.00, 40.0]])
+
+
+@pytest.mark.parametrize("E,expect", [
+    (0.5, (5.0, 1.0, 0.5, 10.0)),                 # below the first node: clamped to row 0
+    (1.0, (5.0, 1.0, 0.5, 10.0)),                 # at node 0
+    (4.0, (13.0 / 3, 4.0 / 3, 0.5 - 0.25 / 3, 40.0 / 3)),   # a third of the way to node 1
+    (10.0, (3.0, 2.0, 0.25, 20.0)),               # at node 1
+    (55.0, (5.0, 2.5, 0.625, 30.0)),              # half way between nodes 1 and 2
+    (100.0, (7.0, 3.0, 1.0, 40.0)),               # at the last node
+    (1e3, (7.0, 3.0, 1.0, 40.0)),                 # beyond it: clamped to the last row
+])
+def test_table_lookup_hand_values(E, expect):
+    """Linear interpolation in |E| (not in log |E|) between the bracketing rows, clamped at both
+    ends: hand-computed values of a three-row table."""
+    got = disc.table_lookup(_HAND_TABLE, np.array([E]))
+    assert np.allclose([c[0] for c in got], expect, rtol=1e-14, atol=0)
+
+
+def test_table_slopes_hand_values():
+    """Segment slopes of the three-row table: (row k+1 - row k) / (E_{k+1} - E_k) inside, zero
+    beyond the ends."""
+    x = np.array([0.5, 4.0, 55.0, 2e3])
+    s = disc.table_slopes(_HAND_TABLE, x)
+    assert np.allclose(s[0], [0.0, -2.0 / 9, 4.0 / 90, 0.0], rtol=1e-14, atol=0)
+    assert np.allclose(s[3], [0.0, 10.0 / 9, 20.0 / 90, 0.0], rtol=1e-14, atol=0)
+
+
+def test_table_lookup_reproduces_linear_columns_on_the_log_spaced_table():
+    """On the 64-row log-spaced |E| nodes, a column that is linear in |E| is reproduced exactly
+    between any two nodes (interpolation in log |E|, or on the wrong segment, is not)."""
+    E = W.transport_table(seed=2)[:, 0]
+    tab = np.stack([E, 3.0 + 2e-4 * E, 1.0 + 0 * E, 7.0 - 1e-6 * E, 2.0 * E], axis=1)
+    rng = np.random.default_rng(5)
+    x = np.concatenate([np.exp(rng.uniform(np.log(E[0]), np.log(E[-1]), 500)), E])
+    got = disc.table_lookup(tab, x)
+    for c, ex in enumerate((3.0 + 2e-4 * x, 1.0 + 0 * x, 7.0 - 1e-6 * x, 2.0 * x)):
+        assert np.allclose(got[c], ex, rtol=1e-13, atol=0), c
