@@ -45,6 +45,35 @@ def _random_state(d, rng, scale=1.0):
     return u
 
 
+# Measured GPU-vs-oracle agreement of the steady paths (FP64, same algorithm, same counts):
+# 1e-16 .. 2e-14 relative max-norm per field on 17^2 ... 257^2, mixed 257^2 9e-13.  The contract
+# tolerances below (FP64 1e-10, mixed 1e-8) therefore hold with orders of magnitude to spare.
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-8
+# GPU and oracle evaluate the scale-free residual of the same state to 1e-9 relative
+# (test_residual_parity); a GPU result that met its tolerance meets the oracle's test up to that.
+RHO_AGREE = 1e-9
+
+
+def _assert_fields(ug, uo, tol, what=""):
+    for q in range(3):
+        err = np.abs(ug[q] - uo[q]).max() / np.abs(uo[q]).max()
+        assert err <= tol, (what, q, err)
+
+
+def _gpu_counts(st):
+    """(coarse steps, coarse Newton, coarse V-cycles, all steps, rejected, Newton, V-cycles)."""
+    return (st["coarse_steps"], st["coarse_newton"], st["coarse_vcycles"],
+            st["steps_accepted"] + st["steps_rejected"], st["steps_rejected"], st["newton_iterations"],
+            st["vcycles"])
+
+
+def _oracle_counts(rec_c, rec_f):
+    rr = rec_c + rec_f
+    return (len(rec_c), sum(r[2] for r in rec_c), sum(r[3] for r in rec_c), len(rr),
+            sum(1 for r in rr if not r[1]), sum(r[2] for r in rr), sum(r[3] for r in rr))
+
+
 CASES = [(8, 8, False), (32, 32, False), (32, 32, True), (64, 16, True), (16, 64, False), (128, 128, True)]
 
 
@@ -185,9 +214,7 @@ def test_line_smoother_linear_solve_parity(mg, n, R, table, precision):
     H = omg.Hierarchy(g, u, dt, phys, line=True)
     x, ho = H.solve(disc.to_vec(g, -F), eta, 200, scale=tn)
     xo = disc.from_vec(g, x)
-    tol = 1e-10 if precision == "fp64" else 1e-7
-    for q in range(3):
-        assert np.abs(xg[q] - xo[q]).max() <= tol * np.abs(xo[q]).max(), q
+    _assert_fields(xg, xo, FP64_TOL if precision == "fp64" else MIXED_TOL, precision)
     if precision == "fp64":
         assert abs(len(hg) - len(ho)) <= 1
         k = min(len(hg), len(ho), 6)
@@ -231,23 +258,24 @@ def test_steady_march_parity_small(mg, rel):
     assert ok
     assert st["steps_accepted"] == sum(1 for r in rec if r[1])
     assert st["newton_iterations"] == sum(r[2] for r in rec)
-    ug = s.get_state()
-    for q in range(3):
-        assert np.abs(ug[q] - uo[q]).max() <= 1e-8 * np.abs(uo[q]).max(), q
+    assert st["vcycles"] == sum(r[3] for r in rec)
+    _assert_fields(s.get_state(), uo, FP64_TOL)
 
 
 def test_solve_steady_continuation_parity_33(mg):
+    """129 -> 257-style two-level continuation at 17^2 -> 33^2 (Sec. 2): the oracle's steps,
+    rejections, Newton iterations and V-cycles on both grids, and its steady state to 1e-10."""
     d = W.make_discharge(32, seed=0, V_cathode=-300.0, use_table=True)
     g, phys = _oracle(d)
     u = np.stack([d.ne0, d.np0, d.V0])
-    s = mg.from_discharge(d, eta=1e-10, max_vcycles=200)
-    rc, st = s.solve_steady(1e-9)
+    s = mg.from_discharge(d, eta=1e-12, max_vcycles=200)
+    rc, st = s.solve_steady(1e-10)
     assert rc == mg.MG_OK
-    uo, ok, rc_, rf_ = osv.solve_steady(g, u, d.S_e, d.S_p, phys, 1e-9, osv.SolverOptions(eta=1e-10, max_vcycles=200))
+    uo, ok, rec_c, rec_f = osv.solve_steady(g, u, d.S_e, d.S_p, phys, 1e-10,
+                                            osv.SolverOptions(eta=1e-12, max_vcycles=200))
     assert ok
-    ug = s.get_state()
-    for q in range(3):
-        assert np.abs(ug[q] - uo[q]).max() <= 1e-7 * np.abs(uo[q]).max(), q
+    assert _gpu_counts(st) == _oracle_counts(rec_c, rec_f)
+    _assert_fields(s.get_state(), uo, FP64_TOL)
 
 
 @pytest.mark.parametrize("chain_from,dt_max", [(2, 1e-6), (3, 1.0)])
@@ -257,42 +285,75 @@ def test_solve_steady_chain_parity_65(mg, chain_from, dt_max):
     d = W.make_discharge(64, seed=1, V_cathode=-300.0, use_table=True)
     g, phys = _oracle(d)
     u = np.stack([d.ne0, d.np0, d.V0])
-    s = mg.from_discharge(d, eta=1e-10, max_vcycles=200, chain_from=chain_from, dt_max=dt_max)
-    rc, st = s.solve_steady(1e-9)
+    s = mg.from_discharge(d, eta=1e-12, max_vcycles=200, chain_from=chain_from, dt_max=dt_max)
+    rc, st = s.solve_steady(1e-10)
     assert rc == mg.MG_OK
-    opt = osv.SolverOptions(eta=1e-10, max_vcycles=200, chain_from=chain_from, dt_max=dt_max)
-    uo, ok, rec_c, rec_f = osv.solve_steady(g, u, d.S_e, d.S_p, phys, 1e-9, opt)
+    opt = osv.SolverOptions(eta=1e-12, max_vcycles=200, chain_from=chain_from, dt_max=dt_max)
+    uo, ok, rec_c, rec_f = osv.solve_steady(g, u, d.S_e, d.S_p, phys, 1e-10, opt)
     assert ok
-    assert st["coarse_steps"] == len(rec_c) and st["steps_accepted"] + st["steps_rejected"] == len(rec_c) + len(rec_f)
-    ug = s.get_state()
-    for q in range(3):
-        assert np.abs(ug[q] - uo[q]).max() <= 1e-7 * np.abs(uo[q]).max(), q
+    assert _gpu_counts(st) == _oracle_counts(rec_c, rec_f)
+    _assert_fields(s.get_state(), uo, FP64_TOL)
 
 
-def test_steady_257_chain_uncapped_residual_property(mg):
-    """257 x 257 from 33^2 up with the uncapped ramp (the paper's own schedule): the oracle's
-    residual of the result."""
+def test_steady_257_chain_uncapped_parity(mg):
+    """257 x 257 from 33^2 up with the uncapped ramp (the paper's own schedule, Sec. 2-3), the
+    library defaults otherwise: the oracle's schedule step for step and its steady state to
+    1e-10, and the oracle's residual of the result <= 1e-8."""
     d = W.steady_257()
     g, phys = _oracle(d)
     s = mg.from_discharge(d, chain_from=3, dt_max=1.0)
+    s.autotune()
     rc, st = s.solve_steady(1e-8)
     assert rc == mg.MG_OK, st
     ug = np.stack(s.get_state())
+    uo, ok, rec_c, rec_f = osv.solve_steady(g, np.stack([d.ne0, d.np0, d.V0]), d.S_e, d.S_p, phys, 1e-8,
+                                            osv.SolverOptions(chain_from=3, dt_max=1.0))
+    assert ok
+    assert _gpu_counts(st) == _oracle_counts(rec_c, rec_f)
+    _assert_fields(ug, uo, FP64_TOL)
     F, T = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
-    assert disc.rho(F, T).max() <= 1.05e-8
-    assert np.all(np.isfinite(ug))
+    assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE)
 
 
-def test_steady_257_full_size_residual_property(mg):
-    """257 x 257, table transport, continuation to rho <= 1e-8: the oracle's residual of the result."""
+@pytest.fixture(scope="module")
+def oracle_steady_257():
+    """The oracle's steady solve of the 257^2 workload with the default options (the two-level
+    129^2 -> 257^2 continuation to rho <= 1e-8): (state, coarse records, fine records)."""
+    d = W.steady_257()
+    g, phys = _oracle(d)
+    uo, ok, rec_c, rec_f = osv.solve_steady(g, np.stack([d.ne0, d.np0, d.V0]), d.S_e, d.S_p, phys, 1e-8,
+                                            osv.SolverOptions())
+    assert ok
+    return uo, rec_c, rec_f
+
+
+def test_steady_257_headline_parity(mg, oracle_steady_257):
+    """The benchmark's step: 257 x 257 nodes, table transport, -300 V, continuation 129^2 ->
+    257^2 to rho <= 1e-8 (abstract and Sec. 2), FP64, launch shapes autotuned as the benchmark
+    runs it.  Against the oracle's solve of the same inputs: the same steps, rejections, Newton
+    iterations and V-cycles on each grid (also the committed counts in
+    tests/golden/oracle_steady_257_counts.json), the steady state to 1e-10 relative max-norm per
+    field, and the oracle's residual of the GPU result <= 1e-8."""
+    import json
+    import os
     d = W.steady_257()
     g, phys = _oracle(d)
     s = mg.from_discharge(d)
+    s.autotune()
     rc, st = s.solve_steady(1e-8)
     assert rc == mg.MG_OK, st
     ug = np.stack(s.get_state())
+    uo, rec_c, rec_f = oracle_steady_257
+    assert _gpu_counts(st) == _oracle_counts(rec_c, rec_f)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_steady_257_counts.json")) as fh:
+        golden = json.load(fh)["levels"]
+    assert (st["coarse_steps"], st["coarse_newton"], st["coarse_vcycles"]) == (
+        golden[0]["steps"] + golden[0]["rejected"], golden[0]["newton"], golden[0]["vcycles"])
+    assert (st["newton_iterations"] - st["coarse_newton"], st["vcycles"] - st["coarse_vcycles"]) == (
+        golden[1]["newton"], golden[1]["vcycles"])
+    _assert_fields(ug, uo, FP64_TOL)
     F, T = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
-    assert disc.rho(F, T).max() <= 1.05e-8
+    assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE)
     assert np.all(np.isfinite(ug))
 
 
@@ -312,7 +373,7 @@ def test_transient_1025_full_size(mg):
         ug = np.stack(s.get_state())
         assert np.all(np.isfinite(ug))
         F, T = disc.residual(g, ug, u0, d.S_e, d.S_p, 1e-9, phys, with_terms=True)
-        assert disc.rho(F, T).max() <= 1.05e-10, (prec, disc.rho(F, T))
+        assert disc.rho(F, T).max() <= 1e-10 * (1 + RHO_AGREE), (prec, disc.rho(F, T))
         out.append(ug)
         s.close()
     for q in range(3):
@@ -339,7 +400,7 @@ def test_batched_full_sizes_residual_property(mg):
         g, phys = _oracle(d)
         ug = np.stack(sv.get_state())
         F, T = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
-        assert disc.rho(F, T).max() <= 1.05e-8, (d.nr, disc.rho(F, T))
+        assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE), (d.nr, disc.rho(F, T))
 
 
 def test_device_and_host_io_agree(mg):
@@ -500,20 +561,22 @@ def test_mixed_transient_33_matches_oracle(mg):
         assert np.abs(ug[q] - u[q]).max() <= 1e-8 * np.abs(u[q]).max(), q
 
 
-def test_mixed_steady_257_matches_fp64(mg):
+def test_mixed_steady_257_matches_oracle(mg, oracle_steady_257):
+    """Mixed precision (FP32 V-cycles inside the FP64 Newton loop) on the benchmark's 257^2
+    continuation: the oracle's residual of the result <= 1e-8, the FP64 oracle's steady state to
+    1e-8 relative per field, and the oracle's steps, Newton iterations and V-cycles."""
     d = W.steady_257()
     g, phys = _oracle(d)
-    s64 = mg.from_discharge(d)
     s32 = mg.from_discharge(d, precision=mg.MG_MIXED)
-    assert s64.solve_steady(1e-8)[0] == mg.MG_OK
+    s32.autotune()
     rc, st = s32.solve_steady(1e-8)
     assert rc == mg.MG_OK, st
-    a, b = np.stack(s64.get_state()), np.stack(s32.get_state())
+    b = np.stack(s32.get_state())
     F, T = disc.residual(g, b, None, d.S_e, d.S_p, None, phys, with_terms=True)
-    assert disc.rho(F, T).max() <= 1.05e-8
-    # both are the same discrete steady state to the solve tolerance
-    for q in range(3):
-        assert np.abs(a[q] - b[q]).max() <= 1e-6 * np.abs(a[q]).max(), q
+    assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE)
+    uo, rec_c, rec_f = oracle_steady_257
+    _assert_fields(b, uo, MIXED_TOL)
+    assert _gpu_counts(st) == _oracle_counts(rec_c, rec_f)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -559,7 +622,7 @@ def test_batched_steady_solves_equal_individual_solves(mg):
             assert np.array_equal(a[q], b[q])     # deterministic kernels: concurrency changes nothing
         g, phys = _oracle(d)
         F, T = disc.residual(g, np.stack(a), None, d.S_e, d.S_p, None, phys, with_terms=True)
-        assert disc.rho(F, T).max() <= 1.05e-8
+        assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE)
 
 
 def test_autotune_keeps_results(mg):
