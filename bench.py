@@ -12,8 +12,9 @@ every implicit step, down to a scale-free steady residual of 1e-8.
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its own
 independent copy of the workload (replicas: the method has no cross-GPU exchange);
 `value` is the total number of solves of all ranks divided by the slowest rank's time.
-`--impl reference` times the FP64 CPU oracle on the host cores instead, on a bounded
-sample of the same workload scaled to solves/s by the oracle's own work counts.
+`--impl reference` times the FP64 CPU oracle on the host cores instead: every step is one
+full steady solve of the same workload, the steps spread over concurrent single-threaded
+processes (one per host core).
 """
 from __future__ import annotations
 
@@ -165,28 +166,94 @@ BAD_REASONS = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
 
 
 # ------------------------------------------------------------------ oracle (CPU baseline)
-def oracle_estimate(sample_vcycles: int = 4):
-    """Estimated oracle seconds per steady solve: per-unit oracle times measured now on this
-    host x the oracle's own work counts for this workload (tests/golden)."""
+_ORACLE_CASE = None
+
+
+def _oracle_worker_init():
+    """Worker start-up (outside any timed region): imports and the workload's inputs."""
+    global _ORACLE_CASE
     import workloads as W
-    from oracle import profile_counts
-    with open(os.path.join(ROOT, "tests", "golden", "oracle_steady_257_counts.json")) as fh:
-        counts = json.load(fh)
+    from oracle import discretization as disc
+    from oracle.grid import Grid
     d = W.steady_257()
+    g = Grid(d.nr, d.nz, d.R, d.z)
+    phys = disc.Physics(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p,
+                        D_p=d.D_p, table=d.table, pressure_factor=d.pressure_factor)
+    _ORACLE_CASE = (d, g, phys)
+
+
+def _oracle_ping(_):
+    return os.getpid()
+
+
+def oracle_solve(_=None):
+    """One full steady solve of the benchmark workload by the FP64 oracle, on one thread:
+    the 129^2 march, the prolongation and the 257^2 march to rho <= 1e-8, with the oracle's
+    default options (the algorithm and counts of the GPU path).  Returns (seconds, steps,
+    Newton iterations, V-cycles)."""
+    from oracle import solver as osv
+    if _ORACLE_CASE is None:
+        _oracle_worker_init()
+    d, g, phys = _ORACLE_CASE
+    u0 = np.stack([d.ne0, d.np0, d.V0])
     t0 = time.perf_counter()
-    total = 0.0
-    detail = {}
-    for lev in counts["levels"]:
-        ut = profile_counts.unit_times(d, lev["n"], vcycles=sample_vcycles)
-        steps = lev["steps"] + lev["rejected"]
-        # per Newton iteration one Jacobian hierarchy; per step (newton + 1) residuals for the
-        # Newton test and one steady residual; per V-cycle one cycle and its residual norm
-        est = (lev["newton"] * ut["hierarchy"] + lev["vcycles"] * ut["vcycle"]
-               + (lev["newton"] + 2 * steps) * ut["residual"])
-        detail[str(lev["n"] + 1)] = {k: round(v, 4) for k, v in ut.items()}
-        total += est
-    sample_s = time.perf_counter() - t0
-    return total, sample_s, detail, counts
+    _, ok, rec_c, rec_f = osv.solve_steady(g, u0, d.S_e, d.S_p, phys, TOL, osv.SolverOptions())
+    sec = time.perf_counter() - t0
+    if not ok:
+        raise RuntimeError("oracle steady solve failed")
+    rr = rec_c + rec_f
+    return sec, len(rr), sum(r[2] for r in rr), sum(r[3] for r in rr)
+
+
+def host_cores() -> int:
+    """Host cores this process may run on (the affinity mask; all cores without one)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_solves(n: int, procs: int, warmup: int = 0):
+    """n full oracle solves on `procs` concurrent single-threaded worker processes (spawned, so
+    safe after CUDA initialisation), after `warmup` untimed solves on the same workers.  The
+    clock starts once every worker has imported the oracle and built its inputs.  Returns
+    (wall seconds of the n solves, per-solve records)."""
+    if procs <= 1:
+        _oracle_worker_init()
+        for _ in range(warmup):
+            oracle_solve()
+        t0 = time.perf_counter()
+        recs = [oracle_solve() for _ in range(n)]
+        return time.perf_counter() - t0, recs
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_oracle_worker_init) as pool:
+        pids = set()
+        while len(pids) < procs:
+            pids |= set(pool.map(_oracle_ping, range(4 * procs), chunksize=1))
+        if warmup:
+            pool.map(oracle_solve, range(warmup), chunksize=1)
+        t0 = time.perf_counter()
+        recs = pool.map(oracle_solve, range(n), chunksize=1)
+        wall = time.perf_counter() - t0
+    return wall, recs
+
+
+def cpu_baseline_legs():
+    """The oracle timed on this host: one full solve on one thread, then one full solve on each
+    host core at once (single-threaded processes: the replica throughput of the host)."""
+    cores = host_cores()
+    t1, rec1 = oracle_solves(1, 1)
+    tn, recn = oracle_solves(cores, cores)
+    sec, steps, newton, vc = rec1[0]
+    return {"value": cores / tn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{cores} full steady solves of the benchmark workload (129^2 march, prolongation, "
+                       f"257^2 march to rho <= 1e-8; {steps} steps, {newton} Newton iterations, {vc} V-cycles "
+                       f"each), one single-threaded oracle process per host core, {tn:.1f} s wall"),
+            "nproc": os.cpu_count(), "wall_s": tn,
+            "per_solve_s": [round(r[0], 3) for r in recn],
+            "single_thread": {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "seconds_per_solve": t1,
+                              "sample": "one full steady solve of the benchmark workload on one thread"}}
 
 
 def max_over_ranks(vals, world, device):
@@ -207,34 +274,28 @@ def whole_job_rate(world, steps, seconds):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper has no code of its own) timed on this
+    host's cores.  Every step is one full steady solve of the benchmark workload; the steps run
+    on min(steps, host cores) concurrent single-threaded processes, after `warmup` untimed
+    solves on the same processes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        oracle_estimate(sample_vcycles=1)
-    ests, samples = [], []
-    detail = counts = None
-    # each step is one bounded sample; with many steps the sample shrinks to one V-cycle per
-    # grid so that the whole run stays within a few minutes
-    nv = args.ref_vcycles if args.steps <= 5 else 1
-    for _ in range(args.steps):
-        est, sample_s, detail, counts = oracle_estimate(sample_vcycles=nv)
-        ests.append(est)
-        samples.append(sample_s)
-    ms = 1000.0 * sum(ests) / len(ests)
-    value = 1000.0 / ms
-    cores = 1
+    procs = max(1, min(args.steps, host_cores()))
+    wall, recs = oracle_solves(args.steps, procs, warmup=min(args.warmup, procs))
+    value = args.steps / wall
+    ms = 1000.0 * wall / args.steps
+    _, steps, newton, vc = recs[0]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "n/a (host CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": (f"per step: oracle residual, Jacobian hierarchy and {nv} "
-                                    f"V-cycles timed on 129^2 and 257^2 ({statistics.mean(samples):.1f} s of CPU), "
-                                    "scaled by the oracle's own counts for the full continuation "
-                                    f"({counts['levels']})"),
-                         "unit_times_s": detail},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": (f"{args.steps} full steady solves of the benchmark workload ({steps} steps, "
+                                    f"{newton} Newton iterations, {vc} V-cycles each) on {procs} concurrent "
+                                    f"single-threaded oracle processes, {wall:.1f} s wall"),
+                         "nproc": os.cpu_count(), "per_solve_s": [round(r[0], 3) for r in recs]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -477,12 +538,7 @@ def run_ours(args):
     if not args.no_forms:
         line["forms"] = measure_forms(args, dev, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, sample_s, detail, counts = oracle_estimate(sample_vcycles=args.ref_vcycles)
-        line["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": (f"oracle residual, Jacobian hierarchy and {args.ref_vcycles} V-cycles "
-                                           f"timed on 129^2 and 257^2 ({sample_s:.1f} s of CPU), scaled by the "
-                                           "oracle's own work counts for the full continuation"),
-                                "unit_times_s": detail}
+        line["cpu_baseline"] = cpu_baseline_legs()
     if world > 1:
         dist.barrier(device_ids=[local])
         dist.destroy_process_group()
@@ -763,7 +819,6 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-vcycles", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / batched form measurements")
     ap.add_argument("--batch-workers", type=int, default=16)

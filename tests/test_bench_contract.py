@@ -13,7 +13,7 @@ def _run(env_extra=None):
     env = dict(os.environ)
     env.update(env_extra or {})
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--ref-vcycles", "1"], cwd=ROOT, env=env, capture_output=True,
+                        "--warmup", "0"], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=600)
     return p
 
@@ -35,6 +35,8 @@ def test_reference_line_has_the_contract_keys():
     assert "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    # one step is one full steady solve of the workload, timed (not extrapolated)
+    assert len(cb["per_solve_s"]) == 1 and abs(cb["per_solve_s"][0] - d["ms_per_step"] / 1000.0) < 1.0
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
