@@ -44,6 +44,34 @@ TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20
 
 
+# Algorithmic (one-pass minimum) figures per node of a level, independent of how a kernel stores
+# or re-reads its operands; the roofline fractions below use these.  A stored-coefficient
+# red-black sweep reads the 12 face coefficients, the right-hand side f and the correction du
+# and writes du once: 12 + 3 + 3 + 3 values = 168 B per node in FP64, 84 B in FP32; a half sweep
+# (one colour per launch) is half a sweep, 84 / 42 B per node of the level.  About 100 FP64
+# flops per node and sweep.  Per V-cycle each level adds its linear residual (168 B per node),
+# the restriction (30 B) and the prolongation with the correction (54 B).
+ALG_SWEEP_BYTES_FP64 = 168
+ALG_SWEEP_FLOPS = 100
+ALG_TRANSFER_BYTES_FP64 = 168 + 30 + 54
+
+
+def alg_vcycle_bytes(n_iv: int, fp64: bool, sweeps_of) -> float:
+    """Algorithmic bytes of one V-cycle on a grid of n_iv intervals per side: every level above
+    the coarsest (n > 2) smooths sweeps_of(n) times and transfers once (the figures above)."""
+    tot, n = 0.0, n_iv
+    while n > 2:
+        tot += (n + 1) * (n - 1) * (sweeps_of(n) * ALG_SWEEP_BYTES_FP64 + ALG_TRANSFER_BYTES_FP64)
+        n //= 2
+    return tot if fp64 else tot / 2
+
+
+def default_sweeps(n: int) -> int:
+    """Pre- + post-smoothing sweeps of the library's default rule on a level of n intervals:
+    V(4,4) above 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down."""
+    return 2 if n <= 8 else (4 if n <= 64 else 8)
+
+
 # DRAM bytes read + written by one half sweep at 1025^2 in an ncu capture (cold caches):
 # k_smooth<double> (profiles/k_smooth_fp64_1025.md), k_smooth<float> (k_smooth_fp32_1025_mixed.md)
 TRAFFIC_K_SMOOTH_FP64_1025 = 182969344
@@ -76,11 +104,16 @@ def _vcycle_1025(precision, peaks):
     n, ms = s.profile_end()
     s.close()
     avg = ms / n / 1000.0
-    # algorithmic bytes of one launch (FP64 figures; FP32 halves them): a half sweep reads all
-    # face coefficients and conductances once, the colour's factors, f and du and the other
-    # colour's du, and writes the colour's du (176 B per unknown node); a fused sweep 228 B
-    byt = (228 if fused else 176) * nodes // (1 if fp64 else 2)
-    flo = 52 * nodes if fused else 26 * nodes
+    # algorithmic bytes and flops of one launch (the one-pass figures above; FP32 halves the
+    # bytes): a half sweep is half a sweep over the level's unknown nodes
+    per_node = ALG_SWEEP_BYTES_FP64 * (1.0 if fp64 else 0.5) * (1.0 if fused else 0.5)
+    byt = per_node * nodes
+    flo = ALG_SWEEP_FLOPS * (1.0 if fused else 0.5) * nodes
+    # what the kernel actually moves and executes (its stored operands: all 12 face coefficients
+    # and 2 conductances per colour launch, the colour's 7 factors, f and du, the other colour's
+    # du; 27 FP64 instructions = 52 flops per updated node), for comparison
+    touched = (228 if fused else 176) * nodes // (1 if fp64 else 2)
+    executed = 52 * nodes if fused else 26 * nodes
     hbm = peaks.get("hbm_gbs", 6800.0)
     name = ("k_sweep" if fused else "k_smooth") + ("<double>" if fp64 else "<float>")
     # ncu DRAM read + write per launch, cold caches (profiles/k_smooth_fp32_1025_mixed.md,
@@ -89,14 +122,22 @@ def _vcycle_1025(precision, peaks):
     roof = {"bound": "hbm", "kernel": name + (" (fused red-black sweep" if fused else " (red-black half sweep")
             + ", 1025x1025 level)", "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6, "algorithmic_bytes_per_launch": byt,
-            "traffic": traffic, "peak_source": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+            "algorithmic_bytes_per_node": per_node,
+            "bytes_touched_per_launch": touched, "frac_bytes_touched": touched / avg / 1e9 / hbm,
+            "traffic": traffic, "traffic_over_algorithmic": (traffic / byt) if traffic else None,
+            "peak_source": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     if fp64:
         fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e9
         roof["fp64"] = {"achieved": flo / avg / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
                         "frac": flo / avg / 1e9 / fp64_peak, "algorithmic_flops_per_launch": flo,
+                        "executed_flops_per_launch": executed, "frac_executed": executed / avg / 1e9 / fp64_peak,
                         "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    vbytes = alg_vcycle_bytes(d.nr, fp64, default_sweeps)
+    roof_v = {"bytes_per_cycle": vbytes, "achieved": vbytes / vc / 1e9, "peak": hbm, "unit": "GB/s",
+              "frac": vbytes / vc / 1e9 / hbm,
+              "note": "one-pass bytes of every level's sweeps and transfers, default sweep counts"}
     return {"vcycle_us": vc * 1e6, "mpts_per_s": (d.nr + 1) * (d.nz + 1) / vc / 1e6,
-            "residual_drop_30_cycles": float(hist[-1]), "roofline": roof}
+            "residual_drop_30_cycles": float(hist[-1]), "roofline": roof, "vcycle_roofline": roof_v}
 
 
 def _peaks():
@@ -474,13 +515,13 @@ def run_ours(args):
         n_iv = d.nr >> lev
         nodes = (n_iv + 1) * (n_iv - 1)        # unknown nodes of the level
         fused = bool(shapes[lev, 2])
-        # fused red-black sweep launch (both colours): the 12 face coefficients, 2 Poisson
-        # conductances, 7 block factors and 3 right-hand sides of every node once (8 B each), the
-        # old black corrections read (3 x 8 B per black node) and both colours' corrections
-        # written.  Half-sweep launch (one colour): all face coefficients and conductances once,
-        # the colour's factors, f and du (8 B each) and the other colour's du read.
-        byt = (228 if fused else 176) * nodes
-        flo = 52 * nodes if fused else 52 * (nodes / 2)   # 20 FMA off-diagonal + block solve per updated node
+        # algorithmic bytes and flops of one launch (one-pass figures, FP64): a half sweep is
+        # half a sweep over the level's unknown nodes; the executed count (27 FP64 instructions,
+        # 52 flops per updated node) and the bytes the kernel touches are kept beside them
+        byt = ALG_SWEEP_BYTES_FP64 * nodes * (1.0 if fused else 0.5)
+        flo = ALG_SWEEP_FLOPS * nodes * (1.0 if fused else 0.5)
+        executed = 52 * nodes if fused else 52 * (nodes / 2)
+        touched = (228 if fused else 176) * nodes
         # duration of one launch as the solve's graphs run it: one smoothing phase of the level
         # (its nu sweeps, as each V-cycle issues them) replayed from a captured graph (back to
         # back, programmatic dependent launch, the level's arrays in L2 as in the V-cycle), the
@@ -497,7 +538,9 @@ def run_ours(args):
                        "sweeps_per_phase": nu_l, "avg_launch_us": us_graph,
                        "avg_launch_us_200_sweep_graph": us_long, "gflops": flo / avg / 1e9,
                        "frac_fp64": flo / avg / 1e9 / fp64_peak_nominal, "gbs": byt / avg / 1e9,
-                       "flops_per_launch": flo, "bytes_per_launch": byt,
+                       "flops_per_launch": flo, "bytes_per_launch": byt, "executed_flops_per_launch": executed,
+                       "frac_fp64_executed": executed / avg / 1e9 / fp64_peak_nominal,
+                       "bytes_touched_per_launch": touched,
                        "traffic": traffic_ncu.get((n_iv, fused))})
     dom = max(levels, key=lambda r: r["launches"] * r["avg_launch_us"])
     half_name = "k_smooth_ilp<double>" if dom["nodes_per_side"] <= 129 else "k_smooth<double>"
@@ -514,8 +557,11 @@ def run_ours(args):
                                          "7 replays (mg_time_smoother)"),
                 "avg_launch_us_200_sweep_graph": dom["avg_launch_us_200_sweep_graph"],
                 "algorithmic_flops_per_launch": dom["flops_per_launch"],
+                "executed_flops_per_launch": dom["executed_flops_per_launch"],
+                "frac_executed": dom["frac_fp64_executed"],
                 "hbm": {"achieved": dom["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": dom["gbs"] / hbm_peak,
                         "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+                        "bytes_touched_per_launch": dom["bytes_touched_per_launch"],
                         "peak_source": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
                 "smoother_levels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                                     for r in levels]}
@@ -527,6 +573,11 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "vcycle_mpts_per_s": vcycle_mpts, "vcycle_us_257": vcycle_s * 1e6, "vcycle_kind": "V(4,4) above 65^2, V(2,2) from 65^2 down",
+        "vcycle_roofline_257": {"bytes_per_cycle": alg_vcycle_bytes(d.nr, True, default_sweeps),
+                                "achieved": alg_vcycle_bytes(d.nr, True, default_sweeps) / vcycle_s / 1e9,
+                                "peak": hbm_peak, "unit": "GB/s",
+                                "frac": alg_vcycle_bytes(d.nr, True, default_sweeps) / vcycle_s / 1e9 / hbm_peak,
+                                "note": "257^2 arrays are L2-resident: HBM is not the bound at this size"},
         "vcycle_v22_mpts_per_s": N0 / vcycle22_s / 1e6, "vcycle_v22_us_257": vcycle22_s * 1e6,
         "solve_stats": {k: st[k] for k in ("steps_accepted", "steps_rejected", "newton_iterations", "vcycles",
                                            "coarse_steps", "coarse_newton", "coarse_vcycles", "steady_rho")},
@@ -683,30 +734,42 @@ def measure_forms(args, dev, peaks):
     argon["workload"] = ("257x257 nodes, d = 1.1 cm, R = 2.7 cm, 0 V / 255.9 V, Dirichlet walls, "
                          "mu_e = 30/p at 0.514 torr, stand-in mu_p = 0.22 m^2/Vs, FP64, rho <= 1e-8")
     out["argon_257"] = argon
+    # the mixed-precision workload in full: ten 1 ns steps at 1025^2, mixed and FP64, the
+    # per-field error against the FP64 oracle's ten steps and the residual history
+    out["transient_1025_ten_steps"] = transient_1025_report(dev)
     # V-cycles at 1025^2 (transient physics, dt = 1 ns): the FP32 inner cycle of the mixed form
     # and the plain FP64 cycle, each with the roofline of its finest-level smoother
     out["mixed_vcycle_1025"] = _vcycle_1025(mg.MG_MIXED, peaks)
     out["fp64_vcycle_1025"] = _vcycle_1025(mg.MG_FP64, peaks)
-    # batched form: 64 independent discharges of seeded sizes 65^2..513^2, mixed precision
+    # batched form: 64 independent discharges of seeded sizes 65^2..513^2, mixed precision, as
+    # the persistent work-list launch (workers = 0: one launch per round of Newton iterations of
+    # every discharge) and, for comparison, as 16 host threads each solving one discharge at a time
     ds = W.batch_64()
     solvers = [mg.from_discharge(dd, precision=mg.MG_MIXED, stream=torch.cuda.Stream(device=dev)) for dd in ds]
     inits = [[np.ascontiguousarray(a) for a in (dd.ne0, dd.np0, dd.V0)] for dd in ds]
     for sv in solvers:
         sv.autotune()
-    for rep in range(2):
-        for sv, ini in zip(solvers, inits):
-            sv.set_state(*ini)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, ms_i, rcs = mg.solve_steady_batch(solvers, TOL, workers=args.batch_workers)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if rc != mg.MG_OK:
-            raise RuntimeError(f"batched solve failed: {rcs}")
     sizes = sorted(set(dd.nr + 1 for dd in ds))
-    out["batch_64"] = {"solves_per_s": len(ds) / wall, "wall_s": wall, "p50_ms": float(np.percentile(ms_i, 50)),
-                       "p99_ms": float(np.percentile(ms_i, 99)), "instances": len(ds), "sizes": sizes,
-                       "workers": args.batch_workers, "precision": "mixed"}
+    batch = {"instances": len(ds), "sizes": sizes, "precision": "mixed"}
+    for name, workers in (("persistent", 0), ("host_threads", args.batch_workers)):
+        for rep in range(2):
+            for sv, ini in zip(solvers, inits):
+                sv.set_state(*ini)
+            torch.cuda.synchronize()
+            n0 = mg.kernel_launches()
+            t0 = time.perf_counter()
+            rc, ms_i, rcs = mg.solve_steady_batch(solvers, TOL, workers=workers)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            launches = mg.kernel_launches() - n0
+            if rc != mg.MG_OK:
+                raise RuntimeError(f"batched solve ({name}) failed: {rcs}")
+        batch[name] = {"solves_per_s": len(ds) / wall, "wall_s": wall, "p50_ms": float(np.percentile(ms_i, 50)),
+                       "p99_ms": float(np.percentile(ms_i, 99)), "kernel_launches": launches,
+                       "workers": workers}
+    batch["persistent"]["per_instance_time"] = "from the batch's start to the instance's solve returning"
+    batch["host_threads"]["per_instance_time"] = "from the instance's start to its stream being idle"
+    out["batch_64"] = batch
     for sv in solvers:
         sv.close()
     # learned initial guess (committed weights, trained on the device): time to rho <= 1e-8 on
@@ -755,6 +818,61 @@ def measure_forms(args, dev, peaks):
     # tensor-core convolutions of the network: forward and training step on a batch of 16 at 257^2
     out["unet_257"] = measure_unet(dev, peaks)
     return out
+
+
+def load_oracle_1025():
+    """The oracle's ten steps of the 1025^2 workload (tests/golden/oracle_transient_1025.npz,
+    written by tests/golden/make_oracle_1025.py from the oracle alone), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_transient_1025.npz")
+    if not os.path.exists(path):
+        return None
+    with np.load(path) as z:
+        return {k: z[k] for k in z.files}
+
+
+def transient_1025_report(dev):
+    """Ten backward-Euler steps of 1 ns on 1025 x 1025 nodes (each to rho <= 1e-10), mixed and
+    FP64, autotuned: per step the Newton iterations, V-cycles and rho, the V-cycle residual
+    history of the first Newton system, and the per-field max relative error against the FP64
+    oracle (max over every 8th node in both directions, relative to the oracle field's max-norm
+    over all nodes)."""
+    import torch
+    import workloads as W
+    from paper_0811_4446_gb300 import mg
+    gold = load_oracle_1025()
+    d = W.transient_1025()
+    res = {"workload": "1025x1025 nodes, constant transport, -200 V, seed 0; 10 steps of 1 ns to rho <= 1e-10",
+           "oracle_golden": None if gold is None else "tests/golden/oracle_transient_1025.npz (every 8th node)"}
+    for name, prec in (("mixed", mg.MG_MIXED), ("fp64", mg.MG_FP64)):
+        s = mg.from_discharge(d, precision=prec)
+        s.autotune()
+        F, _ = s.residual(1e-9)
+        _, hist, _ = s.linear_solve(1e-9, [-a for a in F], 1e-10, 60)
+        s.set_state(*[np.ascontiguousarray(a) for a in (d.ne0, d.np0, d.V0)])
+        steps, errs = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(10):
+            s.reset_stats()
+            rc, st = s.step(1e-9, 1e-10)
+            if rc != mg.MG_OK:
+                raise RuntimeError(f"1025^2 {name} step {k} failed: {rc}")
+            steps.append({"newton": st["last_newton"], "vcycles": st["vcycles"], "rho": st["rho"]})
+            if gold is not None:
+                u = np.stack(s.get_state())[:, ::int(gold["stride"]), ::int(gold["stride"])]
+                errs.append([float(np.abs(u[q] - gold["samples"][k][q]).max() / gold["norms"][k][q])
+                             for q in range(3)])
+        torch.cuda.synchronize()
+        row = {"ms_per_step": 1000.0 * (time.perf_counter() - t0) / 10, "steps": steps,
+               "first_system_residual_history": [float(h) for h in hist]}
+        if gold is not None:
+            row["max_rel_err_per_field_vs_oracle"] = {"n_e": max(e[0] for e in errs), "n_p": max(e[1] for e in errs),
+                                                      "V": max(e[2] for e in errs)}
+            row["max_rel_err_per_field_last_step"] = dict(zip(("n_e", "n_p", "V"), errs[-1]))
+            row["oracle_newton_per_step"] = [int(x) for x in gold["newton"]]
+        res[name] = row
+        s.close()
+    return res
 
 
 def unet_conv_flops(n: int = 256) -> float:

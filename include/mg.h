@@ -258,13 +258,28 @@ int mg_solve_steady(mg_state *s, double tol, mg_stats *stats);
 int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const double *V, int where, double tol,
                           mg_stats *stats, int *used_fallback);
 
-/* Batched form: solve n independent discharges to their steady states (mg_solve_steady on
- * each) concurrently.  `workers` host threads take instances from a shared queue; every state
- * runs on its own stream (give each state a distinct stream at mg_create so that the GPU can
- * overlap them) and every linear solve is a device-side CUDA-graph loop.  ms_out[k] (may be
- * NULL) receives instance k's wall time from its start to its stream being idle, rc_out[k]
- * (may be NULL) its status.  Returns MG_OK or the first failing instance's status.  The
- * states must live on the calling thread's current device. */
+/* Batched form: solve n independent discharges (the paper solves one discharge at a time,
+ * Sec. 2) to their steady states (mg_solve_steady on each).
+ *   workers = 0: the persistent work-list form.  Every discharge runs its own march (Delta-t
+ *     ramp, continuation, accept / reject) on a host thread of its own; whenever all discharges
+ *     still solving have reached a Newton iteration, ONE launch of a persistent kernel (replayed
+ *     from a captured CUDA graph) carries out that iteration for all of them: hierarchy set-up,
+ *     the V-cycle loop with each discharge's own stopping test on the device, the update and
+ *     the residual of the new state.  The CTAs take work items (tiles of a level's phase) from
+ *     whichever discharge has work open; a discharge's phases run in the order of the
+ *     single-discharge path and give the same results bit for bit.  Needs the point smoother,
+ *     the Picard Jacobian, the coarse-cycle kernel (coarse_kernel_n > 0) at or below the
+ *     continuation's first grid, a coarsest level of at most 48 unknowns and smooth_phase = 0;
+ *     otherwise the call falls back to 16 host threads.  ms_out[k]: from the batch's start to
+ *     discharge k's solve returning.  A work list that stops making progress (no work item
+ *     claimed for 5 s) ends the launch with MG_ETIMEOUT.
+ *   workers > 0: the comparison form: `workers` host threads take instances from a shared queue
+ *     and run mg_solve_steady on each state's own stream (give each state a distinct stream at
+ *     mg_create so that the GPU can overlap them), every linear solve a device-side CUDA-graph
+ *     loop; ms_out[k]: instance k's wall time from its start to its stream being idle.
+ * rc_out[k] (may be NULL) receives instance k's status.  Returns MG_OK or the first failing
+ * instance's status; MG_EINVAL for workers < 0.  The states must live on the calling thread's
+ * current device and must not be used by other threads during the call. */
 int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, double *ms_out, int *rc_out);
 
 /* Autotuner of the smoother's launch shapes: times the red-black half sweep and the fused

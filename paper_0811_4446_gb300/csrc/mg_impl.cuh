@@ -130,6 +130,60 @@ struct SolveCtl {
   double hist[kMaxHist];
 };
 
+// ---- batched form: one persistent launch runs a Newton iteration of many discharges --------
+// Each participating discharge follows a program of phases (the launches of one Newton
+// iteration of the single-discharge path, in order: hierarchy set-up, the V-cycle loop with its
+// stopping test, the update and the residual of the new state).  A phase is a list of work items
+// (tiles); the CTAs of the launch claim tiles of any discharge's current phase, and the CTA that
+// finishes a phase's last tile folds its reductions and moves that discharge to its next phase.
+enum BatchKind : int32_t {
+  BK_INJECT = 0, BK_COEFL, BK_FACTORL, BK_CFACT, BK_ZERO64, BK_NORM0, BK_ZERO32, BK_HALF64, BK_HALF32,
+  BK_RESTR64, BK_RESTR32, BK_COARSE64, BK_COARSE32, BK_PROL64, BK_PROL32, BK_MIXUPD, BK_NORMC, BK_UPDATE,
+  BK_COEF0, BK_RESID, BK_DONE
+};
+struct BPhase {
+  int32_t kind;
+  int32_t level;    // the level worked on (the fine level of a transfer, the first of a range)
+  int32_t arg;      // colour of a half sweep; last level of a range
+  int32_t ntiles;   // work items of the phase (0: the end of the program)
+  int32_t grain;    // thread-block rounds per work item
+  int32_t nblocks;  // thread blocks of the kernel the phase stands for (reduction partials)
+};
+constexpr int kBatchThreads = 256;   // threads per CTA of the persistent launch
+constexpr int kBatchMaxProg = 512;   // phases per program
+struct BatchInst {
+  const BPhase *prog;               // device program of this root level
+  int32_t loop_pc, update_pc, l0, last, mixed, max_cycles;
+  const LevelSet *S;
+  const CoarseSet<double> *cs64;
+  const CoarseSet<float> *cs32;
+  Transport tr;
+  double dt_inv, n0, eta, w[3];
+  SolveCtl *ctl;
+  double *partials, *dout, *Minv, *rs, *cs;
+  int *flag;
+  double *fss[3];
+  // run state, reset by the host before each launch
+  unsigned long long claim;         // (sequence << 32) | work items claimed of the current phase
+  unsigned long long ring[4];       // (sequence << 32) | program counter of phase `sequence`, at sequence & 3
+  unsigned int done;                // work items finished of the current phase
+  int32_t pad;
+};
+struct BatchRes {                   // what the host reads back per discharge
+  double out[18];                   // the residual sums (0..15) and the update's max |dV|, non-finite flag
+  double r0, rel;                   // the linear solve's initial weighted residual and last ratio
+  int32_t ncyc, pad;
+};
+struct BatchHead {
+  int32_t n;                        // discharges in this launch
+  int32_t ndone;                    // discharges whose program has ended
+  unsigned int err;                 // 1: a CTA found no work for kBatchIdleNs (the launch gave up)
+  int32_t pad;
+};
+cudaError_t launch_batch(BatchHead *head, BatchInst *inst, BatchRes *res, int grid, cudaStream_t st);
+int batch_grid();                   // CTAs of the persistent launch: SMs x resident CTAs per SM (0: error)
+size_t batch_smem_bytes();
+
 // ---- launch wrappers (mg_kernels.cu) ------------------------------------------------------
 // All take the stream last and return cudaGetLastError() of the launch.  While a stream capture
 // is being recorded (set_capturing(true)) launches are not counted: graph replays are counted

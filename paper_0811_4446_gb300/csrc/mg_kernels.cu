@@ -13,6 +13,8 @@
 // x = radial index (coalesced), y = axial index.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include <cstdio>
 
 #include "mg_impl.cuh"
@@ -447,13 +449,13 @@ cudaError_t launch_inject_levels(const LevelSet *S, const Level &L0, int l0, int
 // (out[12..15]), t = A (|n| + |n|): the residual of a step that starts from this state (u_old
 // = u, so the time term of F vanishes) has the steady F, and its term norms follow for any dt
 // from sum((Ts + t / dt)^2) = sum(Ts^2) + 2 sum(Ts t) / dt + sum(t^2) / dt^2.
-__global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, double dt_inv, int write_f,
-                                                         int steady_too, double *F0, double *F1, double *F2,
-                                                         double *fs0, double *fs1, double *fs2, double *partials,
-                                                         unsigned *counter, double *out) {
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * CBY + threadIdx.y + 1;
-  double acc[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+// One unknown row of k_resid_coef: F and T of node (i, j), the 16 sums' terms in acc (zero
+// outside the unknown rows), f / F / fs written as requested.
+__device__ __forceinline__ void resid_row(const Level &L, const StateView &sv, double dt_inv, int write_f,
+                                          int steady_too, double *F0, double *F1, double *F2, double *fs0,
+                                          double *fs1, double *fs2, int i, int j, double (&acc)[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
   if (i < L.ni && j < L.nz) {
     const int P = L.P;
     const size_t k = (size_t)j * P + i;
@@ -502,6 +504,16 @@ __global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, 
     acc[0] = Fe * Fe; acc[1] = Fp * Fp; acc[2] = FV * FV;
     acc[3] = Te * Te; acc[4] = Tp * Tp; acc[5] = TV * TV;
   }
+}
+
+__global__ void __launch_bounds__(32 * CBY) k_resid_coef(Level L, StateView sv, double dt_inv, int write_f,
+                                                         int steady_too, double *F0, double *F1, double *F2,
+                                                         double *fs0, double *fs1, double *fs2, double *partials,
+                                                         unsigned *counter, double *out) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  double acc[16];
+  resid_row(L, sv, dt_inv, write_f, steady_too, F0, F1, F2, fs0, fs1, fs2, i, j, acc);
   if (steady_too) {
     reduce_finish<16>(acc, partials, counter, out, 0);
   } else {
@@ -1345,27 +1357,23 @@ __device__ __forceinline__ void restrict_node(const LevelT<T> &F, const LevelT<T
 // coarse nodes (plus the one-node ring the full weighting reaches) into shared memory and
 // restricts them; r never goes to global memory.  Same per-node arithmetic and summation order
 // as linres_node followed by restrict_node.
+// One CX x CY tile of coarse nodes from (I0, J0), threads tid of nthr (all of the CTA reach
+// its barrier), sr: 3 x (2 CX + 1)(2 CY + 1) values of shared memory.
 template <typename T, int CX, int CY>
-__global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) k_linres_restrict(LevelT<T> F,
-                                                                                                 LevelT<T> C) {
+__device__ __forceinline__ void linres_restrict_tile(const LevelT<T> &F, const LevelT<T> &C, int I0, int J0, int tid,
+                                                     int nthr, T *sr) {
   constexpr int FW = 2 * CX + 1, FH = 2 * CY + 1;
-  __shared__ T sr[3][FH * FW];
-  pdl_launch_dependents();
-  pdl_wait();
-  const int I0 = blockIdx.x * CX, J0 = 1 + blockIdx.y * CY;
-  const int tid = threadIdx.x;
-  for (int t = tid; t < FW * FH; t += blockDim.x) {
+  for (int t = tid; t < FW * FH; t += nthr) {
     const int fi = 2 * I0 - 1 + t % FW, fj = 2 * J0 - 1 + t / FW;
     Triple<T> r{T(0), T(0), T(0)};
     if (fi >= 0 && fi < F.ni && fj < F.nz)
       r = linres_val<T>(F, fi, fj, F.du[NE], F.du[NP], F.du[NV], F.f[NE], F.f[NP], F.f[NV]);
-    sr[0][t] = r.e; sr[1][t] = r.p; sr[2][t] = r.V;
+    sr[t] = r.e; sr[FH * FW + t] = r.p; sr[2 * FH * FW + t] = r.V;
   }
   __syncthreads();
-  for (int t = tid; t < CX * CY; t += blockDim.x) {
+  for (int t = tid; t < CX * CY; t += nthr) {
     const int I = I0 + t % CX, J = J0 + t / CX;
     if (I >= C.ni || J >= C.nz) continue;
-    const size_t kc = (size_t)J * C.P + I;
     T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
     for (int dj = -1; dj <= 1; ++dj) {
@@ -1377,13 +1385,22 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) 
         if (i < 0 || i >= F.ni) continue;
         const T w = wz * (di == 0 ? T(1) : T(0.5));
         const int ls = (j - (2 * J0 - 1)) * FW + (i - (2 * I0 - 1));
-        s0 += w * sr[0][ls]; s1 += w * sr[1][ls]; s2 += w * sr[2][ls];
+        s0 += w * sr[ls]; s1 += w * sr[FH * FW + ls]; s2 += w * sr[2 * FH * FW + ls];
       }
     }
     const size_t kcf = cidx(C.P, I, J);
     C.f[NE][kcf] = s0; C.f[NP][kcf] = s1; C.f[NV][kcf] = s2;
     C.du[NE][kcf] = T(0); C.du[NP][kcf] = T(0); C.du[NV][kcf] = T(0);
   }
+}
+
+template <typename T, int CX, int CY>
+__global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32) k_linres_restrict(LevelT<T> F,
+                                                                                                 LevelT<T> C) {
+  __shared__ T sr[3 * (2 * CX + 1) * (2 * CY + 1)];
+  pdl_launch_dependents();
+  pdl_wait();
+  linres_restrict_tile<T, CX, CY>(F, C, blockIdx.x * CX, 1 + blockIdx.y * CY, threadIdx.x, blockDim.x, sr);
 }
 
 template <typename T>
@@ -1566,14 +1583,14 @@ __device__ void assemble_coarse(const Level &L, double dt_inv, double *A, int ld
 // warp finds the pivot, swaps and scales the pivot row, then four threads per row eliminate
 // the remaining columns; entries left of the pivot column are never read again and are not
 // updated, so the multiplier A[r][col] stays intact during its step (two barriers per column).
-__global__ void __launch_bounds__(CT) k_coarse_factor_smem(Level L, double dt_inv, double *Minv, double *rs,
-                                                           double *cs, int *flag) {
+// The body, run by CT threads of one CTA (tid = threadIdx.x < CT; others must not call it) on
+// shared arrays sAB (kSmemGJ x 2 kSmemGJ doubles), srs, scs (kSmemGJ each) and *sp_.
+__device__ void coarse_factor_smem_body(const Level &L, double dt_inv, double *Minv, double *rs, double *cs,
+                                        int *flag, double *sAB, double *srs, double *scs, int *sp_) {
   const int n = 3 * L.ni * (L.nz - 1);
   const int W = 2 * n;
   const int tid = threadIdx.x, lane = tid & 31;
-  __shared__ double sAB[kSmemGJ * 2 * kSmemGJ];
-  __shared__ double srs[kSmemGJ], scs[kSmemGJ];
-  __shared__ int sp;
+  int &sp = *sp_;
   for (int e = tid; e < n * W; e += CT) sAB[e] = 0.0;
   __syncthreads();
   assemble_coarse(L, dt_inv, sAB, W, tid, CT);
@@ -1643,6 +1660,14 @@ __global__ void __launch_bounds__(CT) k_coarse_factor_smem(Level L, double dt_in
     Minv[e] = sAB[r * W + n + c];
   }
   if (tid == 0) *flag = 0;
+}
+
+__global__ void __launch_bounds__(CT) k_coarse_factor_smem(Level L, double dt_inv, double *Minv, double *rs,
+                                                           double *cs, int *flag) {
+  __shared__ double sAB[kSmemGJ * 2 * kSmemGJ];
+  __shared__ double srs[kSmemGJ], scs[kSmemGJ];
+  __shared__ int sp;
+  coarse_factor_smem_body(L, dt_inv, Minv, rs, cs, flag, sAB, srs, scs, &sp);
 }
 
 // Larger coarsest levels: the same steps in global memory (M is n x n scratch).
@@ -1775,21 +1800,11 @@ __global__ void __launch_bounds__(CT) k_coarse_solve(LevelT<T> L, const double *
 // nodes strided across all threads of the cluster, separated by cluster-wide barriers.  It
 // calls the same per-node functions in the same order as the per-level kernels, so the result
 // is identical to launching them one by one.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__restrict__ sp) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const CoarseSet<T> &S = *sp;
-  const int nth = (int)(cl.num_blocks() * blockDim.x);
-  const int tid = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
-  // barrier.cluster.arrive / wait default to release / acquire at cluster scope, which orders
-  // the global-memory writes of one phase before the reads of the next for every CTA of the
-  // cluster; a single-CTA set uses the block barrier
-  const bool one = cl.num_blocks() == 1;
-  auto bar = [&]() {
-    if (one) __syncthreads();
-    else cl.sync();
-  };
+// The phases of K8 over threads tid of nth (a cluster's or one CTA's), `bar` separating them;
+// the coarsest solve runs on the first CTA (rank0) with its cta_threads threads.
+template <typename T, typename Bar>
+__device__ __forceinline__ void coarse_cycle_body(const CoarseSet<T> &S, int tid, int nth, bool rank0, int cta_threads,
+                                                  Bar bar) {
   auto sweeps = [&](const LevelT<T> &L, int nu) {
     const int slots = colour_slots(L.ni, L.nz);
     for (int it = 0; it < nu; ++it)
@@ -1815,7 +1830,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
     for (int t = tid; t < (C.nz - 1) * Wc; t += nth) restrict_node<T>(L, C, t % Wc, t / Wc + 1);
     bar();
   }
-  if (cl.block_rank() == 0) coarse_solve_block<T>(S.lv[S.n - 1], S.Minv, S.rs, S.cs, S.nscale, blockDim.x);
+  if (rank0) coarse_solve_block<T>(S.lv[S.n - 1], S.Minv, S.rs, S.cs, S.nscale, cta_threads);
   bar();
   for (int q = S.n - 2; q >= 0; --q) {
     const LevelT<T> &F = S.lv[q];
@@ -1824,6 +1839,23 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__res
     bar();
     sweeps(F, S.nu2[q]);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(const CoarseSet<T> *__restrict__ sp) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const CoarseSet<T> &S = *sp;
+  const int nth = (int)(cl.num_blocks() * blockDim.x);
+  const int tid = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
+  // barrier.cluster.arrive / wait default to release / acquire at cluster scope, which orders
+  // the global-memory writes of one phase before the reads of the next for every CTA of the
+  // cluster; a single-CTA set uses the block barrier
+  const bool one = cl.num_blocks() == 1;
+  coarse_cycle_body<T>(S, tid, nth, cl.block_rank() == 0, (int)blockDim.x, [&]() {
+    if (one) __syncthreads();
+    else cl.sync();
+  });
 }
 
 // Single-CTA form of K8 with every array of the coarse levels in shared memory: the
@@ -2037,10 +2069,8 @@ template cudaError_t launch_coarse_solve<float>(const LevelT<float> &, const dou
                                                 const double *, double, cudaStream_t);
 
 // Newton update u += du on unknown rows; reduces max |dV| and a non-finite indicator.
-__global__ void k_update(Level L, StateView sv, double *partials, unsigned *counter, double *out2) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y + 1;
-  double acc[2] = {0.0, 0.0};
+__device__ __forceinline__ void update_row(const Level &L, const StateView &sv, int i, int j, double (&acc)[2]) {
+  acc[0] = 0.0; acc[1] = 0.0;
   if (i < L.ni && j < L.nz) {
     const size_t k = (size_t)j * L.P + i, kd = cidx(L.P, i, j);
     const double a = L.du[NE][kd], b = L.du[NP][kd], c = L.du[NV][kd];
@@ -2048,6 +2078,13 @@ __global__ void k_update(Level L, StateView sv, double *partials, unsigned *coun
     acc[0] = fabs(c);
     acc[1] = (isfinite(a) && isfinite(b) && isfinite(c)) ? 0.0 : 1.0;
   }
+}
+
+__global__ void k_update(Level L, StateView sv, double *partials, unsigned *counter, double *out2) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  double acc[2];
+  update_row(L, sv, i, j, acc);
   reduce_finish<2>(acc, partials, counter, out2, 1);
 }
 
@@ -2335,13 +2372,9 @@ cudaError_t launch_join_rows(const Level &L, double *const in[3], double *const 
   return cudaGetLastError();
 }
 
-__global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double *partials, unsigned *counter,
-                                 double *out3) {
-  pdl_launch_dependents();
-  pdl_wait();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  double acc[3] = {0, 0, 0};
+__device__ __forceinline__ void outer_row(const Level &L, const LevelT<float> &M, double inv_n0, int i, int j,
+                                          double (&acc)[3]) {
+  acc[0] = 0.0; acc[1] = 0.0; acc[2] = 0.0;
   if (i < L.ni && j < L.nz) {
     const Triple<double> r = linres_val<double>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP], L.f[NV]);
     const double re = r.e, rp = r.p, rV = r.V;
@@ -2351,6 +2384,16 @@ __global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double
     M.f[NV][kf] = (float)rV;
     acc[0] = re * re; acc[1] = rp * rp; acc[2] = rV * rV;
   }
+}
+
+__global__ void k_outer_residual(Level L, LevelT<float> M, double inv_n0, double *partials, unsigned *counter,
+                                 double *out3) {
+  pdl_launch_dependents();
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  double acc[3];
+  outer_row(L, M, inv_n0, i, j, acc);
   reduce_finish<3>(acc, partials, counter, out3, 0);
 }
 
@@ -2449,6 +2492,478 @@ double probe_fp64_gflops(cudaStream_t st) {
   if (err != cudaSuccess || ms <= 0.f) return -1.0;
   const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
   return flops / (ms * 1e-3) / 1e9;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched form (row a11): one persistent launch runs one Newton iteration of every
+// participating discharge.  The CTAs claim work items (tiles) of any discharge's current
+// phase; a discharge's phases follow its program (mg_api.cu builds it from the launches of the
+// single-discharge Newton iteration), and the CTA that finishes a phase's last tile folds the
+// phase's reductions and publishes the next phase.  No CTA ever waits for another: a CTA
+// without work looks again (with a growing pause), so progress needs no co-residency, and a
+// CTA that finds no work for kBatchIdleNs marks the launch as failed and leaves.
+//
+// Every tile runs the per-node functions of the corresponding single-discharge kernel over
+// the same nodes; reductions replicate reduce_finish's per-block partials (virtual blocks of the
+// original block shape) and its fold, so the sums equal the single-discharge ones bit for bit.
+//
+// Claims: claim = (sequence << 32) | count.  A claimer adds 1; the value returned names the
+// phase (ring[sequence & 3] must carry the same sequence) and the tile (count < ntiles).  The
+// finisher writes ring[(sequence + 1) & 3], resets done, fences, then swaps in the next
+// sequence with count 0; a claim that lands after the swap is a valid claim of the new phase.
+// Visibility: tile writes -> barrier -> fence -> atomic on `done`; the finisher fences after its
+// atomic, and the claimer fences after its claim, before reading data of earlier phases.
+constexpr unsigned long long kBatchIdleNs = 5000000000ull;
+constexpr int kBW = kBatchThreads / 32;   // warps per CTA
+
+__device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long *p) {
+  return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// reduce_finish's block partial for a virtual block of nv threads (nv / 32 consecutive warps of
+// the CTA starting at a multiple of nv): warp sums (or maxima), then the block's thread 0 adds
+// its warps in order and writes dst[0..K) when `valid`.  Every thread of the CTA calls it.
+template <int K>
+__device__ __forceinline__ void vblock_partial(const double (&v)[K], int nv, bool valid, double *dst, double *sh,
+                                               int op) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double x = v[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = op ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) sh[q * kBW + wid] = x;
+  }
+  __syncthreads();
+  if ((tid % nv) == 0 && valid) {
+    const int nw = nv >> 5;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double x = sh[q * kBW + wid];
+      for (int w = 1; w < nw; ++w) x = op ? fmax(x, sh[q * kBW + wid + w]) : x + sh[q * kBW + wid + w];
+      dst[q] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// reduce_finish's last-block fold of nblocks partials by nthr threads (the original block size;
+// threads tid >= nthr only pass the barriers), result in out[0..K).
+template <int K>
+__device__ __forceinline__ void fold_partials(const double *partials, int nblocks, int nthr, double *out,
+                                              double *sh, int op) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool act = tid < nthr;
+  double xs[K];
+  bool first = true;
+#pragma unroll
+  for (int q = 0; q < K; ++q) xs[q] = 0.0;
+  if (act) {
+    int b = tid;
+    for (; b + 3 * nthr < nblocks; b += 4 * nthr) {
+      double y[4][K];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q) y[u][q] = __ldcg(partials + (size_t)(b + u * nthr) * K + q);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+          xs[q] = (first && u == 0) ? y[u][q] : (op ? fmax(xs[q], y[u][q]) : xs[q] + y[u][q]);
+      first = false;
+    }
+    for (; b < nblocks; b += nthr) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const double y = __ldcg(partials + (size_t)b * K + q);
+        xs[q] = first ? y : (op ? fmax(xs[q], y) : xs[q] + y);
+      }
+      first = false;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double x = first ? (op ? -1.0 : 0.0) : xs[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = op ? fmax(x, y) : x + y;
+    }
+    if (lane == 0 && act) sh[q * kBW + wid] = x;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int nw = nthr >> 5;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double x = sh[q * kBW];
+      for (int w = 1; w < nw; ++w) x = op ? fmax(x, sh[q * kBW + w]) : x + sh[q * kBW + w];
+      out[q] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Shared memory of the persistent launch: reduction scratch, then the largest phase buffer (the
+// coarsest level's augmented matrix; the restriction tile fits in it too).
+constexpr int kBatchRestrCX = 16, kBatchRestrCY = 3;  // 33 x 7 fine nodes per coarse tile: <= 256 threads
+constexpr size_t kBatchShRed = 16 * kBW * sizeof(double);
+constexpr size_t kBatchShGJ = (size_t)kSmemGJ * 2 * kSmemGJ * sizeof(double) + 2 * kSmemGJ * sizeof(double) + 16;
+constexpr size_t kBatchShRestr = 3 * (2 * kBatchRestrCX + 1) * (2 * kBatchRestrCY + 1) * sizeof(double);
+constexpr size_t kBatchSmem = kBatchShRed + (kBatchShGJ > kBatchShRestr ? kBatchShGJ : kBatchShRestr);
+size_t batch_smem_bytes() { return kBatchSmem; }
+
+// 32 x 8 thread block b of a (gx, gy, levels) grid: level offset, node (i, j) of this thread
+__device__ __forceinline__ void vb328(int b, int gx, int gy, int &lz, int &i, int &j) {
+  const int per = gx * gy;
+  lz = b / per;
+  const int r = b - lz * per;
+  i = (r % gx) * 32 + (threadIdx.x & 31);
+  j = (r / gx) * 8 + (threadIdx.x >> 5);
+}
+
+template <typename T>
+__device__ __forceinline__ const LevelT<T> &lview(const LevelSet *S, int l);
+template <>
+__device__ __forceinline__ const LevelT<double> &lview<double>(const LevelSet *S, int l) { return S->L[l]; }
+template <>
+__device__ __forceinline__ const LevelT<float> &lview<float>(const LevelSet *S, int l) { return S->M[l]; }
+
+template <typename T>
+__device__ __forceinline__ void batch_half(const BatchInst &I, const BPhase &ph, int tile) {
+  const LevelT<T> &L = lview<T>(I.S, ph.level);
+  const int slots = colour_slots(L.ni, L.nz);
+  for (int r = 0; r < ph.grain; ++r) {
+    const int t = (tile * ph.grain + r) * kBatchThreads + threadIdx.x;
+    int i, j;
+    if (t < slots && colour_node(t, L.ni, L.nz, ph.arg, i, j)) smooth_node<T>(L, i, j);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_restrict(const BatchInst &I, const BPhase &ph, int tile, unsigned char *buf) {
+  const LevelT<T> &F = lview<T>(I.S, ph.level);
+  const LevelT<T> &C = lview<T>(I.S, ph.level + 1);
+  const int gx = (C.nr + 1 + kBatchRestrCX - 1) / kBatchRestrCX;
+  for (int r = 0; r < ph.grain; ++r) {
+    const int b = tile * ph.grain + r;
+    // blocks past the grid find every node out of range and only pass the barrier
+    linres_restrict_tile<T, kBatchRestrCX, kBatchRestrCY>(F, C, (b % gx) * kBatchRestrCX, 1 + (b / gx) * kBatchRestrCY,
+                                                          threadIdx.x, kBatchThreads, reinterpret_cast<T *>(buf));
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_prolong(const BatchInst &I, const BPhase &ph, int tile) {
+  const LevelT<T> &F = lview<T>(I.S, ph.level);
+  const LevelT<T> &C = lview<T>(I.S, ph.level + 1);
+  const int n = F.ni * (F.nz - 1);
+  for (int r = 0; r < ph.grain; ++r) {
+    const int t = (tile * ph.grain + r) * kBatchThreads + threadIdx.x;
+    if (t < n) prolong_node<T>(C, F, t % F.ni, t / F.ni + 1);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_zero(const LevelT<T> &L, const BPhase &ph, int tile) {
+  const size_t n = (size_t)(L.nz + 1) * L.P;
+  for (int r = 0; r < ph.grain; ++r) {
+    const size_t t = (size_t)(tile * ph.grain + r) * kBatchThreads + threadIdx.x;
+    if (t < n) { L.du[NE][t] = T(0); L.du[NP][t] = T(0); L.du[NV][t] = T(0); }
+  }
+}
+
+__device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, double *red, unsigned char *buf) {
+  const LevelSet *S = I.S;
+  const int tid = threadIdx.x;
+  switch (ph.kind) {
+    case BK_INJECT: {  // k_inject_levels: levels l0 + 1 .. last from level l0
+      const Level &C1 = S->L[ph.level];
+      const int gx = (C1.nr + 1 + 31) / 32, gy = (C1.nz + 1 + 7) / 8;
+      for (int r = 0; r < ph.grain; ++r) {
+        const int b = tile * ph.grain + r;
+        if (b >= ph.nblocks) break;
+        int lz, I_, J_;
+        vb328(b, gx, gy, lz, I_, J_);
+        const int l = ph.level + lz;
+        const Level &C = S->L[l];
+        if (I_ > C.nr || J_ > C.nz) continue;
+        const int sh = l - I.l0;
+        const size_t kc = (size_t)J_ * C.P + I_, kf = ((size_t)J_ << sh) * S->L[I.l0].P + ((size_t)I_ << sh);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) S->sv[l].u[q][kc] = S->sv[I.l0].u[q][kf];
+      }
+      break;
+    }
+    case BK_COEFL:
+    case BK_COEF0: {  // k_coef_levels / k_coef: face coefficients of levels level .. arg
+      const Level &La = S->L[ph.level];
+      const int gx = (La.nr + 1 + 31) / 32, gy = (La.nz + 1 + 7) / 8;
+      for (int r = 0; r < ph.grain; ++r) {
+        const int b = tile * ph.grain + r;
+        if (b >= ph.nblocks) break;
+        int lz, i, j;
+        vb328(b, gx, gy, lz, i, j);
+        const int l = ph.level + lz;
+        const Level &L = S->L[l];
+        if (i > L.nr || j > L.nz) continue;
+        coef_node(L, S->sv[l], I.tr, i, j);
+      }
+      break;
+    }
+    case BK_FACTORL: {  // k_factor_levels: levels level .. arg
+      const Level &La = S->L[ph.level];
+      const int gx = (La.nr + 1 + 31) / 32, gy = (La.nz + 1 + 7) / 8;
+      for (int r = 0; r < ph.grain; ++r) {
+        const int b = tile * ph.grain + r;
+        if (b >= ph.nblocks) break;
+        int lz, i, j;
+        vb328(b, gx, gy, lz, i, j);
+        const int l = ph.level + lz;
+        const Level &L = S->L[l];
+        if (i > L.nr || j > L.nz) continue;
+        if (I.mixed) coef_to32_node(L, S->M[l], 1.0 / I.n0, (size_t)j * L.P + i);
+        if (j >= 1 && j < L.nz && i < L.ni) factor_node(L, S->M[l], I.mixed, I.dt_inv, I.n0, i, j);
+      }
+      break;
+    }
+    case BK_CFACT: {  // k_coarse_factor_smem on the coarsest level
+      double *sAB = reinterpret_cast<double *>(buf);
+      double *srs = sAB + kSmemGJ * 2 * kSmemGJ, *scs = srs + kSmemGJ;
+      int *sp = reinterpret_cast<int *>(scs + kSmemGJ);
+      coarse_factor_smem_body(S->L[I.last], I.dt_inv, I.Minv, I.rs, I.cs, I.flag, sAB, srs, scs, sp);
+      break;
+    }
+    case BK_ZERO64: batch_zero<double>(S->L[I.l0], ph, tile); break;
+    case BK_ZERO32: batch_zero<float>(S->M[I.l0], ph, tile); break;
+    case BK_NORM0:
+    case BK_NORMC: {
+      const Level &L = S->L[I.l0];
+      if (I.mixed) {  // k_outer_residual: 32 x 8 blocks
+        const int gx = (L.nr + 1 + 31) / 32, gy = (L.nz - 1 + 7) / 8;
+        for (int r = 0; r < ph.grain; ++r) {
+          const int b = tile * ph.grain + r;
+          int lz, i, j;
+          vb328(b, gx, gy, lz, i, j);
+          double acc[3] = {0.0, 0.0, 0.0};
+          if (b < ph.nblocks) outer_row(L, S->M[I.l0], 1.0 / I.n0, i, j + 1, acc);
+          vblock_partial<3>(acc, 256, b < ph.nblocks, I.partials + (size_t)b * 3, red, 0);
+        }
+      } else {  // k_linres (f - J du into r): 32 x 2 blocks, four per round
+        const int gx = (L.nr + 1 + 31) / 32;
+        for (int r = 0; r < ph.grain; ++r) {
+          const int b = (tile * ph.grain + r) * 4 + (tid >> 6);
+          const int i = (b % gx) * 32 + (tid & 31), j = (b / gx) * 2 + ((tid >> 5) & 1) + 1;
+          double acc[3] = {0, 0, 0};
+          if (b < ph.nblocks && i < L.ni && j < L.nz) {
+            const Triple<double> rr = linres_node<double>(L, i, j, L.du[NE], L.du[NP], L.du[NV], L.f[NE], L.f[NP],
+                                                          L.f[NV], L.r[NE], L.r[NP], L.r[NV]);
+            acc[0] = rr.e * rr.e; acc[1] = rr.p * rr.p; acc[2] = rr.V * rr.V;
+          }
+          vblock_partial<3>(acc, 64, b < ph.nblocks, I.partials + (size_t)b * 3, red, 0);
+        }
+      }
+      break;
+    }
+    case BK_HALF64: batch_half<double>(I, ph, tile); break;
+    case BK_HALF32: batch_half<float>(I, ph, tile); break;
+    case BK_RESTR64: batch_restrict<double>(I, ph, tile, buf); break;
+    case BK_RESTR32: batch_restrict<float>(I, ph, tile, buf); break;
+    case BK_COARSE64:
+      coarse_cycle_body<double>(*I.cs64, tid, kBatchThreads, true, kBatchThreads, []() { __syncthreads(); });
+      break;
+    case BK_COARSE32:
+      coarse_cycle_body<float>(*I.cs32, tid, kBatchThreads, true, kBatchThreads, []() { __syncthreads(); });
+      break;
+    case BK_PROL64: batch_prolong<double>(I, ph, tile); break;
+    case BK_PROL32: batch_prolong<float>(I, ph, tile); break;
+    case BK_MIXUPD: {  // k_mixed_update
+      const Level &L = S->L[I.l0];
+      const LevelT<float> &M = S->M[I.l0];
+      const int n = L.ni * (L.nz - 1);
+      for (int r = 0; r < ph.grain; ++r) {
+        const int t = (tile * ph.grain + r) * kBatchThreads + tid;
+        if (t >= n) break;
+        const size_t k = cidx(L.P, t % L.ni, t / L.ni + 1);
+        L.du[NE][k] += I.n0 * (double)M.du[NE][k];
+        L.du[NP][k] += I.n0 * (double)M.du[NP][k];
+        L.du[NV][k] += (double)M.du[NV][k];
+      }
+      break;
+    }
+    case BK_UPDATE: {  // k_update: 32 x 8 blocks, maxima
+      const Level &L = S->L[I.l0];
+      const int gx = (L.nr + 1 + 31) / 32, gy = (L.nz - 1 + 7) / 8;
+      for (int r = 0; r < ph.grain; ++r) {
+        const int b = tile * ph.grain + r;
+        int lz, i, j;
+        vb328(b, gx, gy, lz, i, j);
+        double acc[2] = {0.0, 0.0};
+        if (b < ph.nblocks) update_row(L, S->sv[I.l0], i, j + 1, acc);
+        vblock_partial<2>(acc, 256, b < ph.nblocks, I.partials + (size_t)b * 2, red, 1);
+      }
+      break;
+    }
+    case BK_RESID: {  // k_resid_coef with the steady sums, f and the steady -F: 32 x 2 blocks, four per round
+      const Level &L = S->L[I.l0];
+      const int gx = (L.nr + 1 + 31) / 32;
+      for (int r = 0; r < ph.grain; ++r) {
+        const int b = (tile * ph.grain + r) * 4 + (tid >> 6);
+        const int i = (b % gx) * 32 + (tid & 31), j = (b / gx) * 2 + ((tid >> 5) & 1) + 1;
+        double acc[16];
+        resid_row(L, S->sv[I.l0], I.dt_inv, 1, 1, nullptr, nullptr, nullptr, I.fss[0], I.fss[1], I.fss[2],
+                  b < ph.nblocks ? i : L.ni, j, acc);
+        vblock_partial<16>(acc, 64, b < ph.nblocks, I.partials + (size_t)b * 16, red, 0);
+      }
+      break;
+    }
+    default: break;
+  }
+}
+
+// The finisher of a phase (every thread of its CTA): fold the phase's reduction, then thread 0
+// evaluates the discharge's control (the stopping test of the V-cycle loop, the end of the
+// program) and publishes the next phase.
+__device__ void batch_finish(BatchInst &I, const BPhase &ph, int pc, unsigned seq, BatchRes *res, BatchHead *head,
+                             double *red) {
+  switch (ph.kind) {
+    case BK_NORM0:
+    case BK_NORMC: fold_partials<3>(I.partials, ph.nblocks, I.mixed ? 256 : 64, I.dout, red, 0); break;
+    case BK_UPDATE: fold_partials<2>(I.partials, ph.nblocks, 256, I.dout + 16, red, 1); break;
+    case BK_RESID: fold_partials<16>(I.partials, ph.nblocks, 64, I.dout, red, 0); break;
+    default: break;
+  }
+  if (threadIdx.x != 0) return;
+  int next = pc + 1;
+  SolveCtl *c = I.ctl;
+  if (ph.kind == BK_NORM0) {  // k_solve_init
+    for (int q = 0; q < 3; ++q) c->w[q] = I.w[q];
+    c->eta = I.eta;
+    c->max_cycles = I.max_cycles;
+    const double r0 = weighted_norm(c, I.dout);
+    c->r0 = r0;
+    c->ncyc = 0;
+    c->rel = r0 > 0.0 ? 1.0 : 0.0;
+    c->hist[0] = c->rel;
+    const bool go = r0 > 0.0 && isfinite(r0) && c->rel > c->eta && c->max_cycles > 0;
+    next = go ? I.loop_pc : I.update_pc;
+  } else if (ph.kind == BK_NORMC) {  // k_solve_check
+    const double rel = weighted_norm(c, I.dout) / c->r0;
+    const int n = c->ncyc + 1;
+    c->ncyc = n;
+    c->rel = rel;
+    if (n < kMaxHist) c->hist[n] = rel;
+    const bool go = isfinite(rel) && rel > c->eta && n < c->max_cycles;
+    next = go ? I.loop_pc : I.update_pc;
+  } else if (ph.kind == BK_RESID) {
+    for (int q = 0; q < 18; ++q) res->out[q] = I.dout[q];
+    res->r0 = c->r0;
+    res->rel = c->rel;
+    res->ncyc = c->ncyc;
+    res->pad = 0;
+  }
+  const unsigned ns = seq + 1;
+  I.ring[ns & 3] = ((unsigned long long)ns << 32) | (unsigned)next;
+  I.done = 0u;
+  __threadfence();
+  atomicExch(&I.claim, (unsigned long long)ns << 32);
+  if (I.prog[next].ntiles == 0) atomicAdd(&head->ndone, 1);
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BatchHead *head, BatchInst *inst, BatchRes *res) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  double *red = reinterpret_cast<double *>(bsm);
+  unsigned char *buf = bsm + kBatchShRed;
+  __shared__ int s_k, s_pc, s_tile, s_last, s_exit;
+  __shared__ unsigned s_seq;
+  const int n = head->n;
+  int pref = blockIdx.x % (n > 0 ? n : 1);   // the discharge this CTA looks at first
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_exit = 0;
+      unsigned pause = 32;
+      unsigned long long idle0 = global_ns();
+      for (unsigned spin = 0;; ++spin) {
+        if (*reinterpret_cast<volatile unsigned *>(&head->err) != 0 ||
+            *reinterpret_cast<volatile int *>(&head->ndone) >= n) {
+          s_exit = 1;
+          break;
+        }
+        bool got = false;
+        for (int c = 0; c < n && !got; ++c) {
+          const int k = (pref + c) % n;
+          BatchInst &I = inst[k];
+          const unsigned long long w = ld_vol64(&I.claim);
+          const unsigned seq = (unsigned)(w >> 32), cnt = (unsigned)w;
+          const unsigned long long e = ld_vol64(&I.ring[seq & 3]);
+          if ((unsigned)(e >> 32) != seq || cnt >= (unsigned)I.prog[(unsigned)e].ntiles) continue;
+          const unsigned long long o = atomicAdd(&I.claim, 1ull);
+          __threadfence();
+          const unsigned s2 = (unsigned)(o >> 32), c2 = (unsigned)o;
+          const unsigned long long e2 = ld_vol64(&I.ring[s2 & 3]);
+          if ((unsigned)(e2 >> 32) != s2 || c2 >= (unsigned)I.prog[(unsigned)e2].ntiles) continue;
+          s_k = k; s_pc = (int)(unsigned)e2; s_tile = (int)c2; s_seq = s2;
+          pref = k;
+          got = true;
+        }
+        if (got) break;
+        if ((spin & 15) == 15 && global_ns() - idle0 > kBatchIdleNs) {
+          atomicExch(&head->err, 1u);
+          s_exit = 1;
+          break;
+        }
+        __nanosleep(pause);
+        if (pause < 2048) pause <<= 1;
+      }
+    }
+    __syncthreads();
+    if (s_exit) return;
+    const int k = s_k, pc = s_pc, tile = s_tile;
+    const unsigned seq = s_seq;
+    BatchInst &I = inst[k];
+    const BPhase ph = I.prog[pc];
+    batch_tile(I, ph, tile, red, buf);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned d = atomicAdd(&I.done, 1u);
+      s_last = (d + 1 == (unsigned)ph.ntiles);
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) batch_finish(I, ph, pc, seq, res + k, head, red);
+    __syncthreads();
+  }
+}
+
+int batch_grid() {
+  static int cached = -1;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cached >= 0) return cached;
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, kBatchSmem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cached = sms * occ;
+  return cached;
+}
+
+cudaError_t launch_batch(BatchHead *head, BatchInst *inst, BatchRes *res, int grid, cudaStream_t st) {
+  k_batch<<<grid, kBatchThreads, kBatchSmem, st>>>(head, inst, res);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace mgk

@@ -338,8 +338,12 @@ class Solver:
         return int(n.value), float(ms.value)
 
 
-def solve_steady_batch(solvers, tol: float, workers: int = 8):
-    """Steady solves of independent Solver objects concurrently; returns (rc, ms[n], rc[n])."""
+def solve_steady_batch(solvers, tol: float, workers: int = 0):
+    """Steady solves of independent Solver objects; returns (rc, ms[n], rc[n]).
+
+    workers = 0: the batched persistent launch (every Newton iteration of all discharges in one
+    launch per round); workers > 0: that many host threads solving the discharges one by one
+    (the comparison form).  See mg_solve_steady_batch in include/mg.h."""
     lib = load()
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s.h for s in solvers])

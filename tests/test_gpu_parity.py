@@ -359,31 +359,78 @@ def test_steady_257_headline_parity(mg, oracle_steady_257):
 
 def test_transient_1025_full_size(mg):
     """1025 x 1025 (the mixed-precision workload at full size), autotuned as the benchmark runs
-    it: one backward-Euler step of 1 ns in FP64 and in the mixed form.  The oracle's residual of
-    each result meets the step tolerance, and the two results agree to 1e-8 relative per field."""
+    it: ten backward-Euler steps of 1 ns, each to rho <= 1e-10, in FP64 and in the mixed form,
+    against the oracle's ten steps (tests/golden/oracle_transient_1025.npz, written by
+    tests/golden/make_oracle_1025.py from the oracle alone: every 8th node of each field after
+    every step, and each field's max-norm).  FP64: the oracle's Newton iterations per step and
+    its state to 1e-10 relative per field at every sampled node; mixed: its state to 1e-8.  The
+    oracle's residual of each form's first step meets the step tolerance."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_transient_1025.npz")
+    with np.load(path) as z:
+        gold = {k: z[k] for k in z.files}
+    stride = int(gold["stride"])
     d = W.transient_1025()
     g, phys = _oracle(d)
     u0 = np.stack([d.ne0, d.np0, d.V0])
-    out = []
-    for prec in (mg.MG_FP64, mg.MG_MIXED):
+    for prec, tol in ((mg.MG_FP64, FP64_TOL), (mg.MG_MIXED, MIXED_TOL)):
         s = mg.from_discharge(d, precision=prec)
         s.autotune()
-        rc, st = s.step(1e-9, 1e-10)
-        assert rc == mg.MG_OK, st
-        ug = np.stack(s.get_state())
-        assert np.all(np.isfinite(ug))
-        F, T = disc.residual(g, ug, u0, d.S_e, d.S_p, 1e-9, phys, with_terms=True)
-        assert disc.rho(F, T).max() <= 1e-10 * (1 + RHO_AGREE), (prec, disc.rho(F, T))
-        out.append(ug)
+        for k in range(10):
+            rc, st = s.step(1e-9, 1e-10)
+            assert rc == mg.MG_OK, (prec, k, st)
+            ug = np.stack(s.get_state())
+            assert np.all(np.isfinite(ug))
+            if k == 0:
+                F, T = disc.residual(g, ug, u0, d.S_e, d.S_p, 1e-9, phys, with_terms=True)
+                assert disc.rho(F, T).max() <= 1e-10 * (1 + RHO_AGREE), (prec, disc.rho(F, T))
+            if prec == mg.MG_FP64:
+                assert st["last_newton"] == gold["newton"][k], (k, st["last_newton"], gold["newton"][k])
+            smp = ug[:, ::stride, ::stride]
+            for q in range(3):
+                err = np.abs(smp[q] - gold["samples"][k][q]).max() / gold["norms"][k][q]
+                assert err <= tol, (prec, k, q, err)
         s.close()
-    for q in range(3):
-        assert np.abs(out[0][q] - out[1][q]).max() <= 1e-8 * np.abs(out[0][q]).max(), q
 
 
-def test_batched_full_sizes_residual_property(mg):
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_persistent_batch_equals_individual_solves(mg, precision):
+    """The batched form as one persistent launch per round of Newton iterations (workers = 0):
+    discharges of 33^2 to 129^2 reach their individual solves' steady states bit for bit with
+    the same steps, Newton iterations and V-cycles, with far fewer kernel launches, and the
+    oracle's steady residual of each result is <= 1e-8."""
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    ds = W.batch_64(seed=4, count=6, sizes=(16, 32, 64, 128))
+    solvers = [mg.from_discharge(d, precision=prec, stream=torch.cuda.Stream()) for d in ds]
+    n0 = mg.kernel_launches()
+    rc, ms, rcs = mg.solve_steady_batch(solvers, 1e-8, workers=0)
+    launches_batch = mg.kernel_launches() - n0
+    assert rc == mg.MG_OK, rcs
+    assert np.all(ms > 0)
+    launches_single = 0
+    for d, sb in zip(ds, solvers):
+        si = mg.from_discharge(d, precision=prec)
+        n1 = mg.kernel_launches()
+        rc_i, st_i = si.solve_steady(1e-8)
+        launches_single += mg.kernel_launches() - n1
+        assert rc_i == mg.MG_OK
+        a, b = sb.get_state(), si.get_state()
+        for q in range(3):
+            assert np.array_equal(a[q], b[q]), (d.nr, q)
+        st_b = sb.stats()
+        for key in ("steps_accepted", "steps_rejected", "newton_iterations", "vcycles", "coarse_steps"):
+            assert st_b[key] == st_i[key], (d.nr, key)
+        g, phys = _oracle(d)
+        F, T = disc.residual(g, np.stack(a), None, d.S_e, d.S_p, None, phys, with_terms=True)
+        assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE)
+    assert launches_batch * 10 < launches_single, (launches_batch, launches_single)
+
+
+@pytest.mark.parametrize("workers", [0, 4])
+def test_batched_full_sizes_residual_property(mg, workers):
     """The batched form at its full instance sizes (one instance of each of 65^2, 129^2, 257^2
-    and 513^2 from the 64-discharge workload), autotuned: the oracle's steady residual of every
-    result."""
+    and 513^2 from the 64-discharge workload), autotuned, as the persistent launch (workers = 0)
+    and as host threads (4): the oracle's steady residual of every result."""
     ds = W.batch_64()
     pick, seen = [], set()
     for d in ds:
@@ -394,7 +441,7 @@ def test_batched_full_sizes_residual_property(mg):
     solvers = [mg.from_discharge(d, precision=mg.MG_MIXED, stream=torch.cuda.Stream()) for d in pick]
     for sv in solvers:
         sv.autotune()
-    rc, ms, rcs = mg.solve_steady_batch(solvers, 1e-8, workers=4)
+    rc, ms, rcs = mg.solve_steady_batch(solvers, 1e-8, workers=workers)
     assert rc == mg.MG_OK, rcs
     for d, sv in zip(pick, solvers):
         g, phys = _oracle(d)
