@@ -282,6 +282,14 @@ int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const
  * current device and must not be used by other threads during the call. */
 int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, double *ms_out, int *rc_out);
 
+/* Autotuner of the batched form's work items (mg_solve_steady_batch with workers = 0): solves
+ * the n discharges to tol in one persistent launch once per candidate size of a work item (1,
+ * 2, 4 or 8 rounds of 256 nodes, or of the single-discharge kernel's thread blocks), keeps the
+ * fastest in every state and returns it in *grain_out (may be NULL).  The states' solutions,
+ * statistics and start data are restored afterwards.  MG_EINVAL when a state does not qualify
+ * for the persistent form (see mg_solve_steady_batch). */
+int mg_autotune_batch(mg_state **states, int n, double tol, int *grain_out);
+
 /* Autotuner of the smoother's launch shapes: times the red-black half sweep and the fused
  * sweep of every level (FP64 and, in the mixed form, FP32) over fixed sets of thread-block /
  * tile shapes and keeps the fastest per level.  Leaves the solution state untouched (only

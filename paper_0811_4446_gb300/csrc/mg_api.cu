@@ -2,6 +2,7 @@
 // V-cycle schedule, Newton-Raphson, the Delta-t ramp and the coarse-to-fine continuation
 // (Ristivojevic & Petrovic, arXiv:0811.4446, Sec. 2).  All arithmetic on the solution runs in
 // the kernels of mg_kernels.cu; the host only sequences launches and reads back norms.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdarg>
@@ -9,8 +10,6 @@
 #include <cstring>
 #include <atomic>
 #include <chrono>
-#include <condition_variable>
-#include <mutex>
 #include <new>
 #include <thread>
 #include <string>
@@ -48,8 +47,6 @@ struct LevelBuf {
 };
 
 }  // namespace
-
-struct BatchEngine;
 
 struct mg_state {
   mg_params prm;
@@ -95,14 +92,11 @@ struct mg_state {
   CoarseSet<float> *cset32 = nullptr;
   size_t cc_smem64 = 0, cc_smem32 = 0;  // shared memory of the single-CTA form (0: global-memory form)
   LevelSet *lset = nullptr;   // device copy of every level's views (multi-level set-up kernels)
-  // batched form: set while the state takes part in a persistent batched solve
-  BatchEngine *batch = nullptr;
-  int batch_rc = 0;
-  cudaEvent_t bev = nullptr;                 // recorded on the state's stream before each round
-  BPhase *bprog[kMaxLevels] = {};            // device programs of a Newton iteration per root level
-  int bloop[kMaxLevels] = {}, bupd[kMaxLevels] = {};
+  // batched form: the device program of the steady solve (built on first use)
+  BPhase *bprog = nullptr;
+  int bent[kMaxLevelSet][E_N] = {};          // its subprogram entries per level
   int bgrain = 4;                            // thread-block rounds per work item
-  BatchInst binst;                           // this Newton iteration's descriptor
+  int host_prog_ntiles0 = 0;                 // work items of the program's first phase
 };
 
 namespace {
@@ -710,163 +704,146 @@ BPhase batch_phase(int kind, int level, int arg, int nblocks, int per_round, int
   return p;
 }
 
-// Whether the state's Newton iterations can run in the batched launch: the point smoother, the
-// Picard Jacobian, the coarse-cycle kernel at or below every root level of the continuation, a
-// coarsest level of at most kSmemGJ unknowns (shared-memory inverse), no cooperative phases.
+// Whether a state's steady solve can run in the batched launch: the point smoother, the Picard
+// Jacobian, the coarse-cycle kernel at or below every root level of the continuation, a
+// coarsest level of at most 48 unknowns (shared-memory inverse), no cooperative phases, and a
+// continuation that mg_solve_steady accepts.
 bool batchable(const mg_state *s) {
   const LevelBuf &c = s->lv[s->nlev - 1];
-  return !s->prm.line_smoother && !s->prm.full_jacobian && s->prm.smooth_phase == 0 && s->cc_from > 0 &&
+  return s->nlev >= 2 && s->nlev <= kMaxLevelSet && s->prm.chain_from >= 1 && s->prm.chain_from < s->nlev &&
+         !s->prm.line_smoother && !s->prm.full_jacobian && s->prm.smooth_phase == 0 && s->cc_from > 0 &&
          s->cc_from < s->nlev - 1 && s->prm.chain_from <= s->cc_from && 3 * c.L.ni * (c.nz - 1) <= 48 &&
          s->prof_kernel == 0;
 }
 
-// The program of one Newton iteration on root level l0, in the order the single-discharge path
-// launches its kernels: injection and coefficients of the coarser levels, the factors of every
-// level, the coarsest inverse, du = 0 and the initial norm; the V-cycle loop (pre-smoothing half
-// sweeps and the residual-restriction per level down to the coarse-cycle kernel's first level,
-// the coarse cycle, prolongation and post-smoothing back up; in the mixed form the FP32 cycle
-// between zeroing its correction and the FP64 update), closed by the norm and its stopping test;
-// then the update, the coefficients and the residual of the new state.
-int build_batch_program(mg_state *s, int l0) {
-  if (s->bprog[l0]) return MG_OK;
-  const int last = s->nlev - 1, g = s->bgrain;
+// The program of a steady solve: program counter 0 ends the solve; then, for every level l the
+// continuation marches on (0 .. chain_from), subprograms that each end in BK_RET, in the order
+// of the host driver's launches:
+//   E_INJECT      state and sources injected from level l - 1 (l >= 1)
+//   E_START_COEF  coefficients and the steady residual sums of the current state (start data)
+//   E_START       the same without the coefficients
+//   E_BEGIN_USE   u -> u_old and the stored steady -F -> f (a step starting from start data)
+//   E_BEGIN_COEF  u -> u_old, coefficients and the step's residual (f and the sums)
+//   E_BEGIN       the same without the coefficients
+//   E_NEWTON      one Newton iteration: injection and coefficients of the coarser levels, the
+//                 factors of every level, the coarsest inverse, du = 0 and the initial norm;
+//                 the V-cycle loop from E_NLOOP (pre-smoothing half sweeps and the
+//                 residual-restriction per level down to the coarse-cycle kernel's first level,
+//                 the coarse cycle, prolongation and post-smoothing back up; in the mixed form
+//                 the FP32 cycle between zeroing its correction and the FP64 update), closed by
+//                 the norm and its stopping test; from E_NUPD the update, the coefficients and
+//                 the residual of the new state
+//   E_RESTORE     u_old -> u (a rejected step)
+//   E_PROLONG     the state prolonged from level l + 1 and the boundary values set (l < chain_from)
+int build_batch_program(mg_state *s) {
+  if (s->bprog) return MG_OK;
+  const int last = s->nlev - 1, g = s->bgrain, from = s->prm.chain_from;
   const bool m = mixed(s);
   auto cdiv = [](long a, long b) { return (int)((a + b - 1) / b); };
   auto grid328 = [&](const Level &L, int rows) { return cdiv(L.nr + 1, 32) * cdiv(rows, 8); };
-  const Level &L0 = s->lv[l0].L;
   std::vector<BPhase> p;
-  if (l0 < last) {
-    const Level &C1 = s->lv[l0 + 1].L;
-    p.push_back(batch_phase(BK_INJECT, l0 + 1, last, grid328(C1, C1.nz + 1) * (last - l0), 1, g));
-    p.push_back(batch_phase(BK_COEFL, l0 + 1, last, grid328(C1, C1.nz + 1) * (last - l0), 1, g));
-  }
-  p.push_back(batch_phase(BK_FACTORL, l0, last, grid328(L0, L0.nz + 1) * (last - l0 + 1), 1, g));
-  p.push_back(batch_phase(BK_CFACT, last, 0, 1, 1, 1));
-  const long slots0 = (long)(L0.nz + 1) * L0.P;
-  p.push_back(batch_phase(BK_ZERO64, l0, 0, cdiv(slots0, kBatchThreads), 1, g));
-  const int nb_norm = m ? grid328(L0, L0.nz - 1) : cdiv(L0.nr + 1, 32) * cdiv(L0.nz - 1, 2);
-  p.push_back(batch_phase(BK_NORM0, l0, 0, nb_norm, m ? 1 : 4, g));
-  const int loop_pc = (int)p.size();
-  if (m) p.push_back(batch_phase(BK_ZERO32, l0, 0, cdiv(slots0, kBatchThreads), 1, g));
-  auto halves = [&](int l, int nu) {
-    const Level &L = s->lv[l].L;
-    const int nb = cdiv((long)(L.nz / 2) * L.ni, kBatchThreads);
-    for (int k = 0; k < nu; ++k)
-      for (int col = 0; col < 2; ++col) p.push_back(batch_phase(m ? BK_HALF32 : BK_HALF64, l, col, nb, 1, g));
-  };
-  for (int l = l0; l < s->cc_from; ++l) {
-    halves(l, nu_of(s, l, 1));
-    const Level &C = s->lv[l + 1].L;
-    p.push_back(batch_phase(m ? BK_RESTR32 : BK_RESTR64, l, 0, cdiv(C.nr + 1, 16) * cdiv(C.nz - 1, 3), 1, g));
-  }
-  p.push_back(batch_phase(m ? BK_COARSE32 : BK_COARSE64, s->cc_from, 0, 1, 1, 1));
-  for (int l = s->cc_from - 1; l >= l0; --l) {
-    const Level &F = s->lv[l].L;
-    p.push_back(batch_phase(m ? BK_PROL32 : BK_PROL64, l, 0, cdiv((long)F.ni * (F.nz - 1), kBatchThreads), 1, g));
-    halves(l, nu_of(s, l, 2));
-  }
-  if (m) p.push_back(batch_phase(BK_MIXUPD, l0, 0, cdiv((long)L0.ni * (L0.nz - 1), kBatchThreads), 1, g));
-  p.push_back(batch_phase(BK_NORMC, l0, 0, nb_norm, m ? 1 : 4, g));
-  const int update_pc = (int)p.size();
-  p.push_back(batch_phase(BK_UPDATE, l0, 0, grid328(L0, L0.nz - 1), 1, g));
-  p.push_back(batch_phase(BK_COEF0, l0, l0, grid328(L0, L0.nz + 1), 1, g));
-  p.push_back(batch_phase(BK_RESID, l0, 0, cdiv(L0.nr + 1, 32) * cdiv(L0.nz - 1, 2), 4, g));
   BPhase end = {};
   end.kind = BK_DONE;
   p.push_back(end);
+  BPhase ret = {};
+  ret.kind = BK_RET;
+  std::memset(s->bent, 0, sizeof(s->bent));
+  for (int l0 = 0; l0 <= from; ++l0) {
+    const Level &L0 = s->lv[l0].L;
+    int *E = s->bent[l0];
+    const int nb_resid = cdiv(L0.nr + 1, 32) * cdiv(L0.nz - 1, 2);
+    const int nb_copy = cdiv((long)(L0.nz + 1) * L0.P, kBatchThreads);
+    if (l0 >= 1) {
+      E[E_INJECT] = (int)p.size();
+      p.push_back(batch_phase(BK_INJECT1, l0, 0, grid328(L0, L0.nz + 1), 1, g));
+      p.push_back(ret);
+    }
+    E[E_START_COEF] = (int)p.size();
+    p.push_back(batch_phase(BK_COEF0, l0, l0, grid328(L0, L0.nz + 1), 1, g));
+    E[E_START] = (int)p.size();
+    p.push_back(batch_phase(BK_RESID, l0, RESID_STEADY, nb_resid, 4, g));
+    p.push_back(ret);
+    E[E_BEGIN_USE] = (int)p.size();
+    p.push_back(batch_phase(BK_COPY, l0, COPY_TO_OLD, nb_copy, 1, g));
+    p.push_back(batch_phase(BK_COPY, l0, COPY_FSS_TO_F, nb_copy, 1, g));
+    p.push_back(ret);
+    E[E_BEGIN_COEF] = (int)p.size();
+    p.push_back(batch_phase(BK_COPY, l0, COPY_TO_OLD, nb_copy, 1, g));
+    p.push_back(batch_phase(BK_COEF0, l0, l0, grid328(L0, L0.nz + 1), 1, g));
+    p.push_back(batch_phase(BK_RESID, l0, RESID_WRITE_F | RESID_DT, nb_resid, 4, g));
+    p.push_back(ret);
+    E[E_BEGIN] = (int)p.size();
+    p.push_back(batch_phase(BK_COPY, l0, COPY_TO_OLD, nb_copy, 1, g));
+    p.push_back(batch_phase(BK_RESID, l0, RESID_WRITE_F | RESID_DT, nb_resid, 4, g));
+    p.push_back(ret);
+    // one Newton iteration
+    E[E_NEWTON] = (int)p.size();
+    if (l0 < last) {
+      const Level &C1 = s->lv[l0 + 1].L;
+      p.push_back(batch_phase(BK_INJECT, l0 + 1, last, grid328(C1, C1.nz + 1) * (last - l0), 1, g));
+      p.push_back(batch_phase(BK_COEFL, l0 + 1, last, grid328(C1, C1.nz + 1) * (last - l0), 1, g));
+    }
+    p.push_back(batch_phase(BK_FACTORL, l0, last, grid328(L0, L0.nz + 1) * (last - l0 + 1), 1, g));
+    p.push_back(batch_phase(BK_CFACT, last, 0, 1, 1, 1));
+    p.push_back(batch_phase(BK_ZERO64, l0, 0, nb_copy, 1, g));
+    const int nb_norm = m ? grid328(L0, L0.nz - 1) : cdiv(L0.nr + 1, 32) * cdiv(L0.nz - 1, 2);
+    p.push_back(batch_phase(BK_NORM0, l0, 0, nb_norm, m ? 1 : 4, g));
+    E[E_NLOOP] = (int)p.size();
+    if (m) p.push_back(batch_phase(BK_ZERO32, l0, 0, nb_copy, 1, g));
+    auto halves = [&](int l, int nu) {
+      const Level &L = s->lv[l].L;
+      const int nb = cdiv((long)(L.nz / 2) * L.ni, kBatchThreads);
+      for (int k = 0; k < nu; ++k)
+        for (int col = 0; col < 2; ++col) p.push_back(batch_phase(m ? BK_HALF32 : BK_HALF64, l, col, nb, 1, g));
+    };
+    for (int l = l0; l < s->cc_from; ++l) {
+      halves(l, nu_of(s, l, 1));
+      const Level &C = s->lv[l + 1].L;
+      p.push_back(batch_phase(m ? BK_RESTR32 : BK_RESTR64, l, 0, cdiv(C.nr + 1, 16) * cdiv(C.nz - 1, 3), 1, g));
+    }
+    p.push_back(batch_phase(m ? BK_COARSE32 : BK_COARSE64, s->cc_from, 0, 1, 1, 1));
+    for (int l = s->cc_from - 1; l >= l0; --l) {
+      const Level &F = s->lv[l].L;
+      p.push_back(batch_phase(m ? BK_PROL32 : BK_PROL64, l, 0, cdiv((long)F.ni * (F.nz - 1), kBatchThreads), 1, g));
+      halves(l, nu_of(s, l, 2));
+    }
+    if (m) p.push_back(batch_phase(BK_MIXUPD, l0, 0, cdiv((long)L0.ni * (L0.nz - 1), kBatchThreads), 1, g));
+    p.push_back(batch_phase(BK_NORMC, l0, 0, nb_norm, m ? 1 : 4, g));
+    E[E_NUPD] = (int)p.size();
+    p.push_back(batch_phase(BK_UPDATE, l0, 0, grid328(L0, L0.nz - 1), 1, g));
+    p.push_back(batch_phase(BK_COEF0, l0, l0, grid328(L0, L0.nz + 1), 1, g));
+    p.push_back(batch_phase(BK_RESID, l0, RESID_WRITE_F | RESID_STEADY | RESID_DT, nb_resid, 4, g));
+    p.push_back(ret);
+    E[E_RESTORE] = (int)p.size();
+    p.push_back(batch_phase(BK_COPY, l0, COPY_FROM_OLD, nb_copy, 1, g));
+    p.push_back(ret);
+    if (l0 < from) {
+      E[E_PROLONG] = (int)p.size();
+      p.push_back(batch_phase(BK_PROLST, l0, 0, cdiv((long)(L0.nr + 1) * (L0.nz + 1), kBatchThreads), 1, g));
+      p.push_back(batch_phase(BK_DIRI, l0, 0, 1, 1, 1));
+      p.push_back(ret);
+    }
+  }
   if ((int)p.size() > kBatchMaxProg) return fail(s, MG_EINVAL, "batched program too long (%d phases)", (int)p.size());
+  for (const BPhase &q : p)
+    if (q.ntiles >= (1 << 20)) return fail(s, MG_EINVAL, "batched program: a phase of %d work items", q.ntiles);
+  s->host_prog_ntiles0 = p[s->bent[1][E_INJECT]].ntiles;
   void *d = nullptr;
   CK(cudaMalloc(&d, p.size() * sizeof(BPhase)));
   if (cudaMemcpy(d, p.data(), p.size() * sizeof(BPhase), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(d);
     return fail(s, MG_ECUDA, "batched program upload");
   }
-  s->bprog[l0] = static_cast<BPhase *>(d);
-  s->bloop[l0] = loop_pc;
-  s->bupd[l0] = update_pc;
+  s->bprog = static_cast<BPhase *>(d);
   return MG_OK;
 }
 
-}  // namespace
-
-// The rounds of a batched solve: every discharge runs its own march on its own host thread;
-// a thread that reaches a Newton iteration waits here until every discharge still solving
-// has reached one (or finished), and the last to arrive launches the round for all of them.
-struct BatchEngine {
-  std::mutex mu;
-  std::condition_variable cv;
-  int live = 0, waiting = 0;
-  long round = 0;
-  std::vector<mg_state *> parts;
-  int cap = 0, grid = 0;
-  cudaStream_t st = nullptr;
-  BatchHead *d_head = nullptr, *h_head = nullptr;
-  BatchInst *d_inst = nullptr, *h_inst = nullptr;
-  BatchRes *d_res = nullptr, *h_res = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int fail = MG_OK;      // first error of a round; every later round reports it
-  long rounds = 0;
-};
-
-namespace {
-
-// One round (the engine's lock held): the descriptors go in, the captured graph (descriptor
-// copies, the persistent launch, the results back) runs after every participant's stream has
-// reached its iteration, and each participant gets its results.
-void run_round(BatchEngine &B) {
-  const int n = (int)B.parts.size();
-  int rc = B.fail;
-  if (rc == MG_OK) {
-    for (int k = 0; k < n && rc == MG_OK; ++k) {
-      mg_state *s = B.parts[k];
-      BatchInst I = s->binst;
-      I.claim = 0ull;
-      I.ring[0] = 0ull;
-      I.ring[1] = I.ring[2] = I.ring[3] = ~0ull;
-      I.done = 0u;
-      I.pad = 0;
-      B.h_inst[k] = I;
-      if (cudaStreamWaitEvent(B.st, s->bev, 0) != cudaSuccess) rc = MG_ECUDA;
-    }
-    B.h_head->n = n;
-    B.h_head->ndone = 0;
-    B.h_head->err = 0u;
-    if (rc == MG_OK && cudaGraphLaunch(B.exec, B.st) != cudaSuccess) rc = MG_ECUDA;
-    if (rc == MG_OK && cudaStreamSynchronize(B.st) != cudaSuccess) rc = MG_ECUDA;
-    if (rc == MG_OK && (B.h_head->err != 0u || B.h_head->ndone != n)) rc = MG_ETIMEOUT;
-    count_launch(1);
-    ++B.rounds;
-  }
-  for (int k = 0; k < n; ++k) {
-    mg_state *s = B.parts[k];
-    s->batch_rc = rc;
-    if (rc != MG_OK) continue;
-    const BatchRes &r = B.h_res[k];
-    for (int q = 0; q < 18; ++q) s->hout[q] = r.out[q];
-    s->hctl->ncyc = r.ncyc;
-    s->hctl->r0 = r.r0;
-    s->hctl->rel = r.rel;
-  }
-  if (rc != MG_OK) B.fail = rc;
-  B.parts.clear();
-  B.waiting = 0;
-  ++B.round;
-  B.cv.notify_all();
-}
-
-// A Newton iteration of state s in the next round (see step): hierarchy set-up, linear solve
-// to eta (weights w), update and the residual of the new state; the results land where the
-// single-discharge path reads them (hout[0..17], the control block's ncyc, r0, rel).
-int batch_newton(mg_state *s, int l0, double dt, double eta, const double w[3], int *ncyc, bool *ok) {
-  BatchEngine &B = *s->batch;
-  int rc = build_batch_program(s, l0);
-  if (rc) return rc;
-  BatchInst &I = s->binst;
+// The descriptor of state s's steady solve to tol: parameters and the start of the solve
+// (the injection onto level 1 runs first).
+void batch_describe(mg_state *s, double tol, BatchInst &I) {
   std::memset(&I, 0, sizeof(I));
-  I.prog = s->bprog[l0];
-  I.loop_pc = s->bloop[l0];
-  I.update_pc = s->bupd[l0];
-  I.l0 = l0;
+  I.prog = s->bprog;
+  std::memcpy(I.ent, s->bent, sizeof(I.ent));
   I.last = s->nlev - 1;
   I.mixed = mixed(s) ? 1 : 0;
   I.max_cycles = std::min(s->prm.max_vcycles, kMaxHist - 1);
@@ -874,10 +851,7 @@ int batch_newton(mg_state *s, int l0, double dt, double eta, const double w[3], 
   I.cs64 = s->cset64;
   I.cs32 = s->cset32;
   I.tr = s->tr;
-  I.dt_inv = dt > 0 ? 1.0 / dt : 0.0;
   I.n0 = s->prm.n0;
-  I.eta = eta;
-  for (int q = 0; q < 3; ++q) I.w[q] = w[q];
   I.ctl = s->ctl;
   I.partials = s->partials;
   I.dout = s->dout;
@@ -886,73 +860,53 @@ int batch_newton(mg_state *s, int l0, double dt, double eta, const double w[3], 
   I.cs = s->cs;
   I.flag = s->flag;
   for (int q = 0; q < 3; ++q) I.fss[q] = s->fss[q];
-  CK(cudaEventRecord(s->bev, s->stream));
-  {
-    std::unique_lock<std::mutex> lk(B.mu);
-    const long my = B.round;
-    B.parts.push_back(s);
-    ++B.waiting;
-    if (B.waiting == B.live) run_round(B);
-    else B.cv.wait(lk, [&] { return B.round != my; });
-  }
-  if (s->batch_rc != MG_OK) return fail(s, s->batch_rc, "batched Newton iteration failed (%s)", s->batch_rc == MG_ETIMEOUT
-                                                                                                  ? "device work list gave up"
-                                                                                                  : "CUDA error");
-  *ncyc = s->hctl->ncyc;
-  *ok = (s->hctl->r0 == 0.0) || (s->hctl->rel <= eta);
-  return MG_OK;
+  BatchMarch &M = I.m;
+  M.tol = tol;
+  M.dt1 = s->prm.dt1;
+  M.dt_max = s->prm.dt_max;
+  M.dt_growth = s->prm.dt_growth;
+  M.ntol = s->prm.newton_tol > 0.0 ? s->prm.newton_tol : 0.1 * tol;
+  M.rel = s->prm.newton_tol_rel;
+  M.limit = s->prm.corr_limit_frac * std::fabs(s->prm.V_anode - s->prm.V_cathode);
+  M.eta_p = s->prm.eta;
+  M.Vc = s->prm.V_cathode;
+  M.Va = s->prm.V_anode;
+  M.from = s->prm.chain_from;
+  M.max_steps = s->prm.max_steps;
+  M.max_newton = s->prm.max_newton;
+  M.eta_adapt = s->prm.eta_adapt;
+  M.stage = 0;  // the injection onto level 1 runs first
+  M.lvl = 1;
+  M.start_valid = 0;
+  M.steady_rho = s->stats.steady_rho;
+  M.dt_last = s->stats.dt_last;
+  for (int q = 0; q < 3; ++q) M.srho[q] = s->stats.rho[q];
+  I.claim = 0ull;
+  // ring entry of phase 0: (sequence 0 << 32) | (program counter << 20) | work items
+  const int pc0 = s->bent[1][E_INJECT];
+  I.ring[0] = ((unsigned long long)(unsigned)pc0 << 20) | (unsigned)s->host_prog_ntiles0;
+  I.ring[1] = I.ring[2] = I.ring[3] = ~0ull;
+  I.done = 0u;
 }
 
-// A participant has finished its solve: the others may now be complete for a round.
-void batch_leave(BatchEngine &B) {
-  std::unique_lock<std::mutex> lk(B.mu);
-  --B.live;
-  if (B.waiting > 0 && B.waiting == B.live) run_round(B);
-}
-
-void batch_free(BatchEngine &B) {
-  if (B.exec) cudaGraphExecDestroy(B.exec);
-  if (B.st) cudaStreamDestroy(B.st);
-  cudaFree(B.d_head);
-  cudaFree(B.d_inst);
-  cudaFree(B.d_res);
-  cudaFreeHost(B.h_head);
-  cudaFreeHost(B.h_inst);
-  cudaFreeHost(B.h_res);
-}
-
-// Buffers and the captured round graph for up to n discharges.
-int batch_setup(BatchEngine &B, int n) {
-  B.cap = n;
-  B.grid = batch_grid();
-  if (B.grid <= 0) return MG_ECUDA;
-  if (cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&B.d_head, sizeof(BatchHead)) != cudaSuccess ||
-      cudaMalloc(&B.d_inst, n * sizeof(BatchInst)) != cudaSuccess ||
-      cudaMalloc(&B.d_res, n * sizeof(BatchRes)) != cudaSuccess ||
-      cudaMallocHost(&B.h_head, sizeof(BatchHead)) != cudaSuccess ||
-      cudaMallocHost(&B.h_inst, n * sizeof(BatchInst)) != cudaSuccess ||
-      cudaMallocHost(&B.h_res, n * sizeof(BatchRes)) != cudaSuccess)
-    return MG_ECUDA;
-  std::memset(B.h_inst, 0, n * sizeof(BatchInst));
-  std::memset(B.h_res, 0, n * sizeof(BatchRes));
-  std::memset(B.h_head, 0, sizeof(BatchHead));
-  cudaGraph_t graph = nullptr;
-  set_capturing(true);
-  cudaError_t e = cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    cudaMemcpyAsync(B.d_head, B.h_head, sizeof(BatchHead), cudaMemcpyHostToDevice, B.st);
-    cudaMemcpyAsync(B.d_inst, B.h_inst, n * sizeof(BatchInst), cudaMemcpyHostToDevice, B.st);
-    launch_batch(B.d_head, B.d_inst, B.d_res, B.grid, B.st);
-    cudaMemcpyAsync(B.h_res, B.d_res, n * sizeof(BatchRes), cudaMemcpyDeviceToHost, B.st);
-    cudaMemcpyAsync(B.h_head, B.d_head, sizeof(BatchHead), cudaMemcpyDeviceToHost, B.st);
-    e = cudaStreamEndCapture(B.st, &graph);
-  }
-  set_capturing(false);
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&B.exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
-  cudaGetLastError();
-  return e == cudaSuccess ? MG_OK : MG_ECUDA;
+// The statistics and start data of a finished batched solve into the state.
+void batch_collect(mg_state *s, const BatchInst &I) {
+  const BatchMarch &M = I.m;
+  mg_stats &t = s->stats;
+  t.steps_accepted += M.steps_accepted;
+  t.steps_rejected += M.steps_rejected;
+  t.newton_iterations += M.newton_iterations;
+  t.vcycles += M.vcycles;
+  t.coarse_steps += M.coarse_steps;
+  t.coarse_newton += M.coarse_newton;
+  t.coarse_vcycles += M.coarse_vcycles;
+  if (M.steps_accepted + M.steps_rejected > 0) t.last_newton = M.last_newton;
+  for (int q = 0; q < 3; ++q) t.rho[q] = M.srho[q];
+  t.steady_rho = M.steady_rho;
+  t.dt_last = M.dt_last;
+  t.sim_time += M.sim_time;
+  for (int q = 0; q < 16; ++q) s->start_sums[q] = M.start_sums[q];
+  s->start_valid = M.start_valid != 0;
 }
 
 // One backward-Euler step on level l0 (eq. 7 by Newton-Raphson on eq. 14).
@@ -1047,39 +1001,33 @@ int step(mg_state *s, int l0, double dt, double tol, int *newton_out, bool coef_
     const double eta = s->prm.eta_adapt ? std::max(s->prm.eta, std::min(0.1, 0.5 * tol / rmax)) : s->prm.eta;
     double w[3];
     solve_weights(tn, w);
-    if (s->batch) {
-      // the whole iteration (set-up, linear solve, update, residual) in a round of the batched
-      // persistent launch, together with the other discharges' iterations
-      if ((rc = batch_newton(s, l0, dt, eta, w, &ncyc, &ok))) return rc;
-    } else {
-      rc = build_hierarchy(s, l0, dt);
-      if (rc) return rc;
-      const bool graph = use_graph(s, s->prm.max_vcycles);
-      const bool full = s->prm.full_jacobian != 0;
-      if (graph) rc = linear_solve_graph_begin(s, l0, eta, s->prm.max_vcycles, w);
-      else rc = linear_solve_eager(s, l0, eta, s->prm.max_vcycles, w, nullptr, &ncyc, &ok);
-      if (rc) return rc;
-      if (full) {
-        // the defect corrections need the Picard step first
-        if (graph) {
-          CK(cudaStreamSynchronize(s->stream));
-          linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
-        }
-        if (ok) {
-          int nc2 = 0;
-          if ((rc = full_jacobian_correct(s, l0, eta, tn, rmax, &nc2, &ok))) return rc;
-          ncyc += nc2;
-        }
+    rc = build_hierarchy(s, l0, dt);
+    if (rc) return rc;
+    const bool graph = use_graph(s, s->prm.max_vcycles);
+    const bool full = s->prm.full_jacobian != 0;
+    if (graph) rc = linear_solve_graph_begin(s, l0, eta, s->prm.max_vcycles, w);
+    else rc = linear_solve_eager(s, l0, eta, s->prm.max_vcycles, w, nullptr, &ncyc, &ok);
+    if (rc) return rc;
+    if (full) {
+      // the defect corrections need the Picard step first
+      if (graph) {
+        CK(cudaStreamSynchronize(s->stream));
+        linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
       }
-      // u += du (max |dV| and the non-finite flag into dout[16..17]), then the residual at the
-      // new state (into dout[0..5], its steady rows' sums and start data into dout[6..15] and
-      // fss); used only if the update is accepted
-      CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout + 16, s->stream));
-      if ((rc = residual_launch(s, l0, dt, true, nullptr, true, true))) return rc;
-      rc = sync_read(s, 18);
-      if (rc) return rc;
-      if (graph && !full) linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
+      if (ok) {
+        int nc2 = 0;
+        if ((rc = full_jacobian_correct(s, l0, eta, tn, rmax, &nc2, &ok))) return rc;
+        ncyc += nc2;
+      }
     }
+    // u += du (max |dV| and the non-finite flag into dout[16..17]), then the residual at the new
+    // state (into dout[0..5], its steady rows' sums and start data into dout[6..15] and fss);
+    // used only if the update is accepted
+    CK(launch_update(b.L, b.sv, s->partials, s->counter, s->dout + 16, s->stream));
+    if ((rc = residual_launch(s, l0, dt, true, nullptr, true, true))) return rc;
+    rc = sync_read(s, 18);
+    if (rc) return rc;
+    if (graph && !full) linear_solve_graph_end(s, l0, eta, nullptr, &ncyc, &ok);
     s->stats.vcycles += ncyc;
     if (!ok) { *newton_out = it + 1; reason = MG_ENOCONV; break; }
     if (s->hout[17] != 0.0) { *newton_out = it + 1; reason = MG_ENONFINITE; break; }
@@ -1493,9 +1441,7 @@ void mg_destroy(mg_state *s) {
   if (s->hctl) cudaFreeHost(s->hctl);
   if (s->owns_ws && s->ws) cudaFree(s->ws);
   if (s->hout) cudaFreeHost(s->hout);
-  for (int l = 0; l < kMaxLevels; ++l)
-    if (s->bprog[l]) cudaFree(s->bprog[l]);
-  if (s->bev) cudaEventDestroy(s->bev);
+  if (s->bprog) cudaFree(s->bprog);
   delete s;
 }
 
@@ -1904,43 +1850,86 @@ int mg_num_levels(const mg_state *s) { return s ? s->nlev : 0; }
 
 // ---------------------------------------------------------------- batched steady solves
 namespace {
-// The persistent form: one host thread per discharge runs its march; their Newton iterations
-// meet in rounds of the batched persistent launch.  ms_out[k]: from the batch's start to
-// discharge k's solve returning.
-int solve_batch_persistent(mg_state **states, int n, double tol, int dev, double *ms_out, int *rc_out) {
-  BatchEngine B;
-  int rc = batch_setup(B, n);
-  for (int k = 0; k < n && rc == MG_OK; ++k)
-    if (!states[k]->bev && cudaEventCreateWithFlags(&states[k]->bev, cudaEventDisableTiming) != cudaSuccess) rc = MG_ECUDA;
-  if (rc != MG_OK) {
-    batch_free(B);
-    return rc;
+// The persistent form: every discharge's whole steady solve in one launch of the work-list
+// kernel, replayed from a captured graph (descriptors in, the launch, descriptors back).
+// ms_out[k]: from the launch's start to discharge k's solve ending (device clock).
+int solve_batch_persistent(mg_state **states, int n, double tol, double *ms_out, int *rc_out) {
+  int rc = MG_OK;
+  for (int k = 0; k < n && rc == MG_OK; ++k) {
+    rc = build_batch_program(states[k]);
+    if (rc == MG_OK && cudaStreamSynchronize(states[k]->stream) != cudaSuccess) rc = MG_ECUDA;
   }
-  B.live = n;
-  std::vector<int> rcs(n, MG_OK);
-  const auto t0 = std::chrono::steady_clock::now();
-  auto work = [&](int k) {
-    cudaSetDevice(dev);
-    mg_state *s = states[k];
-    s->batch = &B;
-    int r = mg_solve_steady(s, tol, nullptr);
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess && r == MG_OK) r = MG_ECUDA;
-    s->batch = nullptr;
-    const auto t1 = std::chrono::steady_clock::now();
-    batch_leave(B);
-    rcs[k] = r;
-    if (ms_out) ms_out[k] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  if (rc != MG_OK) return rc;
+  const int grid = batch_grid();
+  if (grid <= 0) return MG_ECUDA;
+  cudaStream_t st = nullptr;
+  BatchHead *d_head = nullptr, *h_head = nullptr;
+  BatchInst *d_inst = nullptr, *h_inst = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(d_head);
+    cudaFree(d_inst);
+    cudaFreeHost(h_head);
+    cudaFreeHost(h_inst);
   };
-  std::vector<std::thread> pool;
-  for (int k = 1; k < n; ++k) pool.emplace_back(work, k);
-  if (n > 0) work(0);
-  for (auto &t : pool) t.join();
-  batch_free(B);
-  int first = MG_OK;
-  for (int k = 0; k < n; ++k) {
-    if (rc_out) rc_out[k] = rcs[k];
-    if (first == MG_OK && rcs[k] != MG_OK) first = rcs[k];
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&d_head, sizeof(BatchHead)) != cudaSuccess || cudaMalloc(&d_inst, n * sizeof(BatchInst)) != cudaSuccess ||
+      cudaMallocHost(&h_head, sizeof(BatchHead)) != cudaSuccess ||
+      cudaMallocHost(&h_inst, n * sizeof(BatchInst)) != cudaSuccess) {
+    cleanup();
+    return MG_ECUDA;
   }
+  // largest discharges first: the CTAs look for work in this order (longest chains first)
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return states[a]->lv[0].nodes > states[b]->lv[0].nodes; });
+  for (int k = 0; k < n; ++k) batch_describe(states[order[k]], tol, h_inst[k]);
+  std::memset(h_head, 0, sizeof(BatchHead));
+  h_head->n = n;
+  h_head->t0 = ~0ull;
+  set_capturing(true);
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemcpyAsync(d_head, h_head, sizeof(BatchHead), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_inst, h_inst, n * sizeof(BatchInst), cudaMemcpyHostToDevice, st);
+    launch_batch(d_head, d_inst, grid, st);
+    cudaMemcpyAsync(h_inst, d_inst, n * sizeof(BatchInst), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h_head, d_head, sizeof(BatchHead), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamEndCapture(st, &graph);
+  }
+  set_capturing(false);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  count_launch(1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return MG_ECUDA;
+  }
+  const bool gave_up = h_head->err != 0u || h_head->ndone != n;
+  int first = MG_OK;
+  for (int j = 0; j < n; ++j) {
+    const int k = order[j];
+    mg_state *s = states[k];
+    const BatchInst &I = h_inst[j];
+    int r = I.m.rc;
+    if (gave_up) {
+      r = MG_ETIMEOUT;
+      fail(s, r, "batched solve: the device work list stopped making progress");
+    } else {
+      batch_collect(s, I);
+      if (r != MG_OK) fail(s, r, "march: steady residual not reached in %d steps", s->prm.max_steps);
+    }
+    if (rc_out) rc_out[k] = r;
+    if (ms_out) ms_out[k] = I.m.t_done > h_head->t0 ? (double)(I.m.t_done - h_head->t0) * 1e-6 : 0.0;
+    if (first == MG_OK && r != MG_OK) first = r;
+  }
+  cleanup();
   return first;
 }
 }  // namespace
@@ -1954,7 +1943,7 @@ int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, dou
   if (workers == 0) {
     bool all = true;
     for (int k = 0; k < n; ++k) all = all && batchable(states[k]);
-    if (all) return solve_batch_persistent(states, n, tol, dev, ms_out, rc_out);
+    if (all) return solve_batch_persistent(states, n, tol, ms_out, rc_out);
     workers = 16;  // a configuration the persistent launch does not cover: host threads
   }
   workers = std::max(1, std::min(workers, n));
@@ -1983,6 +1972,69 @@ int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, dou
     if (first == MG_OK && rcs[k] != MG_OK) first = rcs[k];
   }
   return first;
+}
+
+int mg_autotune_batch(mg_state **states, int n, double tol, int *grain_out) {
+  if (!states || n <= 0 || !(tol > 0.0)) return MG_EINVAL;
+  for (int k = 0; k < n; ++k)
+    if (!states[k] || !batchable(states[k])) return MG_EINVAL;
+  // every trial starts from the states as they are now: solution (finest level), statistics and
+  // start data saved here and restored before each trial and at the end
+  std::vector<mg_stats> st0(n);
+  std::vector<std::vector<double>> ss0(n);
+  std::vector<bool> sv0(n);
+  for (int k = 0; k < n; ++k) {
+    mg_state *s = states[k];
+    LevelBuf &b = s->lv[0];
+    for (int q = 0; q < 3; ++q)
+      if (cudaMemcpyAsync(b.ubak[q], b.sv.u[q], b.nodes * sizeof(double), cudaMemcpyDeviceToDevice, s->stream) !=
+          cudaSuccess)
+        return MG_ECUDA;
+    st0[k] = s->stats;
+    ss0[k].assign(s->start_sums, s->start_sums + 16);
+    sv0[k] = s->start_valid;
+  }
+  auto restore = [&]() -> int {
+    for (int k = 0; k < n; ++k) {
+      mg_state *s = states[k];
+      LevelBuf &b = s->lv[0];
+      for (int q = 0; q < 3; ++q)
+        if (cudaMemcpyAsync(b.sv.u[q], b.ubak[q], b.nodes * sizeof(double), cudaMemcpyDeviceToDevice, s->stream) !=
+            cudaSuccess)
+          return MG_ECUDA;
+      if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MG_ECUDA;
+      s->stats = st0[k];
+      std::copy(ss0[k].begin(), ss0[k].end(), s->start_sums);
+      s->start_valid = sv0[k];
+    }
+    return MG_OK;
+  };
+  auto set_grain = [&](int g) {
+    for (int k = 0; k < n; ++k) {
+      mg_state *s = states[k];
+      if (s->bgrain != g && s->bprog) {
+        cudaFree(s->bprog);
+        s->bprog = nullptr;
+      }
+      s->bgrain = g;
+    }
+  };
+  static const int kGrains[] = {1, 2, 4, 8};
+  int best = 4, rc = MG_OK;
+  double best_ms = 1e300;
+  for (int g : kGrains) {
+    if ((rc = restore())) return rc;
+    set_grain(g);
+    const auto t0 = std::chrono::steady_clock::now();
+    rc = solve_batch_persistent(states, n, tol, nullptr, nullptr);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc != MG_OK) break;
+    if (ms < best_ms) { best_ms = ms; best = g; }
+  }
+  const int rc2 = restore();
+  set_grain(best);
+  if (grain_out) *grain_out = best;
+  return rc != MG_OK ? rc : rc2;
 }
 
 }  // extern "C"

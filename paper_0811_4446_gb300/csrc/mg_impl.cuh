@@ -130,59 +130,80 @@ struct SolveCtl {
   double hist[kMaxHist];
 };
 
-// ---- batched form: one persistent launch runs a Newton iteration of many discharges --------
-// Each participating discharge follows a program of phases (the launches of one Newton
-// iteration of the single-discharge path, in order: hierarchy set-up, the V-cycle loop with its
-// stopping test, the update and the residual of the new state).  A phase is a list of work items
-// (tiles); the CTAs of the launch claim tiles of any discharge's current phase, and the CTA that
-// finishes a phase's last tile folds its reductions and moves that discharge to its next phase.
+// ---- batched form: one persistent launch runs the steady solves of many discharges ---------
+// Each discharge's solve (the continuation, the Delta-t march with its accept / reject logic,
+// the Newton loop of every step) runs as a state machine on the device; its GPU work is a
+// sequence of phases from the discharge's program (the launches of the single-discharge path,
+// in its order).  A phase is a list of work items (tiles); the CTAs of the launch claim tiles
+// of any discharge's current phase, and the CTA that finishes a phase's last tile folds its
+// reductions, advances the discharge's state machine and publishes its next phase.
 enum BatchKind : int32_t {
   BK_INJECT = 0, BK_COEFL, BK_FACTORL, BK_CFACT, BK_ZERO64, BK_NORM0, BK_ZERO32, BK_HALF64, BK_HALF32,
   BK_RESTR64, BK_RESTR32, BK_COARSE64, BK_COARSE32, BK_PROL64, BK_PROL32, BK_MIXUPD, BK_NORMC, BK_UPDATE,
-  BK_COEF0, BK_RESID, BK_DONE
+  BK_COEF0, BK_RESID, BK_INJECT1, BK_COPY, BK_PROLST, BK_DIRI, BK_RET, BK_DONE
 };
+// BK_RESID variants (arg bits): write f, reduce the steady sums and write the steady -F, use 1/dt
+enum { RESID_WRITE_F = 1, RESID_STEADY = 2, RESID_DT = 4 };
+// BK_COPY variants (arg): u -> u_old, u_old -> u, steady -F -> f
+enum { COPY_TO_OLD = 0, COPY_FROM_OLD = 1, COPY_FSS_TO_F = 2 };
 struct BPhase {
   int32_t kind;
-  int32_t level;    // the level worked on (the fine level of a transfer, the first of a range)
-  int32_t arg;      // colour of a half sweep; last level of a range
-  int32_t ntiles;   // work items of the phase (0: the end of the program)
+  int32_t level;    // the level worked on (the root of a Newton iteration, the fine level of a
+                    // transfer, the first of a range)
+  int32_t arg;      // colour of a half sweep; last level of a range; variant
+  int32_t ntiles;   // work items of the phase
   int32_t grain;    // thread-block rounds per work item
   int32_t nblocks;  // thread blocks of the kernel the phase stands for (reduction partials)
 };
 constexpr int kBatchThreads = 256;   // threads per CTA of the persistent launch
-constexpr int kBatchMaxProg = 512;   // phases per program
+constexpr int kBatchMaxProg = 4096;  // phases per program (12 bits of a ring entry)
+// entry points of the subprograms of one level (program counters)
+enum { E_INJECT = 0, E_START_COEF, E_START, E_BEGIN_USE, E_BEGIN_COEF, E_BEGIN, E_NEWTON, E_NLOOP, E_NUPD,
+       E_RESTORE, E_PROLONG, E_N };
+// Device-resident state of one discharge's steady solve (the host's march / step variables)
+struct BatchMarch {
+  // parameters
+  double tol, dt1, dt_max, dt_growth, ntol, rel, limit, eta_p, Vc, Va;
+  int32_t from, max_steps, max_newton, eta_adapt;
+  // where the solve is
+  int32_t stage, lvl, next_lvl, nstep, it, newton_out, reason, coef_current, start_valid, counted, rc, pad;
+  double dt, dt_prev, r_start, step_tol, r_step, eta;
+  double rho[3], tn[3], rho_steady[3], cand[16], start_sums[16];
+  // statistics of this solve (the host adds them to the state's)
+  int32_t steps_accepted, steps_rejected, newton_iterations, vcycles, last_newton;
+  int32_t coarse_steps, coarse_newton, coarse_vcycles;
+  double srho[3], steady_rho, dt_last, sim_time;
+  unsigned long long t_done;         // globaltimer when the solve ended
+};
 struct BatchInst {
-  const BPhase *prog;               // device program of this root level
-  int32_t loop_pc, update_pc, l0, last, mixed, max_cycles;
+  const BPhase *prog;               // device program (every level's subprograms)
+  int32_t ent[kMaxLevelSet][E_N];   // subprogram entries per level
+  int32_t last, mixed, max_cycles, pad0;
   const LevelSet *S;
   const CoarseSet<double> *cs64;
   const CoarseSet<float> *cs32;
   Transport tr;
-  double dt_inv, n0, eta, w[3];
+  double dt_inv, n0, eta, w[3];     // of the current Newton iteration (set by the state machine)
   SolveCtl *ctl;
   double *partials, *dout, *Minv, *rs, *cs;
   int *flag;
   double *fss[3];
-  // run state, reset by the host before each launch
+  BatchMarch m;
+  // run state, reset by the host before the launch
   unsigned long long claim;         // (sequence << 32) | work items claimed of the current phase
-  unsigned long long ring[4];       // (sequence << 32) | program counter of phase `sequence`, at sequence & 3
+  unsigned long long ring[4];       // phase `sequence` at sequence & 3: (sequence << 32) | (pc << 20) | work items
   unsigned int done;                // work items finished of the current phase
-  int32_t pad;
-};
-struct BatchRes {                   // what the host reads back per discharge
-  double out[18];                   // the residual sums (0..15) and the update's max |dV|, non-finite flag
-  double r0, rel;                   // the linear solve's initial weighted residual and last ratio
-  int32_t ncyc, pad;
+  int32_t pad1;
 };
 struct BatchHead {
   int32_t n;                        // discharges in this launch
-  int32_t ndone;                    // discharges whose program has ended
-  unsigned int err;                 // 1: a CTA found no work for kBatchIdleNs (the launch gave up)
-  int32_t pad;
+  int32_t ndone;                    // discharges whose solve has ended
+  unsigned int err;                 // 1: no phase finished anywhere for kBatchIdleNs (the launch gave up)
+  unsigned int progress;            // phases finished (the CTAs' idle clocks restart when it moves)
+  unsigned long long t0;            // globaltimer at the launch's start (the earliest CTA)
 };
-cudaError_t launch_batch(BatchHead *head, BatchInst *inst, BatchRes *res, int grid, cudaStream_t st);
+cudaError_t launch_batch(BatchHead *head, BatchInst *inst, int grid, cudaStream_t st);
 int batch_grid();                   // CTAs of the persistent launch: SMs x resident CTAs per SM (0: error)
-size_t batch_smem_bytes();
 
 // ---- launch wrappers (mg_kernels.cu) ------------------------------------------------------
 // All take the stream last and return cudaGetLastError() of the launch.  While a stream capture

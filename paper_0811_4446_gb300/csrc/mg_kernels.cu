@@ -2495,29 +2495,58 @@ double probe_fp64_gflops(cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Batched form (row a11): one persistent launch runs one Newton iteration of every
-// participating discharge.  The CTAs claim work items (tiles) of any discharge's current
-// phase; a discharge's phases follow its program (mg_api.cu builds it from the launches of the
-// single-discharge Newton iteration), and the CTA that finishes a phase's last tile folds the
-// phase's reductions and publishes the next phase.  No CTA ever waits for another: a CTA
-// without work looks again (with a growing pause), so progress needs no co-residency, and a
-// CTA that finds no work for kBatchIdleNs marks the launch as failed and leaves.
+// Batched form (row a11): one persistent launch runs the steady solves of many discharges.
+// Each discharge's solve is a state machine (batch_control below: the continuation, the
+// Delta-t march with its accept / reject rules, the Newton loop of each step, as the host
+// driver runs them for one discharge) whose GPU work is a sequence of phases taken from the
+// discharge's program (mg_api.cu builds it from the launches of the single-discharge path).
+// The CTAs claim work items (tiles) of any discharge's current phase; the CTA that finishes a
+// phase's last tile folds the phase's reductions, lets the state machine choose the next phase
+// and publishes it.  No CTA waits for another: a CTA without work looks again (with a growing
+// pause), so progress needs no co-residency; if no phase finishes anywhere for kBatchIdleNs a
+// CTA marks the launch as failed and every CTA leaves.
 //
 // Every tile runs the per-node functions of the corresponding single-discharge kernel over
 // the same nodes; reductions replicate reduce_finish's per-block partials (virtual blocks of the
-// original block shape) and its fold, so the sums equal the single-discharge ones bit for bit.
+// original block shape) and its fold, and the state machine evaluates the host driver's
+// expressions operation by operation, so the solves equal the single-discharge ones bit for bit.
 //
 // Claims: claim = (sequence << 32) | count.  A claimer adds 1; the value returned names the
 // phase (ring[sequence & 3] must carry the same sequence) and the tile (count < ntiles).  The
 // finisher writes ring[(sequence + 1) & 3], resets done, fences, then swaps in the next
 // sequence with count 0; a claim that lands after the swap is a valid claim of the new phase.
-// Visibility: tile writes -> barrier -> fence -> atomic on `done`; the finisher fences after its
-// atomic, and the claimer fences after its claim, before reading data of earlier phases.
+// Visibility: tile writes -> CTA barrier -> release-acquire add on `done` (the finisher acquires
+// every tile's writes); the publisher's swap of `claim` releases, and a claim (acquire-release
+// add) acquires, before any data of earlier phases is read.
 constexpr unsigned long long kBatchIdleNs = 5000000000ull;
 constexpr int kBW = kBatchThreads / 32;   // warps per CTA
 
+// ring entry: (sequence << 32) | (program counter << 20) | work items of the phase
+__device__ __forceinline__ unsigned long long ring_entry(unsigned seq, int pc, int ntiles) {
+  return ((unsigned long long)seq << 32) | ((unsigned long long)(unsigned)pc << 20) | (unsigned)ntiles;
+}
+__device__ __forceinline__ int ring_pc(unsigned long long e) { return (int)((e >> 20) & 0xfffu); }
+__device__ __forceinline__ unsigned ring_ntiles(unsigned long long e) { return (unsigned)(e & 0xfffffu); }
 __device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long *p) {
   return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+// Acquire-release atomics at GPU scope: a claim acquires the publisher's writes (ring entry,
+// state machine, data of earlier phases), a finished tile releases its CTA's writes (the CTA
+// barrier before it orders them), and the publisher's swap releases the next phase.
+__device__ __forceinline__ unsigned long long atom_add_acqrel64(unsigned long long *p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned atom_add_acqrel32(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void atom_exch_release64(unsigned long long *p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.release.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  (void)old;
 }
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -2618,7 +2647,6 @@ constexpr size_t kBatchShRed = 16 * kBW * sizeof(double);
 constexpr size_t kBatchShGJ = (size_t)kSmemGJ * 2 * kSmemGJ * sizeof(double) + 2 * kSmemGJ * sizeof(double) + 16;
 constexpr size_t kBatchShRestr = 3 * (2 * kBatchRestrCX + 1) * (2 * kBatchRestrCY + 1) * sizeof(double);
 constexpr size_t kBatchSmem = kBatchShRed + (kBatchShGJ > kBatchShRestr ? kBatchShGJ : kBatchShRestr);
-size_t batch_smem_bytes() { return kBatchSmem; }
 
 // 32 x 8 thread block b of a (gx, gy, levels) grid: level offset, node (i, j) of this thread
 __device__ __forceinline__ void vb328(int b, int gx, int gy, int &lz, int &i, int &j) {
@@ -2654,7 +2682,7 @@ __device__ __forceinline__ void batch_restrict(const BatchInst &I, const BPhase 
   const int gx = (C.nr + 1 + kBatchRestrCX - 1) / kBatchRestrCX;
   for (int r = 0; r < ph.grain; ++r) {
     const int b = tile * ph.grain + r;
-    // blocks past the grid find every node out of range and only pass the barrier
+    // blocks past the grid find every coarse node out of range and only pass the barrier
     linres_restrict_tile<T, kBatchRestrCX, kBatchRestrCY>(F, C, (b % gx) * kBatchRestrCX, 1 + (b / gx) * kBatchRestrCY,
                                                           threadIdx.x, kBatchThreads, reinterpret_cast<T *>(buf));
     __syncthreads();
@@ -2685,8 +2713,9 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
   const LevelSet *S = I.S;
   const int tid = threadIdx.x;
   switch (ph.kind) {
-    case BK_INJECT: {  // k_inject_levels: levels l0 + 1 .. last from level l0
+    case BK_INJECT: {  // k_inject_levels: levels level .. arg from level - 1
       const Level &C1 = S->L[ph.level];
+      const int l0 = ph.level - 1;
       const int gx = (C1.nr + 1 + 31) / 32, gy = (C1.nz + 1 + 7) / 8;
       for (int r = 0; r < ph.grain; ++r) {
         const int b = tile * ph.grain + r;
@@ -2696,10 +2725,28 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
         const int l = ph.level + lz;
         const Level &C = S->L[l];
         if (I_ > C.nr || J_ > C.nz) continue;
-        const int sh = l - I.l0;
-        const size_t kc = (size_t)J_ * C.P + I_, kf = ((size_t)J_ << sh) * S->L[I.l0].P + ((size_t)I_ << sh);
+        const int sh = l - l0;
+        const size_t kc = (size_t)J_ * C.P + I_, kf = ((size_t)J_ << sh) * S->L[l0].P + ((size_t)I_ << sh);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) S->sv[l].u[q][kc] = S->sv[I.l0].u[q][kf];
+        for (int q = 0; q < 3; ++q) S->sv[l].u[q][kc] = S->sv[l0].u[q][kf];
+      }
+      break;
+    }
+    case BK_INJECT1: {  // k_inject (state and sources) from level - 1 to level
+      const Level &C = S->L[ph.level], &F = S->L[ph.level - 1];
+      const StateView &cs = S->sv[ph.level], &fs = S->sv[ph.level - 1];
+      const int gx = (C.nr + 1 + 31) / 32, gy = (C.nz + 1 + 7) / 8;
+      for (int r = 0; r < ph.grain; ++r) {
+        const int b = tile * ph.grain + r;
+        if (b >= ph.nblocks) break;
+        int lz, I_, J_;
+        vb328(b, gx, gy, lz, I_, J_);
+        if (I_ > C.nr || J_ > C.nz) continue;
+        const size_t kc = (size_t)J_ * C.P + I_, kf = (size_t)(2 * J_) * F.P + 2 * I_;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cs.u[q][kc] = fs.u[q][kf];
+        const_cast<double *>(cs.S[0])[kc] = fs.S[0][kf];
+        const_cast<double *>(cs.S[1])[kc] = fs.S[1][kf];
       }
       break;
     }
@@ -2742,11 +2789,11 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
       coarse_factor_smem_body(S->L[I.last], I.dt_inv, I.Minv, I.rs, I.cs, I.flag, sAB, srs, scs, sp);
       break;
     }
-    case BK_ZERO64: batch_zero<double>(S->L[I.l0], ph, tile); break;
-    case BK_ZERO32: batch_zero<float>(S->M[I.l0], ph, tile); break;
+    case BK_ZERO64: batch_zero<double>(S->L[ph.level], ph, tile); break;
+    case BK_ZERO32: batch_zero<float>(S->M[ph.level], ph, tile); break;
     case BK_NORM0:
     case BK_NORMC: {
-      const Level &L = S->L[I.l0];
+      const Level &L = S->L[ph.level];
       if (I.mixed) {  // k_outer_residual: 32 x 8 blocks
         const int gx = (L.nr + 1 + 31) / 32, gy = (L.nz - 1 + 7) / 8;
         for (int r = 0; r < ph.grain; ++r) {
@@ -2754,7 +2801,7 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
           int lz, i, j;
           vb328(b, gx, gy, lz, i, j);
           double acc[3] = {0.0, 0.0, 0.0};
-          if (b < ph.nblocks) outer_row(L, S->M[I.l0], 1.0 / I.n0, i, j + 1, acc);
+          if (b < ph.nblocks) outer_row(L, S->M[ph.level], 1.0 / I.n0, i, j + 1, acc);
           vblock_partial<3>(acc, 256, b < ph.nblocks, I.partials + (size_t)b * 3, red, 0);
         }
       } else {  // k_linres (f - J du into r): 32 x 2 blocks, four per round
@@ -2786,8 +2833,8 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
     case BK_PROL64: batch_prolong<double>(I, ph, tile); break;
     case BK_PROL32: batch_prolong<float>(I, ph, tile); break;
     case BK_MIXUPD: {  // k_mixed_update
-      const Level &L = S->L[I.l0];
-      const LevelT<float> &M = S->M[I.l0];
+      const Level &L = S->L[ph.level];
+      const LevelT<float> &M = S->M[ph.level];
       const int n = L.ni * (L.nz - 1);
       for (int r = 0; r < ph.grain; ++r) {
         const int t = (tile * ph.grain + r) * kBatchThreads + tid;
@@ -2800,28 +2847,91 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
       break;
     }
     case BK_UPDATE: {  // k_update: 32 x 8 blocks, maxima
-      const Level &L = S->L[I.l0];
+      const Level &L = S->L[ph.level];
       const int gx = (L.nr + 1 + 31) / 32, gy = (L.nz - 1 + 7) / 8;
       for (int r = 0; r < ph.grain; ++r) {
         const int b = tile * ph.grain + r;
         int lz, i, j;
         vb328(b, gx, gy, lz, i, j);
         double acc[2] = {0.0, 0.0};
-        if (b < ph.nblocks) update_row(L, S->sv[I.l0], i, j + 1, acc);
+        if (b < ph.nblocks) update_row(L, S->sv[ph.level], i, j + 1, acc);
         vblock_partial<2>(acc, 256, b < ph.nblocks, I.partials + (size_t)b * 2, red, 1);
       }
       break;
     }
-    case BK_RESID: {  // k_resid_coef with the steady sums, f and the steady -F: 32 x 2 blocks, four per round
-      const Level &L = S->L[I.l0];
+    case BK_RESID: {  // k_resid_coef: 32 x 2 blocks, four per round
+      const Level &L = S->L[ph.level];
       const int gx = (L.nr + 1 + 31) / 32;
+      const int wf = (ph.arg & RESID_WRITE_F) ? 1 : 0, st = (ph.arg & RESID_STEADY) ? 1 : 0;
+      const double dti = (ph.arg & RESID_DT) ? I.dt_inv : 0.0;
       for (int r = 0; r < ph.grain; ++r) {
         const int b = (tile * ph.grain + r) * 4 + (tid >> 6);
         const int i = (b % gx) * 32 + (tid & 31), j = (b / gx) * 2 + ((tid >> 5) & 1) + 1;
         double acc[16];
-        resid_row(L, S->sv[I.l0], I.dt_inv, 1, 1, nullptr, nullptr, nullptr, I.fss[0], I.fss[1], I.fss[2],
-                  b < ph.nblocks ? i : L.ni, j, acc);
+        resid_row(L, S->sv[ph.level], dti, wf, st, nullptr, nullptr, nullptr, st ? I.fss[0] : nullptr,
+                  st ? I.fss[1] : nullptr, st ? I.fss[2] : nullptr, b < ph.nblocks ? i : L.ni, j, acc);
         vblock_partial<16>(acc, 64, b < ph.nblocks, I.partials + (size_t)b * 16, red, 0);
+      }
+      break;
+    }
+    case BK_COPY: {  // the host's device-to-device copies of whole node arrays
+      const Level &L = S->L[ph.level];
+      const StateView &sv = S->sv[ph.level];
+      const size_t n = (size_t)(L.nz + 1) * L.P;
+      for (int r = 0; r < ph.grain; ++r) {
+        const size_t t = (size_t)(tile * ph.grain + r) * kBatchThreads + tid;
+        if (t >= n) break;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (ph.arg == COPY_TO_OLD) sv.uold[q][t] = sv.u[q][t];
+          else if (ph.arg == COPY_FROM_OLD) sv.u[q][t] = sv.uold[q][t];
+          else L.f[q][t] = I.fss[q][t];
+        }
+      }
+      break;
+    }
+    case BK_PROLST: {  // k_prolong_state: level + 1 -> level, every node
+      const Level &C = S->L[ph.level + 1], &F = S->L[ph.level];
+      const StateView &cs = S->sv[ph.level + 1], &fs = S->sv[ph.level];
+      const int n = (F.nr + 1) * (F.nz + 1);
+      for (int r = 0; r < ph.grain; ++r) {
+        const int t = (tile * ph.grain + r) * kBatchThreads + tid;
+        if (t >= n) break;
+        const int i = t % (F.nr + 1), j = t / (F.nr + 1);
+        const size_t kf = (size_t)j * F.P + i;
+        int J0, J1;
+        double w0, w1;
+        if (j & 1) { J0 = (j - 1) >> 1; J1 = J0 + 1; w1 = F.wz[j]; w0 = 1.0 - w1; }
+        else { J0 = J1 = j >> 1; w0 = 1.0; w1 = 0.0; }
+        int I0, I1;
+        double v0, v1;
+        if (i & 1) { I0 = (i - 1) >> 1; I1 = I0 + 1; v0 = v1 = 0.5; }
+        else { I0 = I1 = i >> 1; v0 = 1.0; v1 = 0.0; }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const double *c = cs.u[q];
+          const double a = v0 * c[(size_t)J0 * C.P + I0] + v1 * c[(size_t)J0 * C.P + I1];
+          const double b = v0 * c[(size_t)J1 * C.P + I0] + v1 * c[(size_t)J1 * C.P + I1];
+          fs.u[q][kf] = w0 * a + w1 * b;
+        }
+      }
+      break;
+    }
+    case BK_DIRI: {  // k_dirichlet on level
+      const Level &L = S->L[ph.level];
+      const StateView &sv = S->sv[ph.level];
+      const double Vc = I.m.Vc, Va = I.m.Va;
+      const int n = (L.nr > L.nz ? L.nr : L.nz) + 1;
+      for (int t = tid; t < n; t += kBatchThreads) {
+        if (t <= L.nr) {
+          const size_t k0 = t, k1 = (size_t)L.nz * L.P + t;
+          sv.u[NE][k0] = 0.0; sv.u[NP][k0] = 0.0; sv.u[NV][k0] = Vc;
+          sv.u[NE][k1] = 0.0; sv.u[NP][k1] = 0.0; sv.u[NV][k1] = Va;
+        }
+        if (L.ni == L.nr && t <= L.nz) {
+          const size_t kw = (size_t)t * L.P + L.nr;
+          sv.u[NE][kw] = 0.0; sv.u[NP][kw] = 0.0; sv.u[NV][kw] = Vc + (Va - Vc) * L.zf[t];
+        }
       }
       break;
     }
@@ -2829,11 +2939,235 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
   }
 }
 
-// The finisher of a phase (every thread of its CTA): fold the phase's reduction, then thread 0
-// evaluates the discharge's control (the stopping test of the V-cycle loop, the end of the
-// program) and publishes the next phase.
-__device__ void batch_finish(BatchInst &I, const BPhase &ph, int pc, unsigned seq, BatchRes *res, BatchHead *head,
-                             double *red) {
+// ---- the steady solve of one discharge as a state machine (thread 0 of a finishing CTA) ----
+// It follows the host driver (mg_solve_steady -> march -> step in mg_api.cu) statement by
+// statement; std::max / std::min are (a < b ? b : a) / (b < a ? b : a), and the one expression
+// with a product added to a sum is evaluated with rounded operations in the host's order.
+enum { MS_INJECT = 0, MS_START, MS_BEGIN_USE, MS_BEGIN, MS_NEWTON, MS_RESTORE, MS_ACCSTART, MS_PROLONG };
+constexpr int kMgOk = 0, kMgEnoconv = -3, kMgEreject = -4, kMgEnonfinite = -5;
+
+__device__ __forceinline__ double hmax(double a, double b) { return (a < b) ? b : a; }
+__device__ __forceinline__ double hmin(double a, double b) { return (b < a) ? b : a; }
+
+__device__ __forceinline__ double ratio(double f2, double t2) {  // sqrt(f2) / sqrt(t2), as residual_norms
+  const double fn = sqrt(f2), t = sqrt(t2);
+  return fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
+}
+
+__device__ __forceinline__ double steady_of_start(const BatchMarch &M) {
+  double m = 0.0;
+  for (int q = 0; q < 3; ++q) m = hmax(m, ratio(M.start_sums[6 + q], M.start_sums[9 + q]));
+  return m;
+}
+
+__device__ __forceinline__ void count_coarse(BatchMarch &M) {
+  M.coarse_steps = M.steps_accepted + M.steps_rejected;
+  M.coarse_newton = M.newton_iterations;
+  M.coarse_vcycles = M.vcycles;
+}
+
+__device__ int solve_end(BatchInst &I, int rc) {
+  BatchMarch &M = I.m;
+  if (!M.counted) count_coarse(M);
+  M.rc = rc;
+  M.t_done = global_ns();
+  return -1;
+}
+
+__device__ int march_start(BatchInst &I, double dt_start) {
+  BatchMarch &M = I.m;
+  M.dt = dt_start;
+  M.dt_prev = -1.0;
+  M.coef_current = 0;
+  M.r_start = 0.0;
+  M.nstep = 0;
+  M.stage = MS_START;
+  return I.ent[M.lvl][E_START_COEF];
+}
+
+__device__ int step_begin(BatchInst &I) {
+  BatchMarch &M = I.m;
+  if (M.nstep >= M.max_steps) return solve_end(I, kMgEreject);
+  M.step_tol = hmax(M.ntol, M.rel * M.r_start);
+  M.r_step = -1.0;
+  M.reason = kMgEnoconv;
+  M.it = 0;
+  for (int q = 0; q < 3; ++q) M.rho_steady[q] = -1.0;
+  if (M.start_valid) {  // start_norms: the step's first residual from the start data
+    const double *S = M.start_sums, c = 1.0 / M.dt;
+    double t2[3];
+    t2[0] = __dadd_rn(__dadd_rn(S[9], __dmul_rn(__dmul_rn(2.0, c), S[12])), __dmul_rn(__dmul_rn(c, c), S[13]));
+    t2[1] = __dadd_rn(__dadd_rn(S[10], __dmul_rn(__dmul_rn(2.0, c), S[14])), __dmul_rn(__dmul_rn(c, c), S[15]));
+    t2[2] = S[11];
+    for (int q = 0; q < 3; ++q) {
+      const double fn = sqrt(S[6 + q]), t = sqrt(t2[q]);
+      M.tn[q] = t;
+      M.rho[q] = fn == 0.0 ? 0.0 : (t > 0.0 ? fn / t : INFINITY);
+    }
+    M.stage = MS_BEGIN_USE;
+    return I.ent[M.lvl][E_BEGIN_USE];
+  }
+  I.dt_inv = M.dt > 0 ? 1.0 / M.dt : 0.0;
+  M.stage = MS_BEGIN;
+  return I.ent[M.lvl][M.coef_current ? E_BEGIN : E_BEGIN_COEF];
+}
+
+__device__ int step_reject(BatchInst &I) {
+  BatchMarch &M = I.m;
+  M.newton_iterations += M.newton_out;
+  M.last_newton = M.newton_out;
+  M.stage = MS_RESTORE;
+  return I.ent[M.lvl][E_RESTORE];
+}
+
+__device__ int march_end(BatchInst &I, int rc) {
+  BatchMarch &M = I.m;
+  if (rc != kMgOk) return solve_end(I, rc);
+  const int l = M.lvl - 1;
+  if (l < 0) return solve_end(I, kMgOk);
+  if (l == 0) {
+    count_coarse(M);
+    M.counted = 1;
+  }
+  M.next_lvl = l;
+  M.stage = MS_PROLONG;
+  return I.ent[l][E_PROLONG];
+}
+
+__device__ int accepted2(BatchInst &I, double r) {
+  BatchMarch &M = I.m;
+  M.coef_current = 1;
+  M.steady_rho = r;
+  M.r_start = r;
+  if (r <= M.tol) return march_end(I, kMgOk);
+  M.dt_prev = M.dt;
+  M.dt = hmin(M.dt * M.dt_growth, M.dt_max);
+  ++M.nstep;
+  return step_begin(I);
+}
+
+__device__ int step_accept(BatchInst &I) {
+  BatchMarch &M = I.m;
+  M.coef_current = 0;
+  M.dt_last = M.dt;
+  M.steps_accepted++;
+  M.sim_time += M.dt;
+  double r = M.r_step;
+  if (r < 0.0) {
+    if (!M.start_valid) {
+      M.stage = MS_ACCSTART;
+      return I.ent[M.lvl][E_START];
+    }
+    r = steady_of_start(M);
+  }
+  return accepted2(I, r);
+}
+
+// The Newton test at iteration M.it (rho, tn current): accept, reject or enter an iteration.
+__device__ int newton_check(BatchInst &I) {
+  BatchMarch &M = I.m;
+  for (int q = 0; q < 3; ++q) M.srho[q] = M.rho[q];
+  const double rmax = hmax(M.rho[0], hmax(M.rho[1], M.rho[2]));
+  if (!(rmax == rmax) || isinf(rmax)) {
+    M.reason = kMgEnonfinite;
+    M.newton_out = M.it;
+    return step_reject(I);
+  }
+  if (rmax <= M.step_tol) {
+    if (M.it > 0) {
+      M.r_step = hmax(M.rho_steady[0], hmax(M.rho_steady[1], M.rho_steady[2]));
+      for (int q = 0; q < 16; ++q) M.start_sums[q] = M.cand[q];
+      M.start_valid = 1;
+    }
+    M.newton_out = M.it;
+    M.newton_iterations += M.it;
+    M.last_newton = M.it;
+    return step_accept(I);
+  }
+  if (M.it == M.max_newton) {
+    M.newton_out = M.it;
+    return step_reject(I);
+  }
+  M.start_valid = 0;
+  const double eta = M.eta_adapt ? hmax(M.eta_p, hmin(0.1, 0.5 * M.step_tol / rmax)) : M.eta_p;
+  I.eta = eta;
+  for (int q = 0; q < 3; ++q) I.w[q] = M.tn[q] > 0.0 ? M.tn[q] : 1.0;
+  I.dt_inv = M.dt > 0 ? 1.0 / M.dt : 0.0;
+  M.stage = MS_NEWTON;
+  return I.ent[M.lvl][E_NEWTON];
+}
+
+// A subprogram of discharge I has ended: the next program counter (-1: the solve has ended).
+__device__ int batch_control(BatchInst &I) {
+  BatchMarch &M = I.m;
+  const double *o = I.dout;
+  switch (M.stage) {
+    case MS_INJECT:
+      if (M.lvl < M.from) {
+        ++M.lvl;
+        return I.ent[M.lvl][E_INJECT];
+      }
+      return march_start(I, M.dt1);
+    case MS_START:
+      for (int q = 0; q < 16; ++q) M.start_sums[q] = o[q];
+      M.start_valid = 1;
+      M.coef_current = 1;
+      M.r_start = steady_of_start(M);
+      return step_begin(I);
+    case MS_BEGIN:
+      for (int q = 0; q < 3; ++q) {
+        M.tn[q] = sqrt(o[3 + q]);
+        M.rho[q] = ratio(o[q], o[3 + q]);
+      }
+      return newton_check(I);
+    case MS_BEGIN_USE:
+      return newton_check(I);
+    case MS_NEWTON: {
+      const SolveCtl *c = I.ctl;
+      const bool ok = (c->r0 == 0.0) || (c->rel <= I.eta);
+      M.vcycles += c->ncyc;
+      if (!ok) { M.newton_out = M.it + 1; M.reason = kMgEnoconv; return step_reject(I); }
+      if (o[17] != 0.0) { M.newton_out = M.it + 1; M.reason = kMgEnonfinite; return step_reject(I); }
+      if (o[16] > M.limit) { M.newton_out = M.it + 1; M.reason = kMgEnoconv; return step_reject(I); }
+      for (int q = 0; q < 3; ++q) {
+        M.tn[q] = sqrt(o[3 + q]);
+        M.rho[q] = ratio(o[q], o[3 + q]);
+        M.rho_steady[q] = ratio(o[6 + q], o[9 + q]);
+      }
+      for (int q = 0; q < 16; ++q) M.cand[q] = o[q];
+      ++M.it;
+      return newton_check(I);
+    }
+    case MS_RESTORE:
+      M.coef_current = 0;
+      M.dt_last = M.dt;
+      M.steps_rejected++;
+      if (M.dt_prev > 0.0 && M.dt > M.dt_prev) {
+        M.dt = M.dt_prev;
+      } else {
+        M.dt *= 0.5;
+        if (M.dt_prev > 0.0) M.dt_prev = hmin(M.dt_prev, M.dt);
+      }
+      ++M.nstep;
+      return step_begin(I);
+    case MS_ACCSTART:
+      for (int q = 0; q < 16; ++q) M.start_sums[q] = o[q];
+      M.start_valid = 1;
+      return accepted2(I, steady_of_start(M));
+    case MS_PROLONG:
+      M.lvl = M.next_lvl;
+      return march_start(I, M.dt_max);
+    default:
+      return solve_end(I, kMgEreject);
+  }
+}
+
+// The finisher of a phase (every thread of its CTA): fold the phase's reduction; thread 0 then
+// takes the V-cycle loop's stopping test or the state machine's next step and publishes the
+// next phase.
+// Returns (thread 0) the program counter of the new phase whose first work item this CTA keeps,
+// or -1 when the solve has ended.
+__device__ int batch_finish(BatchInst &I, const BPhase &ph, int pc, unsigned seq, BatchHead *head, double *red) {
   switch (ph.kind) {
     case BK_NORM0:
     case BK_NORMC: fold_partials<3>(I.partials, ph.nblocks, I.mixed ? 256 : 64, I.dout, red, 0); break;
@@ -2841,7 +3175,7 @@ __device__ void batch_finish(BatchInst &I, const BPhase &ph, int pc, unsigned se
     case BK_RESID: fold_partials<16>(I.partials, ph.nblocks, 64, I.dout, red, 0); break;
     default: break;
   }
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x != 0) return -1;
   int next = pc + 1;
   SolveCtl *c = I.ctl;
   if (ph.kind == BK_NORM0) {  // k_solve_init
@@ -2854,7 +3188,7 @@ __device__ void batch_finish(BatchInst &I, const BPhase &ph, int pc, unsigned se
     c->rel = r0 > 0.0 ? 1.0 : 0.0;
     c->hist[0] = c->rel;
     const bool go = r0 > 0.0 && isfinite(r0) && c->rel > c->eta && c->max_cycles > 0;
-    next = go ? I.loop_pc : I.update_pc;
+    next = go ? I.ent[ph.level][E_NLOOP] : I.ent[ph.level][E_NUPD];
   } else if (ph.kind == BK_NORMC) {  // k_solve_check
     const double rel = weighted_norm(c, I.dout) / c->r0;
     const int n = c->ncyc + 1;
@@ -2862,66 +3196,79 @@ __device__ void batch_finish(BatchInst &I, const BPhase &ph, int pc, unsigned se
     c->rel = rel;
     if (n < kMaxHist) c->hist[n] = rel;
     const bool go = isfinite(rel) && rel > c->eta && n < c->max_cycles;
-    next = go ? I.loop_pc : I.update_pc;
-  } else if (ph.kind == BK_RESID) {
-    for (int q = 0; q < 18; ++q) res->out[q] = I.dout[q];
-    res->r0 = c->r0;
-    res->rel = c->rel;
-    res->ncyc = c->ncyc;
-    res->pad = 0;
+    next = go ? I.ent[ph.level][E_NLOOP] : I.ent[ph.level][E_NUPD];
   }
+  if (I.prog[next].kind == BK_RET) next = batch_control(I);
+  const bool ended = next < 0;
   const unsigned ns = seq + 1;
-  I.ring[ns & 3] = ((unsigned long long)ns << 32) | (unsigned)next;
+  const int nt = ended ? 0 : I.prog[next].ntiles;
+  I.ring[ns & 3] = ring_entry(ns, ended ? 0 : next, nt);
   I.done = 0u;
-  __threadfence();
-  atomicExch(&I.claim, (unsigned long long)ns << 32);
-  if (I.prog[next].ntiles == 0) atomicAdd(&head->ndone, 1);
+  // the finisher keeps the new phase's first work item for itself (count 1)
+  atom_exch_release64(&I.claim, ((unsigned long long)ns << 32) | (nt > 0 ? 1u : 0u));
+  atomicAdd(&head->progress, 1u);
+  if (ended) atomicAdd(&head->ndone, 1);
+  return nt > 0 ? next : -1;
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BatchHead *head, BatchInst *inst, BatchRes *res) {
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BatchHead *head, BatchInst *inst) {
   extern __shared__ __align__(16) unsigned char bsm[];
   double *red = reinterpret_cast<double *>(bsm);
   unsigned char *buf = bsm + kBatchShRed;
-  __shared__ int s_k, s_pc, s_tile, s_last, s_exit;
+  __shared__ int s_k, s_pc, s_tile, s_last, s_exit, s_keep;
   __shared__ unsigned s_seq;
   const int n = head->n;
-  int pref = blockIdx.x % (n > 0 ? n : 1);   // the discharge this CTA looks at first
+  if (threadIdx.x == 0) {
+    atomicMin(&head->t0, global_ns());
+    s_keep = 0;
+  }
+  int own = blockIdx.x % (n > 0 ? n : 1);   // the discharge this CTA worked on last
   for (;;) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !s_keep) {
       s_exit = 0;
       unsigned pause = 32;
+      unsigned seen = *reinterpret_cast<volatile unsigned *>(&head->progress);
       unsigned long long idle0 = global_ns();
       for (unsigned spin = 0;; ++spin) {
+        // first the discharge this CTA worked on last, then the others, ordered largest first
+        // (the longest chains of phases)
+        bool got = false;
+        for (int c = -1; c < n && !got; ++c) {
+          const int k = c < 0 ? own : c;
+          if (c == own) continue;
+          BatchInst &I = inst[k];
+          const unsigned long long w = ld_vol64(&I.claim);
+          const unsigned seq = (unsigned)(w >> 32), cnt = (unsigned)w;
+          const unsigned long long e = ld_vol64(&I.ring[seq & 3]);
+          if ((unsigned)(e >> 32) != seq || cnt >= ring_ntiles(e)) continue;
+          const unsigned long long o = atom_add_acqrel64(&I.claim, 1ull);
+          const unsigned s2 = (unsigned)(o >> 32), c2 = (unsigned)o;
+          const unsigned long long e2 = ld_vol64(&I.ring[s2 & 3]);
+          if ((unsigned)(e2 >> 32) != s2 || c2 >= ring_ntiles(e2)) continue;
+          s_k = k; s_pc = ring_pc(e2); s_tile = (int)c2; s_seq = s2;
+          own = k;
+          got = true;
+        }
+        if (got) break;
         if (*reinterpret_cast<volatile unsigned *>(&head->err) != 0 ||
             *reinterpret_cast<volatile int *>(&head->ndone) >= n) {
           s_exit = 1;
           break;
         }
-        bool got = false;
-        for (int c = 0; c < n && !got; ++c) {
-          const int k = (pref + c) % n;
-          BatchInst &I = inst[k];
-          const unsigned long long w = ld_vol64(&I.claim);
-          const unsigned seq = (unsigned)(w >> 32), cnt = (unsigned)w;
-          const unsigned long long e = ld_vol64(&I.ring[seq & 3]);
-          if ((unsigned)(e >> 32) != seq || cnt >= (unsigned)I.prog[(unsigned)e].ntiles) continue;
-          const unsigned long long o = atomicAdd(&I.claim, 1ull);
-          __threadfence();
-          const unsigned s2 = (unsigned)(o >> 32), c2 = (unsigned)o;
-          const unsigned long long e2 = ld_vol64(&I.ring[s2 & 3]);
-          if ((unsigned)(e2 >> 32) != s2 || c2 >= (unsigned)I.prog[(unsigned)e2].ntiles) continue;
-          s_k = k; s_pc = (int)(unsigned)e2; s_tile = (int)c2; s_seq = s2;
-          pref = k;
-          got = true;
-        }
-        if (got) break;
-        if ((spin & 15) == 15 && global_ns() - idle0 > kBatchIdleNs) {
-          atomicExch(&head->err, 1u);
-          s_exit = 1;
-          break;
+        if ((spin & 15) == 15) {
+          const unsigned now_seen = *reinterpret_cast<volatile unsigned *>(&head->progress);
+          const unsigned long long now = global_ns();
+          if (now_seen != seen) {
+            seen = now_seen;
+            idle0 = now;
+          } else if (now - idle0 > kBatchIdleNs) {
+            atomicExch(&head->err, 1u);
+            s_exit = 1;
+            break;
+          }
         }
         __nanosleep(pause);
-        if (pause < 2048) pause <<= 1;
+        if (pause < 512) pause <<= 1;
       }
     }
     __syncthreads();
@@ -2933,35 +3280,42 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BatchHead *head, Bat
     batch_tile(I, ph, tile, red, buf);
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned d = atomicAdd(&I.done, 1u);
+      const unsigned d = atom_add_acqrel32(&I.done, 1u);
       s_last = (d + 1 == (unsigned)ph.ntiles);
-      if (s_last) __threadfence();
+      s_keep = 0;
     }
     __syncthreads();
-    if (s_last) batch_finish(I, ph, pc, seq, res + k, head, red);
+    if (s_last) {
+      const int next = batch_finish(I, ph, pc, seq, head, red);
+      if (threadIdx.x == 0 && next >= 0) {  // this CTA runs the new phase's first work item
+        s_k = k; s_pc = next; s_tile = 0; s_seq = seq + 1;
+        s_keep = 1;
+        s_exit = 0;
+      }
+    }
     __syncthreads();
   }
 }
 
 int batch_grid() {
-  static int cached = -1;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lk(mu);
-  if (cached >= 0) return cached;
-  int dev = 0, sms = 0, occ = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, kBatchSmem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  cached = sms * occ;
+  static std::once_flag once;
+  static int cached = 0;
+  std::call_once(once, []() {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, kBatchSmem) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cached = sms * occ;
+  });
   return cached;
 }
 
-cudaError_t launch_batch(BatchHead *head, BatchInst *inst, BatchRes *res, int grid, cudaStream_t st) {
-  k_batch<<<grid, kBatchThreads, kBatchSmem, st>>>(head, inst, res);
+cudaError_t launch_batch(BatchHead *head, BatchInst *inst, int grid, cudaStream_t st) {
+  k_batch<<<grid, kBatchThreads, kBatchSmem, st>>>(head, inst);
   count_launch();
   return cudaGetLastError();
 }

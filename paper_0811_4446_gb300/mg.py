@@ -95,6 +95,7 @@ SIGNATURES = {
     "mg_time_smoother": (_i, [_vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "mg_solve_steady_batch": (_i, [ctypes.POINTER(_vp), _i, _d, _i, _vp, _vp]),
     "mg_autotune": (_i, [_vp, _vp]),
+    "mg_autotune_batch": (_i, [ctypes.POINTER(_vp), _i, _d, ctypes.POINTER(_i)]),
     "mg_solve_steady_guess": (_i, [_vp, _vp, _vp, _vp, _i, _d, ctypes.POINTER(mg_stats), ctypes.POINTER(_i)]),
     "mg_num_levels": (_i, [_vp]),
     "mg_residual_noalloc": (_i, [ctypes.POINTER(mg_grid), ctypes.POINTER(mg_params), _vp, _vp, _vp, _vp, _vp, _vp,
@@ -351,6 +352,19 @@ def solve_steady_batch(solvers, tol: float, workers: int = 0):
     rcs = np.zeros(n, dtype=np.int32)
     rc = lib.mg_solve_steady_batch(hs, n, float(tol), int(workers), ms.ctypes.data, rcs.ctypes.data)
     return rc, ms, rcs
+
+
+def autotune_batch(solvers, tol: float) -> int:
+    """Work-item size of the persistent batched form tuned on these discharges (see
+    mg_autotune_batch in include/mg.h); returns the size kept."""
+    lib = load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.h for s in solvers])
+    g = ctypes.c_int(0)
+    rc = lib.mg_autotune_batch(hs, n, float(tol), ctypes.byref(g))
+    if rc != MG_OK:
+        raise MGError(rc, "mg_autotune_batch failed")
+    return g.value
 
 
 def residual_noalloc(nr: int, nz: int, R: float, z, params: mg_params, state, old_state, sources, dt: float,
