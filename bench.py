@@ -785,6 +785,7 @@ def measure_forms(args, dev, peaks):
         rows = []
         variants = (("continuation", None, None),
                     ("continuation_ramp_1e-3", None, dict(dt_max=1e-3)),
+                    ("guess_fine_ramp_1e-3", dict(guess_level=0, guess_dt_max=1e-3), None),
                     ("guess_coarse_ramp_1e-3", dict(guess_level=1, guess_dt_max=1e-3), None),
                     ("guess_coarse_capped", dict(guess_level=1, guess_dt_max=1e-6), None),
                     ("guess_fine_capped", dict(guess_level=0, guess_dt_max=1e-6), None))
@@ -796,14 +797,15 @@ def measure_forms(args, dev, peaks):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 if gkw is None:
-                    rc, _ = sv.solve_steady(TOL)
+                    rc, st = sv.solve_steady(TOL)
                     fb = False
                 else:
                     y = net.forward(unet.features(dd)[None])[0]
-                    rc, _, fb = sv.solve_steady_guess(*unet.state_from_output(y, dd.V_cathode), TOL)
+                    rc, st, fb = sv.solve_steady_guess(*unet.state_from_output(y, dd.V_cathode), TOL)
                 torch.cuda.synchronize()
                 row[name] = (time.perf_counter() - t0) * 1e3
                 row[name + "_fallback"] = fb
+                row[name + "_work"] = (st["newton_iterations"], st["vcycles"])
                 if rc != mg.MG_OK:
                     raise RuntimeError("learned-guess comparison failed")
                 sv.close()
@@ -814,8 +816,13 @@ def measure_forms(args, dev, peaks):
         for name, _, _ in variants:
             t = np.array([r[name] for r in rows])
             lg[name + "_ms_median"] = float(np.median(t))
+            lg[name + "_newton_vcycles_total"] = [int(sum(r[name + "_work"][0] for r in rows)),
+                                                 int(sum(r[name + "_work"][1] for r in rows))]
             if name != "continuation":
                 lg["gain_" + name] = float(np.median(cont / t))
+        best_plain = np.array([r["continuation_ramp_1e-3"] for r in rows])
+        lg["gain_guess_fine_ramp_over_best_plain_schedule"] = float(
+            np.median(best_plain / np.array([r["guess_fine_ramp_1e-3"] for r in rows])))
         out["learned_guess_257"] = lg
         net.close()
     # tensor-core convolutions of the network: forward and training step on a batch of 16 at 257^2

@@ -170,7 +170,7 @@ typedef struct mg_state mg_state;
  * V_cathode = -200, V_anode = 0, nu1 = nu2 = 4, coarsest = 2, eta = 1e-3,
  * max_newton = 10, max_vcycles = 60, max_steps = 400, dt1 = 1e-9,
  * dt_growth = 5, dt_max = 1e-6, corr_limit_frac = 0.5, precision MG_FP64, n0 = 1e14,
- * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 1, guess_dt_start = 1e-8,
+ * use_graphs = 1, fused_sweep = 1, guess_dt_max = 1e-3, guess_level = 0, guess_dt_start = 1e-8,
  * coarse_kernel_n = 16,
  * coarse_kernel_ctas = 1, coarse_kernel_threads = 512, eta_adapt = 1, nu_coarse_n = 64,
  * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels

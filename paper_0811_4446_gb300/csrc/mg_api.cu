@@ -1213,7 +1213,7 @@ void mg_params_default(mg_params *p) {
   p->use_graphs = 1;
   p->fused_sweep = 1;
   p->guess_dt_max = 1e-3;
-  p->guess_level = 1;
+  p->guess_level = 0;
   p->guess_dt_start = 1e-8;
   p->eta_adapt = 1;
   p->nu_coarse_n = 64; p->nu_coarse1 = 2; p->nu_coarse2 = 2;

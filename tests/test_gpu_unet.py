@@ -59,6 +59,11 @@ def test_forward_matches_oracle(un):
     yo = ou.forward(po, xo).permute(0, 2, 3, 1).numpy()
     rel = np.linalg.norm(y - yo) / np.linalg.norm(yo)
     assert rel <= 3e-2, rel
+    # element by element: every output within 2 % of its channel's scale (BF16 rounds each of
+    # 12 layers to 2^-9 relative; measured at most 0.7 %)
+    for c in range(3):
+        scale = np.abs(yo[..., c]).max()
+        assert np.abs(y[..., c] - yo[..., c]).max() <= 2e-2 * scale, c
 
 
 def test_gradients_match_oracle(un):
@@ -117,13 +122,14 @@ def test_guess_then_refine_small_grid(un):
         ref = mg.from_discharge(d, precision=mg.MG_MIXED)
         assert ref.solve_steady(1e-8)[0] == mg.MG_OK
         ur = np.stack(ref.get_state())
+        # the two paths meet to within the spread the 1e-8 residual tolerance allows
         for q in range(3):
-            assert np.abs(ug[q] - ur[q]).max() <= 1e-6 * np.abs(ur[q]).max(), q
+            assert np.abs(ug[q] - ur[q]).max() <= 1e-5 * np.abs(ur[q]).max(), q
         g = Grid(d.nr, d.nz, d.R, d.z)
         phys = disc.Physics(V_cathode=d.V_cathode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p,
                             pressure_factor=d.pressure_factor)
         F, Tm = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
-        assert disc.rho(F, Tm).max() <= 1.05e-8
+        assert disc.rho(F, Tm).max() <= 1e-8 * (1 + 1e-9)
 
 
 def test_bad_guess_falls_back_to_continuation(un):
@@ -142,18 +148,101 @@ def test_bad_guess_falls_back_to_continuation(un):
         assert np.abs(a[q] - b[q]).max() <= 1e-6 * np.abs(b[q]).max(), (q, fb)
 
 
-@pytest.mark.parametrize("level,gdt", [(0, 1e-6), (1, 1e-6), (1, 1e-3)])
-def test_trained_network_guess_at_257(un, level, gdt):
-    """With the committed weights (trained on the device by paper_0811_4446_gb300.train_guess):
-    on held-out 257 x 257 instances the guess-then-refine solve reaches rho <= 1e-8 at the
-    continuation's steady state; the time ratio against the plain 129 -> 257 continuation is
-    reported (the gain of the network, < 1 means slower)."""
-    from paper_0811_4446_gb300 import mg
+def _steady(un, mg, d, guess=None, tol=1e-8, **kw):
+    """(state, stats, used_fallback) of a mixed-precision steady solve, from the network's guess
+    when one is given."""
+    s = mg.from_discharge(d, precision=mg.MG_MIXED, **kw)
+    if guess is None:
+        rc, st = s.solve_steady(tol)
+        fb = False
+    else:
+        rc, st, fb = s.solve_steady_guess(*guess, tol)
+    assert rc == mg.MG_OK
+    u = np.stack(s.get_state())
+    s.close()
+    return u, st, fb
+
+
+def _net_guess(un, net, d):
+    y = net.forward(un.features(d)[None])[0]
+    return un.state_from_output(y, d.V_cathode)
+
+
+@pytest.fixture(scope="module")
+def trained(un):
     w = un.load_weights()
     if w is None:
         pytest.skip("no trained weights committed")
     net = un.UNet(1, 256)
     net.set_params(w)
+    yield net
+    net.close()
+
+
+def test_trained_network_gain_at_257(un, trained):
+    """What the trained network (committed weights, trained on the device) gains on held-out
+    257 x 257 instances (seeds 9000-9007), counted in the solver's own work units, which do not
+    depend on timing: the fine grid marched from the guess with the growing Delta-t ramp (x5 per
+    step up to 1 ms) needs fewer Newton iterations and fewer V-cycles in total than the plain
+    129 -> 257 continuation AND than the continuation with the same growing ramp (the best
+    schedule without the network), with no fallback.  Every guess-path result is a steady
+    state of the same discrete system: the oracle's residual <= 1e-8, densities non-negative up
+    to the tolerance (min n >= -1e-6 max n, as for the continuation's own result), and the
+    continuation's state to 1e-5 relative per field (the spread the 1e-8 residual tolerance
+    allows between two paths to one state; test_trained_network_paths_meet below shows it
+    shrinking with the tolerance)."""
+    from paper_0811_4446_gb300 import mg
+    tot = {"guess": [0, 0], "cont": [0, 0], "ramp": [0, 0]}
+    for seed in range(9000, 9008):
+        d = un.guess_discharge(seed, 256)
+        ug, sg, fb = _steady(un, mg, d, _net_guess(un, trained, d), guess_level=0, guess_dt_max=1e-3)
+        assert not fb, seed
+        uc, sc, _ = _steady(un, mg, d)
+        _, sr, _ = _steady(un, mg, d, dt_max=1e-3)
+        for key, st in (("guess", sg), ("cont", sc), ("ramp", sr)):
+            tot[key][0] += st["newton_iterations"]
+            tot[key][1] += st["vcycles"]
+        g = Grid(d.nr, d.nz, d.R, d.z)
+        phys = disc.Physics(V_cathode=d.V_cathode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p,
+                            pressure_factor=d.pressure_factor)
+        F, Tm = disc.residual(g, ug, None, d.S_e, d.S_p, None, phys, with_terms=True)
+        assert disc.rho(F, Tm).max() <= 1e-8 * (1 + 1e-9), seed
+        for q in (0, 1):
+            assert ug[q].min() >= -1e-6 * ug[q].max(), (seed, q)
+        for q in range(3):
+            assert np.abs(ug[q] - uc[q]).max() <= 1e-5 * np.abs(uc[q]).max(), (seed, q)
+    print(f"Newton iterations / V-cycles over 8 held-out instances: guess {tot['guess']}, "
+          f"continuation {tot['cont']}, continuation with the growing ramp {tot['ramp']}")
+    for ref in ("cont", "ramp"):
+        assert tot["guess"][0] < 0.75 * tot[ref][0], (ref, tot)
+        assert tot["guess"][1] < 0.75 * tot[ref][1], (ref, tot)
+
+
+def test_trained_network_paths_meet(un, trained):
+    """The guess path and the continuation end in one steady state, not on two branches: their
+    difference falls with the residual tolerance (1e-8 -> 1e-10: from up to 4e-6 to about 1e-8
+    relative per field), as two approximations of one solution do."""
+    from paper_0811_4446_gb300 import mg
+    for seed in (9000, 9001):
+        d = un.guess_discharge(seed, 256)
+        guess = _net_guess(un, trained, d)
+        diffs = {}
+        for tol in (1e-8, 1e-10):
+            ug, _, fb = _steady(un, mg, d, guess, tol, guess_level=0, guess_dt_max=1e-3)
+            uc, _, _ = _steady(un, mg, d, None, tol)
+            diffs[tol] = max(np.abs(ug[q] - uc[q]).max() / np.abs(uc[q]).max() for q in range(3))
+        assert diffs[1e-10] <= 1e-7, (seed, diffs)
+        assert diffs[1e-10] <= 0.1 * diffs[1e-8], (seed, diffs)
+
+
+@pytest.mark.parametrize("level,gdt", [(0, 1e-6), (1, 1e-6), (1, 1e-3)])
+def test_trained_network_guess_at_257(un, trained, level, gdt):
+    """The other guess variants (the fine grid with the capped ramp, the guess injected into the
+    coarse march with the capped and the growing ramp) on held-out 257 x 257 instances: each
+    reaches the oracle's residual <= 1e-8 at the continuation's steady state (1e-5 relative per
+    field, as above); the time ratio against the plain continuation is reported."""
+    from paper_0811_4446_gb300 import mg
+    net = trained
     t_guess, t_cont, fallbacks = [], [], 0
     for seed in range(9000, 9004):
         d = un.guess_discharge(seed, 256)
@@ -171,16 +260,13 @@ def test_trained_network_guess_at_257(un, level, gdt):
         t2 = time.perf_counter()
         assert rc2 == mg.MG_OK
         a, b = np.stack(s.get_state()), np.stack(c.get_state())
-        # the guess path must end in a steady state (checked with the oracle's residual); it
-        # need not be the continuation's: for some instances of this family the two paths reach
-        # different steady states, so their difference is only reported
-        diff = [float(np.abs(a[q] - b[q]).max() / np.abs(b[q]).max()) for q in range(3)]
-        print(f"seed {seed}: max relative difference to the continuation's steady state {diff}")
+        for q in range(3):
+            assert np.abs(a[q] - b[q]).max() <= 1e-5 * np.abs(b[q]).max(), (seed, q)
         g = Grid(d.nr, d.nz, d.R, d.z)
         phys = disc.Physics(V_cathode=d.V_cathode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p,
                             pressure_factor=d.pressure_factor)
         F, Tm = disc.residual(g, a, None, d.S_e, d.S_p, None, phys, with_terms=True)
-        assert disc.rho(F, Tm).max() <= 1.05e-8
+        assert disc.rho(F, Tm).max() <= 1e-8 * (1 + 1e-9)
         t_guess.append(t1 - t0)
         t_cont.append(t2 - t1)
         fallbacks += int(fb)
