@@ -138,15 +138,6 @@ typedef struct mg_params {
                              system solved exactly, robust to strong z-coupling) on every level
                              (the coarse levels then run as separate launches, no coarse-cycle
                              kernel) */
-  int32_t smooth_phase;   /* levels with at most this many intervals per side run each pre- or
-                             post-smoothing phase (all its red-black half sweeps) as one launch
-                             with barriers between the half sweeps (one thread-block cluster with
-                             the hardware cluster barrier up to 65^2 nodes, a cooperative launch
-                             with a bounded grid barrier above) instead of one launch per half
-                             sweep (0: off; 0..1024).  Results
-                             are bit for bit those of the half-sweep launches.  On GB300 it is
-                             slower: a grid barrier costs more than a kernel boundary inside a
-                             graph with programmatic dependent launch, hence off by default */
 } mg_params;
 
 /* Per-call statistics. */
@@ -176,8 +167,7 @@ typedef struct mg_state mg_state;
  * nu_coarse1 = nu_coarse2 = 2, nu_tiny_n = 8, nu_tiny1 = nu_tiny2 = 1 (V(4,4) smoothing on levels
  * larger than 65^2, V(2,2) from 65^2 to 17^2, V(1,1) from 9^2 down),
  * chain_from = 1 (the two-level 129^2 -> 257^2 continuation), pdl = 9 (smoothers and the coarse-cycle kernel), wall_dirichlet = 0,
- * newton_tol_rel = 0.1, full_jacobian = 0, max_corrections = 20, line_smoother = 0,
- * smooth_phase = 0.
+ * newton_tol_rel = 0.1, full_jacobian = 0, max_corrections = 20, line_smoother = 0.
  *
  * precision = MG_MIXED: every linear solve of eq. 14 is an FP64 defect-correction loop whose
  * corrections come from FP32 V-cycles (FP32 smoother, residual, restriction, prolongation on
@@ -269,8 +259,8 @@ int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const
  *     whichever discharge has work open; a discharge's phases run in the order of the
  *     single-discharge path and give the same results bit for bit.  Needs the point smoother,
  *     the Picard Jacobian, the coarse-cycle kernel (coarse_kernel_n > 0) at or below the
- *     continuation's first grid, a coarsest level of at most 48 unknowns and smooth_phase = 0;
- *     otherwise the call falls back to 16 host threads.  ms_out[k]: from the batch's start to
+ *     continuation's first grid and a coarsest level of at most 48 unknowns; otherwise the call
+ *     falls back to 16 host threads.  ms_out[k]: from the batch's start to
  *     discharge k's solve returning.  A work list that stops making progress (no work item
  *     claimed for 5 s) ends the launch with MG_ETIMEOUT.
  *   workers > 0: the comparison form: `workers` host threads take instances from a shared queue
@@ -318,41 +308,6 @@ void mg_reset_stats(mg_state *s);
 
 /* Number of CUDA kernels this library has launched (all states, process-wide). */
 uint64_t mg_kernel_launches(void);
-
-/* Kernel timing for measurement: between mg_profile_begin and mg_profile_end every launch
- * of `kernel` on multigrid level `level` (0 = finest) is bracketed by CUDA events recorded on
- * the state's stream (up to 16384 launches).  mg_profile_end synchronises the stream and
- * returns the number of bracketed launches and their summed device time in milliseconds.
- * MG_PROF_RESTRICT brackets the fused linear-residual + restriction launch from `level`,
- * MG_PROF_LINRES the residual-norm launch of each cycle of a linear solve rooted at `level`.
- * MG_PROF_RESIDUAL brackets the face-coefficient and residual launches of a residual
- * evaluation on `level`; MG_PROF_COEF the hierarchy set-up below a Newton iteration on root
- * level `level` (injection, coarse-level coefficients and the diagonal factors of every level,
- * one launch each); MG_PROF_COARSE the launches of the coarse-cycle kernel that starts on
- * `level`; MG_PROF_COARSE_FACTOR the coarsest-level inverse below a Newton iteration on root
- * level `level`. */
-enum { MG_PROF_SMOOTH = 1, MG_PROF_LINRES = 2, MG_PROF_COEF = 3, MG_PROF_RESIDUAL = 4,
-       MG_PROF_RESTRICT = 5, MG_PROF_PROLONG = 6, MG_PROF_COARSE = 7, MG_PROF_COARSE_FACTOR = 8 };
-int mg_profile_begin(mg_state *s, int kernel, int level);
-int mg_profile_end(mg_state *s, int64_t *launches, double *total_ms);
-
-/* Measured FP64 fused-multiply-add throughput of the current device in GFLOP/s (2 flops per
- * FMA), from a kernel of independent FMA chains on every SM; used as the ALU roofline of the
- * FP64 path.  Returns a negative value on a CUDA error. */
-double mg_probe_fp64_gflops(void *stream);
-
-/* Smoother timing as the V-cycle graphs run it: `sweeps` red-black sweeps of level `level`
- * (0 = finest, below the last level) in the precision view `precision` (0 FP64, 1 the FP32
- * view of the mixed form), issued exactly as a V-cycle issues them (the level's launch shape,
- * half or fused sweeps, programmatic dependent launch), are captured into one CUDA graph on
- * the state's stream and replayed twice; the second replay is timed with CUDA events.
- * *us_per_launch receives its device time divided by the number of launches,
- * *launches_per_sweep (may be NULL) 2 for half sweeps, 1 for fused ones.  Only the level's
- * correction buffers are written, and they are zeroed afterwards; the solution state is not
- * touched.  Synchronises the stream.  MG_EINVAL on a bad level, precision (1 needs the mixed
- * form) or sweep count (1 .. 4096); MG_ECUDA on a CUDA error. */
-int mg_time_smoother(mg_state *s, int level, int precision, int sweeps, double *us_per_launch,
-                     int *launches_per_sweep);
 
 /* Allocation-free residual norms.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory (code running inside another framework's memory

@@ -52,7 +52,14 @@ int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where);
 int mg_unet_loss_grad(mg_unet *n, const float *x, const float *t, int B, double *loss, int where);
 int mg_unet_get_grads(mg_unet *n, float *g, int where);
 
-/* Tensor-core path of the convolutions.
+/* Tensor-core path of the convolutions: a parity and measurement reference, not a choice a
+ * user makes.  The network runs on path 3 (the default), which assigns one kernel to each
+ * layer shape: the halo-load tcgen05 forward (stride-1 layers whose weights fit in 72 KB), the
+ * TMA-tile tcgen05 forward (the other 3x3 layers with 32-channel input parts), the gathering
+ * tcgen05 kernel (the 8-channel first layer and every data gradient), the FP32 CUDA-core head
+ * and the weight gradient below.  Paths 0-2 keep the earlier kernels of those layers so that
+ * the tests can compare each layer's kernel with the one it replaced (same operands, another
+ * order of the sums) and the benchmark can report what each replacement gained:
  *   0 = mma.sync for every convolution.
  *   1 = tcgen05.mma with the accumulator in tensor memory for the forward and data-gradient
  *       convolutions whose output width is a multiple of 16 (<= 256), operands gathered by

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/mg.h"
+#include "../../include/mg_debug.h"
 #include "mg_impl.cuh"
 
 using namespace mgk;
@@ -74,7 +75,6 @@ struct mg_state {
   bool start_valid = false;   // fss and start_sums describe the current state of the march level
   double *line_scr;           // z-line smoother: 12 planes of (nz + 1) x (nr + 2) / 2 of the finest level
   int *flag;
-  unsigned *gsync;            // grid barrier of the smoothing-phase launches: 4 unsigned per level
   double *table_d;
   mg_stats stats;
   std::string err;
@@ -218,7 +218,6 @@ void carve(Carver &c, mg_state *s, int nlev, const int *lnr, const int *lnz, int
   s->rs = c.take<double>(kMaxCoarse);
   s->cs = c.take<double>(kMaxCoarse);
   s->flag = c.take<int>(4);
-  s->gsync = c.take<unsigned>(4 * kMaxLevels);
   s->ctl = c.take<SolveCtl>(1);
   s->cset64 = c.take<CoarseSet<double>>(1);
   s->cset32 = c.take<CoarseSet<float>>(1);
@@ -413,11 +412,6 @@ int smooth_sweeps(mg_state *s, int l, int nu, cudaStream_t st) {
     return MG_OK;
   }
   const LevelT<T> &b = view<T>(s->lv[l]);
-  if (s->prm.smooth_phase > 0 && nu > 0 && std::max(s->lv[l].nr, s->lv[l].nz) <= s->prm.smooth_phase) {
-    ProfScope ps(s, MG_PROF_SMOOTH, l);
-    CK(launch_smooth_phase<T>(b, nu, s->gsync + 4 * l, st));
-    return MG_OK;
-  }
   int rc;
   if (!s->prm.fused_sweep || !level_fused<T>(s->lv[l])) {
     for (int k = 0; k < nu; ++k)
@@ -706,12 +700,12 @@ BPhase batch_phase(int kind, int level, int arg, int nblocks, int per_round, int
 
 // Whether a state's steady solve can run in the batched launch: the point smoother, the Picard
 // Jacobian, the coarse-cycle kernel at or below every root level of the continuation, a
-// coarsest level of at most 48 unknowns (shared-memory inverse), no cooperative phases, and a
-// continuation that mg_solve_steady accepts.
+// coarsest level of at most 48 unknowns (shared-memory inverse), and a continuation that
+// mg_solve_steady accepts.
 bool batchable(const mg_state *s) {
   const LevelBuf &c = s->lv[s->nlev - 1];
   return s->nlev >= 2 && s->nlev <= kMaxLevelSet && s->prm.chain_from >= 1 && s->prm.chain_from < s->nlev &&
-         !s->prm.line_smoother && !s->prm.full_jacobian && s->prm.smooth_phase == 0 && s->cc_from > 0 &&
+         !s->prm.line_smoother && !s->prm.full_jacobian && s->cc_from > 0 &&
          s->cc_from < s->nlev - 1 && s->prm.chain_from <= s->cc_from && 3 * c.L.ni * (c.nz - 1) <= 48 &&
          s->prof_kernel == 0;
 }
@@ -1225,7 +1219,6 @@ void mg_params_default(mg_params *p) {
   p->full_jacobian = 0;
   p->max_corrections = 20;
   p->line_smoother = 0;
-  p->smooth_phase = 0;
   p->coarse_kernel_n = 16;
   p->coarse_kernel_ctas = 1;
   p->coarse_kernel_threads = 512;
@@ -1249,7 +1242,6 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
   if (p->full_jacobian != 0 && p->full_jacobian != 1) { *why = "full_jacobian must be 0 or 1"; return MG_EINVAL; }
   if (p->max_corrections < 1 || p->max_corrections > 100) { *why = "max_corrections must be in 1..100"; return MG_EINVAL; }
   if (p->line_smoother != 0 && p->line_smoother != 1) { *why = "line_smoother must be 0 or 1"; return MG_EINVAL; }
-  if (p->smooth_phase < 0 || p->smooth_phase > 1024) { *why = "smooth_phase must be in 0..1024"; return MG_EINVAL; }
   if (p->pdl < 0 || p->pdl > PDL_ALL) { *why = "pdl: a combination of the PDL kernel-kind bits"; return MG_EINVAL; }
   if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
     *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";

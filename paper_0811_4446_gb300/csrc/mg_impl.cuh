@@ -240,10 +240,6 @@ cudaError_t launch_residual(const Level &L, const StateView &sv, const Transport
                             double *out6, cudaStream_t st);
 template <typename T>
 cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx = 32, int by = 2);
-// nu red-black sweeps in one cooperative launch with bounded grid barriers between the half
-// sweeps (bar: 3 unsigned of the level, zero-initialised)
-template <typename T>
-cudaError_t launch_smooth_phase(const LevelT<T> &L, int nu, unsigned *bar, cudaStream_t st);
 template <typename T>
 cudaError_t launch_sweep(const LevelT<T> &L, const SweepIO<T> &io, int shape, cudaStream_t st);
 // Coarse part of a V-cycle in one launch of a cluster of `cluster` CTAs (1..8) x `threads`.

@@ -824,133 +824,6 @@ cudaError_t launch_smooth(const LevelT<T> &L, int color, cudaStream_t st, int bx
 template cudaError_t launch_smooth<double>(const LevelT<double> &, int, cudaStream_t, int, int);
 template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream_t, int, int);
 
-// Grid barrier of a cooperative launch (every CTA resident): bar[0] counts arrivals, bar[1] is
-// the generation; the last CTA to arrive resets the count and advances the generation, the
-// others poll the generation.  Bounded: false after kGridWaitLimit polls.
-constexpr long kGridWaitLimit = 1L << 21;
-__device__ bool grid_barrier(unsigned *bar) {
-  __shared__ int ok_sh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *vgen = bar + 1;
-    const unsigned g = *vgen;  // read before arriving: the generation cannot move before that
-    __threadfence();
-    int ok = 1;
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      ok = 0;
-      for (long it = 0; it < kGridWaitLimit; ++it)
-        if (*vgen != g) {
-          ok = 1;
-          break;
-        }
-    }
-    __threadfence();
-    ok_sh = ok;
-  }
-  __syncthreads();
-  return ok_sh != 0;
-}
-
-// A whole pre- or post-smoothing phase of a small level (nu red-black sweeps) in one launch: the
-// half sweeps are separated by a barrier, the corrections of the other colour are read through
-// L2 (other CTAs of this launch wrote them), the arithmetic is smooth_node's.
-//   CLUSTER: the whole grid is one thread-block cluster (at most 8 CTAs) and the barrier is the
-//     hardware cluster barrier (release / acquire at cluster scope); launched with programmatic
-//     dependent launch like the half-sweep kernels, so the first half sweep waits for the
-//     previous kernel after requesting its operator data.
-//   otherwise: a cooperative launch with the bounded software grid barrier.  A barrier that gives
-//     up marks the level's barrier as broken (bar[2]; later launches on it stop at once) and
-//     writes NaN into the V correction of the CTA's nodes, which the Newton update's non-finite
-//     check then reports.
-template <typename T, bool CLUSTER>
-__global__ void __launch_bounds__(256, 1) k_smooth_phase(LevelT<T> L, int nu, unsigned *bar) {
-  pdl_launch_dependents();
-  const int slots = colour_slots(L.ni, L.nz);
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  bool ok = CLUSTER || *reinterpret_cast<volatile unsigned *>(bar + 2) == 0;
-  for (int h = 0; h < 2 * nu && ok; ++h) {
-    for (int t = t0; t < slots; t += stride) {
-      int i, j;
-      if (!colour_node(t, L.ni, L.nz, h & 1, i, j)) continue;
-      if (CLUSTER && h == 0) smooth_node<T, true, true>(L, i, j);
-      else smooth_node<T, false, true>(L, i, j);
-    }
-    if (CLUSTER && h == 0) pdl_wait();  // every thread, with or without a node, after the previous kernel
-    if (h + 1 < 2 * nu) {
-      if (CLUSTER) cooperative_groups::this_cluster().sync();
-      else ok = grid_barrier(bar);
-    }
-  }
-  if (!CLUSTER && !ok) {
-    if (threadIdx.x == 0) atomicExch(bar + 2, 1u);
-    int i, j;
-    if (t0 < slots && colour_node(t0, L.ni, L.nz, 0, i, j)) L.du[NV][split_nb(L.P, i, j).self] = T(NAN);
-  }
-}
-
-constexpr int kPhaseClusterMax = 8;      // portable cluster size
-constexpr int kPhaseClusterSlots = 2304; // colour slots up to which a level runs as one cluster (65^2: 2080)
-
-template <typename T>
-int smooth_phase_grid(const LevelT<T> &L, int block) {
-  static int sms = 0, occ = 0;
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_smooth_phase<T, false>, 128, 0) != cudaSuccess)
-      sms = 0;
-  }
-  if (sms <= 0 || occ <= 0) return 0;
-  const int need = (colour_slots(L.ni, L.nz) + block - 1) / block;
-  return std::max(1, std::min(need, sms * occ));
-}
-
-template <typename T>
-cudaError_t launch_smooth_phase(const LevelT<T> &L, int nu, unsigned *bar, cudaStream_t st) {
-  const int slots = colour_slots(L.ni, L.nz);
-  const bool cluster = slots <= kPhaseClusterSlots;
-  const int block = cluster ? (slots > 1024 ? 256 : 128) : 128;
-  const int g = cluster ? std::min(kPhaseClusterMax, (slots + block - 1) / block) : smooth_phase_grid(L, block);
-  if (g <= 0) return cudaErrorInvalidConfiguration;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(g);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute at[2];
-  int na = 0;
-  cudaError_t e;
-  if (cluster) {
-    at[na].id = cudaLaunchAttributeClusterDimension;
-    at[na].val.clusterDim.x = (unsigned)g;
-    at[na].val.clusterDim.y = 1;
-    at[na].val.clusterDim.z = 1;
-    ++na;
-    if (L.pdl & PDL_SMOOTH) {
-      at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      at[na].val.programmaticStreamSerializationAllowed = 1;
-      ++na;
-    }
-    cfg.attrs = at;
-    cfg.numAttrs = na;
-    e = cudaLaunchKernelEx(&cfg, k_smooth_phase<T, true>, L, nu, bar);
-  } else {
-    at[na].id = cudaLaunchAttributeCooperative;
-    at[na].val.cooperative = 1;
-    ++na;
-    cfg.attrs = at;
-    cfg.numAttrs = na;
-    e = cudaLaunchKernelEx(&cfg, k_smooth_phase<T, false>, L, nu, bar);
-  }
-  count_launch();
-  return e;
-}
-template cudaError_t launch_smooth_phase<double>(const LevelT<double> &, int, unsigned *, cudaStream_t);
-template cudaError_t launch_smooth_phase<float>(const LevelT<float> &, int, unsigned *, cudaStream_t);
 
 // ------------------------------------------------------------------------------------------
 // z-line Gauss-Seidel, zebra order (even columns, then odd): one thread per column of the
@@ -1148,11 +1021,13 @@ cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st)
   if (n <= 0) return cudaSuccess;
   if (L.nz <= 512 && (L.nz & (L.nz - 1)) == 0) {
     const size_t smem = (size_t)21 * L.nz * sizeof(T);
-    static bool raised = false;  // the 512-row FP64 case needs 86 KB of dynamic shared memory
-    if (!raised && smem > 48 * 1024) {
-      cudaFuncSetAttribute(k_zline_pcr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 21 * 512 * (int)sizeof(T));
-      raised = true;
-    }
+    // the 512-row FP64 case needs 86 KB of dynamic shared memory: the limit is raised once per
+    // instantiation (call_once: the batched host-thread form launches from several threads)
+    static std::once_flag raised;
+    if (smem > 48 * 1024)
+      std::call_once(raised, []() {
+        cudaFuncSetAttribute(k_zline_pcr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 21 * 512 * (int)sizeof(T));
+      });
     k_zline_pcr<T><<<n, L.nz, smem, st>>>(L, color);
   } else {
     const int cstride = (L.nr + 2) / 2;

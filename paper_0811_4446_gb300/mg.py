@@ -48,8 +48,7 @@ class mg_params(ctypes.Structure):
                 ("nu_tiny_n", ctypes.c_int32), ("nu_tiny1", ctypes.c_int32), ("nu_tiny2", ctypes.c_int32),
                 ("chain_from", ctypes.c_int32), ("pdl", ctypes.c_int32), ("wall_dirichlet", ctypes.c_int32),
                 ("newton_tol_rel", ctypes.c_double), ("full_jacobian", ctypes.c_int32),
-                ("max_corrections", ctypes.c_int32), ("line_smoother", ctypes.c_int32),
-                ("smooth_phase", ctypes.c_int32)]
+                ("max_corrections", ctypes.c_int32), ("line_smoother", ctypes.c_int32)]
 
 
 class mg_stats(ctypes.Structure):

@@ -1,5 +1,5 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads without a GPU, and exports
-every function declared in include/mg.h (no compute calls are made here)."""
+every function declared in include/*.h (no compute calls are made here)."""
 import ctypes
 import os
 import re
@@ -59,8 +59,7 @@ def test_workspace_sizing_without_gpu(lib):
     assert mg.load().mg_workspace_bytes(ctypes.byref(bad), ctypes.byref(p)) == 0
     # parameters of the later forms are validated before any allocation (0 bytes = invalid)
     for kw in (dict(full_jacobian=2), dict(max_corrections=0), dict(max_corrections=101), dict(line_smoother=2),
-               dict(newton_tol_rel=1.0), dict(newton_tol_rel=-0.1), dict(pdl=32), dict(wall_dirichlet=2),
-               dict(smooth_phase=-1), dict(smooth_phase=1025)):
+               dict(newton_tol_rel=1.0), dict(newton_tol_rel=-0.1), dict(pdl=32), dict(wall_dirichlet=2)):
         pb = mg.default_params(**kw)
         assert mg.load().mg_workspace_bytes(ctypes.byref(g), ctypes.byref(pb)) == 0, kw
     # the line smoother's column scratch is allocated only when it is enabled
@@ -75,5 +74,5 @@ def test_params_default_values(lib):
     assert (p.nu_coarse_n, p.nu_coarse1, p.nu_coarse2, p.chain_from) == (64, 2, 2, 1)
     assert (p.nu_tiny_n, p.nu_tiny1, p.nu_tiny2, p.pdl, p.wall_dirichlet) == (8, 1, 1, 9, 0)
     assert p.newton_tol_rel == 0.1 and p.newton_tol == 0.0
-    assert (p.full_jacobian, p.max_corrections, p.line_smoother, p.smooth_phase) == (0, 20, 0, 0)
+    assert (p.full_jacobian, p.max_corrections, p.line_smoother) == (0, 20, 0)
     assert np.isclose(p.mu_p, 0.15) and np.isclose(p.D_p, 0.0038)
