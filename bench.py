@@ -751,9 +751,10 @@ def measure_forms(args, dev, peaks):
         sv.autotune()
     for sv, ini in zip(solvers, inits):
         sv.set_state(*ini)
-    grain = mg.autotune_batch(solvers, TOL)      # work-item size of the persistent form (set-up)
+    grain, coarse = mg.autotune_batch(solvers, TOL)   # work list of the persistent form (set-up)
     sizes = sorted(set(dd.nr + 1 for dd in ds))
-    batch = {"instances": len(ds), "sizes": sizes, "precision": "mixed", "persistent_grain": grain}
+    batch = {"instances": len(ds), "sizes": sizes, "precision": "mixed", "persistent_grain": grain,
+             "persistent_coarse_phase_from_intervals": coarse}
     for name, workers in (("persistent", 0), ("host_threads", args.batch_workers)):
         for rep in range(2):
             for sv, ini in zip(solvers, inits):

@@ -272,12 +272,14 @@ int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const
  * current device and must not be used by other threads during the call. */
 int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, double *ms_out, int *rc_out);
 
-/* Autotuner of the batched form's work items (mg_solve_steady_batch with workers = 0): solves
- * the n discharges to tol in one persistent launch once per candidate size of a work item (1,
- * 2, 4 or 8 rounds of 256 nodes, or of the single-discharge kernel's thread blocks), keeps the
- * fastest in every state and returns it in *grain_out (may be NULL).  The states' solutions,
- * statistics and start data are restored afterwards.  MG_EINVAL when a state does not qualify
- * for the persistent form (see mg_solve_steady_batch). */
+/* Autotuner of the batched form's work list (mg_solve_steady_batch with workers = 0): solves
+ * the n discharges to tol in one persistent launch once per candidate shape and keeps the
+ * fastest in every state: the size of a work item (2, 4 or 8 rounds of 256 nodes, or of the
+ * single-discharge kernel's thread blocks) and the largest level (16, 32 or 64 intervals per
+ * side) from which a V-cycle's coarse part runs as one single-CTA phase (same results: only the
+ * schedule changes).  *grain_out (may be NULL) receives size + 100 x level.  The states'
+ * solutions, statistics and start data are restored afterwards.  MG_EINVAL when a state does
+ * not qualify for the persistent form (see mg_solve_steady_batch). */
 int mg_autotune_batch(mg_state **states, int n, double tol, int *grain_out);
 
 /* Autotuner of the smoother's launch shapes: times the red-black half sweep and the fused

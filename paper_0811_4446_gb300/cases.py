@@ -3,6 +3,7 @@
     python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager] [--autotune] [--half] [--line]
     python -m paper_0811_4446_gb300.cases unet B N [REPS] [--mma | --gather | --tma | --halo]
     python -m paper_0811_4446_gb300.cases steady [--mixed] [--eager]
+    python -m paper_0811_4446_gb300.cases batch COUNT [--fp64]
 
 builds the N x N-node discharge of the benchmark family (table transport for N = 256),
 evaluates the Newton residual at the initial state and runs CYCLES multigrid V-cycles
@@ -21,6 +22,10 @@ steady: one steady solve of the benchmark's 257 x 257 workload (129 -> 257 conti
 table transport, rho <= 1e-8) after one untimed solve, autotuned as the benchmark does, inside
 the NVTX range "measure"; --eager launches every kernel from the host (no graphs), so that a
 kernel profiler sees each launch of the solve.
+
+batch: the persistent batched form (one launch of the work-list kernel) on COUNT discharges of
+the batched workload's family with sizes 33^2 to 129^2 (seed 4), mixed precision (--fp64: FP64),
+after one untimed batch, inside the NVTX range "measure".
 
 unet: REPS (default 2) forward passes plus one training step of the learned-guess network
 on a batch of B random (N+1) x (N+1) inputs; --mma selects the mma.sync convolutions instead
@@ -84,6 +89,32 @@ def steady(mixed: bool = False, eager: bool = False) -> float:
     return float(st["steady_rho"])
 
 
+def batch(count: int, fp64: bool = False) -> int:
+    import numpy as np
+    import torch
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import workloads as W
+    from . import mg
+
+    ds = W.batch_64(seed=4, count=count, sizes=(32, 64, 128))
+    sv = [mg.from_discharge(d, precision=mg.MG_FP64 if fp64 else mg.MG_MIXED, stream=torch.cuda.Stream()) for d in ds]
+    ins = [[np.ascontiguousarray(a) for a in (d.ne0, d.np0, d.V0)] for d in ds]
+    mg.solve_steady_batch(sv, 1e-8, workers=0)
+    for s, i in zip(sv, ins):
+        s.set_state(*i)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("measure")
+    rc, _, _ = mg.solve_steady_batch(sv, 1e-8, workers=0)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if rc != mg.MG_OK:
+        raise RuntimeError(f"batched solve failed: {rc}")
+    return count
+
+
 def unet_case(B: int, n: int, reps: int = 2, mma: bool = False, gather: bool = False, tma: bool = False) -> float:
     import numpy as np
     import torch
@@ -108,6 +139,9 @@ if __name__ == "__main__":
         R = int(sys.argv[4]) if len(sys.argv) > 4 and not sys.argv[4].startswith("--") else 2
         print("ok", unet_case(int(sys.argv[2]), int(sys.argv[3]), R, "--mma" in sys.argv, "--gather" in sys.argv,
                                 "--tma" in sys.argv))
+        sys.exit(0)
+    if len(sys.argv) >= 3 and sys.argv[1] == "batch":
+        print("ok", batch(int(sys.argv[2]), "--fp64" in sys.argv))
         sys.exit(0)
     if len(sys.argv) >= 2 and sys.argv[1] == "steady":
         print("ok", steady("--mixed" in sys.argv, "--eager" in sys.argv))

@@ -96,7 +96,11 @@ struct mg_state {
   BPhase *bprog = nullptr;
   int bent[kMaxLevelSet][E_N] = {};          // its subprogram entries per level
   int bgrain = 4;                            // thread-block rounds per work item
+  int bcoarse_n = 16;                        // levels with at most this many intervals per side run
+                                             // in the single-CTA coarse phase of the V-cycle
   int host_prog_ntiles0 = 0;                 // work items of the program's first phase
+  CoarseSet<double> *bcs64[kMaxLevels] = {}; // device coarse sets of the batched program by start level
+  CoarseSet<float> *bcs32[kMaxLevels] = {};
 };
 
 namespace {
@@ -729,9 +733,47 @@ bool batchable(const mg_state *s) {
 //                 the residual of the new state
 //   E_RESTORE     u_old -> u (a rejected step)
 //   E_PROLONG     the state prolonged from level l + 1 and the boundary values set (l < chain_from)
+// The device coarse set of the levels c .. last (as setup_coarse_kernel builds the one of the
+// coarse-cycle kernel, from level c instead of cc_from).
+int batch_coarse_set(mg_state *s, int c) {
+  if (s->bcs64[c]) return MG_OK;
+  if (s->nlev - c > kMaxCoarseSet) return fail(s, MG_EINVAL, "batched coarse phase: %d levels", s->nlev - c);
+  CoarseSet<double> h64 = {};
+  CoarseSet<float> h32 = {};
+  h64.n = h32.n = s->nlev - c;
+  for (int q = 0; q < h64.n; ++q) {
+    h64.nu1[q] = h32.nu1[q] = nu_of(s, c + q, 1);
+    h64.nu2[q] = h32.nu2[q] = nu_of(s, c + q, 2);
+    h64.lv[q] = s->lv[c + q].L;
+    h32.lv[q] = s->lv[c + q].M;
+  }
+  h64.Minv = h32.Minv = s->Minv;
+  h64.rs = h32.rs = s->rs;
+  h64.cs = h32.cs = s->cs;
+  h64.nscale = 1.0;
+  h32.nscale = s->prm.n0;
+  void *d64 = nullptr, *d32 = nullptr;
+  CK(cudaMalloc(&d64, sizeof(h64)));
+  if (cudaMalloc(&d32, sizeof(h32)) != cudaSuccess) {
+    cudaFree(d64);
+    return fail(s, MG_ECUDA, "batched coarse set");
+  }
+  s->bcs64[c] = static_cast<CoarseSet<double> *>(d64);
+  s->bcs32[c] = static_cast<CoarseSet<float> *>(d32);
+  CK(cudaMemcpy(d64, &h64, sizeof(h64), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d32, &h32, sizeof(h32), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
 int build_batch_program(mg_state *s) {
   if (s->bprog) return MG_OK;
   const int last = s->nlev - 1, g = s->bgrain, from = s->prm.chain_from;
+  // the V-cycle of root level l0 descends level by level until the coarse phase's first level:
+  // the first level with at most bcoarse_n intervals per side (never below the coarse-cycle
+  // kernel's), or l0 itself
+  int bcc = s->cc_from;
+  for (int l = 1; l < s->cc_from; ++l)
+    if (std::max(s->lv[l].nr, s->lv[l].nz) <= s->bcoarse_n) { bcc = l; break; }
   const bool m = mixed(s);
   auto cdiv = [](long a, long b) { return (int)((a + b - 1) / b); };
   auto grid328 = [&](const Level &L, int rows) { return cdiv(L.nr + 1, 32) * cdiv(rows, 8); };
@@ -790,13 +832,16 @@ int build_batch_program(mg_state *s) {
       for (int k = 0; k < nu; ++k)
         for (int col = 0; col < 2; ++col) p.push_back(batch_phase(m ? BK_HALF32 : BK_HALF64, l, col, nb, 1, g));
     };
-    for (int l = l0; l < s->cc_from; ++l) {
+    const int c0 = std::max(l0, bcc);
+    int rc = batch_coarse_set(s, c0);
+    if (rc) return rc;
+    for (int l = l0; l < c0; ++l) {
       halves(l, nu_of(s, l, 1));
       const Level &C = s->lv[l + 1].L;
       p.push_back(batch_phase(m ? BK_RESTR32 : BK_RESTR64, l, 0, cdiv(C.nr + 1, 16) * cdiv(C.nz - 1, 3), 1, g));
     }
-    p.push_back(batch_phase(m ? BK_COARSE32 : BK_COARSE64, s->cc_from, 0, 1, 1, 1));
-    for (int l = s->cc_from - 1; l >= l0; --l) {
+    p.push_back(batch_phase(m ? BK_COARSE32 : BK_COARSE64, c0, 0, 1, 1, 1));
+    for (int l = c0 - 1; l >= l0; --l) {
       const Level &F = s->lv[l].L;
       p.push_back(batch_phase(m ? BK_PROL32 : BK_PROL64, l, 0, cdiv((long)F.ni * (F.nz - 1), kBatchThreads), 1, g));
       halves(l, nu_of(s, l, 2));
@@ -842,8 +887,10 @@ void batch_describe(mg_state *s, double tol, BatchInst &I) {
   I.mixed = mixed(s) ? 1 : 0;
   I.max_cycles = std::min(s->prm.max_vcycles, kMaxHist - 1);
   I.S = s->lset;
-  I.cs64 = s->cset64;
-  I.cs32 = s->cset32;
+  for (int l = 0; l < kMaxLevelSet && l < kMaxLevels; ++l) {
+    I.cs64[l] = s->bcs64[l];
+    I.cs32[l] = s->bcs32[l];
+  }
   I.tr = s->tr;
   I.n0 = s->prm.n0;
   I.ctl = s->ctl;
@@ -1434,6 +1481,10 @@ void mg_destroy(mg_state *s) {
   if (s->owns_ws && s->ws) cudaFree(s->ws);
   if (s->hout) cudaFreeHost(s->hout);
   if (s->bprog) cudaFree(s->bprog);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (s->bcs64[l]) cudaFree(s->bcs64[l]);
+    if (s->bcs32[l]) cudaFree(s->bcs32[l]);
+  }
   delete s;
 }
 
@@ -2001,31 +2052,34 @@ int mg_autotune_batch(mg_state **states, int n, double tol, int *grain_out) {
     }
     return MG_OK;
   };
-  auto set_grain = [&](int g) {
+  auto set_shape = [&](int g, int cn) {
     for (int k = 0; k < n; ++k) {
       mg_state *s = states[k];
-      if (s->bgrain != g && s->bprog) {
+      if ((s->bgrain != g || s->bcoarse_n != cn) && s->bprog) {
         cudaFree(s->bprog);
         s->bprog = nullptr;
       }
       s->bgrain = g;
+      s->bcoarse_n = cn;
     }
   };
-  static const int kGrains[] = {1, 2, 4, 8};
-  int best = 4, rc = MG_OK;
+  static const int kGrains[] = {2, 4, 8};
+  static const int kCoarse[] = {16, 32, 64};
+  int best = 4, best_c = 16, rc = MG_OK;
   double best_ms = 1e300;
-  for (int g : kGrains) {
-    if ((rc = restore())) return rc;
-    set_grain(g);
-    const auto t0 = std::chrono::steady_clock::now();
-    rc = solve_batch_persistent(states, n, tol, nullptr, nullptr);
-    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (rc != MG_OK) break;
-    if (ms < best_ms) { best_ms = ms; best = g; }
-  }
+  for (int cn : kCoarse)
+    for (int g : kGrains) {
+      if ((rc = restore())) return rc;
+      set_shape(g, cn);
+      const auto t0 = std::chrono::steady_clock::now();
+      rc = solve_batch_persistent(states, n, tol, nullptr, nullptr);
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (rc != MG_OK) break;
+      if (ms < best_ms) { best_ms = ms; best = g; best_c = cn; }
+    }
   const int rc2 = restore();
-  set_grain(best);
-  if (grain_out) *grain_out = best;
+  set_shape(best, best_c);
+  if (grain_out) *grain_out = best + 100 * best_c;
   return rc != MG_OK ? rc : rc2;
 }
 

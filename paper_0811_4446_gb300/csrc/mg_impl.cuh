@@ -180,8 +180,8 @@ struct BatchInst {
   int32_t ent[kMaxLevelSet][E_N];   // subprogram entries per level
   int32_t last, mixed, max_cycles, pad0;
   const LevelSet *S;
-  const CoarseSet<double> *cs64;
-  const CoarseSet<float> *cs32;
+  const CoarseSet<double> *cs64[kMaxLevelSet];   // the coarse part of a V-cycle from level l down
+  const CoarseSet<float> *cs32[kMaxLevelSet];    // (one phase on one CTA), by l
   Transport tr;
   double dt_inv, n0, eta, w[3];     // of the current Newton iteration (set by the state machine)
   SolveCtl *ctl;

@@ -2700,10 +2700,10 @@ __device__ void batch_tile(const BatchInst &I, const BPhase &ph, int tile, doubl
     case BK_RESTR64: batch_restrict<double>(I, ph, tile, buf); break;
     case BK_RESTR32: batch_restrict<float>(I, ph, tile, buf); break;
     case BK_COARSE64:
-      coarse_cycle_body<double>(*I.cs64, tid, kBatchThreads, true, kBatchThreads, []() { __syncthreads(); });
+      coarse_cycle_body<double>(*I.cs64[ph.level], tid, kBatchThreads, true, kBatchThreads, []() { __syncthreads(); });
       break;
     case BK_COARSE32:
-      coarse_cycle_body<float>(*I.cs32, tid, kBatchThreads, true, kBatchThreads, []() { __syncthreads(); });
+      coarse_cycle_body<float>(*I.cs32[ph.level], tid, kBatchThreads, true, kBatchThreads, []() { __syncthreads(); });
       break;
     case BK_PROL64: batch_prolong<double>(I, ph, tile); break;
     case BK_PROL32: batch_prolong<float>(I, ph, tile); break;
@@ -3086,7 +3086,7 @@ __device__ int batch_finish(BatchInst &I, const BPhase &ph, int pc, unsigned seq
   return nt > 0 ? next : -1;
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BatchHead *head, BatchInst *inst) {
+__global__ void __launch_bounds__(kBatchThreads, 3) k_batch(BatchHead *head, BatchInst *inst) {
   extern __shared__ __align__(16) unsigned char bsm[];
   double *red = reinterpret_cast<double *>(bsm);
   unsigned char *buf = bsm + kBatchShRed;
@@ -3098,53 +3098,71 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BatchHead *head, Bat
     s_keep = 0;
   }
   int own = blockIdx.x % (n > 0 ? n : 1);   // the discharge this CTA worked on last
+  // whether discharge k has an unclaimed work item (a hint: the claim decides)
+  auto open = [&](int k) {
+    const BatchInst &I = inst[k];
+    const unsigned long long w = ld_vol64(&I.claim);
+    const unsigned seq = (unsigned)(w >> 32), cnt = (unsigned)w;
+    const unsigned long long e = ld_vol64(&I.ring[seq & 3]);
+    return (unsigned)(e >> 32) == seq && cnt < ring_ntiles(e);
+  };
   for (;;) {
-    if (threadIdx.x == 0 && !s_keep) {
-      s_exit = 0;
+    if (threadIdx.x < 32 && !s_keep) {
+      // warp 0 looks for work: first the discharge it worked on last (the next phase it may just
+      // have published), then every discharge at once, one per lane, the first open one in index
+      // order (largest discharges first: the longest chains of phases); lane 0 claims it
+      const int lane = threadIdx.x;
       unsigned pause = 32;
       unsigned seen = *reinterpret_cast<volatile unsigned *>(&head->progress);
       unsigned long long idle0 = global_ns();
+      int exit_now = 0;
       for (unsigned spin = 0;; ++spin) {
-        // first the discharge this CTA worked on last, then the others, ordered largest first
-        // (the longest chains of phases)
-        bool got = false;
-        for (int c = -1; c < n && !got; ++c) {
-          const int k = c < 0 ? own : c;
-          if (c == own) continue;
-          BatchInst &I = inst[k];
-          const unsigned long long w = ld_vol64(&I.claim);
-          const unsigned seq = (unsigned)(w >> 32), cnt = (unsigned)w;
-          const unsigned long long e = ld_vol64(&I.ring[seq & 3]);
-          if ((unsigned)(e >> 32) != seq || cnt >= ring_ntiles(e)) continue;
+        int cand = (lane == 0 && open(own)) ? own : -1;
+        cand = __shfl_sync(0xffffffffu, cand, 0);
+        for (int base = 0; base < n && cand < 0; base += 32) {
+          const int k = base + lane;
+          const unsigned m = __ballot_sync(0xffffffffu, k < n && open(k));
+          if (m) cand = base + __ffs(m) - 1;
+        }
+        int got = 0;
+        if (cand >= 0 && lane == 0) {
+          BatchInst &I = inst[cand];
           const unsigned long long o = atom_add_acqrel64(&I.claim, 1ull);
           const unsigned s2 = (unsigned)(o >> 32), c2 = (unsigned)o;
           const unsigned long long e2 = ld_vol64(&I.ring[s2 & 3]);
-          if ((unsigned)(e2 >> 32) != s2 || c2 >= ring_ntiles(e2)) continue;
-          s_k = k; s_pc = ring_pc(e2); s_tile = (int)c2; s_seq = s2;
-          own = k;
-          got = true;
-        }
-        if (got) break;
-        if (*reinterpret_cast<volatile unsigned *>(&head->err) != 0 ||
-            *reinterpret_cast<volatile int *>(&head->ndone) >= n) {
-          s_exit = 1;
-          break;
-        }
-        if ((spin & 15) == 15) {
-          const unsigned now_seen = *reinterpret_cast<volatile unsigned *>(&head->progress);
-          const unsigned long long now = global_ns();
-          if (now_seen != seen) {
-            seen = now_seen;
-            idle0 = now;
-          } else if (now - idle0 > kBatchIdleNs) {
-            atomicExch(&head->err, 1u);
-            s_exit = 1;
-            break;
+          if ((unsigned)(e2 >> 32) == s2 && c2 < ring_ntiles(e2)) {
+            s_k = cand; s_pc = ring_pc(e2); s_tile = (int)c2; s_seq = s2;
+            got = 1;
           }
         }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got) {
+          own = cand;
+          break;
+        }
+        if (lane == 0) {
+          if (*reinterpret_cast<volatile unsigned *>(&head->err) != 0 ||
+              *reinterpret_cast<volatile int *>(&head->ndone) >= n) {
+            exit_now = 1;
+          } else if ((spin & 15) == 15) {
+            const unsigned now_seen = *reinterpret_cast<volatile unsigned *>(&head->progress);
+            const unsigned long long now = global_ns();
+            if (now_seen != seen) {
+              seen = now_seen;
+              idle0 = now;
+            } else if (now - idle0 > kBatchIdleNs) {
+              atomicExch(&head->err, 1u);
+              exit_now = 1;
+            }
+          }
+        }
+        exit_now = __shfl_sync(0xffffffffu, exit_now, 0);
+        if (exit_now) break;
+        if (cand >= 0) continue;  // lost the race for that item: look again at once
         __nanosleep(pause);
         if (pause < 512) pause <<= 1;
       }
+      if (lane == 0) s_exit = exit_now;
     }
     __syncthreads();
     if (s_exit) return;

@@ -353,9 +353,9 @@ def solve_steady_batch(solvers, tol: float, workers: int = 0):
     return rc, ms, rcs
 
 
-def autotune_batch(solvers, tol: float) -> int:
-    """Work-item size of the persistent batched form tuned on these discharges (see
-    mg_autotune_batch in include/mg.h); returns the size kept."""
+def autotune_batch(solvers, tol: float):
+    """Work list of the persistent batched form tuned on these discharges (see
+    mg_autotune_batch in include/mg.h); returns (work-item size, coarse-phase level) kept."""
     lib = load()
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s.h for s in solvers])
@@ -363,7 +363,7 @@ def autotune_batch(solvers, tol: float) -> int:
     rc = lib.mg_autotune_batch(hs, n, float(tol), ctypes.byref(g))
     if rc != MG_OK:
         raise MGError(rc, "mg_autotune_batch failed")
-    return g.value
+    return g.value % 100, g.value // 100
 
 
 def residual_noalloc(nr: int, nz: int, R: float, z, params: mg_params, state, old_state, sources, dt: float,

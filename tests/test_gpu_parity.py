@@ -431,17 +431,17 @@ def test_persistent_batch_equals_individual_solves(mg, precision):
 
 
 def test_autotune_batch_keeps_results_and_restores_states(mg):
-    """The work-item size of the persistent form changes the schedule, not the arithmetic: the
-    autotuner leaves every state as it found it, and solves after it equal solves before it
-    bit for bit."""
+    """The work-item size and the coarse-phase level of the persistent form change the schedule,
+    not the arithmetic: the autotuner leaves every state as it found it, and solves after it
+    equal solves before it bit for bit."""
     ds = W.batch_64(seed=5, count=4, sizes=(32, 64, 128))
     make = lambda: [mg.from_discharge(d, precision=mg.MG_MIXED, stream=torch.cuda.Stream()) for d in ds]
     ref = make()
     assert mg.solve_steady_batch(ref, 1e-8, workers=0)[0] == mg.MG_OK
     tuned = make()
     before = [s.get_state() for s in tuned]
-    grain = mg.autotune_batch(tuned, 1e-8)
-    assert grain in (1, 2, 4, 8)
+    grain, coarse = mg.autotune_batch(tuned, 1e-8)
+    assert grain in (2, 4, 8) and coarse in (16, 32, 64)
     for s, b in zip(tuned, before):
         a = s.get_state()
         assert all(np.array_equal(a[q], b[q]) for q in range(3))
