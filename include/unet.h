@@ -54,25 +54,32 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
 
 /* Tensor-core path of the convolutions: a parity and measurement reference, not a choice a
  * user makes.  The network runs on path 3 (the default), which assigns one kernel to each
- * layer shape: the halo-load tcgen05 forward (stride-1 layers whose weights fit in 72 KB), the
- * TMA-tile tcgen05 forward (the other 3x3 layers with 32-channel input parts), the gathering
- * tcgen05 kernel (the 8-channel first layer and every data gradient), the FP32 CUDA-core head
- * and the weight gradient below.  Paths 0-2 keep the earlier kernels of those layers so that
- * the tests can compare each layer's kernel with the one it replaced (same operands, another
- * order of the sums) and the benchmark can report what each replacement gained:
+ * layer shape: the halo-load tcgen05 kernel (the forward of stride-1 layers whose weights fit in
+ * 72 KB, and their data gradient where the reversed weights fit), the TMA-tile tcgen05 forward
+ * (the other 3x3 layers with 32-channel input parts), the TMA-fed tcgen05 weight gradient (3x3
+ * layers with 32-channel input parts), the gathering tcgen05 kernels (the 8-channel first layer,
+ * the other data gradients) and the FP32 CUDA-core head.  Paths 0-2 keep the earlier kernels
+ * of those layers so that the tests can compare each layer's kernel with the one it replaced
+ * (same operands, another order of the sums) and the benchmark can report what each
+ * replacement gained:
  *   0 = mma.sync for every convolution.
  *   1 = tcgen05.mma with the accumulator in tensor memory for the forward and data-gradient
- *       convolutions whose output width is a multiple of 16 (<= 256), operands gathered by
- *       threads; the 1x1 head's forward (8 FP32 outputs) on an FP32-accumulating CUDA-core
- *       kernel; the rest on mma.sync.
+ *       convolutions whose output width is a multiple of 16 (<= 256) and the weight gradients
+ *       with 32 <= output channels <= 128, operands gathered by threads (for the weight
+ *       gradient MN-major, straight from the NHWC tensors); the 1x1 head's forward (8 FP32
+ *       outputs) on an FP32-accumulating CUDA-core kernel; the rest on mma.sync.
  *   2 = as 1, except that the forward 3x3 convolutions (stride 1 or 2) whose input
  *       parts have a multiple of 32 channels take their operands by TMA tiled loads (tiles of
  *       16 x 8 output pixels, the padding read as the loads' zero fill) in a persistent kernel.
  *   3 (default) = as 2, except that the stride-1 ones whose weight matrix fits in 72 KB keep it
  *       resident in shared memory and load one 10 x 18-pixel halo per 32-channel chunk for all
- *       nine taps (tiles of 8 x 16 output pixels); their sums round in another order.
- * The weight gradient always uses mma.sync.  Any other value returns MG_EINVAL.  A tcgen05
- * kernel whose bounded wait expires makes the next call return MG_ETIMEOUT. */
+ *       nine taps (tiles of 8 x 16 output pixels), the data gradient of those layers runs on the
+ *       same kernel as a forward convolution of the output gradient with the taps reversed, and
+ *       the weight gradient of the 3x3 layers with 32-channel input parts takes both operands
+ *       by TMA tiled loads (8 x 8-pixel segments, one load per tap and 32-channel slice); their
+ *       sums round in another order.
+ * Any other value returns MG_EINVAL.  A tcgen05 kernel whose bounded wait expires makes the next
+ * call return MG_ETIMEOUT. */
 int mg_unet_set_tensor_path(mg_unet *n, int path);
 
 /* One training step: loss and gradients as above, then an Adam update (beta1 0.9,

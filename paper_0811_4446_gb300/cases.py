@@ -126,12 +126,13 @@ def unet_case(B: int, n: int, reps: int = 2, mma: bool = False, gather: bool = F
     net = unet.UNet(B, n)
     net.set_tensor_path(0 if mma else (1 if gather else (2 if tma else 3)))
     net.set_params(unet.init_params(0))
+    ysum = 0.0
     for _ in range(reps):
-        y = net.forward(x)
+        ysum += float(net.forward(x).abs().mean())
     loss = net.train_step(x, t, 1e-4)
     torch.cuda.synchronize()
     net.close()
-    return float(loss) + float(y.abs().mean())
+    return float(loss) + ysum
 
 
 if __name__ == "__main__":

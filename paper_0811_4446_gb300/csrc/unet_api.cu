@@ -33,6 +33,7 @@ int pad8(int c) { return (c + 7) & ~7; }
 struct Act {
   __nv_bfloat16 *a = nullptr;  // activation, NHWC bf16
   float *g = nullptr;          // gradient, NHWC FP32
+  bool gw = false;             // g holds a contribution of the current backward pass
   int H = 0, W = 0, C = 0;
   size_t elems(int B) const { return (size_t)B * H * W * C; }
 };
@@ -44,7 +45,7 @@ struct mg_unet {
   cudaStream_t st = nullptr;
   size_t nparam = 0, woff[NL], boff[NL];
   float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
-  __nv_bfloat16 *wf[NL], *wd[NL];
+  __nv_bfloat16 *wf[NL], *wd[NL], *wdf[NL];
   float *dwpad = nullptr;
   Act x, e0a, e0b, e1a, e1b, e2a, e2b, e3a, e3b, u3, d2, u2, d1, u1, d0;
   float *out = nullptr, *dout = nullptr, *tgt = nullptr, *xin = nullptr;
@@ -54,6 +55,10 @@ struct mg_unet {
   int use_tc = 3;          // 1: tcgen05 where the layer shape allows it; 2: TMA-fed where it can; 3: halo loads too
   ConvMaps maps[NL];       // tensor maps of the TMA-fed forward convolutions, built on first use
   const void *map_key[NL][4] = {};  // inputs, weights and the kind of map (2: tile boxes, 3: halo boxes)
+  ConvMaps wmaps[NL];      // tensor maps of the TMA-fed weight gradients, built on first use
+  const void *wmap_key[NL][3] = {};  // their inputs and dY
+  ConvMaps dmaps[NL];      // tensor maps of the halo-kernel data gradients, built on first use
+  const void *dmap_key[NL][2] = {};  // their dY and weights
   int step = 0;
   void *block = nullptr;
   std::string err;
@@ -115,6 +120,7 @@ void layout(mg_unet *n, Carve &c) {
     const size_t e = (size_t)kL[l].ks * kL[l].ks * kL[l].ci * pad8(kL[l].co);
     n->wf[l] = c.take<__nv_bfloat16>(e);
     n->wd[l] = c.take<__nv_bfloat16>(e);
+    n->wdf[l] = c.take<__nv_bfloat16>(e);
   }
   n->dwpad = c.take<float>(maxw);
   auto act = [&](Act &t, int Hh, int C) {
@@ -196,8 +202,21 @@ int conv_fwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, Act *out,
 // Backward of layer l given the FP32 gradient of its output (out.g, or dout32 for the head):
 // ReLU mask, weight and bias gradients, and (if want_dx) the data gradient added into the
 // inputs' gradients.
-int conv_bwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, const Act *out, const float *dout32,
-             bool want_dx) {
+// The first data-gradient contribution to an activation's gradient overwrites it (no zeroing
+// pass, no read), later ones add; returns the data-gradient kernels' dacc flag in *dacc.
+int dx_mode(mg_unet *n, int B, Act &in1, Act *in2, int *dacc) {
+  const bool w1 = in1.gw, w2 = in2 ? in2->gw : w1;
+  if (w1 != w2) {
+    Act &z = w1 ? *in2 : in1;
+    UK(cudaMemsetAsync(z.g, 0, z.elems(B) * sizeof(float), n->st));
+  }
+  *dacc = (w1 || w2) ? 1 : 0;
+  in1.gw = true;
+  if (in2) in2->gw = true;
+  return MG_OK;
+}
+
+int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const float *dout32, bool want_dx) {
   ConvArgs a = conv_args(n, l, B, in1, in2);
   const size_t P = (size_t)a.Pout;
   const int cop = a.Cout;
@@ -209,10 +228,51 @@ int conv_bwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, const Act
   w.dy = n->dpre;
   w.dw = n->dwpad;
   UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), n->st));
-  const int tiles = ((w.M + 63) / 64) * ((w.N + 63) / 64);
-  const int splits = std::max(1, std::min((w.K + 255) / 256, 2 * 152 * 2 / std::max(1, tiles)));
-  UK(launch_conv(w, MODE_WGRAD, splits, n->st));
+  if (n->use_tc == 3 && wgrad_tma_supported(w)) {
+    const void *key[3] = {w.x1, w.x2, w.dy};
+    if (std::memcmp(key, n->wmap_key[l], sizeof(key)) != 0) {
+      if (int rc = make_wgrad_maps(w, n->Bmax, &n->wmaps[l]))
+        return fail(n, MG_ECUDA, "weight-gradient tensor maps of layer %d: encode step %d failed", l, rc);
+      std::memcpy(n->wmap_key[l], key, sizeof(key));
+    }
+    UK(launch_wgrad_tma(w, n->wmaps[l], n->tc_err, n->st));
+  } else if (n->use_tc && wgrad_tc_supported(w)) {
+    UK(launch_wgrad_tc(w, n->tc_err, n->st));
+  } else {
+    const int tiles = ((w.M + 63) / 64) * ((w.N + 63) / 64);
+    const int splits = std::max(1, std::min((w.K + 255) / 256, 2 * 152 * 2 / std::max(1, tiles)));
+    UK(launch_conv(w, MODE_WGRAD, splits, n->st));
+  }
   UK(launch_unpad_grad(n->dwpad, n->grad + n->woff[l], (size_t)a.Kf, kL[l].co, cop, n->st));
+  int dacc = 1;
+  if (want_dx)
+    if (int rc = dx_mode(n, B, in1, in2, &dacc)) return rc;
+  if (want_dx && n->use_tc == 3 && a.ks == 3 && a.stride == 1) {
+    // 3x3 stride 1: dX = dY convolved with the reversed taps (wdf), a forward convolution on the
+    // input grid, on the halo kernel where its weight matrix fits
+    ConvArgs f;
+    std::memset(&f, 0, sizeof(f));
+    f.Bn = B;
+    f.Hin = f.Hout = a.Hin;
+    f.Win = f.Wout = a.Win;
+    f.ks = 3; f.stride = 1; f.pad = 1;
+    f.C1 = cop; f.C2 = 0;
+    f.x1 = n->dpre;
+    f.N = f.Cout = f.Nreal = a.C1 + a.C2;
+    f.M = B * a.Hin * a.Win; f.K = 9 * cop; f.Kf = f.K; f.Pout = f.M;
+    f.w = n->wdf[l];
+    f.dx1 = in1.g; f.dx2 = in2 ? in2->g : nullptr; f.dsplit = a.C1; f.dacc = dacc;
+    if (conv_halo_supported(f, MODE_FWD)) {
+      const void *key[2] = {f.x1, f.w};
+      if (std::memcmp(key, n->dmap_key[l], sizeof(key)) != 0) {
+        if (int rc = make_halo_maps(f, n->Bmax, &n->dmaps[l]))
+          return fail(n, MG_ECUDA, "data-gradient tensor maps of layer %d: encode step %d failed", l, rc);
+        std::memcpy(n->dmap_key[l], key, sizeof(key));
+      }
+      UK(launch_conv_halo(f, n->dmaps[l], n->tc_err, n->st));
+      return MG_OK;
+    }
+  }
   if (want_dx) {
     ConvArgs d = a;
     d.M = B * a.Hin * a.Win; d.N = a.C1 + a.C2; d.K = a.ks * a.ks * cop;
@@ -220,6 +280,7 @@ int conv_bwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, const Act
     d.dy = n->dpre;
     d.dx1 = in1.g;
     d.dx2 = in2 ? in2->g : nullptr;
+    d.dacc = dacc;
     if (n->use_tc && conv_tc_supported(d, MODE_DGRAD)) UK(launch_conv_tc(d, MODE_DGRAD, n->tc_err, n->st));
     else UK(launch_conv(d, MODE_DGRAD, 1, n->st));
   }
@@ -228,8 +289,8 @@ int conv_bwd(mg_unet *n, int l, int B, const Act &in1, const Act *in2, const Act
 
 int refresh_weights(mg_unet *n) {
   for (int l = 0; l < NL; ++l)
-    UK(launch_weight_copies(n->master + n->woff[l], n->wf[l], n->wd[l], kL[l].ks, kL[l].ci, kL[l].co, pad8(kL[l].co),
-                            n->st));
+    UK(launch_weight_copies(n->master + n->woff[l], n->wf[l], n->wd[l], n->wdf[l], kL[l].ks, kL[l].ci, kL[l].co,
+                            pad8(kL[l].co), n->st));
   return MG_OK;
 }
 
@@ -257,15 +318,18 @@ int backward(mg_unet *n, int B) {
   int rc;
   Act *all[] = {&n->x, &n->e0a, &n->e0b, &n->e1a, &n->e1b, &n->e2a, &n->e2b, &n->e3a,
                 &n->e3b, &n->u3, &n->d2, &n->u2, &n->d1, &n->u1, &n->d0};
-  for (Act *t : all) UK(cudaMemsetAsync(t->g, 0, t->elems(B) * sizeof(float), n->st));
+  for (Act *t : all) t->gw = false;
   UK(cudaMemsetAsync(n->grad, 0, n->nparam * sizeof(float), n->st));
   if ((rc = conv_bwd(n, HEAD, B, n->d0, nullptr, nullptr, n->dout, true))) return rc;
   if ((rc = conv_bwd(n, D0, B, n->u1, &n->e0b, &n->d0, nullptr, true))) return rc;
   UK(launch_upsample_bwd(n->u1.g, n->d1.g, B, n->d1.H, n->d1.W, n->d1.C, n->st));
+  n->d1.gw = true;
   if ((rc = conv_bwd(n, D1, B, n->u2, &n->e1b, &n->d1, nullptr, true))) return rc;
   UK(launch_upsample_bwd(n->u2.g, n->d2.g, B, n->d2.H, n->d2.W, n->d2.C, n->st));
+  n->d2.gw = true;
   if ((rc = conv_bwd(n, D2, B, n->u3, &n->e2b, &n->d2, nullptr, true))) return rc;
   UK(launch_upsample_bwd(n->u3.g, n->e3b.g, B, n->e3b.H, n->e3b.W, n->e3b.C, n->st));
+  n->e3b.gw = true;
   if ((rc = conv_bwd(n, E3B, B, n->e3a, nullptr, &n->e3b, nullptr, true))) return rc;
   if ((rc = conv_bwd(n, E3A, B, n->e2b, nullptr, &n->e3a, nullptr, true))) return rc;
   if ((rc = conv_bwd(n, E2B, B, n->e2a, nullptr, &n->e2b, nullptr, true))) return rc;

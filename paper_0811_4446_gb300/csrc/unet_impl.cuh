@@ -27,12 +27,19 @@ struct ConvArgs {
   float *y32;                     // or FP32 (network head)
   float *dx1, *dx2;               // data gradient of the two input parts (FP32, accumulated)
   float *dw;                      // weight gradient [M][N] (FP32, atomically accumulated)
+  int dsplit;                     // data gradient as a forward convolution of dY (halo kernel): output
+                                  // channels [0, dsplit) go to dx1, the rest to dx2
+  int dacc;                       // data gradient: 1 = add into dx1 / dx2, 0 = overwrite them (the
+                                  // first contribution of the backward pass)
 };
 
 cudaError_t launch_conv(const ConvArgs &a, int mode, int splits, cudaStream_t st);
 // tcgen05 / TMEM path (forward and data gradient with 16 <= N <= 256, N % 16 == 0)
 bool conv_tc_supported(const ConvArgs &a, int mode);
 cudaError_t launch_conv_tc(const ConvArgs &a, int mode, int *err, cudaStream_t st);
+// tcgen05 weight gradient (MN-major operands from NHWC; 32 <= N <= 128, N % 32 == 0): adds into a.dw
+bool wgrad_tc_supported(const ConvArgs &a);
+cudaError_t launch_wgrad_tc(const ConvArgs &a, int *err, cudaStream_t st);
 // TMA-fed tcgen05 path (forward 3x3 stride-1 convolutions whose input parts have a multiple
 // of 32 channels): tensor maps of the two input parts and of the weight matrix
 struct ConvMaps {
@@ -41,6 +48,12 @@ struct ConvMaps {
 bool conv_tma_supported(const ConvArgs &a, int mode);
 int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
 cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st);
+// TMA-fed tcgen05 weight gradient (3x3, stride 1 or 2, input parts of a multiple of 32 channels,
+// 32 <= N <= 128, N % 32 == 0): tensor maps of the two input parts and of dY (in ConvMaps::w);
+// adds into a.dw
+bool wgrad_tma_supported(const ConvArgs &a);
+int make_wgrad_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
+cudaError_t launch_wgrad_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st);
 // halo variant (3x3 stride 1, the weight matrix resident in shared memory, <= 72 KB)
 bool conv_halo_supported(const ConvArgs &a, int mode);
 int make_halo_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
@@ -56,8 +69,8 @@ cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h
 cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,
                        cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, int step, cudaStream_t st);
-cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, int ks, int ci, int co, int cop,
-                                 cudaStream_t st);
+cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wdf, int ks, int ci,
+                                 int co, int cop, cudaStream_t st);
 cudaError_t launch_unpad_grad(const float *gp, float *g, size_t rows, int co, int cop, cudaStream_t st);
 cudaError_t launch_f32_to_bf16(const float *a, __nv_bfloat16 *b, size_t n, cudaStream_t st);
 

@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
             else a.y[(size_t)m * a.N + nn] = __float2bfloat16(v);
           } else if (MODE == MODE_DGRAD) {
             // accumulate into the FP32 gradient of the concatenated input's two parts
-            if (nn < a.C1) a.dx1[(size_t)m * a.C1 + nn] += v;
-            else a.dx2[(size_t)m * a.C2 + (nn - a.C1)] += v;
+            float *d = nn < a.C1 ? &a.dx1[(size_t)m * a.C1 + nn] : &a.dx2[(size_t)m * a.C2 + (nn - a.C1)];
+            *d = a.dacc ? *d + v : v;
           } else {
             atomicAdd(&a.dw[(size_t)m * a.N + nn], v);
           }
@@ -302,8 +302,9 @@ cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, 
   return cudaGetLastError();
 }
 
-// Transpose of the upsampling on FP32 gradients: dc[Y][X] += sum of fine gradients weighted
-// by the interpolation weights of node (Y, X); four channels (one float4) per thread.
+// Transpose of the upsampling on FP32 gradients: dc[Y][X] = sum of fine gradients weighted by
+// the interpolation weights of node (Y, X) (the coarse tensor's only consumer is the upsampling,
+// so this is its whole gradient); four channels (one float4) per thread.
 __global__ void k_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C) {
   const int H = 2 * h - 1, W = 2 * w - 1, G = C / 4;
   const unsigned n = (unsigned)B * h * w * G;
@@ -324,9 +325,7 @@ __global__ void k_upsample_bwd(const float *dfine, float *dcoarse, int B, int h,
         s.x += wt * f.x; s.y += wt * f.y; s.z += wt * f.z; s.w += wt * f.w;
       }
     }
-    float4 d = dst[i];
-    d.x += s.x; d.y += s.y; d.z += s.z; d.w += s.w;
-    dst[i] = d;
+    dst[i] = s;
   }
 }
 
@@ -387,8 +386,11 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, 
 // bf16 operand copies of one layer's FP32 master weights w[kh][kw][ci][co]:
 //   wf[co][(kh, kw, ci)]  (forward B operand, k contiguous)
 //   wd[ci][(kh, kw, co)]  (data-gradient B operand)
+//   wdf[ci][(2 - kh, 2 - kw, co)]  (the same with the taps reversed: the weights of the data
+//                         gradient written as a forward convolution of dY, stride 1)
 // co is padded to cop (zero rows) so that every operand dimension is a multiple of 8.
-__global__ void k_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, int ks, int ci, int co, int cop) {
+__global__ void k_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wdf, int ks, int ci,
+                                int co, int cop) {
   const int taps = ks * ks;
   const size_t n = (size_t)taps * ci * cop;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -400,13 +402,14 @@ __global__ void k_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16
     const __nv_bfloat16 b = __float2bfloat16(v);
     wf[(size_t)o * taps * ci + (size_t)tap * ci + c] = b;
     wd[(size_t)c * taps * cop + (size_t)tap * cop + o] = b;
+    wdf[(size_t)c * taps * cop + (size_t)(taps - 1 - tap) * cop + o] = b;
   }
 }
 
-cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, int ks, int ci, int co, int cop,
-                                 cudaStream_t st) {
+cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wdf, int ks, int ci,
+                                 int co, int cop, cudaStream_t st) {
   const size_t n = (size_t)ks * ks * ci * cop;
-  k_weight_copies<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(w, wf, wd, ks, ci, co, cop);
+  k_weight_copies<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(w, wf, wd, wdf, ks, ci, co, cop);
   return cudaGetLastError();
 }
 

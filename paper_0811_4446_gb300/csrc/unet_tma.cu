@@ -435,6 +435,28 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (!inside) continue;
+        if (a.dx1) {
+          // data gradient: write (or add) into the FP32 gradient of the input part these 16
+          // channels belong to (dsplit is a multiple of 32: a group of 16 never straddles the parts)
+          const bool p1 = n0 < a.dsplit;
+          const int cw = p1 ? a.dsplit : a.N - a.dsplit;
+          float4 *dst = reinterpret_cast<float4 *>((p1 ? a.dx1 : a.dx2) + pix * cw + (p1 ? n0 : n0 - a.dsplit));
+          float4 o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            o[e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]), __uint_as_float(r[4 * e + 2]),
+                               __uint_as_float(r[4 * e + 3]));
+          if (a.dacc) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float4 q = dst[e];
+              o[e].x += q.x; o[e].y += q.y; o[e].z += q.z; o[e].w += q.w;
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dst[e] = o[e];
+          continue;
+        }
         float v[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -454,6 +476,183 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       arrive(saddr(&acc_empty[ab]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && abort_sh) atomicExch(err, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+// ---- weight gradient fed by TMA (tensor path 3) ------------------------------------------------
+//
+// dW[m][n] = sum over output pixels k of A[m][k] dY[k][n], m = (tap, input channel) in the order of
+// the weight matrix, n = output channel.  Both operands are pixel-major in memory (NHWC), so they
+// enter the tensor core MN-major: a TMA box of 32 channels x 64 output pixels (P columns x R rows
+// of one image; for stride 2 the box spans 2P x 2R input pixels traversed with element strides 2)
+// lands as a stack of eight 64-byte-swizzle atoms (32 channels x 8 pixels, 512 bytes each), a
+// 4 KB "slice".  A CTA owns a group of Cg 32-channel input slices for all nine taps and a range of
+// pixel segments; per segment it loads 9 Cg input slices (one per tap and slice: the window the
+// tap reads) and N / 32 slices of dY.  The input slices are stored in the order of m, so any four
+// consecutive ones form the A operand of one M = 128 MMA (atoms 4 KB apart: the descriptor's
+// leading offset); the accumulators of all ceil(9 Cg / 4) such tiles stay in TMEM over the CTA's
+// whole pixel range and are added into dW once at the end (FP32 atomics).  A last tile that runs
+// past the 9 Cg slices reads the slices after them (or the guard after the ring): those TMEM rows
+// are discarded.  Warp roles as in the forward kernels: lane 0 of warp 0 loads, lane 0 of warp 1
+// issues the MMAs, all four warps drain TMEM; every wait is bounded.
+constexpr int WT_THREADS = 128;
+constexpr int WT_PIX = 64;                       // output pixels per segment (four K = 16 steps)
+constexpr uint32_t WT_SLICE = WT_PIX * 64;       // 32 channels x 64 pixels of bf16
+constexpr int WT_MAXS = 4;
+
+struct WgPlan {
+  int P, R;            // segment: P output columns x R output rows (P * R = 64)
+  int tx, per_img;     // segments per output row band, per image
+  int units;           // segments of the batch
+  int c1;              // 32-channel slices of input part 1 (part 2 follows)
+  int Cg;              // input slices per channel group (gridDim.y groups)
+  int tiles;           // M = 128 tiles: ceil(9 Cg / 4)
+  int nb;              // dY slices: N / 32
+  int S;               // pipeline stages
+  int per_cta;         // segments per CTA
+};
+
+__device__ __forceinline__ uint64_t mn_sw64_desc(uint32_t a) {
+  uint64_t d = 0;
+  d |= (uint64_t)((a >> 4) & 0x3FFFu);
+  d |= (uint64_t)((WT_SLICE >> 4) & 0x3FFFu) << 16;  // LBO: next 32 channels (next atom along M / N)
+  d |= (uint64_t)(512u >> 4) << 32;                  // SBO: next 8 pixels (next atom along K)
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
+__global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap mx1,
+                                                          const __grid_constant__ CUtensorMap mx2,
+                                                          const __grid_constant__ CUtensorMap mdy, ConvArgs a,
+                                                          WgPlan p, int tmem_cols, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
+  const int na = 9 * p.Cg;
+  const uint32_t st_bytes = (uint32_t)(na + p.nb) * WT_SLICE;
+  __shared__ __align__(8) uint64_t full[WT_MAXS], empty[WT_MAXS], mma_done;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+  volatile int *abort = &abort_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = blockIdx.y;
+  const int u0 = blockIdx.x * p.per_cta, u1 = min(p.units, u0 + p.per_cta);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_sh)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 32) {
+    abort_sh = 0;
+    for (int s = 0; s < p.S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mma_done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  bool mma_ok = false;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    const uint64_t pm1 = reinterpret_cast<uint64_t>(&mx1), pm2 = reinterpret_cast<uint64_t>(&mx2),
+                   pmd = reinterpret_cast<uint64_t>(&mdy);
+    long g = 0;
+    for (int u = u0; u < u1 && !*abort; ++u, ++g) {
+      const int s = (int)(g % p.S);
+      const uint32_t use = (uint32_t)(g / p.S);
+      if (use > 0 && !wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort)) break;
+      const int b = u / p.per_img, r = u - b * p.per_img;
+      const int y0 = (r / p.tx) * p.R, x0 = (r % p.tx) * p.P;
+      const uint32_t sa = base + (uint32_t)s * st_bytes, bar = saddr(&full[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes) : "memory");
+      for (int tap = 0; tap < 9; ++tap) {
+        const int kh = tap / 3, kw = tap - kh * 3;
+        const int xi = x0 * a.stride + kw - 1, yi = y0 * a.stride + kh - 1;
+        for (int cg = 0; cg < p.Cg; ++cg) {
+          const int q = grp * p.Cg + cg;
+          const uint64_t mx = q < p.c1 ? pm1 : pm2;
+          const int cc = (q < p.c1 ? q : q - p.c1) * 32;
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+              ::"r"(sa + (uint32_t)(tap * p.Cg + cg) * WT_SLICE), "l"(mx), "r"(cc), "r"(xi), "r"(yi), "r"(b), "r"(bar)
+              : "memory");
+        }
+      }
+      for (int j = 0; j < p.nb; ++j)
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+            ::"r"(sa + (uint32_t)(na + j) * WT_SLICE), "l"(pmd), "r"(32 * j), "r"(x0), "r"(y0), "r"(b), "r"(bar)
+            : "memory");
+    }
+    // loads still in flight: the last min(S, g) issued, each the latest on its stage
+    volatile int never = 0;
+    for (long j = g > p.S ? g - p.S : 0; j < g; ++j)
+      wait_bounded(saddr(&full[j % p.S]), (uint32_t)((j / p.S) & 1), &never);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: every tile accumulates over every segment of the CTA
+    const uint32_t idesc = idesc_bf16_tma(128, a.N) | (1u << 15) | (1u << 16);  // A and B MN-major
+    long g = 0;
+    bool ok = true;
+    for (int u = u0; u < u1; ++u, ++g) {
+      const int s = (int)(g % p.S);
+      if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / p.S) & 1), abort))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base + (uint32_t)s * st_bytes, sb = sa + (uint32_t)na * WT_SLICE;
+      for (int t = 0; t < p.tiles; ++t) {
+#pragma unroll
+        for (int kk = 0; kk < WT_PIX / 16; ++kk) {
+          const uint64_t da = mn_sw64_desc(sa + (uint32_t)(4 * t) * WT_SLICE + kk * 1024);
+          const uint64_t db = mn_sw64_desc(sb + kk * 1024);
+          const uint32_t acc = (g > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(t * a.N)),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        }
+      }
+      commit(saddr(&empty[s]));
+    }
+    commit(saddr(&mma_done));
+    if (!ok) *abort = 1;
+  }
+  __syncwarp();
+  // ---- epilogue: every warp, once the last MMA has completed
+  {
+    const bool got = wait_bounded(saddr(&mma_done), 0, abort);
+    mma_ok = __all_sync(0xffffffffu, got) && !*abort;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (mma_ok && u1 > u0) {
+    const int C = a.C1 + a.C2;
+    for (int t = 0; t < p.tiles; ++t) {
+      const int slot = 4 * t + warp;  // warp w reads TMEM lanes 32 w .. 32 w + 31: slot 4 t + w
+      if (slot >= na) break;
+      const int tap = slot / p.Cg, cg = slot - tap * p.Cg;
+      const int m = tap * C + (grp * p.Cg + cg) * 32 + lane;
+      for (int n0 = 0; n0 < a.N; n0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * a.N + n0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float *dst = a.dw + (size_t)m * a.N + n0;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) atomicAdd(dst + e, __uint_as_float(r[e]));
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -494,9 +693,15 @@ bool conv_tma_supported(const ConvArgs &a, int mode) {
          a.N <= TM_NMAX && a.Nreal <= a.N && encoder() != nullptr;
 }
 
+// Forward (bf16 output with bias and ReLU into a.y) or, with a.dx1 set, the data gradient of a 3x3
+// stride-1 convolution written as a forward convolution of dY with the reversed taps (FP32 added
+// into dx1 / dx2 at the input's pixels; the output grid is the input grid).
 bool conv_halo_supported(const ConvArgs &a, int mode) {
+  const bool out_ok = a.dx1 ? (!a.y && !a.y32 && a.dsplit > 0 && a.dsplit % TM_CH == 0 && a.dsplit <= a.N &&
+                               (a.dsplit == a.N || a.dx2))
+                            : (a.y && !a.y32);
   return mode == MODE_FWD && a.ks == 3 && a.stride == 1 && a.pad == 1 && a.C1 > 0 && a.C1 % TM_CH == 0 &&
-         a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && a.y && !a.y32 && a.N % 16 == 0 && a.N >= 16 &&
+         a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && out_ok && a.N % 16 == 0 && a.N >= 16 &&
          a.N <= TM_NMAX && a.Nreal <= a.N && (size_t)9 * (a.C1 + a.C2) * a.N * 2 <= HWMAX && encoder() != nullptr;
 }
 
@@ -620,6 +825,107 @@ cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cuda
   tg.ntiles = tg.per_img * a.Bn;
   const int grid = std::max(1, std::min(tg.ntiles, sms * occ));
   k_conv_tma<<<grid, TM_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, tg, S, cols, err);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Segment shape P x R (P * R = 64) with the fewest padded output pixels; the channel group: the
+// most input slices per CTA whose accumulators fit in the 512 TMEM columns and whose stage fits
+// at least twice in shared memory (fewer dY re-reads, fewer partial M tiles).
+constexpr size_t WT_SMEM_MAX = 225 * 1024;
+
+WgPlan wgrad_plan(const ConvArgs &a) {
+  WgPlan p;
+  std::memset(&p, 0, sizeof(p));
+  long best = -1;
+  for (int P = 8; P <= 64; P *= 2) {
+    const int R = WT_PIX / P;
+    const long padded = (long)((a.Wout + P - 1) / P) * P * (long)((a.Hout + R - 1) / R) * R;
+    if (best < 0 || padded < best) best = padded, p.P = P, p.R = R;
+  }
+  p.tx = (a.Wout + p.P - 1) / p.P;
+  p.per_img = p.tx * ((a.Hout + p.R - 1) / p.R);
+  p.units = p.per_img * a.Bn;
+  p.c1 = a.C1 / 32;
+  const int c32 = (a.C1 + a.C2) / 32;
+  p.nb = a.N / 32;
+  for (int cg = c32; cg >= 1; --cg) {
+    if (c32 % cg) continue;
+    const int tiles = (9 * cg + 3) / 4;
+    const size_t stage = (size_t)(9 * cg + p.nb) * WT_SLICE;
+    const size_t guard = (size_t)std::max(0, 4 * tiles - 9 * cg - p.nb) * WT_SLICE;
+    if (tiles * a.N > 512 || 1024 + 2 * stage + guard > WT_SMEM_MAX) continue;
+    p.Cg = cg;
+    p.tiles = tiles;
+    p.S = (int)std::min<size_t>(WT_MAXS, (WT_SMEM_MAX - 1024 - guard) / stage);
+    break;
+  }
+  return p;
+}
+
+size_t wgrad_smem(const WgPlan &p) {
+  const size_t stage = (size_t)(9 * p.Cg + p.nb) * WT_SLICE;
+  const size_t guard = (size_t)std::max(0, 4 * p.tiles - 9 * p.Cg - p.nb) * WT_SLICE;
+  return 1024 + (size_t)p.S * stage + guard;
+}
+
+}  // namespace
+
+bool wgrad_tma_supported(const ConvArgs &a) {
+  if (!(a.ks == 3 && (a.stride == 1 || a.stride == 2) && a.pad == 1 && a.C1 > 0 && a.C1 % 32 == 0 &&
+        a.C2 % 32 == 0 && (a.C2 == 0 || a.x2) && a.N % 32 == 0 && a.N >= 32 && a.N <= 128 && a.Cout == a.N &&
+        a.M == a.Kf && a.Pout > 0 && encoder() != nullptr))
+    return false;
+  return wgrad_plan(a).Cg > 0;
+}
+
+// Tensor maps of the weight gradient: the input parts as 4-D (C, W, H, B) tensors with boxes of
+// 32 channels x sP x sR pixels traversed with element strides s (the stride), dY as a 4-D
+// (N, Wout, Hout, B) tensor with boxes of 32 x P x R; 64-byte swizzle, zero fill outside.  The
+// dY map goes into the w slot of ConvMaps.
+int make_wgrad_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
+  EncodeTiled enc = encoder();
+  if (!enc) return 1;
+  const WgPlan p = wgrad_plan(a);
+  std::memset(m, 0, sizeof(*m));
+  const cuuint32_t sd = (cuuint32_t)a.stride;
+  auto map4 = [&](CUtensorMap *t, const __nv_bfloat16 *ptr, int C, int W, int H, cuuint32_t s) {
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bmax};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {32, (cuuint32_t)p.P * s, (cuuint32_t)p.R * s, 1}, es[4] = {1, s, s, 1};
+    return enc(t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!map4(&m->x1, a.x1, a.C1, a.Win, a.Hin, sd)) return 2;
+  if (a.C2 > 0 ? !map4(&m->x2, a.x2, a.C2, a.Win, a.Hin, sd) : !map4(&m->x2, a.x1, a.C1, a.Win, a.Hin, sd)) return 3;
+  if (!map4(&m->w, a.dy, a.N, a.Wout, a.Hout, 1)) return 4;
+  return 0;
+}
+
+cudaError_t launch_wgrad_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st) {
+  WgPlan p = wgrad_plan(a);
+  if (p.Cg <= 0) return cudaErrorInvalidValue;
+  const int cols = tmem_cols_of(p.tiles * a.N);
+  const size_t smem = wgrad_smem(p);
+  cudaError_t e = cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, smem_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  const int occ = std::max(1, std::min(smem_sm / (int)(smem + 2048), 512 / cols));
+  const int groups = (a.C1 + a.C2) / 32 / p.Cg;
+  // pixel ranges: fill the GPU once, but give every CTA at least 16 segments (each CTA ends
+  // with one FP32 atomic per weight of its group)
+  const int splits = std::max(1, std::min((sms * occ + groups - 1) / groups, (p.units + 15) / 16));
+  p.per_cta = (p.units + splits - 1) / splits;
+  const int gx = (p.units + p.per_cta - 1) / p.per_cta;
+  k_wgrad_tma<<<dim3(gx, groups), WT_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, p, cols, err);
   return cudaGetLastError();
 }
 

@@ -103,3 +103,33 @@ def test_halo_forward_matches_tile_path(un, Bmax, B, n):
         net.close()
     rel = np.linalg.norm(ys[1] - ys[0]) / np.linalg.norm(ys[0])
     assert rel <= 1e-2, rel
+
+
+@pytest.mark.parametrize("Bmax,B,n", [(2, 2, 32), (4, 3, 64), (1, 1, 128)])
+def test_layer_gradients_match_mma_sync(un, Bmax, B, n):
+    # Path 3 takes the weight gradient of every 3x3 layer whose input parts have a multiple of 32
+    # channels from the TMA-fed tcgen05 kernel (MN-major operands, 8 x 8-pixel segments: 33, 65
+    # and 129 node rows leave ragged segments, B < Bmax leaves images of the tensor maps unread)
+    # and the data gradient of the stride-1 layers whose reversed weights fit in shared memory
+    # from the halo kernel, each first contribution to an activation gradient overwriting it.
+    # Path 0 runs mma.sync everywhere.  The two forwards round BF16 activations differently, so
+    # per layer the largest difference is compared with the layer's largest gradient entry.
+    from oracle import unet as ou
+    p, x, t = _inputs(un, B, n, 16)
+    out = []
+    for path in (0, 3):
+        net = un.UNet(Bmax, n)
+        net.set_tensor_path(path)
+        net.set_params(p)
+        out.append(net.loss_grad(x, t))
+        net.close()
+    (l0, g0), (l3, g3) = out
+    assert abs(l3 - l0) <= 1e-2 * abs(l0)
+    off = 0
+    for name, k, _, ci, co, _ in ou.LAYERS:
+        for size in (k * k * ci * co, co):
+            a, b = g3[off:off + size], g0[off:off + size]
+            rel = np.abs(a - b).max() / np.abs(b).max()
+            assert rel <= 3e-2, (name, size, rel)
+            off += size
+    assert off == g0.size
