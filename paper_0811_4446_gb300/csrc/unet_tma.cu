@@ -563,64 +563,87 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
   const uint32_t tmem = tmem_sh;
   bool mma_ok = false;
 
-  if (warp == 0 && lane == 0) {
-    // ---- producer
+  if (warp == 0) {
+    // ---- producer warp: lane 0 waits for a free stage and posts its byte count, then each lane
+    // issues its boxes of the segment (box j: input slice (tap, cg) for j < 9 Cg, else dY slice
+    // j - 9 Cg); per lane at most two boxes, whose map, channel, tap offset and destination
+    // offset do not change from segment to segment
     const uint64_t pm1 = reinterpret_cast<uint64_t>(&mx1), pm2 = reinterpret_cast<uint64_t>(&mx2),
                    pmd = reinterpret_cast<uint64_t>(&mdy);
+    const int nbox = na + p.nb;
+    uint64_t bmap[2] = {pmd, pmd};
+    int bc[2] = {0, 0}, bdx[2] = {0, 0}, bdy[2] = {0, 0}, bs[2] = {1, 1};
+    uint32_t boff[2] = {0, 0};
+    int mine = 0;
+    for (int j = lane; j < nbox && mine < 2; j += 32, ++mine) {
+      boff[mine] = (uint32_t)j * WT_SLICE;
+      if (j < na) {
+        const int tap = j / p.Cg, cg = j - tap * p.Cg, kh = tap / 3, kw = tap - kh * 3;
+        const int sl = grp * p.Cg + cg;
+        bmap[mine] = sl < p.c1 ? pm1 : pm2;
+        bc[mine] = (sl < p.c1 ? sl : sl - p.c1) * 32;
+        bdx[mine] = kw - 1;
+        bdy[mine] = kh - 1;
+        bs[mine] = a.stride;
+      } else {
+        bc[mine] = 32 * (j - na);
+      }
+    }
     long g = 0;
-    for (int u = u0; u < u1 && !*abort; ++u, ++g) {
+    for (int u = u0; u < u1; ++u, ++g) {
       const int s = (int)(g % p.S);
-      const uint32_t use = (uint32_t)(g / p.S);
-      if (use > 0 && !wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort)) break;
+      const uint32_t use = (uint32_t)(g / p.S), bar = saddr(&full[s]);
+      int ok = 1;
+      if (lane == 0) {
+        if (use > 0) ok = wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort);
+        if (ok)
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes) : "memory");
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       const int b = u / p.per_img, r = u - b * p.per_img;
       const int y0 = (r / p.tx) * p.R, x0 = (r % p.tx) * p.P;
-      const uint32_t sa = base + (uint32_t)s * st_bytes, bar = saddr(&full[s]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes) : "memory");
-      for (int tap = 0; tap < 9; ++tap) {
-        const int kh = tap / 3, kw = tap - kh * 3;
-        const int xi = x0 * a.stride + kw - 1, yi = y0 * a.stride + kh - 1;
-        for (int cg = 0; cg < p.Cg; ++cg) {
-          const int q = grp * p.Cg + cg;
-          const uint64_t mx = q < p.c1 ? pm1 : pm2;
-          const int cc = (q < p.c1 ? q : q - p.c1) * 32;
-          asm volatile(
-              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-              ::"r"(sa + (uint32_t)(tap * p.Cg + cg) * WT_SLICE), "l"(mx), "r"(cc), "r"(xi), "r"(yi), "r"(b), "r"(bar)
-              : "memory");
-        }
-      }
-      for (int j = 0; j < p.nb; ++j)
+      const uint32_t sa = base + (uint32_t)s * st_bytes;
+      for (int i = 0; i < mine; ++i)
         asm volatile(
             "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-            ::"r"(sa + (uint32_t)(na + j) * WT_SLICE), "l"(pmd), "r"(32 * j), "r"(x0), "r"(y0), "r"(b), "r"(bar)
+            ::"r"(sa + boff[i]), "l"(bmap[i]), "r"(bc[i]), "r"(x0 * bs[i] + bdx[i]), "r"(y0 * bs[i] + bdy[i]), "r"(b),
+              "r"(bar)
             : "memory");
     }
-    // loads still in flight: the last min(S, g) issued, each the latest on its stage
-    volatile int never = 0;
-    for (long j = g > p.S ? g - p.S : 0; j < g; ++j)
-      wait_bounded(saddr(&full[j % p.S]), (uint32_t)((j / p.S) & 1), &never);
+    // loads still in flight: the last min(S, g) stages posted, each the latest on its stage
+    if (lane == 0) {
+      volatile int never = 0;
+      for (long j = g > p.S ? g - p.S : 0; j < g; ++j)
+        wait_bounded(saddr(&full[j % p.S]), (uint32_t)((j / p.S) & 1), &never);
+    }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: every tile accumulates over every segment of the CTA
+    // ---- MMA issuer: every tile accumulates over every segment of the CTA.  The descriptors of
+    // stage 0 are built once; a stage, a tile (four slices) and a K step of 16 pixels (two
+    // 512-byte atoms) only add to the address field (bytes >> 4; addresses stay below 2^18).
     const uint32_t idesc = idesc_bf16_tma(128, a.N) | (1u << 15) | (1u << 16);  // A and B MN-major
+    const uint64_t dA0 = mn_sw64_desc(base), dB0 = mn_sw64_desc(base + (uint32_t)na * WT_SLICE);
+    const uint64_t d_stage = st_bytes >> 4, d_tile = (4 * WT_SLICE) >> 4;
     long g = 0;
     bool ok = true;
     for (int u = u0; u < u1; ++u, ++g) {
       const int s = (int)(g % p.S);
       if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / p.S) & 1), abort))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = base + (uint32_t)s * st_bytes, sb = sa + (uint32_t)na * WT_SLICE;
-      for (int t = 0; t < p.tiles; ++t) {
-#pragma unroll
-        for (int kk = 0; kk < WT_PIX / 16; ++kk) {
-          const uint64_t da = mn_sw64_desc(sa + (uint32_t)(4 * t) * WT_SLICE + kk * 1024);
-          const uint64_t db = mn_sw64_desc(sb + kk * 1024);
-          const uint32_t acc = (g > 0 || kk > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(t * a.N)),
-              "l"(da), "l"(db), "r"(idesc), "r"(acc));
-        }
-      }
+      const uint64_t db = dB0 + (uint64_t)s * d_stage;
+      uint64_t da = dA0 + (uint64_t)s * d_stage;
+      uint32_t dt = tmem;
+      const uint32_t first = g > 0 ? 1u : 0u;
+      for (int t = 0; t < p.tiles; ++t, da += d_tile, dt += (uint32_t)a.N)
+        asm volatile(
+            "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
+            " setp.ne.b32 p, %4, 0;\n setp.eq.b32 q, %4, %4;\n"
+            " add.s64 a1, %1, 64;\n add.s64 a2, %1, 128;\n add.s64 a3, %1, 192;\n"
+            " add.s64 b1, %2, 64;\n add.s64 b2, %2, 128;\n add.s64 b3, %2, 192;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(dt),
+            "l"(da), "l"(db), "r"(idesc), "r"(first));
       commit(saddr(&empty[s]));
     }
     commit(saddr(&mma_done));
