@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     const uint32_t idesc = idesc_bf16_tma(TM_X * TM_Y, BN);
+    const uint64_t dA0 = sw64_desc(base);
     long g = 0;
     int j = 0;  // tiles of this CTA so far
     bool ok = true;
@@ -181,16 +182,15 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
         const int s = (int)(g % S);
         if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / S) & 1), abort))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = base + (uint32_t)s * st_bytes, sb = sa + a_bytes;
-#pragma unroll
-        for (int kk = 0; kk < TM_CH / 16; ++kk) {
-          const uint64_t da = sw64_desc(sa + kk * 32), db = sw64_desc(sb + kk * 32);
-          const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_t),
-              "l"(da), "l"(db), "r"(idesc), "r"(acc));
-        }
+        // stage s: A at dA0 + s * st_bytes, B a_bytes after it; the second K = 16 step 32 bytes on
+        const uint64_t da = dA0 + (uint64_t)((uint32_t)s * (st_bytes >> 4));
+        asm volatile(
+            "{\n .reg .pred p, q;\n .reg .b64 a1, b1, b0;\n"
+            " setp.ne.b32 p, %3, 0;\n setp.eq.b32 q, %3, %3;\n"
+            " add.s64 b0, %1, %4;\n add.s64 a1, %1, 2;\n add.s64 b1, b0, 2;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, b0, %2, p;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %2, q;\n}\n" ::"r"(acc_t),
+            "l"(da), "r"(idesc), "r"(k > 0 ? 1u : 0u), "l"((uint64_t)(a_bytes >> 4)));
         commit(saddr(&empty[s]));
       }
       if (ok) commit(saddr(&acc_full[ab]));
@@ -334,44 +334,57 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
   const uint32_t tmem = tmem_sh;
   const int c1 = a.C1 / TM_CH, nch = Ctot / TM_CH;
 
-  if (warp == 0 && lane == 0) {
-    // ---- producer: the weight matrix once, then the halo of every chunk of every tile
+  if (warp == 0) {
+    // ---- producer warp: the weight matrix once, then the halo of every chunk of every tile;
+    // lane 0 waits for a free stage and posts its byte count, lanes 0-3 load one 8-channel
+    // group each
     const uint64_t pm1 = reinterpret_cast<uint64_t>(&mx1), pm2 = reinterpret_cast<uint64_t>(&mx2),
                    pmw = reinterpret_cast<uint64_t>(&mw);
     const uint32_t wb = saddr(&wfull);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wb), "r"(wbytes) : "memory");
-    for (int i = 0; i < nkb; ++i)
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-          ::"r"(wbase + (uint32_t)i * wblk), "l"(pmw), "r"(i * TM_CH), "r"(0), "r"(wb)
-          : "memory");
+    if (lane == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wb), "r"(wbytes) : "memory");
+      for (int i = 0; i < nkb; ++i)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(wbase + (uint32_t)i * wblk), "l"(pmw), "r"(i * TM_CH), "r"(0), "r"(wb)
+            : "memory");
+    }
     long g = 0;
-    for (int t = blockIdx.x; t < tg.ntiles && !*abort; t += gridDim.x) {
+    bool go = true;
+    for (int t = blockIdx.x; t < tg.ntiles && go; t += gridDim.x) {
       int x0, y0, b;
       halo_origin(tg, t, x0, y0, b);
       for (int c = 0; c < nch; ++c, ++g) {
         const int s = (int)(g % HSTAGES);
-        const uint32_t use = (uint32_t)(g / HSTAGES);
-        if (use > 0 && !wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort)) break;
-        const uint64_t mx = c < c1 ? pm1 : pm2;
-        const int cc = (c < c1 ? c : c - c1) * TM_CH;
-        const uint32_t sa = hbase + (uint32_t)s * HSTAGE, bar = saddr(&full[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(HTX) : "memory");
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
+        const uint32_t use = (uint32_t)(g / HSTAGES), bar = saddr(&full[s]);
+        int ok = 1;
+        if (lane == 0) {
+          ok = !*abort && (use == 0 || wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort));
+          if (ok) asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(HTX) : "memory");
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          go = false;
+          break;
+        }
+        if (lane < 4)
           asm volatile(
               "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-              ::"r"(sa + (uint32_t)q * HPITCH), "l"(mx), "r"(cc + 8 * q), "r"(x0 - 1), "r"(y0 - 1), "r"(b), "r"(bar)
+              ::"r"(hbase + (uint32_t)s * HSTAGE + (uint32_t)lane * HPITCH), "l"(c < c1 ? pm1 : pm2),
+                "r"((c < c1 ? c : c - c1) * TM_CH + 8 * lane), "r"(x0 - 1), "r"(y0 - 1), "r"(b), "r"(bar)
               : "memory");
       }
     }
-    volatile int never = 0;
-    wait_bounded(wb, 0, &never);
-    for (long j = g > HSTAGES ? g - HSTAGES : 0; j < g; ++j)
-      wait_bounded(saddr(&full[j % HSTAGES]), (uint32_t)((j / HSTAGES) & 1), &never);
+    if (lane == 0) {
+      volatile int never = 0;
+      wait_bounded(wb, 0, &never);
+      for (long j = g > HSTAGES ? g - HSTAGES : 0; j < g; ++j)
+        wait_bounded(saddr(&full[j % HSTAGES]), (uint32_t)((j / HSTAGES) & 1), &never);
+    }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     const uint32_t idesc = idesc_bf16_tma(HX * HY, BN);
+    const uint64_t dH0 = nosw_desc(hbase, HPITCH, HW * 16), dW0 = sw64_desc(wbase);
+    const uint64_t w_tap = (uint64_t)(((uint32_t)nch * wblk) >> 4);
     bool ok = wait_bounded(saddr(&wfull), 0, abort);
     long g = 0;
     int j = 0;
@@ -384,22 +397,21 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
         const int s = (int)(g % HSTAGES);
         if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / HSTAGES) & 1), abort))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = hbase + (uint32_t)s * HSTAGE;
-        for (int tap = 0; tap < 9; ++tap) {
-          const int kh = tap / 3, kw = tap - kh * 3;
-          const uint32_t wblock = wbase + (uint32_t)((tap * Ctot + c * TM_CH) / TM_CH) * wblk;
+        // descriptors advance by constants: tap (kh, kw) = window (kh * 10 + kw) * 16 bytes on, its
+        // weight block nch * wblk bytes on; the second K = 16 step two planes / 32 bytes on
+        const uint64_t da0 = dH0 + (uint64_t)((uint32_t)s * (HSTAGE >> 4));
+        const uint64_t db0 = dW0 + (uint64_t)((uint32_t)c * (wblk >> 4));
+        const uint32_t first = c > 0 ? 1u : 0u;
 #pragma unroll
-          for (int kk = 0; kk < TM_CH / 16; ++kk) {
-            const uint64_t da = nosw_desc(sa + (uint32_t)(2 * kk) * HPITCH + (uint32_t)(kh * HW + kw) * 16, HPITCH,
-                                          HW * 16);
-            const uint64_t db = sw64_desc(wblock + kk * 32);
-            const uint32_t acc = (c > 0 || tap > 0 || kk > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_t),
-                "l"(da), "l"(db), "r"(idesc), "r"(acc));
-          }
-        }
+        for (int tap = 0; tap < 9; ++tap)
+          asm volatile(
+              "{\n .reg .pred p, q;\n .reg .b64 a1, b1;\n"
+              " setp.ne.b32 p, %4, 0;\n setp.eq.b32 q, %4, %4;\n"
+              " add.s64 a1, %1, %5;\n add.s64 b1, %2, 2;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n}\n" ::"r"(acc_t),
+              "l"(da0 + (uint64_t)((tap / 3) * HW + tap % 3)), "l"(db0 + (uint64_t)tap * w_tap), "r"(idesc),
+              "r"(tap > 0 ? 1u : first), "n"((2 * HPITCH) >> 4));
         commit(saddr(&empty[s]));
       }
       if (ok) commit(saddr(&acc_full[ab]));
@@ -488,25 +500,25 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
 //
 // dW[m][n] = sum over output pixels k of A[m][k] dY[k][n], m = (tap, input channel) in the order of
 // the weight matrix, n = output channel.  Both operands are pixel-major in memory (NHWC), so they
-// enter the tensor core MN-major: a TMA box of 32 channels x 64 output pixels (P columns x R rows
-// of one image; for stride 2 the box spans 2P x 2R input pixels traversed with element strides 2)
-// lands as a stack of eight 64-byte-swizzle atoms (32 channels x 8 pixels, 512 bytes each), a
-// 4 KB "slice".  A CTA owns a group of Cg 32-channel input slices for all nine taps and a range of
-// pixel segments; per segment it loads 9 Cg input slices (one per tap and slice: the window the
-// tap reads) and N / 32 slices of dY.  The input slices are stored in the order of m, so any four
-// consecutive ones form the A operand of one M = 128 MMA (atoms 4 KB apart: the descriptor's
-// leading offset); the accumulators of all ceil(9 Cg / 4) such tiles stay in TMEM over the CTA's
-// whole pixel range and are added into dW once at the end (FP32 atomics).  A last tile that runs
-// past the 9 Cg slices reads the slices after them (or the guard after the ring): those TMEM rows
-// are discarded.  Warp roles as in the forward kernels: lane 0 of warp 0 loads, lane 0 of warp 1
+// enter the tensor core MN-major: a TMA box of 32 channels x a segment of 64 or 128 output pixels
+// (P columns x R rows of one image; for stride 2 the box spans 2P x 2R input pixels traversed
+// with element strides 2) lands as a stack of 64-byte-swizzle atoms (32 channels x 8 pixels, 512
+// bytes each), a "slice".  A CTA owns a group of Cg 32-channel input slices for all nine taps and
+// a range of pixel segments; per segment it loads 9 Cg input slices (one per tap and slice: the
+// window the tap reads) and N / 32 slices of dY.  The input slices are stored in the order of m,
+// so any four consecutive ones form the A operand of one M = 128 MMA (atoms one slice apart: the
+// descriptor's leading offset); the accumulators of all ceil(9 Cg / 4) such tiles stay in TMEM
+// over the CTA's whole pixel range and are added into dW once at the end (FP32 atomics).  A last
+// tile that runs past the 9 Cg slices reads the slices after them (or the guard after the ring):
+// those TMEM rows are discarded.  Warp roles: warp 0 loads (each lane its boxes), lane 0 of warp 1
 // issues the MMAs, all four warps drain TMEM; every wait is bounded.
 constexpr int WT_THREADS = 128;
-constexpr int WT_PIX = 64;                       // output pixels per segment (four K = 16 steps)
-constexpr uint32_t WT_SLICE = WT_PIX * 64;       // 32 channels x 64 pixels of bf16
-constexpr int WT_MAXS = 4;
+constexpr int WT_MAXS = 6;
 
 struct WgPlan {
-  int P, R;            // segment: P output columns x R output rows (P * R = 64)
+  int pix;             // output pixels per segment: 64 or 128 (four or eight K = 16 steps)
+  uint32_t slice;      // bytes of one slice: 32 channels x pix pixels of bf16
+  int P, R;            // segment: P output columns x R output rows (P * R = pix)
   int tx, per_img;     // segments per output row band, per image
   int units;           // segments of the batch
   int c1;              // 32-channel slices of input part 1 (part 2 follows)
@@ -517,10 +529,10 @@ struct WgPlan {
   int per_cta;         // segments per CTA
 };
 
-__device__ __forceinline__ uint64_t mn_sw64_desc(uint32_t a) {
+__device__ __forceinline__ uint64_t mn_sw64_desc(uint32_t a, uint32_t slice) {
   uint64_t d = 0;
   d |= (uint64_t)((a >> 4) & 0x3FFFu);
-  d |= (uint64_t)((WT_SLICE >> 4) & 0x3FFFu) << 16;  // LBO: next 32 channels (next atom along M / N)
+  d |= (uint64_t)((slice >> 4) & 0x3FFFu) << 16;     // LBO: next 32 channels (next atom along M / N)
   d |= (uint64_t)(512u >> 4) << 32;                  // SBO: next 8 pixels (next atom along K)
   d |= (uint64_t)1u << 46;
   d |= (uint64_t)4u << 61;
@@ -534,7 +546,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
   const int na = 9 * p.Cg;
-  const uint32_t st_bytes = (uint32_t)(na + p.nb) * WT_SLICE;
+  const uint32_t st_bytes = (uint32_t)(na + p.nb) * p.slice;
   __shared__ __align__(8) uint64_t full[WT_MAXS], empty[WT_MAXS], mma_done;
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
@@ -576,7 +588,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
     uint32_t boff[2] = {0, 0};
     int mine = 0;
     for (int j = lane; j < nbox && mine < 2; j += 32, ++mine) {
-      boff[mine] = (uint32_t)j * WT_SLICE;
+      boff[mine] = (uint32_t)j * p.slice;
       if (j < na) {
         const int tap = j / p.Cg, cg = j - tap * p.Cg, kh = tap / 3, kw = tap - kh * 3;
         const int sl = grp * p.Cg + cg;
@@ -621,8 +633,8 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
     // stage 0 are built once; a stage, a tile (four slices) and a K step of 16 pixels (two
     // 512-byte atoms) only add to the address field (bytes >> 4; addresses stay below 2^18).
     const uint32_t idesc = idesc_bf16_tma(128, a.N) | (1u << 15) | (1u << 16);  // A and B MN-major
-    const uint64_t dA0 = mn_sw64_desc(base), dB0 = mn_sw64_desc(base + (uint32_t)na * WT_SLICE);
-    const uint64_t d_stage = st_bytes >> 4, d_tile = (4 * WT_SLICE) >> 4;
+    const uint64_t dA0 = mn_sw64_desc(base, p.slice), dB0 = mn_sw64_desc(base + (uint32_t)na * p.slice, p.slice);
+    const uint64_t d_stage = st_bytes >> 4, d_tile = (4 * p.slice) >> 4;
     long g = 0;
     bool ok = true;
     for (int u = u0; u < u1; ++u, ++g) {
@@ -633,17 +645,20 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
       uint64_t da = dA0 + (uint64_t)s * d_stage;
       uint32_t dt = tmem;
       const uint32_t first = g > 0 ? 1u : 0u;
+      // four K = 16 steps (two 512-byte atoms each) per block; a 128-pixel segment takes two blocks
+      const int blocks = p.pix / 64;
       for (int t = 0; t < p.tiles; ++t, da += d_tile, dt += (uint32_t)a.N)
-        asm volatile(
-            "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
-            " setp.ne.b32 p, %4, 0;\n setp.eq.b32 q, %4, %4;\n"
-            " add.s64 a1, %1, 64;\n add.s64 a2, %1, 128;\n add.s64 a3, %1, 192;\n"
-            " add.s64 b1, %2, 64;\n add.s64 b2, %2, 128;\n add.s64 b3, %2, 192;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(dt),
-            "l"(da), "l"(db), "r"(idesc), "r"(first));
+        for (int h = 0; h < blocks; ++h)
+          asm volatile(
+              "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
+              " setp.ne.b32 p, %4, 0;\n setp.eq.b32 q, %4, %4;\n"
+              " add.s64 a1, %1, 64;\n add.s64 a2, %1, 128;\n add.s64 a3, %1, 192;\n"
+              " add.s64 b1, %2, 64;\n add.s64 b2, %2, 128;\n add.s64 b3, %2, 192;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(dt),
+              "l"(da + (uint64_t)(h * 256)), "l"(db + (uint64_t)(h * 256)), "r"(idesc), "r"(h > 0 ? 1u : first));
       commit(saddr(&empty[s]));
     }
     commit(saddr(&mma_done));
@@ -853,43 +868,63 @@ cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cuda
 
 namespace {
 
-// Segment shape P x R (P * R = 64) with the fewest padded output pixels; the channel group: the
-// most input slices per CTA whose accumulators fit in the 512 TMEM columns and whose stage fits
-// at least twice in shared memory (fewer dY re-reads, fewer partial M tiles).
+// Plan: the channel group Cg (a divisor of the input's 32-channel slices whose ceil(9 Cg / 4)
+// accumulator tiles fit in the 512 TMEM columns) and the segment of 64 or 128 pixels whose stage
+// fits at least twice in shared memory, chosen by a model of the load side, which sets the pace
+// (measured: a TMA box costs about 100 SM cycles plus one per 64-byte line it brings): groups x
+// boxes x (100 + pixels) / pixels per output pixel, padding included.  The segment shape P x R:
+// the one with the fewest padded pixels.
 constexpr size_t WT_SMEM_MAX = 225 * 1024;
 
 WgPlan wgrad_plan(const ConvArgs &a) {
   WgPlan p;
   std::memset(&p, 0, sizeof(p));
+  p.c1 = a.C1 / 32;
+  const int c32 = (a.C1 + a.C2) / 32;
+  p.nb = a.N / 32;
+  double best_cost = 0.0;
+  for (int cg = c32; cg >= 1; --cg) {
+    if (c32 % cg) continue;
+    const int tiles = (9 * cg + 3) / 4;
+    if (tiles * a.N > 512) continue;
+    for (int pix = 64; pix <= 128; pix *= 2) {
+      const size_t slice = (size_t)pix * 64, stage = (size_t)(9 * cg + p.nb) * slice;
+      const size_t guard = (size_t)std::max(0, 4 * tiles - 9 * cg - p.nb) * slice;
+      const int S = (int)std::min<size_t>(WT_MAXS, (WT_SMEM_MAX - 1024 - guard) / stage);
+      if (S < 2) continue;
+      long padded = -1;  // output pixels of the best segment shape, padding included
+      for (int P = 8; P <= pix; P *= 2) {
+        const int R = pix / P;
+        const long n = (long)((a.Wout + P - 1) / P) * P * (long)((a.Hout + R - 1) / R) * R;
+        if (padded < 0 || n < padded) padded = n;
+      }
+      const double cost = (double)(c32 / cg) * (9 * cg + p.nb) * (100.0 + pix) / pix * (double)padded;
+      if (p.Cg == 0 || cost < best_cost) {
+        best_cost = cost;
+        p.Cg = cg;
+        p.tiles = tiles;
+        p.pix = pix;
+        p.slice = (uint32_t)slice;
+        p.S = S;
+      }
+    }
+  }
+  if (p.Cg == 0) return p;
   long best = -1;
-  for (int P = 8; P <= 64; P *= 2) {
-    const int R = WT_PIX / P;
+  for (int P = 8; P <= p.pix; P *= 2) {
+    const int R = p.pix / P;
     const long padded = (long)((a.Wout + P - 1) / P) * P * (long)((a.Hout + R - 1) / R) * R;
     if (best < 0 || padded < best) best = padded, p.P = P, p.R = R;
   }
   p.tx = (a.Wout + p.P - 1) / p.P;
   p.per_img = p.tx * ((a.Hout + p.R - 1) / p.R);
   p.units = p.per_img * a.Bn;
-  p.c1 = a.C1 / 32;
-  const int c32 = (a.C1 + a.C2) / 32;
-  p.nb = a.N / 32;
-  for (int cg = c32; cg >= 1; --cg) {
-    if (c32 % cg) continue;
-    const int tiles = (9 * cg + 3) / 4;
-    const size_t stage = (size_t)(9 * cg + p.nb) * WT_SLICE;
-    const size_t guard = (size_t)std::max(0, 4 * tiles - 9 * cg - p.nb) * WT_SLICE;
-    if (tiles * a.N > 512 || 1024 + 2 * stage + guard > WT_SMEM_MAX) continue;
-    p.Cg = cg;
-    p.tiles = tiles;
-    p.S = (int)std::min<size_t>(WT_MAXS, (WT_SMEM_MAX - 1024 - guard) / stage);
-    break;
-  }
   return p;
 }
 
 size_t wgrad_smem(const WgPlan &p) {
-  const size_t stage = (size_t)(9 * p.Cg + p.nb) * WT_SLICE;
-  const size_t guard = (size_t)std::max(0, 4 * p.tiles - 9 * p.Cg - p.nb) * WT_SLICE;
+  const size_t stage = (size_t)(9 * p.Cg + p.nb) * p.slice;
+  const size_t guard = (size_t)std::max(0, 4 * p.tiles - 9 * p.Cg - p.nb) * p.slice;
   return 1024 + (size_t)p.S * stage + guard;
 }
 
