@@ -56,9 +56,9 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
  * user makes.  The network runs on path 3 (the default), which assigns one kernel to each
  * layer shape: the halo-load tcgen05 kernel (the forward of stride-1 layers whose weights fit in
  * 72 KB, and their data gradient where the reversed weights fit), the TMA-tile tcgen05 forward
- * (the other 3x3 layers with 32-channel input parts), the TMA-fed tcgen05 weight gradient (3x3
- * layers with 32-channel input parts), the gathering tcgen05 kernels (the 8-channel first layer,
- * the other data gradients) and the FP32 CUDA-core head.  Paths 0-2 keep the earlier kernels
+ * (the other 3x3 layers with 32-channel input parts), the TMA-fed tcgen05 weight gradient (every
+ * 3x3 layer), the gathering tcgen05 kernels (the forward of the 8-channel first layer, the other
+ * data gradients) and the FP32 CUDA-core head (forward and backward).  Paths 0-2 keep the earlier kernels
  * of those layers so that the tests can compare each layer's kernel with the one it replaced
  * (same operands, another order of the sums) and the benchmark can report what each
  * replacement gained:
@@ -75,9 +75,9 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
  *       resident in shared memory and load one 10 x 18-pixel halo per 32-channel chunk for all
  *       nine taps (tiles of 8 x 16 output pixels), the data gradient of those layers runs on the
  *       same kernel as a forward convolution of the output gradient with the taps reversed, and
- *       the weight gradient of the 3x3 layers with 32-channel input parts takes both operands
- *       by TMA tiled loads (8 x 8-pixel segments, one load per tap and 32-channel slice); their
- *       sums round in another order.
+ *       the weight gradient of the 3x3 layers takes both operands by TMA tiled loads (segments
+ *       of 64 or 128 output pixels, one load per tap and 32-channel slice, or 8-channel slice
+ *       for the first layer); their sums round in another order.
  * Any other value returns MG_EINVAL.  A tcgen05 kernel whose bounded wait expires makes the next
  * call return MG_ETIMEOUT. */
 int mg_unet_set_tensor_path(mg_unet *n, int path);

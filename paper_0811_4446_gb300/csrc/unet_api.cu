@@ -220,15 +220,17 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
   ConvArgs a = conv_args(n, l, B, in1, in2);
   const size_t P = (size_t)a.Pout;
   const int cop = a.Cout;
-  UK(launch_relu_bwd(out ? out->g : dout32, out ? out->a : nullptr, n->dpre, P * cop, out ? kL[l].relu : 0, n->st));
-  UK(launch_bias_grad(n->dpre, n->grad + n->boff[l], (int)P, cop, kL[l].co, n->st));
+  UK(launch_relu_bias_bwd(out ? out->g : dout32, out ? out->a : nullptr, n->dpre, n->grad + n->boff[l], (int)P, cop,
+                          kL[l].co, out ? kL[l].relu : 0, n->st));
   // weight gradient: GEMM (kh, kw, ci) x cop over the output pixels, split over pixel ranges
   ConvArgs w = a;
   w.M = a.Kf; w.N = cop; w.K = a.Pout;
   w.dy = n->dpre;
   w.dw = n->dwpad;
   UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), n->st));
-  if (n->use_tc == 3 && wgrad_tma_supported(w)) {
+  if (n->use_tc && conv1x1_bwd_supported(a)) {
+    UK(launch_conv1x1_wgrad(a, n->dpre, n->dwpad, n->st));
+  } else if (n->use_tc == 3 && wgrad_tma_supported(w)) {
     const void *key[3] = {w.x1, w.x2, w.dy};
     if (std::memcmp(key, n->wmap_key[l], sizeof(key)) != 0) {
       if (int rc = make_wgrad_maps(w, n->Bmax, &n->wmaps[l]))
@@ -272,6 +274,10 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
       UK(launch_conv_halo(f, n->dmaps[l], n->tc_err, n->st));
       return MG_OK;
     }
+  }
+  if (want_dx && n->use_tc && conv1x1_bwd_supported(a)) {
+    UK(launch_conv1x1_dgrad(a, n->dpre, n->wd[l], in1.g, dacc, n->st));
+    return MG_OK;
   }
   if (want_dx) {
     ConvArgs d = a;

@@ -61,9 +61,14 @@ cudaError_t launch_conv_halo(const ConvArgs &a, const ConvMaps &m, int *err, cud
 // FP32-output 1x1 convolution to 8 channels (the head) on the CUDA cores
 bool conv1x1_f32_supported(const ConvArgs &a);
 cudaError_t launch_conv1x1_f32(const ConvArgs &a, cudaStream_t st);
-cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
-                            cudaStream_t st);
-cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st);
+// ReLU mask, bf16 rounding of the output gradient and the bias gradient in one pass
+cudaError_t launch_relu_bias_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, float *db, int P,
+                                 int C, int Creal, int relu, cudaStream_t st);
+// backward of the 1x1 head (C1 <= 64 input channels, 8 padded output channels) on the CUDA cores
+bool conv1x1_bwd_supported(const ConvArgs &a);
+cudaError_t launch_conv1x1_wgrad(const ConvArgs &a, const __nv_bfloat16 *dy, float *dw, cudaStream_t st);
+cudaError_t launch_conv1x1_dgrad(const ConvArgs &a, const __nv_bfloat16 *dy, const __nv_bfloat16 *wd, float *dx,
+                                 int dacc, cudaStream_t st);
 cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,

@@ -203,48 +203,39 @@ cudaError_t launch_conv(const ConvArgs &a, int mode, int splits, cudaStream_t st
 
 // dPre = dOut * (out > 0) for ReLU layers (relu = 0: plain copy), converted to bf16; eight
 // consecutive elements per thread (n8 = n / 8, n a multiple of 8: whole 8-channel groups).
-__global__ void k_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n8, int relu) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 d0 = reinterpret_cast<const float4 *>(dout)[2 * i], d1 = reinterpret_cast<const float4 *>(dout)[2 * i + 1];
-    float v[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-    if (relu) {
-      const uint4 o = reinterpret_cast<const uint4 *>(out)[i];
-      const __nv_bfloat16 *ob = reinterpret_cast<const __nv_bfloat16 *>(&o);
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        if (!(__bfloat162float(ob[e]) > 0.f)) v[e] = 0.f;
-    }
-    uint32_t pk[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-      pk[e] = *reinterpret_cast<const uint32_t *>(&h);
-    }
-    reinterpret_cast<uint4 *>(dpre)[i] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-  }
-}
-
-cudaError_t launch_relu_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, size_t n, int relu,
-                            cudaStream_t st) {
-  if (n % 8) return cudaErrorInvalidValue;
-  const size_t n8 = n / 8;
-  k_relu_bwd<<<(unsigned)std::min<size_t>((n8 + 255) / 256, 152 * 16), 256, 0, st>>>(dout, out, dpre, n8, relu);
-  return cudaGetLastError();
-}
-
-// db[c] += sum over pixels of dpre[p][c] for c < Creal (C = channel stride, a multiple of 8,
-// at most 256).  A thread sums the 8 channels of one 16-byte group over a pixel-strided set of
-// rows; the block adds its rows up in shared memory and makes one atomic add per channel.
-__global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal) {
+// Backward of a layer's output stage: dpre = dout (FP32) masked by out > 0 for ReLU layers,
+// rounded to bf16 (the operand of the weight and data gradients), and db[c] += sum over pixels
+// of dpre[p][c] for c < Creal (C = channel stride, a multiple of 8, at most 256), in one pass.
+// A thread takes one 16-byte group of 8 channels of a pixel-strided set of rows (a warp reads
+// whole rows: contiguous bytes); the block adds its rows up in shared memory and makes one
+// atomic add per channel.
+__global__ void __launch_bounds__(256) k_relu_bias_bwd(const float *dout, const __nv_bfloat16 *out,
+                                                       __nv_bfloat16 *dpre, float *db, int P, int C, int Creal,
+                                                       int relu) {
   const int G = C / 8, rows = 256 / G;
   const int g = threadIdx.x % G, r = threadIdx.x / G;
   float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (r < rows)
     for (int p = blockIdx.x * rows + r; p < P; p += gridDim.x * rows) {
-      const uint4 q = *reinterpret_cast<const uint4 *>(dpre + (size_t)p * C + 8 * g);
-      const __nv_bfloat16 *hq = reinterpret_cast<const __nv_bfloat16 *>(&q);
+      const size_t i = (size_t)p * G + g;
+      const float4 d0 = reinterpret_cast<const float4 *>(dout)[2 * i], d1 = reinterpret_cast<const float4 *>(dout)[2 * i + 1];
+      float v[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+      if (relu) {
+        const uint4 o = reinterpret_cast<const uint4 *>(out)[i];
+        const __nv_bfloat16 *ob = reinterpret_cast<const __nv_bfloat16 *>(&o);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) s[e] += __bfloat162float(hq[e]);
+        for (int e = 0; e < 8; ++e)
+          if (!(__bfloat162float(ob[e]) > 0.f)) v[e] = 0.f;
+      }
+      uint32_t pk[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+        pk[e] = *reinterpret_cast<const uint32_t *>(&h);
+        s[2 * e] += __low2float(h);
+        s[2 * e + 1] += __high2float(h);
+      }
+      reinterpret_cast<uint4 *>(dpre)[i] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
   __shared__ float sh[256][9];
 #pragma unroll
@@ -258,10 +249,12 @@ __global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16 *dpre, fl
   }
 }
 
-cudaError_t launch_bias_grad(const __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st) {
-  if (C % 8 || C > 256 || Creal > C) return cudaErrorInvalidValue;
+cudaError_t launch_relu_bias_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, float *db, int P,
+                                 int C, int Creal, int relu, cudaStream_t st) {
+  if (C % 8 || C > 256 || Creal > C || (relu && !out)) return cudaErrorInvalidValue;
   const int rows = 256 / (C / 8);
-  k_bias_grad<<<std::max(1, std::min(152 * 4, (P + rows - 1) / rows)), 256, 0, st>>>(dpre, db, P, C, Creal);
+  k_relu_bias_bwd<<<std::max(1, std::min(152 * 4, (P + rows - 1) / rows)), 256, 0, st>>>(dout, out, dpre, db, P, C,
+                                                                                         Creal, relu);
   return cudaGetLastError();
 }
 
@@ -466,6 +459,106 @@ cudaError_t launch_conv1x1_f32(const ConvArgs &a, cudaStream_t st) {
   if (!conv1x1_f32_supported(a)) return cudaErrorInvalidValue;
   const int blocks = std::max(1, std::min((a.Pout + 255) / 256, 152 * 8));
   k_conv1x1_f32<<<blocks, 256, 0, st>>>(a.x1, a.w, a.bias, a.Nreal, a.C1, a.Pout, a.y32);
+  return cudaGetLastError();
+}
+
+// Backward of the 1x1 head (C <= 64 input channels, 8 output channels): memory-bound, on the
+// CUDA cores.  Weight gradient dw[c][o] += sum over pixels of x[p][c] dy[p][o]: a block stages
+// 128 pixels of x and dy in shared memory as FP32 (every thread loading several 16-byte groups
+// at once) and thread (o, c) accumulates its entry over the block's pixels (a warp reads 32
+// consecutive channels of one pixel and one broadcast dy value), then one atomic add per entry.
+constexpr int K1_TP = 128;
+
+__global__ void __launch_bounds__(512) k_conv1x1_wgrad(const __nv_bfloat16 *x, int C, const __nv_bfloat16 *dy, int P,
+                                                       float *dw) {
+  __shared__ float xs[K1_TP][65];
+  __shared__ float ds[K1_TP][8];
+  const int tid = threadIdx.x, c = tid % C, o = tid / C, G = C / 8;
+  float acc = 0.f;
+  for (int p0 = blockIdx.x * K1_TP; p0 < P; p0 += gridDim.x * K1_TP) {
+    // K1_TP * G groups over blockDim = 8 C = 64 G threads: K1_TP / 64 per thread, issued before
+    // any is used
+    constexpr int per = K1_TP / 64;
+    uint4 q[per];
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      q[k] = make_uint4(0u, 0u, 0u, 0u);
+      const int i = tid + k * blockDim.x, pp = i / G, g = i - pp * G;
+      if (p0 + pp < P) q[k] = *reinterpret_cast<const uint4 *>(x + (size_t)(p0 + pp) * C + 8 * g);
+    }
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      const int i = tid + k * blockDim.x, pp = i / G, g = i - pp * G;
+      const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q[k]);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) xs[pp][8 * g + e] = __bfloat162float(h[e]);
+    }
+    for (int i = tid; i < K1_TP; i += blockDim.x) {
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (p0 + i < P) q = *reinterpret_cast<const uint4 *>(dy + (size_t)(p0 + i) * 8);
+      const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) ds[i][e] = __bfloat162float(h[e]);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int pp = 0; pp < K1_TP; ++pp) acc = fmaf(xs[pp][c], ds[pp][o], acc);
+    __syncthreads();
+  }
+  atomicAdd(&dw[c * 8 + o], acc);
+}
+
+// Data gradient of the head: dx[p][c] (+)= sum_o dy[p][o] wd[c][o], one pixel per thread, the
+// 8 x C weights in shared memory as FP32; dacc = 0 overwrites dx.
+__global__ void __launch_bounds__(256) k_conv1x1_dgrad(const __nv_bfloat16 *dy, const __nv_bfloat16 *wd, int C, int P,
+                                                       float *dx, int dacc) {
+  __shared__ float ws[64 * 8];
+  for (int i = threadIdx.x; i < 8 * C; i += blockDim.x) ws[i] = __bfloat162float(wd[i]);
+  __syncthreads();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const uint4 q = *reinterpret_cast<const uint4 *>(dy + (size_t)p * 8);
+    const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q);
+    float d[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) d[e] = __bfloat162float(h[e]);
+    float4 *dst = reinterpret_cast<float4 *>(dx + (size_t)p * C);
+    for (int g = 0; g < C / 4; ++g) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float *w = ws + (4 * g + e) * 8;
+        float t = 0.f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) t = fmaf(d[o], w[o], t);
+        v[e] = t;
+      }
+      float4 r = make_float4(v[0], v[1], v[2], v[3]);
+      if (dacc) {
+        const float4 old = dst[g];
+        r.x += old.x; r.y += old.y; r.z += old.z; r.w += old.w;
+      }
+      dst[g] = r;
+    }
+  }
+}
+
+bool conv1x1_bwd_supported(const ConvArgs &a) {
+  return a.ks == 1 && a.stride == 1 && a.pad == 0 && a.Cout == 8 && a.C2 == 0 && a.C1 % 8 == 0 && a.C1 >= 8 &&
+         a.C1 <= 64;
+}
+
+cudaError_t launch_conv1x1_wgrad(const ConvArgs &a, const __nv_bfloat16 *dy, float *dw, cudaStream_t st) {
+  if (!conv1x1_bwd_supported(a)) return cudaErrorInvalidValue;
+  const int blocks = std::max(1, std::min((a.Pout + K1_TP - 1) / K1_TP, 152 * 4));
+  k_conv1x1_wgrad<<<blocks, 8 * a.C1, 0, st>>>(a.x1, a.C1, dy, a.Pout, dw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv1x1_dgrad(const ConvArgs &a, const __nv_bfloat16 *dy, const __nv_bfloat16 *wd, float *dx,
+                                 int dacc, cudaStream_t st) {
+  if (!conv1x1_bwd_supported(a)) return cudaErrorInvalidValue;
+  const int blocks = std::max(1, std::min((a.Pout + 255) / 256, 152 * 8));
+  k_conv1x1_dgrad<<<blocks, 256, 0, st>>>(dy, wd, a.C1, a.Pout, dx, dacc);
   return cudaGetLastError();
 }
 

@@ -516,37 +516,51 @@ constexpr int WT_THREADS = 128;
 constexpr int WT_MAXS = 6;
 
 struct WgPlan {
+  int sc;              // channels per input slice: 32 (64-byte swizzle) or 8 (no swizzle)
   int pix;             // output pixels per segment: 64 or 128 (four or eight K = 16 steps)
-  uint32_t slice;      // bytes of one slice: 32 channels x pix pixels of bf16
+  uint32_t slice;      // bytes of one input slice: sc channels x pix pixels of bf16
+  uint32_t bslice;     // bytes of one dY slice: 32 channels x pix pixels
+  int a_slots;         // input slots of a stage before the dY slices (9 Cg, or whole tiles for sc 8)
   int P, R;            // segment: P output columns x R output rows (P * R = pix)
   int tx, per_img;     // segments per output row band, per image
   int units;           // segments of the batch
-  int c1;              // 32-channel slices of input part 1 (part 2 follows)
+  int c1;              // input slices of part 1 (part 2 follows)
   int Cg;              // input slices per channel group (gridDim.y groups)
-  int tiles;           // M = 128 tiles: ceil(9 Cg / 4)
+  int tiles;           // M = 128 tiles: ceil(9 Cg sc / 128)
   int nb;              // dY slices: N / 32
   int S;               // pipeline stages
   int per_cta;         // segments per CTA
 };
 
-__device__ __forceinline__ uint64_t mn_sw64_desc(uint32_t a, uint32_t slice) {
+// MN-major shared-memory descriptor: [0,14) address >> 4, [16,30) LBO >> 4, [32,46) SBO >> 4,
+// version 1, layout 4 (64-byte swizzle: atoms of 32 channels x 8 pixels, 512 bytes) or 0 (no
+// swizzle: core matrices of 8 channels x 8 pixels, 128 bytes); which offset steps along M and
+// which along K depends on the layout (see the MMA issuer)
+__device__ __forceinline__ uint64_t mn_desc(uint32_t a, uint32_t lbo, uint32_t sbo, uint32_t layout) {
   uint64_t d = 0;
   d |= (uint64_t)((a >> 4) & 0x3FFFu);
-  d |= (uint64_t)((slice >> 4) & 0x3FFFu) << 16;     // LBO: next 32 channels (next atom along M / N)
-  d |= (uint64_t)(512u >> 4) << 32;                  // SBO: next 8 pixels (next atom along K)
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1u << 46;
-  d |= (uint64_t)4u << 61;
+  d |= (uint64_t)layout << 61;
   return d;
 }
 
+template <int SC>
 __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap mx1,
                                                           const __grid_constant__ CUtensorMap mx2,
                                                           const __grid_constant__ CUtensorMap mdy, ConvArgs a,
                                                           WgPlan p, int tmem_cols, int *err) {
+  // K = 16 pixels: two 8-pixel groups of the input operand (512-byte atoms for SC = 32, 128-byte
+  // core matrices for SC = 8) and of dY (512-byte atoms); in descriptor address units (16 bytes)
+  constexpr uint32_t KA = SC == 32 ? 64 : 16, KB = 64;
+  constexpr int SPT = 128 / SC;  // input slices per M = 128 tile
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
   const int na = 9 * p.Cg;
-  const uint32_t st_bytes = (uint32_t)(na + p.nb) * p.slice;
+  const uint32_t boff0 = (uint32_t)p.a_slots * p.slice;
+  const uint32_t st_bytes = boff0 + (uint32_t)p.nb * p.bslice;
+  const uint32_t tx_bytes = (uint32_t)na * p.slice + (uint32_t)p.nb * p.bslice;
   __shared__ __align__(8) uint64_t full[WT_MAXS], empty[WT_MAXS], mma_done;
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
@@ -588,16 +602,17 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
     uint32_t boff[2] = {0, 0};
     int mine = 0;
     for (int j = lane; j < nbox && mine < 2; j += 32, ++mine) {
-      boff[mine] = (uint32_t)j * p.slice;
       if (j < na) {
         const int tap = j / p.Cg, cg = j - tap * p.Cg, kh = tap / 3, kw = tap - kh * 3;
         const int sl = grp * p.Cg + cg;
+        boff[mine] = (uint32_t)j * p.slice;
         bmap[mine] = sl < p.c1 ? pm1 : pm2;
-        bc[mine] = (sl < p.c1 ? sl : sl - p.c1) * 32;
+        bc[mine] = (sl < p.c1 ? sl : sl - p.c1) * SC;
         bdx[mine] = kw - 1;
         bdy[mine] = kh - 1;
         bs[mine] = a.stride;
       } else {
+        boff[mine] = boff0 + (uint32_t)(j - na) * p.bslice;
         bc[mine] = 32 * (j - na);
       }
     }
@@ -609,7 +624,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
       if (lane == 0) {
         if (use > 0) ok = wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort);
         if (ok)
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes) : "memory");
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx_bytes) : "memory");
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       const int b = u / p.per_img, r = u - b * p.per_img;
@@ -630,11 +645,15 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: every tile accumulates over every segment of the CTA.  The descriptors of
-    // stage 0 are built once; a stage, a tile (four slices) and a K step of 16 pixels (two
-    // 512-byte atoms) only add to the address field (bytes >> 4; addresses stay below 2^18).
+    // stage 0 are built once; a stage, a tile (SPT slices) and a K step of 16 pixels only add to
+    // the address field (bytes >> 4; addresses stay below 2^18).
     const uint32_t idesc = idesc_bf16_tma(128, a.N) | (1u << 15) | (1u << 16);  // A and B MN-major
-    const uint64_t dA0 = mn_sw64_desc(base, p.slice), dB0 = mn_sw64_desc(base + (uint32_t)na * p.slice, p.slice);
-    const uint64_t d_stage = st_bytes >> 4, d_tile = (4 * p.slice) >> 4;
+    // 64-byte swizzle: LBO = next slice along M, SBO = next 8 pixels along K; no swizzle (the
+    // canonical layout of 8 x 16-byte core matrices): LBO = next 8 pixels along K, SBO = next
+    // slice along M
+    const uint64_t dA0 = SC == 32 ? mn_desc(base, p.slice, 512u, 4u) : mn_desc(base, 128u, p.slice, 0u);
+    const uint64_t dB0 = mn_desc(base + boff0, p.bslice, 512u, 4u);
+    const uint64_t d_stage = st_bytes >> 4, d_tile = ((uint32_t)SPT * p.slice) >> 4;
     long g = 0;
     bool ok = true;
     for (int u = u0; u < u1; ++u, ++g) {
@@ -645,20 +664,21 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
       uint64_t da = dA0 + (uint64_t)s * d_stage;
       uint32_t dt = tmem;
       const uint32_t first = g > 0 ? 1u : 0u;
-      // four K = 16 steps (two 512-byte atoms each) per block; a 128-pixel segment takes two blocks
+      // four K = 16 steps per block; a 128-pixel segment takes two blocks
       const int blocks = p.pix / 64;
       for (int t = 0; t < p.tiles; ++t, da += d_tile, dt += (uint32_t)a.N)
         for (int h = 0; h < blocks; ++h)
           asm volatile(
               "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
               " setp.ne.b32 p, %4, 0;\n setp.eq.b32 q, %4, %4;\n"
-              " add.s64 a1, %1, 64;\n add.s64 a2, %1, 128;\n add.s64 a3, %1, 192;\n"
-              " add.s64 b1, %2, 64;\n add.s64 b2, %2, 128;\n add.s64 b3, %2, 192;\n"
+              " add.s64 a1, %1, %5;\n add.s64 a2, %1, %6;\n add.s64 a3, %1, %7;\n"
+              " add.s64 b1, %2, %8;\n add.s64 b2, %2, %9;\n add.s64 b3, %2, %10;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(dt),
-              "l"(da + (uint64_t)(h * 256)), "l"(db + (uint64_t)(h * 256)), "r"(idesc), "r"(h > 0 ? 1u : first));
+              "l"(da + (uint64_t)(h * 4 * KA)), "l"(db + (uint64_t)(h * 4 * KB)), "r"(idesc), "r"(h > 0 ? 1u : first),
+              "n"(KA), "n"(2 * KA), "n"(3 * KA), "n"(KB), "n"(2 * KB), "n"(3 * KB));
       commit(saddr(&empty[s]));
     }
     commit(saddr(&mma_done));
@@ -674,10 +694,15 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
   if (mma_ok && u1 > u0) {
     const int C = a.C1 + a.C2;
     for (int t = 0; t < p.tiles; ++t) {
-      const int slot = 4 * t + warp;  // warp w reads TMEM lanes 32 w .. 32 w + 31: slot 4 t + w
-      if (slot >= na) break;
-      const int tap = slot / p.Cg, cg = slot - tap * p.Cg;
-      const int m = tap * C + (grp * p.Cg + cg) * 32 + lane;
+      // warp w reads TMEM lanes 32 w .. 32 w + 31: A rows 128 t + 32 w + lane, row q * SC + ci of
+      // input slice q (tap q / Cg, slice cg = q % Cg of the group); rows past the 9 Cg slices are
+      // stale operand data and are dropped
+      const int row0 = t * 128 + warp * 32;
+      if (row0 >= na * SC) break;
+      const int q = (row0 + lane) / SC, ci = (row0 + lane) - q * SC;
+      const bool valid = q < na;
+      const int tap = q / p.Cg, cg = q - tap * p.Cg;
+      const int m = tap * C + (grp * p.Cg + cg) * SC + ci;
       for (int n0 = 0; n0 < a.N; n0 += 16) {
         uint32_t r[16];
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * a.N + n0);
@@ -687,6 +712,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!valid) continue;
         float *dst = a.dw + (size_t)m * a.N + n0;
 #pragma unroll
         for (int e = 0; e < 16; ++e) atomicAdd(dst + e, __uint_as_float(r[e]));
@@ -868,44 +894,63 @@ cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cuda
 
 namespace {
 
-// Plan: the channel group Cg (a divisor of the input's 32-channel slices whose ceil(9 Cg / 4)
-// accumulator tiles fit in the 512 TMEM columns) and the segment of 64 or 128 pixels whose stage
-// fits at least twice in shared memory, chosen by a model of the load side, which sets the pace
-// (measured: a TMA box costs about 100 SM cycles plus one per 64-byte line it brings): groups x
-// boxes x (100 + pixels) / pixels per output pixel, padding included.  The segment shape P x R:
-// the one with the fewest padded pixels.
+// Plan: the input slice width (32 channels; 8 for an input of 8 channels), the channel group Cg
+// (a divisor of the input's slices whose accumulator tiles fit in the 512 TMEM columns) and the
+// segment of 64 or 128 pixels whose stage fits at least twice in shared memory, chosen by a model
+// of the load side, which sets the pace (measured: a TMA box costs about 100 SM cycles plus one
+// per line it brings): groups x boxes x (100 + pixels) / pixels per output pixel, padding
+// included.  The segment shape P x R: the one with the fewest padded pixels.
 constexpr size_t WT_SMEM_MAX = 225 * 1024;
+
+int wgrad_slice_channels(const ConvArgs &a) {
+  if (a.C1 % 32 == 0 && a.C2 % 32 == 0) return 32;
+  if (a.C1 == 8 && a.C2 == 0) return 8;
+  return 0;
+}
+
+void wgrad_stage(const WgPlan &p, size_t *stage, size_t *guard) {
+  *stage = (size_t)p.a_slots * p.slice + (size_t)p.nb * p.bslice;
+  // a last tile reads 128 / sc slices from its first: past the stage's end by at most this much
+  const size_t reach = (size_t)p.tiles * (128 / p.sc) * p.slice;
+  *guard = reach > *stage ? reach - *stage : 0;
+}
 
 WgPlan wgrad_plan(const ConvArgs &a) {
   WgPlan p;
   std::memset(&p, 0, sizeof(p));
-  p.c1 = a.C1 / 32;
-  const int c32 = (a.C1 + a.C2) / 32;
+  p.sc = wgrad_slice_channels(a);
+  if (p.sc == 0) return p;
+  const int spt = 128 / p.sc;
+  p.c1 = a.C1 / p.sc;
+  const int cs = (a.C1 + a.C2) / p.sc;
   p.nb = a.N / 32;
   double best_cost = 0.0;
-  for (int cg = c32; cg >= 1; --cg) {
-    if (c32 % cg) continue;
-    const int tiles = (9 * cg + 3) / 4;
+  for (int cg = cs; cg >= 1; --cg) {
+    if (cs % cg) continue;
+    const int tiles = (9 * cg + spt - 1) / spt;
     if (tiles * a.N > 512) continue;
     for (int pix = 64; pix <= 128; pix *= 2) {
-      const size_t slice = (size_t)pix * 64, stage = (size_t)(9 * cg + p.nb) * slice;
-      const size_t guard = (size_t)std::max(0, 4 * tiles - 9 * cg - p.nb) * slice;
-      const int S = (int)std::min<size_t>(WT_MAXS, (WT_SMEM_MAX - 1024 - guard) / stage);
-      if (S < 2) continue;
+      WgPlan q = p;
+      q.Cg = cg;
+      q.tiles = tiles;
+      q.pix = pix;
+      q.slice = (uint32_t)(pix * p.sc * 2);
+      q.bslice = (uint32_t)(pix * 64);
+      q.a_slots = p.sc == 32 ? 9 * cg : tiles * spt;
+      size_t stage, guard;
+      wgrad_stage(q, &stage, &guard);
+      q.S = (int)std::min<size_t>(WT_MAXS, (WT_SMEM_MAX - 1024 - guard) / stage);
+      if (q.S < 2) continue;
       long padded = -1;  // output pixels of the best segment shape, padding included
       for (int P = 8; P <= pix; P *= 2) {
         const int R = pix / P;
         const long n = (long)((a.Wout + P - 1) / P) * P * (long)((a.Hout + R - 1) / R) * R;
         if (padded < 0 || n < padded) padded = n;
       }
-      const double cost = (double)(c32 / cg) * (9 * cg + p.nb) * (100.0 + pix) / pix * (double)padded;
+      const double cost = (double)(cs / cg) * (9 * cg + p.nb) * (100.0 + pix) / pix * (double)padded;
       if (p.Cg == 0 || cost < best_cost) {
         best_cost = cost;
-        p.Cg = cg;
-        p.tiles = tiles;
-        p.pix = pix;
-        p.slice = (uint32_t)slice;
-        p.S = S;
+        p = q;
       }
     }
   }
@@ -923,42 +968,44 @@ WgPlan wgrad_plan(const ConvArgs &a) {
 }
 
 size_t wgrad_smem(const WgPlan &p) {
-  const size_t stage = (size_t)(9 * p.Cg + p.nb) * p.slice;
-  const size_t guard = (size_t)std::max(0, 4 * p.tiles - 9 * p.Cg - p.nb) * p.slice;
+  size_t stage, guard;
+  wgrad_stage(p, &stage, &guard);
   return 1024 + (size_t)p.S * stage + guard;
 }
 
 }  // namespace
 
 bool wgrad_tma_supported(const ConvArgs &a) {
-  if (!(a.ks == 3 && (a.stride == 1 || a.stride == 2) && a.pad == 1 && a.C1 > 0 && a.C1 % 32 == 0 &&
-        a.C2 % 32 == 0 && (a.C2 == 0 || a.x2) && a.N % 32 == 0 && a.N >= 32 && a.N <= 128 && a.Cout == a.N &&
-        a.M == a.Kf && a.Pout > 0 && encoder() != nullptr))
+  if (!(a.ks == 3 && (a.stride == 1 || a.stride == 2) && a.pad == 1 && a.C1 > 0 && (a.C2 == 0 || a.x2) &&
+        a.N % 32 == 0 && a.N >= 32 && a.N <= 128 && a.Cout == a.N && a.M == a.Kf && a.Pout > 0 &&
+        encoder() != nullptr))
     return false;
   return wgrad_plan(a).Cg > 0;
 }
 
 // Tensor maps of the weight gradient: the input parts as 4-D (C, W, H, B) tensors with boxes of
-// 32 channels x sP x sR pixels traversed with element strides s (the stride), dY as a 4-D
-// (N, Wout, Hout, B) tensor with boxes of 32 x P x R; 64-byte swizzle, zero fill outside.  The
-// dY map goes into the w slot of ConvMaps.
+// sc channels x sP x sR pixels traversed with element strides s (the stride; 64-byte swizzle for
+// 32-channel slices, none for 8), dY as a 4-D (N, Wout, Hout, B) tensor with boxes of 32 x P x R
+// (64-byte swizzle); zero fill outside.  The dY map goes into the w slot of ConvMaps.
 int make_wgrad_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
   EncodeTiled enc = encoder();
   if (!enc) return 1;
   const WgPlan p = wgrad_plan(a);
+  if (p.Cg == 0) return 5;
   std::memset(m, 0, sizeof(*m));
   const cuuint32_t sd = (cuuint32_t)a.stride;
-  auto map4 = [&](CUtensorMap *t, const __nv_bfloat16 *ptr, int C, int W, int H, cuuint32_t s) {
+  auto map4 = [&](CUtensorMap *t, const __nv_bfloat16 *ptr, int C, int W, int H, cuuint32_t s, int box_c) {
     const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bmax};
     const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
-    const cuuint32_t box[4] = {32, (cuuint32_t)p.P * s, (cuuint32_t)p.R * s, 1}, es[4] = {1, s, s, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)p.P * s, (cuuint32_t)p.R * s, 1}, es[4] = {1, s, s, 1};
     return enc(t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, box_c == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  if (!map4(&m->x1, a.x1, a.C1, a.Win, a.Hin, sd)) return 2;
-  if (a.C2 > 0 ? !map4(&m->x2, a.x2, a.C2, a.Win, a.Hin, sd) : !map4(&m->x2, a.x1, a.C1, a.Win, a.Hin, sd)) return 3;
-  if (!map4(&m->w, a.dy, a.N, a.Wout, a.Hout, 1)) return 4;
+  if (!map4(&m->x1, a.x1, a.C1, a.Win, a.Hin, sd, p.sc)) return 2;
+  if (a.C2 > 0 ? !map4(&m->x2, a.x2, a.C2, a.Win, a.Hin, sd, p.sc) : !map4(&m->x2, a.x1, a.C1, a.Win, a.Hin, sd, p.sc))
+    return 3;
+  if (!map4(&m->w, a.dy, a.N, a.Wout, a.Hout, 1, 32)) return 4;
   return 0;
 }
 
@@ -967,9 +1014,10 @@ cudaError_t launch_wgrad_tma(const ConvArgs &a, const ConvMaps &m, int *err, cud
   if (p.Cg <= 0) return cudaErrorInvalidValue;
   const int cols = tmem_cols_of(p.tiles * a.N);
   const size_t smem = wgrad_smem(p);
-  cudaError_t e = cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = p.sc == 32 ? k_wgrad_tma<32> : k_wgrad_tma<8>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, smem_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
@@ -977,13 +1025,13 @@ cudaError_t launch_wgrad_tma(const ConvArgs &a, const ConvMaps &m, int *err, cud
       (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
     return e;
   const int occ = std::max(1, std::min(smem_sm / (int)(smem + 2048), 512 / cols));
-  const int groups = (a.C1 + a.C2) / 32 / p.Cg;
+  const int groups = (a.C1 + a.C2) / p.sc / p.Cg;
   // pixel ranges: fill the GPU once, but give every CTA at least 16 segments (each CTA ends
   // with one FP32 atomic per weight of its group)
   const int splits = std::max(1, std::min((sms * occ + groups - 1) / groups, (p.units + 15) / 16));
   p.per_cta = (p.units + splits - 1) / splits;
   const int gx = (p.units + p.per_cta - 1) / p.per_cta;
-  k_wgrad_tma<<<dim3(gx, groups), WT_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, p, cols, err);
+  kern<<<dim3(gx, groups), WT_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, p, cols, err);
   return cudaGetLastError();
 }
 
