@@ -55,8 +55,8 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
 /* Tensor-core path of the convolutions: a parity and measurement reference, not a choice a
  * user makes.  The network runs on path 3 (the default), which assigns one kernel to each
  * layer shape: the halo-load tcgen05 kernel (the forward of stride-1 layers whose weights fit in
- * 72 KB, and their data gradient where the reversed weights fit), the TMA-tile tcgen05 forward
- * (the other 3x3 layers with 32-channel input parts), the TMA-fed tcgen05 weight gradient (every
+ * 72 KB, and the data gradient where the reversed weights fit), the TMA-tile tcgen05 forward
+ * (the other 3x3 layers with 32-channel input parts; also the other stride-1 data gradients), the TMA-fed tcgen05 weight gradient (every
  * 3x3 layer), the gathering tcgen05 kernels (the forward of the 8-channel first layer, the other
  * data gradients) and the FP32 CUDA-core head (forward and backward).  Paths 0-2 keep the earlier kernels
  * of those layers so that the tests can compare each layer's kernel with the one it replaced
@@ -73,8 +73,10 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
  *       16 x 8 output pixels, the padding read as the loads' zero fill) in a persistent kernel.
  *   3 (default) = as 2, except that the stride-1 ones whose weight matrix fits in 72 KB keep it
  *       resident in shared memory and load one 10 x 18-pixel halo per 32-channel chunk for all
- *       nine taps (tiles of 8 x 16 output pixels), the data gradient of those layers runs on the
- *       same kernel as a forward convolution of the output gradient with the taps reversed, and
+ *       nine taps (tiles of 8 x 16 output pixels), the data gradient runs as a forward convolution
+ *       of the output gradient with the taps reversed (for stride 2 of the output gradient
+ *       spread onto the input grid with zeros between) on the halo kernel where the reversed
+ *       weights fit, else for stride 1 on the tile kernel of path 2, and
  *       the weight gradient of the 3x3 layers takes both operands by TMA tiled loads (segments
  *       of 64 or 128 output pixels, one load per tap and 32-channel slice, or 8-channel slice
  *       for the first layer); their sums round in another order.

@@ -71,6 +71,8 @@ cudaError_t launch_conv1x1_dgrad(const ConvArgs &a, const __nv_bfloat16 *dy, con
                                  int dacc, cudaStream_t st);
 cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C, cudaStream_t st);
+// dY of a stride-2 layer (h x w) spread onto the (2h - 1) x (2w - 1) input grid with zeros between
+cudaError_t launch_zero_insert(const __nv_bfloat16 *dy, __nv_bfloat16 *dz, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,
                        cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, int step, cudaStream_t st);

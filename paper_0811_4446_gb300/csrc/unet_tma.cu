@@ -228,6 +228,28 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (!inside) continue;
+        if (a.dx1) {
+          // data gradient (a forward convolution of dY): write (or add) into the FP32 gradient of
+          // the input part these 16 channels belong to (dsplit is a multiple of 32)
+          const bool p1 = n0 < a.dsplit;
+          const int cw = p1 ? a.dsplit : a.N - a.dsplit;
+          float4 *dst = reinterpret_cast<float4 *>((p1 ? a.dx1 : a.dx2) + pix * cw + (p1 ? n0 : n0 - a.dsplit));
+          float4 o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            o[e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]), __uint_as_float(r[4 * e + 2]),
+                               __uint_as_float(r[4 * e + 3]));
+          if (a.dacc) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float4 q = dst[e];
+              o[e].x += q.x; o[e].y += q.y; o[e].z += q.z; o[e].w += q.w;
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dst[e] = o[e];
+          continue;
+        }
         float v[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -750,10 +772,14 @@ EncodeTiled encoder() {
 
 }  // namespace
 
+// Forward (bf16 output into a.y) or, with a.dx1 set, a data gradient written as a forward
+// convolution of (zero-inserted, for stride 2) dY with the reversed taps: FP32 into dx1 / dx2.
 bool conv_tma_supported(const ConvArgs &a, int mode) {
+  const bool out_ok = a.dx1 ? (!a.y && !a.y32 && a.dsplit > 0 && a.dsplit % TM_CH == 0 && a.dsplit <= a.N &&
+                               (a.dsplit == a.N || a.dx2))
+                            : (a.y && !a.y32);
   return mode == MODE_FWD && a.ks == 3 && (a.stride == 1 || a.stride == 2) && a.pad == 1 && a.C1 > 0 &&
-         a.C1 % TM_CH == 0 &&
-         a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && a.y && !a.y32 && a.N % 16 == 0 && a.N >= 16 &&
+         a.C1 % TM_CH == 0 && a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && out_ok && a.N % 16 == 0 && a.N >= 16 &&
          a.N <= TM_NMAX && a.Nreal <= a.N && encoder() != nullptr;
 }
 
