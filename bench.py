@@ -742,8 +742,8 @@ def measure_forms(args, dev, peaks):
     out["mixed_vcycle_1025"] = _vcycle_1025(mg.MG_MIXED, peaks)
     out["fp64_vcycle_1025"] = _vcycle_1025(mg.MG_FP64, peaks)
     # batched form: 64 independent discharges of seeded sizes 65^2..513^2, mixed precision, as
-    # the persistent work-list launch (workers = 0: one launch per round of Newton iterations of
-    # every discharge) and, for comparison, as 16 host threads each solving one discharge at a time
+    # the persistent work-list launch (workers = 0: every discharge's whole steady solve in one
+    # launch) and, for comparison, as 16 host threads each solving one discharge at a time
     ds = W.batch_64()
     solvers = [mg.from_discharge(dd, precision=mg.MG_MIXED, stream=torch.cuda.Stream(device=dev)) for dd in ds]
     inits = [[np.ascontiguousarray(a) for a in (dd.ne0, dd.np0, dd.V0)] for dd in ds]

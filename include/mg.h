@@ -250,19 +250,20 @@ int mg_solve_steady_guess(mg_state *s, const double *ne, const double *np, const
 
 /* Batched form: solve n independent discharges (the paper solves one discharge at a time,
  * Sec. 2) to their steady states (mg_solve_steady on each).
- *   workers = 0: the persistent work-list form.  Every discharge runs its own march (Delta-t
- *     ramp, continuation, accept / reject) on a host thread of its own; whenever all discharges
- *     still solving have reached a Newton iteration, ONE launch of a persistent kernel (replayed
- *     from a captured CUDA graph) carries out that iteration for all of them: hierarchy set-up,
- *     the V-cycle loop with each discharge's own stopping test on the device, the update and
- *     the residual of the new state.  The CTAs take work items (tiles of a level's phase) from
- *     whichever discharge has work open; a discharge's phases run in the order of the
- *     single-discharge path and give the same results bit for bit.  Needs the point smoother,
- *     the Picard Jacobian, the coarse-cycle kernel (coarse_kernel_n > 0) at or below the
- *     continuation's first grid and a coarsest level of at most 48 unknowns; otherwise the call
- *     falls back to 16 host threads.  ms_out[k]: from the batch's start to
- *     discharge k's solve returning.  A work list that stops making progress (no work item
- *     claimed for 5 s) ends the launch with MG_ETIMEOUT.
+ *   workers = 0: the persistent work-list form.  Every discharge's whole steady solve (the
+ *     continuation, the Delta-t march with accept / reject, the Newton iterations and the
+ *     V-cycle loops, as mg_solve_steady runs them) happens in ONE launch of a persistent kernel,
+ *     replayed from a captured CUDA graph.  Each discharge has a program of phases (the
+ *     single-discharge path's kernels in its order); the CTAs claim work items (rounds of a
+ *     phase's thread blocks, the size chosen by mg_autotune_batch) of whichever discharge has a
+ *     phase open, and the CTA that completes a phase runs that discharge's march, step and
+ *     Newton control on the device and opens its next phase.  Same results bit for bit as
+ *     mg_solve_steady on each state (state, steps, Newton iterations, V-cycles).  Needs the
+ *     point smoother, the Picard Jacobian, the coarse-cycle kernel (coarse_kernel_n > 0) at or
+ *     below the continuation's first grid and a coarsest level of at most 48 unknowns;
+ *     otherwise the call falls back to 16 host threads.  ms_out[k]: from the launch's start to
+ *     discharge k's solve ending (device clock).  A launch in which no phase completes for 5 s
+ *     ends with MG_ETIMEOUT.  n = 0 returns MG_OK at once.
  *   workers > 0: the comparison form: `workers` host threads take instances from a shared queue
  *     and run mg_solve_steady on each state's own stream (give each state a distinct stream at
  *     mg_create so that the GPU can overlap them), every linear solve a device-side CUDA-graph

@@ -1978,7 +1978,8 @@ int solve_batch_persistent(mg_state **states, int n, double tol, double *ms_out,
 }  // namespace
 
 int mg_solve_steady_batch(mg_state **states, int n, double tol, int workers, double *ms_out, int *rc_out) {
-  if (!states || n < 0 || !(tol > 0.0) || workers < 0) return MG_EINVAL;
+  if (n < 0 || !(tol > 0.0) || workers < 0 || (n > 0 && !states)) return MG_EINVAL;
+  if (n == 0) return MG_OK;
   for (int k = 0; k < n; ++k)
     if (!states[k]) return MG_EINVAL;
   int dev = 0;

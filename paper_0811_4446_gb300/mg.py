@@ -341,9 +341,9 @@ class Solver:
 def solve_steady_batch(solvers, tol: float, workers: int = 0):
     """Steady solves of independent Solver objects; returns (rc, ms[n], rc[n]).
 
-    workers = 0: the batched persistent launch (every Newton iteration of all discharges in one
-    launch per round); workers > 0: that many host threads solving the discharges one by one
-    (the comparison form).  See mg_solve_steady_batch in include/mg.h."""
+    workers = 0: the batched persistent launch (every discharge's whole steady solve in one
+    launch); workers > 0: that many host threads solving the discharges one by one (the
+    comparison form).  See mg_solve_steady_batch in include/mg.h."""
     lib = load()
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s.h for s in solvers])

@@ -399,10 +399,11 @@ def test_transient_1025_full_size(mg):
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_persistent_batch_equals_individual_solves(mg, precision):
-    """The batched form as one persistent launch per round of Newton iterations (workers = 0):
-    discharges of 33^2 to 129^2 reach their individual solves' steady states bit for bit with
-    the same steps, Newton iterations and V-cycles, with far fewer kernel launches, and the
-    oracle's steady residual of each result is <= 1e-8."""
+    """The batched form as one persistent launch for every discharge's whole steady solve
+    (workers = 0): discharges of 33^2 to 129^2 reach their individual solves' steady states bit
+    for bit with the same steps, Newton iterations and V-cycles, with far fewer kernel launches,
+    and the oracle's steady residual of each result is <= 1e-8.  An empty batch returns at once;
+    a batch of one equals its individual solve too."""
     prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
     ds = W.batch_64(seed=4, count=6, sizes=(16, 32, 64, 128))
     solvers = [mg.from_discharge(d, precision=prec, stream=torch.cuda.Stream()) for d in ds]
@@ -428,6 +429,16 @@ def test_persistent_batch_equals_individual_solves(mg, precision):
         F, T = disc.residual(g, np.stack(a), None, d.S_e, d.S_p, None, phys, with_terms=True)
         assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE)
     assert launches_batch * 10 < launches_single, (launches_batch, launches_single)
+    rc0, ms0, rcs0 = mg.solve_steady_batch([], 1e-8, workers=0)
+    assert rc0 == mg.MG_OK and ms0.size == 0 and rcs0.size == 0
+    d1 = ds[0]
+    one = mg.from_discharge(d1, precision=prec, stream=torch.cuda.Stream())
+    rc1, _, _ = mg.solve_steady_batch([one], 1e-8, workers=0)
+    assert rc1 == mg.MG_OK
+    ref = mg.from_discharge(d1, precision=prec)
+    assert ref.solve_steady(1e-8)[0] == mg.MG_OK
+    for q in range(3):
+        assert np.array_equal(one.get_state()[q], ref.get_state()[q]), q
 
 
 def test_autotune_batch_keeps_results_and_restores_states(mg):
