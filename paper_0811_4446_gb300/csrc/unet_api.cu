@@ -224,12 +224,15 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
   const int cop = a.Cout;
   UK(launch_relu_bias_bwd(out ? out->g : dout32, out ? out->a : nullptr, n->dpre, n->grad + n->boff[l], (int)P, cop,
                           kL[l].co, out ? kL[l].relu : 0, n->st));
-  // weight gradient: GEMM (kh, kw, ci) x cop over the output pixels, split over pixel ranges
+  // weight gradient: GEMM (kh, kw, ci) x cop over the output pixels, split over pixel ranges;
+  // added straight into the (zeroed) gradient vector where no output channel is padded, else
+  // into the padded buffer and copied over
   ConvArgs w = a;
   w.M = a.Kf; w.N = cop; w.K = a.Pout;
   w.dy = n->dpre;
-  w.dw = n->dwpad;
-  UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), n->st));
+  const bool padded = cop != kL[l].co;
+  w.dw = padded ? n->dwpad : n->grad + n->woff[l];
+  if (padded) UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), n->st));
   if (n->use_tc && conv1x1_bwd_supported(a)) {
     UK(launch_conv1x1_wgrad(a, n->dpre, n->dwpad, n->st));
   } else if (n->use_tc == 3 && wgrad_tma_supported(w)) {
@@ -247,7 +250,7 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
     const int splits = std::max(1, std::min((w.K + 255) / 256, 2 * 152 * 2 / std::max(1, tiles)));
     UK(launch_conv(w, MODE_WGRAD, splits, n->st));
   }
-  UK(launch_unpad_grad(n->dwpad, n->grad + n->woff[l], (size_t)a.Kf, kL[l].co, cop, n->st));
+  if (padded) UK(launch_unpad_grad(n->dwpad, n->grad + n->woff[l], (size_t)a.Kf, kL[l].co, cop, n->st));
   int dacc = 1;
   if (want_dx)
     if (int rc = dx_mode(n, B, in1, in2, &dacc)) return rc;
@@ -303,9 +306,13 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
 }
 
 int refresh_weights(mg_unet *n) {
+  static_assert(NL <= kMaxWeightCopies, "weight-copy table");
+  WeightCopies c;
+  std::memset(&c, 0, sizeof(c));
+  c.n = NL;
   for (int l = 0; l < NL; ++l)
-    UK(launch_weight_copies(n->master + n->woff[l], n->wf[l], n->wd[l], n->wdf[l], kL[l].ks, kL[l].ci, kL[l].co,
-                            pad8(kL[l].co), n->st));
+    c.l[l] = {n->master + n->woff[l], n->wf[l], n->wd[l], n->wdf[l], kL[l].ks, kL[l].ci, kL[l].co, pad8(kL[l].co)};
+  UK(launch_weight_copies(c, n->st));
   return MG_OK;
 }
 

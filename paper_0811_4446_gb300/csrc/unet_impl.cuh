@@ -76,8 +76,19 @@ cudaError_t launch_zero_insert(const __nv_bfloat16 *dy, __nv_bfloat16 *dz, int B
 cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,
                        cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, int step, cudaStream_t st);
-cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wdf, int ks, int ci,
-                                 int co, int cop, cudaStream_t st);
+// the bf16 operand copies (wf, wd, wdf) of every layer's FP32 weights, in one launch
+constexpr int kMaxWeightCopies = 12;
+struct WeightCopy {
+  const float *w;
+  __nv_bfloat16 *wf, *wd, *wdf;
+  int ks, ci, co, cop;
+};
+struct WeightCopies {
+  WeightCopy l[kMaxWeightCopies];
+  size_t start[kMaxWeightCopies + 1];  // filled by launch_weight_copies
+  int n;
+};
+cudaError_t launch_weight_copies(WeightCopies c, cudaStream_t st);
 cudaError_t launch_unpad_grad(const float *gp, float *g, size_t rows, int co, int cop, cudaStream_t st);
 cudaError_t launch_f32_to_bf16(const float *a, __nv_bfloat16 *b, size_t n, cudaStream_t st);
 

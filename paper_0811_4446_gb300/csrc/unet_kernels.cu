@@ -400,33 +400,41 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, 
   return cudaGetLastError();
 }
 
-// bf16 operand copies of one layer's FP32 master weights w[kh][kw][ci][co]:
+// bf16 operand copies of the layers' FP32 master weights w[kh][kw][ci][co], every layer in one
+// launch (a grid-stride loop over the concatenated copies; the layer of an index found by a
+// scan of the 12 starts):
 //   wf[co][(kh, kw, ci)]  (forward B operand, k contiguous)
 //   wd[ci][(kh, kw, co)]  (data-gradient B operand)
 //   wdf[ci][(2 - kh, 2 - kw, co)]  (the same with the taps reversed: the weights of the data
 //                         gradient written as a forward convolution of dY, stride 1)
 // co is padded to cop (zero rows) so that every operand dimension is a multiple of 8.
-__global__ void k_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wdf, int ks, int ci,
-                                int co, int cop) {
-  const int taps = ks * ks;
-  const size_t n = (size_t)taps * ci * cop;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int o = i % cop;
-    size_t t = i / cop;
-    const int c = t % ci;
-    const int tap = t / ci;
-    const float v = o < co ? w[((size_t)tap * ci + c) * co + o] : 0.f;
-    const __nv_bfloat16 b = __float2bfloat16(v);
-    wf[(size_t)o * taps * ci + (size_t)tap * ci + c] = b;
-    wd[(size_t)c * taps * cop + (size_t)tap * cop + o] = b;
-    wdf[(size_t)c * taps * cop + (size_t)(taps - 1 - tap) * cop + o] = b;
+__global__ void k_weight_copies(WeightCopies c) {
+  const size_t total = c.start[c.n];
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    int l = 0;
+    while (g >= c.start[l + 1]) ++l;
+    const WeightCopy &L = c.l[l];
+    const size_t i = g - c.start[l];
+    const int taps = L.ks * L.ks;
+    const int o = i % L.cop;
+    size_t t = i / L.cop;
+    const int ch = t % L.ci;
+    const int tap = t / L.ci;
+    const float v = o < L.co ? L.w[((size_t)tap * L.ci + ch) * L.co + o] : 0.f;
+    const __nv_bfloat16 bv = __float2bfloat16(v);
+    L.wf[(size_t)o * taps * L.ci + (size_t)tap * L.ci + ch] = bv;
+    L.wd[(size_t)ch * taps * L.cop + (size_t)tap * L.cop + o] = bv;
+    L.wdf[(size_t)ch * taps * L.cop + (size_t)(taps - 1 - tap) * L.cop + o] = bv;
   }
 }
 
-cudaError_t launch_weight_copies(const float *w, __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wdf, int ks, int ci,
-                                 int co, int cop, cudaStream_t st) {
-  const size_t n = (size_t)ks * ks * ci * cop;
-  k_weight_copies<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(w, wf, wd, wdf, ks, ci, co, cop);
+cudaError_t launch_weight_copies(WeightCopies c, cudaStream_t st) {
+  if (c.n <= 0 || c.n > kMaxWeightCopies) return cudaErrorInvalidValue;
+  c.start[0] = 0;
+  for (int l = 0; l < c.n; ++l)
+    c.start[l + 1] = c.start[l] + (size_t)c.l[l].ks * c.l[l].ks * c.l[l].ci * c.l[l].cop;
+  const size_t n = c.start[c.n];
+  k_weight_copies<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(c);
   return cudaGetLastError();
 }
 
