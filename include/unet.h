@@ -55,10 +55,10 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
 /* Tensor-core path of the convolutions: a parity and measurement reference, not a choice a
  * user makes.  The network runs on path 3 (the default), which assigns one kernel to each
  * layer shape: the halo-load tcgen05 kernel (the forward of stride-1 layers whose weights fit in
- * 72 KB, and the data gradient where the reversed weights fit), the TMA-tile tcgen05 forward
+ * 72 KB, the 8-channel first layer included, and the data gradient where the reversed weights
+ * fit), the TMA-tile tcgen05 forward
  * (the other 3x3 layers with 32-channel input parts; also the other stride-1 data gradients), the TMA-fed tcgen05 weight gradient (every
- * 3x3 layer), the gathering tcgen05 kernels (the forward of the 8-channel first layer, the other
- * data gradients) and the FP32 CUDA-core head (forward and backward).  Paths 0-2 keep the earlier kernels
+ * 3x3 layer), the gathering tcgen05 kernel (the other data gradients) and the FP32 CUDA-core head (forward and backward).  Paths 0-2 keep the earlier kernels
  * of those layers so that the tests can compare each layer's kernel with the one it replaced
  * (same operands, another order of the sums) and the benchmark can report what each
  * replacement gained:

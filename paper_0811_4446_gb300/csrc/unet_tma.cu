@@ -322,8 +322,11 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
                                                           TileGrid tg, int tmem_cols, int *err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int BN = a.N;
-  const int Ctot = a.C1 + a.C2, nkb = 9 * Ctot / TM_CH;  // weight blocks of 32 K values
-  const uint32_t wblk = (uint32_t)BN * 64, wbytes = (uint32_t)nkb * wblk;
+  // c8: an 8-channel input (one plane per tile, taps paired into K = 16 MMAs); the weights then
+  // as ten unswizzled blocks of 8 K values (the tenth past K = 72: the load's zero fill)
+  const bool c8 = a.C1 == 8;
+  const int Ctot = a.C1 + a.C2, nkb = c8 ? 10 : 9 * Ctot / TM_CH;  // weight blocks of 32 (8) K values
+  const uint32_t wblk = (uint32_t)BN * (c8 ? 16 : 64), wbytes = (uint32_t)nkb * wblk;
   const uint32_t wbase = (saddr(smem_raw) + 1023u) & ~1023u, hbase = wbase + wbytes;
   __shared__ __align__(8) uint64_t wfull, full[HSTAGES], empty[HSTAGES], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_sh;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_sh;
-  const int c1 = a.C1 / TM_CH, nch = Ctot / TM_CH;
+  const int c1 = a.C1 / TM_CH, nch = c8 ? 1 : Ctot / TM_CH;
 
   if (warp == 0) {
     // ---- producer warp: the weight matrix once, then the halo of every chunk of every tile;
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
       for (int i = 0; i < nkb; ++i)
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-            ::"r"(wbase + (uint32_t)i * wblk), "l"(pmw), "r"(i * TM_CH), "r"(0), "r"(wb)
+            ::"r"(wbase + (uint32_t)i * wblk), "l"(pmw), "r"(i * (c8 ? 8 : TM_CH)), "r"(0), "r"(wb)
             : "memory");
     }
     long g = 0;
@@ -382,13 +385,15 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
         int ok = 1;
         if (lane == 0) {
           ok = !*abort && (use == 0 || wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort));
-          if (ok) asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(HTX) : "memory");
+          if (ok)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(c8 ? HPLANE : HTX)
+                         : "memory");
         }
         if (!__shfl_sync(0xffffffffu, ok, 0)) {
           go = false;
           break;
         }
-        if (lane < 4)
+        if (lane < (c8 ? 1 : 4))
           asm volatile(
               "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
               ::"r"(hbase + (uint32_t)s * HSTAGE + (uint32_t)lane * HPITCH), "l"(c < c1 ? pm1 : pm2),
@@ -419,6 +424,28 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_halo(const __grid_constant_
         const int s = (int)(g % HSTAGES);
         if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / HSTAGES) & 1), abort))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (c8) {
+          // taps (2q, 2q + 1) form one K = 16 step: the second core matrix along K is the window
+          // of tap 2q + 1, (its offset - tap 2q's) bytes on (the LBO of that MMA; the windows
+          // overlap in memory, which the reads allow); the weights' K blocks 512 B apart
+          const uint32_t sa = hbase + (uint32_t)s * HSTAGE;
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const int t0 = 2 * q, t1 = 2 * q + 1;
+            const uint32_t o0 = (uint32_t)((t0 / 3) * HW + t0 % 3) * 16;
+            // the padding tap (K 72..79, zero weights) reads tap 8's window again: loaded,
+            // finite data (stale shared memory could hold NaN, and NaN x 0 is NaN)
+            const uint32_t o1 = t1 < 9 ? (uint32_t)((t1 / 3) * HW + t1 % 3) * 16 : o0;
+            const uint64_t da = nosw_desc(sa + o0, o1 - o0, HW * 16);
+            const uint64_t db = nosw_desc(wbase + (uint32_t)t0 * wblk, wblk, 128);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_t),
+                "l"(da), "l"(db), "r"(idesc), "r"(q > 0 ? 1u : 0u));
+          }
+          commit(saddr(&empty[s]));
+          continue;
+        }
         // descriptors advance by constants: tap (kh, kw) = window (kh * 10 + kw) * 16 bytes on, its
         // weight block nch * wblk bytes on; the second K = 16 step two planes / 32 bytes on
         const uint64_t da0 = dH0 + (uint64_t)((uint32_t)s * (HSTAGE >> 4));
@@ -790,9 +817,11 @@ bool conv_halo_supported(const ConvArgs &a, int mode) {
   const bool out_ok = a.dx1 ? (!a.y && !a.y32 && a.dsplit > 0 && a.dsplit % TM_CH == 0 && a.dsplit <= a.N &&
                                (a.dsplit == a.N || a.dx2))
                             : (a.y && !a.y32);
-  return mode == MODE_FWD && a.ks == 3 && a.stride == 1 && a.pad == 1 && a.C1 > 0 && a.C1 % TM_CH == 0 &&
-         a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2) && out_ok && a.N % 16 == 0 && a.N >= 16 &&
-         a.N <= TM_NMAX && a.Nreal <= a.N && (size_t)9 * (a.C1 + a.C2) * a.N * 2 <= HWMAX && encoder() != nullptr;
+  const bool chans = (a.C1 > 0 && a.C1 % TM_CH == 0 && a.C2 % TM_CH == 0 && (a.C2 == 0 || a.x2)) ||
+                     (a.C1 == 8 && a.C2 == 0 && !a.dx1);
+  return mode == MODE_FWD && a.ks == 3 && a.stride == 1 && a.pad == 1 && chans && out_ok && a.N % 16 == 0 &&
+         a.N >= 16 && a.N <= TM_NMAX && a.Nreal <= a.N && (size_t)9 * (a.C1 + a.C2) * a.N * 2 <= HWMAX &&
+         encoder() != nullptr;
 }
 
 // Tensor maps of the halo variant: the input parts as 4-D (C, W, H, B) bf16 tensors with boxes
@@ -812,19 +841,21 @@ int make_halo_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
   };
   if (!act(&m->x1, a.x1, a.C1)) return 2;
   if (a.C2 > 0 ? !act(&m->x2, a.x2, a.C2) : !act(&m->x2, a.x1, a.C1)) return 3;
+  // an 8-channel input: blocks of 8 K values, unswizzled 16-byte rows
+  const bool c8 = a.C1 == 8;
   const cuuint64_t wd[2] = {(cuuint64_t)a.K, (cuuint64_t)a.N};
   const cuuint64_t ws[1] = {(cuuint64_t)a.K * 2};
-  const cuuint32_t wbox[2] = {TM_CH, (cuuint32_t)a.N}, wes[2] = {1, 1};
+  const cuuint32_t wbox[2] = {c8 ? 8u : (cuuint32_t)TM_CH, (cuuint32_t)a.N}, wes[2] = {1, 1};
   if (enc(&m->w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(a.w), wd, ws, wbox, wes,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+          CU_TENSOR_MAP_INTERLEAVE_NONE, c8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_64B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return 4;
   return 0;
 }
 
 cudaError_t launch_conv_halo(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st) {
   const int BN = a.N, cols = tmem_cols_of(2 * BN);
-  const size_t wbytes = (size_t)9 * (a.C1 + a.C2) / TM_CH * BN * 64;
+  const size_t wbytes = a.C1 == 8 ? (size_t)10 * BN * 16 : (size_t)9 * (a.C1 + a.C2) / TM_CH * BN * 64;
   // the operand windows end inside their stage: the last tap's last core matrix of a plane ends
   // at (2 * 10 + 2) * 16 + 15 * 160 + 128 = 2,880 bytes, the plane's end
   const size_t smem = 1024 + wbytes + (size_t)HSTAGES * HSTAGE;
