@@ -71,9 +71,10 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
  *   2 = as 1, except that the forward 3x3 convolutions (stride 1 or 2) whose input
  *       parts have a multiple of 32 channels take their operands by TMA tiled loads (tiles of
  *       16 x 8 output pixels, the padding read as the loads' zero fill) in a persistent kernel.
- *   3 (default) = as 2, except that the stride-1 ones whose weight matrix fits in 72 KB keep it
- *       resident in shared memory and load one 10 x 18-pixel halo per 32-channel chunk for all
- *       nine taps (tiles of 8 x 16 output pixels), the data gradient runs as a forward convolution
+ *   3 (default) = as 2, except that the stride-1 ones whose weight matrix fits in 72 KB (the
+ *       8-channel first layer too) keep it resident in shared memory and load one 10 x 18-pixel
+ *       halo per 32-channel chunk (8-channel plane) for all nine taps (tiles of 8 x 16 output
+ *       pixels), the 1x1 head's backward runs on the CUDA cores, the data gradient runs as a forward convolution
  *       of the output gradient with the taps reversed (for stride 2 of the output gradient
  *       spread onto the input grid with zeros between) on the halo kernel where the reversed
  *       weights fit, else for stride 1 on the tile kernel of path 2, and
