@@ -105,13 +105,14 @@ def test_halo_forward_matches_tile_path(un, Bmax, B, n):
     assert rel <= 1e-2, rel
 
 
-@pytest.mark.parametrize("Bmax,B,n", [(2, 2, 32), (4, 3, 64), (1, 1, 128)])
+@pytest.mark.parametrize("Bmax,B,n", [(2, 2, 8), (1, 1, 16), (2, 2, 32), (4, 3, 64), (1, 1, 128)])
 def test_layer_gradients_match_mma_sync(un, Bmax, B, n):
-    # Path 3 takes the weight gradient of every 3x3 layer whose input parts have a multiple of 32
-    # channels from the TMA-fed tcgen05 kernel (MN-major operands, 8 x 8-pixel segments: 33, 65
-    # and 129 node rows leave ragged segments, B < Bmax leaves images of the tensor maps unread)
-    # and the data gradient of the stride-1 layers whose reversed weights fit in shared memory
-    # from the halo kernel, each first contribution to an activation gradient overwriting it.
+    # Path 3 takes the weight gradient of every 3x3 layer from the TMA-fed tcgen05 kernel
+    # (MN-major operands, segments of 64 or 128 pixels: 9 to 129 node rows leave ragged
+    # segments, the smallest grids tiles larger than the image; B < Bmax leaves images of the
+    # tensor maps unread), the data gradient as a forward convolution of (spread) dY on the halo
+    # or tile kernels, each first contribution to an activation gradient overwriting it, and the
+    # head's backward on the CUDA cores.
     # Path 0 runs mma.sync everywhere.  The two forwards round BF16 activations differently, so
     # per layer the largest difference is compared with the layer's largest gradient entry.
     from oracle import unet as ou
