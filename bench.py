@@ -915,6 +915,27 @@ def unet_conv_flops(n: int = 256) -> float:
     return float(sum(2.0 * H[lv] ** 2 * k * co for lv, k, co in layers))
 
 
+def unet_layer_table(n: int = 256, B: int = 16) -> list:
+    """Per convolution of the network at batch B: its FLOPs (2 k^2 C_in C_out per output pixel) and
+    the bytes a forward pass moves (bf16 input and output activations, bf16 weights; the head's
+    output FP32)."""
+    H = [n + 1]
+    for _ in range(3):
+        H.append((H[-1] - 1) // 2 + 1)
+    # name, kernel size, input level, output level, c_in, c_out (the head's 3 outputs padded to 8)
+    spec = [("e0a", 3, 0, 0, 8, 32), ("e0b", 3, 0, 0, 32, 32), ("e1a", 3, 0, 1, 32, 64), ("e1b", 3, 1, 1, 64, 64),
+            ("e2a", 3, 1, 2, 64, 96), ("e2b", 3, 2, 2, 96, 96), ("e3a", 3, 2, 3, 96, 128), ("e3b", 3, 3, 3, 128, 128),
+            ("d2", 3, 2, 2, 224, 64), ("d1", 3, 1, 1, 128, 32), ("d0", 3, 0, 0, 64, 32), ("head", 1, 0, 0, 32, 8)]
+    rows = []
+    for name, k, li, lo, ci, co in spec:
+        pin, pout = B * H[li] ** 2, B * H[lo] ** 2
+        rows.append({"layer": name, "nodes_out": H[lo], "c_in": ci, "c_out": co,
+                     "gflop": 2.0 * k * k * ci * co * pout / 1e9,
+                     "activation_mb": (pin * ci * 2 + pout * co * (4 if name == "head" else 2)) / 1e6,
+                     "weight_kb": k * k * ci * co * 2 / 1e3})
+    return rows
+
+
 def measure_unet(dev, peaks, B: int = 16, reps: int = 10):
     import torch
     from paper_0811_4446_gb300 import unet
@@ -958,6 +979,7 @@ def measure_unet(dev, peaks, B: int = 16, reps: int = 10):
                        "frac": res["tcgen05_halo"]["forward_tflops"] / peak,
                        "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
                        "flops_per_sample": unet_conv_flops(), "traffic": None}
+    res["layers"] = unet_layer_table(256, B)
     return res
 
 

@@ -44,3 +44,14 @@ def test_reference_other_ranks_exit_quietly():
     p = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert not [ln for ln in p.stdout.splitlines() if ln.strip().startswith("{")]
+
+
+def test_unet_layer_table_sums_to_the_network_flops():
+    """The per-convolution accounting of the U-Net report adds up to the FLOPs the TFLOP/s
+    figures divide by (2 k^2 C_in C_out per output pixel), at any batch."""
+    import bench
+    for B in (1, 16):
+        rows = bench.unet_layer_table(256, B)
+        assert [r["layer"] for r in rows][:2] == ["e0a", "e0b"] and rows[-1]["layer"] == "head"
+        assert abs(sum(r["gflop"] for r in rows) * 1e9 - bench.unet_conv_flops() * B) <= 1e-6 * bench.unet_conv_flops() * B
+        assert all(r["activation_mb"] > 0 and r["weight_kb"] > 0 for r in rows)
