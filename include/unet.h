@@ -74,10 +74,11 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
  *   3 (default) = as 2, except that the stride-1 ones whose weight matrix fits in 72 KB (the
  *       8-channel first layer too) keep it resident in shared memory and load one 10 x 18-pixel
  *       halo per 32-channel chunk (8-channel plane) for all nine taps (tiles of 8 x 16 output
- *       pixels), the 1x1 head's backward runs on the CUDA cores, the data gradient runs as a forward convolution
- *       of the output gradient with the taps reversed (for stride 2 of the output gradient
- *       spread onto the input grid with zeros between) on the halo kernel where the reversed
- *       weights fit, else for stride 1 on the tile kernel of path 2, and
+ *       pixels), the 1x1 head's backward runs on the CUDA cores, the data gradient runs as a forward
+ *       convolution of the output gradient: for stride 1 with the taps reversed, on the halo
+ *       kernel where the reversed weights fit, else on the tile kernel of path 2; for stride 2 on
+ *       the tile kernel over the output gradient's own grid, once per parity class of the input
+ *       pixels (the 1, 2, 2 or 4 taps that reach it); and
  *       the weight gradient of the 3x3 layers takes both operands by TMA tiled loads (segments
  *       of 64 or 128 output pixels, one load per tap and 32-channel slice, or 8-channel slice
  *       for the first layer); their sums round in another order.

@@ -50,7 +50,6 @@ struct mg_unet {
   Act x, e0a, e0b, e1a, e1b, e2a, e2b, e3a, e3b, u3, d2, u2, d1, u1, d0;
   float *out = nullptr, *dout = nullptr, *tgt = nullptr, *xin = nullptr;
   __nv_bfloat16 *dpre = nullptr;
-  __nv_bfloat16 *dz = nullptr;  // dY of a stride-2 layer spread onto its input grid
   double *loss_d = nullptr, *loss_h = nullptr;
   int *tc_err = nullptr;   // set by a tcgen05 kernel whose bounded wait expired
   int use_tc = 3;          // 1: tcgen05 where the layer shape allows it; 2: TMA-fed where it can; 3: halo loads too
@@ -59,7 +58,7 @@ struct mg_unet {
   ConvMaps wmaps[NL];      // tensor maps of the TMA-fed weight gradients, built on first use
   const void *wmap_key[NL][3] = {};  // their inputs and dY
   ConvMaps dmaps[NL];      // tensor maps of the TMA-fed data gradients, built on first use
-  const void *dmap_key[NL][3] = {};  // their dY, weights and the kind of map (2: tile, 3: halo)
+  const void *dmap_key[NL][3] = {};  // their dY, weights and the kind of map (2: tile, 3: halo, 4: parity)
   int step = 0;
   void *block = nullptr;
   std::string err;
@@ -144,7 +143,6 @@ void layout(mg_unet *n, Carve &c) {
   n->tgt = c.take<float>(P0 * 3);
   n->xin = c.take<float>(P0 * 8);
   n->dpre = c.take<__nv_bfloat16>(P0 * 32);
-  n->dz = c.take<__nv_bfloat16>(P0 * 64);  // the largest: e1a, 64 channels on the finest grid
   n->loss_d = c.take<double>(1);
   n->tc_err = c.take<int>(4);
 }
@@ -254,12 +252,36 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
   int dacc = 1;
   if (want_dx)
     if (int rc = dx_mode(n, B, in1, in2, &dacc)) return rc;
-  if (want_dx && n->use_tc == 3 && a.ks == 3 && (a.stride == 1 || a.stride == 2)) {
-    // dX = dY convolved with the reversed taps (wdf), a stride-1 forward convolution on the input
-    // grid (for stride 2 of dY spread onto that grid with zeros between): on the halo kernel where
-    // the reversed weights fit in 72 KB, else, for stride 1, on the TMA tile kernel where the input
-    // parts have at most 128 channels in all.  (Stride 2 on the tile kernel reads and multiplies
-    // the three zeros of every four spread pixels: measured slower than the gathering kernel.)
+  if (want_dx && n->use_tc == 3 && a.ks == 3 && a.stride == 2) {
+    // stride 2: the tile kernel on dY's own grid, once per output parity class (the taps that
+    // reach that class), with the data-gradient weights wd
+    ConvArgs f;
+    std::memset(&f, 0, sizeof(f));
+    f.Bn = B;
+    f.Hin = f.Hout = a.Hout;
+    f.Win = f.Wout = a.Wout;
+    f.ks = 3; f.stride = 1; f.pad = 1;
+    f.C1 = cop; f.C2 = 0;
+    f.x1 = n->dpre;
+    f.N = f.Cout = f.Nreal = a.C1 + a.C2;
+    f.M = B * a.Hout * a.Wout; f.K = 9 * cop; f.Kf = f.K; f.Pout = f.M;
+    f.w = n->wd[l];
+    f.dx1 = in1.g; f.dx2 = in2 ? in2->g : nullptr; f.dsplit = a.C1; f.dacc = dacc;
+    if (conv_tma_supported(f, MODE_FWD)) {
+      const void *key[3] = {f.x1, f.w, reinterpret_cast<const void *>(4)};
+      if (std::memcmp(key, n->dmap_key[l], sizeof(key)) != 0) {
+        if (int rc = make_conv_maps(f, n->Bmax, &n->dmaps[l]))
+          return fail(n, MG_ECUDA, "data-gradient tensor maps of layer %d: encode step %d failed", l, rc);
+        std::memcpy(n->dmap_key[l], key, sizeof(key));
+      }
+      UK(launch_conv_tma_parity(f, n->dmaps[l], a.Hin, a.Win, n->tc_err, n->st));
+      return MG_OK;
+    }
+  }
+  if (want_dx && n->use_tc == 3 && a.ks == 3 && a.stride == 1) {
+    // stride 1: dX = dY convolved with the reversed taps (wdf), a forward convolution on the
+    // input grid: on the halo kernel where the reversed weights fit in 72 KB, else on the TMA tile
+    // kernel where the input parts have at most 128 channels in all
     ConvArgs f;
     std::memset(&f, 0, sizeof(f));
     f.Bn = B;
@@ -267,15 +289,13 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
     f.Win = f.Wout = a.Win;
     f.ks = 3; f.stride = 1; f.pad = 1;
     f.C1 = cop; f.C2 = 0;
-    f.x1 = a.stride == 1 ? n->dpre : n->dz;
+    f.x1 = n->dpre;
     f.N = f.Cout = f.Nreal = a.C1 + a.C2;
     f.M = B * a.Hin * a.Win; f.K = 9 * cop; f.Kf = f.K; f.Pout = f.M;
     f.w = n->wdf[l];
     f.dx1 = in1.g; f.dx2 = in2 ? in2->g : nullptr; f.dsplit = a.C1; f.dacc = dacc;
     const bool halo = conv_halo_supported(f, MODE_FWD);
-    const bool tile = !halo && a.stride == 1 && conv_tma_supported(f, MODE_FWD);
-    if (halo || tile) {
-      if (a.stride == 2) UK(launch_zero_insert(n->dpre, n->dz, B, a.Hout, a.Wout, cop, n->st));
+    if (halo || conv_tma_supported(f, MODE_FWD)) {
       const void *key[3] = {f.x1, f.w, reinterpret_cast<const void *>(halo ? 3 : 2)};
       if (std::memcmp(key, n->dmap_key[l], sizeof(key)) != 0) {
         if (int rc = halo ? make_halo_maps(f, n->Bmax, &n->dmaps[l]) : make_conv_maps(f, n->Bmax, &n->dmaps[l]))

@@ -27,7 +27,7 @@ struct ConvArgs {
   float *y32;                     // or FP32 (network head)
   float *dx1, *dx2;               // data gradient of the two input parts (FP32, accumulated)
   float *dw;                      // weight gradient [M][N] (FP32, atomically accumulated)
-  int dsplit;                     // data gradient as a forward convolution of dY (halo kernel): output
+  int dsplit;                     // data gradient as a forward convolution of dY (halo / tile kernel): output
                                   // channels [0, dsplit) go to dx1, the rest to dx2
   int dacc;                       // data gradient: 1 = add into dx1 / dx2, 0 = overwrite them (the
                                   // first contribution of the backward pass)
@@ -48,6 +48,9 @@ struct ConvMaps {
 bool conv_tma_supported(const ConvArgs &a, int mode);
 int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m);
 cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st);
+// the same kernel as the data gradient of a stride-2 layer, split by output parity (a describes a
+// stride-1 convolution of dY on its own grid with the data-gradient weights; output on Hf x Wf)
+cudaError_t launch_conv_tma_parity(const ConvArgs &a, const ConvMaps &m, int Hf, int Wf, int *err, cudaStream_t st);
 // TMA-fed tcgen05 weight gradient (3x3, stride 1 or 2, input parts of a multiple of 32 channels,
 // 32 <= N <= 128, N % 32 == 0): tensor maps of the two input parts and of dY (in ConvMaps::w);
 // adds into a.dw
@@ -71,8 +74,6 @@ cudaError_t launch_conv1x1_dgrad(const ConvArgs &a, const __nv_bfloat16 *dy, con
                                  int dacc, cudaStream_t st);
 cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C, cudaStream_t st);
-// dY of a stride-2 layer (h x w) spread onto the (2h - 1) x (2w - 1) input grid with zeros between
-cudaError_t launch_zero_insert(const __nv_bfloat16 *dy, __nv_bfloat16 *dz, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,
                        cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, int step, cudaStream_t st);

@@ -295,30 +295,6 @@ cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, 
   return cudaGetLastError();
 }
 
-// dY of a stride-2 3x3 convolution spread onto its input grid: dz[b][y][x] = dy[b][y/2][x/2] at
-// even (y, x), zero elsewhere (H = 2h - 1, W = 2w - 1), so that the data gradient is the stride-1
-// convolution of dz with the reversed taps; one 16-byte group of 8 channels per thread.
-__global__ void k_zero_insert(const __nv_bfloat16 *dy, __nv_bfloat16 *dz, int B, int h, int w, int C) {
-  const unsigned H = 2 * h - 1, W = 2 * w - 1, G = C / 8;
-  const unsigned n = (unsigned)B * H * W * G;
-  const uint4 *src = reinterpret_cast<const uint4 *>(dy);
-  uint4 *dst = reinterpret_cast<uint4 *>(dz);
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const unsigned g = i % G, t = i / G, x = t % W, t2 = t / W, y = t2 % H, b = t2 / H;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (!(x & 1) && !(y & 1)) v = src[(((size_t)b * h + (y >> 1)) * w + (x >> 1)) * G + g];
-    dst[i] = v;
-  }
-}
-
-cudaError_t launch_zero_insert(const __nv_bfloat16 *dy, __nv_bfloat16 *dz, int B, int h, int w, int C, cudaStream_t st) {
-  const size_t n = (size_t)B * (2 * h - 1) * (2 * w - 1) * (C / 8);
-  if (C % 8 || n >= (1u << 31)) return cudaErrorInvalidValue;
-  k_zero_insert<<<(unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)), 256, 0, st>>>(dy, dz, B, h, w,
-                                                                                                             C);
-  return cudaGetLastError();
-}
-
 // Transpose of the upsampling on FP32 gradients: dc[Y][X] = sum of fine gradients weighted by
 // the interpolation weights of node (Y, X) (the coarse tensor's only consumer is the upsampling,
 // so this is its whole gradient); four channels (one float4) per thread.

@@ -94,10 +94,35 @@ __device__ __forceinline__ void tile_origin(const TileGrid &g, int t, int &x0, i
   x0 = (r % g.tx) * TM_X;
 }
 
+// The tile kernel as the data gradient of a stride-2 3x3 convolution, split by output parity:
+// input pixel (2Y + a, 2X + c) receives the taps (kh, kw) with kh = a + 1 and kw = c + 1 (mod 2),
+// which read dY at (Y + (a + 1 - kh) / 2, X + (c + 1 - kw) / 2).  So class (a, c) is a stride-1
+// convolution of dY on the coarse grid with 1, 2, 2 or 4 taps (each tap's K block of the
+// data-gradient weights wd), written at every second input pixel.  The tiles of the four classes
+// follow one another in the launch.
+struct ParityTaps {
+  int on;             // 0: a plain convolution (nine taps, output at the tile's pixels)
+  int per_class;      // tiles of one class
+  int Hf, Wf;         // the input (fine) grid the gradient is written on
+  int n[4];           // taps of class 2 a + c
+  int dx[4][4], dy[4][4], tap[4][4];
+};
+
+__device__ __forceinline__ void tile_of(const TileGrid &g, const ParityTaps &pt, int t, int &x0, int &y0, int &b,
+                                        int &cls) {
+  cls = 0;
+  if (pt.on) {
+    cls = t / pt.per_class;
+    t -= cls * pt.per_class;
+  }
+  tile_origin(g, t, x0, y0, b);
+}
+
 __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__ CUtensorMap mx1,
                                                          const __grid_constant__ CUtensorMap mx2,
                                                          const __grid_constant__ CUtensorMap mw, ConvArgs a,
-                                                         TileGrid tg, int S, int tmem_cols, int *err) {
+                                                         TileGrid tg, ParityTaps pt, int S, int tmem_cols,
+                                                         int *err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int BN = a.N;
   const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
@@ -140,21 +165,32 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
                    pmw = reinterpret_cast<uint64_t>(&mw);
     long g = 0;  // chunks issued so far
     for (int t = blockIdx.x; t < tg.ntiles && !*abort; t += gridDim.x) {
-      int x0, y0, b;
-      tile_origin(tg, t, x0, y0, b);
-      for (int k = 0; k < nk; ++k, ++g) {
+      int x0, y0, b, cls;
+      tile_of(tg, pt, t, x0, y0, b, cls);
+      const int nkt = pt.on ? pt.n[cls] * per_tap : nk;
+      for (int k = 0; k < nkt; ++k, ++g) {
         const int s = (int)(g % S);
         const uint32_t use = (uint32_t)(g / S);
         if (use > 0 && !wait_bounded(saddr(&empty[s]), (use - 1) & 1, abort)) break;
-        const int tap = k / per_tap, q = k - tap * per_tap;
-        const int kh = tap / 3, kw = tap - kh * 3;
+        const int i = k / per_tap, q = k - i * per_tap;
+        int tap, xs, ys;
+        if (pt.on) {
+          tap = pt.tap[cls][i];
+          xs = x0 + pt.dx[cls][i];
+          ys = y0 + pt.dy[cls][i];
+        } else {
+          tap = i;
+          const int kh = tap / 3, kw = tap - kh * 3;
+          xs = x0 * a.stride + kw - 1;
+          ys = y0 * a.stride + kh - 1;
+        }
         const uint64_t mx = q < c1 ? pm1 : pm2;
         const int cc = (q < c1 ? q : q - c1) * TM_CH;
         const uint32_t sa = base + (uint32_t)s * st_bytes, sb = sa + a_bytes, bar = saddr(&full[s]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(st_bytes) : "memory");
         asm volatile(
             "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-            ::"r"(sa), "l"(mx), "r"(cc), "r"(x0 * a.stride + kw - 1), "r"(y0 * a.stride + kh - 1), "r"(b), "r"(bar)
+            ::"r"(sa), "l"(mx), "r"(cc), "r"(xs), "r"(ys), "r"(b), "r"(bar)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -178,7 +214,8 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
       if (j >= 2 && !(ok = wait_bounded(saddr(&acc_empty[ab]), (uint32_t)(((j >> 1) - 1) & 1), abort))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc_t = tmem + (uint32_t)(ab * (tmem_cols >> 1));
-      for (int k = 0; k < nk; ++k, ++g) {
+      const int nkt = pt.on ? pt.n[t / pt.per_class] * per_tap : nk;
+      for (int k = 0; k < nkt; ++k, ++g) {
         const int s = (int)(g % S);
         if (!(ok = wait_bounded(saddr(&full[s]), (uint32_t)((g / S) & 1), abort))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -213,11 +250,17 @@ __global__ void __launch_bounds__(TM_THREADS) k_conv_tma(const __grid_constant__
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      int x0, y0, b;
-      tile_origin(tg, t, x0, y0, b);
-      const int xx = x0 + (m % TM_X), yy = y0 + (m / TM_X);
-      const bool inside = xx < a.Wout && yy < a.Hout;
-      const size_t pix = ((size_t)b * a.Hout + yy) * a.Wout + xx;
+      int x0, y0, b, cls;
+      tile_of(tg, pt, t, x0, y0, b, cls);
+      int xx = x0 + (m % TM_X), yy = y0 + (m / TM_X), Wo = a.Wout, Ho = a.Hout;
+      if (pt.on) {  // class (a, c) of the parity split: every second input pixel
+        xx = 2 * xx + (cls & 1);
+        yy = 2 * yy + (cls >> 1);
+        Wo = pt.Wf;
+        Ho = pt.Hf;
+      }
+      const bool inside = xx < Wo && yy < Ho;
+      const size_t pix = ((size_t)b * Ho + yy) * Wo + xx;
       for (int n0 = 0; n0 < BN; n0 += 16) {
         uint32_t r[16];
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * (tmem_cols >> 1) + n0);
@@ -800,7 +843,8 @@ EncodeTiled encoder() {
 }  // namespace
 
 // Forward (bf16 output into a.y) or, with a.dx1 set, a data gradient written as a forward
-// convolution of (zero-inserted, for stride 2) dY with the reversed taps: FP32 into dx1 / dx2.
+// convolution of dY (stride 1: with the reversed taps; stride 2: split by output parity, see
+// ParityTaps): FP32 into dx1 / dx2.
 bool conv_tma_supported(const ConvArgs &a, int mode) {
   const bool out_ok = a.dx1 ? (!a.y && !a.y32 && a.dsplit > 0 && a.dsplit % TM_CH == 0 && a.dsplit <= a.N &&
                                (a.dsplit == a.N || a.dx2))
@@ -923,7 +967,10 @@ size_t smem_for(int BN) { return 1024 + (size_t)stages_for(BN) * (TM_X * TM_Y * 
 
 }  // namespace
 
-cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st) {
+namespace {
+
+cudaError_t launch_conv_tma_impl(const ConvArgs &a, const ConvMaps &m, const ParityTaps &pt, int *err,
+                                 cudaStream_t st) {
   const int BN = a.N, S = stages_for(BN), cols = tmem_cols_of(2 * BN);
   const size_t smem = smem_for(BN);
   cudaError_t e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -944,9 +991,49 @@ cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cuda
   tg.ty = (a.Hout + TM_Y - 1) / TM_Y;
   tg.per_img = tg.tx * tg.ty;
   tg.ntiles = tg.per_img * a.Bn;
+  ParityTaps p = pt;
+  if (p.on) {
+    p.per_class = tg.ntiles;
+    tg.ntiles *= 4;
+  }
   const int grid = std::max(1, std::min(tg.ntiles, sms * occ));
-  k_conv_tma<<<grid, TM_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, tg, S, cols, err);
+  k_conv_tma<<<grid, TM_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, tg, p, S, cols, err);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_conv_tma(const ConvArgs &a, const ConvMaps &m, int *err, cudaStream_t st) {
+  ParityTaps off;
+  std::memset(&off, 0, sizeof(off));
+  return launch_conv_tma_impl(a, m, off, err, st);
+}
+
+// Data gradient of a stride-2 3x3 layer on the coarse grid of dY (a: a stride-1 convolution of dY,
+// a.x1 = dY with C1 = its channels, Hout x Wout = dY's grid, a.w = wd, the data-gradient weights
+// with the taps in their own order, the FP32 data-gradient outputs), written on the Hf x Wf input
+// grid by output parity.
+cudaError_t launch_conv_tma_parity(const ConvArgs &a, const ConvMaps &m, int Hf, int Wf, int *err, cudaStream_t st) {
+  ParityTaps p;
+  std::memset(&p, 0, sizeof(p));
+  p.on = 1;
+  p.Hf = Hf;
+  p.Wf = Wf;
+  for (int pa = 0; pa < 2; ++pa)
+    for (int pc = 0; pc < 2; ++pc) {
+      const int cls = 2 * pa + pc;
+      int n = 0;
+      for (int kh = 0; kh < 3; ++kh)
+        for (int kw = 0; kw < 3; ++kw) {
+          if ((kh + pa + 1) % 2 || (kw + pc + 1) % 2) continue;  // kh = a + 1, kw = c + 1 (mod 2)
+          p.dy[cls][n] = (pa + 1 - kh) / 2;
+          p.dx[cls][n] = (pc + 1 - kw) / 2;
+          p.tap[cls][n] = 3 * kh + kw;
+          ++n;
+        }
+      p.n[cls] = n;
+    }
+  return launch_conv_tma_impl(a, m, p, err, st);
 }
 
 namespace {
