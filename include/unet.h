@@ -54,34 +54,39 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
 
 /* Tensor-core path of the convolutions: a parity and measurement reference, not a choice a
  * user makes.  The network runs on path 3 (the default), which assigns one kernel to each
- * layer shape: the halo-load tcgen05 kernel (the forward of stride-1 layers whose weights fit in
- * 72 KB, the 8-channel first layer included, and the data gradient where the reversed weights
- * fit), the TMA-tile tcgen05 forward
- * (the other 3x3 layers with 32-channel input parts; also the other stride-1 data gradients), the TMA-fed tcgen05 weight gradient (every
- * 3x3 layer), the gathering tcgen05 kernel (the other data gradients) and the FP32 CUDA-core head (forward and backward).  Paths 0-2 keep the earlier kernels
- * of those layers so that the tests can compare each layer's kernel with the one it replaced
- * (same operands, another order of the sums) and the benchmark can report what each
- * replacement gained:
+ * layer shape:
+ *   - the halo-load tcgen05 kernel: the forward of the stride-1 layers whose weights fit in
+ *     72 KB (the 8-channel first layer included) and the stride-1 data gradients whose reversed
+ *     weights fit;
+ *   - the TMA-tile tcgen05 kernel: the other 3x3 forward convolutions, the other stride-1 data
+ *     gradients with at most 128 input channels, and the stride-2 data gradients;
+ *   - the TMA-fed tcgen05 weight gradient: every 3x3 layer;
+ *   - the thread-gathering tcgen05 kernel: the remaining data gradient (d2, 224 channels);
+ *   - FP32 CUDA-core kernels: the 1x1 head, forward and backward.
+ * Paths 0-2 keep the earlier kernels of those layers so that the tests can compare each layer's
+ * kernel with the one it replaced (same operands, another order of the sums) and the benchmark
+ * can report what each replacement gained:
  *   0 = mma.sync for every convolution.
  *   1 = tcgen05.mma with the accumulator in tensor memory for the forward and data-gradient
  *       convolutions whose output width is a multiple of 16 (<= 256) and the weight gradients
  *       with 32 <= output channels <= 128, operands gathered by threads (for the weight
- *       gradient MN-major, straight from the NHWC tensors); the 1x1 head's forward (8 FP32
- *       outputs) on an FP32-accumulating CUDA-core kernel; the rest on mma.sync.
- *   2 = as 1, except that the forward 3x3 convolutions (stride 1 or 2) whose input
- *       parts have a multiple of 32 channels take their operands by TMA tiled loads (tiles of
- *       16 x 8 output pixels, the padding read as the loads' zero fill) in a persistent kernel.
- *   3 (default) = as 2, except that the stride-1 ones whose weight matrix fits in 72 KB (the
- *       8-channel first layer too) keep it resident in shared memory and load one 10 x 18-pixel
- *       halo per 32-channel chunk (8-channel plane) for all nine taps (tiles of 8 x 16 output
- *       pixels), the 1x1 head's backward runs on the CUDA cores, the data gradient runs as a forward
- *       convolution of the output gradient: for stride 1 with the taps reversed, on the halo
- *       kernel where the reversed weights fit, else on the tile kernel of path 2; for stride 2 on
- *       the tile kernel over the output gradient's own grid, once per parity class of the input
- *       pixels (the 1, 2, 2 or 4 taps that reach it); and
- *       the weight gradient of the 3x3 layers takes both operands by TMA tiled loads (segments
- *       of 64 or 128 output pixels, one load per tap and 32-channel slice, or 8-channel slice
- *       for the first layer); their sums round in another order.
+ *       gradient MN-major, straight from the NHWC tensors); the 1x1 head, forward and backward,
+ *       on FP32 CUDA-core kernels; the rest on mma.sync.
+ *   2 = as 1, except that the forward 3x3 convolutions (stride 1 or 2) whose input parts have a
+ *       multiple of 32 channels take their operands by TMA tiled loads (tiles of 16 x 8 output
+ *       pixels, the padding read as the loads' zero fill) in a persistent kernel.
+ *   3 (default) = as 2, except that
+ *       - the stride-1 forward convolutions whose weight matrix fits in 72 KB (the 8-channel
+ *         first layer too) keep it resident in shared memory and load one 10 x 18-pixel halo
+ *         per 32-channel chunk (8-channel plane) for all nine taps (tiles of 8 x 16 pixels);
+ *       - the data gradient runs as a forward convolution of the output gradient: for stride 1
+ *         with the taps reversed, on the halo kernel where the reversed weights fit, else on the
+ *         tile kernel; for stride 2 on the tile kernel over the output gradient's own grid, once
+ *         per parity class of the input pixels (the 1, 2, 2 or 4 taps that reach it);
+ *       - the weight gradient of the 3x3 layers takes both operands by TMA tiled loads (segments
+ *         of 64 or 128 output pixels, one load per tap and 32-channel slice, or 8-channel slice
+ *         for the first layer).
+ *       Their sums round in another order.
  * Any other value returns MG_EINVAL.  A tcgen05 kernel whose bounded wait expires makes the next
  * call return MG_ETIMEOUT. */
 int mg_unet_set_tensor_path(mg_unet *n, int path);
