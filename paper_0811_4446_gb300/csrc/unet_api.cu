@@ -50,6 +50,7 @@ struct mg_unet {
   Act x, e0a, e0b, e1a, e1b, e2a, e2b, e3a, e3b, u3, d2, u2, d1, u1, d0;
   float *out = nullptr, *dout = nullptr, *tgt = nullptr, *xin = nullptr;
   __nv_bfloat16 *dpre = nullptr;
+  __nv_bfloat16 *dpre_head = nullptr;  // the head's output gradient when d0's output stage folds it in
   double *loss_d = nullptr, *loss_h = nullptr;
   int *tc_err = nullptr;   // set by a tcgen05 kernel whose bounded wait expired
   int use_tc = 3;          // 1: tcgen05 where the layer shape allows it; 2: TMA-fed where it can; 3: halo loads too
@@ -143,6 +144,7 @@ void layout(mg_unet *n, Carve &c) {
   n->tgt = c.take<float>(P0 * 3);
   n->xin = c.take<float>(P0 * 8);
   n->dpre = c.take<__nv_bfloat16>(P0 * 32);
+  n->dpre_head = c.take<__nv_bfloat16>(P0 * 8);
   n->loss_d = c.take<double>(1);
   n->tc_err = c.take<int>(4);
 }
@@ -216,23 +218,31 @@ int dx_mode(mg_unet *n, int B, Act &in1, Act *in2, int *dacc) {
   return MG_OK;
 }
 
-int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const float *dout32, bool want_dx) {
+// dpre_buf (may be null: dpre) receives the layer's bf16 output gradient; head_dy (may be null)
+// makes the layer's output stage the fused head data gradient + ReLU + bias pass
+int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const float *dout32, bool want_dx,
+             __nv_bfloat16 *dpre_buf = nullptr, const __nv_bfloat16 *head_dy = nullptr) {
+  __nv_bfloat16 *const dpre = dpre_buf ? dpre_buf : n->dpre;
   ConvArgs a = conv_args(n, l, B, in1, in2);
   const size_t P = (size_t)a.Pout;
   const int cop = a.Cout;
-  UK(launch_relu_bias_bwd(out ? out->g : dout32, out ? out->a : nullptr, n->dpre, n->grad + n->boff[l], (int)P, cop,
-                          kL[l].co, out ? kL[l].relu : 0, n->st));
+  if (head_dy)
+    UK(launch_head_relu_bias_bwd(head_dy, n->wd[HEAD], out->a, dpre, n->grad + n->boff[l], (int)P, cop, kL[l].co,
+                                 n->st));
+  else
+    UK(launch_relu_bias_bwd(out ? out->g : dout32, out ? out->a : nullptr, dpre, n->grad + n->boff[l], (int)P, cop,
+                            kL[l].co, out ? kL[l].relu : 0, n->st));
   // weight gradient: GEMM (kh, kw, ci) x cop over the output pixels, split over pixel ranges;
   // added straight into the (zeroed) gradient vector where no output channel is padded, else
   // into the padded buffer and copied over
   ConvArgs w = a;
   w.M = a.Kf; w.N = cop; w.K = a.Pout;
-  w.dy = n->dpre;
+  w.dy = dpre;
   const bool padded = cop != kL[l].co;
   w.dw = padded ? n->dwpad : n->grad + n->woff[l];
   if (padded) UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), n->st));
   if (n->use_tc && conv1x1_bwd_supported(a)) {
-    UK(launch_conv1x1_wgrad(a, n->dpre, n->dwpad, n->st));
+    UK(launch_conv1x1_wgrad(a, dpre, n->dwpad, n->st));
   } else if (n->use_tc == 3 && wgrad_tma_supported(w)) {
     const void *key[3] = {w.x1, w.x2, w.dy};
     if (std::memcmp(key, n->wmap_key[l], sizeof(key)) != 0) {
@@ -262,7 +272,7 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
     f.Win = f.Wout = a.Wout;
     f.ks = 3; f.stride = 1; f.pad = 1;
     f.C1 = cop; f.C2 = 0;
-    f.x1 = n->dpre;
+    f.x1 = dpre;
     f.N = f.Cout = f.Nreal = a.C1 + a.C2;
     f.M = B * a.Hout * a.Wout; f.K = 9 * cop; f.Kf = f.K; f.Pout = f.M;
     f.w = n->wd[l];
@@ -289,7 +299,7 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
     f.Win = f.Wout = a.Win;
     f.ks = 3; f.stride = 1; f.pad = 1;
     f.C1 = cop; f.C2 = 0;
-    f.x1 = n->dpre;
+    f.x1 = dpre;
     f.N = f.Cout = f.Nreal = a.C1 + a.C2;
     f.M = B * a.Hin * a.Win; f.K = 9 * cop; f.Kf = f.K; f.Pout = f.M;
     f.w = n->wdf[l];
@@ -308,14 +318,14 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
     }
   }
   if (want_dx && n->use_tc && conv1x1_bwd_supported(a)) {
-    UK(launch_conv1x1_dgrad(a, n->dpre, n->wd[l], in1.g, dacc, n->st));
+    UK(launch_conv1x1_dgrad(a, dpre, n->wd[l], in1.g, dacc, n->st));
     return MG_OK;
   }
   if (want_dx) {
     ConvArgs d = a;
     d.M = B * a.Hin * a.Win; d.N = a.C1 + a.C2; d.K = a.ks * a.ks * cop;
     d.w = n->wd[l];
-    d.dy = n->dpre;
+    d.dy = dpre;
     d.dx1 = in1.g;
     d.dx2 = in2 ? in2->g : nullptr;
     d.dacc = dacc;
@@ -362,8 +372,13 @@ int backward(mg_unet *n, int B) {
                 &n->e3b, &n->u3, &n->d2, &n->u2, &n->d1, &n->u1, &n->d0};
   for (Act *t : all) t->gw = false;
   UK(cudaMemsetAsync(n->grad, 0, n->nparam * sizeof(float), n->st));
-  if ((rc = conv_bwd(n, HEAD, B, n->d0, nullptr, nullptr, n->dout, true))) return rc;
-  if ((rc = conv_bwd(n, D0, B, n->u1, &n->e0b, &n->d0, nullptr, true))) return rc;
+  // with the head's backward on the CUDA cores its data gradient is folded into d0's output
+  // stage (never stored): the head's bf16 output gradient goes to its own buffer for that
+  const ConvArgs ha = conv_args(n, HEAD, B, n->d0, nullptr);
+  const bool fold = n->use_tc && conv1x1_bwd_supported(ha) && kL[D0].relu && kL[D0].co == n->d0.C;
+  if ((rc = conv_bwd(n, HEAD, B, n->d0, nullptr, nullptr, n->dout, !fold, fold ? n->dpre_head : nullptr))) return rc;
+  if ((rc = conv_bwd(n, D0, B, n->u1, &n->e0b, &n->d0, nullptr, true, nullptr, fold ? n->dpre_head : nullptr)))
+    return rc;
   UK(launch_upsample_bwd(n->u1.g, n->d1.g, B, n->d1.H, n->d1.W, n->d1.C, n->st));
   n->d1.gw = true;
   if ((rc = conv_bwd(n, D1, B, n->u2, &n->e1b, &n->d1, nullptr, true))) return rc;

@@ -67,6 +67,10 @@ cudaError_t launch_conv1x1_f32(const ConvArgs &a, cudaStream_t st);
 // ReLU mask, bf16 rounding of the output gradient and the bias gradient in one pass
 cudaError_t launch_relu_bias_bwd(const float *dout, const __nv_bfloat16 *out, __nv_bfloat16 *dpre, float *db, int P,
                                  int C, int Creal, int relu, cudaStream_t st);
+// the output stage of the layer feeding the head, fed by the head's output gradient dyh (8
+// channels): the head's data gradient, ReLU mask, bf16 rounding and bias gradient in one pass
+cudaError_t launch_head_relu_bias_bwd(const __nv_bfloat16 *dyh, const __nv_bfloat16 *wd, const __nv_bfloat16 *out,
+                                      __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st);
 // backward of the 1x1 head (C1 <= 64 input channels, 8 padded output channels) on the CUDA cores
 bool conv1x1_bwd_supported(const ConvArgs &a);
 cudaError_t launch_conv1x1_wgrad(const ConvArgs &a, const __nv_bfloat16 *dy, float *dw, cudaStream_t st);

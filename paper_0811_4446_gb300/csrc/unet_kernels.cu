@@ -258,6 +258,73 @@ cudaError_t launch_relu_bias_bwd(const float *dout, const __nv_bfloat16 *out, __
   return cudaGetLastError();
 }
 
+// The output stage of the layer feeding the 1x1 head (d0), fed straight by the head's output
+// gradient: g[p][c] = sum_o dyh[p][o] wd[c][o] (the head's data gradient, 8 outputs, never
+// stored), then the ReLU mask by the layer's output, bf16 rounding into dpre and the bias
+// gradient, in one pass.  Mapping and reduction as k_relu_bias_bwd; the head's 8 x C weights
+// in shared memory as FP32 (padded rows), the sum over o in order in FP32.
+__global__ void __launch_bounds__(256) k_head_relu_bias_bwd(const __nv_bfloat16 *dyh, const __nv_bfloat16 *wd,
+                                                               const __nv_bfloat16 *out, __nv_bfloat16 *dpre,
+                                                               float *db, int P, int C, int Creal) {
+  // rows of 9 floats: the four channel groups a warp's threads read at once fall in distinct banks
+  __shared__ float ws[64 * 9];
+  for (int i = threadIdx.x; i < 8 * C; i += blockDim.x) ws[(i / 8) * 9 + i % 8] = __bfloat162float(wd[i]);
+  __syncthreads();
+  const int G = C / 8, rows = 256 / G;
+  const int g = threadIdx.x % G, r = threadIdx.x / G;
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (r < rows)
+    for (int p = blockIdx.x * rows + r; p < P; p += gridDim.x * rows) {
+      const size_t i = (size_t)p * G + g;
+      const uint4 q = reinterpret_cast<const uint4 *>(dyh)[p];
+      const __nv_bfloat16 *qh = reinterpret_cast<const __nv_bfloat16 *>(&q);
+      float d[8];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) d[o] = __bfloat162float(qh[o]);
+      const uint4 ov = reinterpret_cast<const uint4 *>(out)[i];
+      const __nv_bfloat16 *ob = reinterpret_cast<const __nv_bfloat16 *>(&ov);
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        // volatile: read in the loop (conflict-free), not hoisted into 64 registers, which would
+        // halve the blocks an SM holds and the loads in flight
+        const volatile float *w = ws + (8 * g + e) * 9;
+        float t = 0.f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) t = fmaf(d[o], w[o], t);
+        v[e] = __bfloat162float(ob[e]) > 0.f ? t : 0.f;
+      }
+      uint32_t pk[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+        pk[e] = *reinterpret_cast<const uint32_t *>(&h);
+        s[2 * e] += __low2float(h);
+        s[2 * e + 1] += __high2float(h);
+      }
+      reinterpret_cast<uint4 *>(dpre)[i] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+  __shared__ float sh[256][9];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) sh[threadIdx.x][e] = s[e];
+  __syncthreads();
+  if ((int)threadIdx.x < Creal) {
+    const int c = threadIdx.x, gg = c / 8, e = c % 8;
+    float t = 0.f;
+    for (int rr = 0; rr < rows; ++rr) t += sh[rr * G + gg][e];
+    atomicAdd(&db[c], t);
+  }
+}
+
+cudaError_t launch_head_relu_bias_bwd(const __nv_bfloat16 *dyh, const __nv_bfloat16 *wd, const __nv_bfloat16 *out,
+                                      __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st) {
+  if (C % 8 || C > 64 || Creal > C) return cudaErrorInvalidValue;
+  const int rows = 256 / (C / 8);
+  k_head_relu_bias_bwd<<<std::max(1, std::min(152 * 4, (P + rows - 1) / rows)), 256, 0, st>>>(dyh, wd, out, dpre, db,
+                                                                                              P, C, Creal);
+  return cudaGetLastError();
+}
+
 // Node-aligned bilinear upsampling of NHWC bf16: (h, w) -> (2h - 1, 2w - 1); one 16-byte group
 // of 8 channels per thread (C a multiple of 8), 32-bit indices (host-checked).
 __global__ void k_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C) {
