@@ -317,10 +317,6 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
       return MG_OK;
     }
   }
-  if (want_dx && n->use_tc && conv1x1_bwd_supported(a)) {
-    UK(launch_conv1x1_dgrad(a, dpre, n->wd[l], in1.g, dacc, n->st));
-    return MG_OK;
-  }
   if (want_dx) {
     ConvArgs d = a;
     d.M = B * a.Hin * a.Win; d.N = a.C1 + a.C2; d.K = a.ks * a.ks * cop;

@@ -71,11 +71,10 @@ cudaError_t launch_relu_bias_bwd(const float *dout, const __nv_bfloat16 *out, __
 // channels): the head's data gradient, ReLU mask, bf16 rounding and bias gradient in one pass
 cudaError_t launch_head_relu_bias_bwd(const __nv_bfloat16 *dyh, const __nv_bfloat16 *wd, const __nv_bfloat16 *out,
                                       __nv_bfloat16 *dpre, float *db, int P, int C, int Creal, cudaStream_t st);
-// backward of the 1x1 head (C1 <= 64 input channels, 8 padded output channels) on the CUDA cores
+// weight gradient of the 1x1 head (C1 <= 64 input channels, 8 padded output channels) on the CUDA
+// cores (its data gradient: launch_head_relu_bias_bwd)
 bool conv1x1_bwd_supported(const ConvArgs &a);
 cudaError_t launch_conv1x1_wgrad(const ConvArgs &a, const __nv_bfloat16 *dy, float *dw, cudaStream_t st);
-cudaError_t launch_conv1x1_dgrad(const ConvArgs &a, const __nv_bfloat16 *dy, const __nv_bfloat16 *wd, float *dx,
-                                 int dacc, cudaStream_t st);
 cudaError_t launch_upsample(const __nv_bfloat16 *in, __nv_bfloat16 *out, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_upsample_bwd(const float *dfine, float *dcoarse, int B, int h, int w, int C, cudaStream_t st);
 cudaError_t launch_mse(const float *y, const float *t, float *dy, size_t P, int ld, int nc, double *loss,

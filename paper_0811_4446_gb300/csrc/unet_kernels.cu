@@ -583,40 +583,6 @@ __global__ void __launch_bounds__(512) k_conv1x1_wgrad(const __nv_bfloat16 *x, i
   atomicAdd(&dw[c * 8 + o], acc);
 }
 
-// Data gradient of the head: dx[p][c] (+)= sum_o dy[p][o] wd[c][o], one pixel per thread, the
-// 8 x C weights in shared memory as FP32; dacc = 0 overwrites dx.
-__global__ void __launch_bounds__(256) k_conv1x1_dgrad(const __nv_bfloat16 *dy, const __nv_bfloat16 *wd, int C, int P,
-                                                       float *dx, int dacc) {
-  __shared__ float ws[64 * 8];
-  for (int i = threadIdx.x; i < 8 * C; i += blockDim.x) ws[i] = __bfloat162float(wd[i]);
-  __syncthreads();
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    const uint4 q = *reinterpret_cast<const uint4 *>(dy + (size_t)p * 8);
-    const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q);
-    float d[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) d[e] = __bfloat162float(h[e]);
-    float4 *dst = reinterpret_cast<float4 *>(dx + (size_t)p * C);
-    for (int g = 0; g < C / 4; ++g) {
-      float v[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float *w = ws + (4 * g + e) * 8;
-        float t = 0.f;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) t = fmaf(d[o], w[o], t);
-        v[e] = t;
-      }
-      float4 r = make_float4(v[0], v[1], v[2], v[3]);
-      if (dacc) {
-        const float4 old = dst[g];
-        r.x += old.x; r.y += old.y; r.z += old.z; r.w += old.w;
-      }
-      dst[g] = r;
-    }
-  }
-}
-
 bool conv1x1_bwd_supported(const ConvArgs &a) {
   return a.ks == 1 && a.stride == 1 && a.pad == 0 && a.Cout == 8 && a.C2 == 0 && a.C1 % 8 == 0 && a.C1 >= 8 &&
          a.C1 <= 64;
@@ -626,14 +592,6 @@ cudaError_t launch_conv1x1_wgrad(const ConvArgs &a, const __nv_bfloat16 *dy, flo
   if (!conv1x1_bwd_supported(a)) return cudaErrorInvalidValue;
   const int blocks = std::max(1, std::min((a.Pout + K1_TP - 1) / K1_TP, 152 * 4));
   k_conv1x1_wgrad<<<blocks, 8 * a.C1, 0, st>>>(a.x1, a.C1, dy, a.Pout, dw);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_conv1x1_dgrad(const ConvArgs &a, const __nv_bfloat16 *dy, const __nv_bfloat16 *wd, float *dx,
-                                 int dacc, cudaStream_t st) {
-  if (!conv1x1_bwd_supported(a)) return cudaErrorInvalidValue;
-  const int blocks = std::max(1, std::min((a.Pout + 255) / 256, 152 * 8));
-  k_conv1x1_dgrad<<<blocks, 256, 0, st>>>(dy, wd, a.C1, a.Pout, dx, dacc);
   return cudaGetLastError();
 }
 
