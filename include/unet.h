@@ -19,6 +19,10 @@
  * followed by its biases b[c_out].
  * Input x: B x H x W x 8 FP32 (NHWC; channels 5..7 zero), output y: B x H x W x 3 FP32.
  * `where`: MG_HOST or MG_DEVICE (mg.h) for the caller arrays.  Calls synchronise the stream.
+ * The kernels of a forward pass, and of a loss-and-gradient pass, run as a CUDA graph per batch
+ * size (captured on the network's own stream at the first call with that size, replayed on the
+ * caller's stream); the input copies, the Adam update and the bf16 weight copies are launched
+ * around it.
  * Return values: MG_OK or a negative MG_E* code of mg.h.
  */
 #ifndef PAPER_0811_4446_GB300_UNET_H

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/mg.h"
 #include "../../include/unet.h"
@@ -63,6 +64,10 @@ struct mg_unet {
   int step = 0;
   void *block = nullptr;
   std::string err;
+  // The kernels of a forward pass, and of forward + loss + backward, as CUDA graphs per batch
+  // size for the current tensor path (captured on a private stream, launched on the caller's)
+  cudaStream_t cap = nullptr;
+  std::vector<cudaGraphExec_t> gfwd, gtrain;
 };
 
 namespace {
@@ -410,19 +415,67 @@ int check_tc(mg_unet *n) {
 int load_input(mg_unet *n, const float *x, int B, int where) {
   const size_t e = (size_t)B * n->H * n->H * 8;
   UK(cudaMemcpyAsync(n->xin, x, e * sizeof(float), kin(where), n->st));
-  UK(launch_f32_to_bf16(n->xin, n->x.a, e, n->st));
+  return MG_OK;
+}
+
+// the device work of a forward pass from the FP32 input in xin
+int forward_body(mg_unet *n, int B) {
+  UK(launch_f32_to_bf16(n->xin, n->x.a, (size_t)B * n->H * n->H * 8, n->st));
+  return forward(n, B);
+}
+
+// ... and of the loss against the targets in tgt and the backward pass
+int train_body(mg_unet *n, int B) {
+  int rc = forward_body(n, B);
+  if (rc) return rc;
+  const size_t P = (size_t)B * n->H * n->H;
+  UK(cudaMemsetAsync(n->loss_d, 0, sizeof(double), n->st));
+  UK(launch_mse(n->out, n->tgt, n->dout, P, 8, 3, n->loss_d, n->st));
+  return backward(n, B);
+}
+
+void drop_graphs(mg_unet *n) {
+  for (auto *v : {&n->gfwd, &n->gtrain})
+    for (auto &g : *v)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
+// Runs body's kernels for batch size B as a CUDA graph: captured on the private stream the first
+// time (the host-side choices of every launch, tensor maps included, are fixed for a batch size
+// and tensor path), then launched on the caller's stream.  If capturing fails the body runs
+// launch by launch.
+int run_graph(mg_unet *n, std::vector<cudaGraphExec_t> &cache, int B, int (*body)(mg_unet *, int)) {
+  if (!cache[B] && n->cap) {
+    cudaStream_t user = n->st;
+    n->st = n->cap;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(n->cap, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? body(n, B) : MG_ECUDA;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(n->cap, &g);
+    n->st = user;
+    if (rc == MG_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&cache[B], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rc != MG_OK || e != cudaSuccess) {
+      cache[B] = nullptr;
+      cudaGetLastError();
+      return body(n, B);
+    }
+  }
+  if (!cache[B]) return body(n, B);
+  UK(cudaGraphLaunch(cache[B], n->st));
   return MG_OK;
 }
 
 int loss_grad(mg_unet *n, const float *x, const float *t, int B, double *loss, int where) {
   if (!n || !x || !t || B < 1 || B > n->Bmax) return MG_EINVAL;
   int rc;
-  if ((rc = load_input(n, x, B, where)) || (rc = forward(n, B))) return rc;
   const size_t P = (size_t)B * n->H * n->H;
+  if ((rc = load_input(n, x, B, where))) return rc;
   UK(cudaMemcpyAsync(n->tgt, t, P * 3 * sizeof(float), kin(where), n->st));
-  UK(cudaMemsetAsync(n->loss_d, 0, sizeof(double), n->st));
-  UK(launch_mse(n->out, n->tgt, n->dout, P, 8, 3, n->loss_d, n->st));
-  if ((rc = backward(n, B))) return rc;
+  if ((rc = run_graph(n, n->gtrain, B, train_body))) return rc;
   UK(cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, n->st));
   UK(cudaStreamSynchronize(n->st));
   if (loss) *loss = *n->loss_h;
@@ -450,10 +503,13 @@ int mg_unet_create(int batch_max, int n_intervals, void *stream, mg_unet **out) 
   if (cudaMallocHost(&n->loss_h, sizeof(double)) != cudaSuccess) { cudaFree(n->block); delete n; return MG_ECUDA; }
   Carve c{(char *)n->block, 0};
   layout(n, c);
-  if (cudaMemsetAsync(n->block, 0, sz.off, n->st) != cudaSuccess || cudaStreamSynchronize(n->st) != cudaSuccess) {
+  if (cudaMemsetAsync(n->block, 0, sz.off, n->st) != cudaSuccess || cudaStreamSynchronize(n->st) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking) != cudaSuccess) {
     mg_unet_destroy(n);
     return MG_ECUDA;
   }
+  n->gfwd.assign(batch_max + 1, nullptr);
+  n->gtrain.assign(batch_max + 1, nullptr);
   *out = n;
   return MG_OK;
 }
@@ -461,6 +517,8 @@ int mg_unet_create(int batch_max, int n_intervals, void *stream, mg_unet **out) 
 void mg_unet_destroy(mg_unet *n) {
   if (!n) return;
   if (n->st) cudaStreamSynchronize(n->st);
+  drop_graphs(n);
+  if (n->cap) cudaStreamDestroy(n->cap);
   if (n->block) cudaFree(n->block);
   if (n->loss_h) cudaFreeHost(n->loss_h);
   delete n;
@@ -497,7 +555,7 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where) {
 int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where) {
   if (!n || !x || !y || B < 1 || B > n->Bmax) return MG_EINVAL;
   int rc;
-  if ((rc = load_input(n, x, B, where)) || (rc = forward(n, B))) return rc;
+  if ((rc = load_input(n, x, B, where)) || (rc = run_graph(n, n->gfwd, B, forward_body))) return rc;
   // out is [P][8]; copy the 3 real channels with a pitched copy
   const size_t P = (size_t)B * n->H * n->H;
   UK(cudaMemcpy2DAsync(y, 3 * sizeof(float), n->out, 8 * sizeof(float), 3 * sizeof(float), P, kout(where), n->st));
@@ -507,6 +565,10 @@ int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where) {
 
 int mg_unet_set_tensor_path(mg_unet *n, int path) {
   if (!n || path < 0 || path > 3) return MG_EINVAL;
+  if (path != n->use_tc) {
+    if (cudaStreamSynchronize(n->st) != cudaSuccess) return fail(n, MG_ECUDA, "set_tensor_path: stream sync");
+    drop_graphs(n);
+  }
   n->use_tc = path;
   return MG_OK;
 }
