@@ -978,7 +978,11 @@ def measure_unet(dev, peaks, B: int = 16, reps: int = 10):
                        "achieved": res["tcgen05_halo"]["forward_tflops"], "peak": peak, "unit": "TFLOP/s",
                        "frac": res["tcgen05_halo"]["forward_tflops"] / peak,
                        "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
-                       "flops_per_sample": unet_conv_flops(), "traffic": None}
+                       "flops_per_sample": unet_conv_flops(), "traffic": None,
+                       "train_step": {"achieved": res["tcgen05_halo"]["train_tflops"], "peak": peak,
+                                      "unit": "TFLOP/s", "frac": res["tcgen05_halo"]["train_tflops"] / peak,
+                                      "flops_per_sample": 3 * unet_conv_flops(),
+                                      "note": "forward + data and weight gradients (3x the forward's FLOPs)"}}
     res["layers"] = unet_layer_table(256, B)
     return res
 
