@@ -48,6 +48,12 @@ double mg_probe_fp64_gflops(void *stream);
 int mg_time_smoother(mg_state *s, int level, int precision, int sweeps, double *us_per_launch,
                      int *launches_per_sweep);
 
+/* Launch mode of the learned-guess network (unet.h): on = 1 (the default) runs a forward pass
+ * and a loss-and-gradient pass as CUDA graphs per batch size, on = 0 launch by launch, so that a
+ * kernel profiler sees and attributes every launch (the results are the same). */
+typedef struct mg_unet mg_unet;
+int mg_unet_set_graphs(mg_unet *n, int on);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,9 +63,9 @@ int mg_unet_get_grads(mg_unet *n, float *g, int where);
  *     72 KB (the 8-channel first layer included) and the stride-1 data gradients whose reversed
  *     weights fit;
  *   - the TMA-tile tcgen05 kernel: the other 3x3 forward convolutions, the other stride-1 data
- *     gradients with at most 128 input channels, and the stride-2 data gradients;
+ *     gradients (one launch per input part where the parts have more than 128 channels in all),
+ *     and the stride-2 data gradients;
  *   - the TMA-fed tcgen05 weight gradient: every 3x3 layer;
- *   - the thread-gathering tcgen05 kernel: the remaining data gradient (d2, 224 channels);
  *   - FP32 CUDA-core kernels: the 1x1 head, forward and backward.
  * Paths 0-2 keep the earlier kernels of those layers so that the tests can compare each layer's
  * kernel with the one it replaced (same operands, another order of the sums) and the benchmark

@@ -1,7 +1,7 @@
 """Small fixed workloads for profiling runs (ncu captures of single kernels).
 
     python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager] [--autotune] [--half] [--line]
-    python -m paper_0811_4446_gb300.cases unet B N [REPS] [--mma | --gather | --tma | --halo]
+    python -m paper_0811_4446_gb300.cases unet B N [REPS] [--mma | --gather | --tma | --halo] [--eager]
     python -m paper_0811_4446_gb300.cases steady [--mixed] [--eager]
     python -m paper_0811_4446_gb300.cases batch COUNT [--fp64]
 
@@ -30,7 +30,9 @@ after one untimed batch, inside the NVTX range "measure".
 unet: REPS (default 2) forward passes plus one training step of the learned-guess network
 on a batch of B random (N+1) x (N+1) inputs; --mma selects the mma.sync convolutions instead
 of the tcgen05 ones, --gather the thread-gathered tcgen05 forward convolutions instead of the
-TMA-fed ones, --tma the TMA-fed ones without the halo loads (default, --halo: with them).
+TMA-fed ones, --tma the TMA-fed ones without the halo loads (default, --halo: with them); --eager launches kernel by
+kernel instead of the per-batch-size CUDA graphs (kernel profilers cannot attribute the graphs'
+launches).
 """
 from __future__ import annotations
 
@@ -115,7 +117,8 @@ def batch(count: int, fp64: bool = False) -> int:
     return count
 
 
-def unet_case(B: int, n: int, reps: int = 2, mma: bool = False, gather: bool = False, tma: bool = False) -> float:
+def unet_case(B: int, n: int, reps: int = 2, mma: bool = False, gather: bool = False, tma: bool = False,
+              eager: bool = False) -> float:
     import numpy as np
     import torch
     from . import unet
@@ -125,6 +128,8 @@ def unet_case(B: int, n: int, reps: int = 2, mma: bool = False, gather: bool = F
     t = torch.from_numpy(rng.standard_normal((B, n + 1, n + 1, 3)).astype(np.float32)).cuda()
     net = unet.UNet(B, n)
     net.set_tensor_path(0 if mma else (1 if gather else (2 if tma else 3)))
+    if eager:
+        net.set_graphs(False)
     net.set_params(unet.init_params(0))
     ysum = 0.0
     for _ in range(reps):
@@ -139,7 +144,7 @@ if __name__ == "__main__":
     if len(sys.argv) >= 4 and sys.argv[1] == "unet":
         R = int(sys.argv[4]) if len(sys.argv) > 4 and not sys.argv[4].startswith("--") else 2
         print("ok", unet_case(int(sys.argv[2]), int(sys.argv[3]), R, "--mma" in sys.argv, "--gather" in sys.argv,
-                                "--tma" in sys.argv))
+                                "--tma" in sys.argv, "--eager" in sys.argv))
         sys.exit(0)
     if len(sys.argv) >= 3 and sys.argv[1] == "batch":
         print("ok", batch(int(sys.argv[2]), "--fp64" in sys.argv))

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/mg.h"
+#include "../../include/mg_debug.h"
 #include "../../include/unet.h"
 #include "unet_impl.cuh"
 
@@ -60,7 +61,9 @@ struct mg_unet {
   ConvMaps wmaps[NL];      // tensor maps of the TMA-fed weight gradients, built on first use
   const void *wmap_key[NL][3] = {};  // their inputs and dY
   ConvMaps dmaps[NL];      // tensor maps of the TMA-fed data gradients, built on first use
-  const void *dmap_key[NL][3] = {};  // their dY, weights and the kind of map (2: tile, 3: halo, 4: parity)
+  ConvMaps dmaps2[NL];     // ... of the second input part where the parts run as two launches
+  const void *dmap_key[NL][3] = {};  // their dY, weights and the kind of map (2: tile, 3: halo, 4: parity,
+                                     // 5: tile per input part)
   int step = 0;
   void *block = nullptr;
   std::string err;
@@ -68,6 +71,7 @@ struct mg_unet {
   // size for the current tensor path (captured on a private stream, launched on the caller's)
   cudaStream_t cap = nullptr;
   std::vector<cudaGraphExec_t> gfwd, gtrain;
+  int graphs = 1;          // 0: launch by launch (mg_unet_set_graphs, for kernel profilers)
 };
 
 namespace {
@@ -321,6 +325,25 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
       else UK(launch_conv_tma(f, n->dmaps[l], n->tc_err, n->st));
       return MG_OK;
     }
+    // wider than one tile kernel's 128 outputs (d2): one launch per input part, each with its
+    // rows of the reversed weights
+    ConvArgs f1 = f, f2 = f;
+    f1.N = f1.Cout = f1.Nreal = a.C1; f1.dsplit = a.C1; f1.dx2 = nullptr;
+    f2.N = f2.Cout = f2.Nreal = a.C2; f2.dsplit = a.C2; f2.dx1 = f.dx2; f2.dx2 = nullptr;
+    f2.w = f.w + (size_t)a.C1 * f.K;
+    if (a.C2 > 0 && conv_tma_supported(f1, MODE_FWD) && conv_tma_supported(f2, MODE_FWD)) {
+      const void *key[3] = {f.x1, f.w, reinterpret_cast<const void *>(5)};
+      if (std::memcmp(key, n->dmap_key[l], sizeof(key)) != 0) {
+        if (int rc = make_conv_maps(f1, n->Bmax, &n->dmaps[l]))
+          return fail(n, MG_ECUDA, "data-gradient tensor maps of layer %d: encode step %d failed", l, rc);
+        if (int rc = make_conv_maps(f2, n->Bmax, &n->dmaps2[l]))
+          return fail(n, MG_ECUDA, "data-gradient tensor maps of layer %d: encode step %d failed", l, rc);
+        std::memcpy(n->dmap_key[l], key, sizeof(key));
+      }
+      UK(launch_conv_tma(f1, n->dmaps[l], n->tc_err, n->st));
+      UK(launch_conv_tma(f2, n->dmaps2[l], n->tc_err, n->st));
+      return MG_OK;
+    }
   }
   if (want_dx) {
     ConvArgs d = a;
@@ -448,6 +471,7 @@ void drop_graphs(mg_unet *n) {
 // and tensor path), then launched on the caller's stream.  If capturing fails the body runs
 // launch by launch.
 int run_graph(mg_unet *n, std::vector<cudaGraphExec_t> &cache, int B, int (*body)(mg_unet *, int)) {
+  if (!n->graphs) return body(n, B);
   if (!cache[B] && n->cap) {
     cudaStream_t user = n->st;
     n->st = n->cap;
@@ -561,6 +585,12 @@ int mg_unet_forward(mg_unet *n, const float *x, int B, float *y, int where) {
   UK(cudaMemcpy2DAsync(y, 3 * sizeof(float), n->out, 8 * sizeof(float), 3 * sizeof(float), P, kout(where), n->st));
   UK(cudaStreamSynchronize(n->st));
   return check_tc(n);
+}
+
+int mg_unet_set_graphs(mg_unet *n, int on) {
+  if (!n || (on != 0 && on != 1)) return MG_EINVAL;
+  n->graphs = on;
+  return MG_OK;
 }
 
 int mg_unet_set_tensor_path(mg_unet *n, int path) {

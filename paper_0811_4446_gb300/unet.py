@@ -33,6 +33,7 @@ SIGNATURES = {
     "mg_unet_get_grads": (_i, [_vp, _vp, _i]),
     "mg_unet_train_step": (_i, [_vp, _vp, _vp, _i, _f, _c.POINTER(_d), _i]),
     "mg_unet_set_tensor_path": (_i, [_vp, _i]),
+    "mg_unet_set_graphs": (_i, [_vp, _i]),
 }
 
 WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
@@ -96,6 +97,11 @@ class UNet:
         whose input parts have a multiple of 32 channels, 3 (default): as 2 with one halo load
         per 32-channel chunk for all nine taps where the weights fit in shared memory."""
         self._check(self.lib.mg_unet_set_tensor_path(self.h, int(path)))
+
+    def set_graphs(self, on: bool):
+        """Launch mode (mg_unet_set_graphs in include/mg_debug.h): CUDA graphs (default) or
+        launch by launch, for kernel profilers."""
+        self._check(self.lib.mg_unet_set_graphs(self.h, int(bool(on))))
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32) if isinstance(p, np.ndarray) else p
