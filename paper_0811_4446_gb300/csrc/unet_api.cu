@@ -71,6 +71,8 @@ struct mg_unet {
   // size for the current tensor path (captured on a private stream, launched on the caller's)
   cudaStream_t cap = nullptr;
   std::vector<cudaGraphExec_t> gfwd, gtrain;
+  cudaStream_t side = nullptr;            // a layer's weight gradient beside its data gradient
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int graphs = 1;          // 0: launch by launch (mg_unet_set_graphs, for kernel profilers)
 };
 
@@ -227,31 +229,19 @@ int dx_mode(mg_unet *n, int B, Act &in1, Act *in2, int *dacc) {
   return MG_OK;
 }
 
-// dpre_buf (may be null: dpre) receives the layer's bf16 output gradient; head_dy (may be null)
-// makes the layer's output stage the fused head data gradient + ReLU + bias pass
-int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const float *dout32, bool want_dx,
-             __nv_bfloat16 *dpre_buf = nullptr, const __nv_bfloat16 *head_dy = nullptr) {
-  __nv_bfloat16 *const dpre = dpre_buf ? dpre_buf : n->dpre;
-  ConvArgs a = conv_args(n, l, B, in1, in2);
-  const size_t P = (size_t)a.Pout;
+// The weight gradient of layer l (GEMM (kh, kw, ci) x cop over the output pixels) on stream st:
+// added straight into the (zeroed) gradient vector where no output channel is padded, else into
+// the padded buffer and copied over
+int wgrad_part(mg_unet *n, int l, const ConvArgs &a, const __nv_bfloat16 *dpre, cudaStream_t st) {
   const int cop = a.Cout;
-  if (head_dy)
-    UK(launch_head_relu_bias_bwd(head_dy, n->wd[HEAD], out->a, dpre, n->grad + n->boff[l], (int)P, cop, kL[l].co,
-                                 n->st));
-  else
-    UK(launch_relu_bias_bwd(out ? out->g : dout32, out ? out->a : nullptr, dpre, n->grad + n->boff[l], (int)P, cop,
-                            kL[l].co, out ? kL[l].relu : 0, n->st));
-  // weight gradient: GEMM (kh, kw, ci) x cop over the output pixels, split over pixel ranges;
-  // added straight into the (zeroed) gradient vector where no output channel is padded, else
-  // into the padded buffer and copied over
   ConvArgs w = a;
   w.M = a.Kf; w.N = cop; w.K = a.Pout;
   w.dy = dpre;
   const bool padded = cop != kL[l].co;
   w.dw = padded ? n->dwpad : n->grad + n->woff[l];
-  if (padded) UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), n->st));
+  if (padded) UK(cudaMemsetAsync(n->dwpad, 0, (size_t)a.Kf * cop * sizeof(float), st));
   if (n->use_tc && conv1x1_bwd_supported(a)) {
-    UK(launch_conv1x1_wgrad(a, dpre, n->dwpad, n->st));
+    UK(launch_conv1x1_wgrad(a, dpre, n->dwpad, st));
   } else if (n->use_tc == 3 && wgrad_tma_supported(w)) {
     const void *key[3] = {w.x1, w.x2, w.dy};
     if (std::memcmp(key, n->wmap_key[l], sizeof(key)) != 0) {
@@ -259,15 +249,22 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
         return fail(n, MG_ECUDA, "weight-gradient tensor maps of layer %d: encode step %d failed", l, rc);
       std::memcpy(n->wmap_key[l], key, sizeof(key));
     }
-    UK(launch_wgrad_tma(w, n->wmaps[l], n->tc_err, n->st));
+    UK(launch_wgrad_tma(w, n->wmaps[l], n->tc_err, st));
   } else if (n->use_tc && wgrad_tc_supported(w)) {
-    UK(launch_wgrad_tc(w, n->tc_err, n->st));
+    UK(launch_wgrad_tc(w, n->tc_err, st));
   } else {
     const int tiles = ((w.M + 63) / 64) * ((w.N + 63) / 64);
     const int splits = std::max(1, std::min((w.K + 255) / 256, 2 * 152 * 2 / std::max(1, tiles)));
-    UK(launch_conv(w, MODE_WGRAD, splits, n->st));
+    UK(launch_conv(w, MODE_WGRAD, splits, st));
   }
-  if (padded) UK(launch_unpad_grad(n->dwpad, n->grad + n->woff[l], (size_t)a.Kf, kL[l].co, cop, n->st));
+  if (padded) UK(launch_unpad_grad(n->dwpad, n->grad + n->woff[l], (size_t)a.Kf, kL[l].co, cop, st));
+  return MG_OK;
+}
+
+// The data gradient of layer l into its inputs' gradients, on the network's stream
+int dgrad_part(mg_unet *n, int l, int B, const ConvArgs &a, Act &in1, Act *in2, const __nv_bfloat16 *dpre,
+               bool want_dx) {
+  const int cop = a.Cout;
   int dacc = 1;
   if (want_dx)
     if (int rc = dx_mode(n, B, in1, in2, &dacc)) return rc;
@@ -357,6 +354,36 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
     else UK(launch_conv(d, MODE_DGRAD, 1, n->st));
   }
   return MG_OK;
+}
+
+// dpre_buf (may be null: dpre) receives the layer's bf16 output gradient; head_dy (may be null)
+// makes the layer's output stage the fused head data gradient + ReLU + bias pass
+int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const float *dout32, bool want_dx,
+             __nv_bfloat16 *dpre_buf = nullptr, const __nv_bfloat16 *head_dy = nullptr) {
+  __nv_bfloat16 *const dpre = dpre_buf ? dpre_buf : n->dpre;
+  ConvArgs a = conv_args(n, l, B, in1, in2);
+  const size_t P = (size_t)a.Pout;
+  const int cop = a.Cout;
+  if (head_dy)
+    UK(launch_head_relu_bias_bwd(head_dy, n->wd[HEAD], out->a, dpre, n->grad + n->boff[l], (int)P, cop, kL[l].co,
+                                 n->st));
+  else
+    UK(launch_relu_bias_bwd(out ? out->g : dout32, out ? out->a : nullptr, dpre, n->grad + n->boff[l], (int)P, cop,
+                            kL[l].co, out ? kL[l].relu : 0, n->st));
+  // the weight and the data gradient are independent (one reads the input and dY, the other dY
+  // and the weights): the weight gradient runs on the side stream beside the data gradient, and
+  // the network's stream waits for it before the next layer overwrites dY
+  if (n->side) {
+    UK(cudaEventRecord(n->ev_fork, n->st));
+    UK(cudaStreamWaitEvent(n->side, n->ev_fork, 0));
+    if (int rc = wgrad_part(n, l, a, dpre, n->side)) return rc;
+    if (int rc = dgrad_part(n, l, B, a, in1, in2, dpre, want_dx)) return rc;
+    UK(cudaEventRecord(n->ev_join, n->side));
+    UK(cudaStreamWaitEvent(n->st, n->ev_join, 0));
+    return MG_OK;
+  }
+  if (int rc = wgrad_part(n, l, a, dpre, n->st)) return rc;
+  return dgrad_part(n, l, B, a, in1, in2, dpre, want_dx);
 }
 
 int refresh_weights(mg_unet *n) {
@@ -528,7 +555,10 @@ int mg_unet_create(int batch_max, int n_intervals, void *stream, mg_unet **out) 
   Carve c{(char *)n->block, 0};
   layout(n, c);
   if (cudaMemsetAsync(n->block, 0, sz.off, n->st) != cudaSuccess || cudaStreamSynchronize(n->st) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&n->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     mg_unet_destroy(n);
     return MG_ECUDA;
   }
@@ -542,6 +572,10 @@ void mg_unet_destroy(mg_unet *n) {
   if (!n) return;
   if (n->st) cudaStreamSynchronize(n->st);
   drop_graphs(n);
+  if (n->side) cudaStreamSynchronize(n->side);
+  if (n->ev_fork) cudaEventDestroy(n->ev_fork);
+  if (n->ev_join) cudaEventDestroy(n->ev_join);
+  if (n->side) cudaStreamDestroy(n->side);
   if (n->cap) cudaStreamDestroy(n->cap);
   if (n->block) cudaFree(n->block);
   if (n->loss_h) cudaFreeHost(n->loss_h);
