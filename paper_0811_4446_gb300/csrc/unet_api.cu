@@ -51,7 +51,7 @@ struct mg_unet {
   float *dwpad = nullptr;
   Act x, e0a, e0b, e1a, e1b, e2a, e2b, e3a, e3b, u3, d2, u2, d1, u1, d0;
   float *out = nullptr, *dout = nullptr, *tgt = nullptr, *xin = nullptr;
-  __nv_bfloat16 *dpre = nullptr;
+  __nv_bfloat16 *dpre = nullptr, *dpre2 = nullptr;  // a layer's bf16 output gradient, by layer parity
   __nv_bfloat16 *dpre_head = nullptr;  // the head's output gradient when d0's output stage folds it in
   double *loss_d = nullptr, *loss_h = nullptr;
   int *tc_err = nullptr;   // set by a tcgen05 kernel whose bounded wait expired
@@ -71,8 +71,8 @@ struct mg_unet {
   // size for the current tensor path (captured on a private stream, launched on the caller's)
   cudaStream_t cap = nullptr;
   std::vector<cudaGraphExec_t> gfwd, gtrain;
-  cudaStream_t side = nullptr;            // a layer's weight gradient beside its data gradient
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side = nullptr;            // a layer's weight gradient beside the later layers' work
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};  // per dY buffer
   int graphs = 1;          // 0: launch by launch (mg_unet_set_graphs, for kernel profilers)
 };
 
@@ -155,6 +155,7 @@ void layout(mg_unet *n, Carve &c) {
   n->tgt = c.take<float>(P0 * 3);
   n->xin = c.take<float>(P0 * 8);
   n->dpre = c.take<__nv_bfloat16>(P0 * 32);
+  n->dpre2 = c.take<__nv_bfloat16>(P0 * 32);
   n->dpre_head = c.take<__nv_bfloat16>(P0 * 8);
   n->loss_d = c.take<double>(1);
   n->tc_err = c.take<int>(4);
@@ -360,7 +361,11 @@ int dgrad_part(mg_unet *n, int l, int B, const ConvArgs &a, Act &in1, Act *in2, 
 // makes the layer's output stage the fused head data gradient + ReLU + bias pass
 int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const float *dout32, bool want_dx,
              __nv_bfloat16 *dpre_buf = nullptr, const __nv_bfloat16 *head_dy = nullptr) {
-  __nv_bfloat16 *const dpre = dpre_buf ? dpre_buf : n->dpre;
+  // the layer's dY buffer: its own (the head's) or one of two by layer parity, which the weight
+  // gradient of the layer two steps back (on the side stream) must have finished reading
+  const int jb = dpre_buf ? 2 : (l & 1);
+  __nv_bfloat16 *const dpre = dpre_buf ? dpre_buf : ((l & 1) ? n->dpre2 : n->dpre);
+  if (n->side) UK(cudaStreamWaitEvent(n->st, n->ev_join[jb], 0));
   ConvArgs a = conv_args(n, l, B, in1, in2);
   const size_t P = (size_t)a.Pout;
   const int cop = a.Cout;
@@ -371,16 +376,14 @@ int conv_bwd(mg_unet *n, int l, int B, Act &in1, Act *in2, const Act *out, const
     UK(launch_relu_bias_bwd(out ? out->g : dout32, out ? out->a : nullptr, dpre, n->grad + n->boff[l], (int)P, cop,
                             kL[l].co, out ? kL[l].relu : 0, n->st));
   // the weight and the data gradient are independent (one reads the input and dY, the other dY
-  // and the weights): the weight gradient runs on the side stream beside the data gradient, and
-  // the network's stream waits for it before the next layer overwrites dY
+  // and the weights): the weight gradient runs on the side stream beside the data gradient and
+  // the later layers' work, until the layer two steps on reuses this dY buffer
   if (n->side) {
     UK(cudaEventRecord(n->ev_fork, n->st));
     UK(cudaStreamWaitEvent(n->side, n->ev_fork, 0));
     if (int rc = wgrad_part(n, l, a, dpre, n->side)) return rc;
-    if (int rc = dgrad_part(n, l, B, a, in1, in2, dpre, want_dx)) return rc;
-    UK(cudaEventRecord(n->ev_join, n->side));
-    UK(cudaStreamWaitEvent(n->st, n->ev_join, 0));
-    return MG_OK;
+    UK(cudaEventRecord(n->ev_join[jb], n->side));
+    return dgrad_part(n, l, B, a, in1, in2, dpre, want_dx);
   }
   if (int rc = wgrad_part(n, l, a, dpre, n->st)) return rc;
   return dgrad_part(n, l, B, a, in1, in2, dpre, want_dx);
@@ -422,6 +425,9 @@ int backward(mg_unet *n, int B) {
   Act *all[] = {&n->x, &n->e0a, &n->e0b, &n->e1a, &n->e1b, &n->e2a, &n->e2b, &n->e3a,
                 &n->e3b, &n->u3, &n->d2, &n->u2, &n->d1, &n->u1, &n->d0};
   for (Act *t : all) t->gw = false;
+  // the dY buffers' events start out complete in this stream's order (and inside a capture)
+  if (n->side)
+    for (auto &e : n->ev_join) UK(cudaEventRecord(e, n->st));
   UK(cudaMemsetAsync(n->grad, 0, n->nparam * sizeof(float), n->st));
   // with the head's backward on the CUDA cores its data gradient is folded into d0's output
   // stage (never stored): the head's bf16 output gradient goes to its own buffer for that
@@ -445,7 +451,11 @@ int backward(mg_unet *n, int B) {
   if ((rc = conv_bwd(n, E1B, B, n->e1a, nullptr, &n->e1b, nullptr, true))) return rc;
   if ((rc = conv_bwd(n, E1A, B, n->e0b, nullptr, &n->e1a, nullptr, true))) return rc;
   if ((rc = conv_bwd(n, E0B, B, n->e0a, nullptr, &n->e0b, nullptr, true))) return rc;
-  return conv_bwd(n, E0A, B, n->x, nullptr, &n->e0a, nullptr, false);
+  if ((rc = conv_bwd(n, E0A, B, n->x, nullptr, &n->e0a, nullptr, false))) return rc;
+  // every weight gradient is in before the caller reads the gradients or Adam runs
+  if (n->side)
+    for (auto &e : n->ev_join) UK(cudaStreamWaitEvent(n->st, e, 0));
+  return MG_OK;
 }
 
 cudaMemcpyKind kin(int where) { return where == MG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
@@ -558,7 +568,9 @@ int mg_unet_create(int batch_max, int n_intervals, void *stream, mg_unet **out) 
       cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&n->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&n->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&n->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&n->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_join[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_join[2], cudaEventDisableTiming) != cudaSuccess) {
     mg_unet_destroy(n);
     return MG_ECUDA;
   }
@@ -574,7 +586,8 @@ void mg_unet_destroy(mg_unet *n) {
   drop_graphs(n);
   if (n->side) cudaStreamSynchronize(n->side);
   if (n->ev_fork) cudaEventDestroy(n->ev_fork);
-  if (n->ev_join) cudaEventDestroy(n->ev_join);
+  for (auto &e : n->ev_join)
+    if (e) cudaEventDestroy(e);
   if (n->side) cudaStreamDestroy(n->side);
   if (n->cap) cudaStreamDestroy(n->cap);
   if (n->block) cudaFree(n->block);
