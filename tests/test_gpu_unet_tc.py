@@ -134,3 +134,27 @@ def test_layer_gradients_match_mma_sync(un, Bmax, B, n):
             assert rel <= 3e-2, (name, size, rel)
             off += size
     assert off == g0.size
+
+
+def test_graphs_match_launch_by_launch(un):
+    """The per-batch-size CUDA graphs (the default) replay the launches of the kernel-by-kernel
+    mode: the same forward outputs bit for bit, also when batch sizes alternate on one network
+    (one graph each), and the same loss and gradients up to the order of the weight gradient's
+    FP32 atomic adds."""
+    p, x, t = _inputs(un, 3, 32, 17)
+    res = []
+    for graphs in (True, False):
+        net = un.UNet(3, 32)
+        net.set_params(p)
+        net.set_graphs(graphs)
+        y2 = net.forward(x[:2])
+        y3 = net.forward(x)
+        y2b = net.forward(x[:2])
+        loss, g = net.loss_grad(x[:2], t[:2])
+        res.append((y2, y3, y2b, loss, g))
+        net.close()
+    (a2, a3, a2b, la, ga), (b2, b3, b2b, lb, gb) = res
+    assert np.array_equal(a2, b2) and np.array_equal(a3, b3) and np.array_equal(a2b, a2)
+    assert np.array_equal(b2b, b2)
+    assert abs(la - lb) <= 1e-6 * abs(lb)
+    assert np.linalg.norm(ga - gb) <= 1e-5 * np.linalg.norm(gb)
