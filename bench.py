@@ -76,10 +76,17 @@ def default_sweeps(n: int) -> int:
 # k_smooth<double> (profiles/k_smooth_fp64_1025.md), k_smooth<float> (k_smooth_fp32_1025_mixed.md)
 TRAFFIC_K_SMOOTH_FP64_1025 = 182969344
 TRAFFIC_K_SMOOTH_FP32_1025 = 90871296
+# the same launches inside the V-cycle, the caches as the preceding kernels leave them (mean of
+# the eight pre-smoothing launches of the finest level, profiles/k_smooth_1025_in_vcycle.md)
+TRAFFIC_K_SMOOTH_FP64_1025_IN_VCYCLE = 188766656
+TRAFFIC_K_SMOOTH_FP32_1025_IN_VCYCLE = 62613888
 
 
 def _vcycle_1025(precision, peaks):
     """V-cycle time at 1025^2 and the roofline of its finest-level smoother launch."""
+    import ctypes
+
+    import torch
     import workloads as W
     from paper_0811_4446_gb300 import mg
     d = W.transient_1025()
@@ -90,20 +97,52 @@ def _vcycle_1025(precision, peaks):
     fused = bool(tuned[0, 2] if fp64 else tuned[0, 5])
     F, _ = s.residual(1e-9)
     f = [-a for a in F]
-    s.linear_solve(1e-9, f, 0.0, 0)
-    t0 = time.perf_counter()
-    s.linear_solve(1e-9, f, 0.0, 0)
-    t1 = time.perf_counter()
-    x, hist, _ = s.linear_solve(1e-9, f, 0.0, 30)
-    t2 = time.perf_counter()
-    vc = ((t2 - t1) - (t1 - t0)) / 30
-    # per-launch duration inside V-cycles (event-bracketed launches of 10 host-driven cycles):
-    # a graph replay of sweeps alone would keep the FP32 level (114 MB) in the 129 MB L2
+    stream = torch.cuda.current_stream()  # the solver's stream
+    # right-hand side and solution in device memory, so that no host copy sits inside the timing
+    fd = [torch.from_numpy(np.ascontiguousarray(a)).to("cuda") for a in f]
+    xd = [torch.empty_like(a) for a in fd]
+    hbuf = np.zeros(64)
+    ncyc = ctypes.c_int(0)
+
+    def solve_dev(cycles):
+        rc = s.lib.mg_linear_solve(s.h, 1e-9, *(t.data_ptr() for t in fd), *(t.data_ptr() for t in xd), 0.0,
+                                   int(cycles), hbuf.ctypes.data, ctypes.byref(ncyc), mg.MG_DEVICE)
+        if rc not in (mg.MG_OK, mg.MG_ENOCONV):
+            raise mg.MGError(rc, "mg_linear_solve failed")
+
+    def cycle_s(cycles=30):
+        """Device seconds per V-cycle of the graph-driven linear solve (CUDA events on the
+        solver's stream; the solve's fixed part, timed with no cycle, taken off)."""
+        solve_dev(2)
+        ts = []
+        for k in (0, cycles):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solve_dev(k)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return (ts[1] - ts[0]) / cycles
+
+    vc = cycle_s()
+    hist = hbuf[:ncyc.value + 1].copy()
+    # a finest-level sweep as the V-cycle runs it: the slope of the cycle's device time over
+    # 1+1 .. 4+4 sweeps on that level (the other levels unchanged), per launch of the sweep
+    pts = []
+    for nu in (4, 3, 2, 1):
+        s.set_level_sweeps(0, nu, nu)
+        pts.append((2 * nu, cycle_s(20)))
+    s.set_level_sweeps(0, -1, -1)
+    slope = float(np.polyfit([p_[0] for p_ in pts], [p_[1] for p_ in pts], 1)[0])
+    lps = 1 if fused else 2
+    avg = slope / lps
+    # for comparison: events around each launch of 10 host-driven cycles (the host's launch
+    # latency between kernels included)
     s.profile_begin(mg.MG_PROF_SMOOTH, 0)
     s.linear_solve(1e-9, f, 0.0, 10)
     n, ms = s.profile_end()
     s.close()
-    avg = ms / n / 1000.0
+    avg_host = ms / n / 1000.0
     # algorithmic bytes and flops of one launch (the one-pass figures above; FP32 halves the
     # bytes): a half sweep is half a sweep over the level's unknown nodes
     per_node = ALG_SWEEP_BYTES_FP64 * (1.0 if fp64 else 0.5) * (1.0 if fused else 0.5)
@@ -116,15 +155,24 @@ def _vcycle_1025(precision, peaks):
     executed = 52 * nodes if fused else 26 * nodes
     hbm = peaks.get("hbm_gbs", 6800.0)
     name = ("k_sweep" if fused else "k_smooth") + ("<double>" if fp64 else "<float>")
-    # ncu DRAM read + write per launch, cold caches (profiles/k_smooth_fp32_1025_mixed.md,
-    # profiles/k_smooth_fp64_1025.md)
-    traffic = None if fused else (TRAFFIC_K_SMOOTH_FP32_1025 if not fp64 else TRAFFIC_K_SMOOTH_FP64_1025)
+    # ncu DRAM read + write per launch inside the V-cycle (profiles/k_smooth_1025_in_vcycle.md), and
+    # with cold caches (profiles/k_smooth_fp32_1025_mixed.md, profiles/k_smooth_fp64_1025.md)
+    traffic = None if fused else (TRAFFIC_K_SMOOTH_FP32_1025_IN_VCYCLE if not fp64
+                                  else TRAFFIC_K_SMOOTH_FP64_1025_IN_VCYCLE)
+    traffic_cold = None if fused else (TRAFFIC_K_SMOOTH_FP32_1025 if not fp64 else TRAFFIC_K_SMOOTH_FP64_1025)
     roof = {"bound": "hbm", "kernel": name + (" (fused red-black sweep" if fused else " (red-black half sweep")
             + ", 1025x1025 level)", "achieved": byt / avg / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6, "algorithmic_bytes_per_launch": byt,
+            "frac": byt / avg / 1e9 / hbm, "avg_launch_us": avg * 1e6,
+            "avg_launch_us_source": "slope of the graph-driven V-cycle's device time (CUDA events) over 1+1 .. 4+4 "
+                                    "sweeps on the 1025^2 level, per launch of a sweep",
+            "vcycle_us_by_fine_sweeps": {str(k): v * 1e6 for k, v in pts},
+            "avg_launch_us_host_driven": avg_host * 1e6, "frac_host_driven": byt / avg_host / 1e9 / hbm,
+            "algorithmic_bytes_per_launch": byt,
             "algorithmic_bytes_per_node": per_node,
             "bytes_touched_per_launch": touched, "frac_bytes_touched": touched / avg / 1e9 / hbm,
             "traffic": traffic, "traffic_over_algorithmic": (traffic / byt) if traffic else None,
+            "traffic_source": "ncu DRAM bytes per launch inside the V-cycle (caches not flushed)",
+            "traffic_cold": traffic_cold, "traffic_cold_over_algorithmic": (traffic_cold / byt) if traffic_cold else None,
             "peak_source": "MEASURED_PEAKS hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     if fp64:
         fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e9
@@ -603,6 +651,8 @@ def measure_forms(args, dev, peaks):
     """The other forms of the hot path, measured once each after the headline steps:
     mixed-precision steady 257^2 solve, FP32 inner V-cycle at 1025^2 (HBM roofline of its
     smoother), and the 64-instance batch of uneven discharges (solves/s, p50/p99)."""
+    import ctypes
+
     import torch
     import workloads as W
     from paper_0811_4446_gb300 import mg
@@ -864,6 +914,8 @@ def transient_1025_report(dev):
     history of the first Newton system, and the per-field max relative error against the FP64
     oracle after the first and the last step (max over every 8th node in both directions,
     relative to the oracle field's max-norm over all nodes)."""
+    import ctypes
+
     import torch
     import workloads as W
     from paper_0811_4446_gb300 import mg
