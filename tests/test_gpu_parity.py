@@ -226,6 +226,61 @@ def test_line_smoother_linear_solve_parity(mg, n, R, table, precision):
         assert len(hg) * 2 < len(hp), (len(hg), len(hp))
 
 
+@pytest.mark.parametrize("nr,nz,table,precision,line", [(64, 16, False, "fp64", 0), (16, 64, True, "fp64", 0),
+                                                       (128, 32, True, "fp64", 0), (32, 128, False, "mixed", 0),
+                                                       (64, 16, True, "mixed", 0), (32, 64, True, "fp64", 1),
+                                                       (64, 32, False, "fp64", 1)])
+def test_nonsquare_linear_solve_parity(mg, nr, nz, table, precision, line):
+    """V-cycles on grids with N_r != N_z (both sides halved per level down to a shorter side of
+    2 intervals: 64 x 16 -> 8 x 2, 16 x 64 -> 2 x 8), with the point smoother or the z-line one:
+    the oracle's solution per field (FP64 1e-10, mixed 1e-8) and, in FP64, its residual history
+    cycle by cycle.  FP64 solves on both sides stop at a relative residual of 1e-13: the ion
+    density, weakly coupled, amplifies a residual of 1e-12 to about 1e-10 of its own scale on
+    these grids.  The cycle counts are compared where the oracle reaches that tolerance: its
+    z-line column solves level off near 2e-12 on the 64 x 32 grid, where the GPU's cycle
+    reaches 5e-14."""
+    d = W.make_discharge(nr, nz=nz, seed=9, V_cathode=-300.0, use_table=table)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    dt = 1e-7
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    s = mg.from_discharge(d, precision=prec, line_smoother=line)
+    s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, dt, phys, with_terms=True)
+    eta = 1e-13 if precision == "fp64" else 1e-11
+    xg, hg, rc = s.linear_solve(dt, list(-F), eta, 300)
+    assert rc == mg.MG_OK, hg
+    H = omg.Hierarchy(g, u, dt, phys, line=bool(line))
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    x, ho = H.solve(disc.to_vec(g, -F), 1e-13, 300, scale=tn)
+    xo = disc.from_vec(g, x)
+    _assert_fields(xg, xo, FP64_TOL if precision == "fp64" else MIXED_TOL, (nr, nz))
+    if precision == "fp64":
+        if ho[-1] <= 1e-13:
+            assert abs(len(hg) - len(ho)) <= 1
+        k = min(len(hg), len(ho), 6)
+        assert np.allclose(hg[:k], ho[:k], rtol=1e-5, atol=1e-14)
+    else:
+        assert len(hg) <= len(ho) + 3
+
+
+@pytest.mark.parametrize("nr,nz", [(32, 8), (8, 32), (64, 32)])
+def test_nonsquare_step_parity(mg, nr, nz):
+    """Backward-Euler steps (Newton with V-cycle solves) on grids with N_r != N_z: the oracle's
+    Newton iteration count and state per field to 1e-10."""
+    d = W.make_discharge(nr, nz=nz, seed=10, V_cathode=-250.0, use_table=True)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-12, max_vcycles=100)
+    opt = osv.SolverOptions(eta=1e-12)
+    for k in range(3):
+        rc, st = s.step(1e-9, 1e-10)
+        assert rc == mg.MG_OK
+        u, so = osv.step(g, u, d.S_e, d.S_p, 1e-9, phys, 1e-10, opt)
+        assert so.accepted and st["last_newton"] == so.newton
+    _assert_fields(s.get_state(), u, FP64_TOL, (nr, nz))
+
+
 def test_transient_33_ten_steps_parity(mg):
     d = W.transient_33()
     g, phys = _oracle(d)
