@@ -582,7 +582,7 @@ int mg_unet_create(int batch_max, int n_intervals, void *stream, mg_unet **out) 
 
 void mg_unet_destroy(mg_unet *n) {
   if (!n) return;
-  if (n->st) cudaStreamSynchronize(n->st);
+  cudaStreamSynchronize(n->st);  // the caller's stream (null: the legacy default stream)
   drop_graphs(n);
   if (n->side) cudaStreamSynchronize(n->side);
   if (n->ev_fork) cudaEventDestroy(n->ev_fork);

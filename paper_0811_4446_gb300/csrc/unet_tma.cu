@@ -956,14 +956,32 @@ int make_conv_maps(const ConvArgs &a, int Bmax, ConvMaps *m) {
 
 namespace {
 
-// A short ring per CTA and several CTAs per SM: the rate of a CTA's load / MMA / commit chain
-// hardly depends on its ring depth (4 or 8 stages ran alike), the rate of an SM grows with the
-// CTAs it holds, up to a point.  N = 32: 3 stages (31 KB) fit 7 CTAs per SM, within the 8 that
-// its 64 TMEM columns allow (measured: the forward within 2 % of 5 CTAs per SM with 4 stages);
-// wider layers keep 4 (their TMEM share caps them at 2-4 CTAs per SM anyway).
-int stages_for(int BN) { return BN <= 32 ? 3 : 4; }
+size_t smem_of(int BN, int S) { return 1024 + (size_t)S * (TM_X * TM_Y * 64 + (size_t)BN * 64); }
 
-size_t smem_for(int BN) { return 1024 + (size_t)stages_for(BN) * (TM_X * TM_Y * 64 + (size_t)BN * 64); }
+// CTAs per SM: as many as the shared memory holds (the ring, the static barriers and the 1 KB
+// each CTA reserves) and whose accumulators fit together in the 512 TMEM columns of an SM, so
+// that a resident CTA never waits in tcgen05.alloc; a CTA that finds no room starts later.
+int occupancy_of(int BN, int S, int cols, int smem_sm) {
+  return std::max(1, std::min(smem_sm / (int)(smem_of(BN, S) + 2048), 512 / cols));
+}
+
+// Ring depth: the depth that maximises the stages in flight on the GPU, S x the CTAs that have a
+// tile (ties to the shallower ring): 6-7 stages on 2-3 CTAs per SM for the U-Net's layers.  The
+// rate hardly depends on it (against 3-4 stages: forward the same, training step 1.4 % faster);
+// what bounds these layers is the SM's TMA engine, about 100 cycles per box plus one per 64-byte
+// line, with each chunk's A and B box (the weights are reloaded for every tile).
+int stages_for(int BN, int cols, long ntiles, int sms, int smem_sm) {
+  int best = 2;
+  long best_score = -1;
+  for (int S = 2; S <= TM_MAXS; ++S) {
+    const long chains = std::min(ntiles, (long)sms * occupancy_of(BN, S, cols, smem_sm));
+    if (chains * S > best_score) {
+      best_score = chains * S;
+      best = S;
+    }
+  }
+  return best;
+}
 
 }  // namespace
 
@@ -971,21 +989,13 @@ namespace {
 
 cudaError_t launch_conv_tma_impl(const ConvArgs &a, const ConvMaps &m, const ParityTaps &pt, int *err,
                                  cudaStream_t st) {
-  const int BN = a.N, S = stages_for(BN), cols = tmem_cols_of(2 * BN);
-  const size_t smem = smem_for(BN);
-  cudaError_t e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  const int BN = a.N, cols = tmem_cols_of(2 * BN);
   int dev = 0, sms = 0, smem_sm = 0;
+  cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
     return e;
-  // CTAs per SM: as many as the shared memory holds (the ring, the static barriers and the 1 KB
-  // each CTA reserves) and whose accumulators fit together in the 512 TMEM columns of an SM, so
-  // that a resident CTA never waits in tcgen05.alloc; a CTA that finds no room starts later.
-  const int occ = std::max(1, std::min(smem_sm / (int)(smem + 2048), 512 / cols));
   TileGrid tg;
   tg.tx = (a.Wout + TM_X - 1) / TM_X;
   tg.ty = (a.Hout + TM_Y - 1) / TM_Y;
@@ -996,6 +1006,13 @@ cudaError_t launch_conv_tma_impl(const ConvArgs &a, const ConvMaps &m, const Par
     p.per_class = tg.ntiles;
     tg.ntiles *= 4;
   }
+  const int S = stages_for(BN, cols, tg.ntiles, sms, smem_sm);
+  const size_t smem = smem_of(BN, S);
+  const int occ = occupancy_of(BN, S, cols, smem_sm);
+  e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(tg.ntiles, sms * occ));
   k_conv_tma<<<grid, TM_THREADS, smem, st>>>(m.x1, m.x2, m.w, a, tg, p, S, cols, err);
   return cudaGetLastError();
