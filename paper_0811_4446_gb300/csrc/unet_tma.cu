@@ -965,22 +965,20 @@ int occupancy_of(int BN, int S, int cols, int smem_sm) {
   return std::max(1, std::min(smem_sm / (int)(smem_of(BN, S) + 2048), 512 / cols));
 }
 
-// Ring depth: the depth that maximises the stages in flight on the GPU, S x the CTAs that have a
-// tile (ties to the shallower ring): 6-7 stages on 2-3 CTAs per SM for the U-Net's layers.  The
-// rate hardly depends on it (against 3-4 stages: forward the same, training step 1.4 % faster);
-// what bounds these layers is the SM's TMA engine, about 100 cycles per box plus one per 64-byte
-// line, with each chunk's A and B box (the weights are reloaded for every tile).
+// Ring depth: 3 stages for N = 32 (6-7 CTAs per SM), 4 for wider layers (their TMEM share caps
+// them at 2-4 CTAs per SM); a chain per CTA, so more CTAs per SM beat deeper rings (N = 32: 3
+// stages on 7 CTAs within 2 % of 4 on 5, 7 stages on 3 CTAs 12 % slower).  A layer with no more
+// tiles than that many resident CTAs takes the deepest ring that still keeps all its tiles
+// resident at once (the coarse layers e3a, e3b: 6 stages).  The rate hardly depends on the depth
+// (the training step 1 % faster): what bounds these layers is the SM's TMA engine, about 100 cycles
+// per box plus one per 64-byte line, with each chunk's A and B box (the weights are reloaded for
+// every tile).
 int stages_for(int BN, int cols, long ntiles, int sms, int smem_sm) {
-  int best = 2;
-  long best_score = -1;
-  for (int S = 2; S <= TM_MAXS; ++S) {
-    const long chains = std::min(ntiles, (long)sms * occupancy_of(BN, S, cols, smem_sm));
-    if (chains * S > best_score) {
-      best_score = chains * S;
-      best = S;
-    }
-  }
-  return best;
+  const int S0 = BN <= 32 ? 3 : 4;
+  if (ntiles > (long)sms * occupancy_of(BN, S0, cols, smem_sm)) return S0;
+  int S = S0;
+  while (S < TM_MAXS && ntiles <= (long)sms * occupancy_of(BN, S + 1, cols, smem_sm)) ++S;
+  return S;
 }
 
 }  // namespace
