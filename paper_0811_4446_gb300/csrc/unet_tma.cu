@@ -970,9 +970,7 @@ int occupancy_of(int BN, int S, int cols, int smem_sm) {
 // stages on 7 CTAs within 2 % of 4 on 5, 7 stages on 3 CTAs 12 % slower).  A layer with no more
 // tiles than that many resident CTAs takes the deepest ring that still keeps all its tiles
 // resident at once (the coarse layers e3a, e3b: 6 stages).  The rate hardly depends on the depth
-// (the training step 1 % faster): what bounds these layers is the SM's TMA engine, about 100 cycles
-// per box plus one per 64-byte line, with each chunk's A and B box (the weights are reloaded for
-// every tile).
+// (the training step 1 % faster), so load latency does not bound these layers.
 int stages_for(int BN, int cols, long ntiles, int sms, int smem_sm) {
   const int S0 = BN <= 32 ? 3 : 4;
   if (ntiles > (long)sms * occupancy_of(BN, S0, cols, smem_sm)) return S0;
