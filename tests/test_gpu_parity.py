@@ -117,6 +117,51 @@ def test_jacobian_apply_parity(mg, nr, nz, table):
             assert np.abs(Jg[f] - Jv[f]).max() <= 1e-12 * scale[f].max(), f
 
 
+@pytest.mark.parametrize("state", ["zero_field", "zero_density"])
+@pytest.mark.parametrize("table", [False, True])
+def test_degenerate_states_parity(mg, state, table):
+    """Degenerate states of the method against the oracle.  zero_field: no applied voltage and
+    V = 0, so alpha = 0 on every face and the Scharfetter-Gummel weights take the Bernoulli
+    series branch (B(0) = 1) everywhere; with the table, |E| = 0 lies below its range.
+    zero_density: n_e = n_p = 0 under the applied field, so the fluxes, their V couplings and
+    the space charge vanish.  Residual rows and Jacobian products to 1e-12 of the row scale, and
+    linear solves to the FP64 (1e-10) and mixed (1e-8) bars."""
+    d = W.make_discharge(32, seed=3, V_cathode=0.0 if state == "zero_field" else -300.0, use_table=table)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    if state == "zero_field":
+        assert not u[2].any()
+    else:
+        u[0:2] = 0.0
+    uo = u * 0.99
+    dt = 1e-9
+    F, T = disc.residual(g, u, uo, d.S_e, d.S_p, dt, phys, with_terms=True)
+    J = disc.jacobian(g, u, dt, phys)
+    rng = np.random.default_rng(5)
+    v = np.zeros((3,) + d.shape)
+    v[:, 1:-1] = rng.standard_normal((3, d.nz - 1, d.nr + 1))
+    v[0:2] *= 1e12
+    Jv = disc.from_vec(g, J @ disc.to_vec(g, v))
+    scale_j = disc.from_vec(g, abs(J) @ np.abs(disc.to_vec(g, v)))
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    x, ho = omg.Hierarchy(g, u, dt, phys).solve(disc.to_vec(g, -F), 1e-12, 200, scale=tn)
+    xo = disc.from_vec(g, x)
+    for prec, tol in ((mg.MG_FP64, FP64_TOL), (mg.MG_MIXED, MIXED_TOL)):
+        s = mg.from_discharge(d, precision=prec)
+        s.set_state(*[np.ascontiguousarray(a) for a in u])
+        s.set_old_state(*[np.ascontiguousarray(a) for a in uo])
+        Fg, _ = s.residual(dt)
+        for f in range(3):
+            assert np.abs(Fg[f] - F[f]).max() <= 1e-12 * max(np.abs(T[f]).max(), 1e-300), (prec, f)
+        Jg = s.jacobian_apply(dt, list(v))
+        for f in range(3):
+            assert np.abs(Jg[f] - Jv[f]).max() <= 1e-12 * scale_j[f].max(), (prec, f)
+        xg, hg, rc = s.linear_solve(dt, list(-F), 1e-12, 200)  # the oracle's stopping residual
+        assert rc == mg.MG_OK, (prec, hg)
+        _assert_fields(xg, xo, tol, (state, prec))
+        s.close()
+
+
 @pytest.mark.parametrize("nr,nz", [(16, 16), (64, 64), (32, 16)])
 def test_full_jacobian_apply_parity(mg, nr, nz):
     """f4: the full Jacobian (mu, D functions of |E|) times a random vector, FP64 GPU against
