@@ -825,6 +825,31 @@ def test_autotune_keeps_results(mg):
         assert np.array_equal(res[0][0][q], res[1][0][q])
 
 
+def test_vcycle_histories_match_oracle_257_to_2049(mg):
+    """V-cycles on 257^2 .. 2049^2 nodes (the largest grid, 4.2 M nodes, about 2 GB with its
+    hierarchy): the oracle's residual history cycle by cycle, to 1e-5 relative per cycle as on
+    the small grids (tests/golden/oracle_vcycle_factors.json, written from the oracle alone by
+    tests/golden/make_oracle_vcycle_factors.py).  At this Delta t the factor grows with the grid,
+    from 0.17 at 257^2 to 0.44 at 2049^2 on both sides: the algorithm's behaviour on the ions'
+    drift-dominated coarse levels, which the GPU reproduces; every cycle still contracts."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_vcycle_factors.json")) as fh:
+        gold = json.load(fh)
+    dt, cycles = gold["dt"], gold["cycles"]
+    for n_str, ho in gold["histories"].items():
+        n = int(n_str)
+        d = W.make_discharge(n, seed=0, V_cathode=-300.0)
+        s = mg.from_discharge(d)
+        s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in (d.ne0, d.np0, d.V0)])
+        F, _ = s.residual(dt)
+        x, h, rc = s.linear_solve(dt, [-a for a in F], 0.0, cycles)
+        s.close()
+        assert len(h) == len(ho), (n, len(h), len(ho))
+        assert np.all(np.diff(h) < 0), (n, h)
+        assert np.allclose(h, ho, rtol=1e-5, atol=1e-14), (n, list(h), ho)
+
+
 def _force_fused(s, tile):
     """Fused sweeps with the given tile on every level of both views."""
     for lev in range(s.lib.mg_num_levels(s.h)):
