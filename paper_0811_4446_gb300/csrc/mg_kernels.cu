@@ -920,8 +920,8 @@ __device__ __forceinline__ void mm3(const T (&a)[9], const T *b, T (&c)[9]) {
     for (int q = 0; q < 3; ++q) c[3 * r + q] = a[3 * r] * b[q] + a[3 * r + 1] * b[3 + q] + a[3 * r + 2] * b[6 + q];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512) k_zline_pcr(LevelT<T> L, int color) {
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_zline_pcr(LevelT<T> L, int color) {
   extern __shared__ __align__(16) unsigned char zl_smem[];
   T *X = reinterpret_cast<T *>(zl_smem);  // [21][nz]
   const int nz = L.nz, P = L.P, tid = threadIdx.x;
@@ -1026,9 +1026,21 @@ cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st)
     static std::once_flag raised;
     if (smem > 48 * 1024)
       std::call_once(raised, []() {
-        cudaFuncSetAttribute(k_zline_pcr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 21 * 512 * (int)sizeof(T));
+        cudaFuncSetAttribute(k_zline_pcr<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             21 * 512 * (int)sizeof(T));
       });
-    k_zline_pcr<T><<<n, L.nz, smem, st>>>(L, color);
+    k_zline_pcr<T, 512><<<n, L.nz, smem, st>>>(L, color);
+  } else if (sizeof(T) == 4 && L.nz == 1024) {
+    // 1,024 rows, one thread each: FP32 only (64 registers a thread; the FP64 kernel takes 128),
+    // 86 KB of shared memory
+    if constexpr (sizeof(T) == 4) {
+      static std::once_flag raised1024;
+      std::call_once(raised1024, []() {
+        cudaFuncSetAttribute(k_zline_pcr<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             21 * 1024 * (int)sizeof(T));
+      });
+      k_zline_pcr<T, 1024><<<n, L.nz, (size_t)21 * L.nz * sizeof(T), st>>>(L, color);
+    }
   } else {
     const int cstride = (L.nr + 2) / 2;
     k_zline<T><<<(n + 63) / 64, 64, 0, st>>>(L, color, scr, cstride);

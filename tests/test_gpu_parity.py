@@ -309,6 +309,28 @@ def test_nonsquare_linear_solve_parity(mg, nr, nz, table, precision, line):
         assert len(hg) <= len(ho) + 3
 
 
+def test_line_smoother_1023_row_columns_mixed(mg):
+    """z-line smoothing of the FP32 inner cycle on a level whose columns have 1,023 rows
+    (129 x 1025 nodes): one shared-memory cyclic reduction per column, a thread per row.  The
+    mixed linear solve against the oracle's z-line solve, both stopped at a relative residual of
+    1e-11 (the oracle's column solves level off near 1e-12 on this grid): the solution per field
+    to 1e-8, and at most three cycles more than the oracle."""
+    d = W.make_discharge(128, nz=1024, seed=9, V_cathode=-300.0)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    dt = 1e-7
+    s = mg.from_discharge(d, precision=mg.MG_MIXED, line_smoother=1)
+    s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, dt, phys, with_terms=True)
+    xg, hg, rc = s.linear_solve(dt, list(-F), 1e-11, 100)
+    assert rc == mg.MG_OK, hg
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    x, ho = omg.Hierarchy(g, u, dt, phys, line=True).solve(disc.to_vec(g, -F), 1e-11, 100, scale=tn)
+    assert ho[-1] <= 1e-11
+    _assert_fields(xg, disc.from_vec(g, x), MIXED_TOL, "1023-row columns")
+    assert len(hg) <= len(ho) + 3
+
+
 @pytest.mark.parametrize("nr,nz", [(32, 8), (8, 32), (64, 32)])
 def test_nonsquare_step_parity(mg, nr, nz):
     """Backward-Euler steps (Newton with V-cycle solves) on grids with N_r != N_z: the oracle's
