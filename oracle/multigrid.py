@@ -10,9 +10,12 @@ names no component.  The components below are this project's readings:
 * smoother: collective (3x3 point-block) Gauss-Seidel in red-black order,
   red = (i + j) even first; in a five-point stencil nodes of one colour do not
   couple, so a half sweep is an exact block solve of the colour's own rows;
-  or (line=True) z-line Gauss-Seidel in zebra order, even columns first: a half
+  or (line=True or "z") z-line Gauss-Seidel in zebra order, even columns first: a half
   sweep solves the block-tridiagonal system of every column of one parity
-  exactly, its r-neighbours (the other parity) held fixed;
+  exactly, its r-neighbours (the other parity) held fixed; (line="r") r-line
+  Gauss-Seidel, the same along the rows, even rows first (row index j counted from the
+  cathode row 0); (line="alt") alternating lines: each sweep a z-line sweep, then an
+  r-line sweep;
 * prolongation P: bilinear interpolation in the node coordinates (r equidistant,
   z by distance weights), identity across the three fields; electrode rows carry 0;
 * restriction R = P^T acting on the finite-volume-integrated residual;
@@ -65,10 +68,22 @@ def inject(gf: Grid, a: np.ndarray) -> np.ndarray:
     return a[..., ::2, ::2].copy()
 
 
+class _ScaledLU:
+    """Solve of an equilibrated system: A = diag(1/rs) (rs A cs) diag(1/cs)."""
+
+    def __init__(self, lu, rs, cs):
+        self.lu, self.rs, self.cs = lu, rs, cs
+
+    def solve(self, b):
+        return self.cs * self.lu.solve(self.rs * b)
+
+
 class Level:
-    def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics, line: bool = False):
+    def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics, line=False):
         self.g = g
-        self.line = line
+        if line not in (False, True, "z", "r", "alt"):
+            raise ValueError("line must be False, True / 'z', 'r' or 'alt'")
+        self.line = "z" if line is True else line
         self.J = disc.jacobian(g, u, dt, phys)
         nodes = np.arange(g.n_nodes_unknown)
         jj = nodes // g.ni + 1
@@ -85,17 +100,32 @@ class Level:
             blocks = np.zeros((len(nc), 3, 3))
             blocks[Jcc.row // 3, Jcc.row % 3, Jcc.col % 3] = Jcc.data
             self.colors.append((U, O, blocks, self.J[U][:, O].tocsr()))
+        # line half sweeps in their order within a sweep: z-lines (columns of one parity), then
+        # r-lines (rows of one parity); the unknowns of one parity's lines couple only along
+        # their own line, so one sparse LU solves every line of the half sweep exactly.  The
+        # line matrices are equilibrated first (every column, then every row scaled to a unit
+        # max-abs entry, as in `direct`): unscaled, densities (~1e14) and potentials (~1e2) in
+        # one system left the sparse LU's pivots off by up to 1e-6 of a field on lines along the
+        # weakly coupled direction
         self.lines = []
-        if line:
+        groups = {"z": [ii], "r": [jj], "alt": [ii, jj]}.get(self.line, [])
+        for idx in groups:
             for c in (0, 1):
-                nc = nodes[ii % 2 == c]
-                oc = nodes[ii % 2 != c]
+                nc = nodes[idx % 2 == c]
+                oc = nodes[idx % 2 != c]
+                if len(nc) == 0:
+                    continue  # a level with a single line across: no line of this parity
                 U = (3 * nc[:, None] + np.arange(3)[None, :]).ravel()
                 O = (3 * oc[:, None] + np.arange(3)[None, :]).ravel()
                 JUU = self.J[U][:, U].tocoo()
-                if np.any(ii[nc[JUU.row // 3]] != ii[nc[JUU.col // 3]]):
-                    raise AssertionError("columns of one parity couple: not a five-point stencil")
-                self.lines.append((U, O, spla.splu(JUU.tocsc()), self.J[U][:, O].tocsr()))
+                if np.any(idx[nc[JUU.row // 3]] != idx[nc[JUU.col // 3]]):
+                    raise AssertionError("lines of one parity couple: not a five-point stencil")
+                A = JUU.tocsr()
+                cs = 1.0 / np.asarray(abs(A).max(axis=0).todense()).ravel()
+                A = A @ sp.diags(cs)
+                rs = 1.0 / np.asarray(abs(A).max(axis=1).todense()).ravel()
+                A = sp.diags(rs) @ A
+                self.lines.append((U, O, _ScaledLU(spla.splu(A.tocsc()), rs, cs), self.J[U][:, O].tocsr()))
         self.dense = None
 
     def smooth(self, x: np.ndarray, f: np.ndarray, sweeps: int) -> np.ndarray:
@@ -133,7 +163,7 @@ class Hierarchy:
     def __init__(self, g: Grid, u: np.ndarray, dt: Optional[float], phys: disc.Physics,
                  coarsest: int = 2, nu1: int = 4, nu2: int = 4, nu_coarse_n: int = 64,
                  nu_coarse1: int = 2, nu_coarse2: int = 2, nu_tiny_n: int = 8, nu_tiny1: int = 1,
-                 nu_tiny2: int = 1, line: bool = False):
+                 nu_tiny2: int = 1, line=False):
         """Smoothing: nu1 / nu2 sweeps before / after the coarse-grid correction, except on
         levels whose larger side has at most nu_tiny_n intervals (nu_tiny1 / nu_tiny2) or else at
         most nu_coarse_n intervals (nu_coarse1 / nu_coarse2); 0 switches a tier off."""

@@ -181,3 +181,60 @@ def test_line_smoother_converges_and_resists_anisotropy(R):
     assert res[True][1] < 0.05
     if R >= 1e-1:
         assert res[False][1] > 0.2 and res[False][1] > 10 * res[True][1]
+
+
+def test_rline_half_sweep_solves_its_rows():
+    """f1, r-lines: a zebra half sweep leaves zero residual (to rounding) in every unknown of the
+    rows of its parity, whatever the other rows hold (each row's block-tridiagonal system along
+    r solved exactly); the two parities together cover every unknown once; alternating lines
+    run the z-line half sweeps, then the r-line ones."""
+    g, u, phys, f, tn = _line_case(1e-3)
+    lev = mg.Level(g, u, 1e-7, phys, line="r")
+    rng = np.random.default_rng(1)
+    for c in (0, 1):
+        x = rng.standard_normal(f.shape) * np.tile([1e12, 1e12, 1.0], len(f) // 3)
+        U, O, lu, JUO = lev.lines[c]
+        x[U] = lu.solve(f[U] - JUO @ x[O])
+        r = f - lev.J @ x
+        sc = abs(lev.J) @ np.abs(x) + np.abs(f)
+        assert np.abs(r[U]).max() <= 1e-13 * sc[U].max(), c
+        assert np.abs(r[O]).max() > 1e-3 * sc[O].max()
+        # the rows of parity c: unknowns of the rows j with j % 2 == c (j from the cathode row 0)
+        rows = (U[::3] // 3) // g.ni + 1
+        assert np.all(rows % 2 == c)
+    assert sorted(np.concatenate([lev.lines[0][0], lev.lines[1][0]])) == list(range(len(f)))
+    alt = mg.Level(g, u, 1e-7, phys, line="alt")
+    zl = mg.Level(g, u, 1e-7, phys, line=True)
+    assert len(alt.lines) == 4
+    for q in range(2):
+        assert np.array_equal(alt.lines[q][0], zl.lines[q][0])
+        assert np.array_equal(alt.lines[2 + q][0], lev.lines[q][0])
+
+
+@pytest.mark.parametrize("R", [1e-3, 1e-1])
+def test_line_directions_resist_anisotropy_along_their_lines(R):
+    """f1: smoothing along the strongly coupled direction.  With dr = dz / 10 (R = d / 10: the
+    r-faces couple 100 times more strongly) r-lines and alternating lines converge with a factor
+    below 0.2 while point and z-line smoothing stall above 0.5; with dr = 10 dz (R = 10 d) z-lines
+    and alternating lines stay below 0.05 while point and r-line smoothing exceed 0.2.  Every
+    smoother that reaches the tolerance reaches the alternating lines' solution."""
+    g, u, phys, f, tn = _line_case(R)
+    res = {}
+    for line in (False, "z", "r", "alt"):
+        H = mg.Hierarchy(g, u, 1e-7, phys, line=line)
+        x, hist = H.solve(f, 1e-11, 150, scale=tn)
+        fac = (hist[min(6, len(hist) - 1)] / hist[1]) ** (1.0 / (min(6, len(hist) - 1) - 1))
+        res[line] = (x, fac, hist[-1] <= 1e-11)
+    if R < 1e-2:
+        good, bad, good_max, bad_min = ("r", "alt"), (False, "z"), 0.2, 0.5
+    else:
+        good, bad, good_max, bad_min = ("z", "alt"), (False, "r"), 0.05, 0.2
+    for line in good:
+        assert res[line][2] and res[line][1] < good_max, (line, res[line][1])
+    for line in bad:
+        assert res[line][1] > bad_min, (line, res[line][1])
+    xa = res["alt"][0]
+    for line in (False, "z", "r"):
+        if res[line][2]:
+            for k in range(3):
+                assert np.abs(res[line][0][k::3] - xa[k::3]).max() <= 1e-6 * np.abs(xa[k::3]).max(), (line, k)
