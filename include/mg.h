@@ -135,9 +135,12 @@ typedef struct mg_params {
                              not converged -> the step is rejected like a failed linear solve */
   int32_t line_smoother;  /* 0: point-block red-black Gauss-Seidel; 1: z-line Gauss-Seidel in
                              zebra order (even columns, then odd; each column's block-tridiagonal
-                             system solved exactly, robust to strong z-coupling) on every level
-                             (the coarse levels then run as separate launches, no coarse-cycle
-                             kernel) */
+                             system solved exactly, robust to strong z-coupling); 2: r-line
+                             Gauss-Seidel (even rows, then odd; each row's system along r,
+                             robust to strong r-coupling; rows of at most 512 unknowns, i.e.
+                             N_r <= 256, or 512 with a Dirichlet wall); 3: alternating lines,
+                             each sweep z-lines then r-lines.  On every level (the coarse levels
+                             then run as separate launches, no coarse-cycle kernel) */
 } mg_params;
 
 /* Per-call statistics. */

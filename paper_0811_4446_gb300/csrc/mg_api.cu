@@ -407,12 +407,22 @@ template <> int sweep_shape<float>(const LevelBuf &b) { return b.sw32; }
 template <typename T>
 int smooth_sweeps(mg_state *s, int l, int nu, cudaStream_t st) {
   if (s->prm.line_smoother) {
+    // a sweep: z-line half sweeps (even columns, then odd), r-line half sweeps (even rows, then
+    // odd), or both in that order (alternating lines)
     T *scr = reinterpret_cast<T *>(s->line_scr);
-    for (int k = 0; k < nu; ++k)
-      for (int col = 0; col < 2; ++col) {
-        ProfScope ps(s, MG_PROF_SMOOTH, l);
-        CK(launch_zline<T>(view<T>(s->lv[l]), col, scr, st));
-      }
+    const int lm = s->prm.line_smoother;
+    for (int k = 0; k < nu; ++k) {
+      if (lm & 1)
+        for (int col = 0; col < 2; ++col) {
+          ProfScope ps(s, MG_PROF_SMOOTH, l);
+          CK(launch_zline<T>(view<T>(s->lv[l]), col, scr, st));
+        }
+      if (lm & 2)
+        for (int row = 0; row < 2; ++row) {
+          ProfScope ps(s, MG_PROF_SMOOTH, l);
+          CK(launch_rline<T>(view<T>(s->lv[l]), row, st));
+        }
+    }
     return MG_OK;
   }
   const LevelT<T> &b = view<T>(s->lv[l]);
@@ -1288,7 +1298,11 @@ static int validate(const mg_grid *g, const mg_params *p, std::string *why) {
   if (!(p->newton_tol_rel >= 0.0 && p->newton_tol_rel < 1.0)) { *why = "newton_tol_rel must be in [0, 1)"; return MG_EINVAL; }
   if (p->full_jacobian != 0 && p->full_jacobian != 1) { *why = "full_jacobian must be 0 or 1"; return MG_EINVAL; }
   if (p->max_corrections < 1 || p->max_corrections > 100) { *why = "max_corrections must be in 1..100"; return MG_EINVAL; }
-  if (p->line_smoother != 0 && p->line_smoother != 1) { *why = "line_smoother must be 0 or 1"; return MG_EINVAL; }
+  if (p->line_smoother < 0 || p->line_smoother > 3) { *why = "line_smoother must be 0, 1, 2 or 3"; return MG_EINVAL; }
+  if ((p->line_smoother & 2) && (p->wall_dirichlet ? g->nr : g->nr + 1) > kRlineMax) {
+    *why = "r-lines need rows of at most 512 unknowns";
+    return MG_EINVAL;
+  }
   if (p->pdl < 0 || p->pdl > PDL_ALL) { *why = "pdl: a combination of the PDL kernel-kind bits"; return MG_EINVAL; }
   if (p->nu_tiny_n < 0 || (p->nu_tiny_n > 0 && (p->nu_tiny1 < 0 || p->nu_tiny2 < 0 || p->nu_tiny1 + p->nu_tiny2 < 1))) {
     *why = "nu_tiny_n >= 0 and, when set, at least one smoothing sweep on those levels";

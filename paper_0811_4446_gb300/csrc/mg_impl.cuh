@@ -281,6 +281,10 @@ cudaError_t launch_add_transport(const Level &L, const StateView &sv, const Tran
                                  double *out[3], cudaStream_t st);
 template <typename T>
 cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st);
+// r-line zebra half sweep (rows of one parity; at most kRlineMax unknowns a row)
+constexpr int kRlineMax = 512;
+template <typename T>
+cudaError_t launch_rline(const LevelT<T> &L, int color, cudaStream_t st);
 cudaError_t launch_add3(double *const acc[3], double *const x[3], size_t n, cudaStream_t st);
 cudaError_t launch_split_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);
 cudaError_t launch_join_rows(const Level &L, double *const in[3], double *const out[3], cudaStream_t st);

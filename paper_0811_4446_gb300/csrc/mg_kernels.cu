@@ -1051,6 +1051,128 @@ cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st)
 template cudaError_t launch_zline<double>(const LevelT<double> &, int, double *, cudaStream_t);
 template cudaError_t launch_zline<float>(const LevelT<float> &, int, float *, cudaStream_t);
 
+// r-line Gauss-Seidel, zebra order (even rows first, then odd): one CTA per row of the parity
+// solves the row's block-tridiagonal system along r (unknown columns 0 .. ni-1) exactly by the
+// same parallel cyclic reduction as the z-lines, a thread per unknown, its z-neighbours (rows
+// j +- 1, the other parity) held at their current values.  Column i:
+// Lo_i x_{i-1} + D_i x_i + Up_i x_{i+1} = f_i - (N and S couplings), the W / E face blocks
+// [[-c_xe, 0, c_ve], [0, -c_xp, c_vp], [0, 0, g]] of the r-faces (c_x = cG towards the west
+// neighbour, cF towards the east one); the wall column of a Dirichlet wall is not an unknown.
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_rline_pcr(LevelT<T> L, int color) {
+  extern __shared__ __align__(16) unsigned char rl_smem[];
+  T *X = reinterpret_cast<T *>(rl_smem);  // [21][ni]
+  const int n = L.ni, P = L.P, t = threadIdx.x;
+  const int j = 2 * blockIdx.x + 2 - color;  // color 0: rows 2, 4, ...; color 1: rows 1, 3, ...
+  const int i = t;
+  const bool node = i < n;
+  T D[9], Lo[9], Up[9], r[3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) { D[q] = T(0); Lo[q] = T(0); Up[q] = T(0); }
+  r[0] = r[1] = r[2] = T(0);
+  if (node) {
+    const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
+    const SplitNb d = split_nb(P, i, j);
+    T re = L.f[NE][d.self], rp = L.f[NP][d.self], rV = L.f[NV][d.self];
+    acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], L.du[NE][d.N],
+             L.du[NP][d.N], L.du[NV][d.N]);
+    acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], L.du[NE][d.S],
+             L.du[NP][d.S], L.du[NV][d.S]);
+    r[0] = re; r[1] = rp; r[2] = rV;
+    const T ak = L.Ak[k];
+    D[0] = L.dia[DA11][k]; D[2] = L.fac[FA13][d.self];
+    D[4] = L.dia[DA22][k]; D[5] = L.fac[FA23][d.self];
+    D[6] = -ak; D[7] = ak; D[8] = L.dia[DA33][k];
+    if (i > 0) {
+      Lo[0] = -L.cr[CGE][kW]; Lo[2] = L.cr[CVE][kW]; Lo[4] = -L.cr[CGP][kW]; Lo[5] = L.cr[CVP][kW];
+      Lo[8] = L.gR[kW];
+    }
+    if (i < n - 1) {
+      Up[0] = -L.cr[CFE][k]; Up[2] = L.cr[CVE][k]; Up[4] = -L.cr[CFP][k]; Up[5] = L.cr[CVP][k]; Up[8] = L.gR[k];
+    }
+  }
+  for (int h = 1; h < n; h <<= 1) {
+    if (node) {
+      T Di[9], t9[9];
+      inv3(D, Di);
+      mm3(Di, Lo, t9);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) X[q * n + i] = t9[q];
+      mm3(Di, Up, t9);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) X[(9 + q) * n + i] = t9[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) X[(18 + q) * n + i] = Di[3 * q] * r[0] + Di[3 * q + 1] * r[1] + Di[3 * q + 2] * r[2];
+    }
+    __syncthreads();
+    if (node) {
+      const int m = i - h, p = i + h;
+      T nLo[9], nUp[9], a9[9], b9[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) { nLo[q] = T(0); nUp[q] = T(0); }
+      if (m >= 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { a9[q] = X[q * n + m]; b9[q] = X[(9 + q) * n + m]; }
+        T c9[9];
+        mm3(Lo, b9, c9);  // Lo (D^-1 Up)_m
+#pragma unroll
+        for (int q = 0; q < 9; ++q) D[q] -= c9[q];
+        mm3(Lo, a9, c9);  // Lo (D^-1 Lo)_m
+#pragma unroll
+        for (int q = 0; q < 9; ++q) nLo[q] = -c9[q];
+        const T y0 = X[18 * n + m], y1 = X[19 * n + m], y2 = X[20 * n + m];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r[q] -= Lo[3 * q] * y0 + Lo[3 * q + 1] * y1 + Lo[3 * q + 2] * y2;
+      }
+      if (p < n) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { a9[q] = X[q * n + p]; b9[q] = X[(9 + q) * n + p]; }
+        T c9[9];
+        mm3(Up, a9, c9);  // Up (D^-1 Lo)_p
+#pragma unroll
+        for (int q = 0; q < 9; ++q) D[q] -= c9[q];
+        mm3(Up, b9, c9);  // Up (D^-1 Up)_p
+#pragma unroll
+        for (int q = 0; q < 9; ++q) nUp[q] = -c9[q];
+        const T y0 = X[18 * n + p], y1 = X[19 * n + p], y2 = X[20 * n + p];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r[q] -= Up[3 * q] * y0 + Up[3 * q + 1] * y1 + Up[3 * q + 2] * y2;
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) { Lo[q] = nLo[q]; Up[q] = nUp[q]; }
+    }
+    __syncthreads();
+  }
+  if (node) {
+    T Di[9];
+    inv3(D, Di);
+    const size_t kd = cidx(P, i, j);
+    L.du[NE][kd] = Di[0] * r[0] + Di[1] * r[1] + Di[2] * r[2];
+    L.du[NP][kd] = Di[3] * r[0] + Di[4] * r[1] + Di[5] * r[2];
+    L.du[NV][kd] = Di[6] * r[0] + Di[7] * r[1] + Di[8] * r[2];
+  }
+}
+
+// rows of one parity: color 0 the even rows 2, 4, ... < nz, color 1 the odd rows 1, 3, ... < nz;
+// rows of at most kRlineMax unknowns (mg_create checks)
+template <typename T>
+cudaError_t launch_rline(const LevelT<T> &L, int color, cudaStream_t st) {
+  const int rows = color == 0 ? (L.nz - 2) / 2 : L.nz / 2;
+  if (rows <= 0) return cudaSuccess;
+  if (L.ni > kRlineMax) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)21 * L.ni * sizeof(T);
+  static std::once_flag raised;
+  std::call_once(raised, []() {
+    cudaFuncSetAttribute(k_rline_pcr<T, kRlineMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         21 * kRlineMax * (int)sizeof(T));
+  });
+  k_rline_pcr<T, kRlineMax><<<rows, (L.ni + 31) / 32 * 32, smem, st>>>(L, color);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_rline<double>(const LevelT<double> &, int, cudaStream_t);
+template cudaError_t launch_rline<float>(const LevelT<float> &, int, cudaStream_t);
+
 // K3 fused: one full red-black sweep per launch.  A block owns a TX x TY tile of nodes.
 // Phase 1 updates the red nodes of the tile and of a one-node ring around it (ring nodes are
 // also updated by the neighbouring tiles, with identical inputs and arithmetic), keeping them
