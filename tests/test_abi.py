@@ -58,10 +58,18 @@ def test_workspace_sizing_without_gpu(lib):
     bad = mg.mg_grid(255, 256, 1e-2, z.ctypes.data_as(mg._dp))
     assert mg.load().mg_workspace_bytes(ctypes.byref(bad), ctypes.byref(p)) == 0
     # parameters of the later forms are validated before any allocation (0 bytes = invalid)
-    for kw in (dict(full_jacobian=2), dict(max_corrections=0), dict(max_corrections=101), dict(line_smoother=2),
+    for kw in (dict(full_jacobian=2), dict(max_corrections=0), dict(max_corrections=101), dict(line_smoother=4),
                dict(newton_tol_rel=1.0), dict(newton_tol_rel=-0.1), dict(pdl=32), dict(wall_dirichlet=2)):
         pb = mg.default_params(**kw)
         assert mg.load().mg_workspace_bytes(ctypes.byref(g), ctypes.byref(pb)) == 0, kw
+    # r-lines (2) and alternating lines (3): rows of at most 512 unknowns
+    z512 = W.z_nodes(512, 1e-2)
+    g512 = mg.mg_grid(512, 512, 1e-2, z512.ctypes.data_as(mg._dp))
+    for line in (2, 3):
+        assert mg.load().mg_workspace_bytes(ctypes.byref(g), ctypes.byref(mg.default_params(line_smoother=line))) > 0
+        assert mg.load().mg_workspace_bytes(ctypes.byref(g512), ctypes.byref(mg.default_params(line_smoother=line))) == 0
+        assert mg.load().mg_workspace_bytes(ctypes.byref(g512), ctypes.byref(
+            mg.default_params(line_smoother=line, wall_dirichlet=1))) > 0
     # the line smoother's column scratch is allocated only when it is enabled
     nl = mg.load().mg_workspace_bytes(ctypes.byref(g), ctypes.byref(mg.default_params(line_smoother=1)))
     assert 0 <= nl - n256 - 8 * 12 * 257 * 129 < 256     # plus its 256-byte alignment
