@@ -722,6 +722,32 @@ def measure_forms(args, dev, peaks):
                                           "converged": rc == mg.MG_OK}
             s.close()
     out["line_smoother_257"] = line
+    # r-lines and alternating lines against point smoothing on a strongly r-coupled Newton system
+    # (257^2 nodes, R = d / 5 so that dz = 5 dr, table transport, dt = 100 ns)
+    dr_ = W.make_discharge(256, seed=0, V_cathode=-300.0, use_table=True, R=2e-3)
+    rline = {"workload": "257x257 nodes, R = 2 mm, d = 1 cm (dz = 5 dr), table transport, dt = 1e-7 s, "
+                         "linear solve of one Newton system to 1e-8"}
+    for prec_name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
+        for name, ls in (("point", 0), ("r_line", 2), ("alternating", 3)):
+            s = mg.from_discharge(dr_, precision=prec, line_smoother=ls)
+            s.autotune()
+            F, _ = s.residual(1e-7)
+            f = [-a for a in F]
+            s.linear_solve(1e-7, f, 0.0, 0)
+            t0 = time.perf_counter()
+            s.linear_solve(1e-7, f, 0.0, 0)
+            t1 = time.perf_counter()
+            _, hist, _ = s.linear_solve(1e-7, f, 0.0, 6)
+            t2 = time.perf_counter()
+            vc_us = ((t2 - t1) - (t1 - t0)) / 6 * 1e6
+            t3 = time.perf_counter()
+            _, h2, rc = s.linear_solve(1e-7, f, 1e-8, 400)
+            t4 = time.perf_counter()
+            rline[f"{prec_name}_{name}"] = {"vcycle_us": vc_us, "factor": float((hist[-1] / hist[1]) ** 0.2),
+                                           "cycles_to_1e-8": len(h2) - 1, "solve_ms": 1000 * (t4 - t3),
+                                           "converged": rc == mg.MG_OK}
+            s.close()
+    out["r_line_smoother_257"] = rline
     # mixed-precision steady solve of the same 257^2 workload
     s = mg.from_discharge(d, precision=mg.MG_MIXED)
     s.autotune()
