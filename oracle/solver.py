@@ -55,7 +55,8 @@ class SolverOptions:
     eta_adapt: bool = True          # relax eta when the Newton residual is near its target
     full_jacobian: bool = False     # Newton with the field dependence of mu, D in the Jacobian
     max_corrections: int = 20       # defect corrections per Newton iteration (full_jacobian)
-    line_smoother: bool = False     # z-line zebra Gauss-Seidel instead of point red-black
+    line_smoother: object = False   # line Gauss-Seidel instead of point red-black: True / "z"
+                                    # (z-lines), "r" (r-lines), "alt" (alternating)
 
 
 @dataclasses.dataclass

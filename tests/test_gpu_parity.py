@@ -406,6 +406,24 @@ def test_solve_steady_continuation_parity_33(mg):
     _assert_fields(s.get_state(), uo, FP64_TOL)
 
 
+@pytest.mark.parametrize("line,R", [(1, 0.1), (2, 2e-3), (3, 2e-3)])
+def test_line_smoother_steady_continuation_parity_33(mg, line, R):
+    """f1 in whole solves: the 17^2 -> 33^2 continuation with z-lines (R = 10 d), r-lines or
+    alternating lines (R = d / 5) on every level: the oracle's steps, rejections, Newton
+    iterations and V-cycles on both grids, and its steady state to 1e-10."""
+    d = W.make_discharge(32, seed=0, V_cathode=-300.0, use_table=True, R=R)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    s = mg.from_discharge(d, eta=1e-12, max_vcycles=200, line_smoother=line)
+    rc, st = s.solve_steady(1e-10)
+    assert rc == mg.MG_OK
+    opt = osv.SolverOptions(eta=1e-12, max_vcycles=200, line_smoother={1: "z", 2: "r", 3: "alt"}[line])
+    uo, ok, rec_c, rec_f = osv.solve_steady(g, u, d.S_e, d.S_p, phys, 1e-10, opt)
+    assert ok
+    assert _gpu_counts(st) == _oracle_counts(rec_c, rec_f)
+    _assert_fields(s.get_state(), uo, FP64_TOL)
+
+
 @pytest.mark.parametrize("chain_from,dt_max", [(2, 1e-6), (3, 1.0)])
 def test_solve_steady_chain_parity_65(mg, chain_from, dt_max):
     """Multilevel continuation from the grid coarsened chain_from times (17^2 or 9^2 up to 65^2),
