@@ -1,6 +1,6 @@
 """Small fixed workloads for profiling runs (ncu captures of single kernels).
 
-    python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager] [--autotune] [--half] [--line]
+    python -m paper_0811_4446_gb300.cases vcycles N [CYCLES] [--mixed] [--eager] [--autotune] [--half] [--line | --rline | --alt]
     python -m paper_0811_4446_gb300.cases unet B N [REPS] [--mma | --gather | --tma | --halo] [--eager]
     python -m paper_0811_4446_gb300.cases steady [--mixed] [--eager]
     python -m paper_0811_4446_gb300.cases batch COUNT [--fp64]
@@ -16,7 +16,9 @@ sweep, two per half-sweep pair, as the autotuner chose for the level), finest le
 benchmark does (its timing launches come before the V-cycles).  The linear solve (its
 residual, hierarchy set-up and V-cycles) runs inside the NVTX range "measure".  --half
 smooths with two half-sweep launches per sweep on every level (no fused sweeps); --line
-uses the z-line zebra smoother (on a grid with R = 10 d, dr = 10 dz, where it pays).
+uses the z-line zebra smoother (on a grid with R = 10 d, dr = 10 dz, where it pays); --rline the
+r-line one and --alt alternating z- and r-lines (on a grid with R = d / 5, dz = 5 dr, where r-lines
+pay).
 
 steady: one steady solve of the benchmark's 257 x 257 workload (129 -> 257 continuation,
 table transport, rho <= 1e-8) after one untimed solve, autotuned as the benchmark does, inside
@@ -41,7 +43,7 @@ import sys
 
 
 def vcycles(n: int, cycles: int = 3, mixed: bool = False, eager: bool = False, autotune: bool = False,
-            half: bool = False, line: bool = False) -> float:
+            half: bool = False, line: int = 0) -> float:
     import torch
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -50,9 +52,10 @@ def vcycles(n: int, cycles: int = 3, mixed: bool = False, eager: bool = False, a
     import workloads as W
     from . import mg
 
-    d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=(n == 256), R=0.1 if line else 1e-2)
+    R = {0: 1e-2, 1: 0.1, 2: 2e-3, 3: 2e-3}[line]
+    d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=(n == 256), R=R)
     s = mg.from_discharge(d, precision=mg.MG_MIXED if mixed else mg.MG_FP64, use_graphs=0 if eager else 1,
-                          fused_sweep=0 if half else 1, line_smoother=1 if line else 0)
+                          fused_sweep=0 if half else 1, line_smoother=line)
     if autotune:
         s.autotune()
     F, _ = s.residual(1e-6)
@@ -158,4 +161,5 @@ if __name__ == "__main__":
     N = int(sys.argv[2])
     C = int(sys.argv[3]) if len(sys.argv) > 3 and not sys.argv[3].startswith("--") else 3
     print("ok", N, vcycles(N, C, "--mixed" in sys.argv, "--eager" in sys.argv, "--autotune" in sys.argv,
-                           "--half" in sys.argv, "--line" in sys.argv))
+                           "--half" in sys.argv,
+                           1 if "--line" in sys.argv else 2 if "--rline" in sys.argv else 3 if "--alt" in sys.argv else 0))
