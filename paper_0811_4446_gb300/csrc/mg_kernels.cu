@@ -834,7 +834,9 @@ template cudaError_t launch_smooth<float>(const LevelT<float> &, int, cudaStream
 // blocks [[-c_xe, 0, c_ve], [0, -c_xp, c_vp], [0, 0, g]] (c_x = cF towards the north
 // neighbour, cG towards the south one).  Forward: M_j = D_j - Lo_j C_{j-1}, C_j = M_j^-1 Up_j,
 // y_j = M_j^-1 (rhs_j - Lo_j y_{j-1}) (kept in scr, 12 planes of (nz+1) x cstride);
-// backward: x_j = y_j - C_j x_{j+1}, the electrode rows held at zero.
+// backward: x_j = y_j - C_j x_{j+1}, the electrode rows held at zero.  The form for columns the
+// shared-memory kernels below do not take: FP64 columns of more than 512 rows, FP32 ones of more
+// than 1,024.
 
 // inverse of a general 3x3 matrix (row-major) by its cofactors
 template <typename T>
@@ -911,13 +913,78 @@ __global__ void k_zline(LevelT<T> L, int color, T *scr, int cstride) {
 //   Lo <- -Lo (D^-1 Lo)_{j-h},  Up <- -Up (D^-1 Up)_{j+h},
 // so the couplings move 2h rows away; after log2(nz) rounds the rows are decoupled and
 // x_j = D_j^-1 r_j.  Rows past the column ends couple to the electrode rows (x = 0) and are
-// dropped.  nz threads (a power of two, up to 512).
+// dropped.  nz threads (a power of two, up to 1,024).  The FP32 form: its rounds are short and
+// it is bound by their latency; in FP64 the rounds' arithmetic bounds it (every row inverts a
+// 3x3 block and forms five 3x3 products per round), and block cyclic reduction (k_line_cr, below)
+// does about a sixth of that work.
 template <typename T>
 __device__ __forceinline__ void mm3(const T (&a)[9], const T *b, T (&c)[9]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int q = 0; q < 3; ++q) c[3 * r + q] = a[3 * r] * b[q] + a[3 * r + 1] * b[3 + q] + a[3 * r + 2] * b[6 + q];
+}
+
+// One unknown of a z-line (column i, row j; rows 1 .. nz-1): the diagonal block, the blocks to the
+// rows below (Lo) and above (Up), zero at the column's ends, and the right-hand side with the
+// r-neighbours (the other parity's columns) held at their current corrections.
+template <typename T>
+__device__ __forceinline__ void zline_row(const LevelT<T> &L, int i, int j, T (&D)[9], T (&Lo)[9], T (&Up)[9],
+                                          T (&r)[3]) {
+  const int P = L.P, nz = L.nz;
+  const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
+  const SplitNb d = split_nb(P, i, j);
+  T re = L.f[NE][d.self], rp = L.f[NP][d.self], rV = L.f[NV][d.self];
+  acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], L.du[NE][d.E],
+           L.du[NP][d.E], L.du[NV][d.E]);
+  acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], L.du[NE][d.W],
+           L.du[NP][d.W], L.du[NV][d.W]);
+  r[0] = re; r[1] = rp; r[2] = rV;
+  const T ak = L.Ak[k];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) { D[q] = T(0); Lo[q] = T(0); Up[q] = T(0); }
+  D[0] = L.dia[DA11][k]; D[2] = L.fac[FA13][d.self];
+  D[4] = L.dia[DA22][k]; D[5] = L.fac[FA23][d.self];
+  D[6] = -ak; D[7] = ak; D[8] = L.dia[DA33][k];
+  if (j > 1) {
+    Lo[0] = -L.cz[CGE][kS]; Lo[2] = L.cz[CVE][kS]; Lo[4] = -L.cz[CGP][kS]; Lo[5] = L.cz[CVP][kS];
+    Lo[8] = L.gZ[kS];
+  }
+  if (j < nz - 1) {
+    Up[0] = -L.cz[CFE][k]; Up[2] = L.cz[CVE][k]; Up[4] = -L.cz[CFP][k]; Up[5] = L.cz[CVP][k]; Up[8] = L.gZ[k];
+  }
+}
+
+// One unknown of an r-line (row j, column i; columns 0 .. ni-1): the blocks to the west (Lo) and
+// east (Up) neighbours, [[-c_xe, 0, c_ve], [0, -c_xp, c_vp], [0, 0, g]] of the r-faces (c_x = cG
+// towards the west neighbour, cF towards the east one), zero at the row's ends, and the
+// right-hand side with the z-neighbours (rows j +- 1, the other parity) held at their current
+// corrections.
+template <typename T>
+__device__ __forceinline__ void rline_row(const LevelT<T> &L, int i, int j, T (&D)[9], T (&Lo)[9], T (&Up)[9],
+                                          T (&r)[3]) {
+  const int P = L.P, n = L.ni;
+  const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
+  const SplitNb d = split_nb(P, i, j);
+  T re = L.f[NE][d.self], rp = L.f[NP][d.self], rV = L.f[NV][d.self];
+  acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], L.du[NE][d.N],
+           L.du[NP][d.N], L.du[NV][d.N]);
+  acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], L.du[NE][d.S],
+           L.du[NP][d.S], L.du[NV][d.S]);
+  r[0] = re; r[1] = rp; r[2] = rV;
+  const T ak = L.Ak[k];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) { D[q] = T(0); Lo[q] = T(0); Up[q] = T(0); }
+  D[0] = L.dia[DA11][k]; D[2] = L.fac[FA13][d.self];
+  D[4] = L.dia[DA22][k]; D[5] = L.fac[FA23][d.self];
+  D[6] = -ak; D[7] = ak; D[8] = L.dia[DA33][k];
+  if (i > 0) {
+    Lo[0] = -L.cr[CGE][kW]; Lo[2] = L.cr[CVE][kW]; Lo[4] = -L.cr[CGP][kW]; Lo[5] = L.cr[CVP][kW];
+    Lo[8] = L.gR[kW];
+  }
+  if (i < n - 1) {
+    Up[0] = -L.cr[CFE][k]; Up[2] = L.cr[CVE][k]; Up[4] = -L.cr[CFP][k]; Up[5] = L.cr[CVP][k]; Up[8] = L.gR[k];
+  }
 }
 
 template <typename T, int MAXT>
@@ -932,27 +999,7 @@ __global__ void __launch_bounds__(MAXT) k_zline_pcr(LevelT<T> L, int color) {
 #pragma unroll
   for (int q = 0; q < 9; ++q) { D[q] = T(0); Lo[q] = T(0); Up[q] = T(0); }
   r[0] = r[1] = r[2] = T(0);
-  if (row) {
-    const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
-    const SplitNb d = split_nb(P, i, j);
-    T re = L.f[NE][d.self], rp = L.f[NP][d.self], rV = L.f[NV][d.self];
-    acc_face(re, rp, rV, L.cr[CVE][k], L.cr[CFE][k], L.cr[CVP][k], L.cr[CFP][k], L.gR[k], L.du[NE][d.E],
-             L.du[NP][d.E], L.du[NV][d.E]);
-    acc_face(re, rp, rV, L.cr[CVE][kW], L.cr[CGE][kW], L.cr[CVP][kW], L.cr[CGP][kW], L.gR[kW], L.du[NE][d.W],
-             L.du[NP][d.W], L.du[NV][d.W]);
-    r[0] = re; r[1] = rp; r[2] = rV;
-    const T ak = L.Ak[k];
-    D[0] = L.dia[DA11][k]; D[2] = L.fac[FA13][d.self];
-    D[4] = L.dia[DA22][k]; D[5] = L.fac[FA23][d.self];
-    D[6] = -ak; D[7] = ak; D[8] = L.dia[DA33][k];
-    if (j > 1) {
-      Lo[0] = -L.cz[CGE][kS]; Lo[2] = L.cz[CVE][kS]; Lo[4] = -L.cz[CGP][kS]; Lo[5] = L.cz[CVP][kS];
-      Lo[8] = L.gZ[kS];
-    }
-    if (j < nz - 1) {
-      Up[0] = -L.cz[CFE][k]; Up[2] = L.cz[CVE][k]; Up[4] = -L.cz[CFP][k]; Up[5] = L.cz[CVP][k]; Up[8] = L.gZ[k];
-    }
-  }
+  if (row) zline_row(L, i, j, D, Lo, Up, r);
   for (int h = 1; h < nz; h <<= 1) {
     if (row) {
       T Di[9], t9[9];
@@ -1015,36 +1062,168 @@ __global__ void __launch_bounds__(MAXT) k_zline_pcr(LevelT<T> L, int color) {
   }
 }
 
+// The same line solves by block cyclic reduction (the FP64 form): rows q = 1 .. n of the line
+// (z-lines: q = j, n = nz - 1; r-lines: q = i + 1, n = ni).  Level h = 1, 2, 4, ...: the rows
+// q = h (2g + 1) are eliminated, each publishing D^-1 [Lo | Up | r] = [a | c | y]; the rows
+// q = 2h (g + 1) fold in their neighbours q -+ h exactly as a round of parallel cyclic reduction
+// does, so their couplings move 2h rows away; the level whose rows have no survivor left is
+// decoupled (x = y).  Back substitution from the top level down: x_q = y_q - a_q x_{q-h} - c_q x_{q+h}.
+// A level does the arithmetic of its own rows only, about 1/6 of the cyclic-reduction work over
+// the whole line.  Three lanes per row, lane rr owning row rr of every 3x3 block (its row of
+// D^-1 from the cofactors of column rr, det expanded along that column), keep the warps full
+// while the levels shrink.  Shared memory: 30 planes of the rows' current blocks [D | Lo | Up | r],
+// then 21 of [a | c | y]; the solution goes to the D planes once the forward pass is done.
+// 3 ceil(n / 2) threads (at least n: one per row assembles the system).
+template <typename T, bool ZL>
+__global__ void __launch_bounds__(768, 1) k_line_cr(LevelT<T> L, int color) {
+  extern __shared__ __align__(16) unsigned char lc_smem[];
+  T *S = reinterpret_cast<T *>(lc_smem);
+  const int n = ZL ? L.nz - 1 : L.ni;
+  const int line = ZL ? 2 * blockIdx.x + color : 2 * blockIdx.x + 2 - color;
+  T *N = S + 30 * n;
+  const int tid = threadIdx.x;
+  if (tid < n) {
+    T D[9], Lo[9], Up[9], r[3];
+    if (ZL)
+      zline_row(L, line, tid + 1, D, Lo, Up, r);
+    else
+      rline_row(L, tid, line, D, Lo, Up, r);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      S[q * n + tid] = D[q];
+      S[(9 + q) * n + tid] = Lo[q];
+      S[(18 + q) * n + tid] = Up[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S[(27 + q) * n + tid] = r[q];
+  }
+  __syncthreads();
+  const int g = tid / 3, rr = tid - 3 * g;
+  const int c1 = rr == 2 ? 0 : rr + 1, c2 = rr == 0 ? 2 : rr - 1;  // (rr + 1) % 3, (rr + 2) % 3
+  int h = 1;
+  for (;; h <<= 1) {
+    const int E = (n / h + 1) >> 1, Sv = n / (2 * h);
+    if (g < E) {
+      const T *Su = S + h * (2 * g + 1) - 1;
+      T *Nu = N + h * (2 * g + 1) - 1;
+      const T d0a = Su[c1 * n], d1a = Su[(3 + c1) * n], d2a = Su[(6 + c1) * n];
+      const T d0b = Su[c2 * n], d1b = Su[(3 + c2) * n], d2b = Su[(6 + c2) * n];
+      const T d0r = Su[rr * n], d1r = Su[(3 + rr) * n], d2r = Su[(6 + rr) * n];
+      // cofactors of column rr (rows k = 0, 1, 2)
+      const T C0 = d1a * d2b - d1b * d2a, C1 = d2a * d0b - d2b * d0a, C2 = d0a * d1b - d0b * d1a;
+      const T id = T(1) / (d0r * C0 + d1r * C1 + d2r * C2);
+      const T e0 = C0 * id, e1 = C1 * id, e2 = C2 * id;  // row rr of D^-1
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Nu[(3 * rr + c) * n] = e0 * Su[(9 + c) * n] + e1 * Su[(12 + c) * n] + e2 * Su[(15 + c) * n];
+        Nu[(9 + 3 * rr + c) * n] = e0 * Su[(18 + c) * n] + e1 * Su[(21 + c) * n] + e2 * Su[(24 + c) * n];
+      }
+      Nu[(18 + rr) * n] = e0 * Su[27 * n] + e1 * Su[28 * n] + e2 * Su[29 * n];
+    }
+    __syncthreads();
+    if (Sv == 0) break;
+    if (g < Sv) {
+      const int u = 2 * h * (g + 1) - 1;
+      T *Su = S + u;
+      const T *Nm = N + (u - h);
+      T Lr[3], Ur[3], Dr[3], nL[3], nU[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Lr[k] = Su[(9 + 3 * rr + k) * n];
+        Ur[k] = Su[(18 + 3 * rr + k) * n];
+        Dr[k] = Su[(3 * rr + k) * n];
+      }
+      T r0 = Su[(27 + rr) * n];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        nL[c] = -(Lr[0] * Nm[c * n] + Lr[1] * Nm[(3 + c) * n] + Lr[2] * Nm[(6 + c) * n]);
+        Dr[c] -= Lr[0] * Nm[(9 + c) * n] + Lr[1] * Nm[(12 + c) * n] + Lr[2] * Nm[(15 + c) * n];
+        nU[c] = T(0);
+      }
+      r0 -= Lr[0] * Nm[18 * n] + Lr[1] * Nm[19 * n] + Lr[2] * Nm[20 * n];
+      if (u + h < n) {
+        const T *Np = N + (u + h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Dr[c] -= Ur[0] * Np[c * n] + Ur[1] * Np[(3 + c) * n] + Ur[2] * Np[(6 + c) * n];
+          nU[c] = -(Ur[0] * Np[(9 + c) * n] + Ur[1] * Np[(12 + c) * n] + Ur[2] * Np[(15 + c) * n]);
+        }
+        r0 -= Ur[0] * Np[18 * n] + Ur[1] * Np[19 * n] + Ur[2] * Np[20 * n];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Su[(3 * rr + c) * n] = Dr[c];
+        Su[(9 + 3 * rr + c) * n] = nL[c];
+        Su[(18 + 3 * rr + c) * n] = nU[c];
+      }
+      Su[(27 + rr) * n] = r0;
+    }
+    __syncthreads();
+  }
+  T *X = S;  // planes 0 .. 2: the solution
+  T *du = rr == 0 ? L.du[NE] : rr == 1 ? L.du[NP] : L.du[NV];
+  for (; h >= 1; h >>= 1) {
+    const int E = (n / h + 1) >> 1;
+    if (g < E) {
+      const int u = h * (2 * g + 1) - 1;
+      const T *Nu = N + u;
+      T x = Nu[(18 + rr) * n];
+      if (u - h >= 0)
+        x -= Nu[(3 * rr) * n] * X[u - h] + Nu[(3 * rr + 1) * n] * X[n + u - h] + Nu[(3 * rr + 2) * n] * X[2 * n + u - h];
+      if (u + h < n)
+        x -= Nu[(9 + 3 * rr) * n] * X[u + h] + Nu[(10 + 3 * rr) * n] * X[n + u + h] +
+             Nu[(11 + 3 * rr) * n] * X[2 * n + u + h];
+      X[rr * n + u] = x;
+      du[ZL ? cidx(L.P, line, u + 1) : cidx(L.P, u, line)] = x;
+    }
+    __syncthreads();
+  }
+}
+
+// shared memory and threads of the cyclic-reduction line kernel for a line of n unknowns
+template <typename T>
+__host__ __forceinline__ size_t line_cr_smem(int n) { return (size_t)51 * n * sizeof(T); }
+__host__ __forceinline__ int line_cr_threads(int n) { return (3 * ((n + 1) / 2) + 31) / 32 * 32; }
+
+template <typename T, bool ZL>
+cudaError_t launch_line_cr(const LevelT<T> &L, int lines, int color, int n, cudaStream_t st) {
+  static std::once_flag raised;
+  std::call_once(raised, []() {
+    cudaFuncSetAttribute(k_line_cr<T, ZL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)line_cr_smem<T>(kRlineMax));
+  });
+  k_line_cr<T, ZL><<<lines, line_cr_threads(n), line_cr_smem<T>(n), st>>>(L, color);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_zline(const LevelT<T> &L, int color, T *scr, cudaStream_t st) {
   const int n = (L.ni - color + 1) / 2;
   if (n <= 0) return cudaSuccess;
-  if (L.nz <= 512 && (L.nz & (L.nz - 1)) == 0) {
+  if constexpr (sizeof(T) == 8) {
+    // FP64: block cyclic reduction, columns of up to 512 unknowns (208 KB of shared memory)
+    if (L.nz - 1 <= kRlineMax) return launch_line_cr<T, true>(L, n, color, L.nz - 1, st);
+  } else if (L.nz <= 1024 && (L.nz & (L.nz - 1)) == 0) {
+    // FP32: parallel cyclic reduction, one thread per row, 2^k-row columns up to 1,024 (86 KB of
+    // shared memory at 1,024; the limit is raised once per instantiation, call_once because the
+    // batched host-thread form launches from several threads)
     const size_t smem = (size_t)21 * L.nz * sizeof(T);
-    // the 512-row FP64 case needs 86 KB of dynamic shared memory: the limit is raised once per
-    // instantiation (call_once: the batched host-thread form launches from several threads)
-    static std::once_flag raised;
-    if (smem > 48 * 1024)
-      std::call_once(raised, []() {
-        cudaFuncSetAttribute(k_zline_pcr<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             21 * 512 * (int)sizeof(T));
-      });
-    k_zline_pcr<T, 512><<<n, L.nz, smem, st>>>(L, color);
-  } else if (sizeof(T) == 4 && L.nz == 1024) {
-    // 1,024 rows, one thread each: FP32 only (64 registers a thread; the FP64 kernel takes 128),
-    // 86 KB of shared memory
-    if constexpr (sizeof(T) == 4) {
+    if (L.nz <= 512) {
+      k_zline_pcr<T, 512><<<n, L.nz, smem, st>>>(L, color);
+    } else {
       static std::once_flag raised1024;
       std::call_once(raised1024, []() {
         cudaFuncSetAttribute(k_zline_pcr<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              21 * 1024 * (int)sizeof(T));
       });
-      k_zline_pcr<T, 1024><<<n, L.nz, (size_t)21 * L.nz * sizeof(T), st>>>(L, color);
+      k_zline_pcr<T, 1024><<<n, L.nz, smem, st>>>(L, color);
     }
-  } else {
-    const int cstride = (L.nr + 2) / 2;
-    k_zline<T><<<(n + 63) / 64, 64, 0, st>>>(L, color, scr, cstride);
+    count_launch();
+    return cudaGetLastError();
   }
+  const int cstride = (L.nr + 2) / 2;
+  k_zline<T><<<(n + 63) / 64, 64, 0, st>>>(L, color, scr, cstride);
   count_launch();
   return cudaGetLastError();
 }
@@ -1052,9 +1231,10 @@ template cudaError_t launch_zline<double>(const LevelT<double> &, int, double *,
 template cudaError_t launch_zline<float>(const LevelT<float> &, int, float *, cudaStream_t);
 
 // r-line Gauss-Seidel, zebra order (even rows first, then odd): one CTA per row of the parity
-// solves the row's block-tridiagonal system along r (unknown columns 0 .. ni-1) exactly by the
-// same parallel cyclic reduction as the z-lines, a thread per unknown, its z-neighbours (rows
-// j +- 1, the other parity) held at their current values.  Column i:
+// solves the row's block-tridiagonal system along r (unknown columns 0 .. ni-1) exactly, its
+// z-neighbours (rows j +- 1, the other parity) held at their current values: in FP32 by the same
+// parallel cyclic reduction as the z-lines, a thread per unknown; in FP64 by block cyclic
+// reduction (k_line_cr).  Column i:
 // Lo_i x_{i-1} + D_i x_i + Up_i x_{i+1} = f_i - (N and S couplings), the W / E face blocks
 // [[-c_xe, 0, c_ve], [0, -c_xp, c_vp], [0, 0, g]] of the r-faces (c_x = cG towards the west
 // neighbour, cF towards the east one); the wall column of a Dirichlet wall is not an unknown.
@@ -1070,27 +1250,7 @@ __global__ void __launch_bounds__(MAXT) k_rline_pcr(LevelT<T> L, int color) {
 #pragma unroll
   for (int q = 0; q < 9; ++q) { D[q] = T(0); Lo[q] = T(0); Up[q] = T(0); }
   r[0] = r[1] = r[2] = T(0);
-  if (node) {
-    const size_t k = (size_t)j * P + i, kW = k - 1, kS = k - P;
-    const SplitNb d = split_nb(P, i, j);
-    T re = L.f[NE][d.self], rp = L.f[NP][d.self], rV = L.f[NV][d.self];
-    acc_face(re, rp, rV, L.cz[CVE][k], L.cz[CFE][k], L.cz[CVP][k], L.cz[CFP][k], L.gZ[k], L.du[NE][d.N],
-             L.du[NP][d.N], L.du[NV][d.N]);
-    acc_face(re, rp, rV, L.cz[CVE][kS], L.cz[CGE][kS], L.cz[CVP][kS], L.cz[CGP][kS], L.gZ[kS], L.du[NE][d.S],
-             L.du[NP][d.S], L.du[NV][d.S]);
-    r[0] = re; r[1] = rp; r[2] = rV;
-    const T ak = L.Ak[k];
-    D[0] = L.dia[DA11][k]; D[2] = L.fac[FA13][d.self];
-    D[4] = L.dia[DA22][k]; D[5] = L.fac[FA23][d.self];
-    D[6] = -ak; D[7] = ak; D[8] = L.dia[DA33][k];
-    if (i > 0) {
-      Lo[0] = -L.cr[CGE][kW]; Lo[2] = L.cr[CVE][kW]; Lo[4] = -L.cr[CGP][kW]; Lo[5] = L.cr[CVP][kW];
-      Lo[8] = L.gR[kW];
-    }
-    if (i < n - 1) {
-      Up[0] = -L.cr[CFE][k]; Up[2] = L.cr[CVE][k]; Up[4] = -L.cr[CFP][k]; Up[5] = L.cr[CVP][k]; Up[8] = L.gR[k];
-    }
-  }
+  if (node) rline_row(L, i, j, D, Lo, Up, r);
   for (int h = 1; h < n; h <<= 1) {
     if (node) {
       T Di[9], t9[9];
@@ -1160,15 +1320,14 @@ cudaError_t launch_rline(const LevelT<T> &L, int color, cudaStream_t st) {
   const int rows = color == 0 ? (L.nz - 2) / 2 : L.nz / 2;
   if (rows <= 0) return cudaSuccess;
   if (L.ni > kRlineMax) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)21 * L.ni * sizeof(T);
-  static std::once_flag raised;
-  std::call_once(raised, []() {
-    cudaFuncSetAttribute(k_rline_pcr<T, kRlineMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         21 * kRlineMax * (int)sizeof(T));
-  });
-  k_rline_pcr<T, kRlineMax><<<rows, (L.ni + 31) / 32 * 32, smem, st>>>(L, color);
-  count_launch();
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 8) {
+    return launch_line_cr<T, false>(L, rows, color, L.ni, st);  // FP64: block cyclic reduction
+  } else {
+    // FP32: parallel cyclic reduction, a thread per unknown (42 KB of shared memory at most)
+    k_rline_pcr<T, kRlineMax><<<rows, (L.ni + 31) / 32 * 32, (size_t)21 * L.ni * sizeof(T), st>>>(L, color);
+    count_launch();
+    return cudaGetLastError();
+  }
 }
 template cudaError_t launch_rline<double>(const LevelT<double> &, int, cudaStream_t);
 template cudaError_t launch_rline<float>(const LevelT<float> &, int, cudaStream_t);

@@ -337,6 +337,48 @@ def test_line_smoother_1023_row_columns_mixed(mg):
     assert len(hg) <= len(ho) + 3
 
 
+@pytest.mark.parametrize("nr,nz,line,wall,R,precision", [
+    (64, 512, 1, False, 1e-2, "fp64"), (256, 32, 2, False, 1e-2, "fp64"), (512, 64, 2, True, 2.7e-2, "fp64"),
+    (512, 64, 2, True, 2.7e-2, "mixed")])
+def test_longest_lines_linear_solve_parity(mg, nr, nz, line, wall, R, precision):
+    """Line smoothing at the longest lines the line kernels take: z-lines of 511 rows (65 x 513
+    nodes), r-lines of 257 unknowns, and r-lines of 512 unknowns (513 x 65 nodes with the
+    Dirichlet wall, whose column is not an unknown).  In FP64 these run the block
+    cyclic-reduction kernel at its largest launch (768 threads, 51 planes of 512 values in
+    shared memory).  Both sides solve to a relative residual of 1e-12; the oracle's residual
+    history cycle by cycle, the cycle count within one, and the solution per field (FP64 1e-10,
+    mixed 1e-8).  The wall case takes R = 2.7 cm: with R = 1 cm (dz = 8 dr) the oracle's r-line
+    solves level off near 1e-11."""
+    import dataclasses
+    d = W.make_discharge(nr, nz=nz, seed=9, V_cathode=-300.0, R=R)
+    if wall:
+        d = dataclasses.replace(d, wall_dirichlet=True)
+    g = Grid(d.nr, d.nz, d.R, d.z, wall_dirichlet=wall)
+    phys = disc.Physics(V_cathode=d.V_cathode, V_anode=d.V_anode, mu_e=d.mu_e, D_e=d.D_e, mu_p=d.mu_p, D_p=d.D_p)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    if wall:
+        u = disc.apply_dirichlet(u, phys, g)
+    dt = 1e-7
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    s = mg.from_discharge(d, precision=prec, line_smoother=line)
+    s.set_state(*[np.ascontiguousarray(a) for a in u])
+    s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, dt, phys, with_terms=True)
+    xg, hg, rc = s.linear_solve(dt, list(-F), 1e-12, 100)
+    assert rc == mg.MG_OK, hg
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    x, ho = omg.Hierarchy(g, u, dt, phys, line={1: "z", 2: "r"}[line]).solve(disc.to_vec(g, -F), 1e-12, 100,
+                                                                            scale=tn)
+    assert ho[-1] <= 1e-12
+    _assert_fields(xg, disc.from_vec(g, x), FP64_TOL if precision == "fp64" else MIXED_TOL, (nr, nz, line))
+    if precision == "fp64":
+        assert abs(len(hg) - len(ho)) <= 1
+        k = min(len(hg), len(ho), 6)
+        assert np.allclose(hg[:k], ho[:k], rtol=1e-5, atol=1e-14)
+    else:
+        assert len(hg) <= len(ho) + 3
+
+
 @pytest.mark.parametrize("nr,nz", [(32, 8), (8, 32), (64, 32)])
 def test_nonsquare_step_parity(mg, nr, nz):
     """Backward-Euler steps (Newton with V-cycle solves) on grids with N_r != N_z: the oracle's
