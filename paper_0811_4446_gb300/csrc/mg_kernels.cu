@@ -13,6 +13,7 @@
 // x = radial index (coalesced), y = axial index.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include <cstdio>
@@ -1071,9 +1072,14 @@ __global__ void __launch_bounds__(MAXT) k_zline_pcr(LevelT<T> L, int color) {
 // A level does the arithmetic of its own rows only, about 1/6 of the cyclic-reduction work over
 // the whole line.  Three lanes per row, lane rr owning row rr of every 3x3 block (its row of
 // D^-1 from the cofactors of column rr, det expanded along that column), keep the warps full
-// while the levels shrink.  Shared memory: 30 planes of the rows' current blocks [D | Lo | Up | r],
-// then 21 of [a | c | y]; the solution goes to the D planes once the forward pass is done.
-// 3 ceil(n / 2) threads (at least n: one per row assembles the system).
+// while the levels shrink; a level of at most kLineG9 rows takes nine lanes per row instead, one
+// per block entry, three rows to a warp (lanes 0 .. 26), the cofactors and the rows of D^-1
+// exchanged by shuffles: the chain of FP64 instructions one warp issues per level, which bounds
+// the small levels, is then half as long.  Shared memory: 30 planes of the rows' current blocks
+// [D | Lo | Up | r], then 21 of [a | c | y]; the solution goes to the D planes once the forward
+// pass is done.  Threads: 3 ceil(n / 2) (at least n: one per row assembles the system), and at
+// least a warp per three rows of the largest nine-lane level.
+constexpr int kLineG9 = 12;
 template <typename T, bool ZL>
 __global__ void __launch_bounds__(768, 1) k_line_cr(LevelT<T> L, int color) {
   extern __shared__ __align__(16) unsigned char lc_smem[];
@@ -1100,10 +1106,32 @@ __global__ void __launch_bounds__(768, 1) k_line_cr(LevelT<T> L, int color) {
   __syncthreads();
   const int g = tid / 3, rr = tid - 3 * g;
   const int c1 = rr == 2 ? 0 : rr + 1, c2 = rr == 0 ? 2 : rr - 1;  // (rr + 1) % 3, (rr + 2) % 3
+  // nine-lane layout: group g9 (three per warp), entry (r9, c9) of the row's blocks
+  const int lane = tid & 31, l9 = lane % 9;
+  const int g9 = lane < 27 ? (tid >> 5) * 3 + lane / 9 : 1 << 30;
+  const int r9 = l9 / 3, c9 = l9 - 3 * r9;
+  const int a1 = r9 == 2 ? 0 : r9 + 1, a2 = r9 == 0 ? 2 : r9 - 1;  // columns other than r9
+  const int k1 = c9 == 2 ? 0 : c9 + 1, k2 = c9 == 0 ? 2 : c9 - 1;  // rows other than c9
+  const int base9 = lane - c9;                                      // lane of entry (r9, 0)
   int h = 1;
   for (;; h <<= 1) {
     const int E = (n / h + 1) >> 1, Sv = n / (2 * h);
-    if (g < E) {
+    if (E <= kLineG9) {
+      const unsigned m9 = __ballot_sync(0xffffffffu, g9 < E);
+      if (g9 < E) {
+        const T *Su = S + h * (2 * g9 + 1) - 1;
+        T *Nu = N + h * (2 * g9 + 1) - 1;
+        // cofactor C[c9][r9]; det expanded along column r9 from the cofactors of lanes (r9, 0 .. 2)
+        const T Ck = Su[(3 * k1 + a1) * n] * Su[(3 * k2 + a2) * n] - Su[(3 * k1 + a2) * n] * Su[(3 * k2 + a1) * n];
+        const T C0 = __shfl_sync(m9, Ck, base9), C1 = __shfl_sync(m9, Ck, base9 + 1),
+                C2 = __shfl_sync(m9, Ck, base9 + 2);
+        const T e = Ck * (T(1) / (Su[r9 * n] * C0 + Su[(3 + r9) * n] * C1 + Su[(6 + r9) * n] * C2));
+        const T e0 = __shfl_sync(m9, e, base9), e1 = __shfl_sync(m9, e, base9 + 1), e2 = __shfl_sync(m9, e, base9 + 2);
+        Nu[(3 * r9 + c9) * n] = e0 * Su[(9 + c9) * n] + e1 * Su[(12 + c9) * n] + e2 * Su[(15 + c9) * n];
+        Nu[(9 + 3 * r9 + c9) * n] = e0 * Su[(18 + c9) * n] + e1 * Su[(21 + c9) * n] + e2 * Su[(24 + c9) * n];
+        if (c9 == 0) Nu[(18 + r9) * n] = e0 * Su[27 * n] + e1 * Su[28 * n] + e2 * Su[29 * n];
+      }
+    } else if (g < E) {
       const T *Su = S + h * (2 * g + 1) - 1;
       T *Nu = N + h * (2 * g + 1) - 1;
       const T d0a = Su[c1 * n], d1a = Su[(3 + c1) * n], d2a = Su[(6 + c1) * n];
@@ -1122,7 +1150,31 @@ __global__ void __launch_bounds__(768, 1) k_line_cr(LevelT<T> L, int color) {
     }
     __syncthreads();
     if (Sv == 0) break;
-    if (g < Sv) {
+    if (Sv <= kLineG9) {
+      const unsigned m9 = __ballot_sync(0xffffffffu, g9 < Sv);
+      if (g9 < Sv) {
+        const int u = 2 * h * (g9 + 1) - 1;
+        T *Su = S + u;
+        const T *Nm = N + (u - h);
+        const T L0 = Su[(9 + 3 * r9) * n], L1 = Su[(10 + 3 * r9) * n], L2 = Su[(11 + 3 * r9) * n];
+        const T U0 = Su[(18 + 3 * r9) * n], U1 = Su[(19 + 3 * r9) * n], U2 = Su[(20 + 3 * r9) * n];
+        T Dv = Su[(3 * r9 + c9) * n], r0 = Su[(27 + r9) * n], nU = T(0);
+        const T nL = -(L0 * Nm[c9 * n] + L1 * Nm[(3 + c9) * n] + L2 * Nm[(6 + c9) * n]);
+        Dv -= L0 * Nm[(9 + c9) * n] + L1 * Nm[(12 + c9) * n] + L2 * Nm[(15 + c9) * n];
+        r0 -= L0 * Nm[18 * n] + L1 * Nm[19 * n] + L2 * Nm[20 * n];
+        if (u + h < n) {
+          const T *Np = N + (u + h);
+          Dv -= U0 * Np[c9 * n] + U1 * Np[(3 + c9) * n] + U2 * Np[(6 + c9) * n];
+          nU = -(U0 * Np[(9 + c9) * n] + U1 * Np[(12 + c9) * n] + U2 * Np[(15 + c9) * n]);
+          r0 -= U0 * Np[18 * n] + U1 * Np[19 * n] + U2 * Np[20 * n];
+        }
+        __syncwarp(m9);  // the row's blocks are read by all nine lanes before any is overwritten
+        Su[(3 * r9 + c9) * n] = Dv;
+        Su[(9 + 3 * r9 + c9) * n] = nL;
+        Su[(18 + 3 * r9 + c9) * n] = nU;
+        if (c9 == 0) Su[(27 + r9) * n] = r0;
+      }
+    } else if (g < Sv) {
       const int u = 2 * h * (g + 1) - 1;
       T *Su = S + u;
       const T *Nm = N + (u - h);
@@ -1183,7 +1235,10 @@ __global__ void __launch_bounds__(768, 1) k_line_cr(LevelT<T> L, int color) {
 // shared memory and threads of the cyclic-reduction line kernel for a line of n unknowns
 template <typename T>
 __host__ __forceinline__ size_t line_cr_smem(int n) { return (size_t)51 * n * sizeof(T); }
-__host__ __forceinline__ int line_cr_threads(int n) { return (3 * ((n + 1) / 2) + 31) / 32 * 32; }
+__host__ __forceinline__ int line_cr_threads(int n) {
+  const int half = (n + 1) / 2;
+  return std::max((3 * half + 31) / 32 * 32, 32 * ((std::min(half, kLineG9) + 2) / 3));
+}
 
 template <typename T, bool ZL>
 cudaError_t launch_line_cr(const LevelT<T> &L, int lines, int color, int n, cudaStream_t st) {
