@@ -701,9 +701,12 @@ def measure_forms(args, dev, peaks):
     dl = W.make_discharge(256, seed=0, V_cathode=-300.0, use_table=True, R=0.1)
     line = {"workload": "257x257 nodes, R = 10 cm, d = 1 cm (dr = 10 dz), table transport, dt = 1e-7 s, "
                         "linear solve of one Newton system to 1e-8"}
+    # sweeps: the default tiers (V(4,4) above 65^2, V(2,2) to 65^2, V(1,1) to 9^2), or V(nu,nu)
+    # on every level above 9^2 (line sweeps cost more than point sweeps, and reduce more)
     for prec_name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
-        for name, ls in (("point", 0), ("z_line", 1)):
-            s = mg.from_discharge(dl, precision=prec, line_smoother=ls)
+        for name, ls, nu in (("point", 0, 0), ("z_line", 1, 0), ("z_line_v11", 1, 1), ("z_line_v22", 1, 2)):
+            sw = dict(nu1=nu, nu2=nu, nu_coarse1=nu, nu_coarse2=nu) if nu else {}
+            s = mg.from_discharge(dl, precision=prec, line_smoother=ls, **sw)
             s.autotune()
             F, _ = s.residual(1e-7)
             f = [-a for a in F]
@@ -728,8 +731,9 @@ def measure_forms(args, dev, peaks):
     rline = {"workload": "257x257 nodes, R = 2 mm, d = 1 cm (dz = 5 dr), table transport, dt = 1e-7 s, "
                          "linear solve of one Newton system to 1e-8"}
     for prec_name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
-        for name, ls in (("point", 0), ("r_line", 2), ("alternating", 3)):
-            s = mg.from_discharge(dr_, precision=prec, line_smoother=ls)
+        for name, ls, nu in (("point", 0, 0), ("r_line", 2, 0), ("alternating", 3, 0), ("alternating_v11", 3, 1)):
+            sw = dict(nu1=nu, nu2=nu, nu_coarse1=nu, nu_coarse2=nu) if nu else {}
+            s = mg.from_discharge(dr_, precision=prec, line_smoother=ls, **sw)
             s.autotune()
             F, _ = s.residual(1e-7)
             f = [-a for a in F]

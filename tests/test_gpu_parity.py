@@ -277,6 +277,37 @@ def test_line_smoother_linear_solve_parity(mg, n, R, table, precision, line):
         assert len(hg) * 2 < len(hp), (len(hg), len(hp))
 
 
+@pytest.mark.parametrize("n,R,line,nu,precision", [(64, 1e-1, 1, 1, "fp64"), (32, 2e-3, 3, 1, "fp64"),
+                                                  (64, 1e-1, 1, 2, "mixed"), (32, 2e-3, 2, 2, "fp64")])
+def test_line_smoother_sweep_counts_parity(mg, n, R, line, nu, precision):
+    """Line smoothing with V(1,1) or V(2,2) on every level above 9^2 (nu1 = nu2 = nu_coarse1 =
+    nu_coarse2 = nu), the sweep counts of the benchmark's faster line-smoothed solves: the
+    oracle with the same sweep counts, its residual history cycle by cycle (FP64) and its
+    solution per field (FP64 1e-10, mixed 1e-8)."""
+    d = W.make_discharge(n, seed=0, V_cathode=-300.0, use_table=True, R=R)
+    g, phys = _oracle(d)
+    u = np.stack([d.ne0, d.np0, d.V0])
+    dt = 1e-7
+    F, T = disc.residual(g, u, u * 0.99, d.S_e, d.S_p, dt, phys, with_terms=True)
+    tn = np.array([np.linalg.norm(T[k, 1:-1]) for k in range(3)])
+    sw = dict(nu1=nu, nu2=nu, nu_coarse1=nu, nu_coarse2=nu)
+    prec = mg.MG_MIXED if precision == "mixed" else mg.MG_FP64
+    s = mg.from_discharge(d, precision=prec, line_smoother=line, **sw)
+    s.set_old_state(*[np.ascontiguousarray(a * 0.99) for a in u])
+    eta = 1e-12 if precision == "fp64" else 1e-10
+    xg, hg, rc = s.linear_solve(dt, list(-F), eta, 200)
+    assert rc == mg.MG_OK
+    H = omg.Hierarchy(g, u, dt, phys, line={1: "z", 2: "r", 3: "alt"}[line], **sw)
+    x, ho = H.solve(disc.to_vec(g, -F), eta, 200, scale=tn)
+    _assert_fields(xg, disc.from_vec(g, x), FP64_TOL if precision == "fp64" else MIXED_TOL, (n, line, nu))
+    if precision == "fp64":
+        assert abs(len(hg) - len(ho)) <= 1
+        k = min(len(hg), len(ho), 6)
+        assert np.allclose(hg[:k], ho[:k], rtol=1e-5, atol=1e-14)
+    else:
+        assert len(hg) <= len(ho) + 3
+
+
 @pytest.mark.parametrize("nr,nz,table,precision,line", [(64, 16, False, "fp64", 0), (16, 64, True, "fp64", 0),
                                                        (128, 32, True, "fp64", 0), (32, 128, False, "mixed", 0),
                                                        (64, 16, True, "mixed", 0), (32, 64, True, "fp64", 1),
