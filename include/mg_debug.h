@@ -54,6 +54,15 @@ int mg_time_smoother(mg_state *s, int level, int precision, int sweeps, double *
 typedef struct mg_unet mg_unet;
 int mg_unet_set_graphs(mg_unet *n, int on);
 
+/* The network's activations after its last forward pass, for per-layer tests: which = 0 the
+ * input (8 channels, bf16), 1 .. 11 the outputs of e0a, e0b, e1a, e1b, e2a, e2b, e3a, e3b, d2,
+ * d1, d0 (after ReLU), 12 .. 14 the node-aligned upsampled inputs of d2, d1, d0 (from e3b, d2,
+ * d1).  hwc (3 ints, may be NULL) receives the layer's grid nodes H, W and channels C; out
+ * (host, may be NULL for the sizes alone) receives the bit patterns of the B x H x W x C bf16
+ * values, NHWC.  Synchronises the stream.  MG_EINVAL for a bad index or B outside
+ * 1 .. batch_max; MG_ECUDA on a CUDA error. */
+int mg_unet_get_activation(mg_unet *n, int which, int B, uint16_t *out, int *hwc);
+
 #ifdef __cplusplus
 }
 #endif

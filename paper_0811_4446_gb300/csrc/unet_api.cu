@@ -640,6 +640,18 @@ int mg_unet_set_graphs(mg_unet *n, int on) {
   return MG_OK;
 }
 
+int mg_unet_get_activation(mg_unet *n, int which, int B, uint16_t *out, int *hwc) {
+  if (!n || which < 0 || which > 14 || B < 1 || B > n->Bmax) return MG_EINVAL;
+  const Act *all[] = {&n->x,   &n->e0a, &n->e0b, &n->e1a, &n->e1b, &n->e2a, &n->e2b, &n->e3a,
+                      &n->e3b, &n->d2,  &n->d1,  &n->d0,  &n->u3,  &n->u2,  &n->u1};
+  const Act &t = *all[which];
+  if (hwc) { hwc[0] = t.H; hwc[1] = t.W; hwc[2] = t.C; }
+  if (!out) return MG_OK;
+  UK(cudaMemcpyAsync(out, t.a, t.elems(B) * sizeof(__nv_bfloat16), cudaMemcpyDeviceToHost, n->st));
+  UK(cudaStreamSynchronize(n->st));
+  return MG_OK;
+}
+
 int mg_unet_set_tensor_path(mg_unet *n, int path) {
   if (!n || path < 0 || path > 3) return MG_EINVAL;
   if (path != n->use_tc) {

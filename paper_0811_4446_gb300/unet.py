@@ -34,6 +34,7 @@ SIGNATURES = {
     "mg_unet_train_step": (_i, [_vp, _vp, _vp, _i, _f, _c.POINTER(_d), _i]),
     "mg_unet_set_tensor_path": (_i, [_vp, _i]),
     "mg_unet_set_graphs": (_i, [_vp, _i]),
+    "mg_unet_get_activation": (_i, [_vp, _i, _i, _vp, _c.POINTER(_i)]),
 }
 
 WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
@@ -102,6 +103,16 @@ class UNet:
         """Launch mode (mg_unet_set_graphs in include/mg_debug.h): CUDA graphs (default) or
         launch by launch, for kernel profilers."""
         self._check(self.lib.mg_unet_set_graphs(self.h, int(bool(on))))
+
+    def activation(self, which: int, B: int) -> np.ndarray:
+        """A layer's bf16 activations after the last forward pass (mg_unet_get_activation in
+        include/mg_debug.h), as float32 (B, H, W, C): 0 the input, 1 .. 11 the outputs of e0a ..
+        d0, 12 .. 14 the upsampled inputs of d2, d1, d0."""
+        hwc = (_i * 3)()
+        self._check(self.lib.mg_unet_get_activation(self.h, int(which), int(B), None, hwc))
+        bits = np.empty((B, hwc[0], hwc[1], hwc[2]), np.uint16)
+        self._check(self.lib.mg_unet_get_activation(self.h, int(which), int(B), bits.ctypes.data, hwc))
+        return (bits.astype(np.uint32) << 16).view(np.float32)
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32) if isinstance(p, np.ndarray) else p

@@ -66,6 +66,55 @@ def test_forward_matches_oracle(un):
         assert np.abs(y[..., c] - yo[..., c]).max() <= 2e-2 * scale, c
 
 
+@pytest.mark.parametrize("B,n", [(2, 40), (1, 32), (3, 64)])
+def test_each_layer_matches_oracle_element_by_element(un, B, n):
+    """Every layer of the default forward path (the tcgen05 halo and TMA-tile convolutions, the
+    node-aligned upsampling, the CUDA-core 1x1 head) against the FP64 oracle applied to the
+    GPU's own bf16 inputs of that layer and to the bf16 weights, element by element, so that no
+    error carries over from earlier layers.  A 3x3 layer's output is bf16(ReLU(sum + bias)), the
+    sum of its K exact bf16 products accumulated in FP32: it may differ from the FP64 value by
+    the bf16 rounding (2^-8 of the value, allowing a rounding to the neighbour) plus the FP32
+    accumulation error (at most K 2^-23 of the sum of the terms' magnitudes, any order, round or
+    truncate).  n = 40 (41 x 41 nodes) leaves partial tiles on every level (41, 21, 11, 6 nodes)."""
+    p, x, _ = _setup(un, seed=3, B=B, n=n)
+    net = un.UNet(B, n)
+    net.set_params(p)
+    y = net.forward(x)
+    A = [net.activation(k, B).astype(np.float64) for k in range(15)]
+    net.close()
+    xb = _bf16(x)
+    assert np.abs(A[0] - xb).max() <= 2.0 ** -8 * np.abs(xb).max()
+    assert np.all(A[0][..., 5:] == 0.0)
+    names = ["e0a", "e0b", "e1a", "e1b", "e2a", "e2b", "e3a", "e3b", "d2", "d1", "d0"]
+    outs = {name: A[i + 1] for i, name in enumerate(names)}
+    outs["head"] = y.astype(np.float64)
+    ins = {"e0a": A[0], "e0b": A[1], "e1a": A[2], "e1b": A[3], "e2a": A[4], "e2b": A[5], "e3a": A[6],
+           "e3b": A[7], "d2": np.concatenate([A[12], A[6]], axis=3), "d1": np.concatenate([A[13], A[4]], axis=3),
+           "d0": np.concatenate([A[14], A[2]], axis=3), "head": A[11]}
+    po = ou.unflatten(torch.from_numpy(p.astype(np.float64)))
+    nchw = lambda a: torch.from_numpy(np.ascontiguousarray(a)).permute(0, 3, 1, 2)
+    for name, k, stride, ci, co, relu in ou.LAYERS:
+        xi = nchw(ins[name])
+        assert xi.shape[1] == ci, name
+        w = torch.from_numpy(_bf16(po[name + ".w"].numpy()))
+        b = po[name + ".b"]
+        z = ou.conv(xi, w, b, stride)
+        mag = ou.conv(xi.abs(), w.abs(), b.abs(), stride).permute(0, 2, 3, 1).numpy()
+        ref = (torch.relu(z) if relu else z).permute(0, 2, 3, 1).numpy()
+        got = outs[name]
+        assert got.shape == ref.shape, (name, got.shape, ref.shape)
+        K = k * k * ci + 1
+        tol = (2.0 ** -8 if relu else 0.0) * np.abs(ref) + K * 2.0 ** -23 * mag + 1e-30
+        worst = (np.abs(got - ref) / tol).max()
+        assert worst <= 1.0, (name, worst)
+        assert np.abs(ref).max() > 0, name
+    # the upsampled inputs of the decoder: bf16 of the bilinear interpolation of bf16 values
+    for ui, src in ((12, 8), (13, 9), (14, 10)):
+        ref = ou.upsample_nodes(nchw(A[src])).permute(0, 2, 3, 1).numpy()
+        assert A[ui].shape == ref.shape
+        assert np.all(np.abs(A[ui] - ref) <= 2.0 ** -8 * np.abs(ref)), ui
+
+
 def test_gradients_match_oracle(un):
     p, x, t = _setup(un, seed=2)
     net = un.UNet(2, 32)
