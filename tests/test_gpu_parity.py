@@ -930,6 +930,28 @@ def test_batched_steady_solves_equal_individual_solves(mg):
         assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE)
 
 
+def test_batched_line_smoothed_solves_fall_back_and_equal_individual_solves(mg):
+    """Line-smoothed states (z-lines, r-lines, alternating lines) are outside the persistent
+    launch: a batch of them asked for the persistent form (workers = 0) runs as host threads,
+    the line kernels launched from several threads at once.  Each discharge's FP64 steady solve
+    equals its individual solve bit for bit, and the oracle's steady residual of the result
+    meets the tolerance."""
+    ds = W.batch_64(seed=4, count=6, sizes=(16, 32, 64))
+    lines = [1, 2, 3, 3, 2, 1]
+    solvers = [mg.from_discharge(d, line_smoother=ls, stream=torch.cuda.Stream()) for d, ls in zip(ds, lines)]
+    rc, ms, rcs = mg.solve_steady_batch(solvers, 1e-8, workers=0)
+    assert rc == mg.MG_OK, rcs
+    for d, ls, sb in zip(ds, lines, solvers):
+        si = mg.from_discharge(d, line_smoother=ls)
+        assert si.solve_steady(1e-8)[0] == mg.MG_OK
+        a, b = sb.get_state(), si.get_state()
+        for q in range(3):
+            assert np.array_equal(a[q], b[q]), (d.nr, ls, q)
+        g, phys = _oracle(d)
+        F, T = disc.residual(g, np.stack(a), None, d.S_e, d.S_p, None, phys, with_terms=True)
+        assert disc.rho(F, T).max() <= 1e-8 * (1 + RHO_AGREE), (d.nr, ls)
+
+
 def test_autotune_keeps_results(mg):
     d = W.make_discharge(128, seed=3, V_cathode=-300.0, use_table=True)
     res = []
