@@ -1069,8 +1069,8 @@ __global__ void __launch_bounds__(MAXT) k_zline_pcr(LevelT<T> L, int color) {
 // q = 2h (g + 1) fold in their neighbours q -+ h exactly as a round of parallel cyclic reduction
 // does, so their couplings move 2h rows away; the level whose rows have no survivor left is
 // decoupled (x = y).  Back substitution from the top level down: x_q = y_q - a_q x_{q-h} - c_q x_{q+h}.
-// A level does the arithmetic of its own rows only, about 1/6 of the cyclic-reduction work over
-// the whole line.  Three lanes per row, lane rr owning row rr of every 3x3 block (its row of
+// Every row is eliminated once, at its own level: over the whole line about a sixth of the
+// arithmetic of parallel cyclic reduction, where every row works in every round.  Three lanes per row, lane rr owning row rr of every 3x3 block (its row of
 // D^-1 from the cofactors of column rr, det expanded along that column), keep the warps full
 // while the levels shrink; a level of at most kLineG9 rows takes nine lanes per row instead, one
 // per block entry, three rows to a warp (lanes 0 .. 26), the cofactors and the rows of D^-1
