@@ -370,13 +370,16 @@ def test_line_smoother_1023_row_columns_mixed(mg):
 
 @pytest.mark.parametrize("nr,nz,line,wall,R,precision", [
     (64, 512, 1, False, 1e-2, "fp64"), (256, 32, 2, False, 1e-2, "fp64"), (512, 64, 2, True, 2.7e-2, "fp64"),
-    (512, 64, 2, True, 2.7e-2, "mixed")])
+    (512, 64, 2, True, 2.7e-2, "mixed"), (128, 1024, 1, False, 1e-2, "fp64")])
 def test_longest_lines_linear_solve_parity(mg, nr, nz, line, wall, R, precision):
     """Line smoothing at the longest lines the line kernels take: z-lines of 511 rows (65 x 513
     nodes), r-lines of 257 unknowns, and r-lines of 512 unknowns (513 x 65 nodes with the
     Dirichlet wall, whose column is not an unknown).  In FP64 these run the block
     cyclic-reduction kernel at its largest launch (768 threads, 51 planes of 512 values in
-    shared memory).  Both sides solve to a relative residual of 1e-12; the oracle's residual
+    shared memory); FP64 columns of 1,023 rows (129 x 1025 nodes) are longer than that kernel
+    takes and run the thread-per-column block elimination on the finest level (the coarser
+    levels' 511-row columns the cyclic reduction).  Both sides solve to a relative residual of
+    1e-12; the oracle's residual
     history cycle by cycle, the cycle count within one, and the solution per field (FP64 1e-10,
     mixed 1e-8).  The wall case takes R = 2.7 cm: with R = 1 cm (dz = 8 dr) the oracle's r-line
     solves level off near 1e-11."""
